@@ -1,0 +1,420 @@
+"""Oracle: one time step of the non-planar spectral BIEM, plain FP64 on the CPU.
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import this
+package; only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` use it.
+
+The step follows Sec. 3.3 in the paper's order (after Lapusta et al. 2000):
+
+  (1) slip and state prediction with the pass velocity Vbar,
+  (2) tractions from the spectral formulas of Sec. 3.1 with the history
+      integral over [dt, T_w] and the current interval [0, dt],
+      midpoint quadrature of the kernels,
+  (3) rate-and-state momentum balance (Eq. momentum) solved per element for V,
+  then the same three steps again with Vbar = (V + V1)/2, and the history of
+  the slip rate spectrum is extended with that averaged value.
+
+Readings taken where the paper is silent or garbled (each is listed, with its
+reason, in the design notes of the repository):
+
+* radiation damping -mu/(2 c_s) V is added to the shear traction explicitly
+  (Sec. 2.3 states that the kernel contains it; the spectral form has none);
+* the normal traction is compression-positive and carries the odd factor
+  -i sgn(k) under F[f]_n = sum_i f_i exp(-i k_n x_i); it is zero at k = 0 and
+  at the Nyquist mode;
+* k_c = 200/(eta L) in rad/m by default; windows M_n = ceil(T_w(k_n)/dt_min);
+* quadrature weights w_{n,j} = dt_min * C(k_n, (j+1/2) dt_min), j = 0..M_n-1;
+* the state variable follows the aging law integrated exactly at constant
+  Vbar over the step (Lapusta et al. 2000); the explicit form of Sec. 3.3
+  (theta + thetadot dt) is an option;
+* a step of length dt = m dt_min (m >= 1 integer) advances the history by m
+  slots; its current interval takes the sum of the first m weights.
+
+FFTs are numpy's (a library primitive); the operators applied per mode are
+translation invariant, so the index-based DFT equals the one over x_i.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .kernels import G_N, G_T
+
+__all__ = ["Params", "windows", "weights", "Oracle", "newton_lnV", "state_update",
+           "STATUS_OK", "STATUS_NEWTON", "STATUS_OPENING", "STATUS_STATE"]
+
+STATUS_OK = 0
+STATUS_NEWTON = 1      # Newton did not converge within the cap
+STATUS_OPENING = 2     # sigma_load + sigma_el <= 0 (Sec. 3.2, failure conditions)
+STATUS_STATE = 4       # theta <= 0 (explicit state update only)
+
+
+@dataclass
+class Params:
+    """Material, grid and truncation parameters (Table 1 names)."""
+    N: int
+    dx: float
+    mu: float
+    cs: float
+    cp: float
+    dt_min: float                 # beta_min * dx / cs (Sec. 3.2)
+    eta_w: float = 1.0            # truncation parameter eta (Sec. 3.1)
+    kc_L: float = 200.0           # k_c * (eta * L) (Sec. 3.1)
+    kc_units: str = "rad"         # "rad": k_c in rad/m; "cycles": k_c in cycles/m
+    state_law: str = "analytic"   # "analytic" aging at constant Vbar, or "explicit"
+    newton_tol: float = 1e-13
+    newton_maxit: int = 200
+
+    @property
+    def L(self) -> float:
+        return self.N * self.dx
+
+    @property
+    def r(self) -> float:
+        return self.cs / self.cp
+
+    @property
+    def S(self) -> float:
+        """Static mode-II stiffness factor mu (1 - c_s^2/c_p^2) (Sec. 2.3)."""
+        return self.mu * (1.0 - self.r ** 2)
+
+    @property
+    def eta_rd(self) -> float:
+        """Radiation damping coefficient mu / (2 c_s) (Sec. 2.3)."""
+        return self.mu / (2.0 * self.cs)
+
+
+def wavenumbers(p: Params) -> np.ndarray:
+    """k_n = 2 pi n / L for n = 0..N/2 (rad/m)."""
+    return 2.0 * np.pi * np.arange(p.N // 2 + 1) / p.L
+
+
+def windows(p: Params) -> np.ndarray:
+    """Number of dt_min intervals M_n covering the truncation window T_w(k_n) (Sec. 3.1).
+
+    T_w = eta L / c_s for k <= k_c and (eta L / c_s)(k_c / k) above.  M_n is
+    the ceiling of T_w / dt_min, taken with a relative slack of 1e-12 so that
+    an exact integer ratio is not pushed up by rounding.  Mode 0 has no
+    traction (|k| = 0) and gets M_0 = 0.
+    """
+    k = wavenumbers(p)
+    Omega = p.L
+    kc = p.kc_L / (p.eta_w * Omega)
+    if p.kc_units == "cycles":
+        kc = 2.0 * np.pi * kc
+    elif p.kc_units != "rad":
+        raise ValueError("kc_units must be 'rad' or 'cycles'")
+    Tw = np.where(k <= kc, p.eta_w * Omega / p.cs, 0.0)
+    above = k > kc
+    Tw[above] = (p.eta_w * Omega / p.cs) * (kc / k[above])
+    M = np.ceil(Tw / p.dt_min * (1.0 - 1e-12)).astype(np.int64)
+    M[0] = 0
+    return M
+
+
+def weights(p: Params, M: np.ndarray | None = None):
+    """Midpoint weights w_{n,j} = dt_min * C(k_n, (j + 1/2) dt_min), j = 0..M_n-1 (Sec. 3.3).
+
+    Returns (wT, wN, offsets): flat arrays with mode n occupying
+    [offsets[n], offsets[n+1]).
+    """
+    if M is None:
+        M = windows(p)
+    k = wavenumbers(p)
+    offsets = np.zeros(M.size + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(M)
+    mode = np.repeat(np.arange(M.size), M)
+    j = np.arange(offsets[-1]) - offsets[mode]
+    s = p.cs * k[mode] * (j + 0.5) * p.dt_min
+    wT = p.dt_min * G_T(s, p.r)
+    wN = p.dt_min * G_N(s, p.r)
+    return wT, wN, offsets
+
+
+def state_update(theta0, Vbar, thetadot_bar, Dc, dt, law: str):
+    """Predicted state theta_p over one step (Sec. 3.3 step (1)).
+
+    analytic: aging law d theta/dt = 1 - theta V / Dc integrated exactly at
+              constant V = Vbar (Lapusta et al. 2000);
+    explicit: theta0 + thetadot_bar * dt, as printed in Sec. 3.3.
+    """
+    if law == "analytic":
+        # theta0 e^{-u} + (Dc/Vbar)(1 - e^{-u}), u = Vbar dt / Dc, written as
+        # theta0 e^{-u} + dt (1 - e^{-u})/u so that Vbar -> 0 gives theta0 + dt
+        u = np.asarray(Vbar * dt / Dc, dtype=np.float64)
+        phi = np.ones_like(u)
+        nz = u > 0
+        phi[nz] = -np.expm1(-u[nz]) / u[nz]
+        return theta0 * np.exp(-u) + dt * phi
+    if law == "explicit":
+        return theta0 + thetadot_bar * dt
+    raise ValueError("state law must be 'analytic' or 'explicit'")
+
+
+def newton_lnV(tau, sigma, theta, a, b, Dc, f0, V0, eta, x_start, tol, maxit):
+    """Solve Eq. (momentum) with radiation damping for x = ln V, per element.
+
+    g(x) = tau - eta e^x - sigma [f0 + a (x - ln V0) + b ln(theta V0 / Dc)] = 0.
+    For sigma > 0 and a > 0, g is strictly decreasing, so the root is unique.
+    The quasi-static root x_qs (eta = 0) bounds it from above; a lower bound is
+    found by stepping down until g >= 0.  Newton steps that leave the bracket
+    are replaced by bisection.  Returns (x, iterations, converged mask).
+    """
+    psi_term = b * (np.log(theta) + np.log(V0 / Dc))
+    lnV0 = np.log(V0)
+
+    def g(x):
+        return tau - eta * np.exp(x) - sigma * (f0 + a * (x - lnV0) + psi_term)
+
+    hi = lnV0 + (tau / sigma - f0 - psi_term) / a
+    hi = np.minimum(hi, 700.0)
+    lo = hi - 1.0
+    step = 1.0
+    for _ in range(80):
+        bad = g(lo) < 0
+        if not bad.any():
+            break
+        step *= 2.0
+        lo = np.where(bad, hi - step, lo)
+    x = np.clip(x_start, lo, hi)
+    conv = np.zeros(x.shape, dtype=bool)
+    iters = np.zeros(x.shape, dtype=np.int64)
+    for it in range(maxit):
+        gx = g(x)
+        lo = np.where(gx > 0, x, lo)
+        hi = np.where(gx <= 0, x, hi)
+        e = eta * np.exp(x)
+        q = gx + e                      # tau - sigma F(x), linear in x
+        # Newton on g where friction dominates; where radiation damping
+        # dominates (q > sigma a, so that h' lies in (1, 2)) Newton on
+        # h(x) = x - ln(q(x)/eta), which has the same root and is nearly
+        # linear there.
+        rad = q > sigma * a
+        xg = x - gx / (-e - sigma * a)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xh = x - (x - np.log(np.where(rad, q, 1.0) / eta)) / (1.0 + sigma * a / np.where(rad, q, 1.0))
+        xn = np.where(rad, xh, xg)
+        # a step below the tolerance is accepted as converged even when
+        # rounding puts it a hair outside the bracket
+        small = np.abs(xn - x) <= tol
+        outside = ((xn < lo) | (xn > hi)) & ~small
+        xn = np.where(outside, 0.5 * (lo + hi), xn)
+        dx = np.abs(xn - x)
+        iters = np.where(conv, iters, it + 1)
+        x = np.where(conv, x, xn)
+        conv = conv | (dx <= tol)
+        if conv.all():
+            break
+    return x, iters, conv
+
+
+@dataclass
+class Oracle:
+    """Fault state and history of the plain FP64 spectral BIEM (Sec. 3)."""
+    p: Params
+    kappa: np.ndarray
+    a: np.ndarray
+    b: np.ndarray
+    Dc: np.ndarray
+    f0: float
+    V0: float
+    sigma_load: np.ndarray
+    tau_load: np.ndarray
+    V: np.ndarray
+    theta: np.ndarray
+    tau_load_rate: np.ndarray | None = None
+    prescribed: np.ndarray | None = None
+    V_presc: np.ndarray | None = None
+    delta: np.ndarray | None = None
+    t: float = 0.0
+    steps: int = 0
+    thetadot: np.ndarray | None = field(default=None)
+
+    def __post_init__(self):
+        p = self.p
+        N = p.N
+        if N % 2:
+            raise ValueError("N must be even")
+        f = lambda v, fill: (np.full(N, fill, dtype=np.float64) if v is None
+                             else np.array(v, dtype=np.float64).reshape(N))
+        self.kappa = f(self.kappa, 0.0)
+        self.a, self.b, self.Dc = f(self.a, 0), f(self.b, 0), f(self.Dc, 1)
+        self.sigma_load = f(self.sigma_load, 0)
+        equilibrium = self.tau_load is None
+        self.tau_load = f(self.tau_load, 0)
+        self.tau_load_rate = f(self.tau_load_rate, 0.0)
+        self.V, self.theta = f(self.V, 0), f(self.theta, 1)
+        self.delta = f(self.delta, 0.0)
+        self.prescribed = (np.zeros(N, dtype=bool) if self.prescribed is None
+                           else np.asarray(self.prescribed, dtype=bool).reshape(N))
+        self.V_presc = f(self.V_presc, 0.0)
+        self.V = np.where(self.prescribed, self.V_presc, self.V)
+        if self.thetadot is None:
+            self.thetadot = 1.0 - self.theta * self.V / self.Dc
+        if equilibrium:
+            # loading in equilibrium with the initial state (Eq. momentum with
+            # radiation damping and zero elastic change at t = 0)
+            fr = (self.f0 + self.a * np.log(self.V / self.V0)
+                  + self.b * np.log(self.theta * self.V0 / self.Dc))
+            self.tau_load = np.where(self.prescribed, 0.0,
+                                     self.sigma_load * fr + p.eta_rd * self.V)
+        self.k = wavenumbers(p)
+        self.M = windows(p)
+        self.wT, self.wN, self.woff = weights(p, self.M)
+        # history: mode n keeps R_n = M_n - 1 past spectra; lag j (>= 1) of
+        # mode n sits at ring slot (head_n + j - 1) mod R_n.
+        self.R = np.maximum(self.M - 1, 0)
+        self.hoff = np.zeros(self.R.size + 1, dtype=np.int64)
+        self.hoff[1:] = np.cumsum(self.R)
+        self.hist_T = np.zeros(self.hoff[-1], dtype=np.complex128)
+        self.hist_N = np.zeros(self.hoff[-1], dtype=np.complex128)
+        self.head = np.zeros(self.R.size, dtype=np.int64)
+        self.last = {}
+
+    # ------------------------------------------------------------------ history
+    def history_slot(self, n: int, lag: int) -> int:
+        """Flat index of lag ``lag`` (>= 1) of mode n."""
+        return int(self.hoff[n] + (self.head[n] + lag - 1) % self.R[n])
+
+    def set_history(self, HT: list, HN: list) -> None:
+        """Load history: HT[n][i] is the spectrum of lag i+1 (newest first)."""
+        for n in range(self.R.size):
+            Rn = int(self.R[n])
+            self.head[n] = 0
+            self.hist_T[self.hoff[n]:self.hoff[n] + Rn] = np.asarray(HT[n], np.complex128)[:Rn]
+            self.hist_N[self.hoff[n]:self.hoff[n] + Rn] = np.asarray(HN[n], np.complex128)[:Rn]
+
+    def get_history(self):
+        """History as lists of per-mode arrays, newest first."""
+        HT, HN = [], []
+        for n in range(self.R.size):
+            Rn = int(self.R[n])
+            idx = self.hoff[n] + (self.head[n] + np.arange(Rn)) % max(Rn, 1)
+            HT.append(self.hist_T[idx].copy())
+            HN.append(self.hist_N[idx].copy())
+        return HT, HN
+
+    def history_sums(self, m: int = 1):
+        """A^X_n = sum_{j=m}^{M_n-1} w^X_{n,j} H^X_n[j-m]: the integral over [m dt_min, T_w].
+
+        Sums run over j in ascending order, mode by mode.
+        """
+        nm = self.R.size
+        AT = np.zeros(nm, dtype=np.complex128)
+        AN = np.zeros(nm, dtype=np.complex128)
+        for n in range(1, nm):
+            Mn, Rn = int(self.M[n]), int(self.R[n])
+            if Mn <= m:
+                continue
+            j = np.arange(m, Mn)
+            idx = self.hoff[n] + (self.head[n] + (j - m)) % Rn
+            AT[n] = np.sum(self.wT[self.woff[n] + j] * self.hist_T[idx])
+            AN[n] = np.sum(self.wN[self.woff[n] + j] * self.hist_N[idx])
+        return AT, AN
+
+    def current_weights(self, m: int = 1):
+        """Weight of the current interval [0, m dt_min]: sum of the first m weights."""
+        nm = self.R.size
+        w0T = np.zeros(nm)
+        w0N = np.zeros(nm)
+        for n in range(1, nm):
+            Mn = int(self.M[n])
+            j = np.arange(min(m, Mn))
+            w0T[n] = np.sum(self.wT[self.woff[n] + j])
+            w0N[n] = np.sum(self.wN[self.woff[n] + j])
+        return w0T, w0N
+
+    def push(self, UT: np.ndarray, UN: np.ndarray, m: int = 1) -> None:
+        """Extend every ring by m copies of this step's spectra (Sec. 3.3, last paragraph)."""
+        for n in range(1, self.R.size):
+            Rn = int(self.R[n])
+            if Rn == 0:
+                continue
+            for _ in range(min(m, Rn)):
+                self.head[n] = (self.head[n] - 1) % Rn
+                self.hist_T[self.hoff[n] + self.head[n]] = UT[n]
+                self.hist_N[self.hoff[n] + self.head[n]] = UN[n]
+            if m > Rn:
+                # the ring now holds Rn copies; the head position is still
+                # defined as m pushes from the start
+                self.head[n] = (self.head[n] - (m - Rn)) % Rn
+
+    # -------------------------------------------------------------- tractions
+    def tractions(self, delta_p, Vbar, AT, AN, w0T, w0N):
+        """Elastic shear and normal traction changes (Sec. 3.1 and Sec. 3.3 step (2))."""
+        p = self.p
+        kap = self.kappa
+        U = np.fft.rfft(Vbar)              # F[Vbar]
+        Q = np.fft.rfft(kap * Vbar)        # F[kappa Vbar]
+        D = np.fft.rfft(delta_p)           # F[delta_p]
+        K = np.fft.rfft(kap * delta_p)     # F[kappa delta_p]
+        absk = self.k
+        tau_hat = -p.S * absk * D - p.mu * absk * (AT + w0T * U)
+        sgn = np.ones_like(absk)
+        sgn[0] = 0.0
+        sgn[-1] = 0.0                      # Nyquist: odd operator has no real representation
+        sig_hat = -1j * sgn * (p.S * K + p.mu * (AN + w0N * Q))
+        tau_el = np.fft.irfft(tau_hat, n=p.N)
+        sig_el = np.fft.irfft(sig_hat, n=p.N)
+        return tau_el, sig_el, U, Q
+
+    # ---------------------------------------------------------------- the step
+    def _pass(self, Vbar, thetadot_bar, dt, t_end, AT, AN, w0T, w0N):
+        p = self.p
+        delta_p = self.delta + Vbar * dt
+        theta_p = state_update(self.theta, Vbar, thetadot_bar, self.Dc, dt, p.state_law)
+        status = STATUS_OK
+        if np.any(theta_p <= 0):
+            status |= STATUS_STATE
+        tau_el, sig_el, U, Q = self.tractions(delta_p, Vbar, AT, AN, w0T, w0N)
+        tau = self.tau_load + self.tau_load_rate * t_end + tau_el
+        sigma = self.sigma_load + sig_el
+        free = ~self.prescribed
+        if np.any(sigma[free] <= 0):
+            status |= STATUS_OPENING
+        Vnew = self.V_presc.copy()
+        iters = np.zeros(p.N, dtype=np.int64)
+        if free.any() and not (status & (STATUS_OPENING | STATUS_STATE)):
+            x, it, conv = newton_lnV(tau[free], sigma[free], theta_p[free], self.a[free],
+                                     self.b[free], self.Dc[free], self.f0, self.V0, p.eta_rd,
+                                     np.log(self.V[free]), p.newton_tol, p.newton_maxit)
+            if not conv.all():
+                status |= STATUS_NEWTON
+            Vnew[free] = np.exp(x)
+            iters[free] = it
+        thetadot_new = 1.0 - theta_p * Vnew / self.Dc
+        return dict(V=Vnew, theta=theta_p, thetadot=thetadot_new, delta=delta_p,
+                    tau_el=tau_el, sig_el=sig_el, U=U, Q=Q, status=status, iters=iters)
+
+    def step(self, m: int = 1) -> int:
+        """Advance by dt = m * dt_min; returns a status bitmask (0 on success).
+
+        On failure the state is left unchanged.
+        """
+        if m < 1:
+            raise ValueError("m >= 1")
+        dt = m * self.p.dt_min
+        t_end = self.t + dt
+        AT, AN = self.history_sums(m)
+        w0T, w0N = self.current_weights(m)
+        r1 = self._pass(self.V, self.thetadot, dt, t_end, AT, AN, w0T, w0N)
+        if r1["status"]:
+            self.last = r1
+            return r1["status"]
+        Vbar = 0.5 * (self.V + r1["V"])
+        thd_bar = 0.5 * (self.thetadot + r1["thetadot"])
+        r2 = self._pass(Vbar, thd_bar, dt, t_end, AT, AN, w0T, w0N)
+        if r2["status"]:
+            self.last = r2
+            return r2["status"]
+        self.delta = r2["delta"]
+        self.V = r2["V"]
+        self.theta = r2["theta"]
+        self.thetadot = r2["thetadot"]
+        self.push(r2["U"], r2["Q"], m)
+        self.t = t_end
+        self.steps += 1
+        r2["pass1"] = r1
+        self.last = r2
+        return STATUS_OK

@@ -1,0 +1,258 @@
+"""Pins for the oracle's time step (Sec. 3), each against an independent fact.
+
+* static stiffness vs the textbook mu/(2(1-nu)) and Table 1's nucleation lengths;
+* uniform slip rate: no elastic shear change (only k = 0 is excited);
+* flat fault: the normal traction change vanishes bitwise;
+* a single Fourier mode of prescribed slip rate: closed form of the
+  static + truncated dynamic response, which fixes the lag/weight indexing;
+* truncation: a slip pulse is forgotten after the window;
+* tiny N: a brute-force space-time double sum with real-space kernels equals
+  the spectral step (FFT plumbing, sgn(k), Nyquist);
+* Newton vs plain bisection on the same residual;
+* aging law: steady state is a fixed point; explicit and exact updates agree
+  to second order;
+* the sign of the normal traction: the slip/curvature scaling law of Sec. 5.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, Params, newton_lnV, state_update
+from oracle.kernels import G_N, G_T
+from oracle.sbiem import windows
+from paper_2107_03550_gb300.workloads import element_x, rough_fault, seamount_rupture
+from tests.golden.paper import paper_numbers
+
+
+def _params(N=64, dx=25.0, kc_L=200.0, mu=30e9, cs=3464.0, cp=None):
+    cp = cp or np.sqrt(3.0) * cs
+    return Params(N=N, dx=dx, mu=mu, cs=cs, cp=cp, dt_min=0.25 * dx / cs, kc_L=kc_L)
+
+
+def _prescribed_oracle(p, kappa, V):
+    N = p.N
+    return Oracle(p, kappa, np.full(N, 0.01), np.full(N, 0.015), np.full(N, 1e-3), 0.6, 1e-6,
+                  np.full(N, 50e6), np.zeros(N), V.copy(), np.full(N, 1.0),
+                  prescribed=np.ones(N, dtype=bool), V_presc=V.copy())
+
+
+def test_static_stiffness_and_table1_lengths():
+    pn = paper_numbers()
+    mu, cs, cp = pn["table1_mu"], pn["table1_cs"], pn["table1_cp"]
+    p = Params(N=8, dx=pn["table1_ds"], mu=mu, cs=cs, cp=cp, dt_min=1.0)
+    nu = (cp ** 2 - 2 * cs ** 2) / (2 * (cp ** 2 - cs ** 2))
+    assert p.S == pytest.approx(mu / (2 * (1 - nu)), rel=1e-14)
+    # Table 1: with mu' = mu/(1-nu) = 2 S the printed nucleation lengths follow.
+    mup = 2 * p.S
+    a, b, Dc, sig = pn["table1_a"], pn["table1_b"], pn["table1_Dc"], pn["table1_sigma_n"]
+    assert mup * Dc / (b * sig) == pytest.approx(pn["table1_L_b"], rel=2e-3)
+    assert 2 * mup * b * Dc / (np.pi * sig * (b - a) ** 2) == pytest.approx(pn["table1_L_inf"], rel=1e-3)
+
+
+def test_uniform_slip_rate_gives_no_elastic_shear_change():
+    w = rough_fault(128, 25.0, 3e-3, seed=2, lam_min=100.0)
+    p = _params(N=128, dx=25.0)
+    V = np.full(p.N, 2e-3)
+    o = Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, None, V, np.full(p.N, 0.5))
+    assert o.step() == 0
+    r1 = o.last["pass1"]
+    assert np.abs(r1["tau_el"]).max() < 1e-18 * p.S
+    # with tau_el = 0 the pass-1 Newton balances tau_load - eta V against friction alone
+    assert np.abs(r1["sig_el"]).max() > 0.0   # curvature still loads the normal traction
+
+
+def test_flat_fault_has_zero_normal_traction_change():
+    w = seamount_rupture(N=128, dx=25.0)
+    p = _params(N=128, dx=25.0)
+    o = Oracle(p, np.zeros(p.N), w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, None,
+               w.V_init, w.theta_init)
+    for _ in range(5):
+        assert o.step() == 0
+        assert not np.any(o.last["sig_el"])
+        assert not np.any(o.last["pass1"]["sig_el"])
+
+
+@pytest.mark.parametrize("steps", [1, 7, 60])
+def test_single_mode_closed_form(steps):
+    # Prescribed V = Va cos(q x) from t = 0 on a fault of constant curvature k0.
+    # Shear: -|k| acts on cos as -q cos; normal: -i sgn(k) acts on cos as sin.
+    # After s steps of dt = dt_min (V constant so Vbar = V every pass):
+    #   tau = -q cos(qx) Va [S s dt + mu sum_{j < min(s, M)} wT_j]
+    #   sig = sin(qx) k0 Va [S s dt + mu sum_{j < min(s, M)} wN_j]
+    p = _params(N=64, kc_L=20.0)
+    m = 16
+    q = 2 * np.pi * m / p.L
+    x = element_x(p.N, p.dx)
+    Va, k0 = 1e-3, 3e-4
+    V = Va * np.cos(q * x)
+    o = _prescribed_oracle(p, np.full(p.N, k0), V)
+    M = windows(p)[m]
+    assert 10 < M < 60
+    for _ in range(steps):
+        assert o.step() == 0
+    dt = p.dt_min
+    j = np.arange(min(steps, M))
+    sT = dt * G_T(p.cs * q * (j + 0.5) * dt, p.r).sum()
+    sN = dt * G_N(p.cs * q * (j + 0.5) * dt, p.r).sum()
+    tau = -q * np.cos(q * x) * Va * (p.S * steps * dt + p.mu * sT)
+    sig = np.sin(q * x) * k0 * Va * (p.S * steps * dt + p.mu * sN)
+    scale = q * Va * p.S * steps * dt
+    assert np.abs(o.last["tau_el"] - tau).max() < 1e-12 * scale
+    assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * scale
+
+
+def test_truncation_forgets_a_pulse():
+    p = _params(N=32, kc_L=20.0)
+    rng = np.random.default_rng(0)
+    kappa = 1e-4 * rng.standard_normal(p.N)
+    o = _prescribed_oracle(p, kappa, np.zeros(p.N))
+    for V in (rng.standard_normal(p.N) * 1e-2, rng.standard_normal(p.N) * 1e-2, np.zeros(p.N)):
+        o.V_presc = V
+        assert o.step() == 0
+    Mmax = int(windows(p).max())
+    for _ in range(Mmax + 1):
+        assert o.step() == 0
+    k = 2 * np.pi * np.arange(p.N // 2 + 1) / p.L
+    tau_static = np.fft.irfft(-p.S * k * np.fft.rfft(o.delta), n=p.N)
+    assert np.allclose(o.last["tau_el"], tau_static, rtol=0, atol=1e-12 * np.abs(tau_static).max())
+
+
+def _real_space_kernels(p, wT, wN, woff, M):
+    """Even (shear) and odd (normal) real-space kernels by explicit sums over all N modes."""
+    N = p.N
+    k = 2 * np.pi * np.arange(N // 2 + 1) / p.L
+    Jmax = int(M.max())
+    d = np.arange(N)
+    KsT = np.zeros(N)
+    KsN = np.zeros(N)
+    KT = np.zeros((Jmax, N))
+    KN = np.zeros((Jmax, N))
+    for n in range(N):
+        nn = min(n, N - n)
+        ph = 2 * np.pi * n * d / N
+        # even operator c(|n|): c cos(2 pi n d / N) / N from every n
+        KsT += -p.S * k[nn] * np.cos(ph) / N
+        # odd operator -i sgn(k) c: the pair (n, N-n) adds 2 c sin(2 pi nn d / N) / N,
+        # one half from each member; n = 0 and n = N/2 add nothing
+        odd = (0 < n < N // 2) or (n > N // 2)
+        sin_nn = np.sin(2 * np.pi * nn * d / N)
+        if odd:
+            KsN += p.S * sin_nn / N
+        for j in range(int(M[nn])):
+            KT[j] += -p.mu * k[nn] * wT[woff[nn] + j] * np.cos(ph) / N
+            if odd:
+                KN[j] += p.mu * wN[woff[nn] + j] * sin_nn / N
+    return KsT, KsN, KT, KN
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_tiny_N_space_time_double_sum_equals_spectral(N):
+    p = _params(N=N, kc_L=20.0)
+    rng = np.random.default_rng(N)
+    kappa = 1e-4 * rng.standard_normal(N)
+    o = _prescribed_oracle(p, kappa, np.zeros(N))
+    Vbars = []                       # real-space pass-2 Vbar per step, oldest first
+    Vold = np.zeros(N)
+    for s in range(int(o.M.max()) + 5):
+        Vn = 1e-2 * rng.standard_normal(N)
+        o.V_presc = Vn
+        assert o.step() == 0
+        Vbars.append(0.5 * (Vold + Vn))
+        Vold = Vn
+    KsT, KsN, KT, KN = _real_space_kernels(p, o.wT, o.wN, o.woff, o.M)
+    delta = o.delta
+    tau = np.zeros(N)
+    sig = np.zeros(N)
+    for i in range(N):
+        for l in range(N):
+            dd = (i - l) % N
+            tau[i] += KsT[dd] * delta[l]
+            sig[i] += KsN[dd] * kappa[l] * delta[l]
+            for j in range(KT.shape[0]):
+                if j < len(Vbars):
+                    Vl = Vbars[-1 - j][l]
+                    tau[i] += KT[j, dd] * Vl
+                    sig[i] += KN[j, dd] * kappa[l] * Vl
+    st = np.abs(tau).max()
+    assert np.abs(o.last["tau_el"] - tau).max() < 1e-12 * st
+    assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * max(np.abs(sig).max(), 1e-30)
+
+
+def _bisect(tau, sig, theta, a, b, Dc, f0, V0, eta):
+    g = lambda x: tau - eta * np.exp(x) - sig * (f0 + a * (x - np.log(V0)) + b * np.log(theta * V0 / Dc))
+    lo, hi = -200.0, 50.0
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        if g(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_newton_matches_bisection():
+    rng = np.random.default_rng(3)
+    n = 200
+    sig = rng.uniform(1e6, 1e8, n)
+    a = rng.uniform(0.005, 0.03, n)
+    b = rng.uniform(0.005, 0.03, n)
+    Dc = rng.uniform(1e-4, 1e-1, n)
+    theta = np.exp(rng.uniform(-5, 25, n))
+    f = rng.uniform(0.3, 0.9, n)
+    eta = 4.33e6
+    tau = sig * f
+    x, it, conv = newton_lnV(tau, sig, theta, a, b, Dc, 0.6, 1e-6, eta,
+                             np.log(1e-9) * np.ones(n), 1e-13, 200)
+    assert conv.all()
+    ref = np.array([_bisect(tau[i], sig[i], theta[i], a[i], b[i], Dc[i], 0.6, 1e-6, eta) for i in range(n)])
+    assert np.abs(x - ref).max() < 1e-11
+    assert it.max() < 40
+
+
+def test_aging_law_fixed_point_and_explicit_agreement():
+    V = np.array([1e-9, 1e-3, 1.0])
+    Dc = np.full(3, 1e-3)
+    th_ss = Dc / V
+    out = state_update(th_ss, V, np.zeros(3), Dc, 0.3, "analytic")
+    assert np.allclose(out, th_ss, rtol=1e-14)
+    # small V dt / Dc: explicit trapezoid-free Euler and exact agree to O((V dt/Dc)^2)
+    th0 = np.full(3, 7.0)
+    for dt in (1e-4, 1e-5):
+        u = V * dt / Dc
+        ex = state_update(th0, V, 1 - th0 * V / Dc, Dc, dt, "explicit")
+        an = state_update(th0, V, None, Dc, dt, "analytic")
+        assert np.all(np.abs(ex - an) <= 2 * (u ** 2) * np.maximum(th0, Dc / V) + 1e-15)
+
+
+@pytest.mark.slow
+def test_normal_traction_sign_follows_scaling_law():
+    # Sec. 5: (1/(f delta)) d delta/dx = -kappa.  A rough-fault rupture must
+    # show a positive correlation of the two sides, and a regression slope near 1.
+    w = rough_fault(256, 25.0, 3e-3, seed=5, lam_min=200.0)
+    p = _params(N=256, dx=25.0)
+    o = Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, None, w.V_init, w.theta_init)
+    for _ in range(2000):
+        assert o.step() == 0
+    d = o.delta
+    lhs = np.gradient(d, p.dx) / (0.6 * d)
+    rhs = -w.kappa
+    assert d.min() > 0.3 * d.max()
+    c = np.corrcoef(lhs, rhs)[0, 1]
+    slope = np.polyfit(rhs, lhs, 1)[0]
+    assert c > 0.4
+    assert 0.5 < slope < 1.5
+
+
+@pytest.mark.slow
+def test_seamount_rupture_nucleates_and_crosses():
+    w = seamount_rupture()
+    p = Params(N=w.N, dx=w.dx, mu=w.mu, cs=w.cs, cp=w.cp, dt_min=w.dt_min)
+    o = Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, None, w.V_init, w.theta_init)
+    x = element_x(w.N, w.dx)
+    crossed = False
+    vmax = 0.0
+    for _ in range(1300):
+        assert o.step() == 0
+        vmax = max(vmax, o.V.max())
+        crossed = crossed or (o.V[np.argmin(np.abs(x - 1000.0))] > 1e-1)
+    assert vmax > 0.1
+    assert crossed
