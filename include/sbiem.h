@@ -1,0 +1,203 @@
+/*
+ * sbiem.h -- C ABI of the GB300 spectral boundary integral element method
+ * (sBIEM) for a mildly non-planar 2D in-plane (mode II) fault, after Romanet &
+ * Ozawa, "Fully dynamic earthquake cycle simulations on a non-planar fault
+ * using the spectral boundary integral element method" (arXiv 2107.03550).
+ *
+ * One handle = one periodic fault of N elements on one GPU.  Every step of
+ * the time integration runs in the library's own sm_103a CUDA kernels; the
+ * host only validates arguments, enqueues launches and copies results out.
+ *
+ * Conventions shared by all entry points
+ *   - Host pointers are plain C arrays in element order i = 0..N-1 (element
+ *     centres x_i = -L/2 + (i + 1/2) dx, L = N dx, periodic).  Inputs are
+ *     copied; the caller keeps ownership of every buffer it passes.
+ *   - Outputs are written into caller-owned host buffers; a NULL output
+ *     pointer skips that output.
+ *   - The handle owns all device memory it allocates (through the allocator
+ *     given in sbiem_params, else cudaMalloc) and frees it in sbiem_destroy.
+ *   - Return value: SBIEM_OK (0) or a negative SBIEM_ERR_* code;
+ *     sbiem_strerror() gives a message, sbiem_last_error() adds detail.
+ *   - A handle is bound to the CUDA device that was current at creation and
+ *     to one stream (default: the legacy default stream); it is not
+ *     thread-safe.
+ */
+#ifndef SBIEM_H
+#define SBIEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status */
+#define SBIEM_OK                 0
+#define SBIEM_ERR_INVALID       -1  /* bad argument (N, dt, parameters, NULL input) */
+#define SBIEM_ERR_NOMEM         -2  /* device allocation failed */
+#define SBIEM_ERR_CUDA          -3  /* a CUDA runtime call failed */
+#define SBIEM_ERR_NEWTON        -4  /* friction Newton iteration cap hit (Sec. 3.2 failure) */
+#define SBIEM_ERR_OPENING       -5  /* sigma_load + sigma_el <= 0 on a sliding element (Sec. 3.2) */
+#define SBIEM_ERR_STATE         -6  /* theta <= 0 with the explicit state update (Sec. 3.2) */
+#define SBIEM_ERR_DTMIN         -7  /* failure at dt = dt_min in the adaptive run (Sec. 3.2) */
+#define SBIEM_ERR_UNSUPPORTED   -8  /* valid request outside what this build implements */
+
+/* bit flags of the device status word (sbiem_status) */
+#define SBIEM_FLAG_NEWTON   1u
+#define SBIEM_FLAG_OPENING  2u
+#define SBIEM_FLAG_STATE    4u
+
+typedef struct sbiem_s* sbiem_t;
+
+typedef void* (*sbiem_alloc_fn)(size_t bytes, void* user);
+typedef void  (*sbiem_free_fn)(void* ptr, void* user);
+
+/*
+ * Parameters of one fault.  Table 1 names; Sec. 3.1 truncation; Sec. 3.2
+ * minimum time step.  Fill with sbiem_default_params() first.
+ */
+typedef struct sbiem_params {
+  int64_t N;            /* elements; a power of two, 16 <= N <= 2^20          */
+  double  dx;           /* element size Delta s (m)                            */
+  double  mu;           /* shear modulus (Pa)                                  */
+  double  cs, cp;       /* shear and dilatational wave speeds (m/s), cp > cs   */
+  double  beta_min;     /* dt_min = beta_min dx / cs (Sec. 3.2), default 0.25  */
+  double  eta_w;        /* truncation parameter eta (Sec. 3.1), default 1      */
+  double  kc_L;         /* k_c * eta * Omega (Sec. 3.1), default 200           */
+  int32_t kc_units;     /* 0: k_c in rad/m (default); 1: in cycles/m           */
+  int32_t precision;    /* 0: FP64 throughout (default); 1: FP32 history
+                           convolution and FFTs, FP64 state and Newton        */
+  int32_t state_law;    /* 0: aging law integrated exactly at constant Vbar
+                           over the step (default); 1: explicit
+                           theta + thetadot dt as printed in Sec. 3.3          */
+  int32_t newton_maxit; /* Newton iteration cap per solve, default 50          */
+  double  newton_tol;   /* |delta ln V| convergence tolerance, default 1e-12   */
+  double  f0, V0;       /* reference friction and slip rate (Eq. momentum)     */
+  sbiem_alloc_fn alloc_fn; /* optional device allocator (NULL: cudaMalloc)     */
+  sbiem_free_fn  free_fn;  /* matching free (NULL: cudaFree)                   */
+  void*   alloc_user;      /* passed to alloc_fn / free_fn                     */
+} sbiem_params;
+
+/* Fill p with the defaults listed above (N = 0: the caller must set N, dx,
+ * mu, cs, cp, f0, V0). */
+void sbiem_default_params(sbiem_params* p);
+
+/*
+ * sbiem_create -- set up one fault (Sec. 3; geometry Sec. 2.2).
+ *
+ * h:          fault profile x2 = h(x_i) (m); used only when kappa is NULL, in
+ *             which case kappa = h'' by spectral differentiation on the device.
+ * kappa:      curvature h''(x_i) (1/m), or NULL.
+ * a, b, Dc:   rate-and-state parameters per element (Eq. momentum, aging law).
+ * sigma_load: compressive normal load per element (Pa), > 0.
+ * tau_load:   shear load per element (Pa), or NULL for the load in equilibrium
+ *             with the initial state: sigma f(V_init, theta_init) + mu/(2cs) V.
+ * tau_load_rate: d tau_load / dt per element (Pa/s), or NULL for zero.
+ * prescribed: per element 0 = frictional, 1 = slip rate prescribed (the
+ *             null-slip-rate zones of Sec. 4, plate-rate loading); NULL = none.
+ * V_presc:    prescribed slip rate (m/s); may be NULL when prescribed is NULL.
+ * V_init, theta_init: initial slip rate (> 0 on frictional elements) and
+ *             state (> 0).
+ * On success *out receives the handle.  Slip starts at zero; history is empty.
+ * Errors: SBIEM_ERR_INVALID, SBIEM_ERR_NOMEM, SBIEM_ERR_CUDA.
+ */
+int sbiem_create(sbiem_t* out, const sbiem_params* p,
+                 const double* h, const double* kappa,
+                 const double* a, const double* b, const double* Dc,
+                 const double* sigma_load, const double* tau_load,
+                 const double* tau_load_rate,
+                 const uint8_t* prescribed, const double* V_presc,
+                 const double* V_init, const double* theta_init);
+
+/* Free every device buffer of the handle.  NULL is accepted. */
+void sbiem_destroy(sbiem_t s);
+
+/* Bind the handle to a CUDA stream (cudaStream_t passed as void*; NULL is the
+ * default stream).  All later work of the handle is enqueued there. */
+int sbiem_set_stream(sbiem_t s, void* cuda_stream);
+
+/*
+ * sbiem_step -- one accepted time step of length dt (Sec. 3.3): predictor,
+ * tractions from the spectral formulas with the truncated history
+ * convolution (Sec. 3.1), Newton for the slip rate, then the same with the
+ * averaged slip rate and state rate, then the history push.
+ * dt must be m * dt_min for an integer m >= 1 (the history is kept on the
+ * dt_min grid).  Synchronizes with the stream to read the status.
+ * Errors: SBIEM_ERR_INVALID (dt), SBIEM_ERR_NEWTON, SBIEM_ERR_OPENING,
+ * SBIEM_ERR_STATE -- on these the fault state is left as it was before the
+ * step.
+ */
+int sbiem_step(sbiem_t s, double dt);
+
+/*
+ * sbiem_enqueue -- enqueue nsteps steps of length dt without synchronizing
+ * (a captured CUDA graph of one step is replayed nsteps times).  A step that
+ * fails sets the device status word; it and every later step then leave the
+ * state untouched.  Read the outcome with sbiem_status().
+ */
+int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps);
+
+/* Synchronize and read the device status bits (SBIEM_FLAG_*) and the number of
+ * committed steps; clear != 0 resets the status word (state is unaffected). */
+int sbiem_status(sbiem_t s, uint32_t* flags, int64_t* steps_done, int clear);
+
+/*
+ * sbiem_step_host -- a step driven from host memory: copies tau_load (N
+ * doubles, replaces the shear load) host->device, runs one step and copies the
+ * new slip rate V (N doubles) device->host.  Either pointer may be NULL.
+ * Host buffers should be pinned for asynchronous copies.  Errors as
+ * sbiem_step.
+ */
+int sbiem_step_host(sbiem_t s, double dt, const double* tau_load, double* V_out);
+
+/* Copy the committed state to host buffers (N doubles each): slip delta,
+ * slip rate V, state theta, and the elastic traction changes tau_el and
+ * sigma_el (compression positive) of the last pass of the last step; *t is
+ * the simulated time.  Synchronizes. */
+int sbiem_get_state(sbiem_t s, double* delta, double* V, double* theta,
+                    double* tau_el, double* sigma_el, double* t);
+
+/* Replace the committed state (any pointer NULL keeps that field).  The
+ * spectral running sums F[delta], F[kappa delta] are recomputed. */
+int sbiem_set_state(sbiem_t s, const double* delta, const double* V,
+                    const double* theta);
+
+/* Number of modes (N/2 + 1) and per-mode window lengths M_n (Sec. 3.1):
+ * M must hold N/2 + 1 int64.  The history of mode n holds M_n - 1 slots. */
+int sbiem_windows(sbiem_t s, int64_t* M);
+
+/* Load / read the history rings (Sec. 3.3, last paragraph).  Layout: for
+ * each mode n = 0..N/2 in turn, M_n - 1 complex values (re, im interleaved,
+ * FP64), newest first: first the shear field F[Vbar], then (a second array)
+ * the normal field F[kappa Vbar].  Length of each array: 2 * sum_n (M_n - 1)
+ * doubles.  The spectral convention is F[f]_n = sum_i f_i exp(-2 pi i n i/N). */
+int sbiem_set_history(sbiem_t s, const double* hist_T, const double* hist_N);
+int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
+
+/* Device-side quantities of the last step: Newton iterations (sum, max over
+ * elements and passes). */
+int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);
+
+/* Bytes the history convolution must read per step (rings plus weights) and
+ * the total device footprint of the handle. */
+int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_bytes);
+
+/*
+ * sbiem_kernel_values -- host FP64 evaluation of the convolution kernels
+ * C^T_II (Eq. Ct, Sec. 2.3) and C^N_II (Sec. 2.4) at n points s = c_s |k| t
+ * (s >= 0) for r = c_s / c_p, by the library's own route (the one its
+ * weight tables are built from).  No GPU work.  Returns SBIEM_ERR_INVALID on
+ * NULL pointers, negative s or r outside (0, 1).
+ */
+int sbiem_kernel_values(const double* s, int64_t n, double r, double* cT, double* cN);
+
+/* Static message for an SBIEM_* code; sbiem_last_error() returns the detail
+ * of the last failure on the calling thread. */
+const char* sbiem_strerror(int code);
+const char* sbiem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBIEM_H */

@@ -1,0 +1,699 @@
+// C ABI of libsbiem: handle life cycle, tables, step enqueueing and I/O.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "sbiem.h"
+
+using namespace sbiem;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(SBIEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+constexpr int kChunkSlots = 2048;  // history slots per chunk of the convolution
+
+}  // namespace
+
+struct sbiem_s {
+  sbiem_params p{};
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;      // where work is enqueued
+  cudaStream_t own = nullptr;         // the handle's own stream (also used for graph capture)
+  bool user_stream = false;
+  int N = 0, nmodes = 0;
+  double L = 0, dt_min = 0, S = 0, eta = 0;
+  std::vector<int64_t> M, Rn, ring_off, w_off;
+  int64_t total_slots = 0, total_w = 0;
+  std::vector<Chunk> chunks;
+  std::vector<void*> allocs;
+  int64_t device_bytes = 0;
+  DevFault<double> f64{};
+  DevFault<float> f32{};
+  FftGeom g64{};
+  double2 *u_a = nullptr, *u_b = nullptr, *u_c = nullptr;  // FP64 utility buffers
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  unsigned* h_status = nullptr;  // pinned
+  long long* h_steps = nullptr;  // pinned
+  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, cudaGraph_t> graph_defs;
+
+  bool fp32() const { return p.precision == 1; }
+};
+
+namespace {
+
+void* dev_alloc(sbiem_s* s, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (s->p.alloc_fn) {
+    ptr = s->p.alloc_fn(bytes, s->p.alloc_user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    ptr = nullptr;
+  }
+  if (ptr) {
+    s->allocs.push_back(ptr);
+    s->device_bytes += static_cast<int64_t>(bytes);
+    cudaMemsetAsync(ptr, 0, bytes, s->stream);
+  }
+  return ptr;
+}
+
+template <class T>
+T* alloc_n(sbiem_s* s, size_t n, bool* ok) {
+  T* ptr = static_cast<T*>(dev_alloc(s, n * sizeof(T)));
+  if (!ptr) *ok = false;
+  return ptr;
+}
+
+void free_all(sbiem_s* s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
+  s->graphs.clear();
+  s->graph_defs.clear();
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (void* ptr : s->allocs) {
+    if (s->p.free_fn) s->p.free_fn(ptr, s->p.alloc_user);
+    else cudaFree(ptr);
+  }
+  s->allocs.clear();
+  if (s->h_status) cudaFreeHost(s->h_status);
+  if (s->h_steps) cudaFreeHost(s->h_steps);
+  if (s->own) cudaStreamDestroy(s->own);
+}
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Windows of the truncated convolution (Sec. 3.1): T_w = eta Omega / cs for
+// k <= k_c, (eta Omega / cs)(k_c / k) above; M_n = ceil(T_w / dt_min) with a
+// relative slack of 1e-12 against rounding of exact ratios; M_0 = 0.
+void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t>& M) {
+  const int64_t nm = p.N / 2 + 1;
+  M.assign(nm, 0);
+  double kc = p.kc_L / (p.eta_w * L);
+  if (p.kc_units == 1) kc *= 2.0 * M_PI;
+  for (int64_t n = 1; n < nm; ++n) {
+    const double k = 2.0 * M_PI * static_cast<double>(n) / L;
+    double Tw = p.eta_w * L / p.cs;
+    if (k > kc) Tw *= kc / k;
+    M[n] = static_cast<int64_t>(std::ceil(Tw / dt_min * (1.0 - 1e-12)));
+  }
+}
+
+template <class R>
+void fill_dev(sbiem_s* s, DevFault<R>& f) {
+  f.N = s->N;
+  f.nmodes = s->nmodes;
+  f.L = s->L;
+  f.S = s->S;
+  f.mu = s->p.mu;
+  f.eta = s->eta;
+  f.dt_min = s->dt_min;
+  f.f0 = s->p.f0;
+  f.V0 = s->p.V0;
+  f.state_law = s->p.state_law;
+  f.newton_maxit = s->p.newton_maxit;
+  f.newton_tol = s->p.newton_tol;
+}
+
+template <class R>
+int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
+  // element and spectral arrays are shared with the FP64 view
+  f = DevFault<R>{};
+  fill_dev(s, f);
+#define COPYP(x) f.x = base.x
+  COPYP(V); COPYP(psi); COPYP(thd); COPYP(delta); COPYP(V1); COPYP(thd1); COPYP(Vbar);
+  COPYP(V2); COPYP(psi2); COPYP(thd2); COPYP(delta2); COPYP(a); COPYP(b); COPYP(Dc);
+  COPYP(sig0); COPYP(tau0); COPYP(taur); COPYP(Vp); COPYP(kappa); COPYP(presc);
+  COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(partial);
+  COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
+  COPYP(chunks); COPYP(nchunks); COPYP(status); COPYP(steps_done); COPYP(t);
+  COPYP(it_sum); COPYP(it_max);
+#undef COPYP
+  bool ok = true;
+  f.ring = alloc_n<Slot<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
+  f.w = alloc_n<W2<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_w, 1)), &ok);
+  f.zt = alloc_n<Cx<R>>(s, s->N, &ok);
+  f.Z = alloc_n<Cx<R>>(s, s->N, &ok);
+  f.y = alloc_n<Cx<R>>(s, s->N, &ok);
+  if (!ok) return fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
+  f.g = make_geom(s->N, sizeof(Cx<R>));
+  if constexpr (sizeof(R) == 8) f.tw = s->tw64;
+  else f.tw = s->tw32;
+  configure_kernels<R>(f.g);
+  return SBIEM_OK;
+}
+
+template <class R>
+void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
+  cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
+  launch_history<R>(f, m, s->sm_count * 4, st);
+  launch_pass<R>(f, 1, m, st);
+  launch_pass<R>(f, 2, m, st);
+  launch_commit<R>(f, m, st);
+}
+
+void enqueue_step(sbiem_s* s, int m, cudaStream_t st) {
+  if (s->fp32()) enqueue_step_t<float>(s, s->f32, m, st);
+  else enqueue_step_t<double>(s, s->f64, m, st);
+}
+
+int status_to_code(unsigned st) {
+  if (st & SBIEM_FLAG_NEWTON) return SBIEM_ERR_NEWTON;
+  if (st & SBIEM_FLAG_OPENING) return SBIEM_ERR_OPENING;
+  if (st & SBIEM_FLAG_STATE) return SBIEM_ERR_STATE;
+  return SBIEM_OK;
+}
+
+int dt_to_m(const sbiem_s* s, double dt, int* m) {
+  if (!(dt > 0.0)) return fail(SBIEM_ERR_INVALID, "dt must be positive");
+  const double r = dt / s->dt_min;
+  const double mr = std::floor(r + 0.5);
+  if (mr < 1.0 || std::fabs(r - mr) > 1e-9 * mr || mr > 1e9)
+    return fail(SBIEM_ERR_INVALID, "dt must be an integer multiple m >= 1 of dt_min = beta_min dx / cs");
+  *m = static_cast<int>(mr);
+  return SBIEM_OK;
+}
+
+// F[delta], F[kappa delta] of the committed slip (FP64 utility FFT).
+int recompute_spectral_sums(sbiem_s* s) {
+  auto& f = s->f64;
+  launch_pack(s->N, f.delta, f.delta, f.kappa, s->u_a, s->stream);
+  launch_fft64(s->g64, s->tw64, s->u_a, s->u_b, s->u_c, false, s->stream);
+  launch_unpack(s->N, s->u_c, f.dhat, f.khat, s->stream);
+  CK(cudaGetLastError());
+  return SBIEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sbiem_default_params(sbiem_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->beta_min = 0.25;
+  p->eta_w = 1.0;
+  p->kc_L = 200.0;
+  p->kc_units = 0;
+  p->precision = 0;
+  p->state_law = 0;
+  p->newton_maxit = 50;
+  p->newton_tol = 1e-12;
+}
+
+const char* sbiem_strerror(int code) {
+  switch (code) {
+    case SBIEM_OK: return "ok";
+    case SBIEM_ERR_INVALID: return "invalid argument";
+    case SBIEM_ERR_NOMEM: return "device out of memory";
+    case SBIEM_ERR_CUDA: return "CUDA runtime error";
+    case SBIEM_ERR_NEWTON: return "friction Newton iteration did not converge";
+    case SBIEM_ERR_OPENING: return "effective normal stress not positive (fault opening)";
+    case SBIEM_ERR_STATE: return "state variable not positive";
+    case SBIEM_ERR_DTMIN: return "failure at the minimum time step";
+    case SBIEM_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown error";
+  }
+}
+
+const char* sbiem_last_error(void) { return g_last_error.c_str(); }
+
+int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const double* kappa,
+                 const double* a, const double* b, const double* Dc, const double* sigma_load,
+                 const double* tau_load, const double* tau_load_rate, const uint8_t* prescribed,
+                 const double* V_presc, const double* V_init, const double* theta_init) {
+  if (!out || !pin) return fail(SBIEM_ERR_INVALID, "NULL handle or parameter pointer");
+  *out = nullptr;
+  const sbiem_params& p = *pin;
+  if (!is_pow2(p.N) || p.N < 16 || p.N > (1 << 20))
+    return fail(SBIEM_ERR_INVALID, "N must be a power of two in [16, 2^20]");
+  if (!(p.dx > 0) || !(p.mu > 0) || !(p.cs > 0) || !(p.cp > p.cs) || !(p.beta_min > 0) ||
+      !(p.eta_w > 0) || !(p.kc_L > 0) || !(p.V0 > 0) || !(p.newton_tol > 0) || p.newton_maxit < 1)
+    return fail(SBIEM_ERR_INVALID, "parameters out of range (dx, mu, cs < cp, beta_min, eta_w, kc_L, V0, Newton)");
+  if (p.precision != 0 && p.precision != 1) return fail(SBIEM_ERR_INVALID, "precision must be 0 or 1");
+  if (p.state_law != 0 && p.state_law != 1) return fail(SBIEM_ERR_INVALID, "state_law must be 0 or 1");
+  if (p.kc_units != 0 && p.kc_units != 1) return fail(SBIEM_ERR_INVALID, "kc_units must be 0 or 1");
+  if ((!h && !kappa) || !a || !b || !Dc || !sigma_load || !V_init || !theta_init)
+    return fail(SBIEM_ERR_INVALID, "required input array is NULL");
+  if (prescribed && !V_presc) return fail(SBIEM_ERR_INVALID, "prescribed given without V_presc");
+  const int N = static_cast<int>(p.N);
+  for (int i = 0; i < N; ++i) {
+    const bool pr = prescribed && prescribed[i];
+    if (!(Dc[i] > 0) || !(sigma_load[i] > 0) || !(theta_init[i] > 0))
+      return fail(SBIEM_ERR_INVALID, "Dc, sigma_load and theta_init must be positive at element " + std::to_string(i));
+    if (!pr && (!(a[i] > 0) || !(V_init[i] > 0)))
+      return fail(SBIEM_ERR_INVALID, "a and V_init must be positive on frictional element " + std::to_string(i));
+  }
+
+  auto* s = new sbiem_s();
+  s->p = p;
+  cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete s;
+    return fail(SBIEM_ERR_CUDA, "cudaStreamCreate failed");
+  }
+  s->stream = s->own;
+  s->N = N;
+  s->nmodes = N / 2 + 1;
+  s->L = N * p.dx;
+  s->dt_min = p.beta_min * p.dx / p.cs;
+  const double r = p.cs / p.cp;
+  s->S = p.mu * (1.0 - r * r);
+  s->eta = p.mu / (2.0 * p.cs);
+  windows(p, s->L, s->dt_min, s->M);
+  s->Rn.assign(s->nmodes, 0);
+  s->ring_off.assign(s->nmodes + 1, 0);
+  s->w_off.assign(s->nmodes + 1, 0);
+  for (int n = 0; n < s->nmodes; ++n) {
+    s->Rn[n] = std::max<int64_t>(s->M[n] - 1, 0);
+    s->ring_off[n + 1] = s->ring_off[n] + s->Rn[n];
+    s->w_off[n + 1] = s->w_off[n] + s->M[n];
+    const int64_t cnt = (s->Rn[n] + kChunkSlots - 1) / kChunkSlots;
+    for (int64_t c = 0; c < cnt; ++c) {
+      Chunk ch{};
+      ch.mode = n;
+      ch.first = static_cast<int32_t>(s->chunks.size() - c);
+      ch.count = static_cast<int32_t>(cnt);
+      ch.i0 = c * kChunkSlots;
+      ch.i1 = std::min<int64_t>((c + 1) * kChunkSlots, s->Rn[n]);
+      s->chunks.push_back(ch);
+    }
+  }
+  // fix 'first': index of the mode's first chunk
+  for (size_t c = 0; c < s->chunks.size();) {
+    const int cnt = s->chunks[c].count;
+    for (int q = 0; q < cnt; ++q) s->chunks[c + q].first = static_cast<int32_t>(c);
+    c += cnt;
+  }
+  s->total_slots = s->ring_off[s->nmodes];
+  s->total_w = s->w_off[s->nmodes];
+  if (s->total_slots > (int64_t(1) << 31) || s->Rn[1] > (int64_t(1) << 30)) {
+    free_all(s);
+    delete s;
+    return fail(SBIEM_ERR_INVALID, "history too long for this build");
+  }
+
+  auto& f = s->f64;
+  fill_dev(s, f);
+  bool ok = true;
+  double** darr[] = {&f.V, &f.psi, &f.thd, &f.delta, &f.V1, &f.thd1, &f.Vbar, &f.V2, &f.psi2, &f.thd2,
+                     &f.delta2, &f.a, &f.b, &f.Dc, &f.sig0, &f.tau0, &f.taur, &f.Vp, &f.kappa};
+  for (double** d : darr) *d = alloc_n<double>(s, N, &ok);
+  f.presc = alloc_n<uint8_t>(s, N, &ok);
+  double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN};
+  for (double2** c : carr) *c = alloc_n<double2>(s, s->nmodes, &ok);
+  f.partial = alloc_n<double4>(s, std::max<size_t>(s->chunks.size(), 1), &ok);
+  f.counter = alloc_n<int>(s, s->nmodes, &ok);
+  int64_t* d_roff = alloc_n<int64_t>(s, s->nmodes + 1, &ok);
+  int64_t* d_woff = alloc_n<int64_t>(s, s->nmodes + 1, &ok);
+  int32_t* d_Rn = alloc_n<int32_t>(s, s->nmodes, &ok);
+  int32_t* d_Mn = alloc_n<int32_t>(s, s->nmodes, &ok);
+  f.head = alloc_n<int32_t>(s, s->nmodes, &ok);
+  Chunk* d_chunks = alloc_n<Chunk>(s, std::max<size_t>(s->chunks.size(), 1), &ok);
+  f.status = alloc_n<unsigned>(s, 1, &ok);
+  f.steps_done = alloc_n<long long>(s, 1, &ok);
+  f.t = alloc_n<double>(s, 1, &ok);
+  f.it_sum = alloc_n<unsigned long long>(s, 1, &ok);
+  f.it_max = alloc_n<int>(s, 1, &ok);
+  s->tw64 = alloc_n<double2>(s, N, &ok);
+  s->u_a = alloc_n<double2>(s, N, &ok);
+  s->u_b = alloc_n<double2>(s, N, &ok);
+  s->u_c = alloc_n<double2>(s, N, &ok);
+  if (s->fp32()) s->tw32 = alloc_n<float2>(s, N, &ok);
+  f.ring_off = d_roff;
+  f.w_off = d_woff;
+  f.Rn = d_Rn;
+  f.Mn = d_Mn;
+  f.chunks = d_chunks;
+  f.nchunks = static_cast<int>(s->chunks.size());
+  if (!ok) {
+    free_all(s);
+    delete s;
+    return fail(SBIEM_ERR_NOMEM, "device allocation failed");
+  }
+  cudaMallocHost(&s->h_status, sizeof(unsigned));
+  cudaMallocHost(&s->h_steps, sizeof(long long));
+
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+  };
+  std::vector<int32_t> Rn32(s->nmodes), Mn32(s->nmodes);
+  for (int n = 0; n < s->nmodes; ++n) {
+    Rn32[n] = static_cast<int32_t>(s->Rn[n]);
+    Mn32[n] = static_cast<int32_t>(s->M[n]);
+  }
+  std::vector<double> tw;
+  build_twiddles(N, tw);
+  std::vector<float> tw32;
+  if (s->fp32()) {
+    tw32.resize(tw.size());
+    for (size_t i = 0; i < tw.size(); ++i) tw32[i] = static_cast<float>(tw[i]);
+  }
+  // friction arrays, load, state
+  std::vector<double> psi(N), thd(N), taul(N, 0.0), taur(N, 0.0), Vp(N, 0.0), V(N);
+  std::vector<uint8_t> pr(N, 0);
+  for (int i = 0; i < N; ++i) {
+    pr[i] = (prescribed && prescribed[i]) ? 1 : 0;
+    Vp[i] = pr[i] ? V_presc[i] : 0.0;
+    V[i] = pr[i] ? V_presc[i] : V_init[i];
+    psi[i] = std::log(theta_init[i]);
+    thd[i] = 1.0 - theta_init[i] * V[i] / Dc[i];
+    if (tau_load_rate) taur[i] = tau_load_rate[i];
+    if (tau_load) {
+      taul[i] = tau_load[i];
+    } else if (!pr[i]) {
+      // equilibrium with the initial state (Eq. momentum + radiation damping)
+      const double fr = p.f0 + a[i] * std::log(V[i] / p.V0) + b[i] * std::log(theta_init[i] * p.V0 / Dc[i]);
+      taul[i] = sigma_load[i] * fr + s->eta * V[i];
+    }
+  }
+  const size_t nb = sizeof(double) * N;
+  bool cu = up(f.a, a, nb) == cudaSuccess && up(f.b, b, nb) == cudaSuccess && up(f.Dc, Dc, nb) == cudaSuccess &&
+            up(f.sig0, sigma_load, nb) == cudaSuccess && up(f.tau0, taul.data(), nb) == cudaSuccess &&
+            up(f.taur, taur.data(), nb) == cudaSuccess && up(f.Vp, Vp.data(), nb) == cudaSuccess &&
+            up(f.presc, pr.data(), N) == cudaSuccess && up(f.V, V.data(), nb) == cudaSuccess &&
+            up(f.psi, psi.data(), nb) == cudaSuccess && up(f.thd, thd.data(), nb) == cudaSuccess &&
+            up(d_roff, s->ring_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
+            up(d_woff, s->w_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
+            up(d_Rn, Rn32.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
+            up(d_Mn, Mn32.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
+            (s->chunks.empty() || up(d_chunks, s->chunks.data(), sizeof(Chunk) * s->chunks.size()) == cudaSuccess) &&
+            up(s->tw64, tw.data(), sizeof(double) * tw.size()) == cudaSuccess &&
+            (!s->fp32() || up(s->tw32, tw32.data(), sizeof(float) * tw32.size()) == cudaSuccess);
+  s->g64 = make_geom(N, sizeof(double2));
+  configure_kernels<double>(s->g64);
+  // curvature: given, or kappa = h'' by spectral differentiation (Sec. 2.2, small slope)
+  if (kappa) {
+    cu = cu && up(f.kappa, kappa, nb) == cudaSuccess;
+  } else {
+    cu = cu && up(f.Vbar, h, nb) == cudaSuccess;  // scratch for h
+    launch_pack(N, f.Vbar, nullptr, nullptr, s->u_a, s->stream);
+    launch_fft64(s->g64, s->tw64, s->u_a, s->u_b, s->u_c, false, s->stream);
+    launch_d2(N, s->L, s->u_c, s->stream);
+    launch_fft64(s->g64, s->tw64, s->u_c, s->u_b, s->u_a, true, s->stream);
+    launch_real_part(N, s->u_a, f.kappa, s->stream);
+  }
+  // kernel tables: piecewise Chebyshev of C^T, C^N on the s range the weights need
+  double smax = 0.0;
+  for (int n = 1; n < s->nmodes; ++n) {
+    const double k = 2.0 * M_PI * n / s->L;
+    smax = std::max(smax, p.cs * k * (s->M[n] - 0.5) * s->dt_min);
+  }
+  ChebTable tab;
+  build_cheb(r, smax + 1.0, &tab);
+  double* d_cheb = alloc_n<double>(s, tab.coef.size(), &ok);
+  if (!ok || !cu) {
+    free_all(s);
+    delete s;
+    return fail(ok ? SBIEM_ERR_CUDA : SBIEM_ERR_NOMEM, "upload failed");
+  }
+  up(d_cheb, tab.coef.data(), sizeof(double) * tab.coef.size());
+  int rc;
+  if (s->fp32()) {
+    rc = setup_device<float>(s, s->f32, f);
+    if (rc == SBIEM_OK) launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+  } else {
+    f.ring = alloc_n<Slot64>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
+    f.w = alloc_n<W2<double>>(s, static_cast<size_t>(std::max<int64_t>(s->total_w, 1)), &ok);
+    f.zt = alloc_n<double2>(s, N, &ok);
+    f.Z = alloc_n<double2>(s, N, &ok);
+    f.y = alloc_n<double2>(s, N, &ok);
+    f.g = make_geom(N, sizeof(double2));
+    f.tw = s->tw64;
+    rc = ok ? SBIEM_OK : fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
+    if (rc == SBIEM_OK) launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+  }
+  if (rc == SBIEM_OK) rc = recompute_spectral_sums(s);
+  if (rc == SBIEM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
+    rc = fail(SBIEM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(cudaGetLastError()));
+  if (rc != SBIEM_OK) {
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return SBIEM_OK;
+}
+
+void sbiem_destroy(sbiem_t s) {
+  if (!s) return;
+  free_all(s);
+  delete s;
+}
+
+int sbiem_set_stream(sbiem_t s, void* stream) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  CK(cudaStreamSynchronize(s->stream));
+  s->stream = stream ? static_cast<cudaStream_t>(stream) : s->own;
+  s->user_stream = stream != nullptr;
+  return SBIEM_OK;
+}
+
+int sbiem_status(sbiem_t s, uint32_t* flags, int64_t* steps_done, int clear) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  CK(cudaMemcpyAsync(s->h_status, s->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_steps, s->f64.steps_done, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (flags) *flags = *s->h_status;
+  if (steps_done) *steps_done = *s->h_steps;
+  if (clear) CK(cudaMemsetAsync(s->f64.status, 0, sizeof(unsigned), s->stream));
+  return SBIEM_OK;
+}
+
+int sbiem_step(sbiem_t s, double dt) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  int m;
+  int rc = dt_to_m(s, dt, &m);
+  if (rc) return rc;
+  uint32_t before;
+  rc = sbiem_status(s, &before, nullptr, 1);
+  if (rc) return rc;
+  enqueue_step(s, m, s->stream);
+  CK(cudaGetLastError());
+  uint32_t st;
+  rc = sbiem_status(s, &st, nullptr, 1);
+  if (rc) return rc;
+  rc = status_to_code(st);
+  if (rc) return fail(rc, "step rejected; state left at the start of the step");
+  return SBIEM_OK;
+}
+
+int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  if (nsteps < 0) return fail(SBIEM_ERR_INVALID, "nsteps < 0");
+  int m;
+  int rc = dt_to_m(s, dt, &m);
+  if (rc) return rc;
+  auto it = s->graphs.find(m);
+  if (it == s->graphs.end()) {
+    // capture one step on the handle's own stream, replay it on s->stream
+    cudaGraph_t gdef = nullptr;
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(s, m, s->own);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(s->own, &gdef);
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+      return fail(SBIEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaGraphInstantiate(&exec, gdef, 0));
+    s->graphs[m] = exec;
+    s->graph_defs[m] = gdef;
+    it = s->graphs.find(m);
+  }
+  for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(it->second, s->stream));
+  return SBIEM_OK;
+}
+
+int sbiem_step_host(sbiem_t s, double dt, const double* tau_load, double* V_out) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  int m;
+  int rc = dt_to_m(s, dt, &m);
+  if (rc) return rc;
+  if (tau_load)
+    CK(cudaMemcpyAsync(s->f64.tau0, tau_load, sizeof(double) * s->N, cudaMemcpyHostToDevice, s->stream));
+  rc = sbiem_enqueue(s, dt, 1);
+  if (rc) return rc;
+  if (V_out) CK(cudaMemcpyAsync(V_out, s->f64.V, sizeof(double) * s->N, cudaMemcpyDeviceToHost, s->stream));
+  uint32_t st;
+  rc = sbiem_status(s, &st, nullptr, 1);
+  if (rc) return rc;
+  rc = status_to_code(st);
+  if (rc) return fail(rc, "step rejected; state left at the start of the step");
+  return SBIEM_OK;
+}
+
+int sbiem_get_state(sbiem_t s, double* delta, double* V, double* theta, double* tau_el,
+                    double* sigma_el, double* t) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  const auto& f = s->f64;
+  const size_t nb = sizeof(double) * s->N;
+  if (delta) CK(cudaMemcpyAsync(delta, f.delta, nb, cudaMemcpyDeviceToHost, s->stream));
+  if (V) CK(cudaMemcpyAsync(V, f.V, nb, cudaMemcpyDeviceToHost, s->stream));
+  if (theta) CK(cudaMemcpyAsync(theta, f.psi, nb, cudaMemcpyDeviceToHost, s->stream));
+  std::vector<double> y;
+  std::vector<float> y32;
+  if (tau_el || sigma_el) {
+    if (s->fp32()) {
+      y32.resize(2 * s->N);
+      CK(cudaMemcpyAsync(y32.data(), s->f32.y, sizeof(float) * 2 * s->N, cudaMemcpyDeviceToHost, s->stream));
+    } else {
+      y.resize(2 * s->N);
+      CK(cudaMemcpyAsync(y.data(), f.y, sizeof(double) * 2 * s->N, cudaMemcpyDeviceToHost, s->stream));
+    }
+  }
+  if (t) CK(cudaMemcpyAsync(t, f.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (theta)
+    for (int i = 0; i < s->N; ++i) theta[i] = std::exp(theta[i]);
+  for (int i = 0; i < s->N; ++i) {
+    const double tr = s->fp32() ? static_cast<double>(y32.empty() ? 0.f : y32[2 * i]) : (y.empty() ? 0.0 : y[2 * i]);
+    const double si = s->fp32() ? static_cast<double>(y32.empty() ? 0.f : y32[2 * i + 1]) : (y.empty() ? 0.0 : y[2 * i + 1]);
+    if (tau_el) tau_el[i] = tr;
+    if (sigma_el) sigma_el[i] = si;
+  }
+  return SBIEM_OK;
+}
+
+int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const double* theta) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  auto& f = s->f64;
+  const int N = s->N;
+  const size_t nb = sizeof(double) * N;
+  std::vector<double> Vh(N), th(N), Dc(N), psi(N), thd(N);
+  std::vector<uint8_t> pr(N);
+  CK(cudaMemcpyAsync(Vh.data(), f.V, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(psi.data(), f.psi, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(Dc.data(), f.Dc, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (V) Vh.assign(V, V + N);
+  for (int i = 0; i < N; ++i) {
+    th[i] = theta ? theta[i] : std::exp(psi[i]);
+    if (!(th[i] > 0)) return fail(SBIEM_ERR_INVALID, "theta must be positive");
+    psi[i] = std::log(th[i]);
+    thd[i] = 1.0 - th[i] * Vh[i] / Dc[i];
+  }
+  if (delta) CK(cudaMemcpyAsync(f.delta, delta, nb, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(f.V, Vh.data(), nb, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(f.psi, psi.data(), nb, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(f.thd, thd.data(), nb, cudaMemcpyHostToDevice, s->stream));
+  int rc = recompute_spectral_sums(s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s->stream));
+  return SBIEM_OK;
+}
+
+int sbiem_windows(sbiem_t s, int64_t* M) {
+  if (!s || !M) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  std::memcpy(M, s->M.data(), sizeof(int64_t) * s->nmodes);
+  return SBIEM_OK;
+}
+
+int sbiem_set_history(sbiem_t s, const double* hT, const double* hN) {
+  if (!s || !hT || !hN) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  const int64_t tot = s->total_slots;
+  if (tot == 0) return SBIEM_OK;
+  std::vector<int32_t> heads(s->nmodes, 0);
+  if (s->fp32()) {
+    std::vector<float4> buf(tot);
+    for (int64_t i = 0; i < tot; ++i)
+      buf[i] = make_float4(static_cast<float>(hT[2 * i]), static_cast<float>(hT[2 * i + 1]),
+                           static_cast<float>(hN[2 * i]), static_cast<float>(hN[2 * i + 1]));
+    CK(cudaMemcpyAsync(s->f32.ring, buf.data(), sizeof(float4) * tot, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->f32.head, heads.data(), sizeof(int32_t) * s->nmodes, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  } else {
+    std::vector<Slot64> buf(tot);
+    for (int64_t i = 0; i < tot; ++i) {
+      buf[i].t = make_double2(hT[2 * i], hT[2 * i + 1]);
+      buf[i].n = make_double2(hN[2 * i], hN[2 * i + 1]);
+    }
+    CK(cudaMemcpyAsync(s->f64.ring, buf.data(), sizeof(Slot64) * tot, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->f64.head, heads.data(), sizeof(int32_t) * s->nmodes, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  return SBIEM_OK;
+}
+
+int sbiem_get_history(sbiem_t s, double* hT, double* hN) {
+  if (!s || !hT || !hN) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  const int64_t tot = s->total_slots;
+  if (tot == 0) return SBIEM_OK;
+  std::vector<int32_t> heads(s->nmodes);
+  CK(cudaMemcpyAsync(heads.data(), s->f64.head, sizeof(int32_t) * s->nmodes, cudaMemcpyDeviceToHost, s->stream));
+  std::vector<Slot64> b64;
+  std::vector<float4> b32;
+  if (s->fp32()) {
+    b32.resize(tot);
+    CK(cudaMemcpyAsync(b32.data(), s->f32.ring, sizeof(float4) * tot, cudaMemcpyDeviceToHost, s->stream));
+  } else {
+    b64.resize(tot);
+    CK(cudaMemcpyAsync(b64.data(), s->f64.ring, sizeof(Slot64) * tot, cudaMemcpyDeviceToHost, s->stream));
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  for (int n = 0; n < s->nmodes; ++n) {
+    const int64_t Rn = s->Rn[n], off = s->ring_off[n];
+    for (int64_t i = 0; i < Rn; ++i) {
+      const int64_t src = off + (heads[n] + i) % Rn, dst = off + i;
+      if (s->fp32()) {
+        hT[2 * dst] = b32[src].x;
+        hT[2 * dst + 1] = b32[src].y;
+        hN[2 * dst] = b32[src].z;
+        hN[2 * dst + 1] = b32[src].w;
+      } else {
+        hT[2 * dst] = b64[src].t.x;
+        hT[2 * dst + 1] = b64[src].t.y;
+        hN[2 * dst] = b64[src].n.x;
+        hN[2 * dst + 1] = b64[src].n.y;
+      }
+    }
+  }
+  return SBIEM_OK;
+}
+
+int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  unsigned long long sum = 0;
+  int mx = 0;
+  CK(cudaMemcpyAsync(&sum, s->f64.it_sum, sizeof(sum), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&mx, s->f64.it_max, sizeof(mx), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (iters_sum) *iters_sum = static_cast<int64_t>(sum);
+  if (iters_max) *iters_max = mx;
+  return SBIEM_OK;
+}
+
+int sbiem_footprint(sbiem_t s, int64_t* hist_bytes, int64_t* device_bytes) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  const int64_t slot = s->fp32() ? 16 : 32, wb = s->fp32() ? 8 : 16;
+  if (hist_bytes) *hist_bytes = s->total_slots * (slot + wb);
+  if (device_bytes) *device_bytes = s->device_bytes;
+  return SBIEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,22 @@
+// Internal declarations shared by the host table builder and the CUDA
+// translation unit of libsbiem.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace sbiem {
+
+// Piecewise Chebyshev interpolants of C^T and C^N on s in [0, npieces * h].
+// coef[(p * (deg + 1) + k) * 2 + {0: C^T, 1: C^N}].
+struct ChebTable {
+  double h = 0.5;
+  int deg = 16;
+  int npieces = 0;
+  std::vector<double> coef;
+};
+
+void kernel_values(double s, double r, double* cT, double* cN);
+void build_cheb(double r, double smax, ChebTable* tab);
+void build_twiddles(int64_t N, std::vector<double>& tw);
+
+}  // namespace sbiem

@@ -1,0 +1,699 @@
+// sm_103a kernels of the non-planar spectral BIEM time step (Sec. 3.3).
+//
+//   k_history  truncated history convolution A^X_n = sum_j w^X_{n,j} H^X_n
+//              (Sec. 3.1, Sec. 3.3 step (2)), the bandwidth-bound hot loop
+//   k_col      column pass of the four-step FFT; forward with the predictor
+//              prologue (Vbar, kappa Vbar), inverse with the spectral
+//              assembly prologue (static + current-interval + history terms)
+//   k_row      row pass of the four-step FFT
+//   k_newton   per-element state update and Newton solve of Eq. (momentum)
+//              with radiation damping (Sec. 3.3 step (3))
+//   k_commit   accept the step: state, spectral running sums, history push
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace sbiem {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// --------------------------------------------------------- complex helpers
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// --------------------------------------------------------- shared-memory FFT
+// B independent radix-2 Stockham (decimation in frequency, self-sorting)
+// transforms of length M = 2^lgM on buf[b * M + i].  twm[j] = exp(-2 pi i j/M),
+// j < M/2.  Each stage reads every butterfly into registers, synchronizes,
+// then writes, so one buffer suffices.
+constexpr int kMaxBfly = 8;
+
+template <class C, bool INV>
+__device__ void fft_batch(C* buf, int lgM, int B, const C* twm, int tid, int nth) {
+  const int M = 1 << lgM;
+  const int half = M >> 1;
+  const int total = B * half;
+  int lgs = 0;
+  for (int lgn = lgM; lgn >= 1; --lgn, ++lgs) {
+    const int s = 1 << lgs;
+    const int m = 1 << (lgn - 1);
+    C ra[kMaxBfly], rb[kMaxBfly];
+#pragma unroll
+    for (int k = 0; k < kMaxBfly; ++k) {
+      const int beta = tid + k * nth;
+      if (beta < total) {
+        const int col = beta >> (lgM - 1);
+        const int bb = beta & (half - 1);
+        const int p = bb >> lgs;
+        const int q = bb & (s - 1);
+        const C* base = buf + col * M;
+        const C a = base[q + s * p];
+        const C c = base[q + s * (p + m)];
+        C w = twm[p * s];
+        if (INV) w.y = -w.y;
+        ra[k] = cadd(a, c);
+        rb[k] = cmul(csub(a, c), w);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMaxBfly; ++k) {
+      const int beta = tid + k * nth;
+      if (beta < total) {
+        const int col = beta >> (lgM - 1);
+        const int bb = beta & (half - 1);
+        const int p = bb >> lgs;
+        const int q = bb & (s - 1);
+        C* base = buf + col * M;
+        base[q + s * (2 * p)] = ra[k];
+        base[q + s * (2 * p + 1)] = rb[k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+enum { PRO_LOAD = 0, PRO_PASS = 1, PRO_ASSEMBLE = 2 };
+
+// Spectral assembly of mode m = min(n, N-n) (Sec. 3.1, Sec. 3.3 step (2)):
+//   U = F[Vbar], Q = F[kappa Vbar] from the packed spectrum Z of Vbar + i kappa Vbar,
+//   tau_m = -|k| [ S (Dhat + dt U) + mu (w0T U + AT) ]
+//   sig_m = -i sgn(k) [ S (Khat + dt Q) + mu (w0N Q + AN) ]   (0 at m = 0, N/2)
+// and Y_n = tau_n + i sig_n of the full spectrum (conjugates for n > N/2).
+template <class R>
+__device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass, int m_dt, double dt) {
+  const int N = f.N;
+  const int m = n <= (N >> 1) ? n : N - n;
+  const Cx<R> Zm = f.Z[m];
+  const Cx<R> Zc = f.Z[(N - m) & (N - 1)];
+  double2 U, Q;
+  U.x = 0.5 * (static_cast<double>(Zm.x) + static_cast<double>(Zc.x));
+  U.y = 0.5 * (static_cast<double>(Zm.y) - static_cast<double>(Zc.y));
+  Q.x = 0.5 * (static_cast<double>(Zm.y) + static_cast<double>(Zc.y));
+  Q.y = -0.5 * (static_cast<double>(Zm.x) - static_cast<double>(Zc.x));
+  double tr = 0.0, ti = 0.0, sr = 0.0, si = 0.0;
+  if (m > 0) {
+    const double k = kTwoPi * m / f.L;
+    double w0T = 0.0, w0N = 0.0;
+    const int lim = min(m_dt, f.Mn[m]);
+    const int64_t wo = f.w_off[m];
+    for (int j = 0; j < lim; ++j) {
+      const W2<R> w = f.w[wo + j];
+      w0T += static_cast<double>(w.x);
+      w0N += static_cast<double>(w.y);
+    }
+    const double2 D = f.dhat[m], K = f.khat[m], AT = f.AT[m], AN = f.AN[m];
+    tr = -k * (f.S * (D.x + dt * U.x) + f.mu * (w0T * U.x + AT.x));
+    ti = -k * (f.S * (D.y + dt * U.y) + f.mu * (w0T * U.y + AT.y));
+    if (m < (N >> 1)) {
+      const double xr = f.S * (K.x + dt * Q.x) + f.mu * (w0N * Q.x + AN.x);
+      const double xi = f.S * (K.y + dt * Q.y) + f.mu * (w0N * Q.y + AN.y);
+      sr = xi;   // -i (xr + i xi)
+      si = -xr;
+    }
+  }
+  if (pass == 2 && n <= (N >> 1)) {
+    f.U2[n] = U;
+    f.Q2[n] = Q;
+  }
+  if (n > (N >> 1)) {
+    ti = -ti;
+    si = -si;
+  }
+  Cx<R> Y;
+  Y.x = static_cast<R>(tr - si);
+  Y.y = static_cast<R>(ti + sr);
+  return Y;
+}
+
+// Column pass: for n1 in this CTA's B columns, transform x[n1 + N1 n2] over
+// n2 (length N2), multiply by exp(-+2 pi i n1 k2 / N), store to
+// out[k2 N1 + n1].
+template <class R, bool INV, int PRO>
+__global__ void k_col(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ in,
+                      Cx<R>* __restrict__ out, DevFault<R> f, int pass, int m_dt, double dt) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int M = g.N2, B = g.Bc;
+  C* twm = buf + B * M;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  // the status word only changes in k_newton, never while this kernel runs
+  if (PRO != PRO_LOAD && *f.status) return;
+  for (int j = tid; j < (M >> 1); j += nth) twm[j] = tw[j * g.N1];
+  const int c0 = blockIdx.x * B;
+  for (int t = tid; t < B * M; t += nth) {
+    const int b = t % B;
+    const int n2 = t / B;
+    const int n = c0 + b + g.N1 * n2;
+    C v;
+    if (PRO == PRO_LOAD) {
+      v = in[n];
+    } else if (PRO == PRO_PASS) {
+      // predictor slip rate of this pass (Sec. 3.3): V, then (V + V1)/2
+      const double vb = (pass == 1) ? f.V[n] : 0.5 * (f.V[n] + f.V1[n]);
+      f.Vbar[n] = vb;
+      v.x = static_cast<R>(vb);
+      v.y = static_cast<R>(f.kappa[n] * vb);
+    } else {
+      v = assemble<R>(f, n, pass, m_dt, dt);
+    }
+    buf[b * M + n2] = v;
+  }
+  __syncthreads();
+  fft_batch<C, INV>(buf, g.lgN2, B, twm, tid, nth);
+  for (int t = tid; t < B * M; t += nth) {
+    const int b = t % B;
+    const int k2 = t / B;
+    const int n1 = c0 + b;
+    C w = tw[n1 * k2];
+    if (INV) w.y = -w.y;
+    out[k2 * g.N1 + n1] = cmul(buf[b * M + k2], w);
+  }
+}
+
+// Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
+// (length N1) and store to out[k2 + N2 k1], times scale.
+template <class R, bool INV>
+__global__ void k_row(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ in,
+                      Cx<R>* __restrict__ out, R scale, const unsigned* status) {
+  using C = Cx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int M = g.N1, B = g.Br;
+  C* twm = buf + B * M;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (status && *status) return;
+  for (int j = tid; j < (M >> 1); j += nth) twm[j] = tw[j * g.N2];
+  const int c0 = blockIdx.x * B;
+  for (int t = tid; t < B * M; t += nth) {
+    const int n1 = t % M;
+    const int b = t / M;
+    buf[b * M + n1] = in[(c0 + b) * g.N1 + n1];
+  }
+  __syncthreads();
+  fft_batch<C, INV>(buf, g.lgN1, B, twm, tid, nth);
+  for (int t = tid; t < B * M; t += nth) {
+    const int b = t % B;
+    const int k1 = t / B;
+    C v = buf[b * M + k1];
+    v.x *= scale;
+    v.y *= scale;
+    out[(c0 + b) + g.N2 * k1] = v;
+  }
+}
+
+// ---------------------------------------------------- history convolution
+// Ring slot i of mode n (i = 0 newest) holds the spectra of the interval
+// lying i dt_min before the current step; with a step of m dt_min it meets
+// the weight of interval j = i + m (Sec. 3.3, midpoint weights of Sec. 3.3).
+template <class R> struct Acc4 { R tr, ti, nr, ni; };
+
+__device__ __forceinline__ void slot_fma(Acc4<double>& a, const Slot64& s, const double2 w) {
+  a.tr = fma(w.x, s.t.x, a.tr);
+  a.ti = fma(w.x, s.t.y, a.ti);
+  a.nr = fma(w.y, s.n.x, a.nr);
+  a.ni = fma(w.y, s.n.y, a.ni);
+}
+__device__ __forceinline__ void slot_fma(Acc4<float>& a, const float4& s, const float2 w) {
+  a.tr = fmaf(w.x, s.x, a.tr);
+  a.ti = fmaf(w.x, s.y, a.ti);
+  a.nr = fmaf(w.y, s.z, a.nr);
+  a.ni = fmaf(w.y, s.w, a.ni);
+}
+__device__ __forceinline__ Slot64 ld_slot(const Slot64* p) {
+  Slot64 s;
+  s.t = __ldg(&p->t);
+  s.n = __ldg(&p->n);
+  return s;
+}
+__device__ __forceinline__ float4 ld_slot(const float4* p) { return __ldg(p); }
+
+template <class R> struct HistCfg;
+template <> struct HistCfg<double> { static constexpr int kUnroll = 2; };
+template <> struct HistCfg<float> { static constexpr int kUnroll = 4; };
+
+constexpr int kHistThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of four doubles; result valid in thread 0.
+__device__ __forceinline__ double4 block_sum4(double4 v, double4* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  v.z = warp_sum(v.z);
+  v.w = warp_sum(v.w);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double4 r = make_double4(0.0, 0.0, 0.0, 0.0);
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    if (lane < nw) r = sh[lane];
+    r.x = warp_sum(r.x);
+    r.y = warp_sum(r.y);
+    r.z = warp_sum(r.z);
+    r.w = warp_sum(r.w);
+  }
+  __syncthreads();
+  return r;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_dt) {
+  __shared__ double4 sh[kHistThreads / 32];
+  __shared__ int s_last;
+  if (*f.status) return;
+  constexpr int U = HistCfg<R>::kUnroll;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int c = blockIdx.x; c < f.nchunks; c += gridDim.x) {
+    const Chunk cd = f.chunks[c];
+    const int n = cd.mode;
+    const int Rn = f.Rn[n];
+    const int h = f.head[n];
+    const int64_t iend = min(cd.i1, static_cast<int64_t>(f.Mn[n]) - m_dt);
+    const Slot<R>* ring = f.ring + f.ring_off[n];
+    const W2<R>* w = f.w + f.w_off[n] + m_dt;
+    Acc4<R> acc = {R(0), R(0), R(0), R(0)};
+    for (int64_t i = cd.i0 + tid; i < iend; i += static_cast<int64_t>(U) * nth) {
+      Slot<R> s[U];
+      W2<R> ww[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t ii = i + static_cast<int64_t>(u) * nth;
+        if (ii < iend) {
+          int64_t slot = h + ii;
+          if (slot >= Rn) slot -= Rn;
+          s[u] = ld_slot(ring + slot);
+          ww[u] = __ldg(w + ii);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t ii = i + static_cast<int64_t>(u) * nth;
+        if (ii < iend) slot_fma(acc, s[u], ww[u]);
+      }
+    }
+    double4 v = make_double4(acc.tr, acc.ti, acc.nr, acc.ni);
+    v = block_sum4(v, sh);
+    if (tid == 0) {
+      if (cd.count == 1) {
+        f.AT[n] = make_double2(v.x, v.y);
+        f.AN[n] = make_double2(v.z, v.w);
+        s_last = 0;
+      } else {
+        f.partial[c] = v;
+        __threadfence();
+        const int prev = atomicAdd(f.counter + n, 1);
+        s_last = (prev == cd.count - 1);
+      }
+    }
+    __syncthreads();
+    if (s_last) {
+      // last chunk of the mode to finish: add the partials in chunk order
+      __threadfence();
+      double4 r = make_double4(0.0, 0.0, 0.0, 0.0);
+      for (int q = tid; q < cd.count; q += nth) {
+        const double2* pp = reinterpret_cast<const double2*>(f.partial + cd.first + q);
+        const double2 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
+        const double4 p = make_double4(p0.x, p0.y, p1.x, p1.y);
+        r.x += p.x;
+        r.y += p.y;
+        r.z += p.z;
+        r.w += p.w;
+      }
+      r = block_sum4(r, sh);
+      if (tid == 0) {
+        f.AT[n] = make_double2(r.x, r.y);
+        f.AN[n] = make_double2(r.z, r.w);
+        f.counter[n] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ friction
+// x = ln V solves g(x) = q(x) - eta e^x = 0 with q(x) = tau - sigma (c0 + a x),
+// c0 = f0 + b ln(theta V0 / Dc) - a ln V0 (Eq. momentum plus radiation
+// damping).  g is strictly decreasing; the quasi-static root x_qs (q = 0)
+// bounds the root from above, a lower bound comes from doubling steps.
+// Newton on g where friction dominates, on h(x) = x - ln(q/eta) where
+// radiation damping dominates (q > sigma a), bisection when a step leaves the
+// bracket.  Returns iterations (negative: not converged).
+__device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, double a, double eta,
+                                          double x0, double tol, int maxit, double* xout) {
+  double hi = (tau / sig - c0) / a;
+  hi = fmin(hi, 700.0);
+  double d = 1.0, lo = hi - d;
+  for (int k = 0; k < 64; ++k) {
+    const double g = tau - sig * (c0 + a * lo) - eta * exp(lo);
+    if (g >= 0.0) break;
+    d *= 2.0;
+    lo = hi - d;
+  }
+  double x = fmin(fmax(x0, lo), hi);
+  const double sa = sig * a;
+  for (int it = 1; it <= maxit; ++it) {
+    const double e = eta * exp(x);
+    const double q = tau - sig * (c0 + a * x);
+    const double g = q - e;
+    if (g > 0.0) lo = x; else hi = x;
+    double xn;
+    if (q > sa) xn = x - (x - log(q / eta)) / (1.0 + sa / q);
+    else xn = x + g / (e + sa);
+    if (fabs(xn - x) <= tol) {
+      *xout = xn;
+      return it;
+    }
+    if (xn < lo || xn > hi) xn = 0.5 * (lo + hi);
+    x = xn;
+  }
+  *xout = x;
+  return -maxit;
+}
+
+template <class R>
+__global__ void k_newton(DevFault<R> f, int pass, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ unsigned s_flags, s_skip;
+  __shared__ int s_itmax;
+  __shared__ unsigned long long s_itsum;
+  // one read of the status word per block: other blocks may set it while
+  // this one runs, and the decision must be uniform across __syncthreads
+  if (threadIdx.x == 0) { s_flags = 0u; s_itmax = 0; s_itsum = 0ull; s_skip = *f.status; }
+  __syncthreads();
+  if (s_skip) return;
+  unsigned flags = 0u;
+  int iters = 0;
+  if (i < f.N) {
+    const double vb = f.Vbar[i];
+    const double Dc = f.Dc[i];
+    const double th0 = exp(f.psi[i]);
+    double thp;
+    if (f.state_law == 0) {
+      // aging law integrated at constant Vbar: theta e^{-u} + dt (1 - e^{-u})/u
+      const double u = vb * dt / Dc;
+      const double phi = (u > 0.0) ? -expm1(-u) / u : 1.0;
+      thp = th0 * exp(-u) + dt * phi;
+    } else {
+      const double thdb = (pass == 1) ? f.thd[i] : 0.5 * (f.thd[i] + f.thd1[i]);
+      thp = th0 + thdb * dt;
+      if (!(thp > 0.0)) flags |= SBIEM_FLAG_STATE;
+    }
+    const double t_end = *f.t + dt;
+    const Cx<R> y = f.y[i];
+    const double tau = f.tau0[i] + f.taur[i] * t_end + static_cast<double>(y.x);
+    const double sig = f.sig0[i] + static_cast<double>(y.y);
+    double Vn;
+    if (f.presc[i]) {
+      Vn = f.Vp[i];
+    } else if (!(sig > 0.0)) {
+      flags |= SBIEM_FLAG_OPENING;
+      Vn = f.V[i];
+    } else if (flags) {
+      Vn = f.V[i];
+    } else {
+      const double a = f.a[i];
+      const double c0 = f.f0 + f.b[i] * (log(thp) + log(f.V0 / Dc)) - a * log(f.V0);
+      const double xstart = log((pass == 1) ? f.V[i] : f.V1[i]);
+      double x;
+      const int it = solve_lnV(tau, sig, c0, a, f.eta, xstart, f.newton_tol, f.newton_maxit, &x);
+      if (it < 0) flags |= SBIEM_FLAG_NEWTON;
+      iters = it < 0 ? -it : it;
+      Vn = exp(x);
+    }
+    const double thd_new = 1.0 - thp * Vn / Dc;
+    if (pass == 1) {
+      f.V1[i] = Vn;
+      f.thd1[i] = thd_new;
+    } else {
+      f.V2[i] = Vn;
+      f.psi2[i] = log(thp);
+      f.thd2[i] = thd_new;
+      f.delta2[i] = f.delta[i] + vb * dt;
+    }
+  }
+  if (flags) atomicOr(&s_flags, flags);
+  if (iters) {
+    atomicMax(&s_itmax, iters);
+    atomicAdd(&s_itsum, static_cast<unsigned long long>(iters));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_flags) atomicOr(f.status, s_flags);
+    if (s_itmax) atomicMax(f.it_max, s_itmax);
+    if (s_itsum) atomicAdd(f.it_sum, s_itsum);
+  }
+}
+
+// ------------------------------------------------------------- commit
+template <class R>
+__global__ void k_commit(DevFault<R> f, int m_dt, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (*f.status) return;
+  if (i < f.N) {
+    f.V[i] = f.V2[i];
+    f.psi[i] = f.psi2[i];
+    f.thd[i] = f.thd2[i];
+    f.delta[i] = f.delta2[i];
+  }
+  if (i < f.nmodes) {
+    const double2 U = f.U2[i], Q = f.Q2[i];
+    double2 D = f.dhat[i], K = f.khat[i];
+    D.x += dt * U.x;
+    D.y += dt * U.y;
+    K.x += dt * Q.x;
+    K.y += dt * Q.y;
+    f.dhat[i] = D;
+    f.khat[i] = K;
+    const int Rn = f.Rn[i];
+    if (Rn > 0) {
+      Slot<R> s;
+      if constexpr (sizeof(R) == 8) {
+        s.t = U;
+        s.n = Q;
+      } else {
+        s = make_float4(static_cast<float>(U.x), static_cast<float>(U.y), static_cast<float>(Q.x),
+                        static_cast<float>(Q.y));
+      }
+      Slot<R>* ring = f.ring + f.ring_off[i];
+      int h = f.head[i];
+      const int cnt = min(m_dt, Rn);
+      for (int c = 0; c < cnt; ++c) {
+        h = (h == 0) ? Rn - 1 : h - 1;
+        ring[h] = s;
+      }
+      if (m_dt > Rn) h = static_cast<int>(((h - static_cast<int64_t>(m_dt - Rn)) % Rn + Rn) % Rn);
+      f.head[i] = h;
+    }
+  }
+  if (i == 0) {
+    *f.steps_done += 1;
+    *f.t += dt;
+  }
+}
+
+// ------------------------------------------------------------- weights
+// w_{n,j} = dt_min C(k_n, (j + 1/2) dt_min): midpoint rule (Sec. 3.3),
+// kernels from the piecewise Chebyshev table (Clenshaw recurrence).
+template <class R>
+__global__ void k_weights(W2<R>* w, const int64_t* w_off, const int32_t* Mn, int nmodes, double L,
+                          double cs, double dt, const double* __restrict__ cheb, int npieces, int deg,
+                          double h) {
+  const int n = blockIdx.x;
+  if (n == 0 || n >= nmodes) return;
+  const double k = kTwoPi * n / L;
+  const int M = Mn[n];
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    const double s = cs * k * (j + 0.5) * dt;
+    int p = static_cast<int>(s / h);
+    p = min(p, npieces - 1);
+    const double t = 2.0 * (s - p * h) / h - 1.0;
+    const double* c = cheb + static_cast<size_t>(p) * (deg + 1) * 2;
+    double bT1 = 0.0, bT2 = 0.0, bN1 = 0.0, bN2 = 0.0;
+    for (int kk = deg; kk >= 1; --kk) {
+      const double tT = 2.0 * t * bT1 - bT2 + c[2 * kk];
+      const double tN = 2.0 * t * bN1 - bN2 + c[2 * kk + 1];
+      bT2 = bT1;
+      bT1 = tT;
+      bN2 = bN1;
+      bN1 = tN;
+    }
+    W2<R> out;
+    out.x = static_cast<R>(dt * (t * bT1 - bT2 + c[0]));
+    out.y = static_cast<R>(dt * (t * bN1 - bN2 + c[1]));
+    w[w_off[n] + j] = out;
+  }
+}
+
+// ------------------------------------------------------------- utilities
+__global__ void k_pack(int N, const double* x, const double* y, const double* ymul, double2* z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double yi = 0.0;
+  if (y) yi = y[i] * (ymul ? ymul[i] : 1.0);
+  z[i] = make_double2(x[i], yi);
+}
+
+__global__ void k_unpack(int N, const double2* Z, double2* X, double2* Y) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n > N / 2) return;
+  const double2 a = Z[n], c = Z[(N - n) & (N - 1)];
+  if (X) X[n] = make_double2(0.5 * (a.x + c.x), 0.5 * (a.y - c.y));
+  if (Y) Y[n] = make_double2(0.5 * (a.y + c.y), -0.5 * (a.x - c.x));
+}
+
+__global__ void k_d2(int N, double L, double2* Z) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int m = n <= N / 2 ? n : N - n;
+  const double k = kTwoPi * m / L;
+  Z[n].x *= -k * k;
+  Z[n].y *= -k * k;
+}
+
+__global__ void k_real_part(int N, const double2* z, double* x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) x[i] = z[i].x;
+}
+
+// ------------------------------------------------------------- launchers
+FftGeom make_geom(int N, int elem_bytes) {
+  FftGeom g{};
+  g.N = N;
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  g.lgN1 = (lg + 1) / 2;
+  g.lgN2 = lg - g.lgN1;
+  g.N1 = 1 << g.lgN1;
+  g.N2 = 1 << g.lgN2;
+  // B rows or columns per CTA: 32 contiguous bytes per global segment
+  const int B = elem_bytes >= 32 ? 1 : 32 / elem_bytes;
+  g.Bc = B < g.N1 ? B : g.N1;
+  g.Br = B < g.N2 ? B : g.N2;
+  auto threads = [](int work) {
+    int t = work;
+    if (t > 256) t = 256;
+    if (t < 32) t = 32;
+    return t;
+  };
+  g.tc = threads(g.Bc * g.N2 / 2);
+  g.tr = threads(g.Br * g.N1 / 2);
+  return g;
+}
+
+template <class R>
+static size_t col_smem(const FftGeom& g) { return (static_cast<size_t>(g.Bc) * g.N2 + g.N2 / 2) * sizeof(Cx<R>); }
+template <class R>
+static size_t row_smem(const FftGeom& g) { return (static_cast<size_t>(g.Br) * g.N1 + g.N1 / 2) * sizeof(Cx<R>); }
+
+template <class K>
+static void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+
+template <class R>
+void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
+  const FftGeom& g = f.g;
+  const double dt = m_dt * f.dt_min;
+  const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
+  auto kfa = k_col<R, false, PRO_PASS>;
+  auto kfb = k_row<R, false>;
+  auto kia = k_col<R, true, PRO_ASSEMBLE>;
+  auto kib = k_row<R, true>;
+  kfa<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
+  kfb<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.Z, R(1), f.status);
+  kia<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
+  kib<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.y, R(1.0 / g.N), f.status);
+  const int nt = 64;
+  k_newton<R><<<(f.N + nt - 1) / nt, nt, 0, st>>>(f, pass, dt);
+}
+
+template <class R>
+void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+  if (f.nchunks == 0) return;
+  const int gr = grid < f.nchunks ? grid : f.nchunks;
+  k_history<R><<<gr, kHistThreads, 0, st>>>(f, m_dt);
+}
+
+template <class R>
+void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st) {
+  const int n = f.N > f.nmodes ? f.N : f.nmodes;
+  const int nt = 256;
+  k_commit<R><<<(n + nt - 1) / nt, nt, 0, st>>>(f, m_dt, m_dt * f.dt_min);
+}
+
+template <class R>
+void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg, double h, double cs,
+                    cudaStream_t st) {
+  k_weights<R><<<f.nmodes, 256, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.L, cs, f.dt_min, cheb, npieces, deg, h);
+}
+
+void launch_fft64(const FftGeom& g, const double2* tw, const double2* in, double2* tmp, double2* out,
+                  bool inverse, cudaStream_t st) {
+  DevFault<double> none{};
+  const size_t cs = col_smem<double>(g), rs = row_smem<double>(g);
+  if (!inverse) {
+    auto kc = k_col<double, false, PRO_LOAD>;
+    auto kr = k_row<double, false>;
+    kc<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, tw, in, tmp, none, 0, 0, 0.0);
+    kr<<<g.N2 / g.Br, g.tr, rs, st>>>(g, tw, tmp, out, 1.0, nullptr);
+  } else {
+    auto kc = k_col<double, true, PRO_LOAD>;
+    auto kr = k_row<double, true>;
+    kc<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, tw, in, tmp, none, 0, 0, 0.0);
+    kr<<<g.N2 / g.Br, g.tr, rs, st>>>(g, tw, tmp, out, 1.0 / g.N, nullptr);
+  }
+}
+
+void launch_pack(int N, const double* x, const double* y, const double* ymul, double2* z, cudaStream_t st) {
+  k_pack<<<(N + 255) / 256, 256, 0, st>>>(N, x, y, ymul, z);
+}
+void launch_unpack(int N, const double2* Z, double2* X, double2* Y, cudaStream_t st) {
+  k_unpack<<<(N / 2 + 1 + 255) / 256, 256, 0, st>>>(N, Z, X, Y);
+}
+void launch_d2(int N, double L, double2* Z, cudaStream_t st) { k_d2<<<(N + 255) / 256, 256, 0, st>>>(N, L, Z); }
+void launch_real_part(int N, const double2* z, double* x, cudaStream_t st) {
+  k_real_part<<<(N + 255) / 256, 256, 0, st>>>(N, z, x);
+}
+
+template <class R>
+void configure_kernels(const FftGeom& g) {
+  const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
+  allow_smem(k_col<R, false, PRO_PASS>, cs);
+  allow_smem(k_col<R, true, PRO_ASSEMBLE>, cs);
+  allow_smem(k_row<R, false>, rs);
+  allow_smem(k_row<R, true>, rs);
+  const FftGeom g64 = make_geom(g.N, sizeof(double2));
+  allow_smem(k_col<double, false, PRO_LOAD>, col_smem<double>(g64));
+  allow_smem(k_col<double, true, PRO_LOAD>, col_smem<double>(g64));
+  allow_smem(k_row<double, false>, row_smem<double>(g64));
+  allow_smem(k_row<double, true>, row_smem<double>(g64));
+}
+
+template void configure_kernels<double>(const FftGeom&);
+template void configure_kernels<float>(const FftGeom&);
+template void launch_history<double>(const DevFault<double>&, int, int, cudaStream_t);
+template void launch_history<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_pass<double>(const DevFault<double>&, int, int, cudaStream_t);
+template void launch_pass<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_commit<double>(const DevFault<double>&, int, cudaStream_t);
+template void launch_commit<float>(const DevFault<float>&, int, cudaStream_t);
+template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double, cudaStream_t);
+template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double, cudaStream_t);
+
+}  // namespace sbiem

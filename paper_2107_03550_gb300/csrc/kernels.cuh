@@ -1,0 +1,108 @@
+// Device types, launch descriptors and host-side launch wrappers of libsbiem.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "sbiem.h"
+
+namespace sbiem {
+
+// ------------------------------------------------------------ complex types
+template <class R> struct CxT;
+template <> struct CxT<double> { using T = double2; };
+template <> struct CxT<float> { using T = float2; };
+template <class R> using Cx = typename CxT<R>::T;
+
+// One history slot of one mode: F[Vbar] (shear field) and F[kappa Vbar]
+// (normal field), complex each.
+struct __align__(32) Slot64 { double2 t, n; };
+using Slot32 = float4;  // (T.re, T.im, N.re, N.im)
+template <class R> struct SlotT;
+template <> struct SlotT<double> { using T = Slot64; };
+template <> struct SlotT<float> { using T = Slot32; };
+template <class R> using Slot = typename SlotT<R>::T;
+
+// Kernel weight pair (w^T_{n,j}, w^N_{n,j}) of one lag.
+template <class R> using W2 = Cx<R>;
+
+// One chunk of consecutive history slots of one mode.
+struct Chunk {
+  int32_t mode;
+  int32_t first;  // chunk index of the mode's first chunk
+  int32_t count;  // chunks of this mode
+  int32_t pad;
+  int64_t i0, i1;  // slot range [i0, i1) within the mode's ring
+};
+
+// Four-step FFT geometry: N = N1 * N2, column pass (length N2) then row pass
+// (length N1); B columns or rows per CTA.
+struct FftGeom {
+  int N, N1, N2, lgN1, lgN2, Bc, Br, tc, tr;
+};
+
+// Pointers of one fault on the device.
+template <class R>
+struct DevFault {
+  int N;
+  int nmodes;          // N/2 + 1
+  double L, S, mu, eta, dt_min, f0, V0;
+  int state_law;
+  int newton_maxit;
+  double newton_tol;
+  // element state (FP64)
+  double *V, *psi, *thd, *delta;          // committed
+  double *V1, *thd1;                       // pass-1 results
+  double *Vbar;                            // pass slip rate
+  double *V2, *psi2, *thd2, *delta2;       // pass-2 results (staged)
+  double *a, *b, *Dc, *sig0, *tau0, *taur, *Vp, *kappa;
+  uint8_t* presc;
+  // spectral state (FP64)
+  double2 *dhat, *khat;                    // F[delta], F[kappa delta]
+  double2 *U2, *Q2;                        // staged pass-2 spectra
+  double2 *AT, *AN;                        // history sums
+  double4* partial;                        // per-chunk partial sums
+  int* counter;                            // per-mode chunk counters
+  // history
+  Slot<R>* ring;
+  W2<R>* w;
+  const int64_t *ring_off, *w_off;
+  const int32_t *Rn, *Mn;
+  int32_t* head;
+  const Chunk* chunks;
+  int nchunks;
+  // FFT work
+  Cx<R> *z, *zt, *Z, *y;                   // natural-order input, transposed, spectrum, output
+  const Cx<R>* tw;                         // exp(-2 pi i j/N)
+  FftGeom g;
+  // bookkeeping
+  unsigned* status;
+  long long* steps_done;
+  double* t;
+  unsigned long long* it_sum;
+  int* it_max;
+};
+
+// Host launch wrappers (kernels.cu).
+template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
+template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
+template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st);
+template <class R> void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg,
+                                       double h, double cs, cudaStream_t st);
+
+// FP64 utility transforms on caller buffers of length N (natural order):
+// forward: Z = sum_i z_i exp(-2 pi i n i/N); inverse: z = (1/N) sum_n Z_n exp(+...).
+void launch_fft64(const FftGeom& g, const double2* tw, const double2* in, double2* tmp,
+                  double2* out, bool inverse, cudaStream_t st);
+// Pack z = x + i y from two real arrays; y may be NULL (zero imaginary part).
+void launch_pack(int N, const double* x, const double* y, const double* ymul, double2* z, cudaStream_t st);
+// From the spectrum Z of z = x + i y: X_n, Y_n for n = 0..N/2.
+void launch_unpack(int N, const double2* Z, double2* X, double2* Y, cudaStream_t st);
+// Z_n *= -k_{|n|}^2 (second derivative on the periodic grid of length L).
+void launch_d2(int N, double L, double2* Z, cudaStream_t st);
+void launch_real_part(int N, const double2* z, double* x, cudaStream_t st);
+
+FftGeom make_geom(int N, int elem_bytes);
+// Opt the FFT kernels into the dynamic shared memory they need (once per geometry).
+template <class R> void configure_kernels(const FftGeom& g);
+
+}  // namespace sbiem

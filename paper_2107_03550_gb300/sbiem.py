@@ -1,0 +1,296 @@
+"""Python binding of libsbiem (ctypes): argument marshalling only.
+
+Every step of the time integration runs in the library's CUDA kernels; this
+module converts numpy arrays to pointers, maps return codes to exceptions
+and, when PyTorch is present, routes the library's device allocations
+through PyTorch's caching allocator and its launches onto a PyTorch stream.
+There is no CPU fallback: if ``libsbiem.so`` is missing the import of
+:class:`Fault` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Fault", "SbiemError", "kernel_values", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
+           "FLAG_STATE", "ERR"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+FLAG_NEWTON, FLAG_OPENING, FLAG_STATE = 1, 2, 4
+ERR = {0: "OK", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -4: "NEWTON", -5: "OPENING", -6: "STATE",
+       -7: "DTMIN", -8: "UNSUPPORTED"}
+
+_alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("dx", ctypes.c_double), ("mu", ctypes.c_double),
+                ("cs", ctypes.c_double), ("cp", ctypes.c_double), ("beta_min", ctypes.c_double),
+                ("eta_w", ctypes.c_double), ("kc_L", ctypes.c_double), ("kc_units", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("state_law", ctypes.c_int32),
+                ("newton_maxit", ctypes.c_int32), ("newton_tol", ctypes.c_double),
+                ("f0", ctypes.c_double), ("V0", ctypes.c_double),
+                ("alloc_fn", _alloc_t), ("free_fn", _free_t), ("alloc_user", ctypes.c_void_p)]
+
+
+class SbiemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sbiem error {code} ({ERR.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return os.environ.get("SBIEM_LIB", os.path.join(_HERE, "_lib", "libsbiem.so"))
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
+_VP = ctypes.c_void_p
+
+_SIGS = {
+    "sbiem_default_params": (None, [ctypes.POINTER(Params)]),
+    "sbiem_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(Params), _D, _D, _D, _D, _D, _D, _D,
+                                    _D, _U8, _D, _D, _D]),
+    "sbiem_destroy": (None, [_VP]),
+    "sbiem_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "sbiem_step": (ctypes.c_int, [_VP, ctypes.c_double]),
+    "sbiem_enqueue": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int64]),
+    "sbiem_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _I64, ctypes.c_int]),
+    "sbiem_step_host": (ctypes.c_int, [_VP, ctypes.c_double, _D, _D]),
+    "sbiem_get_state": (ctypes.c_int, [_VP, _D, _D, _D, _D, _D, _D]),
+    "sbiem_set_state": (ctypes.c_int, [_VP, _D, _D, _D]),
+    "sbiem_windows": (ctypes.c_int, [_VP, _I64]),
+    "sbiem_set_history": (ctypes.c_int, [_VP, _D, _D]),
+    "sbiem_get_history": (ctypes.c_int, [_VP, _D, _D]),
+    "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
+    "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
+    "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
+    "sbiem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sbiem_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libsbiem.so and declare its signatures; raises if it is missing."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise ImportError(f"libsbiem.so not found at {p}; build it with "
+                          f"`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _ptr(a, dtype=np.float64, n=None):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if n is not None and arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    ct = ctypes.c_uint8 if dtype == np.uint8 else ctypes.c_double
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _torch_allocator():
+    """(alloc, free) callbacks backed by torch's CUDA caching allocator, or None."""
+    try:
+        import torch
+    except ImportError:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, _user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev))
+        except Exception:  # out of memory: the library reports SBIEM_ERR_NOMEM
+            return None
+
+    def _free(ptr, _user):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _alloc_t(_alloc), _free_t(_free)
+
+
+def kernel_values(s, r: float):
+    """Library route of (C^T_II, C^N_II) at points s = c_s |k| t (host FP64, no GPU)."""
+    lib = load_library()
+    sa = np.ascontiguousarray(np.asarray(s, np.float64).ravel())
+    cT = np.empty_like(sa)
+    cN = np.empty_like(sa)
+    rc = lib.sbiem_kernel_values(sa.ctypes.data_as(_D), sa.size, float(r), cT.ctypes.data_as(_D),
+                                 cN.ctypes.data_as(_D))
+    if rc != 0:
+        raise SbiemError(rc, "kernel_values: invalid argument")
+    return cT, cN
+
+
+class Fault:
+    """One periodic non-planar fault on the GPU (a libsbiem handle)."""
+
+    def __init__(self, N, dx, mu, cs, cp, f0, V0, a, b, Dc, sigma_load, V_init, theta_init,
+                 kappa=None, h=None, tau_load=None, tau_load_rate=None, prescribed=None,
+                 V_presc=None, beta_min=0.25, eta_w=1.0, kc_L=200.0, kc_units=0, precision=0,
+                 state_law=0, newton_maxit=50, newton_tol=1e-12, use_torch=True, lib=None):
+        self.lib = lib or load_library()
+        self.N = int(N)
+        p = Params()
+        self.lib.sbiem_default_params(ctypes.byref(p))
+        p.N, p.dx, p.mu, p.cs, p.cp = self.N, dx, mu, cs, cp
+        p.beta_min, p.eta_w, p.kc_L, p.kc_units = beta_min, eta_w, kc_L, kc_units
+        p.precision, p.state_law = precision, state_law
+        p.newton_maxit, p.newton_tol, p.f0, p.V0 = newton_maxit, newton_tol, f0, V0
+        self._cb = _torch_allocator() if use_torch else None
+        if self._cb is not None:
+            p.alloc_fn, p.free_fn = self._cb
+        self.params = p
+        n = self.N
+        keep = []
+
+        def P(x, dtype=np.float64):
+            arr, ptr = _ptr(x, dtype, n)
+            keep.append(arr)
+            return ptr
+
+        handle = _VP()
+        rc = self.lib.sbiem_create(ctypes.byref(handle), ctypes.byref(p), P(h), P(kappa), P(a), P(b), P(Dc),
+                                   P(sigma_load), P(tau_load), P(tau_load_rate),
+                                   P(None if prescribed is None else np.asarray(prescribed).astype(np.uint8),
+                                     np.uint8),
+                                   P(V_presc), P(V_init), P(theta_init))
+        self._check(rc)
+        self.h = handle
+        self.dt_min = beta_min * dx / cs
+        self._stream = None
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        """Handle for a :class:`paper_2107_03550_gb300.workloads.Workload`."""
+        args = dict(N=w.N, dx=w.dx, mu=w.mu, cs=w.cs, cp=w.cp, f0=w.f0, V0=w.V0, a=w.a, b=w.b, Dc=w.Dc,
+                    sigma_load=w.sigma_load, V_init=w.V_init, theta_init=w.theta_init, kappa=w.kappa,
+                    tau_load=w.tau_load, tau_load_rate=w.tau_load_rate,
+                    prescribed=w.prescribed if np.any(w.prescribed) else None,
+                    V_presc=w.V_presc if np.any(w.prescribed) else None,
+                    beta_min=w.dt_min * w.cs / w.dx)
+        args.update(kw)
+        return cls(**args)
+
+    # ---------------------------------------------------------------- errors
+    def _check(self, rc):
+        if rc != 0:
+            raise SbiemError(rc, self.lib.sbiem_last_error().decode())
+
+    # ------------------------------------------------------------------ steps
+    def set_stream(self, stream) -> None:
+        """Bind to a CUDA stream: a torch.cuda.Stream, a raw handle (int) or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._stream = stream
+        self._check(self.lib.sbiem_set_stream(self.h, _VP(raw or None)))
+
+    def step(self, dt=None) -> None:
+        self._check(self.lib.sbiem_step(self.h, float(dt or self.dt_min)))
+
+    def try_step(self, dt=None) -> int:
+        """One step; returns the SBIEM code instead of raising on a rejected step."""
+        return int(self.lib.sbiem_step(self.h, float(dt or self.dt_min)))
+
+    def enqueue(self, nsteps: int, dt=None) -> None:
+        self._check(self.lib.sbiem_enqueue(self.h, float(dt or self.dt_min), int(nsteps)))
+
+    def status(self, clear: bool = False):
+        fl = ctypes.c_uint32()
+        st = ctypes.c_int64()
+        self._check(self.lib.sbiem_status(self.h, ctypes.byref(fl), ctypes.byref(st), int(clear)))
+        return int(fl.value), int(st.value)
+
+    def step_host(self, dt=None, tau_load=None, V_out=None) -> None:
+        ta, tp = _ptr(tau_load, np.float64, self.N)
+        vp = None
+        if V_out is not None:
+            assert V_out.dtype == np.float64 and V_out.flags.c_contiguous and V_out.size == self.N
+            vp = V_out.ctypes.data_as(_D)
+        self._check(self.lib.sbiem_step_host(self.h, float(dt or self.dt_min), tp, vp))
+
+    # ------------------------------------------------------------------ state
+    def get_state(self) -> dict:
+        n = self.N
+        out = {k: np.empty(n) for k in ("delta", "V", "theta", "tau_el", "sigma_el")}
+        t = ctypes.c_double()
+        self._check(self.lib.sbiem_get_state(self.h, *(out[k].ctypes.data_as(_D) for k in
+                                                       ("delta", "V", "theta", "tau_el", "sigma_el")),
+                                             ctypes.byref(t)))
+        out["t"] = t.value
+        return out
+
+    def set_state(self, delta=None, V=None, theta=None) -> None:
+        a1, p1 = _ptr(delta, np.float64, self.N)
+        a2, p2 = _ptr(V, np.float64, self.N)
+        a3, p3 = _ptr(theta, np.float64, self.N)
+        self._check(self.lib.sbiem_set_state(self.h, p1, p2, p3))
+
+    def windows(self) -> np.ndarray:
+        M = np.empty(self.N // 2 + 1, dtype=np.int64)
+        self._check(self.lib.sbiem_windows(self.h, M.ctypes.data_as(_I64)))
+        return M
+
+    def history_size(self) -> int:
+        return int(np.maximum(self.windows() - 1, 0).sum())
+
+    def set_history(self, HT: np.ndarray, HN: np.ndarray) -> None:
+        """Flat complex128 arrays, modes in order, newest slot first per mode."""
+        tot = self.history_size()
+        a = np.ascontiguousarray(np.asarray(HT, np.complex128).reshape(tot)).view(np.float64)
+        b = np.ascontiguousarray(np.asarray(HN, np.complex128).reshape(tot)).view(np.float64)
+        self._check(self.lib.sbiem_set_history(self.h, a.ctypes.data_as(_D), b.ctypes.data_as(_D)))
+
+    def get_history(self):
+        tot = self.history_size()
+        a = np.empty(2 * tot)
+        b = np.empty(2 * tot)
+        self._check(self.lib.sbiem_get_history(self.h, a.ctypes.data_as(_D), b.ctypes.data_as(_D)))
+        return a.view(np.complex128), b.view(np.complex128)
+
+    def newton_stats(self):
+        s = ctypes.c_int64()
+        m = ctypes.c_int32()
+        self._check(self.lib.sbiem_newton_stats(self.h, ctypes.byref(s), ctypes.byref(m)))
+        return int(s.value), int(m.value)
+
+    def footprint(self):
+        hb = ctypes.c_int64()
+        db = ctypes.c_int64()
+        self._check(self.lib.sbiem_footprint(self.h, ctypes.byref(hb), ctypes.byref(db)))
+        return int(hb.value), int(db.value)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.sbiem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

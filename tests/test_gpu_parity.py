@@ -1,0 +1,245 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: the plain FP64 path must match the oracle to 1e-10 relative
+(max-norm) in slip and tractions; the precision form (FP32 history
+convolution and FFTs, FP64 state) to 1e-4 relative in final slip with the
+rupture front arriving within one time step.
+"""
+import numpy as np
+import pytest
+
+from paper_2107_03550_gb300.workloads import (element_x, rough_cycle, rough_fault,
+                                              seamount_rupture)
+from tests.gpu_helpers import compare, gpu_for, oracle_for, prefill, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_03550_gb300 import sbiem
+    sbiem.load_library()
+
+
+def test_seamount_rupture_1000_steps_fp64():
+    w = seamount_rupture()
+    o = oracle_for(w)
+    g = gpu_for(w)
+    worst = {}
+    for s in range(1000):
+        assert o.step() == 0
+        g.step()
+        if s % 25 == 24 or s == 999:
+            err = compare(o, g)
+            for k, v in err.items():
+                worst[k] = max(worst.get(k, 0.0), v)
+    assert o.V.max() > 1.0          # the rupture is under way
+    for k in ("delta", "tau_el", "sigma_el"):
+        assert worst[k] < TOL64, (k, worst)
+    assert worst["V"] < 1e-9, worst
+    g.close()
+
+
+@pytest.mark.parametrize("N,dx,seed", [(16, 25.0, 1), (64, 25.0, 2), (256, 10.0, 3), (2048, 10.0, 4)])
+def test_prefilled_history_random_state(N, dx, seed):
+    # random state and a full, random history: several chunks per mode with
+    # ragged tails (N = 2048: 8191 slots in mode 1, 2048 per chunk)
+    w = rough_fault(N, dx, 3e-3, seed=seed)
+    rng = np.random.default_rng(seed)
+    w.V_init = np.exp(rng.uniform(np.log(1e-9), np.log(1.0), N))
+    w.theta_init = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), N))
+    w.tau_load = w.sigma_load * 0.6 + rng.normal(0, 1e5, N)
+    o = oracle_for(w)
+    g = gpu_for(w)
+    delta0 = rng.uniform(0.0, 0.5, N)
+    o.delta = delta0.copy()
+    g.set_state(delta=delta0)
+    prefill(o, g, seed, scale=1e-4)
+    for _ in range(3):
+        assert o.step() == 0
+        g.step()
+        err = compare(o, g)
+        for k in ("delta", "tau_el", "sigma_el", "theta"):
+            assert err[k] < TOL64, (k, err)
+        assert err["V"] < 1e-9, err
+    g.close()
+
+
+def test_full_size_rough_cycle_step():
+    # the bench configuration: N = 4096, full windows of seeded history
+    w = rough_cycle()
+    o = oracle_for(w)
+    g = gpu_for(w)
+    prefill(o, g, seed=7, scale=1e-10)
+    for _ in range(2):
+        assert o.step() == 0
+        g.step()
+    err = compare(o, g)
+    for k in ("delta", "tau_el", "sigma_el", "theta"):
+        assert err[k] < TOL64, (k, err)
+    assert err["V"] < 1e-9, err
+    g.close()
+
+
+def test_graph_replay_equals_single_steps_and_is_deterministic():
+    w = seamount_rupture(N=256)
+    g1 = gpu_for(w)
+    g2 = gpu_for(w)
+    for _ in range(60):
+        g1.step()
+    g2.enqueue(60)
+    flags, done = g2.status()
+    assert flags == 0 and done == 60
+    s1, s2 = g1.get_state(), g2.get_state()
+    for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+        assert np.array_equal(s1[k], s2[k]), k
+    g1.close()
+    g2.close()
+
+
+def test_step_host_matches_device_state():
+    w = seamount_rupture(N=256)
+    g = gpu_for(w)
+    V = np.empty(w.N)
+    o = oracle_for(w)
+    tau = o.tau_load.copy()
+    for _ in range(5):
+        g.step_host(tau_load=tau, V_out=V)
+        assert o.step() == 0
+    assert np.array_equal(V, g.get_state()["V"])
+    assert rel(V, o.V) < 1e-9
+    g.close()
+
+
+def test_flat_fault_and_uniform_slip_rate():
+    w = seamount_rupture(N=256)
+    w.kappa = np.zeros(w.N)
+    g = gpu_for(w)
+    for _ in range(20):
+        g.step()
+    s = g.get_state()
+    assert np.abs(s["sigma_el"]).max() <= 1e-13 * np.abs(s["tau_el"]).max()
+    g.close()
+    w2 = rough_fault(256, 25.0, 3e-3, seed=9)
+    w2.V_init = np.full(w2.N, 1e-3)
+    w2.theta_init = np.full(w2.N, 1.0)
+    g2 = gpu_for(w2)
+    o2 = oracle_for(w2)
+    g2.step()
+    assert o2.step() == 0
+    s2 = g2.get_state()
+    assert rel(s2["V"], o2.V) < 1e-9
+    g2.close()
+
+
+def test_failures_leave_state_unchanged():
+    from paper_2107_03550_gb300.sbiem import SbiemError
+    # Newton cap of one iteration cannot converge from the nucleation state
+    w = seamount_rupture(N=256)
+    g = gpu_for(w, newton_maxit=1)
+    before = g.get_state()
+    with pytest.raises(SbiemError) as ei:
+        g.step()
+    assert ei.value.code == -4
+    after = g.get_state()
+    for k in ("delta", "V", "theta"):
+        assert np.array_equal(before[k], after[k]), k
+    g.close()
+    # opening: tiny normal load and a curved, slipping fault
+    w = seamount_rupture(N=256, amp=400.0)
+    w.sigma_load = np.full(w.N, 1.0)
+    g = gpu_for(w)
+    g.set_state(delta=np.full(w.N, 1.0))
+    before = g.get_state()
+    with pytest.raises(SbiemError) as ei:
+        g.step()
+    assert ei.value.code == -5
+    after = g.get_state()
+    for k in ("delta", "V", "theta"):
+        assert np.array_equal(before[k], after[k]), k
+    g.close()
+    # explicit state update overshooting to theta < 0 (V dt / Dc >> 1)
+    w = seamount_rupture(N=256)
+    w.V_init = np.full(w.N, 10.0)
+    g = gpu_for(w, state_law=1)
+    with pytest.raises(SbiemError) as ei:
+        g.step()
+    assert ei.value.code == -6
+    g.close()
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2107_03550_gb300.sbiem import Fault, SbiemError
+    w = seamount_rupture(N=256)
+    g = gpu_for(w)
+    with pytest.raises(SbiemError) as ei:
+        g.step(1.5 * g.dt_min)
+    assert ei.value.code == -1
+    g.close()
+    with pytest.raises(SbiemError) as ei:
+        Fault(N=100, dx=w.dx, mu=w.mu, cs=w.cs, cp=w.cp, f0=w.f0, V0=w.V0, a=np.ones(100) * 0.01,
+              b=np.ones(100) * 0.015, Dc=np.ones(100) * 1e-3, sigma_load=np.ones(100) * 5e7,
+              V_init=np.ones(100) * 1e-9, theta_init=np.ones(100), kappa=np.zeros(100))
+    assert ei.value.code == -1
+
+
+def test_curvature_from_profile():
+    # kappa = h'' by spectral differentiation on the device vs numpy's
+    w = rough_fault(512, 10.0, 3e-3, seed=4)
+    k = 2 * np.pi * np.fft.rfftfreq(w.N, w.dx)
+    kap = np.fft.irfft(-(k ** 2) * np.fft.rfft(w.h), n=w.N)
+    w.kappa = kap
+    o = oracle_for(w)
+    from paper_2107_03550_gb300.sbiem import Fault
+    args = dict(N=w.N, dx=w.dx, mu=w.mu, cs=w.cs, cp=w.cp, f0=w.f0, V0=w.V0, a=w.a, b=w.b, Dc=w.Dc,
+                sigma_load=w.sigma_load, V_init=w.V_init, theta_init=w.theta_init, h=w.h)
+    g = Fault(**args)
+    for _ in range(30):
+        assert o.step() == 0
+        g.step()
+    err = compare(o, g)
+    assert err["sigma_el"] < 1e-9, err
+    g.close()
+
+
+def test_history_roundtrip_and_windows():
+    w = rough_fault(512, 10.0, 1e-3, seed=5)
+    g = gpu_for(w)
+    o = oracle_for(w)
+    HT, HN = prefill(o, g, seed=3)
+    hT, hN = g.get_history()
+    assert np.array_equal(hT, HT) and np.array_equal(hN, HN)
+    assert np.array_equal(g.windows(), o.M)
+    g.close()
+
+
+def test_precision_form_rupture():
+    # FP32 history convolution and FFTs, FP64 state: final slip within 1e-4
+    # relative and rupture-front arrival within one step of the oracle's.
+    w = seamount_rupture()
+    o = oracle_for(w)
+    g = gpu_for(w, precision=1)
+    x = element_x(w.N, w.dx)
+    probe = [np.argmin(np.abs(x - xp)) for xp in (-500.0, 0.0, 500.0, 1000.0)]
+    arr_o = {p: None for p in probe}
+    arr_g = {p: None for p in probe}
+    for s in range(1300):
+        assert o.step() == 0
+        g.step()
+        Vg = g.get_state()["V"]
+        for p in probe:
+            if arr_o[p] is None and o.V[p] > 1e-3:
+                arr_o[p] = s
+            if arr_g[p] is None and Vg[p] > 1e-3:
+                arr_g[p] = s
+    assert all(arr_o[p] is not None for p in probe)
+    for p in probe:
+        assert abs(arr_o[p] - arr_g[p]) <= 1, (p, arr_o[p], arr_g[p])
+    st = g.get_state()
+    assert rel(st["delta"], o.delta) < 1e-4
+    g.close()
