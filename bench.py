@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Throughput of the non-planar spectral BIEM time step on one GB300.
+
+Metric: element-steps/s (N elements x accepted steps / device time) of the
+whole step -- history convolution, two passes of predictor / FFTs / spectral
+assembly / Newton, commit -- on the rough-fault cycle workload (N = 4096,
+dx = 10 m, Hurst-1 roughness) with every history window full (steady state).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py --impl reference     # the FP64 CPU oracle on the same workload
+
+Timing: each timed step runs as one CUDA-graph launch; CUDA events recorded
+inside the graph on the launch stream bracket the step and its history
+convolution.  L2 is flushed (256 MiB write) before every timed step, outside
+the events.  Under torchrun every rank runs an independent replica (the path
+has no exchange step), the maximum device time over ranks is taken and the
+value sums all ranks' element-steps.  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "element-steps/s"
+UNIT = "element-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+HIST_AMP = 1e-3   # m/s: slip-rate amplitude of the seeded history (spectral scale amp*sqrt(N))
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--N", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(N):
+    from paper_2107_03550_gb300.workloads import rough_cycle
+    return rough_cycle(N=N, lam_max=min(40e3, N * 10.0))
+
+
+def _history(M, seed, N):
+    from paper_2107_03550_gb300.workloads import random_history
+    R = np.maximum(np.asarray(M) - 1, 0)
+    return random_history(R, seed, HIST_AMP * np.sqrt(N))
+
+
+def _workload_name(w, N):
+    return (f"rough-fault cycle, steady state: N={N}, dx={w.dx:g} m, Hurst-1 roughness alpha=0.005, "
+            f"lambda in [20 m, {min(40e3, N * 10.0) / 1e3:g} km], central 70% rate-and-state, "
+            f"outer 30% at V_pl; dt = dt_min = 0.25 dx/cs; every history window full")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.idx = device_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def _oracle_leg(N: int, seconds: float, max_steps: int | None = None) -> dict:
+    """The FP64 oracle, as it stands, on the same workload (steady state)."""
+    from oracle import Oracle, Params
+    w = _workload(N)
+    p = Params(N=w.N, dx=w.dx, mu=w.mu, cs=w.cs, cp=w.cp, dt_min=w.dt_min)
+    o = Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, None, w.V_init, w.theta_init,
+               prescribed=w.prescribed, V_presc=w.V_presc)
+    HT, HN, off = _history(o.M, 11, N)
+    o.set_history([HT[off[n]:off[n + 1]] for n in range(o.M.size)],
+                  [HN[off[n]:off[n + 1]] for n in range(o.M.size)])
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        if o.step() != 0:
+            raise RuntimeError("oracle step failed")
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and steps >= max_steps):
+            break
+    return {"value": N * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steady-state steps of the N={N} rough-fault workload "
+                      f"(numpy FP64, single thread), {el:.1f} s"}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(precision: str, N: int):
+    """ncu DRAM bytes per history-convolution launch, if recorded for the current kernel source."""
+    src = open(os.path.join(ROOT, "paper_2107_03550_gb300", "csrc", "kernels.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", f"k_history_{precision}_rough_cycle_N{N}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("kernels.cu sha256[:16]") != sha:
+        return None
+    try:
+        return float(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# -------------------------------------------------------------- reference
+def run_reference(a):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    # bounded sample: at most K steps and at most about a minute of CPU time
+    cpu = _oracle_leg(a.N, 60.0, max_steps=max(a.steps, 1))
+    line = {"impl": "reference", "metric": METRIC, "value": cpu["value"], "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_name(_workload(a.N), a.N), "N": a.N, "precision": "fp64"},
+            "cpu_baseline": {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": cpu["sample"]},
+            "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(a):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2107_03550_gb300.sbiem import Fault
+
+    N = a.N
+    w = _workload(N)
+    prec = 1 if a.precision == "fp32" else 0
+    g = Fault.from_workload(w, precision=prec)
+    stream = torch.cuda.current_stream()
+    g.set_stream(stream)
+    HT, HN, _ = _history(g.windows(), 11 + rank, N)
+    g.set_history(HT, HN)
+    hist_bytes, dev_bytes = g.footprint()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    # warm-up (graph capture happens here)
+    g.probe_enable(True)
+    for _ in range(max(a.warmup, 3)):
+        flush.zero_()
+        g.enqueue(1)
+        g.probe_read()
+    flags, _ = g.status(clear=True)
+    if flags:
+        raise RuntimeError(f"warm-up step failed, status {flags}")
+
+    dev_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and "," not in vis and vis.strip().isdigit():
+        dev_index = int(vis)
+    clocks = ClockSampler(dev_index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ms_step, ms_hist = [], []
+    for _ in range(a.steps):
+        flush.zero_()
+        g.enqueue(1)
+        s_ms, h_ms = g.probe_read()
+        ms_step.append(s_ms)
+        ms_hist.append(h_ms)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    flags, done = g.status(clear=True)
+    if flags:
+        raise RuntimeError(f"timed step failed, status {flags}")
+    it_sum, it_max = g.newton_stats()
+
+    total_s = sum(ms_step) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * N * a.steps / total_s
+    hist_ms = statistics.mean(ms_hist)
+    peak, peak_kind = _peaks()
+    achieved = hist_bytes / (hist_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: per step, tau_load in, V out
+    e2e = None
+    if not a.no_e2e:
+        g.probe_enable(False)
+        tau_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        v_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        tau_np = tau_h.numpy()
+        sig = w.sigma_load
+        fr = w.f0 + w.a * np.log(w.V_init / w.V0) + w.b * np.log(w.theta_init * w.V0 / w.Dc)
+        tau_np[:] = np.where(w.prescribed, 0.0, sig * fr + w.mu / (2 * w.cs) * w.V_init)
+        v_np = v_h.numpy()
+        for _ in range(3):
+            g.step_host(tau_load=tau_np, V_out=v_np)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            g.step_host(tau_load=tau_np, V_out=v_np)
+        el = time.perf_counter() - t0
+        e2e = {"value": N * a.e2e_steps / el * world, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * N + 12}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = _oracle_leg(N, a.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": _workload_name(w, N), "N": N, "dx_m": w.dx,
+                       "precision": a.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed step (256 MiB write outside the timed events)",
+                       "history_slots": int(np.maximum(g.windows() - 1, 0).sum()),
+                       "history_bytes_per_step": hist_bytes, "device_bytes": dev_bytes,
+                       "newton_iters_last_step": {"sum": it_sum, "max": it_max}},
+            "roofline": {"bound": "hbm", "kernel": "k_history", "achieved": achieved, "peak": peak,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": _traffic(a.precision, N), "ms_per_launch": hist_ms,
+                         "algorithmic_bytes_per_launch": hist_bytes},
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": 12 * a.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

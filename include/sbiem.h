@@ -175,6 +175,17 @@ int sbiem_windows(sbiem_t s, int64_t* M);
 int sbiem_set_history(sbiem_t s, const double* hist_T, const double* hist_N);
 int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
 
+/*
+ * Timing probe.  sbiem_probe_enable(s, 1) makes every later step record four
+ * CUDA events on the handle's stream (inside the captured graph as well): at
+ * the start of the step, before and after the history convolution kernel,
+ * and at the end of the step.  sbiem_probe_read synchronizes on the last
+ * event and returns the elapsed milliseconds of the most recent step and of
+ * its history convolution.  Enabling or disabling rebuilds the step graph.
+ */
+int sbiem_probe_enable(sbiem_t s, int on);
+int sbiem_probe_read(sbiem_t s, float* ms_step, float* ms_history);
+
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);

@@ -94,17 +94,33 @@ def W(x) -> np.ndarray:
     return (1.0 - (base + rest)).reshape(x.shape)
 
 
+def _parts(s, r: float):
+    """W, J0, J1 at the S-wave argument s and the P-wave argument s/r."""
+    s = np.asarray(s, dtype=np.float64)
+    sp_ = s / r
+    return (s, sp_, W(s), W(sp_), special.j0(s), special.j1(s), special.j0(sp_), special.j1(sp_))
+
+
+def _gt(parts, r):
+    s, sp_, Ws, Wp, J0s, J1s, J0p, J1p = parts
+    return ((s * s + r * r) * Wp - (s * s + 1.0) * Ws
+            - r * r * J1p + 0.5 * J1s - r * s * J0p + s * J0s)
+
+
+def _gn(parts, r):
+    s, sp_, Ws, Wp, J0s, J1s, J0p, J1p = parts
+    A = (1.0 / (r * r) - 2.0) ** 2 * r * r / 2.0
+    return ((A - r * r - s * s) * Wp + (1.0 + s * s - 1.0 / (2.0 * r * r)) * Ws
+            + (r * r - A) * J1p + (1.0 / (2.0 * r * r) - 1.0) * J1s + r * s * J0p - s * J0s)
+
+
 def G_T(s, r: float) -> np.ndarray:
     """Shear kernel C^T_II as a function of s = c_s k t (Eq. Ct).
 
     C^T = (s^2 + r^2) W(s/r) - (s^2 + 1) W(s) - r^2 J1(s/r) + J1(s)/2
           - r s J0(s/r) + s J0(s),   with c_p k t = s/r and (c_s^2/c_p) k t = r s.
     """
-    s = np.asarray(s, dtype=np.float64)
-    sp_ = s / r
-    return ((s * s + r * r) * W(sp_) - (s * s + 1.0) * W(s)
-            - r * r * special.j1(sp_) + 0.5 * special.j1(s)
-            - r * s * special.j0(sp_) + s * special.j0(s))
+    return _gt(_parts(s, r), r)
 
 
 def G_N(s, r: float) -> np.ndarray:
@@ -114,14 +130,10 @@ def G_N(s, r: float) -> np.ndarray:
     C^N = (A - r^2 - s^2) W(s/r) + (1 + s^2 - 1/(2 r^2)) W(s)
           + (r^2 - A) J1(s/r) + (1/(2 r^2) - 1) J1(s) + r s J0(s/r) - s J0(s).
     """
-    s = np.asarray(s, dtype=np.float64)
-    sp_ = s / r
-    A = (1.0 / (r * r) - 2.0) ** 2 * r * r / 2.0
-    return ((A - r * r - s * s) * W(sp_) + (1.0 + s * s - 1.0 / (2.0 * r * r)) * W(s)
-            + (r * r - A) * special.j1(sp_) + (1.0 / (2.0 * r * r) - 1.0) * special.j1(s)
-            + r * s * special.j0(sp_) - s * special.j0(s))
+    return _gn(_parts(s, r), r)
 
 
 def kernel_pair(s, r: float):
-    """(G_T(s), G_N(s)) evaluated on the same points."""
-    return G_T(s, r), G_N(s, r)
+    """(G_T(s), G_N(s)) from one evaluation of W, J0, J1 at s and s/r."""
+    parts = _parts(s, r)
+    return _gt(parts, r), _gn(parts, r)

@@ -39,7 +39,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .kernels import G_N, G_T
+from .kernels import kernel_pair
 
 __all__ = ["Params", "windows", "weights", "Oracle", "newton_lnV", "state_update",
            "STATUS_OK", "STATUS_NEWTON", "STATUS_OPENING", "STATUS_STATE"]
@@ -127,9 +127,8 @@ def weights(p: Params, M: np.ndarray | None = None):
     mode = np.repeat(np.arange(M.size), M)
     j = np.arange(offsets[-1]) - offsets[mode]
     s = p.cs * k[mode] * (j + 0.5) * p.dt_min
-    wT = p.dt_min * G_T(s, p.r)
-    wN = p.dt_min * G_N(s, p.r)
-    return wT, wN, offsets
+    GT, GN = kernel_pair(s, p.r)
+    return p.dt_min * GT, p.dt_min * GN, offsets
 
 
 def state_update(theta0, Vbar, thetadot_bar, Dc, dt, law: str):
@@ -195,10 +194,11 @@ def newton_lnV(tau, sigma, theta, a, b, Dc, f0, V0, eta, x_start, tol, maxit):
         with np.errstate(divide="ignore", invalid="ignore"):
             xh = x - (x - np.log(np.where(rad, q, 1.0) / eta)) / (1.0 + sigma * a / np.where(rad, q, 1.0))
         xn = np.where(rad, xh, xg)
-        # a step below the tolerance is accepted as converged even when
-        # rounding puts it a hair outside the bracket
+        # a step below the tolerance is accepted as converged, and a Newton
+        # point within tol of the bracket is kept (roots next to the
+        # quasi-static bound land there up to rounding)
         small = np.abs(xn - x) <= tol
-        outside = ((xn < lo) | (xn > hi)) & ~small
+        outside = ((xn < lo - tol) | (xn > hi + tol)) & ~small
         xn = np.where(outside, 0.5 * (lo + hi), xn)
         dx = np.abs(xn - x)
         iters = np.where(conv, iters, it + 1)

@@ -59,6 +59,8 @@ struct sbiem_s {
   long long* h_steps = nullptr;  // pinned
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> graph_defs;
+  bool probe = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   bool fp32() const { return p.precision == 1; }
 };
@@ -94,6 +96,8 @@ void free_all(sbiem_s* s) {
   s->graphs.clear();
   s->graph_defs.clear();
   if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto& e : s->ev)
+    if (e) cudaEventDestroy(e);
   for (void* ptr : s->allocs) {
     if (s->p.free_fn) s->p.free_fn(ptr, s->p.alloc_user);
     else cudaFree(ptr);
@@ -166,14 +170,22 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   return SBIEM_OK;
 }
 
+void probe_mark(sbiem_s* s, int k, cudaStream_t st) {
+  if (s->probe) cudaEventRecordWithFlags(s->ev[k], st, cudaEventRecordExternal);
+}
+
 template <class R>
 void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
+  probe_mark(s, 0, st);
   cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
+  probe_mark(s, 1, st);
   launch_history<R>(f, m, s->sm_count * 4, st);
+  probe_mark(s, 2, st);
   launch_pass<R>(f, 1, m, st);
   launch_pass<R>(f, 2, m, st);
   launch_commit<R>(f, m, st);
+  probe_mark(s, 3, st);
 }
 
 void enqueue_step(sbiem_s* s, int m, cudaStream_t st) {
@@ -673,6 +685,32 @@ int sbiem_get_history(sbiem_t s, double* hT, double* hN) {
       }
     }
   }
+  return SBIEM_OK;
+}
+
+int sbiem_probe_enable(sbiem_t s, int on) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  CK(cudaStreamSynchronize(s->stream));
+  if (on && !s->ev[0])
+    for (auto& e : s->ev) CK(cudaEventCreate(&e));
+  if (static_cast<bool>(on) != s->probe) {
+    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
+    s->graphs.clear();
+    s->graph_defs.clear();
+  }
+  s->probe = on != 0;
+  return SBIEM_OK;
+}
+
+int sbiem_probe_read(sbiem_t s, float* ms_step, float* ms_history) {
+  if (!s || !s->probe) return fail(SBIEM_ERR_INVALID, "probe not enabled");
+  CK(cudaEventSynchronize(s->ev[3]));
+  float a = 0.f, b = 0.f;
+  CK(cudaEventElapsedTime(&a, s->ev[0], s->ev[3]));
+  CK(cudaEventElapsedTime(&b, s->ev[1], s->ev[2]));
+  if (ms_step) *ms_step = a;
+  if (ms_history) *ms_history = b;
   return SBIEM_OK;
 }
 

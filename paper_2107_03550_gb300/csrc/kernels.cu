@@ -113,7 +113,8 @@ __device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass,
     }
     const double2 D = f.dhat[m], K = f.khat[m], AT = f.AT[m], AN = f.AN[m];
     tr = -k * (f.S * (D.x + dt * U.x) + f.mu * (w0T * U.x + AT.x));
-    ti = -k * (f.S * (D.y + dt * U.y) + f.mu * (w0T * U.y + AT.y));
+    // the Nyquist coefficient of a real sequence is real: keep its real part
+    ti = (m < (N >> 1)) ? -k * (f.S * (D.y + dt * U.y) + f.mu * (w0T * U.y + AT.y)) : 0.0;
     if (m < (N >> 1)) {
       const double xr = f.S * (K.x + dt * Q.x) + f.mu * (w0N * Q.x + AN.x);
       const double xi = f.S * (K.y + dt * Q.y) + f.mu * (w0N * Q.y + AN.y);
@@ -379,7 +380,9 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
       *xout = xn;
       return it;
     }
-    if (xn < lo || xn > hi) xn = 0.5 * (lo + hi);
+    // keep Newton points within tol of the bracket: roots next to the
+    // quasi-static bound (vanishing radiation damping) land on it up to rounding
+    if (xn < lo - tol || xn > hi + tol) xn = 0.5 * (lo + hi);
     x = xn;
   }
   *xout = x;

@@ -69,6 +69,8 @@ _SIGS = {
     "sbiem_set_history": (ctypes.c_int, [_VP, _D, _D]),
     "sbiem_get_history": (ctypes.c_int, [_VP, _D, _D]),
     "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
+    "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
     "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
     "sbiem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -265,6 +267,16 @@ class Fault:
         b = np.empty(2 * tot)
         self._check(self.lib.sbiem_get_history(self.h, a.ctypes.data_as(_D), b.ctypes.data_as(_D)))
         return a.view(np.complex128), b.view(np.complex128)
+
+    def probe_enable(self, on: bool = True) -> None:
+        self._check(self.lib.sbiem_probe_enable(self.h, int(on)))
+
+    def probe_read(self):
+        """(ms of the last step, ms of its history convolution), device events."""
+        a = ctypes.c_float()
+        b = ctypes.c_float()
+        self._check(self.lib.sbiem_probe_read(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return float(a.value), float(b.value)
 
     def newton_stats(self):
         s = ctypes.c_int64()

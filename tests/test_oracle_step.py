@@ -179,7 +179,7 @@ def test_tiny_N_space_time_double_sum_equals_spectral(N):
 
 def _bisect(tau, sig, theta, a, b, Dc, f0, V0, eta):
     g = lambda x: tau - eta * np.exp(x) - sig * (f0 + a * (x - np.log(V0)) + b * np.log(theta * V0 / Dc))
-    lo, hi = -200.0, 50.0
+    lo, hi = -400.0, 50.0
     for _ in range(400):
         mid = 0.5 * (lo + hi)
         if g(mid) > 0:
@@ -200,12 +200,15 @@ def test_newton_matches_bisection():
     f = rng.uniform(0.3, 0.9, n)
     eta = 4.33e6
     tau = sig * f
+    # a quarter of the cases sit far below steady sliding (V ~ 1e-30 m/s): the
+    # root then lies next to the quasi-static bound
+    tau[: n // 4] = sig[: n // 4] * rng.uniform(0.0, 0.05, n // 4)
     x, it, conv = newton_lnV(tau, sig, theta, a, b, Dc, 0.6, 1e-6, eta,
                              np.log(1e-9) * np.ones(n), 1e-13, 200)
     assert conv.all()
     ref = np.array([_bisect(tau[i], sig[i], theta[i], a[i], b[i], Dc[i], 0.6, 1e-6, eta) for i in range(n)])
     assert np.abs(x - ref).max() < 1e-11
-    assert it.max() < 40
+    assert it.max() <= 12
 
 
 def test_aging_law_fixed_point_and_explicit_agreement():
