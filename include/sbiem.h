@@ -186,6 +186,17 @@ int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
 int sbiem_probe_enable(sbiem_t s, int on);
 int sbiem_probe_read(sbiem_t s, float* ms_step, float* ms_history);
 
+/*
+ * sbiem_history_sums -- run the truncated history convolution alone (Sec. 3.1
+ * window, Sec. 3.3 step (2), midpoint weights) on the current rings:
+ *   A^T_n = sum_{j=m}^{M_n-1} w^T_{n,j} H^T_n[j-m],  A^N_n likewise,
+ * for the history shift m >= 1 (a step of m dt_min).  AT and AN receive
+ * N/2 + 1 complex values each (re, im interleaved, FP64) in caller-owned host
+ * memory.  The state is not modified.  Synchronizes.
+ * Errors: SBIEM_ERR_INVALID (NULL, m < 1), SBIEM_ERR_CUDA.
+ */
+int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN);
+
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);

@@ -137,6 +137,7 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   f.dt_min = s->dt_min;
   f.f0 = s->p.f0;
   f.V0 = s->p.V0;
+  f.lnV0 = std::log(s->p.V0);
   f.state_law = s->p.state_law;
   f.newton_maxit = s->p.newton_maxit;
   f.newton_tol = s->p.newton_tol;
@@ -150,6 +151,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
 #define COPYP(x) f.x = base.x
   COPYP(V); COPYP(psi); COPYP(thd); COPYP(delta); COPYP(V1); COPYP(thd1); COPYP(Vbar);
   COPYP(V2); COPYP(psi2); COPYP(thd2); COPYP(delta2); COPYP(a); COPYP(b); COPYP(Dc);
+  COPYP(xV); COPYP(x1); COPYP(x2); COPYP(lvd);
   COPYP(sig0); COPYP(tau0); COPYP(taur); COPYP(Vp); COPYP(kappa); COPYP(presc);
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
@@ -334,7 +336,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   fill_dev(s, f);
   bool ok = true;
   double** darr[] = {&f.V, &f.psi, &f.thd, &f.delta, &f.V1, &f.thd1, &f.Vbar, &f.V2, &f.psi2, &f.thd2,
-                     &f.delta2, &f.a, &f.b, &f.Dc, &f.sig0, &f.tau0, &f.taur, &f.Vp, &f.kappa};
+                     &f.delta2, &f.a, &f.b, &f.Dc, &f.sig0, &f.tau0, &f.taur, &f.Vp, &f.kappa,
+                     &f.xV, &f.x1, &f.x2, &f.lvd};
   for (double** d : darr) *d = alloc_n<double>(s, N, &ok);
   f.presc = alloc_n<uint8_t>(s, N, &ok);
   double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN};
@@ -387,7 +390,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     for (size_t i = 0; i < tw.size(); ++i) tw32[i] = static_cast<float>(tw[i]);
   }
   // friction arrays, load, state
-  std::vector<double> psi(N), thd(N), taul(N, 0.0), taur(N, 0.0), Vp(N, 0.0), V(N);
+  std::vector<double> psi(N), thd(N), taul(N, 0.0), taur(N, 0.0), Vp(N, 0.0), V(N), xV(N), lvd(N);
   std::vector<uint8_t> pr(N, 0);
   for (int i = 0; i < N; ++i) {
     pr[i] = (prescribed && prescribed[i]) ? 1 : 0;
@@ -395,6 +398,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     V[i] = pr[i] ? V_presc[i] : V_init[i];
     psi[i] = std::log(theta_init[i]);
     thd[i] = 1.0 - theta_init[i] * V[i] / Dc[i];
+    xV[i] = V[i] > 0.0 ? std::log(V[i]) : -745.0;
+    lvd[i] = std::log(p.V0 / Dc[i]);
     if (tau_load_rate) taur[i] = tau_load_rate[i];
     if (tau_load) {
       taul[i] = tau_load[i];
@@ -410,6 +415,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
             up(f.taur, taur.data(), nb) == cudaSuccess && up(f.Vp, Vp.data(), nb) == cudaSuccess &&
             up(f.presc, pr.data(), N) == cudaSuccess && up(f.V, V.data(), nb) == cudaSuccess &&
             up(f.psi, psi.data(), nb) == cudaSuccess && up(f.thd, thd.data(), nb) == cudaSuccess &&
+            up(f.xV, xV.data(), nb) == cudaSuccess && up(f.lvd, lvd.data(), nb) == cudaSuccess &&
             up(d_roff, s->ring_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
             up(d_woff, s->w_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
             up(d_Rn, Rn32.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
@@ -597,7 +603,7 @@ int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const doubl
   auto& f = s->f64;
   const int N = s->N;
   const size_t nb = sizeof(double) * N;
-  std::vector<double> Vh(N), th(N), Dc(N), psi(N), thd(N);
+  std::vector<double> Vh(N), th(N), Dc(N), psi(N), thd(N), xV(N);
   std::vector<uint8_t> pr(N);
   CK(cudaMemcpyAsync(Vh.data(), f.V, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(psi.data(), f.psi, nb, cudaMemcpyDeviceToHost, s->stream));
@@ -609,11 +615,13 @@ int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const doubl
     if (!(th[i] > 0)) return fail(SBIEM_ERR_INVALID, "theta must be positive");
     psi[i] = std::log(th[i]);
     thd[i] = 1.0 - th[i] * Vh[i] / Dc[i];
+    xV[i] = Vh[i] > 0.0 ? std::log(Vh[i]) : -745.0;
   }
   if (delta) CK(cudaMemcpyAsync(f.delta, delta, nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.V, Vh.data(), nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.psi, psi.data(), nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.thd, thd.data(), nb, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(f.xV, xV.data(), nb, cudaMemcpyHostToDevice, s->stream));
   int rc = recompute_spectral_sums(s);
   if (rc) return rc;
   CK(cudaStreamSynchronize(s->stream));
@@ -685,6 +693,19 @@ int sbiem_get_history(sbiem_t s, double* hT, double* hN) {
       }
     }
   }
+  return SBIEM_OK;
+}
+
+int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
+  if (!s || !AT || !AN || m < 1 || m > (int64_t(1) << 30)) return fail(SBIEM_ERR_INVALID, "bad argument");
+  const int mi = static_cast<int>(m);
+  if (s->fp32()) launch_history<float>(s->f32, mi, s->sm_count * 4, s->stream);
+  else launch_history<double>(s->f64, mi, s->sm_count * 4, s->stream);
+  CK(cudaGetLastError());
+  const size_t nb = sizeof(double2) * s->nmodes;
+  CK(cudaMemcpyAsync(AT, s->f64.AT, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(AN, s->f64.AN, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
   return SBIEM_OK;
 }
 

@@ -390,14 +390,12 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
 }
 
 template <class R>
-__global__ void k_newton(DevFault<R> f, int pass, double dt) {
+__global__ void __launch_bounds__(32) k_newton(DevFault<R> f, int pass, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  __shared__ unsigned s_flags, s_skip;
-  __shared__ int s_itmax;
-  __shared__ unsigned long long s_itsum;
   // one read of the status word per block: other blocks may set it while
-  // this one runs, and the decision must be uniform across __syncthreads
-  if (threadIdx.x == 0) { s_flags = 0u; s_itmax = 0; s_itsum = 0ull; s_skip = *f.status; }
+  // this one runs, and the decision must be uniform across __syncwarp
+  __shared__ unsigned s_skip;
+  if (threadIdx.x == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
   unsigned flags = 0u;
@@ -405,61 +403,70 @@ __global__ void k_newton(DevFault<R> f, int pass, double dt) {
   if (i < f.N) {
     const double vb = f.Vbar[i];
     const double Dc = f.Dc[i];
-    const double th0 = exp(f.psi[i]);
-    double thp;
+    const double psi0 = f.psi[i];
+    double thp, psip;
     if (f.state_law == 0) {
       // aging law integrated at constant Vbar: theta e^{-u} + dt (1 - e^{-u})/u
       const double u = vb * dt / Dc;
       const double phi = (u > 0.0) ? -expm1(-u) / u : 1.0;
-      thp = th0 * exp(-u) + dt * phi;
+      thp = exp(psi0 - u) + dt * phi;
+      psip = log(thp);
     } else {
       const double thdb = (pass == 1) ? f.thd[i] : 0.5 * (f.thd[i] + f.thd1[i]);
-      thp = th0 + thdb * dt;
+      thp = exp(psi0) + thdb * dt;
       if (!(thp > 0.0)) flags |= SBIEM_FLAG_STATE;
+      psip = log(thp);
     }
     const double t_end = *f.t + dt;
     const Cx<R> y = f.y[i];
     const double tau = f.tau0[i] + f.taur[i] * t_end + static_cast<double>(y.x);
     const double sig = f.sig0[i] + static_cast<double>(y.y);
-    double Vn;
+    double x;
     if (f.presc[i]) {
-      Vn = f.Vp[i];
+      const double vp = f.Vp[i];
+      x = vp > 0.0 ? log(vp) : -745.0;
     } else if (!(sig > 0.0)) {
       flags |= SBIEM_FLAG_OPENING;
-      Vn = f.V[i];
+      x = f.xV[i];
     } else if (flags) {
-      Vn = f.V[i];
+      x = f.xV[i];
     } else {
       const double a = f.a[i];
-      const double c0 = f.f0 + f.b[i] * (log(thp) + log(f.V0 / Dc)) - a * log(f.V0);
-      const double xstart = log((pass == 1) ? f.V[i] : f.V1[i]);
-      double x;
+      // f0 + a (x - ln V0) + b ln(theta V0 / Dc) = c0 + a x
+      const double c0 = f.f0 + f.b[i] * (psip + f.lvd[i]) - a * f.lnV0;
+      const double xstart = (pass == 1) ? f.xV[i] : f.x1[i];
       const int it = solve_lnV(tau, sig, c0, a, f.eta, xstart, f.newton_tol, f.newton_maxit, &x);
       if (it < 0) flags |= SBIEM_FLAG_NEWTON;
       iters = it < 0 ? -it : it;
-      Vn = exp(x);
     }
+    const double Vn = f.presc[i] ? f.Vp[i] : exp(x);
     const double thd_new = 1.0 - thp * Vn / Dc;
     if (pass == 1) {
       f.V1[i] = Vn;
+      f.x1[i] = x;
       f.thd1[i] = thd_new;
     } else {
       f.V2[i] = Vn;
-      f.psi2[i] = log(thp);
+      f.x2[i] = x;
+      f.psi2[i] = psip;
       f.thd2[i] = thd_new;
       f.delta2[i] = f.delta[i] + vb * dt;
     }
   }
-  if (flags) atomicOr(&s_flags, flags);
-  if (iters) {
-    atomicMax(&s_itmax, iters);
-    atomicAdd(&s_itsum, static_cast<unsigned long long>(iters));
+  // warp-level aggregation of flags and iteration counts, one atomic per warp
+  unsigned fl = flags;
+  int im = iters;
+  unsigned long long is = static_cast<unsigned long long>(iters);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    im = max(im, __shfl_xor_sync(0xffffffffu, im, o));
+    is += __shfl_xor_sync(0xffffffffu, is, o);
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    if (s_flags) atomicOr(f.status, s_flags);
-    if (s_itmax) atomicMax(f.it_max, s_itmax);
-    if (s_itsum) atomicAdd(f.it_sum, s_itsum);
+    if (fl) atomicOr(f.status, fl);
+    if (im) atomicMax(f.it_max, im);
+    if (is) atomicAdd(f.it_sum, is);
   }
 }
 
@@ -470,6 +477,7 @@ __global__ void k_commit(DevFault<R> f, int m_dt, double dt) {
   if (*f.status) return;
   if (i < f.N) {
     f.V[i] = f.V2[i];
+    f.xV[i] = f.x2[i];
     f.psi[i] = f.psi2[i];
     f.thd[i] = f.thd2[i];
     f.delta[i] = f.delta2[i];
@@ -622,7 +630,7 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   kfb<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.Z, R(1), f.status);
   kia<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
   kib<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.y, R(1.0 / g.N), f.status);
-  const int nt = 64;
+  const int nt = 32;
   k_newton<R><<<(f.N + nt - 1) / nt, nt, 0, st>>>(f, pass, dt);
 }
 

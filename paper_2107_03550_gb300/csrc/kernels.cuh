@@ -45,7 +45,7 @@ template <class R>
 struct DevFault {
   int N;
   int nmodes;          // N/2 + 1
-  double L, S, mu, eta, dt_min, f0, V0;
+  double L, S, mu, eta, dt_min, f0, V0, lnV0;
   int state_law;
   int newton_maxit;
   double newton_tol;
@@ -54,7 +54,9 @@ struct DevFault {
   double *V1, *thd1;                       // pass-1 results
   double *Vbar;                            // pass slip rate
   double *V2, *psi2, *thd2, *delta2;       // pass-2 results (staged)
+  double *xV, *x1, *x2;                    // ln V: committed, pass 1, staged
   double *a, *b, *Dc, *sig0, *tau0, *taur, *Vp, *kappa;
+  double *lvd;                             // ln(V0 / Dc) per element
   uint8_t* presc;
   // spectral state (FP64)
   double2 *dhat, *khat;                    // F[delta], F[kappa delta]

@@ -70,6 +70,7 @@ _SIGS = {
     "sbiem_get_history": (ctypes.c_int, [_VP, _D, _D]),
     "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
     "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
     "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
     "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
@@ -267,6 +268,14 @@ class Fault:
         b = np.empty(2 * tot)
         self._check(self.lib.sbiem_get_history(self.h, a.ctypes.data_as(_D), b.ctypes.data_as(_D)))
         return a.view(np.complex128), b.view(np.complex128)
+
+    def history_sums(self, m: int = 1):
+        """(A^T_n, A^N_n) of the current rings for a step of m dt_min (complex arrays)."""
+        nm = self.N // 2 + 1
+        at = np.empty(2 * nm)
+        an = np.empty(2 * nm)
+        self._check(self.lib.sbiem_history_sums(self.h, int(m), at.ctypes.data_as(_D), an.ctypes.data_as(_D)))
+        return at.view(np.complex128), an.view(np.complex128)
 
     def probe_enable(self, on: bool = True) -> None:
         self._check(self.lib.sbiem_probe_enable(self.h, int(on)))
