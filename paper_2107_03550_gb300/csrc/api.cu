@@ -39,6 +39,7 @@ struct sbiem_s {
   sbiem_params p{};
   int device = 0;
   int sm_count = 0;
+  int hist_grid = 0;  // resident CTAs of the history convolution
   cudaStream_t stream = nullptr;      // where work is enqueued
   cudaStream_t own = nullptr;         // the handle's own stream (also used for graph capture)
   bool user_stream = false;
@@ -182,7 +183,7 @@ void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
   cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
   probe_mark(s, 1, st);
-  launch_history<R>(f, m, s->sm_count * 4, st);
+  launch_history<R>(f, m, s->hist_grid, st);
   probe_mark(s, 2, st);
   launch_pass<R>(f, 1, m, st);
   launch_pass<R>(f, 2, m, st);
@@ -466,6 +467,10 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     rc = ok ? SBIEM_OK : fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
     if (rc == SBIEM_OK) launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
   }
+  if (rc == SBIEM_OK) {
+    const int per_sm = s->fp32() ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
+    s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
+  }
   if (rc == SBIEM_OK) rc = recompute_spectral_sums(s);
   if (rc == SBIEM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
     rc = fail(SBIEM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(cudaGetLastError()));
@@ -699,8 +704,8 @@ int sbiem_get_history(sbiem_t s, double* hT, double* hN) {
 int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   if (!s || !AT || !AN || m < 1 || m > (int64_t(1) << 30)) return fail(SBIEM_ERR_INVALID, "bad argument");
   const int mi = static_cast<int>(m);
-  if (s->fp32()) launch_history<float>(s->f32, mi, s->sm_count * 4, s->stream);
-  else launch_history<double>(s->f64, mi, s->sm_count * 4, s->stream);
+  if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
+  else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
   CK(cudaGetLastError());
   const size_t nb = sizeof(double2) * s->nmodes;
   CK(cudaMemcpyAsync(AT, s->f64.AT, nb, cudaMemcpyDeviceToHost, s->stream));

@@ -240,8 +240,8 @@ __device__ __forceinline__ Slot64 ld_slot(const Slot64* p) {
 __device__ __forceinline__ float4 ld_slot(const float4* p) { return __ldg(p); }
 
 template <class R> struct HistCfg;
-template <> struct HistCfg<double> { static constexpr int kUnroll = 2; };
-template <> struct HistCfg<float> { static constexpr int kUnroll = 4; };
+template <> struct HistCfg<double> { static constexpr int kUnroll = 4; };
+template <> struct HistCfg<float> { static constexpr int kUnroll = 8; };
 
 constexpr int kHistThreads = 256;
 
@@ -251,36 +251,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum of four doubles; result valid in thread 0.
-__device__ __forceinline__ double4 block_sum4(double4 v, double4* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v.x = warp_sum(v.x);
-  v.y = warp_sum(v.y);
-  v.z = warp_sum(v.z);
-  v.w = warp_sum(v.w);
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double4 r = make_double4(0.0, 0.0, 0.0, 0.0);
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    if (lane < nw) r = sh[lane];
-    r.x = warp_sum(r.x);
-    r.y = warp_sum(r.y);
-    r.z = warp_sum(r.z);
-    r.w = warp_sum(r.w);
-  }
-  __syncthreads();
-  return r;
-}
-
+// One warp per chunk of consecutive slots of one mode: lanes stride over the
+// slots (each warp load is one contiguous segment), reduce with shuffles.  A
+// mode split over several chunks is finished by the warp whose chunk
+// completes last (atomic counter per mode, no waiting): it adds the partial
+// sums in chunk order, so the result does not depend on scheduling.
 template <class R>
 __global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_dt) {
-  __shared__ double4 sh[kHistThreads / 32];
-  __shared__ int s_last;
-  if (*f.status) return;
+  if (*f.status) return;  // the status word does not change while this kernel runs
   constexpr int U = HistCfg<R>::kUnroll;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int c = blockIdx.x; c < f.nchunks; c += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = static_cast<int>((gridDim.x * blockDim.x) >> 5);
+  for (int c = gw; c < f.nchunks; c += nw) {
     const Chunk cd = f.chunks[c];
     const int n = cd.mode;
     const int Rn = f.Rn[n];
@@ -289,61 +272,56 @@ __global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_d
     const Slot<R>* ring = f.ring + f.ring_off[n];
     const W2<R>* w = f.w + f.w_off[n] + m_dt;
     Acc4<R> acc = {R(0), R(0), R(0), R(0)};
-    for (int64_t i = cd.i0 + tid; i < iend; i += static_cast<int64_t>(U) * nth) {
-      Slot<R> s[U];
-      W2<R> ww[U];
+    for (int64_t i = cd.i0 + lane; i < iend; i += 32 * U) {
+      Slot<R> sv[U];
+      W2<R> wv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t ii = i + static_cast<int64_t>(u) * nth;
+        const int64_t ii = i + 32 * u;
         if (ii < iend) {
           int64_t slot = h + ii;
           if (slot >= Rn) slot -= Rn;
-          s[u] = ld_slot(ring + slot);
-          ww[u] = __ldg(w + ii);
+          sv[u] = ld_slot(ring + slot);
+          wv[u] = __ldg(w + ii);
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t ii = i + static_cast<int64_t>(u) * nth;
-        if (ii < iend) slot_fma(acc, s[u], ww[u]);
-      }
+      for (int u = 0; u < U; ++u)
+        if (i + 32 * u < iend) slot_fma(acc, sv[u], wv[u]);
     }
-    double4 v = make_double4(acc.tr, acc.ti, acc.nr, acc.ni);
-    v = block_sum4(v, sh);
-    if (tid == 0) {
-      if (cd.count == 1) {
+    double4 v = make_double4(warp_sum(acc.tr), warp_sum(acc.ti), warp_sum(acc.nr), warp_sum(acc.ni));
+    if (cd.count == 1) {
+      if (lane == 0) {
         f.AT[n] = make_double2(v.x, v.y);
         f.AN[n] = make_double2(v.z, v.w);
-        s_last = 0;
-      } else {
-        f.partial[c] = v;
-        __threadfence();
-        const int prev = atomicAdd(f.counter + n, 1);
-        s_last = (prev == cd.count - 1);
       }
+      continue;
     }
-    __syncthreads();
-    if (s_last) {
-      // last chunk of the mode to finish: add the partials in chunk order
+    int prev = 0;
+    if (lane == 0) {
+      f.partial[c] = v;
+      __threadfence();
+      prev = atomicAdd(f.counter + n, 1);
+    }
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev == cd.count - 1) {
       __threadfence();
       double4 r = make_double4(0.0, 0.0, 0.0, 0.0);
-      for (int q = tid; q < cd.count; q += nth) {
+      for (int q = lane; q < cd.count; q += 32) {
         const double2* pp = reinterpret_cast<const double2*>(f.partial + cd.first + q);
         const double2 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
-        const double4 p = make_double4(p0.x, p0.y, p1.x, p1.y);
-        r.x += p.x;
-        r.y += p.y;
-        r.z += p.z;
-        r.w += p.w;
+        r.x += p0.x;
+        r.y += p0.y;
+        r.z += p1.x;
+        r.w += p1.y;
       }
-      r = block_sum4(r, sh);
-      if (tid == 0) {
+      r = make_double4(warp_sum(r.x), warp_sum(r.y), warp_sum(r.z), warp_sum(r.w));
+      if (lane == 0) {
         f.AT[n] = make_double2(r.x, r.y);
         f.AN[n] = make_double2(r.z, r.w);
         f.counter[n] = 0;
       }
     }
-    __syncthreads();
   }
 }
 
@@ -637,8 +615,17 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
 template <class R>
 void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   if (f.nchunks == 0) return;
-  const int gr = grid < f.nchunks ? grid : f.nchunks;
+  const int warps = kHistThreads / 32;
+  const int need = (f.nchunks + warps - 1) / warps;
+  const int gr = grid < need ? grid : need;
   k_history<R><<<gr, kHistThreads, 0, st>>>(f, m_dt);
+}
+
+template <class R>
+int history_blocks_per_sm() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_history<R>, kHistThreads, 0);
+  return n;
 }
 
 template <class R>
@@ -696,6 +683,8 @@ void configure_kernels(const FftGeom& g) {
   allow_smem(k_row<double, true>, row_smem<double>(g64));
 }
 
+template int history_blocks_per_sm<double>();
+template int history_blocks_per_sm<float>();
 template void configure_kernels<double>(const FftGeom&);
 template void configure_kernels<float>(const FftGeom&);
 template void launch_history<double>(const DevFault<double>&, int, int, cudaStream_t);

@@ -86,6 +86,8 @@ struct DevFault {
 
 // Host launch wrappers (kernels.cu).
 template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
+// Resident CTAs per SM of the history convolution (occupancy calculator).
+template <class R> int history_blocks_per_sm();
 template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
 template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st);
 template <class R> void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg,

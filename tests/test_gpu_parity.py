@@ -86,7 +86,9 @@ def test_full_size_rough_cycle_step():
     g.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 2e-6)])
+# FP64: the oracle's weights carry its own kernel rounding (W = 1 - int_0^x
+# gives a few ulps of 1, times s^2 in the kernels: up to 1e-11 at s = 200)
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-6)])
 @pytest.mark.parametrize("m", [1, 3])
 def test_history_sums_match_oracle(precision, tol, m):
     # the hot kernel alone: full rings (several chunks per mode, ragged tails)
