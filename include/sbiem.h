@@ -176,15 +176,18 @@ int sbiem_set_history(sbiem_t s, const double* hist_T, const double* hist_N);
 int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
 
 /*
- * Timing probe.  sbiem_probe_enable(s, 1) makes every later step record four
- * CUDA events on the handle's stream (inside the captured graph as well): at
- * the start of the step, before and after the history convolution kernel,
- * and at the end of the step.  sbiem_probe_read synchronizes on the last
- * event and returns the elapsed milliseconds of the most recent step and of
- * its history convolution.  Enabling or disabling rebuilds the step graph.
+ * Timing probe.  sbiem_probe_enable(s, nslots) with nslots >= 1 makes every
+ * later step record four CUDA events on the handle's stream (as event-record
+ * nodes inside the step graph as well): at the start of the step, before and
+ * after the history convolution kernel, and at the end of the step.  Step k
+ * (counted from the call) uses event slot k mod nslots, so nslots steps can
+ * be enqueued back to back and read afterwards.  nslots = 0 disables the
+ * probe.  sbiem_probe_read synchronizes on the slot's last event and returns
+ * the elapsed milliseconds of that step and of its history convolution.
+ * Enabling or disabling rebuilds the step graph.
  */
-int sbiem_probe_enable(sbiem_t s, int on);
-int sbiem_probe_read(sbiem_t s, float* ms_step, float* ms_history);
+int sbiem_probe_enable(sbiem_t s, int nslots);
+int sbiem_probe_read(sbiem_t s, int slot, float* ms_step, float* ms_history);
 
 /*
  * sbiem_history_sums -- run the truncated history convolution alone (Sec. 3.1

@@ -31,7 +31,6 @@ int fail(int code, const std::string& msg) {
       return fail(SBIEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
   } while (0)
 
-constexpr int kChunkSlots = 2048;  // history slots per chunk of the convolution
 
 }  // namespace
 
@@ -60,8 +59,14 @@ struct sbiem_s {
   long long* h_steps = nullptr;  // pinned
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> graph_defs;
-  bool probe = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // timing probe: 4 events per slot; graph event-record nodes are retargeted
+  // to the slot of each launch
+  int pslots = 0;
+  int64_t pcount = 0;
+  int pcur = 0;
+  std::vector<cudaEvent_t> pev;
+  std::map<int, std::vector<cudaGraphNode_t>> pnodes;  // per graph: nodes of marks 0..3
+  int64_t chunk_slots = 2048;
 
   bool fp32() const { return p.precision == 1; }
 };
@@ -97,8 +102,9 @@ void free_all(sbiem_s* s) {
   s->graphs.clear();
   s->graph_defs.clear();
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (auto& e : s->ev)
+  for (auto& e : s->pev)
     if (e) cudaEventDestroy(e);
+  s->pev.clear();
   for (void* ptr : s->allocs) {
     if (s->p.free_fn) s->p.free_fn(ptr, s->p.alloc_user);
     else cudaFree(ptr);
@@ -157,7 +163,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
   COPYP(chunks); COPYP(nchunks); COPYP(status); COPYP(steps_done); COPYP(t);
-  COPYP(it_sum); COPYP(it_max);
+  COPYP(it_sum); COPYP(it_max); COPYP(work);
 #undef COPYP
   bool ok = true;
   f.ring = alloc_n<Slot<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
@@ -174,7 +180,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
 }
 
 void probe_mark(sbiem_s* s, int k, cudaStream_t st) {
-  if (s->probe) cudaEventRecordWithFlags(s->ev[k], st, cudaEventRecordExternal);
+  if (s->pslots) cudaEventRecordWithFlags(s->pev[4 * s->pcur + k], st, cudaEventRecordExternal);
 }
 
 template <class R>
@@ -182,6 +188,7 @@ void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
   probe_mark(s, 0, st);
   cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
   cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
+  cudaMemsetAsync(f.work, 0, sizeof(int), st);
   probe_mark(s, 1, st);
   launch_history<R>(f, m, s->hist_grid, st);
   probe_mark(s, 2, st);
@@ -301,6 +308,17 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   s->S = p.mu * (1.0 - r * r);
   s->eta = p.mu / (2.0 * p.cs);
   windows(p, s->L, s->dt_min, s->M);
+  {
+    // chunk length: about four chunks per resident warp of the history
+    // convolution, a multiple of 128 slots, within [128, 4096]
+    const int per_sm = s->fp32() ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
+    s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
+    int64_t tot = 0;
+    for (int64_t Mn : s->M) tot += std::max<int64_t>(Mn - 1, 0);
+    const int64_t warps = static_cast<int64_t>(s->hist_grid) * 8;
+    int64_t cs = (tot / (4 * warps) + 127) / 128 * 128;
+    s->chunk_slots = std::min<int64_t>(std::max<int64_t>(cs, 128), 4096);
+  }
   s->Rn.assign(s->nmodes, 0);
   s->ring_off.assign(s->nmodes + 1, 0);
   s->w_off.assign(s->nmodes + 1, 0);
@@ -308,14 +326,15 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     s->Rn[n] = std::max<int64_t>(s->M[n] - 1, 0);
     s->ring_off[n + 1] = s->ring_off[n] + s->Rn[n];
     s->w_off[n + 1] = s->w_off[n] + s->M[n];
-    const int64_t cnt = (s->Rn[n] + kChunkSlots - 1) / kChunkSlots;
+    const int64_t cs = s->chunk_slots;
+    const int64_t cnt = (s->Rn[n] + cs - 1) / cs;
     for (int64_t c = 0; c < cnt; ++c) {
       Chunk ch{};
       ch.mode = n;
       ch.first = static_cast<int32_t>(s->chunks.size() - c);
       ch.count = static_cast<int32_t>(cnt);
-      ch.i0 = c * kChunkSlots;
-      ch.i1 = std::min<int64_t>((c + 1) * kChunkSlots, s->Rn[n]);
+      ch.i0 = c * cs;
+      ch.i1 = std::min<int64_t>((c + 1) * cs, s->Rn[n]);
       s->chunks.push_back(ch);
     }
   }
@@ -355,6 +374,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   f.steps_done = alloc_n<long long>(s, 1, &ok);
   f.t = alloc_n<double>(s, 1, &ok);
   f.it_sum = alloc_n<unsigned long long>(s, 1, &ok);
+  f.work = alloc_n<int>(s, 1, &ok);
   f.it_max = alloc_n<int>(s, 1, &ok);
   s->tw64 = alloc_n<double2>(s, N, &ok);
   s->u_a = alloc_n<double2>(s, N, &ok);
@@ -467,10 +487,6 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     rc = ok ? SBIEM_OK : fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
     if (rc == SBIEM_OK) launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
   }
-  if (rc == SBIEM_OK) {
-    const int per_sm = s->fp32() ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
-    s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
-  }
   if (rc == SBIEM_OK) rc = recompute_spectral_sums(s);
   if (rc == SBIEM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
     rc = fail(SBIEM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(cudaGetLastError()));
@@ -516,6 +532,7 @@ int sbiem_step(sbiem_t s, double dt) {
   uint32_t before;
   rc = sbiem_status(s, &before, nullptr, 1);
   if (rc) return rc;
+  if (s->pslots) s->pcur = static_cast<int>(s->pcount++ % s->pslots);
   enqueue_step(s, m, s->stream);
   CK(cudaGetLastError());
   uint32_t st;
@@ -538,6 +555,7 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
     cudaGraph_t gdef = nullptr;
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
+    s->pcur = 0;
     enqueue_step(s, m, s->own);
     cudaError_t e1 = cudaGetLastError();
     cudaError_t e2 = cudaStreamEndCapture(s->own, &gdef);
@@ -547,9 +565,37 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
     CK(cudaGraphInstantiate(&exec, gdef, 0));
     s->graphs[m] = exec;
     s->graph_defs[m] = gdef;
+    if (s->pslots) {
+      // the event-record nodes of the probe marks, in mark order
+      size_t nn = 0;
+      CK(cudaGraphGetNodes(gdef, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CK(cudaGraphGetNodes(gdef, nodes.data(), &nn));
+      std::vector<cudaGraphNode_t> marks(4, nullptr);
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        CK(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t e;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &e));
+        for (int k = 0; k < 4; ++k)
+          if (e == s->pev[k]) marks[k] = nd;
+      }
+      for (auto nd : marks)
+        if (!nd) return fail(SBIEM_ERR_CUDA, "probe event nodes not found in the step graph");
+      s->pnodes[m] = marks;
+    }
     it = s->graphs.find(m);
   }
-  for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(it->second, s->stream));
+  for (int64_t k = 0; k < nsteps; ++k) {
+    if (s->pslots) {
+      const int slot = static_cast<int>(s->pcount++ % s->pslots);
+      const auto& marks = s->pnodes[m];
+      for (int q = 0; q < 4; ++q)
+        CK(cudaGraphExecEventRecordNodeSetEvent(it->second, marks[q], s->pev[4 * slot + q]));
+    }
+    CK(cudaGraphLaunch(it->second, s->stream));
+  }
   return SBIEM_OK;
 }
 
@@ -704,6 +750,7 @@ int sbiem_get_history(sbiem_t s, double* hT, double* hN) {
 int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   if (!s || !AT || !AN || m < 1 || m > (int64_t(1) << 30)) return fail(SBIEM_ERR_INVALID, "bad argument");
   const int mi = static_cast<int>(m);
+  CK(cudaMemsetAsync(s->f64.work, 0, sizeof(int), s->stream));
   if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
   else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
   CK(cudaGetLastError());
@@ -714,27 +761,31 @@ int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   return SBIEM_OK;
 }
 
-int sbiem_probe_enable(sbiem_t s, int on) {
-  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+int sbiem_probe_enable(sbiem_t s, int nslots) {
+  if (!s || nslots < 0 || nslots > (1 << 20)) return fail(SBIEM_ERR_INVALID, "bad argument");
   CK(cudaStreamSynchronize(s->stream));
-  if (on && !s->ev[0])
-    for (auto& e : s->ev) CK(cudaEventCreate(&e));
-  if (static_cast<bool>(on) != s->probe) {
-    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
-    for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
-    s->graphs.clear();
-    s->graph_defs.clear();
-  }
-  s->probe = on != 0;
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
+  s->graphs.clear();
+  s->graph_defs.clear();
+  s->pnodes.clear();
+  for (auto& e : s->pev)
+    if (e) cudaEventDestroy(e);
+  s->pev.assign(static_cast<size_t>(4) * nslots, nullptr);
+  for (auto& e : s->pev) CK(cudaEventCreate(&e));
+  s->pslots = nslots;
+  s->pcount = 0;
+  s->pcur = 0;
   return SBIEM_OK;
 }
 
-int sbiem_probe_read(sbiem_t s, float* ms_step, float* ms_history) {
-  if (!s || !s->probe) return fail(SBIEM_ERR_INVALID, "probe not enabled");
-  CK(cudaEventSynchronize(s->ev[3]));
+int sbiem_probe_read(sbiem_t s, int slot, float* ms_step, float* ms_history) {
+  if (!s || !s->pslots || slot < 0 || slot >= s->pslots) return fail(SBIEM_ERR_INVALID, "probe not enabled or bad slot");
+  cudaEvent_t* e = &s->pev[4 * slot];
+  CK(cudaEventSynchronize(e[3]));
   float a = 0.f, b = 0.f;
-  CK(cudaEventElapsedTime(&a, s->ev[0], s->ev[3]));
-  CK(cudaEventElapsedTime(&b, s->ev[1], s->ev[2]));
+  CK(cudaEventElapsedTime(&a, e[0], e[3]));
+  CK(cudaEventElapsedTime(&b, e[1], e[2]));
   if (ms_step) *ms_step = a;
   if (ms_history) *ms_history = b;
   return SBIEM_OK;

@@ -261,9 +261,11 @@ __global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_d
   if (*f.status) return;  // the status word does not change while this kernel runs
   constexpr int U = HistCfg<R>::kUnroll;
   const int lane = threadIdx.x & 31;
-  const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int nw = static_cast<int>((gridDim.x * blockDim.x) >> 5);
-  for (int c = gw; c < f.nchunks; c += nw) {
+  // chunks are handed out dynamically (counter zeroed before the launch)
+  int c = 0;
+  if (lane == 0) c = atomicAdd(f.work, 1);
+  c = __shfl_sync(0xffffffffu, c, 0);
+  for (; c < f.nchunks; c = __shfl_sync(0xffffffffu, c, 0)) {
     const Chunk cd = f.chunks[c];
     const int n = cd.mode;
     const int Rn = f.Rn[n];
@@ -290,6 +292,8 @@ __global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_d
         if (i + 32 * u < iend) slot_fma(acc, sv[u], wv[u]);
     }
     double4 v = make_double4(warp_sum(acc.tr), warp_sum(acc.ti), warp_sum(acc.nr), warp_sum(acc.ni));
+    const int cur = c;
+    if (lane == 0) c = atomicAdd(f.work, 1);
     if (cd.count == 1) {
       if (lane == 0) {
         f.AT[n] = make_double2(v.x, v.y);
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_d
     }
     int prev = 0;
     if (lane == 0) {
-      f.partial[c] = v;
+      f.partial[cur] = v;
       __threadfence();
       prev = atomicAdd(f.counter + n, 1);
     }

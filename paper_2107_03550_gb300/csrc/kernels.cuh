@@ -82,6 +82,7 @@ struct DevFault {
   double* t;
   unsigned long long* it_sum;
   int* it_max;
+  int* work;                               // next chunk of the history convolution
 };
 
 // Host launch wrappers (kernels.cu).

@@ -71,7 +71,8 @@ _SIGS = {
     "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
     "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
-    "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
     "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
     "sbiem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -277,14 +278,15 @@ class Fault:
         self._check(self.lib.sbiem_history_sums(self.h, int(m), at.ctypes.data_as(_D), an.ctypes.data_as(_D)))
         return at.view(np.complex128), an.view(np.complex128)
 
-    def probe_enable(self, on: bool = True) -> None:
-        self._check(self.lib.sbiem_probe_enable(self.h, int(on)))
+    def probe_enable(self, nslots: int = 1) -> None:
+        """Record step / history-convolution events into a ring of nslots slots (0: off)."""
+        self._check(self.lib.sbiem_probe_enable(self.h, int(nslots)))
 
-    def probe_read(self):
-        """(ms of the last step, ms of its history convolution), device events."""
+    def probe_read(self, slot: int = 0):
+        """(ms of the step in this slot, ms of its history convolution), device events."""
         a = ctypes.c_float()
         b = ctypes.c_float()
-        self._check(self.lib.sbiem_probe_read(self.h, ctypes.byref(a), ctypes.byref(b)))
+        self._check(self.lib.sbiem_probe_read(self.h, int(slot), ctypes.byref(a), ctypes.byref(b)))
         return float(a.value), float(b.value)
 
     def newton_stats(self):
