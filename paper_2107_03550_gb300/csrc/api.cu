@@ -588,7 +588,7 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
     it = s->graphs.find(m);
   }
   for (int64_t k = 0; k < nsteps; ++k) {
-    if (s->pslots) {
+    if (s->pslots > 1) {
       const int slot = static_cast<int>(s->pcount++ % s->pslots);
       const auto& marks = s->pnodes[m];
       for (int q = 0; q < 4; ++q)
