@@ -200,6 +200,50 @@ int sbiem_probe_read(sbiem_t s, int slot, float* ms_step, float* ms_history);
  */
 int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN);
 
+/*
+ * sbiem_history_sums_noalloc -- the history convolution of
+ * sbiem_history_sums for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this entry point exists for library users.
+ *
+ * Who needs it: code that must not call cudaMalloc or any allocating routine
+ * -- work recorded into the caller's own CUDA graph (device allocation is not
+ * allowed during global-mode stream capture), real-time loops that cannot
+ * afford the allocator's latency or locks, and frameworks that hand out all
+ * device memory from their own fixed arena.  Such a caller keeps the history
+ * in its own buffers and needs only the sums.
+ *
+ * Inputs (device pointers, caller-owned, not modified):
+ *   ring     nslots history slots in the library's layout: per slot the
+ *            shear value F[Vbar] then the normal value F[kappa Vbar], complex,
+ *            FP64 (32 bytes per slot) or FP32 (16 bytes) per `precision`;
+ *   weights  per lag the pair (w^T, w^N), FP64 (16 bytes) or FP32 (8 bytes);
+ *   ring_off[n], w_off[n] (int64, nmodes entries) start slot / weight of mode n;
+ *   R[n] = M_n - 1 (int32, slots of mode n), M[n] = M_n (int32, weights of
+ *   mode n), head[n] (int32, ring position of the newest slot of mode n).
+ * Outputs: AT, AN (device, nmodes complex FP64 each, re/im interleaved).
+ * m: the history shift (a step of m dt_min), m >= 1.  stream: cudaStream_t or
+ * NULL.
+ *
+ * Scratch: one static device array of about 3.8 MB that every GPU loading
+ * the library holds until exit; it bounds the sizes to nmodes <=
+ * SBIEM_NOALLOC_MAX_MODES (N <= 65536) and to
+ * sum_n ceil(R[n] / 2048) <= SBIEM_NOALLOC_MAX_CHUNKS.  Larger inputs return
+ * SBIEM_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Each call clears the counters it needs, but every call shares the
+ * one array: calls that overlap on the GPU (several streams, or several host
+ * threads) race, so serialize them on one stream.  The call synchronizes the
+ * stream once (to read the chunk count) and returns with the sums enqueued.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ */
+#define SBIEM_NOALLOC_MAX_MODES  32769
+#define SBIEM_NOALLOC_MAX_CHUNKS 65536
+int sbiem_history_sums_noalloc(int64_t nmodes, int32_t precision, int64_t m,
+                               const void* ring, const void* weights,
+                               const int64_t* ring_off, const int64_t* w_off,
+                               const int32_t* R, const int32_t* M, const int32_t* head,
+                               double* AT, double* AN, void* stream);
+
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);

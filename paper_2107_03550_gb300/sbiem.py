@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Fault", "SbiemError", "kernel_values", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
+__all__ = ["Fault", "SbiemError", "kernel_values", "history_sums_noalloc", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
            "FLAG_STATE", "ERR"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +74,8 @@ _SIGS = {
     "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
+    "sbiem_history_sums_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP,
+                                                  _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
     "sbiem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sbiem_last_error": (ctypes.c_char_p, []),
@@ -143,6 +145,21 @@ def kernel_values(s, r: float):
     if rc != 0:
         raise SbiemError(rc, "kernel_values: invalid argument")
     return cT, cN
+
+
+def history_sums_noalloc(nmodes: int, precision: int, m: int, ring: int, weights: int, ring_off: int,
+                         w_off: int, R: int, M: int, head: int, AT: int, AN: int, stream=None) -> None:
+    """History convolution on caller-owned device buffers (raw device pointers), no allocation.
+
+    For callers that cannot allocate device memory; see the C header for the
+    buffer layouts, the size limits and the one-stream rule.
+    """
+    lib = load_library()
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = lib.sbiem_history_sums_noalloc(int(nmodes), int(precision), int(m), ring, weights, ring_off, w_off, R, M,
+                                        head, AT, AN, raw or None)
+    if rc != 0:
+        raise SbiemError(rc, "history_sums_noalloc: invalid sizes or CUDA failure")
 
 
 class Fault:
