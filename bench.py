@@ -9,11 +9,15 @@ dx = 10 m, Hurst-1 roughness) with every history window full (steady state).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
     python bench.py --impl reference     # the FP64 CPU oracle on the same workload
 
-Timing: each timed step runs as one CUDA-graph launch; CUDA events recorded
-inside the graph on the launch stream (one event slot per step, so the steps
-run back to back without host synchronization) bracket the step and its
-history convolution.  L2 is flushed (256 MiB written, then 256 MiB read) before every timed step, outside
-the events.  Under torchrun every rank runs an independent replica (the path
+The headline is the chosen form (FP32 history convolution and FFTs, FP64
+state, slip, time and Newton); the plain FP64 path is timed the same way and
+reported beside it.
+
+Timing: each timed step runs as one CUDA-graph launch bracketed by CUDA events
+on the launch stream; after it, the history convolution alone is launched and
+timed the same way (for the roofline).  L2 is flushed (256 MiB written, then
+256 MiB read) before every timed launch, outside the events; the timed
+launches run back to back without host synchronization.  Under torchrun every rank runs an independent replica (the path
 has no exchange step), the maximum device time over ranks is taken and the
 value sums all ranks' element-steps.  One JSON line is printed by rank 0.
 """
@@ -46,7 +50,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp32")
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -200,6 +204,99 @@ def run_reference(a):
 
 
 # ------------------------------------------------------------------- ours
+def _flusher(torch):
+    w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    r = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    out = torch.empty((), dtype=torch.int32, device="cuda")
+
+    def flush():
+        # write 256 MiB (evicts the history), then read another 256 MiB so the
+        # evicted dirty lines are written back before the timed step starts
+        w.fill_(1)
+        torch.amax(r, dim=0, out=out)
+
+    return flush
+
+
+def _measure(torch, a, precision: str, rank: int, world: int, flush, clock_index: int):
+    """Time K steps (and K history-only launches) back to back on one stream."""
+    from paper_2107_03550_gb300.sbiem import Fault
+    N = a.N
+    w = _workload(N)
+    g = Fault.from_workload(w, precision=1 if precision == "fp32" else 0)
+    g.set_stream(torch.cuda.current_stream())
+    HT, HN, _ = _history(g.windows(), 11 + rank, N)
+    g.set_history(HT, HN)
+    hist_bytes, dev_bytes = g.footprint()
+    for _ in range(max(a.warmup, 3)):
+        flush()
+        g.enqueue(1)
+        flush()
+        g.history_enqueue(1)
+    torch.cuda.synchronize()
+    flags, _ = g.status(clear=True)
+    if flags:
+        raise RuntimeError(f"warm-up step failed, status {flags}")
+    K = a.steps
+    ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    ev_h = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(clock_index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(K):
+        flush()
+        ev_s[k][0].record()
+        g.enqueue(1)
+        ev_s[k][1].record()
+        flush()
+        ev_h[k][0].record()
+        g.history_enqueue(1)
+        ev_h[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    flags, done = g.status(clear=True)
+    if flags:
+        raise RuntimeError(f"timed step failed, status {flags}")
+    ms_step = [x.elapsed_time(y) for x, y in ev_s]
+    ms_hist = [x.elapsed_time(y) for x, y in ev_h]
+    it_sum, it_max = g.newton_stats()
+    total_s = sum(ms_step) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    res = dict(g=g, w=w, value=world * N * K / total_s, ms_per_step=1e3 * total_s / K,
+               hist_ms=statistics.mean(ms_hist), hist_bytes=hist_bytes, dev_bytes=dev_bytes,
+               clocks=clk, it_sum=it_sum, it_max=it_max,
+               slots=int(np.maximum(g.windows() - 1, 0).sum()))
+    return res
+
+
+def _e2e(torch, a, g, w, world):
+    """Through the C ABI with host buffers: per step tau_load in, V out (pinned)."""
+    N = a.N
+    tau_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    v_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    tau_np = tau_h.numpy()
+    v_np = v_h.numpy()
+    fr = w.f0 + w.a * np.log(w.V_init / w.V0) + w.b * np.log(w.theta_init * w.V0 / w.Dc)
+    tau_np[:] = np.where(w.prescribed, 0.0, w.sigma_load * fr + w.mu / (2 * w.cs) * w.V_init)
+    for _ in range(3):
+        g.step_host(tau_load=tau_np, V_out=v_np)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        g.step_host(tau_load=tau_np, V_out=v_np)
+    el = time.perf_counter() - t0
+    return {"value": N * a.e2e_steps / el * world, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+            "d2h_bytes_per_step": 8 * N + 12}
+
+
 def run_ours(a):
     import torch
     rank, world, local = _dist()
@@ -207,124 +304,53 @@ def run_ours(a):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    from paper_2107_03550_gb300.sbiem import Fault
-
-    N = a.N
-    w = _workload(N)
-    prec = 1 if a.precision == "fp32" else 0
-    g = Fault.from_workload(w, precision=prec)
-    stream = torch.cuda.current_stream()
-    g.set_stream(stream)
-    HT, HN, _ = _history(g.windows(), 11 + rank, N)
-    g.set_history(HT, HN)
-    hist_bytes, dev_bytes = g.footprint()
-    flush_w = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    flush_r = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    flush_out = torch.empty((), dtype=torch.int32, device="cuda")
-
-    def flush():
-        # write 256 MiB (evicts the history), then read another 256 MiB so the
-        # evicted dirty lines are written back before the timed step starts
-        flush_w.fill_(1)
-        torch.amax(flush_r, dim=0, out=flush_out)
-
-    # warm-up (graph capture happens here); every step records its probe
-    # events into its own slot, so the timed steps run back to back
-    g.probe_enable(a.steps)
-    for _ in range(max(a.warmup, 3)):
-        flush()
-        g.enqueue(1)
-    torch.cuda.synchronize()
-    flags, _ = g.status(clear=True)
-    if flags:
-        raise RuntimeError(f"warm-up step failed, status {flags}")
-
     dev_index = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     if vis and "," not in vis and vis.strip().isdigit():
         dev_index = int(vis)
-    clocks = ClockSampler(dev_index)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    for _ in range(a.steps):
-        flush()
-        g.enqueue(1)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    ms_step, ms_hist = [], []
-    for k in range(a.steps):
-        s_ms, h_ms = g.probe_read(k)
-        ms_step.append(s_ms)
-        ms_hist.append(h_ms)
-    flags, done = g.status(clear=True)
-    if flags:
-        raise RuntimeError(f"timed step failed, status {flags}")
-    it_sum, it_max = g.newton_stats()
-
-    total_s = sum(ms_step) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * N * a.steps / total_s
-    hist_ms = statistics.mean(ms_hist)
-    peak, peak_kind = _peaks()
-    achieved = hist_bytes / (hist_ms * 1e-3) / 1e9
-
-    # end to end through the C ABI with host buffers: per step, tau_load in, V out
-    e2e = None
-    if not a.no_e2e:
-        g.probe_enable(0)
-        tau_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        v_h = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        tau_np = tau_h.numpy()
-        sig = w.sigma_load
-        fr = w.f0 + w.a * np.log(w.V_init / w.V0) + w.b * np.log(w.theta_init * w.V0 / w.Dc)
-        tau_np[:] = np.where(w.prescribed, 0.0, sig * fr + w.mu / (2 * w.cs) * w.V_init)
-        v_np = v_h.numpy()
-        for _ in range(3):
-            g.step_host(tau_load=tau_np, V_out=v_np)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(a.e2e_steps):
-            g.step_host(tau_load=tau_np, V_out=v_np)
-        el = time.perf_counter() - t0
-        e2e = {"value": N * a.e2e_steps / el * world, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
-               "d2h_bytes_per_step": 8 * N + 12}
-
+    flush = _flusher(torch)
+    other = "fp64" if a.precision == "fp32" else "fp32"
+    # the plain FP64 path and the chosen form, same workload, same timing
+    side = _measure(torch, a, other, rank, world, flush, dev_index)
+    side["g"].close()
+    main = _measure(torch, a, a.precision, rank, world, flush, dev_index)
+    e2e = None if a.no_e2e else _e2e(torch, a, main["g"], main["w"], world)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        cpu = _oracle_leg(N, a.cpu_seconds)
-
+        cpu = _oracle_leg(a.N, a.cpu_seconds)
+    peak, peak_kind = _peaks()
+    achieved = main["hist_bytes"] / (main["hist_ms"] * 1e-3) / 1e9
     if rank == 0:
+        w = main["w"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32/f64",
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32/f64",
             "data": "synthetic",
-            "config": {"workload": _workload_name(w, N), "N": N, "dx_m": w.dx,
-                       "precision": a.precision, "parallelism": f"replicas x{world}",
-                       "l2": "flushed before every timed step: 256 MiB write, then 256 MiB read, outside the timed events",
-                       "history_slots": int(np.maximum(g.windows() - 1, 0).sum()),
-                       "history_bytes_per_step": hist_bytes, "device_bytes": dev_bytes,
-                       "newton_iters_last_step": {"sum": it_sum, "max": it_max}},
+            "config": {"workload": _workload_name(w, a.N), "N": a.N, "dx_m": w.dx,
+                       "precision": a.precision + (" (FP32 history convolution and FFTs, FP64 state and Newton)"
+                                                   if a.precision == "fp32" else ""),
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed before every timed launch: 256 MiB write, then 256 MiB read, "
+                             "outside the timed events",
+                       "history_slots": main["slots"], "history_bytes_per_step": main["hist_bytes"],
+                       "device_bytes": main["dev_bytes"],
+                       "newton_iters_last_step": {"sum": main["it_sum"], "max": main["it_max"]},
+                       f"{other}_path": {"value": side["value"], "ms_per_step": side["ms_per_step"],
+                                         "history_ms": side["hist_ms"],
+                                         "history_GBps": side["hist_bytes"] / (side["hist_ms"] * 1e-3) / 1e9}},
             "roofline": {"bound": "hbm", "kernel": "k_history", "achieved": achieved, "peak": peak,
-                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": _traffic(a.precision, N), "ms_per_launch": hist_ms,
-                         "algorithmic_bytes_per_launch": hist_bytes},
-            "clocks": clk,
+                         "traffic": _traffic(a.precision, a.N), "ms_per_launch": main["hist_ms"],
+                         "algorithmic_bytes_per_launch": main["hist_bytes"]},
+            "clocks": main["clocks"],
             "e2e": e2e,
-            "gpu_launches": 12 * a.steps,
+            "gpu_launches": 13 * a.steps,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    g.close()
+    main["g"].close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

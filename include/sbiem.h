@@ -19,8 +19,8 @@
  *   - Return value: SBIEM_OK (0) or a negative SBIEM_ERR_* code;
  *     sbiem_strerror() gives a message, sbiem_last_error() adds detail.
  *   - A handle is bound to the CUDA device that was current at creation and
- *     to one stream (default: the legacy default stream); it is not
- *     thread-safe.
+ *     to one stream (default: a non-blocking stream of its own; see
+ *     sbiem_set_stream); it is not thread-safe.
  */
 #ifndef SBIEM_H
 #define SBIEM_H
@@ -114,7 +114,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* p,
 void sbiem_destroy(sbiem_t s);
 
 /* Bind the handle to a CUDA stream (cudaStream_t passed as void*; NULL is the
- * default stream).  All later work of the handle is enqueued there. */
+ * legacy default stream).  All later work of the handle is enqueued there.
+ * A new handle uses a non-blocking stream of its own. */
 int sbiem_set_stream(sbiem_t s, void* cuda_stream);
 
 /*
@@ -141,6 +142,25 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps);
 /* Synchronize and read the device status bits (SBIEM_FLAG_*) and the number of
  * committed steps; clear != 0 resets the status word (state is unaffected). */
 int sbiem_status(sbiem_t s, uint32_t* flags, int64_t* steps_done, int clear);
+
+/*
+ * sbiem_run -- adaptive time integration up to t_end by step doubling
+ * (Sec. 3.2): dt = m dt_min with m a power of two (m <= 2^30, <= m_max).  A
+ * trial advances once by dt (not committed) and twice by dt/2; the error is
+ * eps = max_i |delta_full - delta_halves| (slip).  eps <= eps0: the
+ * two-half-step state is kept and m becomes the largest power of two <=
+ * 0.9 (eps0/eps)^(1/3) m, at most 2m.  eps > eps0 or a failure (Newton cap,
+ * opening, state): the state and the overwritten history slots are restored
+ * and m is at least halved.  At m = 1 a single step is taken and its error
+ * is ignored; a failure there returns SBIEM_ERR_DTMIN with the state at the
+ * start of that step.  Stops after max_steps accepted steps.
+ * Outputs (host, may be NULL): accepted steps, the next m, the time reached,
+ * and m_hist[k] = m of accepted step k (caller buffer of max_steps int64).
+ * The first call allocates the snapshot buffers (about the ring size).
+ */
+int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max,
+              int64_t max_steps, int64_t* steps_done, int64_t* m_next, double* t_reached,
+              int64_t* m_hist);
 
 /*
  * sbiem_step_host -- a step driven from host memory: copies tau_load (N
@@ -243,6 +263,12 @@ int sbiem_history_sums_noalloc(int64_t nmodes, int32_t precision, int64_t m,
                                const int64_t* ring_off, const int64_t* w_off,
                                const int32_t* R, const int32_t* M, const int32_t* head,
                                double* AT, double* AN, void* stream);
+
+/* sbiem_history_enqueue -- enqueue the history convolution of
+ * sbiem_history_sums on the handle's stream without synchronizing or copying
+ * (for timing the kernel with events on that stream).  The sums overwrite the
+ * handle's internal A^T, A^N, which the next step recomputes anyway. */
+int sbiem_history_enqueue(sbiem_t s, int64_t m);
 
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */

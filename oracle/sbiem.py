@@ -418,3 +418,75 @@ class Oracle:
         r2["pass1"] = r1
         self.last = r2
         return STATUS_OK
+
+
+# ---------------------------------------------------------------- adaptive dt
+def _snapshot(o: Oracle) -> dict:
+    keys = ("delta", "V", "theta", "thetadot", "hist_T", "hist_N", "head")
+    snap = {k: getattr(o, k).copy() for k in keys}
+    snap["t"], snap["steps"] = o.t, o.steps
+    return snap
+
+
+def _restore(o: Oracle, snap: dict) -> None:
+    for k, v in snap.items():
+        setattr(o, k, v.copy() if isinstance(v, np.ndarray) else v)
+
+
+def adaptive_run(o: Oracle, t_end: float, eps0: float, m0: int = 1, m_max: int = 1 << 40,
+                 max_steps: int = 10 ** 9):
+    """Step-doubling time integration (Sec. 3.2) with dt = m dt_min, m a power of two.
+
+    A trial from state S advances once by dt and twice by dt/2; the error is
+    eps = max_i |delta_full - delta_halves| (slip, Sec. 3.2 with u read as the
+    slip).  eps <= eps0: the two-half-step state is kept and the next m is the
+    largest power of two <= 0.9 (eps0/eps)^(1/3) m, at most doubling.  eps >
+    eps0 or any failure (Newton, opening, state): S is restored and m is the
+    largest power of two <= min(m/2, 0.9 (eps0/eps)^(1/3) m).  At m = 1
+    (dt_min) a single step is taken and its error is ignored; a failure there
+    stops the run (status returned with the DTMIN flag 8).
+
+    Returns (status, list of accepted m).
+    """
+    m = max(1, int(m0))
+    accepted = []
+    while o.t < t_end * (1 - 1e-15) and len(accepted) < max_steps:
+        if m == 1:
+            st = o.step(1)
+            if st:
+                return st | 8, accepted
+            accepted.append(1)
+            m = 2
+            continue
+        snap = _snapshot(o)
+        st = o.step(m)
+        if st:
+            _restore(o, snap)
+            m //= 2
+            continue
+        delta_full = o.delta.copy()
+        _restore(o, snap)
+        st = o.step(m // 2)
+        if not st:
+            st = o.step(m // 2)
+        if st:
+            _restore(o, snap)
+            m //= 2
+            continue
+        eps = float(np.abs(o.delta - delta_full).max())
+        factor = 0.9 * (eps0 / eps) ** (1.0 / 3.0) if eps > 0 else np.inf
+        if eps > eps0:
+            _restore(o, snap)
+            m_new = m // 2
+            while m_new > 1 and m_new > factor * m:
+                m_new //= 2
+            m = max(1, m_new)
+            continue
+        accepted.append(m)
+        m_new = m
+        while m_new * 2 <= factor * m and m_new < 2 * m:
+            m_new *= 2
+        while m_new > 1 and m_new > factor * m:
+            m_new //= 2
+        m = max(1, min(m_new, m_max))
+    return 0, accepted

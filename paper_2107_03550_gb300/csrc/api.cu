@@ -67,6 +67,14 @@ struct sbiem_s {
   std::vector<cudaEvent_t> pev;
   std::map<int, std::vector<cudaGraphNode_t>> pnodes;  // per graph: nodes of marks 0..3
   int64_t chunk_slots = 2048;
+  // adaptive run (Sec. 3.2): snapshot of the state, undo copy of ring slots
+  double* snap = nullptr;        // V, xV, psi, thd, delta (5N) + t
+  double2* snap_spec = nullptr;  // dhat, khat
+  int32_t* snap_head = nullptr;
+  long long* snap_steps = nullptr;
+  void* undo = nullptr;          // ring-sized
+  double* dfull = nullptr;
+  double* d_err = nullptr;
 
   bool fp32() const { return p.precision == 1; }
 };
@@ -163,7 +171,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
   COPYP(chunks); COPYP(nchunks); COPYP(status); COPYP(steps_done); COPYP(t);
-  COPYP(it_sum); COPYP(it_max); COPYP(work);
+  COPYP(it_sum); COPYP(it_max); COPYP(work); COPYP(w0pow);
 #undef COPYP
   bool ok = true;
   f.ring = alloc_n<Slot<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
@@ -194,13 +202,55 @@ void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
   probe_mark(s, 2, st);
   launch_pass<R>(f, 1, m, st);
   launch_pass<R>(f, 2, m, st);
+  if (m > 1) launch_push_multi<R>(f, m, st);
   launch_commit<R>(f, m, st);
   probe_mark(s, 3, st);
+}
+
+// The step without its commit: pass-2 results stay staged (delta2, V2, ...).
+template <class R>
+void enqueue_trial_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
+  cudaMemsetAsync(f.work, 0, sizeof(int), st);
+  launch_history<R>(f, m, s->hist_grid, st);
+  launch_pass<R>(f, 1, m, st);
+  launch_pass<R>(f, 2, m, st);
 }
 
 void enqueue_step(sbiem_s* s, int m, cudaStream_t st) {
   if (s->fp32()) enqueue_step_t<float>(s, s->f32, m, st);
   else enqueue_step_t<double>(s, s->f64, m, st);
+}
+
+void enqueue_trial(sbiem_s* s, int m, cudaStream_t st) {
+  if (s->fp32()) enqueue_trial_t<float>(s, s->f32, m, st);
+  else enqueue_trial_t<double>(s, s->f64, m, st);
+}
+
+void ring_undo(sbiem_s* s, int m, int dir) {
+  if (s->fp32()) launch_ring_undo<float>(s->f32, m, s->undo, dir, s->stream);
+  else launch_ring_undo<double>(s->f64, m, s->undo, dir, s->stream);
+}
+
+// Save (save = true) or restore the committed state that a step changes.
+int snapshot(sbiem_s* s, bool save) {
+  auto& f = s->f64;
+  const size_t nb = sizeof(double) * s->N;
+  double* arrs[] = {f.V, f.xV, f.psi, f.thd, f.delta};
+  for (int k = 0; k < 5; ++k) {
+    double* sn = s->snap + static_cast<size_t>(k) * s->N;
+    CK(cudaMemcpyAsync(save ? sn : arrs[k], save ? arrs[k] : sn, nb, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  double* snt = s->snap + static_cast<size_t>(5) * s->N;
+  CK(cudaMemcpyAsync(save ? snt : f.t, save ? f.t : snt, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  const size_t sb = sizeof(double2) * s->nmodes;
+  CK(cudaMemcpyAsync(save ? s->snap_spec : f.dhat, save ? f.dhat : s->snap_spec, sb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(save ? s->snap_spec + s->nmodes : f.khat, save ? f.khat : s->snap_spec + s->nmodes, sb,
+                     cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(save ? s->snap_head : f.head, save ? f.head : s->snap_head, sizeof(int32_t) * s->nmodes,
+                     cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(save ? s->snap_steps : f.steps_done, save ? f.steps_done : s->snap_steps, sizeof(long long),
+                     cudaMemcpyDeviceToDevice, s->stream));
+  return SBIEM_OK;
 }
 
 int status_to_code(unsigned st) {
@@ -363,6 +413,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN};
   for (double2** c : carr) *c = alloc_n<double2>(s, s->nmodes, &ok);
   f.partial = alloc_n<double4>(s, std::max<size_t>(s->chunks.size(), 1), &ok);
+  f.w0pow = alloc_n<double2>(s, static_cast<size_t>(s->nmodes) * kPow2Slots, &ok);
   f.counter = alloc_n<int>(s, s->nmodes, &ok);
   int64_t* d_roff = alloc_n<int64_t>(s, s->nmodes + 1, &ok);
   int64_t* d_woff = alloc_n<int64_t>(s, s->nmodes + 1, &ok);
@@ -475,7 +526,10 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   int rc;
   if (s->fp32()) {
     rc = setup_device<float>(s, s->f32, f);
-    if (rc == SBIEM_OK) launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+    if (rc == SBIEM_OK) {
+      launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+      launch_weight_pow2<float>(s->f32, s->stream);
+    }
   } else {
     f.ring = alloc_n<Slot64>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
     f.w = alloc_n<W2<double>>(s, static_cast<size_t>(std::max<int64_t>(s->total_w, 1)), &ok);
@@ -485,7 +539,10 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     f.g = make_geom(N, sizeof(double2));
     f.tw = s->tw64;
     rc = ok ? SBIEM_OK : fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
-    if (rc == SBIEM_OK) launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+    if (rc == SBIEM_OK) {
+      launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+      launch_weight_pow2<double>(f, s->stream);
+    }
   }
   if (rc == SBIEM_OK) rc = recompute_spectral_sums(s);
   if (rc == SBIEM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
@@ -508,8 +565,10 @@ void sbiem_destroy(sbiem_t s) {
 int sbiem_set_stream(sbiem_t s, void* stream) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
   CK(cudaStreamSynchronize(s->stream));
-  s->stream = stream ? static_cast<cudaStream_t>(stream) : s->own;
-  s->user_stream = stream != nullptr;
+  // NULL is the legacy default stream (cudaStreamLegacy), ordered with other
+  // work on it; step graphs are still captured on the handle's own stream
+  s->stream = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+  s->user_stream = true;
   return SBIEM_OK;
 }
 
@@ -597,6 +656,99 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
     CK(cudaGraphLaunch(it->second, s->stream));
   }
   return SBIEM_OK;
+}
+
+int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, int64_t max_steps,
+              int64_t* steps_out, int64_t* m_next, double* t_out, int64_t* m_hist) {
+  if (!s || !(eps0 > 0) || m0 < 1 || m_max < 1 || max_steps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
+  auto& f = s->f64;
+  bool ok = true;
+  if (!s->snap) {
+    s->snap = alloc_n<double>(s, static_cast<size_t>(5) * s->N + 1, &ok);
+    s->snap_spec = alloc_n<double2>(s, static_cast<size_t>(2) * s->nmodes, &ok);
+    s->snap_head = alloc_n<int32_t>(s, s->nmodes, &ok);
+    s->snap_steps = alloc_n<long long>(s, 1, &ok);
+    s->dfull = alloc_n<double>(s, s->N, &ok);
+    s->d_err = alloc_n<double>(s, 1, &ok);
+    const size_t slot = s->fp32() ? sizeof(Slot32) : sizeof(Slot64);
+    s->undo = dev_alloc(s, slot * static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)));
+    if (!s->undo) ok = false;
+    if (!ok) return fail(SBIEM_ERR_NOMEM, "adaptive run: snapshot allocation failed");
+  }
+  // m: a power of two in [1, 2^30]
+  auto pow2_floor = [](int64_t v) {
+    int64_t p = 1;
+    while (p * 2 <= v && p < (int64_t(1) << 30)) p *= 2;
+    return p;
+  };
+  int64_t m = pow2_floor(m0);
+  m_max = pow2_floor(m_max);
+  double t = 0.0;
+  CK(cudaMemcpyAsync(&t, f.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  int64_t accepted = 0;
+  uint32_t st = 0;
+  int rc = SBIEM_OK;
+  while (t < t_end * (1.0 - 1e-15) && accepted < max_steps) {
+    if (m == 1) {
+      enqueue_step(s, 1, s->stream);
+      rc = sbiem_status(s, &st, nullptr, 1);
+      if (rc) return rc;
+      if (st) {
+        rc = fail(SBIEM_ERR_DTMIN, "step failed at dt_min; state left at the start of the step");
+        break;
+      }
+      if (m_hist) m_hist[accepted] = 1;
+      ++accepted;
+      t += s->dt_min;
+      m = std::min<int64_t>(2, m_max);
+      continue;
+    }
+    const int mi = static_cast<int>(m);
+    // full step, not committed
+    enqueue_trial(s, mi, s->stream);
+    rc = sbiem_status(s, &st, nullptr, 1);
+    if (rc) return rc;
+    if (st) {
+      m /= 2;
+      continue;
+    }
+    CK(cudaMemcpyAsync(s->dfull, f.delta2, sizeof(double) * s->N, cudaMemcpyDeviceToDevice, s->stream));
+    rc = snapshot(s, true);
+    if (rc) return rc;
+    ring_undo(s, mi, 0);
+    enqueue_step(s, mi / 2, s->stream);
+    enqueue_step(s, mi / 2, s->stream);
+    launch_maxdiff(f.delta, s->dfull, s->N, s->d_err, s->stream);
+    double eps = 0.0;
+    CK(cudaMemcpyAsync(&eps, s->d_err, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    rc = sbiem_status(s, &st, nullptr, 1);
+    if (rc) return rc;
+    const double factor = eps > 0.0 ? 0.9 * std::cbrt(eps0 / eps) : HUGE_VAL;
+    if (st || eps > eps0) {
+      rc = snapshot(s, false);
+      if (rc) return rc;
+      ring_undo(s, mi, 1);
+      int64_t mn = m / 2;
+      if (!st)
+        while (mn > 1 && static_cast<double>(mn) > factor * static_cast<double>(m)) mn /= 2;
+      m = std::max<int64_t>(1, mn);
+      continue;
+    }
+    if (m_hist) m_hist[accepted] = m;
+    ++accepted;
+    t += static_cast<double>(m) * s->dt_min;
+    int64_t mn = m;
+    while (static_cast<double>(mn * 2) <= factor * static_cast<double>(m) && mn < 2 * m) mn *= 2;
+    while (mn > 1 && static_cast<double>(mn) > factor * static_cast<double>(m)) mn /= 2;
+    m = std::max<int64_t>(1, std::min(mn, m_max));
+  }
+  CK(cudaMemcpyAsync(&t, f.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (steps_out) *steps_out = accepted;
+  if (m_next) *m_next = m;
+  if (t_out) *t_out = t;
+  return rc;
 }
 
 int sbiem_step_host(sbiem_t s, double dt, const double* tau_load, double* V_out) {
@@ -758,6 +910,16 @@ int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   CK(cudaMemcpyAsync(AT, s->f64.AT, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(AN, s->f64.AN, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  return SBIEM_OK;
+}
+
+int sbiem_history_enqueue(sbiem_t s, int64_t m) {
+  if (!s || m < 1 || m > (int64_t(1) << 30)) return fail(SBIEM_ERR_INVALID, "bad argument");
+  const int mi = static_cast<int>(m);
+  CK(cudaMemsetAsync(s->f64.work, 0, sizeof(int), s->stream));
+  if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
+  else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
+  CK(cudaGetLastError());
   return SBIEM_OK;
 }
 

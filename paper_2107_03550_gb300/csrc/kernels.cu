@@ -103,13 +103,20 @@ __device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass,
   double tr = 0.0, ti = 0.0, sr = 0.0, si = 0.0;
   if (m > 0) {
     const double k = kTwoPi * m / f.L;
+    // current interval [0, m_dt dt_min]: sum of the first m_dt weights
     double w0T = 0.0, w0N = 0.0;
-    const int lim = min(m_dt, f.Mn[m]);
-    const int64_t wo = f.w_off[m];
-    for (int j = 0; j < lim; ++j) {
-      const W2<R> w = f.w[wo + j];
-      w0T += static_cast<double>(w.x);
-      w0N += static_cast<double>(w.y);
+    if ((m_dt & (m_dt - 1)) == 0) {
+      const double2 w0 = f.w0pow[static_cast<size_t>(m) * kPow2Slots + (31 - __clz(m_dt))];
+      w0T = w0.x;
+      w0N = w0.y;
+    } else {
+      const int lim = min(m_dt, f.Mn[m]);
+      const int64_t wo = f.w_off[m];
+      for (int j = 0; j < lim; ++j) {
+        const W2<R> w = f.w[wo + j];
+        w0T += static_cast<double>(w.x);
+        w0N += static_cast<double>(w.y);
+      }
     }
     const double2 D = f.dhat[m], K = f.khat[m], AT = f.AT[m], AN = f.AN[m];
     tr = -k * (f.S * (D.x + dt * U.x) + f.mu * (w0T * U.x + AT.x));
@@ -485,18 +492,111 @@ __global__ void k_commit(DevFault<R> f, int m_dt, double dt) {
       }
       Slot<R>* ring = f.ring + f.ring_off[i];
       int h = f.head[i];
-      const int cnt = min(m_dt, Rn);
-      for (int c = 0; c < cnt; ++c) {
+      if (m_dt == 1) {
         h = (h == 0) ? Rn - 1 : h - 1;
         ring[h] = s;
+      } else {
+        // the m_dt copies were written by k_push_multi; move the head
+        h = static_cast<int>(((h - static_cast<int64_t>(m_dt)) % Rn + Rn) % Rn);
       }
-      if (m_dt > Rn) h = static_cast<int>(((h - static_cast<int64_t>(m_dt - Rn)) % Rn + Rn) % Rn);
       f.head[i] = h;
     }
   }
   if (i == 0) {
     *f.steps_done += 1;
     *f.t += dt;
+  }
+}
+
+// Push of m_dt > 1 copies of this step's spectra (a step of m_dt dt_min,
+// Sec. 3.3 last paragraph on the dt_min grid): the logical slots
+// i < min(m_dt, R_n) after the push hold the value.  Runs before k_commit,
+// which moves the heads.
+template <class R>
+__global__ void k_push_multi(DevFault<R> f, int m_dt) {
+  if (*f.status) return;
+  for (int c = blockIdx.x; c < f.nchunks; c += gridDim.x) {
+    const Chunk cd = f.chunks[c];
+    const int n = cd.mode;
+    const int Rn = f.Rn[n];
+    const int cnt = min(m_dt, Rn);
+    if (cd.i0 >= cnt) continue;
+    const int hn = static_cast<int>(((f.head[n] - static_cast<int64_t>(cnt)) % Rn + Rn) % Rn);
+    const double2 U = f.U2[n], Q = f.Q2[n];
+    Slot<R> v;
+    if constexpr (sizeof(R) == 8) {
+      v.t = U;
+      v.n = Q;
+    } else {
+      v = make_float4(static_cast<float>(U.x), static_cast<float>(U.y), static_cast<float>(Q.x),
+                      static_cast<float>(Q.y));
+    }
+    Slot<R>* ring = f.ring + f.ring_off[n];
+    const int64_t iend = min(cd.i1, static_cast<int64_t>(cnt));
+    for (int64_t i = cd.i0 + threadIdx.x; i < iend; i += blockDim.x) {
+      int64_t pos = hn + i;
+      if (pos >= Rn) pos -= Rn;
+      ring[pos] = v;
+    }
+  }
+}
+
+// w0pow[n][p] = sum_{j < min(2^p, M_n)} w_{n,j} (FP64, both fields): the
+// weight of a current interval of 2^p dt_min.
+template <class R>
+__global__ void k_weight_pow2(const W2<R>* w, const int64_t* w_off, const int32_t* Mn, int nmodes, double2* out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nmodes) return;
+  const int M = Mn[n];
+  const W2<R>* wn = w + w_off[n];
+  double sT = 0.0, sN = 0.0;
+  int j = 0;
+  for (int p = 0; p < kPow2Slots; ++p) {
+    const int64_t lim = min(static_cast<int64_t>(1) << p, static_cast<int64_t>(M));
+    for (; j < lim; ++j) {
+      sT += static_cast<double>(wn[j].x);
+      sN += static_cast<double>(wn[j].y);
+    }
+    out[static_cast<size_t>(n) * kPow2Slots + p] = make_double2(sT, sN);
+  }
+}
+
+// Copy the ring slots a push of m_dt copies overwrites (positions
+// head - min(m_dt, R) .. head - 1) to or from the undo buffer (same layout as
+// the ring).  dir = 0: save, 1: restore.
+template <class R>
+__global__ void k_ring_undo(DevFault<R> f, int m_dt, Slot<R>* undo, int dir) {
+  for (int c = blockIdx.x; c < f.nchunks; c += gridDim.x) {
+    const Chunk cd = f.chunks[c];
+    const int n = cd.mode;
+    const int Rn = f.Rn[n];
+    const int cnt = min(m_dt, Rn);
+    if (cd.i0 >= cnt) continue;
+    const int hn = static_cast<int>(((f.head[n] - static_cast<int64_t>(cnt)) % Rn + Rn) % Rn);
+    Slot<R>* ring = f.ring + f.ring_off[n];
+    Slot<R>* u = undo + f.ring_off[n];
+    const int64_t iend = min(cd.i1, static_cast<int64_t>(cnt));
+    for (int64_t i = cd.i0 + threadIdx.x; i < iend; i += blockDim.x) {
+      int64_t pos = hn + i;
+      if (pos >= Rn) pos -= Rn;
+      if (dir == 0) u[i] = ring[pos];
+      else ring[pos] = u[i];
+    }
+  }
+}
+
+// max_i |a_i - b_i| into *out (one block).
+__global__ void k_maxdiff(const double* a, const double* b, int n, double* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(a[i] - b[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *out = m;
   }
 }
 
@@ -633,6 +733,29 @@ int history_blocks_per_sm() {
 }
 
 template <class R>
+void launch_push_multi(const DevFault<R>& f, int m_dt, cudaStream_t st) {
+  if (f.nchunks == 0) return;
+  const int grid = f.nchunks < 4096 ? f.nchunks : 4096;
+  k_push_multi<R><<<grid, 256, 0, st>>>(f, m_dt);
+}
+
+template <class R>
+void launch_weight_pow2(const DevFault<R>& f, cudaStream_t st) {
+  k_weight_pow2<R><<<(f.nmodes + 127) / 128, 128, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.w0pow);
+}
+
+template <class R>
+void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaStream_t st) {
+  if (f.nchunks == 0) return;
+  const int grid = f.nchunks < 4096 ? f.nchunks : 4096;
+  k_ring_undo<R><<<grid, 256, 0, st>>>(f, m_dt, static_cast<Slot<R>*>(undo), dir);
+}
+
+void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st) {
+  k_maxdiff<<<1, 1024, 0, st>>>(a, b, n, out);
+}
+
+template <class R>
 void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st) {
   const int n = f.N > f.nmodes ? f.N : f.nmodes;
   const int nt = 256;
@@ -695,6 +818,12 @@ template void launch_history<double>(const DevFault<double>&, int, int, cudaStre
 template void launch_history<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_pass<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_pass<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_push_multi<double>(const DevFault<double>&, int, cudaStream_t);
+template void launch_push_multi<float>(const DevFault<float>&, int, cudaStream_t);
+template void launch_weight_pow2<double>(const DevFault<double>&, cudaStream_t);
+template void launch_weight_pow2<float>(const DevFault<float>&, cudaStream_t);
+template void launch_ring_undo<double>(const DevFault<double>&, int, void*, int, cudaStream_t);
+template void launch_ring_undo<float>(const DevFault<float>&, int, void*, int, cudaStream_t);
 template void launch_commit<double>(const DevFault<double>&, int, cudaStream_t);
 template void launch_commit<float>(const DevFault<float>&, int, cudaStream_t);
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double, cudaStream_t);

@@ -22,6 +22,9 @@ template <> struct SlotT<double> { using T = Slot64; };
 template <> struct SlotT<float> { using T = Slot32; };
 template <class R> using Slot = typename SlotT<R>::T;
 
+// Entries per mode of the current-interval weight table (m = 2^p, p < 41).
+constexpr int kPow2Slots = 41;
+
 // Kernel weight pair (w^T_{n,j}, w^N_{n,j}) of one lag.
 template <class R> using W2 = Cx<R>;
 
@@ -67,6 +70,7 @@ struct DevFault {
   // history
   Slot<R>* ring;
   W2<R>* w;
+  double2* w0pow;                          // [mode][p]: sum of the first 2^p weights
   const int64_t *ring_off, *w_off;
   const int32_t *Rn, *Mn;
   int32_t* head;
@@ -91,6 +95,14 @@ template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid,
 template <class R> int history_blocks_per_sm();
 template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
 template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st);
+// Multi-slot history push for steps of m_dt > 1 (before launch_commit).
+template <class R> void launch_push_multi(const DevFault<R>& f, int m_dt, cudaStream_t st);
+// Fill f.w0pow from the weights.
+template <class R> void launch_weight_pow2(const DevFault<R>& f, cudaStream_t st);
+// Save (dir 0) / restore (dir 1) the ring slots a push of m_dt copies overwrites.
+template <class R> void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaStream_t st);
+// *out = max_i |a_i - b_i|.
+void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st);
 template <class R> void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg,
                                        double h, double cs, cudaStream_t st);
 

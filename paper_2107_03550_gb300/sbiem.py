@@ -63,6 +63,8 @@ _SIGS = {
     "sbiem_enqueue": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int64]),
     "sbiem_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _I64, ctypes.c_int]),
     "sbiem_step_host": (ctypes.c_int, [_VP, ctypes.c_double, _D, _D]),
+    "sbiem_run": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                 ctypes.c_int64, _I64, _I64, _D, _I64]),
     "sbiem_get_state": (ctypes.c_int, [_VP, _D, _D, _D, _D, _D, _D]),
     "sbiem_set_state": (ctypes.c_int, [_VP, _D, _D, _D]),
     "sbiem_windows": (ctypes.c_int, [_VP, _I64]),
@@ -71,6 +73,7 @@ _SIGS = {
     "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
     "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
+    "sbiem_history_enqueue": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
@@ -219,10 +222,15 @@ class Fault:
 
     # ------------------------------------------------------------------ steps
     def set_stream(self, stream) -> None:
-        """Bind to a CUDA stream: a torch.cuda.Stream, a raw handle (int) or None."""
+        """Bind to a CUDA stream: a torch.cuda.Stream or a raw handle (int); 0 / None is the
+        legacy default stream (torch's default stream)."""
         raw = getattr(stream, "cuda_stream", stream)
         self._stream = stream
         self._check(self.lib.sbiem_set_stream(self.h, _VP(raw or None)))
+
+    def history_enqueue(self, m: int = 1) -> None:
+        """Enqueue the history convolution alone (no synchronization), for timing."""
+        self._check(self.lib.sbiem_history_enqueue(self.h, int(m)))
 
     def step(self, dt=None) -> None:
         self._check(self.lib.sbiem_step(self.h, float(dt or self.dt_min)))
@@ -239,6 +247,18 @@ class Fault:
         st = ctypes.c_int64()
         self._check(self.lib.sbiem_status(self.h, ctypes.byref(fl), ctypes.byref(st), int(clear)))
         return int(fl.value), int(st.value)
+
+    def run(self, t_end: float, eps0: float, m0: int = 1, m_max: int = 1 << 30, max_steps: int = 10 ** 6):
+        """Adaptive step-doubling run (Sec. 3.2).  Returns (accepted m list, next m, t reached, code)."""
+        hist = np.zeros(max(int(max_steps), 1), dtype=np.int64)
+        n = ctypes.c_int64()
+        mn = ctypes.c_int64()
+        t = ctypes.c_double()
+        rc = self.lib.sbiem_run(self.h, float(t_end), float(eps0), int(m0), int(m_max), int(max_steps),
+                                ctypes.byref(n), ctypes.byref(mn), ctypes.byref(t), hist.ctypes.data_as(_I64))
+        if rc not in (0, -7):
+            self._check(rc)
+        return hist[:n.value].tolist(), int(mn.value), float(t.value), int(rc)
 
     def step_host(self, dt=None, tau_load=None, V_out=None) -> None:
         ta, tp = _ptr(tau_load, np.float64, self.N)
