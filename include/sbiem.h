@@ -270,6 +270,35 @@ int sbiem_history_sums_noalloc(int64_t nmodes, int32_t precision, int64_t m,
  * handle's internal A^T, A^N, which the next step recomputes anyway. */
 int sbiem_history_enqueue(sbiem_t s, int64_t m);
 
+/* ------------------------------------------------------------- ensembles
+ * A batch advances many faults together (independent realizations of uneven
+ * N): one launch of the history convolution covers the chunks of every
+ * member, and per group of equal N one launch of each pass kernel handles
+ * all members of the group (the groups run as parallel branches of one CUDA
+ * graph per step).  Members keep their own state, read with sbiem_get_state
+ * after sbiem_batch_status; they must share the device and the precision.
+ * A member whose step fails stops committing (its own status word) while the
+ * others go on.
+ *
+ * sbiem_batch_create: n member handles (not owned); chunk_slots = history
+ *   slots per chunk of the batched convolution (0: derived from the resident
+ *   warps).  Errors: SBIEM_ERR_INVALID, SBIEM_ERR_NOMEM.
+ * sbiem_batch_enqueue: nsteps steps of each member's dt_min, asynchronous.
+ * sbiem_batch_status: synchronize; per member (caller order) status flags
+ *   and committed steps (arrays of n, may be NULL).
+ * sbiem_batch_tune: autotuner -- times the batched history convolution for
+ *   chunk lengths {256 ... 8192} slots and resident-CTA counts, reps timed
+ *   launches each (median), and keeps the fastest; returns the choice and its
+ *   time.  The state is not changed.
+ */
+typedef struct sbiem_batch_s* sbiem_batch_t;
+int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_t chunk_slots);
+void sbiem_batch_destroy(sbiem_batch_t b);
+int sbiem_batch_set_stream(sbiem_batch_t b, void* cuda_stream);
+int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps);
+int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done);
+int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* blocks_per_sm, float* ms);
+
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);

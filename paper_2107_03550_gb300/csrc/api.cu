@@ -974,3 +974,313 @@ int sbiem_footprint(sbiem_t s, int64_t* hist_bytes, int64_t* device_bytes) {
 }
 
 }  // extern "C"
+
+// ============================================================ ensembles
+// A batch steps many faults at once: one history-convolution launch over the
+// chunks of every member, then per group of equal N one launch of each pass
+// kernel with one member per blockIdx.y, the groups as parallel graph branches.
+struct sbiem_batch_s {
+  std::vector<sbiem_s*> members;  // grouped order
+  std::vector<int> order;         // grouped position -> caller index
+  bool fp32 = false;
+  int sm_count = 0, hist_grid = 0, per_sm = 1;
+  int64_t chunk_slots = 0;
+  cudaStream_t stream = nullptr, own = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> fork_join;
+  struct Group {
+    int N, first, count;
+    FftGeom g;
+  };
+  std::vector<Group> groups;
+  void* fs = nullptr;  // DevFault<R>[members] on the device
+  Chunk* chunks = nullptr;
+  int nchunks = 0;
+  double4* partial = nullptr;
+  int* counter = nullptr;
+  int* work = nullptr;
+  std::vector<void*> allocs;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_def = nullptr;
+};
+
+namespace {
+
+void batch_free(sbiem_batch_s* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->graph_def) cudaGraphDestroy(b->graph_def);
+  b->graph = nullptr;
+  b->graph_def = nullptr;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+  for (auto e : b->fork_join) cudaEventDestroy(e);
+  for (auto st : b->branch) cudaStreamDestroy(st);
+  if (b->own) cudaStreamDestroy(b->own);
+}
+
+void* batch_alloc(sbiem_batch_s* b, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  b->allocs.push_back(p);
+  return p;
+}
+
+// Chunk table over all members for a given chunk length; partial, counter
+// and work buffers sized for it; member descriptors pointing at them.
+template <class R>
+int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
+  std::vector<Chunk> ch;
+  std::vector<int64_t> cbase(b->members.size() + 1, 0);
+  for (size_t r = 0; r < b->members.size(); ++r) {
+    const sbiem_s* s = b->members[r];
+    cbase[r + 1] = cbase[r] + s->nmodes;
+    for (int n = 0; n < s->nmodes; ++n) {
+      const int64_t cnt = (s->Rn[n] + chunk_slots - 1) / chunk_slots;
+      const int first = static_cast<int>(ch.size());
+      for (int64_t c = 0; c < cnt; ++c) {
+        Chunk k{};
+        k.mode = n;
+        k.first = first;
+        k.count = static_cast<int32_t>(cnt);
+        k.pad = static_cast<int32_t>(r);
+        k.i0 = c * chunk_slots;
+        k.i1 = std::min<int64_t>((c + 1) * chunk_slots, s->Rn[n]);
+        ch.push_back(k);
+      }
+    }
+  }
+  if (ch.size() > static_cast<size_t>(1) << 30) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
+  // (re)allocate the chunk-dependent buffers
+  auto realloc = [&](void** p, size_t bytes) {
+    if (*p) {
+      cudaFree(*p);
+      b->allocs.erase(std::remove(b->allocs.begin(), b->allocs.end(), *p), b->allocs.end());
+    }
+    *p = batch_alloc(b, bytes);
+    return *p != nullptr;
+  };
+  bool ok = realloc(reinterpret_cast<void**>(&b->chunks), sizeof(Chunk) * std::max<size_t>(ch.size(), 1)) &&
+            realloc(reinterpret_cast<void**>(&b->partial), sizeof(double4) * std::max<size_t>(ch.size(), 1));
+  if (!b->counter) ok = ok && (b->counter = static_cast<int*>(batch_alloc(b, sizeof(int) * cbase.back()))) != nullptr;
+  if (!b->work) ok = ok && (b->work = static_cast<int*>(batch_alloc(b, sizeof(int)))) != nullptr;
+  if (!b->fs) ok = ok && (b->fs = batch_alloc(b, sizeof(DevFault<R>) * b->members.size())) != nullptr;
+  if (!ok) return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed");
+  std::vector<DevFault<R>> fs(b->members.size());
+  for (size_t r = 0; r < b->members.size(); ++r) {
+    DevFault<R> f;
+    if constexpr (sizeof(R) == 8) f = b->members[r]->f64;
+    else f = b->members[r]->f32;
+    f.partial = b->partial;
+    f.counter = b->counter + cbase[r];
+    f.work = b->work;
+    fs[r] = f;
+  }
+  CK(cudaMemsetAsync(b->counter, 0, sizeof(int) * cbase.back(), b->stream));
+  CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->fs, fs.data(), sizeof(DevFault<R>) * fs.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  b->nchunks = static_cast<int>(ch.size());
+  b->chunk_slots = chunk_slots;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    cudaGraphDestroy(b->graph_def);
+    b->graph = nullptr;
+    b->graph_def = nullptr;
+  }
+  return SBIEM_OK;
+}
+
+template <class R>
+void batch_history(sbiem_batch_s* b, cudaStream_t st) {
+  cudaMemsetAsync(b->work, 0, sizeof(int), st);
+  launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->work, 1,
+                          b->hist_grid, st);
+}
+
+template <class R>
+void batch_group_step(sbiem_batch_s* b, const sbiem_batch_s::Group& gr, cudaStream_t st) {
+  const DevFault<R>* fs = static_cast<const DevFault<R>*>(b->fs) + gr.first;
+  launch_pass_batch<R>(gr.g, fs, gr.count, gr.N, 1, 1, st);
+  launch_pass_batch<R>(gr.g, fs, gr.count, gr.N, 2, 1, st);
+  launch_commit_batch<R>(fs, gr.count, gr.N, 1, st);
+}
+
+template <class R>
+void batch_enqueue_step(sbiem_batch_s* b, cudaStream_t st) {
+  batch_history<R>(b, st);
+  // groups as parallel branches: fork after the history convolution, join at the end
+  const size_t ng = b->groups.size();
+  cudaEventRecord(b->fork_join[0], st);
+  for (size_t k = 0; k < ng; ++k) {
+    cudaStream_t bs = k == 0 ? st : b->branch[k - 1];
+    if (k > 0) cudaStreamWaitEvent(bs, b->fork_join[0], 0);
+    batch_group_step<R>(b, b->groups[k], bs);
+    if (k > 0) {
+      cudaEventRecord(b->fork_join[k], bs);
+      cudaStreamWaitEvent(st, b->fork_join[k], 0);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_t chunk_slots) {
+  if (!out || n < 1 || !members) return fail(SBIEM_ERR_INVALID, "bad argument");
+  *out = nullptr;
+  const bool fp32 = members[0] && members[0]->fp32();
+  for (int r = 0; r < n; ++r) {
+    if (!members[r]) return fail(SBIEM_ERR_INVALID, "NULL member");
+    if (members[r]->fp32() != fp32) return fail(SBIEM_ERR_INVALID, "batch members must share the precision");
+    if (members[r]->device != members[0]->device) return fail(SBIEM_ERR_INVALID, "batch members on several devices");
+    for (int q = 0; q < r; ++q)
+      if (members[q] == members[r]) return fail(SBIEM_ERR_INVALID, "a member appears twice");
+  }
+  auto* b = new sbiem_batch_s();
+  b->fp32 = fp32;
+  // group by N (stable), groups in order of first appearance
+  std::vector<int> Ns;
+  for (int r = 0; r < n; ++r)
+    if (std::find(Ns.begin(), Ns.end(), members[r]->N) == Ns.end()) Ns.push_back(members[r]->N);
+  for (int Nv : Ns) {
+    sbiem_batch_s::Group gr{};
+    gr.N = Nv;
+    gr.first = static_cast<int>(b->members.size());
+    for (int r = 0; r < n; ++r)
+      if (members[r]->N == Nv) {
+        b->members.push_back(members[r]);
+        b->order.push_back(r);
+      }
+    gr.count = static_cast<int>(b->members.size()) - gr.first;
+    gr.g = fp32 ? make_geom(Nv, sizeof(float2)) : make_geom(Nv, sizeof(double2));
+    if (fp32) configure_batch_kernels<float>(gr.g);
+    else configure_batch_kernels<double>(gr.g);
+    b->groups.push_back(gr);
+  }
+  cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, members[0]->device);
+  b->per_sm = fp32 ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
+  if (b->per_sm < 1) b->per_sm = 1;
+  b->hist_grid = b->sm_count * b->per_sm;
+  if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return fail(SBIEM_ERR_CUDA, "stream creation failed");
+  }
+  b->stream = b->own;
+  b->branch.resize(b->groups.size() > 1 ? b->groups.size() - 1 : 0);
+  for (auto& st : b->branch) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  b->fork_join.resize(b->groups.size());
+  for (auto& e : b->fork_join) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  for (auto* m : b->members) cudaStreamSynchronize(m->stream);
+  if (chunk_slots <= 0) {
+    int64_t tot = 0;
+    for (auto* m : b->members) tot += m->total_slots;
+    const int64_t warps = static_cast<int64_t>(b->hist_grid) * 8;
+    chunk_slots = std::min<int64_t>(std::max<int64_t>((tot / (4 * warps) + 127) / 128 * 128, 128), 4096);
+  }
+  int rc = fp32 ? batch_build<float>(b, chunk_slots) : batch_build<double>(b, chunk_slots);
+  if (rc) {
+    batch_free(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return SBIEM_OK;
+}
+
+void sbiem_batch_destroy(sbiem_batch_t b) {
+  if (!b) return;
+  batch_free(b);
+  delete b;
+}
+
+int sbiem_batch_set_stream(sbiem_batch_t b, void* stream) {
+  if (!b) return fail(SBIEM_ERR_INVALID, "NULL batch");
+  CK(cudaStreamSynchronize(b->stream));
+  b->stream = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
+  return SBIEM_OK;
+}
+
+int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps) {
+  if (!b || nsteps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
+  if (!b->graph) {
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
+    if (b->fp32) batch_enqueue_step<float>(b, b->own);
+    else batch_enqueue_step<double>(b, b->own);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(b->own, &b->graph_def);
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+      return fail(SBIEM_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    CK(cudaGraphInstantiate(&b->graph, b->graph_def, 0));
+  }
+  for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(b->graph, b->stream));
+  return SBIEM_OK;
+}
+
+int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done) {
+  if (!b) return fail(SBIEM_ERR_INVALID, "NULL batch");
+  CK(cudaStreamSynchronize(b->stream));
+  for (size_t q = 0; q < b->members.size(); ++q) {
+    uint32_t fl = 0;
+    int64_t sd = 0;
+    int rc = sbiem_status(b->members[q], &fl, &sd, 0);
+    if (rc) return rc;
+    if (flags) flags[b->order[q]] = fl;
+    if (steps_done) steps_done[b->order[q]] = sd;
+  }
+  return SBIEM_OK;
+}
+
+int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_out, float* ms_out) {
+  if (!b || reps < 1) return fail(SBIEM_ERR_INVALID, "bad argument");
+  const int64_t cand_c[] = {256, 512, 1024, 2048, 4096, 8192};
+  std::vector<int> cand_b = {b->per_sm};
+  if (b->per_sm > 1) cand_b.push_back(b->per_sm - 1);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int64_t best_c = b->chunk_slots;
+  int best_b = b->hist_grid / b->sm_count;
+  for (int64_t c : cand_c) {
+    int rc = b->fp32 ? batch_build<float>(b, c) : batch_build<double>(b, c);
+    if (rc) return rc;
+    for (int bl : cand_b) {
+      b->hist_grid = b->sm_count * bl;
+      // one untimed launch, then reps timed ones; take the median
+      if (b->fp32) batch_history<float>(b, b->stream);
+      else batch_history<double>(b, b->stream);
+      std::vector<float> t;
+      for (int k = 0; k < reps; ++k) {
+        CK(cudaEventRecord(e0, b->stream));
+        if (b->fp32) batch_history<float>(b, b->stream);
+        else batch_history<double>(b, b->stream);
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+      }
+      std::sort(t.begin(), t.end());
+      const float med = t[t.size() / 2];
+      if (med < best) {
+        best = med;
+        best_c = c;
+        best_b = bl;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->hist_grid = b->sm_count * best_b;
+  int rc = b->fp32 ? batch_build<float>(b, best_c) : batch_build<double>(b, best_c);
+  if (rc) return rc;
+  if (chunk_out) *chunk_out = best_c;
+  if (blocks_out) *blocks_out = best_b;
+  if (ms_out) *ms_out = best;
+  return SBIEM_OK;
+}
+
+}  // extern "C"

@@ -147,8 +147,9 @@ __device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass,
 // n2 (length N2), multiply by exp(-+2 pi i n1 k2 / N), store to
 // out[k2 N1 + n1].
 template <class R, bool INV, int PRO>
-__global__ void k_col(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ in,
-                      Cx<R>* __restrict__ out, DevFault<R> f, int pass, int m_dt, double dt) {
+__device__ __forceinline__ void col_body(const FftGeom& g, const Cx<R>* __restrict__ tw,
+                                         const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
+                                         const DevFault<R>& f, int pass, int m_dt, double dt) {
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -189,11 +190,26 @@ __global__ void k_col(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>
   }
 }
 
+template <class R, bool INV, int PRO>
+__global__ void k_col(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ in,
+                      Cx<R>* __restrict__ out, const __grid_constant__ DevFault<R> f, int pass, int m_dt,
+                      double dt) {
+  col_body<R, INV, PRO>(g, tw, in, out, f, pass, m_dt, dt);
+}
+
+// Batched column pass: member blockIdx.y of an ensemble of equal-N faults.
+template <class R, bool INV, int PRO>
+__global__ void k_col_b(const FftGeom g, const DevFault<R>* __restrict__ fs, int pass, int m_dt) {
+  const DevFault<R>& f = fs[blockIdx.y];
+  col_body<R, INV, PRO>(g, f.tw, nullptr, f.zt, f, pass, m_dt, m_dt * f.dt_min);
+}
+
 // Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
 // (length N1) and store to out[k2 + N2 k1], times scale.
 template <class R, bool INV>
-__global__ void k_row(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ in,
-                      Cx<R>* __restrict__ out, R scale, const unsigned* status) {
+__device__ __forceinline__ void row_body(const FftGeom& g, const Cx<R>* __restrict__ tw,
+                                         const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out, R scale,
+                                         const unsigned* status) {
   using C = Cx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -218,6 +234,18 @@ __global__ void k_row(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>
     v.y *= scale;
     out[(c0 + b) + g.N2 * k1] = v;
   }
+}
+
+template <class R, bool INV>
+__global__ void k_row(const FftGeom g, const Cx<R>* __restrict__ tw, const Cx<R>* __restrict__ in,
+                      Cx<R>* __restrict__ out, R scale, const unsigned* status) {
+  row_body<R, INV>(g, tw, in, out, scale, status);
+}
+
+template <class R, bool INV>
+__global__ void k_row_b(const FftGeom g, const DevFault<R>* __restrict__ fs) {
+  const DevFault<R>& f = fs[blockIdx.y];
+  row_body<R, INV>(g, f.tw, f.zt, INV ? f.y : f.Z, INV ? R(1.0 / g.N) : R(1), f.status);
 }
 
 // ---------------------------------------------------- history convolution
@@ -263,17 +291,26 @@ __device__ __forceinline__ double warp_sum(double v) {
 // mode split over several chunks is finished by the warp whose chunk
 // completes last (atomic counter per mode, no waiting): it adds the partial
 // sums in chunk order, so the result does not depend on scheduling.
-template <class R>
-__global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_dt) {
-  if (*f.status) return;  // the status word does not change while this kernel runs
+// BATCH: the chunks of an ensemble, chunk.member selects the fault in fs
+// (partial sums, counters and the work counter of fs[*] are the ensemble's).
+template <class R, bool BATCH>
+__global__ void __launch_bounds__(kHistThreads)
+    k_history_t(const __grid_constant__ DevFault<R> f0, const DevFault<R>* __restrict__ fs,
+                const Chunk* __restrict__ chunks, int nchunks, int* work, int m_dt) {
+  if (!BATCH && *f0.status) return;  // the status word does not change while this kernel runs
   constexpr int U = HistCfg<R>::kUnroll;
   const int lane = threadIdx.x & 31;
   // chunks are handed out dynamically (counter zeroed before the launch)
   int c = 0;
-  if (lane == 0) c = atomicAdd(f.work, 1);
+  if (lane == 0) c = atomicAdd(work, 1);
   c = __shfl_sync(0xffffffffu, c, 0);
-  for (; c < f.nchunks; c = __shfl_sync(0xffffffffu, c, 0)) {
-    const Chunk cd = f.chunks[c];
+  for (; c < nchunks; c = __shfl_sync(0xffffffffu, c, 0)) {
+    const Chunk cd = chunks[c];
+    const DevFault<R>& f = BATCH ? fs[cd.pad] : f0;
+    if (BATCH && *f.status) {
+      if (lane == 0) c = atomicAdd(work, 1);
+      continue;
+    }
     const int n = cd.mode;
     const int Rn = f.Rn[n];
     const int h = f.head[n];
@@ -300,7 +337,7 @@ __global__ void __launch_bounds__(kHistThreads) k_history(DevFault<R> f, int m_d
     }
     double4 v = make_double4(warp_sum(acc.tr), warp_sum(acc.ti), warp_sum(acc.nr), warp_sum(acc.ni));
     const int cur = c;
-    if (lane == 0) c = atomicAdd(f.work, 1);
+    if (lane == 0) c = atomicAdd(work, 1);
     if (cd.count == 1) {
       if (lane == 0) {
         f.AT[n] = make_double2(v.x, v.y);
@@ -379,7 +416,7 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
 }
 
 template <class R>
-__global__ void __launch_bounds__(32) k_newton(DevFault<R> f, int pass, double dt) {
+__device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   // one read of the status word per block: other blocks may set it while
   // this one runs, and the decision must be uniform across __syncwarp
@@ -459,9 +496,20 @@ __global__ void __launch_bounds__(32) k_newton(DevFault<R> f, int pass, double d
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(32) k_newton(const __grid_constant__ DevFault<R> f, int pass, double dt) {
+  newton_body<R>(f, pass, dt);
+}
+
+template <class R>
+__global__ void __launch_bounds__(32) k_newton_b(const DevFault<R>* __restrict__ fs, int pass, int m_dt) {
+  const DevFault<R>& f = fs[blockIdx.y];
+  newton_body<R>(f, pass, m_dt * f.dt_min);
+}
+
 // ------------------------------------------------------------- commit
 template <class R>
-__global__ void k_commit(DevFault<R> f, int m_dt, double dt) {
+__device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (*f.status) return;
   if (i < f.N) {
@@ -506,6 +554,17 @@ __global__ void k_commit(DevFault<R> f, int m_dt, double dt) {
     *f.steps_done += 1;
     *f.t += dt;
   }
+}
+
+template <class R>
+__global__ void k_commit(const __grid_constant__ DevFault<R> f, int m_dt, double dt) {
+  commit_body<R>(f, m_dt, dt);
+}
+
+template <class R>
+__global__ void k_commit_b(const DevFault<R>* __restrict__ fs, int m_dt) {
+  const DevFault<R>& f = fs[blockIdx.y];
+  commit_body<R>(f, m_dt, m_dt * f.dt_min);
 }
 
 // Push of m_dt > 1 copies of this step's spectra (a step of m_dt dt_min,
@@ -722,13 +781,50 @@ void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   const int warps = kHistThreads / 32;
   const int need = (f.nchunks + warps - 1) / warps;
   const int gr = grid < need ? grid : need;
-  k_history<R><<<gr, kHistThreads, 0, st>>>(f, m_dt);
+  k_history_t<R, false><<<gr, kHistThreads, 0, st>>>(f, nullptr, f.chunks, f.nchunks, f.work, m_dt);
+}
+
+template <class R>
+void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, int* work, int m_dt, int grid,
+                          cudaStream_t st) {
+  if (nchunks == 0) return;
+  const int warps = kHistThreads / 32;
+  const int need = (nchunks + warps - 1) / warps;
+  const int gr = grid < need ? grid : need;
+  DevFault<R> none{};
+  k_history_t<R, true><<<gr, kHistThreads, 0, st>>>(none, fs, chunks, nchunks, work, m_dt);
+}
+
+template <class R>
+void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass, int m_dt,
+                       cudaStream_t st) {
+  const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
+  const dim3 gc(g.N1 / g.Bc, members), gr(g.N2 / g.Br, members);
+  k_col_b<R, false, PRO_PASS><<<gc, g.tc, cs, st>>>(g, fs, pass, m_dt);
+  k_row_b<R, false><<<gr, g.tr, rs, st>>>(g, fs);
+  k_col_b<R, true, PRO_ASSEMBLE><<<gc, g.tc, cs, st>>>(g, fs, pass, m_dt);
+  k_row_b<R, true><<<gr, g.tr, rs, st>>>(g, fs);
+  k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);
+}
+
+template <class R>
+void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st) {
+  const int n = N;  // N > N/2 + 1 modes
+  k_commit_b<R><<<dim3((n + 255) / 256, members), 256, 0, st>>>(fs, m_dt);
+}
+
+template <class R>
+void configure_batch_kernels(const FftGeom& g) {
+  allow_smem(k_col_b<R, false, PRO_PASS>, col_smem<R>(g));
+  allow_smem(k_col_b<R, true, PRO_ASSEMBLE>, col_smem<R>(g));
+  allow_smem(k_row_b<R, false>, row_smem<R>(g));
+  allow_smem(k_row_b<R, true>, row_smem<R>(g));
 }
 
 template <class R>
 int history_blocks_per_sm() {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_history<R>, kHistThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_history_t<R, false>, kHistThreads, 0);
   return n;
 }
 
@@ -810,6 +906,14 @@ void configure_kernels(const FftGeom& g) {
   allow_smem(k_row<double, true>, row_smem<double>(g64));
 }
 
+template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, int*, int, int, cudaStream_t);
+template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, int*, int, int, cudaStream_t);
+template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
+template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
+template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t);
+template void launch_commit_batch<float>(const DevFault<float>*, int, int, int, cudaStream_t);
+template void configure_batch_kernels<double>(const FftGeom&);
+template void configure_batch_kernels<float>(const FftGeom&);
 template int history_blocks_per_sm<double>();
 template int history_blocks_per_sm<float>();
 template void configure_kernels<double>(const FftGeom&);

@@ -33,7 +33,7 @@ struct Chunk {
   int32_t mode;
   int32_t first;  // chunk index of the mode's first chunk
   int32_t count;  // chunks of this mode
-  int32_t pad;
+  int32_t pad;    // ensemble member (batched history convolution), else 0
   int64_t i0, i1;  // slot range [i0, i1) within the mode's ring
 };
 
@@ -91,6 +91,14 @@ struct DevFault {
 
 // Host launch wrappers (kernels.cu).
 template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
+// Ensemble launches: fs is a device array of member descriptors; the pass and
+// commit kernels take one member per blockIdx.y (all members of equal N).
+template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, int* work,
+                                             int m_dt, int grid, cudaStream_t st);
+template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
+                                          int m_dt, cudaStream_t st);
+template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st);
+template <class R> void configure_batch_kernels(const FftGeom& g);
 // Resident CTAs per SM of the history convolution (occupancy calculator).
 template <class R> int history_blocks_per_sm();
 template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);

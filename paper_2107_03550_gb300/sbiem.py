@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Fault", "SbiemError", "kernel_values", "history_sums_noalloc", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
+__all__ = ["Fault", "Batch", "SbiemError", "kernel_values", "history_sums_noalloc", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
            "FLAG_STATE", "ERR"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -79,6 +79,13 @@ _SIGS = {
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
     "sbiem_history_sums_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP,
                                                   _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sbiem_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int64]),
+    "sbiem_batch_destroy": (None, [_VP]),
+    "sbiem_batch_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "sbiem_batch_enqueue": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "sbiem_batch_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _I64]),
+    "sbiem_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
     "sbiem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sbiem_last_error": (ctypes.c_char_p, []),
@@ -354,3 +361,54 @@ class Fault:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """An ensemble of Fault handles advanced together (batched launches, one graph per step)."""
+
+    def __init__(self, members, chunk_slots: int = 0, lib=None):
+        self.lib = lib or load_library()
+        self.members = list(members)
+        arr = (_VP * len(self.members))(*[m.h for m in self.members])
+        h = _VP()
+        rc = self.lib.sbiem_batch_create(ctypes.byref(h), len(self.members), arr, int(chunk_slots))
+        if rc != 0:
+            raise SbiemError(rc, self.lib.sbiem_last_error().decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise SbiemError(rc, self.lib.sbiem_last_error().decode())
+
+    def set_stream(self, stream) -> None:
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.sbiem_batch_set_stream(self.h, _VP(raw or None)))
+
+    def enqueue(self, nsteps: int) -> None:
+        self._check(self.lib.sbiem_batch_enqueue(self.h, int(nsteps)))
+
+    def status(self):
+        n = len(self.members)
+        fl = (ctypes.c_uint32 * n)()
+        sd = np.zeros(n, dtype=np.int64)
+        self._check(self.lib.sbiem_batch_status(self.h, fl, sd.ctypes.data_as(_I64)))
+        return np.array(list(fl), dtype=np.uint32), sd
+
+    def tune(self, reps: int = 5):
+        """Autotune chunk length and resident CTAs of the batched history convolution."""
+        c = ctypes.c_int64()
+        b = ctypes.c_int()
+        ms = ctypes.c_float()
+        self._check(self.lib.sbiem_batch_tune(self.h, int(reps), ctypes.byref(c), ctypes.byref(b), ctypes.byref(ms)))
+        return int(c.value), int(b.value), float(ms.value)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.sbiem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,75 @@
+"""Ensembles (uneven N) in batched launches vs the same faults stepped one by
+one, and vs the FP64 oracle for one member."""
+import numpy as np
+import pytest
+
+from paper_2107_03550_gb300.workloads import rough_fault
+from tests.gpu_helpers import compare, gpu_for, oracle_for, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _ensemble(seed0=100):
+    rng = np.random.default_rng(seed0)
+    out = []
+    for k, N in enumerate((256, 512, 256, 1024, 512, 256)):
+        out.append(rough_fault(N, 10.0, float(rng.uniform(1e-3, 1e-2)), seed=seed0 + k))
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+def test_batch_equals_individual_steps(precision, tol):
+    from paper_2107_03550_gb300.sbiem import Batch
+    ws = _ensemble()
+    solo = [gpu_for(w, precision=precision) for w in ws]
+    mem = [gpu_for(w, precision=precision) for w in ws]
+    b = Batch(mem)
+    steps = 40
+    b.enqueue(steps)
+    fl, sd = b.status()
+    assert np.all(fl == 0) and np.all(sd == steps)
+    for g in solo:
+        g.enqueue(steps)
+        assert g.status()[0] == 0
+    for g1, g2 in zip(solo, mem):
+        s1, s2 = g1.get_state(), g2.get_state()
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert rel(s2[k], s1[k]) <= tol, k
+    b.close()
+
+
+def test_batch_member_matches_oracle_and_tuner_keeps_results():
+    from paper_2107_03550_gb300.sbiem import Batch
+    ws = _ensemble(200)
+    mem = [gpu_for(w) for w in ws]
+    o = oracle_for(ws[3])
+    b = Batch(mem)
+    chunk, blocks, ms = b.tune(reps=3)
+    assert chunk in (256, 512, 1024, 2048, 4096, 8192) and blocks >= 1 and ms > 0
+    b.enqueue(30)
+    for _ in range(30):
+        assert o.step() == 0
+    assert np.all(b.status()[0] == 0)
+    err = compare(o, mem[3])
+    for k in ("delta", "tau_el", "sigma_el"):
+        assert err[k] < 1e-10, (k, err)
+    b.close()
+
+
+def test_failed_member_stops_alone():
+    from paper_2107_03550_gb300.sbiem import Batch
+    ws = _ensemble(300)
+    mem = [gpu_for(w, newton_maxit=(1 if k == 2 else 50)) for k, w in enumerate(ws)]
+    b = Batch(mem)
+    b.enqueue(5)
+    fl, sd = b.status()
+    assert fl[2] != 0 and sd[2] == 0
+    assert np.all(np.delete(fl, 2) == 0) and np.all(np.delete(sd, 2) == 5)
+    b.close()
