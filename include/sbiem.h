@@ -299,6 +299,43 @@ int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps);
 int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done);
 int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* blocks_per_sm, float* ms);
 
+/* ------------------------------------------------ learned Newton initial guess
+ * A 5 -> 64 -> 64 -> 1 perceptron (GELU = x Phi(x)) predicts ln V* - ln V_prev
+ * of the friction Newton solve (Eq. momentum) from the features
+ * (ln V_prev, ln theta, tau/sigma, a, b) of an element.  Parameter vector
+ * (FP32, SBIEM_MLP_PARAMS + SBIEM_MLP_NORM values): W1[64][5], b1[64],
+ * W2[64][64], b2[64], W3[64], b3, then in_mean[5], in_std[5], out_mean,
+ * out_std (features are normalized as (f - mean)/std, the output is
+ * out_mean + out_std * y).  The deployed network runs in BF16 with FP32
+ * accumulation (warp mma.sync); its guess starts Newton only when it is
+ * finite and inside the solve's bracket, otherwise ln V_prev does, so the
+ * converged slip rates are those of plain Newton to its tolerance.
+ */
+#define SBIEM_MLP_PARAMS 4609
+#define SBIEM_MLP_NORM   12
+/* Deploy a network in the handle's Newton kernel (NULL: plain Newton). */
+int sbiem_set_mlp(sbiem_t s, const float* params);
+/* Record (features, converged ln V) rows of later Newton solves into a device
+ * buffer of capacity rows (0 disables); rows beyond capacity are dropped. */
+int sbiem_harvest_enable(sbiem_t s, int64_t capacity);
+/* Copy up to max_rows harvested rows of 6 floats (ln V_prev, ln theta,
+ * tau/sigma, a, b, ln V*) to rows_out; *rows = rows stored; reset != 0
+ * restarts the buffer. */
+int sbiem_harvest_read(sbiem_t s, float* rows_out, int64_t max_rows, int64_t* rows, int reset);
+/* Network evaluation on the GPU for n raw feature rows X[n][5] (host) ->
+ * out[n] predicted residuals (host).  Allocates its own device buffers. */
+int sbiem_mlp_predict(const float* params, const float* X, int64_t n, float* out);
+/* Mean-squared-error loss over normalized inputs X[n][5] and targets t[n]
+ * and its gradient with respect to the SBIEM_MLP_PARAMS weights (FP32, own
+ * forward / backward kernels, fixed-order reduction). */
+int sbiem_mlp_grad(const float* params, const float* X, const float* t, int64_t n, float* grad, float* loss);
+/* Train on n harvested rows (host, 6 floats each): normalization from the
+ * data, seeded initialization, Adam (lr) on shuffled batches for `epochs`
+ * passes, all on the GPU; writes SBIEM_MLP_PARAMS + SBIEM_MLP_NORM values
+ * to params and the last batch's loss to *final_loss. */
+int sbiem_mlp_train(const float* samples, int64_t n, int epochs, int batch, float lr, uint64_t seed,
+                    float* params, float* final_loss);
+
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);

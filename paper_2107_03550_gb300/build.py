@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(ROOT, "_build", "sbiem")
 LIB = os.path.join(LIBDIR, "libsbiem.so")
-SOURCES = ["kernels.cu", "api.cu", "tables.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "api.cu", "tables.cpp", "noalloc.cu", "mlp.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -11,9 +12,14 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "mlp.cuh"
 #include "sbiem.h"
 
 using namespace sbiem;
+
+namespace sbiem {
+int mlp_deploy(const float* params_host, MlpDev* dst, cudaStream_t st);
+}
 
 namespace {
 
@@ -75,6 +81,10 @@ struct sbiem_s {
   void* undo = nullptr;          // ring-sized
   double* dfull = nullptr;
   double* d_err = nullptr;
+  MlpDev* mlp = nullptr;         // deployed Newton initial-guess network
+  float* harvest = nullptr;
+  unsigned long long* harvest_count = nullptr;
+  int64_t harvest_cap = 0;
 
   bool fp32() const { return p.precision == 1; }
 };
@@ -154,6 +164,17 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   f.V0 = s->p.V0;
   f.lnV0 = std::log(s->p.V0);
   f.state_law = s->p.state_law;
+  {
+    // elements per Newton warp: about two warps per SM partition, at least 4
+    int epw = 32;
+    const int parts = 4 * (s->sm_count > 0 ? s->sm_count : 1);
+    while (epw > 4 && (s->N + epw - 1) / epw < 2 * parts) epw /= 2;
+    if (const char* e = std::getenv("SBIEM_NEWTON_EPW")) {
+      const int v = std::atoi(e);
+      if (v >= 1 && v <= 32) epw = v;
+    }
+    f.newton_epw = epw;
+  }
   f.newton_maxit = s->p.newton_maxit;
   f.newton_tol = s->p.newton_tol;
 }
@@ -171,7 +192,8 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
   COPYP(chunks); COPYP(nchunks); COPYP(status); COPYP(steps_done); COPYP(t);
-  COPYP(it_sum); COPYP(it_max); COPYP(work); COPYP(w0pow);
+  COPYP(it_sum); COPYP(it_max); COPYP(work); COPYP(w0pow); COPYP(c0pow); COPYP(dhat32); COPYP(khat32);
+  COPYP(AT32); COPYP(AN32);
 #undef COPYP
   bool ok = true;
   f.ring = alloc_n<Slot<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
@@ -250,6 +272,11 @@ int snapshot(sbiem_s* s, bool save) {
                      cudaMemcpyDeviceToDevice, s->stream));
   CK(cudaMemcpyAsync(save ? s->snap_steps : f.steps_done, save ? f.steps_done : s->snap_steps, sizeof(long long),
                      cudaMemcpyDeviceToDevice, s->stream));
+  if (!save && f.dhat32) {
+    // the FP32 copies of the restored running sums
+    launch_to_float2(f.dhat, f.dhat32, s->nmodes, s->stream);
+    launch_to_float2(f.khat, f.khat32, s->nmodes, s->stream);
+  }
   return SBIEM_OK;
 }
 
@@ -276,6 +303,10 @@ int recompute_spectral_sums(sbiem_s* s) {
   launch_pack(s->N, f.delta, f.delta, f.kappa, s->u_a, s->stream);
   launch_fft64(s->g64, s->tw64, s->u_a, s->u_b, s->u_c, false, s->stream);
   launch_unpack(s->N, s->u_c, f.dhat, f.khat, s->stream);
+  if (f.dhat32) {
+    launch_to_float2(f.dhat, f.dhat32, s->nmodes, s->stream);
+    launch_to_float2(f.khat, f.khat32, s->nmodes, s->stream);
+  }
   CK(cudaGetLastError());
   return SBIEM_OK;
 }
@@ -359,15 +390,16 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   s->eta = p.mu / (2.0 * p.cs);
   windows(p, s->L, s->dt_min, s->M);
   {
-    // chunk length: about four chunks per resident warp of the history
-    // convolution, a multiple of 128 slots, within [128, 4096]
+    // chunk length: about two chunks per resident warp of the history
+    // convolution (load balance vs per-chunk reduction cost), a multiple of
+    // 128 slots, within [512, 4096]
     const int per_sm = s->fp32() ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
     int64_t tot = 0;
     for (int64_t Mn : s->M) tot += std::max<int64_t>(Mn - 1, 0);
     const int64_t warps = static_cast<int64_t>(s->hist_grid) * 8;
-    int64_t cs = (tot / (4 * warps) + 127) / 128 * 128;
-    s->chunk_slots = std::min<int64_t>(std::max<int64_t>(cs, 128), 4096);
+    int64_t cs = (tot / (2 * warps) + 127) / 128 * 128;
+    s->chunk_slots = std::min<int64_t>(std::max<int64_t>(cs, 512), 4096);
   }
   s->Rn.assign(s->nmodes, 0);
   s->ring_off.assign(s->nmodes + 1, 0);
@@ -414,6 +446,13 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   for (double2** c : carr) *c = alloc_n<double2>(s, s->nmodes, &ok);
   f.partial = alloc_n<double4>(s, std::max<size_t>(s->chunks.size(), 1), &ok);
   f.w0pow = alloc_n<double2>(s, static_cast<size_t>(s->nmodes) * kPow2Slots, &ok);
+  if (s->fp32()) {
+    f.c0pow = alloc_n<float2>(s, static_cast<size_t>(s->nmodes) * kPow2Slots, &ok);
+    f.dhat32 = alloc_n<float2>(s, s->nmodes, &ok);
+    f.khat32 = alloc_n<float2>(s, s->nmodes, &ok);
+    f.AT32 = alloc_n<float2>(s, s->nmodes, &ok);
+    f.AN32 = alloc_n<float2>(s, s->nmodes, &ok);
+  }
   f.counter = alloc_n<int>(s, s->nmodes, &ok);
   int64_t* d_roff = alloc_n<int64_t>(s, s->nmodes + 1, &ok);
   int64_t* d_woff = alloc_n<int64_t>(s, s->nmodes + 1, &ok);
@@ -923,6 +962,77 @@ int sbiem_history_enqueue(sbiem_t s, int64_t m) {
   return SBIEM_OK;
 }
 
+namespace {
+void drop_graphs(sbiem_s* s) {
+  cudaStreamSynchronize(s->stream);
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
+  s->graphs.clear();
+  s->graph_defs.clear();
+  s->pnodes.clear();
+}
+}  // namespace
+
+int sbiem_set_mlp(sbiem_t s, const float* params) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  drop_graphs(s);
+  if (!params) {
+    s->f64.mlp = nullptr;
+    s->f32.mlp = nullptr;
+    return SBIEM_OK;
+  }
+  if (!s->mlp) {
+    s->mlp = static_cast<MlpDev*>(dev_alloc(s, sizeof(MlpDev)));
+    if (!s->mlp) return fail(SBIEM_ERR_NOMEM, "network allocation failed");
+  }
+  int rc = mlp_deploy(params, s->mlp, s->stream);
+  if (rc) return fail(rc, "network upload failed");
+  s->f64.mlp = s->mlp;
+  s->f32.mlp = s->mlp;
+  return SBIEM_OK;
+}
+
+int sbiem_harvest_enable(sbiem_t s, int64_t capacity) {
+  if (!s || capacity < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
+  drop_graphs(s);
+  if (capacity == 0) {
+    s->f64.harvest = s->f32.harvest = nullptr;
+    return SBIEM_OK;
+  }
+  if (capacity > s->harvest_cap) {
+    s->harvest = static_cast<float*>(dev_alloc(s, sizeof(float) * 6 * static_cast<size_t>(capacity)));
+    if (!s->harvest_count)
+      s->harvest_count = static_cast<unsigned long long*>(dev_alloc(s, sizeof(unsigned long long)));
+    if (!s->harvest || !s->harvest_count) return fail(SBIEM_ERR_NOMEM, "harvest buffer allocation failed");
+    s->harvest_cap = capacity;
+  }
+  CK(cudaMemsetAsync(s->harvest_count, 0, sizeof(unsigned long long), s->stream));
+  for (auto* f : {&s->f64}) {
+    f->harvest = s->harvest;
+    f->harvest_count = s->harvest_count;
+    f->harvest_cap = s->harvest_cap;
+  }
+  s->f32.harvest = s->harvest;
+  s->f32.harvest_count = s->harvest_count;
+  s->f32.harvest_cap = s->harvest_cap;
+  return SBIEM_OK;
+}
+
+int sbiem_harvest_read(sbiem_t s, float* rows_out, int64_t max_rows, int64_t* rows, int reset) {
+  if (!s || max_rows < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
+  unsigned long long cnt = 0;
+  if (s->harvest_count) {
+    CK(cudaMemcpyAsync(&cnt, s->harvest_count, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  int64_t n = std::min<int64_t>(static_cast<int64_t>(std::min<unsigned long long>(cnt, s->harvest_cap)), max_rows);
+  if (rows_out && n > 0)
+    CK(cudaMemcpy(rows_out, s->harvest, sizeof(float) * 6 * n, cudaMemcpyDeviceToHost));
+  if (rows) *rows = static_cast<int64_t>(std::min<unsigned long long>(cnt, s->harvest_cap));
+  if (reset && s->harvest_count) CK(cudaMemsetAsync(s->harvest_count, 0, sizeof(unsigned long long), s->stream));
+  return SBIEM_OK;
+}
+
 int sbiem_probe_enable(sbiem_t s, int nslots) {
   if (!s || nslots < 0 || nslots > (1 << 20)) return fail(SBIEM_ERR_INVALID, "bad argument");
   CK(cudaStreamSynchronize(s->stream));
@@ -1074,6 +1184,7 @@ int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
     f.partial = b->partial;
     f.counter = b->counter + cbase[r];
     f.work = b->work;
+    f.newton_epw = 32;  // the batched Newton launch covers 32 elements per warp
     fs[r] = f;
   }
   CK(cudaMemsetAsync(b->counter, 0, sizeof(int) * cbase.back(), b->stream));

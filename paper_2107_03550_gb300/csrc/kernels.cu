@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include <math_constants.h>
 
 namespace sbiem {
 
@@ -119,12 +120,16 @@ __device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass,
       }
     }
     const double2 D = f.dhat[m], K = f.khat[m], AT = f.AT[m], AN = f.AN[m];
-    tr = -k * (f.S * (D.x + dt * U.x) + f.mu * (w0T * U.x + AT.x));
+    // the static term of the current interval and its instantaneous dynamic
+    // term nearly cancel (C(k, 0) = -(1 - r^2)): combine their coefficients
+    // first, S dt + mu w0, then multiply the spectrum
+    const double cT = f.S * dt + f.mu * w0T, cN = f.S * dt + f.mu * w0N;
+    tr = -k * (f.S * D.x + cT * U.x + f.mu * AT.x);
     // the Nyquist coefficient of a real sequence is real: keep its real part
-    ti = (m < (N >> 1)) ? -k * (f.S * (D.y + dt * U.y) + f.mu * (w0T * U.y + AT.y)) : 0.0;
+    ti = (m < (N >> 1)) ? -k * (f.S * D.y + cT * U.y + f.mu * AT.y) : 0.0;
     if (m < (N >> 1)) {
-      const double xr = f.S * (K.x + dt * Q.x) + f.mu * (w0N * Q.x + AN.x);
-      const double xi = f.S * (K.y + dt * Q.y) + f.mu * (w0N * Q.y + AN.y);
+      const double xr = f.S * K.x + cN * Q.x + f.mu * AN.x;
+      const double xi = f.S * K.y + cN * Q.y + f.mu * AN.y;
       sr = xi;   // -i (xr + i xi)
       si = -xr;
     }
@@ -202,6 +207,97 @@ template <class R, bool INV, int PRO>
 __global__ void k_col_b(const FftGeom g, const DevFault<R>* __restrict__ fs, int pass, int m_dt) {
   const DevFault<R>& f = fs[blockIdx.y];
   col_body<R, INV, PRO>(g, f.tw, nullptr, f.zt, f, pass, m_dt, m_dt * f.dt_min);
+}
+
+// Whole spectral side of one pass of the precision form (FP32 FFTs) for
+// N <= 16384 in one CTA: predictor prologue, forward FFT of Vbar + i kappa
+// Vbar, assembly of each mode pair (m, N-m) in FP32 (Sec. 3.1, Sec. 3.3 step
+// (2)), inverse FFT, scaled output tau_el + i sigma_el.  Shared memory: N
+// complex values and N/2 twiddles.
+__device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = f.N, half = N >> 1;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tw = buf + N;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  __shared__ unsigned s_skip;
+  if (tid == 0) s_skip = *f.status;
+  __syncthreads();
+  if (s_skip) return;
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  for (int j = tid; j < half; j += nth) tw[j] = f.tw[j];
+  for (int n = tid; n < N; n += nth) {
+    const double vb = (pass == 1) ? f.V[n] : 0.5 * (f.V[n] + f.V1[n]);
+    f.Vbar[n] = vb;
+    buf[n] = make_float2(static_cast<float>(vb), static_cast<float>(f.kappa[n] * vb));
+  }
+  __syncthreads();
+  fft_batch<C, false>(buf, lg, 1, tw, tid, nth);
+  const float mu = static_cast<float>(f.mu);
+  const float kf = static_cast<float>(kTwoPi / f.L);
+  const bool pow2 = (m_dt & (m_dt - 1)) == 0;
+  const int p2 = pow2 ? 31 - __clz(m_dt) : 0;
+  for (int m = tid; m <= half; m += nth) {
+    const C Zm = buf[m];
+    const C Zc = buf[(N - m) & (N - 1)];
+    const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
+    const float Qx = 0.5f * (Zm.y + Zc.y), Qy = -0.5f * (Zm.x - Zc.x);
+    float tr = 0.f, ti = 0.f, sr = 0.f, si = 0.f;
+    if (m > 0) {
+      const float k = kf * static_cast<float>(m);
+      float cT, cN;
+      if (pow2) {
+        const float2 c = f.c0pow[static_cast<size_t>(m) * kPow2Slots + p2];
+        cT = c.x;
+        cN = c.y;
+      } else {
+        double w0T = 0.0, w0N = 0.0;
+        const int lim = min(m_dt, f.Mn[m]);
+        for (int j = 0; j < lim; ++j) {
+          const W2<float> w = f.w[f.w_off[m] + j];
+          w0T += w.x;
+          w0N += w.y;
+        }
+        cT = static_cast<float>(f.S * dt + f.mu * w0T);
+        cN = static_cast<float>(f.S * dt + f.mu * w0N);
+      }
+      // S dt + mu w0 was combined in FP64 (near cancellation); FP32 products
+      const float2 D = f.dhat32[m], K = f.khat32[m], AT = f.AT32[m], AN = f.AN32[m];
+      const float S = static_cast<float>(f.S);
+      tr = -k * (S * D.x + cT * Ux + mu * AT.x);
+      ti = (m < half) ? -k * (S * D.y + cT * Uy + mu * AT.y) : 0.f;
+      if (m < half) {
+        const float xr = S * K.x + cN * Qx + mu * AN.x;
+        const float xi = S * K.y + cN * Qy + mu * AN.y;
+        sr = xi;
+        si = -xr;
+      }
+    }
+    if (pass == 2) {
+      f.U2[m] = make_double2(Ux, Uy);
+      f.Q2[m] = make_double2(Qx, Qy);
+    }
+    // Y_m = tau_m + i sig_m; Y_{N-m} = conj(tau_m) + i conj(sig_m)
+    buf[m] = make_float2(tr - si, ti + sr);
+    if (m > 0 && m < half) buf[N - m] = make_float2(tr + si, -ti + sr);
+  }
+  __syncthreads();
+  fft_batch<C, true>(buf, lg, 1, tw, tid, nth);
+  const float scale = 1.0f / static_cast<float>(N);
+  for (int n = tid; n < N; n += nth) f.y[n] = make_float2(buf[n].x * scale, buf[n].y * scale);
+}
+
+__global__ void __launch_bounds__(1024) k_spectral_fused(const __grid_constant__ DevFault<float> f, int pass,
+                                                         int m_dt, double dt) {
+  spectral_fused_body(f, pass, m_dt, dt);
+}
+
+__global__ void __launch_bounds__(1024) k_spectral_fused_b(const DevFault<float>* __restrict__ fs, int pass,
+                                                           int m_dt) {
+  const DevFault<float>& f = fs[blockIdx.x];
+  spectral_fused_body(f, pass, m_dt, m_dt * f.dt_min);
 }
 
 // Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
@@ -285,6 +381,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // One warp per chunk of consecutive slots of one mode: lanes stride over the
 // slots (each warp load is one contiguous segment), reduce with shuffles.  A
@@ -335,13 +436,20 @@ __global__ void __launch_bounds__(kHistThreads)
       for (int u = 0; u < U; ++u)
         if (i + 32 * u < iend) slot_fma(acc, sv[u], wv[u]);
     }
-    double4 v = make_double4(warp_sum(acc.tr), warp_sum(acc.ti), warp_sum(acc.nr), warp_sum(acc.ni));
+    // reduce in the accumulation precision (FP32 partial sums in the precision
+    // form), widen once per chunk for the cross-chunk sum
+    const double4 v = make_double4(static_cast<double>(warp_sum(acc.tr)), static_cast<double>(warp_sum(acc.ti)),
+                                   static_cast<double>(warp_sum(acc.nr)), static_cast<double>(warp_sum(acc.ni)));
     const int cur = c;
     if (lane == 0) c = atomicAdd(work, 1);
     if (cd.count == 1) {
       if (lane == 0) {
         f.AT[n] = make_double2(v.x, v.y);
         f.AN[n] = make_double2(v.z, v.w);
+        if (f.AT32) {
+          f.AT32[n] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+          f.AN32[n] = make_float2(static_cast<float>(v.z), static_cast<float>(v.w));
+        }
       }
       continue;
     }
@@ -367,6 +475,10 @@ __global__ void __launch_bounds__(kHistThreads)
       if (lane == 0) {
         f.AT[n] = make_double2(r.x, r.y);
         f.AN[n] = make_double2(r.z, r.w);
+        if (f.AT32) {
+          f.AT32[n] = make_float2(static_cast<float>(r.x), static_cast<float>(r.y));
+          f.AN32[n] = make_float2(static_cast<float>(r.z), static_cast<float>(r.w));
+        }
         f.counter[n] = 0;
       }
     }
@@ -382,7 +494,7 @@ __global__ void __launch_bounds__(kHistThreads)
 // radiation damping dominates (q > sigma a), bisection when a step leaves the
 // bracket.  Returns iterations (negative: not converged).
 __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, double a, double eta,
-                                          double x0, double tol, int maxit, double* xout) {
+                                          double x0, double xguess, double tol, int maxit, double* xout) {
   double hi = (tau / sig - c0) / a;
   hi = fmin(hi, 700.0);
   double d = 1.0, lo = hi - d;
@@ -392,7 +504,9 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     d *= 2.0;
     lo = hi - d;
   }
-  double x = fmin(fmax(x0, lo), hi);
+  // a learned guess is used when it is finite and inside the bracket;
+  // otherwise the previous slip rate (clamped to the bracket) starts Newton
+  double x = (isfinite(xguess) && xguess >= lo && xguess <= hi) ? xguess : fmin(fmax(x0, lo), hi);
   const double sa = sig * a;
   for (int it = 1; it <= maxit; ++it) {
     const double e = eta * exp(x);
@@ -417,53 +531,81 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
 
 template <class R>
 __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, double dt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // each warp (block) takes newton_epw elements: fewer than 32 spreads the
+  // FP64 work of small faults over more SM partitions
+  const int epw = f.newton_epw;
+  const int i = threadIdx.x < epw ? blockIdx.x * epw + threadIdx.x : f.N;
   // one read of the status word per block: other blocks may set it while
-  // this one runs, and the decision must be uniform across __syncwarp
+  // this one runs, and the decision must be uniform across the warp
   __shared__ unsigned s_skip;
   if (threadIdx.x == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
   unsigned flags = 0u;
   int iters = 0;
-  if (i < f.N) {
-    const double vb = f.Vbar[i];
-    const double Dc = f.Dc[i];
+  const bool have = i < f.N;
+  // per-element quantities of the solve (dummies on lanes without an element,
+  // which still take part in the warp-wide network evaluation)
+  double vb = 0.0, Dc = 1.0, thp = 1.0, psip = 0.0, tau = 0.0, sig = 1.0, xstart = 0.0, a = 0.01, c0 = 0.0;
+  bool solve = false;
+  if (have) {
+    vb = f.Vbar[i];
+    Dc = f.Dc[i];
     const double psi0 = f.psi[i];
-    double thp, psip;
     if (f.state_law == 0) {
       // aging law integrated at constant Vbar: theta e^{-u} + dt (1 - e^{-u})/u
       const double u = vb * dt / Dc;
       const double phi = (u > 0.0) ? -expm1(-u) / u : 1.0;
       thp = exp(psi0 - u) + dt * phi;
-      psip = log(thp);
     } else {
       const double thdb = (pass == 1) ? f.thd[i] : 0.5 * (f.thd[i] + f.thd1[i]);
       thp = exp(psi0) + thdb * dt;
       if (!(thp > 0.0)) flags |= SBIEM_FLAG_STATE;
-      psip = log(thp);
     }
+    psip = log(thp);
     const double t_end = *f.t + dt;
     const Cx<R> y = f.y[i];
-    const double tau = f.tau0[i] + f.taur[i] * t_end + static_cast<double>(y.x);
-    const double sig = f.sig0[i] + static_cast<double>(y.y);
+    tau = f.tau0[i] + f.taur[i] * t_end + static_cast<double>(y.x);
+    sig = f.sig0[i] + static_cast<double>(y.y);
+    xstart = (pass == 1) ? f.xV[i] : f.x1[i];
+    if (!f.presc[i]) {
+      if (!(sig > 0.0)) flags |= SBIEM_FLAG_OPENING;
+      solve = flags == 0u;
+      a = f.a[i];
+      // f0 + a (x - ln V0) + b ln(theta V0 / Dc) = c0 + a x
+      c0 = f.f0 + f.b[i] * (psip + f.lvd[i]) - a * f.lnV0;
+    }
+  }
+  double xguess = CUDART_NAN;
+  if (f.mlp) {
+    const float feat[kMlpIn] = {static_cast<float>(xstart), static_cast<float>(psip),
+                                static_cast<float>(tau / sig), static_cast<float>(a),
+                                static_cast<float>(have ? f.b[i] : 0.015)};
+    xguess = xstart + static_cast<double>(mlp_residual_warp(*f.mlp, feat));
+  }
+  if (have) {
     double x;
     if (f.presc[i]) {
       const double vp = f.Vp[i];
       x = vp > 0.0 ? log(vp) : -745.0;
-    } else if (!(sig > 0.0)) {
-      flags |= SBIEM_FLAG_OPENING;
-      x = f.xV[i];
-    } else if (flags) {
+    } else if (!solve) {
       x = f.xV[i];
     } else {
-      const double a = f.a[i];
-      // f0 + a (x - ln V0) + b ln(theta V0 / Dc) = c0 + a x
-      const double c0 = f.f0 + f.b[i] * (psip + f.lvd[i]) - a * f.lnV0;
-      const double xstart = (pass == 1) ? f.xV[i] : f.x1[i];
-      const int it = solve_lnV(tau, sig, c0, a, f.eta, xstart, f.newton_tol, f.newton_maxit, &x);
+      const int it = solve_lnV(tau, sig, c0, a, f.eta, xstart, xguess, f.newton_tol, f.newton_maxit, &x);
       if (it < 0) flags |= SBIEM_FLAG_NEWTON;
       iters = it < 0 ? -it : it;
+      if (it > 0 && f.harvest) {
+        const unsigned long long k = atomicAdd(f.harvest_count, 1ull);
+        if (k < static_cast<unsigned long long>(f.harvest_cap)) {
+          float* row = f.harvest + 6 * k;
+          row[0] = static_cast<float>(xstart);
+          row[1] = static_cast<float>(psip);
+          row[2] = static_cast<float>(tau / sig);
+          row[3] = static_cast<float>(a);
+          row[4] = static_cast<float>(f.b[i]);
+          row[5] = static_cast<float>(x);
+        }
+      }
     }
     const double Vn = f.presc[i] ? f.Vp[i] : exp(x);
     const double thd_new = 1.0 - thp * Vn / Dc;
@@ -528,6 +670,10 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
     K.y += dt * Q.y;
     f.dhat[i] = D;
     f.khat[i] = K;
+    if (f.dhat32) {
+      f.dhat32[i] = make_float2(static_cast<float>(D.x), static_cast<float>(D.y));
+      f.khat32[i] = make_float2(static_cast<float>(K.x), static_cast<float>(K.y));
+    }
     const int Rn = f.Rn[i];
     if (Rn > 0) {
       Slot<R> s;
@@ -601,22 +747,47 @@ __global__ void k_push_multi(DevFault<R> f, int m_dt) {
 }
 
 // w0pow[n][p] = sum_{j < min(2^p, M_n)} w_{n,j} (FP64, both fields): the
-// weight of a current interval of 2^p dt_min.
+// weight of a current interval of 2^p dt_min.  One block per mode; segment
+// [2^(p-1), 2^p) summed by a fixed-order block reduction, so the result does
+// not depend on scheduling.
 template <class R>
-__global__ void k_weight_pow2(const W2<R>* w, const int64_t* w_off, const int32_t* Mn, int nmodes, double2* out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_weight_pow2(const W2<R>* w, const int64_t* w_off, const int32_t* Mn, int nmodes, double2* out,
+                              float2* c0, double S, double mu, double dt_min) {
+  __shared__ double shT[32], shN[32];
+  const int n = blockIdx.x;
   if (n >= nmodes) return;
   const int M = Mn[n];
   const W2<R>* wn = w + w_off[n];
-  double sT = 0.0, sN = 0.0;
-  int j = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double run_T = 0.0, run_N = 0.0;
   for (int p = 0; p < kPow2Slots; ++p) {
-    const int64_t lim = min(static_cast<int64_t>(1) << p, static_cast<int64_t>(M));
-    for (; j < lim; ++j) {
+    const int64_t lo = p == 0 ? 0 : (static_cast<int64_t>(1) << (p - 1));
+    const int64_t hi = min(static_cast<int64_t>(1) << p, static_cast<int64_t>(M));
+    double sT = 0.0, sN = 0.0;
+    for (int64_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
       sT += static_cast<double>(wn[j].x);
       sN += static_cast<double>(wn[j].y);
     }
-    out[static_cast<size_t>(n) * kPow2Slots + p] = make_double2(sT, sN);
+    sT = warp_sum(sT);
+    sN = warp_sum(sN);
+    if (lane == 0) {
+      shT[wid] = sT;
+      shN[wid] = sN;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < nw; ++q) {
+        run_T += shT[q];
+        run_N += shN[q];
+      }
+      out[static_cast<size_t>(n) * kPow2Slots + p] = make_double2(run_T, run_N);
+      if (c0) {
+        const double sdt = S * dt_min * static_cast<double>(static_cast<int64_t>(1) << p);
+        c0[static_cast<size_t>(n) * kPow2Slots + p] =
+            make_float2(static_cast<float>(sdt + mu * run_T), static_cast<float>(sdt + mu * run_N));
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -758,10 +929,21 @@ static void allow_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
 }
 
+constexpr int kFusedMaxN = 8192;
+
+static size_t fused_smem(int N) { return static_cast<size_t>(N + N / 2) * sizeof(float2); }
+
 template <class R>
 void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   const FftGeom& g = f.g;
   const double dt = m_dt * f.dt_min;
+  if constexpr (sizeof(R) == 4) {
+    if (f.N <= kFusedMaxN) {
+      k_spectral_fused<<<1, 1024, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
+      k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
+      return;
+    }
+  }
   const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
   auto kfa = k_col<R, false, PRO_PASS>;
   auto kfb = k_row<R, false>;
@@ -771,8 +953,7 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   kfb<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.Z, R(1), f.status);
   kia<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
   kib<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.y, R(1.0 / g.N), f.status);
-  const int nt = 32;
-  k_newton<R><<<(f.N + nt - 1) / nt, nt, 0, st>>>(f, pass, dt);
+  k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
 }
 
 template <class R>
@@ -798,13 +979,20 @@ void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunk
 template <class R>
 void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass, int m_dt,
                        cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (N <= kFusedMaxN) {
+      k_spectral_fused_b<<<members, 1024, fused_smem(N), st>>>(fs, pass, m_dt);
+      k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);
+      return;
+    }
+  }
   const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
   const dim3 gc(g.N1 / g.Bc, members), gr(g.N2 / g.Br, members);
   k_col_b<R, false, PRO_PASS><<<gc, g.tc, cs, st>>>(g, fs, pass, m_dt);
   k_row_b<R, false><<<gr, g.tr, rs, st>>>(g, fs);
   k_col_b<R, true, PRO_ASSEMBLE><<<gc, g.tc, cs, st>>>(g, fs, pass, m_dt);
   k_row_b<R, true><<<gr, g.tr, rs, st>>>(g, fs);
-  k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);
+  k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);  // members use 32 per warp
 }
 
 template <class R>
@@ -815,6 +1003,9 @@ void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cu
 
 template <class R>
 void configure_batch_kernels(const FftGeom& g) {
+  if constexpr (sizeof(R) == 4) {
+    if (g.N <= kFusedMaxN) allow_smem(k_spectral_fused_b, fused_smem(g.N));
+  }
   allow_smem(k_col_b<R, false, PRO_PASS>, col_smem<R>(g));
   allow_smem(k_col_b<R, true, PRO_ASSEMBLE>, col_smem<R>(g));
   allow_smem(k_row_b<R, false>, row_smem<R>(g));
@@ -837,7 +1028,7 @@ void launch_push_multi(const DevFault<R>& f, int m_dt, cudaStream_t st) {
 
 template <class R>
 void launch_weight_pow2(const DevFault<R>& f, cudaStream_t st) {
-  k_weight_pow2<R><<<(f.nmodes + 127) / 128, 128, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.w0pow);
+  k_weight_pow2<R><<<f.nmodes, 256, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.w0pow, f.c0pow, f.S, f.mu, f.dt_min);
 }
 
 template <class R>
@@ -845,6 +1036,15 @@ void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaS
   if (f.nchunks == 0) return;
   const int grid = f.nchunks < 4096 ? f.nchunks : 4096;
   k_ring_undo<R><<<grid, 256, 0, st>>>(f, m_dt, static_cast<Slot<R>*>(undo), dir);
+}
+
+__global__ void k_to_float2(const double2* a, float2* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2(static_cast<float>(a[i].x), static_cast<float>(a[i].y));
+}
+
+void launch_to_float2(const double2* a, float2* out, int n, cudaStream_t st) {
+  k_to_float2<<<(n + 255) / 256, 256, 0, st>>>(a, out, n);
 }
 
 void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st) {
@@ -894,6 +1094,9 @@ void launch_real_part(int N, const double2* z, double* x, cudaStream_t st) {
 
 template <class R>
 void configure_kernels(const FftGeom& g) {
+  if constexpr (sizeof(R) == 4) {
+    if (g.N <= kFusedMaxN) allow_smem(k_spectral_fused, fused_smem(g.N));
+  }
   const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
   allow_smem(k_col<R, false, PRO_PASS>, cs);
   allow_smem(k_col<R, true, PRO_ASSEMBLE>, cs);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "mlp.cuh"
 #include "sbiem.h"
 
 namespace sbiem {
@@ -50,6 +51,7 @@ struct DevFault {
   int nmodes;          // N/2 + 1
   double L, S, mu, eta, dt_min, f0, V0, lnV0;
   int state_law;
+  int newton_epw;                          // elements per Newton warp (1..32)
   int newton_maxit;
   double newton_tol;
   // element state (FP64)
@@ -71,6 +73,8 @@ struct DevFault {
   Slot<R>* ring;
   W2<R>* w;
   double2* w0pow;                          // [mode][p]: sum of the first 2^p weights
+  float2* c0pow;                           // [mode][p]: S 2^p dt_min + mu w0 (T, N), FP32 form
+  float2 *dhat32, *khat32, *AT32, *AN32;   // FP32 copies for the fused FP32 spectral kernel
   const int64_t *ring_off, *w_off;
   const int32_t *Rn, *Mn;
   int32_t* head;
@@ -86,6 +90,10 @@ struct DevFault {
   double* t;
   unsigned long long* it_sum;
   int* it_max;
+  const MlpDev* mlp;                       // Newton initial-guess network (NULL: off)
+  float* harvest;                          // rows (ln V_prev, ln theta, tau/sigma, a, b, ln V*)
+  unsigned long long* harvest_count;
+  long long harvest_cap;
   int* work;                               // next chunk of the history convolution
 };
 
@@ -105,8 +113,10 @@ template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cu
 template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st);
 // Multi-slot history push for steps of m_dt > 1 (before launch_commit).
 template <class R> void launch_push_multi(const DevFault<R>& f, int m_dt, cudaStream_t st);
-// Fill f.w0pow from the weights.
+// Fill f.w0pow from the weights (and f.c0pow when present).
 template <class R> void launch_weight_pow2(const DevFault<R>& f, cudaStream_t st);
+// FP32 copies of the spectral running sums (after they are recomputed).
+void launch_to_float2(const double2* a, float2* out, int n, cudaStream_t st);
 // Save (dir 0) / restore (dir 1) the ring slots a push of m_dt copies overwrites.
 template <class R> void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaStream_t st);
 // *out = max_i |a_i - b_i|.

@@ -14,7 +14,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Fault", "Batch", "SbiemError", "kernel_values", "history_sums_noalloc", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
+__all__ = ["Fault", "Batch", "SbiemError", "mlp_predict", "mlp_grad", "mlp_train", "kernel_values", "history_sums_noalloc", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
            "FLAG_STATE", "ERR"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -86,6 +86,17 @@ _SIGS = {
     "sbiem_batch_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _I64]),
     "sbiem_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
+    "sbiem_set_mlp": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "sbiem_harvest_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "sbiem_harvest_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _I64, ctypes.c_int]),
+    "sbiem_mlp_predict": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_float)]),
+    "sbiem_mlp_grad": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "sbiem_mlp_train": (ctypes.c_int, [ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_float)]),
     "sbiem_kernel_values": (ctypes.c_int, [_D, ctypes.c_int64, ctypes.c_double, _D, _D]),
     "sbiem_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sbiem_last_error": (ctypes.c_char_p, []),
@@ -170,6 +181,58 @@ def history_sums_noalloc(nmodes: int, precision: int, m: int, ring: int, weights
                                         head, AT, AN, raw or None)
     if rc != 0:
         raise SbiemError(rc, "history_sums_noalloc: invalid sizes or CUDA failure")
+
+
+MLP_PARAMS, MLP_NORM = 4609, 12
+_F = ctypes.POINTER(ctypes.c_float)
+
+
+def _f32(a, n=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    return arr, arr.ctypes.data_as(_F)
+
+
+def mlp_predict(params, X) -> np.ndarray:
+    """Evaluate the Newton-guess network on the GPU: X [n, 5] raw features -> residuals [n]."""
+    lib = load_library()
+    p, pp = _f32(params, MLP_PARAMS + MLP_NORM)
+    x, xp = _f32(X)
+    n = x.size // 5
+    out = np.empty(n, dtype=np.float32)
+    rc = lib.sbiem_mlp_predict(pp, xp, n, out.ctypes.data_as(_F))
+    if rc != 0:
+        raise SbiemError(rc, "mlp_predict failed")
+    return out
+
+
+def mlp_grad(params, X, t):
+    """(loss, gradient) of the mean squared error on normalized X [n, 5], targets t [n]."""
+    lib = load_library()
+    p, pp = _f32(params)
+    x, xp = _f32(X)
+    tt, tp = _f32(t)
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    rc = lib.sbiem_mlp_grad(pp, xp, tp, tt.size, g.ctypes.data_as(_F), ctypes.byref(loss))
+    if rc != 0:
+        raise SbiemError(rc, "mlp_grad failed")
+    return float(loss.value), g
+
+
+def mlp_train(samples, epochs=5, batch=8192, lr=1e-3, seed=0):
+    """Train on harvested rows [n, 6]; returns (params [4621], final batch loss)."""
+    lib = load_library()
+    s, sp = _f32(samples)
+    n = s.size // 6
+    params = np.empty(MLP_PARAMS + MLP_NORM, dtype=np.float32)
+    loss = ctypes.c_float()
+    rc = lib.sbiem_mlp_train(sp, n, int(epochs), int(batch), float(lr), int(seed), params.ctypes.data_as(_F),
+                             ctypes.byref(loss))
+    if rc != 0:
+        raise SbiemError(rc, "mlp_train failed")
+    return params, float(loss.value)
 
 
 class Fault:
@@ -332,6 +395,26 @@ class Fault:
         b = ctypes.c_float()
         self._check(self.lib.sbiem_probe_read(self.h, int(slot), ctypes.byref(a), ctypes.byref(b)))
         return float(a.value), float(b.value)
+
+    def set_mlp(self, params) -> None:
+        """Deploy a Newton initial-guess network (None: plain Newton)."""
+        if params is None:
+            self._check(self.lib.sbiem_set_mlp(self.h, None))
+            return
+        p, pp = _f32(params, MLP_PARAMS + MLP_NORM)
+        self._check(self.lib.sbiem_set_mlp(self.h, pp))
+
+    def harvest_enable(self, capacity: int) -> None:
+        self._check(self.lib.sbiem_harvest_enable(self.h, int(capacity)))
+
+    def harvest_read(self, reset: bool = False) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.sbiem_harvest_read(self.h, None, 0, ctypes.byref(n), 0))
+        out = np.empty((n.value, 6), dtype=np.float32)
+        m = ctypes.c_int64()
+        self._check(self.lib.sbiem_harvest_read(self.h, out.ctypes.data_as(_F), n.value, ctypes.byref(m),
+                                                int(reset)))
+        return out
 
     def newton_stats(self):
         s = ctypes.c_int64()

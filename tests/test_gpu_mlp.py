@@ -1,0 +1,106 @@
+"""Learned Newton initial guess: GPU training gradients vs the FP64 oracle,
+GPU inference vs a BF16 emulation of the same network, and the harvested /
+trained / deployed network on a rupture (fewer Newton iterations, same
+converged slip rates)."""
+import numpy as np
+import pytest
+
+from oracle.mlp import N_PARAMS, forward, loss_and_grad
+from paper_2107_03550_gb300.workloads import seamount_rupture
+from tests.gpu_helpers import gpu_for, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _random_params(rng, scale=0.3):
+    return rng.normal(0, scale, N_PARAMS)
+
+
+def test_training_gradient_matches_oracle():
+    from paper_2107_03550_gb300.sbiem import mlp_grad
+    rng = np.random.default_rng(1)
+    theta = _random_params(rng)
+    X = rng.normal(0, 1, (1000, 5))
+    t = rng.normal(0, 1, 1000)
+    loss_g, g = mlp_grad(theta.astype(np.float32), X.astype(np.float32), t.astype(np.float32))
+    loss_o, g_o = loss_and_grad(theta.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64),
+                                t.astype(np.float32).astype(np.float64))
+    assert abs(loss_g - loss_o) <= 1e-5 * loss_o
+    assert np.abs(g - g_o).max() <= 1e-4 * np.abs(g_o).max()
+
+
+def _bf16(x):
+    """Round FP32 values to BF16 (round to nearest even), back to FP32."""
+    a = np.asarray(x, dtype=np.float32).copy()
+    u = a.view(np.uint32)
+    u += 0x7FFF + ((u >> 16) & 1)
+    u &= 0xFFFF0000
+    return a
+
+
+def test_inference_matches_bf16_emulation():
+    from paper_2107_03550_gb300.sbiem import mlp_predict
+    rng = np.random.default_rng(2)
+    theta = _random_params(rng, 0.2).astype(np.float32)
+    norm = np.array([-10, 5, 0.6, 0.01, 0.015, 3, 4, 0.05, 0.005, 0.004, 0.1, 0.5], dtype=np.float32)
+    params = np.concatenate([theta, norm])
+    X = np.stack([rng.uniform(-25, 2, 300), rng.uniform(-5, 15, 300), rng.uniform(0.5, 0.7, 300),
+                  rng.uniform(0.005, 0.02, 300), rng.uniform(0.01, 0.02, 300)], axis=1).astype(np.float32)
+    y = mlp_predict(params, X)
+    # emulation: inputs, W1, W2 and the first hidden layer rounded to BF16
+    from scipy import special
+    xn = (X - norm[:5]) / norm[5:10]
+    W1 = _bf16(theta[:320]).reshape(64, 5).astype(np.float64)
+    b1 = theta[320:384].astype(np.float64)
+    W2 = _bf16(theta[384:4480]).reshape(64, 64).astype(np.float64)
+    b2 = theta[4480:4544].astype(np.float64)
+    W3 = theta[4544:4608].astype(np.float64)
+    b3 = float(theta[4608])
+    gelu = lambda z: 0.5 * z * (1 + special.erf(z / np.sqrt(2)))
+    h1 = _bf16(gelu(_bf16(xn).astype(np.float64) @ W1.T + b1)).astype(np.float64)
+    h2 = gelu(h1 @ W2.T + b2)
+    ref = norm[10] + norm[11] * (h2 @ W3 + b3)
+    assert np.abs(y - ref).max() <= 2e-3 * max(1.0, np.abs(ref).max())
+    # and close to the FP64 network itself (BF16 rounding only)
+    y64, _ = forward(theta.astype(np.float64), xn.astype(np.float64))
+    assert np.abs(y - (norm[10] + norm[11] * y64)).max() <= 0.05 * max(1.0, np.abs(ref).max())
+
+
+def test_harvest_train_deploy_on_rupture():
+    from paper_2107_03550_gb300.sbiem import mlp_train
+    w = seamount_rupture()
+    # harvest (features, converged ln V) from the method's own run
+    g = gpu_for(w)
+    g.harvest_enable(2_000_000)
+    for _ in range(1300):
+        g.step()
+    rows = g.harvest_read()
+    g.close()
+    assert rows.shape[0] > 100_000 and np.all(np.isfinite(rows))
+    params, loss = mlp_train(rows, epochs=20, batch=4096, lr=2e-3, seed=3)
+    assert np.isfinite(loss) and loss < 0.5
+    # deploy: same workload, with and without the learned guess, side by side
+    plain = gpu_for(w)
+    guided = gpu_for(w)
+    guided.set_mlp(params)
+    it_plain = it_guided = 0
+    worst = 0.0
+    for s in range(1300):
+        plain.step()
+        guided.step()
+        it_plain += plain.newton_stats()[0]
+        it_guided += guided.newton_stats()[0]
+        if s % 50 == 49 and s < 1000:
+            a, b = plain.get_state(), guided.get_state()
+            worst = max(worst, rel(b["V"], a["V"]), rel(b["delta"], a["delta"]))
+    assert worst < 1e-9, worst
+    assert it_guided < 0.85 * it_plain, (it_guided, it_plain)
+    plain.close()
+    guided.close()
