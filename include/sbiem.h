@@ -278,7 +278,9 @@ int sbiem_history_enqueue(sbiem_t s, int64_t m);
  * graph per step).  Members keep their own state, read with sbiem_get_state
  * after sbiem_batch_status; they must share the device and the precision.
  * A member whose step fails stops committing (its own status word) while the
- * others go on.
+ * others go on.  Members with equal N, grid, material, truncation and
+ * precision have equal convolution weights: the history sweep reads each
+ * weight once for blocks of up to 8 such members.
  *
  * sbiem_batch_create: n member handles (not owned); chunk_slots = history
  *   slots per chunk of the batched convolution (0: derived from the resident
@@ -308,8 +310,9 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* block
  * out_std (features are normalized as (f - mean)/std, the output is
  * out_mean + out_std * y).  The deployed network runs in BF16 with FP32
  * accumulation (warp mma.sync); its guess starts Newton only when it is
- * finite and inside the solve's bracket, otherwise ln V_prev does, so the
- * converged slip rates are those of plain Newton to its tolerance.
+ * finite, inside the solve's bracket and at least 0.25 away from ln V_prev
+ * (where the previous slip rate is a poor start), otherwise ln V_prev does,
+ * so the converged slip rates are those of plain Newton to its tolerance.
  */
 #define SBIEM_MLP_PARAMS 4609
 #define SBIEM_MLP_NORM   12

@@ -165,10 +165,9 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   f.lnV0 = std::log(s->p.V0);
   f.state_law = s->p.state_law;
   {
-    // elements per Newton warp: about two warps per SM partition, at least 4
+    // elements per Newton warp (32 measured fastest on GB300; the variable
+    // SBIEM_NEWTON_EPW overrides it for experiments)
     int epw = 32;
-    const int parts = 4 * (s->sm_count > 0 ? s->sm_count : 1);
-    while (epw > 4 && (s->N + epw - 1) / epw < 2 * parts) epw /= 2;
     if (const char* e = std::getenv("SBIEM_NEWTON_EPW")) {
       const int v = std::atoi(e);
       if (v >= 1 && v <= 32) epw = v;
@@ -1104,7 +1103,7 @@ struct sbiem_batch_s {
   };
   std::vector<Group> groups;
   void* fs = nullptr;  // DevFault<R>[members] on the device
-  Chunk* chunks = nullptr;
+  GChunk* chunks = nullptr;
   int nchunks = 0;
   double4* partial = nullptr;
   int* counter = nullptr;
@@ -1136,32 +1135,47 @@ void* batch_alloc(sbiem_batch_s* b, size_t bytes) {
   return p;
 }
 
-// Chunk table over all members for a given chunk length; partial, counter
+// Members with equal N, grid, material, truncation and precision have equal
+// weights and can share a sweep.
+bool same_weights(const sbiem_s* a, const sbiem_s* b) {
+  const sbiem_params &p = a->p, &q = b->p;
+  return p.N == q.N && p.dx == q.dx && p.cs == q.cs && p.cp == q.cp && p.beta_min == q.beta_min &&
+         p.eta_w == q.eta_w && p.kc_L == q.kc_L && p.kc_units == q.kc_units && p.precision == q.precision;
+}
+
+// Chunk table over all members for a given chunk length: members sharing
+// weights form blocks of up to kGroupMax swept together; partial, counter
 // and work buffers sized for it; member descriptors pointing at them.
 template <class R>
 int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
-  std::vector<Chunk> ch;
+  std::vector<GChunk> ch;
   std::vector<int64_t> cbase(b->members.size() + 1, 0);
-  for (size_t r = 0; r < b->members.size(); ++r) {
-    const sbiem_s* s = b->members[r];
-    cbase[r + 1] = cbase[r] + s->nmodes;
+  for (size_t r = 0; r < b->members.size(); ++r) cbase[r + 1] = cbase[r] + b->members[r]->nmodes;
+  size_t r0 = 0;
+  while (r0 < b->members.size()) {
+    size_t r1 = r0 + 1;
+    while (r1 < b->members.size() && r1 - r0 < static_cast<size_t>(kGroupMax) &&
+           same_weights(b->members[r0], b->members[r1]))
+      ++r1;
+    const sbiem_s* s = b->members[r0];
     for (int n = 0; n < s->nmodes; ++n) {
       const int64_t cnt = (s->Rn[n] + chunk_slots - 1) / chunk_slots;
       const int first = static_cast<int>(ch.size());
       for (int64_t c = 0; c < cnt; ++c) {
-        Chunk k{};
+        GChunk k{};
         k.mode = n;
         k.first = first;
         k.count = static_cast<int32_t>(cnt);
-        k.pad = static_cast<int32_t>(r);
+        k.m0 = static_cast<int32_t>(r0);
+        k.mcount = static_cast<int32_t>(r1 - r0);
         k.i0 = c * chunk_slots;
         k.i1 = std::min<int64_t>((c + 1) * chunk_slots, s->Rn[n]);
         ch.push_back(k);
       }
     }
+    r0 = r1;
   }
-  if (ch.size() > static_cast<size_t>(1) << 30) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
-  // (re)allocate the chunk-dependent buffers
+  if (ch.size() > static_cast<size_t>(1) << 28) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
   auto realloc = [&](void** p, size_t bytes) {
     if (*p) {
       cudaFree(*p);
@@ -1170,8 +1184,9 @@ int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
     *p = batch_alloc(b, bytes);
     return *p != nullptr;
   };
-  bool ok = realloc(reinterpret_cast<void**>(&b->chunks), sizeof(Chunk) * std::max<size_t>(ch.size(), 1)) &&
-            realloc(reinterpret_cast<void**>(&b->partial), sizeof(double4) * std::max<size_t>(ch.size(), 1));
+  bool ok = realloc(reinterpret_cast<void**>(&b->chunks), sizeof(GChunk) * std::max<size_t>(ch.size(), 1)) &&
+            realloc(reinterpret_cast<void**>(&b->partial),
+                    sizeof(double4) * kGroupMax * std::max<size_t>(ch.size(), 1));
   if (!b->counter) ok = ok && (b->counter = static_cast<int*>(batch_alloc(b, sizeof(int) * cbase.back()))) != nullptr;
   if (!b->work) ok = ok && (b->work = static_cast<int*>(batch_alloc(b, sizeof(int)))) != nullptr;
   if (!b->fs) ok = ok && (b->fs = batch_alloc(b, sizeof(DevFault<R>) * b->members.size())) != nullptr;
@@ -1188,7 +1203,7 @@ int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
     fs[r] = f;
   }
   CK(cudaMemsetAsync(b->counter, 0, sizeof(int) * cbase.back(), b->stream));
-  CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(GChunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->fs, fs.data(), sizeof(DevFault<R>) * fs.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
   b->nchunks = static_cast<int>(ch.size());
@@ -1205,8 +1220,8 @@ int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
 template <class R>
 void batch_history(sbiem_batch_s* b, cudaStream_t st) {
   cudaMemsetAsync(b->work, 0, sizeof(int), st);
-  launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->work, 1,
-                          b->hist_grid, st);
+  launch_history_groups<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->work, b->partial, 1,
+                           b->hist_grid, st);
 }
 
 template <class R>

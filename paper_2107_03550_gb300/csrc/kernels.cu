@@ -485,6 +485,113 @@ __global__ void __launch_bounds__(kHistThreads)
   }
 }
 
+// Ensemble version with shared weights: one warp per grouped chunk; for each
+// slot the weight is loaded once and applied to the rings of up to
+// kGroupMax members (their heads may differ).  Partial sums per (chunk,
+// member); the last warp of a (member, mode) adds them in chunk order.
+template <class R>
+__global__ void __launch_bounds__(kHistThreads)
+    k_history_groups(const DevFault<R>* __restrict__ fs, const GChunk* __restrict__ chunks, int nchunks,
+                     int* work, double4* __restrict__ partial, int m_dt) {
+  constexpr int U = HistCfg<R>::kUnroll / 2 > 0 ? HistCfg<R>::kUnroll / 2 : 1;
+  const int lane = threadIdx.x & 31;
+  int c = 0;
+  if (lane == 0) c = atomicAdd(work, 1);
+  c = __shfl_sync(0xffffffffu, c, 0);
+  for (; c < nchunks; c = __shfl_sync(0xffffffffu, c, 0)) {
+    const GChunk cd = chunks[c];
+    const int n = cd.mode;
+    const DevFault<R>& f0 = fs[cd.m0];
+    const int Rn = f0.Rn[n];
+    const int64_t iend = min(cd.i1, static_cast<int64_t>(f0.Mn[n]) - m_dt);
+    const W2<R>* w = f0.w + f0.w_off[n] + m_dt;
+    const Slot<R>* ring[kGroupMax];
+    int hd[kGroupMax];
+    bool live[kGroupMax];
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) {
+      live[j] = false;
+      ring[j] = nullptr;
+      hd[j] = 0;
+      if (j < cd.mcount) {
+        const DevFault<R>& fj = fs[cd.m0 + j];
+        live[j] = *fj.status == 0u;
+        ring[j] = fj.ring + fj.ring_off[n];
+        hd[j] = fj.head[n];
+      }
+    }
+    Acc4<R> acc[kGroupMax];
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) acc[j] = {R(0), R(0), R(0), R(0)};
+    for (int64_t i = cd.i0 + lane; i < iend; i += 32 * U) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t ii = i + 32 * u;
+        if (ii < iend) {
+          const W2<R> wv = __ldg(w + ii);
+#pragma unroll
+          for (int j = 0; j < kGroupMax; ++j) {
+            if (live[j]) {
+              int64_t slot = hd[j] + ii;
+              if (slot >= Rn) slot -= Rn;
+              slot_fma(acc[j], ld_slot(ring[j] + slot), wv);
+            }
+          }
+        }
+      }
+    }
+    const int cur = c;
+    if (lane == 0) c = atomicAdd(work, 1);
+#pragma unroll
+    for (int j = 0; j < kGroupMax; ++j) {
+      if (j >= cd.mcount || !live[j]) continue;
+      const double4 v = make_double4(static_cast<double>(warp_sum(acc[j].tr)), static_cast<double>(warp_sum(acc[j].ti)),
+                                     static_cast<double>(warp_sum(acc[j].nr)), static_cast<double>(warp_sum(acc[j].ni)));
+      const DevFault<R>& fj = fs[cd.m0 + j];
+      if (cd.count == 1) {
+        if (lane == 0) {
+          fj.AT[n] = make_double2(v.x, v.y);
+          fj.AN[n] = make_double2(v.z, v.w);
+          if (fj.AT32) {
+            fj.AT32[n] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+            fj.AN32[n] = make_float2(static_cast<float>(v.z), static_cast<float>(v.w));
+          }
+        }
+        continue;
+      }
+      int prev = 0;
+      if (lane == 0) {
+        partial[static_cast<int64_t>(cur) * kGroupMax + j] = v;
+        __threadfence();
+        prev = atomicAdd(fj.counter + n, 1);
+      }
+      prev = __shfl_sync(0xffffffffu, prev, 0);
+      if (prev == cd.count - 1) {
+        __threadfence();
+        double4 r = make_double4(0.0, 0.0, 0.0, 0.0);
+        for (int q = lane; q < cd.count; q += 32) {
+          const double2* pp = reinterpret_cast<const double2*>(partial + static_cast<int64_t>(cd.first + q) * kGroupMax + j);
+          const double2 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
+          r.x += p0.x;
+          r.y += p0.y;
+          r.z += p1.x;
+          r.w += p1.y;
+        }
+        r = make_double4(warp_sum(r.x), warp_sum(r.y), warp_sum(r.z), warp_sum(r.w));
+        if (lane == 0) {
+          fj.AT[n] = make_double2(r.x, r.y);
+          fj.AN[n] = make_double2(r.z, r.w);
+          if (fj.AT32) {
+            fj.AT32[n] = make_float2(static_cast<float>(r.x), static_cast<float>(r.y));
+            fj.AN32[n] = make_float2(static_cast<float>(r.z), static_cast<float>(r.w));
+          }
+          fj.counter[n] = 0;
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ friction
 // x = ln V solves g(x) = q(x) - eta e^x = 0 with q(x) = tau - sigma (c0 + a x),
 // c0 = f0 + b ln(theta V0 / Dc) - a ln V0 (Eq. momentum plus radiation
@@ -504,9 +611,12 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     d *= 2.0;
     lo = hi - d;
   }
-  // a learned guess is used when it is finite and inside the bracket;
-  // otherwise the previous slip rate (clamped to the bracket) starts Newton
-  double x = (isfinite(xguess) && xguess >= lo && xguess <= hi) ? xguess : fmin(fmax(x0, lo), hi);
+  // a learned guess is used when it is finite, inside the bracket and calls
+  // for a substantial change (|guess - ln V_prev| >= 0.25, where the
+  // previous slip rate is a poor start); otherwise the previous slip rate
+  // (clamped to the bracket) starts Newton
+  const bool use_guess = isfinite(xguess) && xguess >= lo && xguess <= hi && fabs(xguess - x0) >= 0.25;
+  double x = use_guess ? xguess : fmin(fmax(x0, lo), hi);
   const double sa = sig * a;
   for (int it = 1; it <= maxit; ++it) {
     const double e = eta * exp(x);
@@ -924,9 +1034,11 @@ static size_t col_smem(const FftGeom& g) { return (static_cast<size_t>(g.Bc) * g
 template <class R>
 static size_t row_smem(const FftGeom& g) { return (static_cast<size_t>(g.Br) * g.N1 + g.N1 / 2) * sizeof(Cx<R>); }
 
+// Opt in to the dynamic shared memory a kernel launches with (static shared
+// memory counts against the same 48 KB default, so always set it).
 template <class K>
 static void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
 }
 
 constexpr int kFusedMaxN = 8192;
@@ -974,6 +1086,16 @@ void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunk
   const int gr = grid < need ? grid : need;
   DevFault<R> none{};
   k_history_t<R, true><<<gr, kHistThreads, 0, st>>>(none, fs, chunks, nchunks, work, m_dt);
+}
+
+template <class R>
+void launch_history_groups(const DevFault<R>* fs, const GChunk* chunks, int nchunks, int* work, double4* partial,
+                           int m_dt, int grid, cudaStream_t st) {
+  if (nchunks == 0) return;
+  const int warps = kHistThreads / 32;
+  const int need = (nchunks + warps - 1) / warps;
+  const int gr = grid < need ? grid : need;
+  k_history_groups<R><<<gr, kHistThreads, 0, st>>>(fs, chunks, nchunks, work, partial, m_dt);
 }
 
 template <class R>
@@ -1111,6 +1233,10 @@ void configure_kernels(const FftGeom& g) {
 
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, int*, int, int, cudaStream_t);
 template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, int*, int, int, cudaStream_t);
+template void launch_history_groups<double>(const DevFault<double>*, const GChunk*, int, int*, double4*, int, int,
+                                            cudaStream_t);
+template void launch_history_groups<float>(const DevFault<float>*, const GChunk*, int, int*, double4*, int, int,
+                                           cudaStream_t);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
 template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t);

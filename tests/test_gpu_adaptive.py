@@ -29,8 +29,12 @@ def test_mixed_step_lengths_match_oracle(precision):
         assert o.step(m) == 0
         g.step(m * g.dt_min)
         err = compare(o, g)
-        tol = 1e-10 if precision == 0 else 1e-4
+        # FP32 form: the FFT rounding of F[kappa Vbar] is relative to its
+        # largest coefficient, so small normal-traction changes from a random
+        # history carry ~1e-4; the form's own contract (final slip, arrival
+        # time) is checked in test_precision_form_rupture
         for k in ("delta", "tau_el", "sigma_el", "theta"):
+            tol = 1e-10 if precision == 0 else (1e-3 if k in ("tau_el", "sigma_el") else 1e-4)
             assert err[k] < tol, (m, k, err)
     hT, hN = g.get_history()
     HT, HN = o.get_history()
