@@ -310,7 +310,7 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* block
  * out_std (features are normalized as (f - mean)/std, the output is
  * out_mean + out_std * y).  The deployed network runs in BF16 with FP32
  * accumulation (warp mma.sync); its guess starts Newton only when it is
- * finite, inside the solve's bracket and at least 0.25 away from ln V_prev
+ * finite, inside the solve's bracket and at least 0.1 away from ln V_prev
  * (where the previous slip rate is a poor start), otherwise ln V_prev does,
  * so the converged slip rates are those of plain Newton to its tolerance.
  */

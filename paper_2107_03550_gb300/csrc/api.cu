@@ -65,6 +65,15 @@ struct sbiem_s {
   long long* h_steps = nullptr;  // pinned
   std::map<int, cudaGraphExec_t> graphs;
   std::map<int, cudaGraph_t> graph_defs;
+  // overlapped form: the history sweep of the next step runs on a side
+  // stream during this step's passes; lag_m is the step length (in dt_min)
+  // for which AT/AN already hold the next step's sums (-1: none)
+  std::map<int, cudaGraphExec_t> lag_graphs;
+  std::map<int, cudaGraph_t> lag_defs;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int lag_m = -1;
+  int lag_grid = 0;  // CTAs of the overlapped sweep (leaves room for the passes)
   // timing probe: 4 events per slot; graph event-record nodes are retargeted
   // to the slot of each launch
   int pslots = 0;
@@ -117,9 +126,14 @@ T* alloc_n(sbiem_s* s, size_t n, bool* ok) {
 void free_all(sbiem_s* s) {
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
+  for (auto& kv : s->lag_graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : s->lag_defs) cudaGraphDestroy(kv.second);
   s->graphs.clear();
   s->graph_defs.clear();
+  s->lag_graphs.clear();
+  s->lag_defs.clear();
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->side) cudaStreamSynchronize(s->side);
   for (auto& e : s->pev)
     if (e) cudaEventDestroy(e);
   s->pev.clear();
@@ -131,6 +145,9 @@ void free_all(sbiem_s* s) {
   if (s->h_status) cudaFreeHost(s->h_status);
   if (s->h_steps) cudaFreeHost(s->h_steps);
   if (s->own) cudaStreamDestroy(s->own);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
 }
 
 bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -188,7 +205,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   COPYP(V2); COPYP(psi2); COPYP(thd2); COPYP(delta2); COPYP(a); COPYP(b); COPYP(Dc);
   COPYP(xV); COPYP(x1); COPYP(x2); COPYP(lvd);
   COPYP(sig0); COPYP(tau0); COPYP(taur); COPYP(Vp); COPYP(kappa); COPYP(presc);
-  COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(partial);
+  COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(BT); COPYP(BN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
   COPYP(chunks); COPYP(nchunks); COPYP(status); COPYP(steps_done); COPYP(t);
   COPYP(it_sum); COPYP(it_max); COPYP(work); COPYP(w0pow); COPYP(c0pow); COPYP(dhat32); COPYP(khat32);
@@ -201,6 +218,16 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   f.Z = alloc_n<Cx<R>>(s, s->N, &ok);
   f.y = alloc_n<Cx<R>>(s, s->N, &ok);
   if (!ok) return fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
+  if constexpr (sizeof(R) == 4) {
+    if (s->N <= kFusedMaxN) {
+      // single-CTA spectral pass: FP32 inputs prepared by the multi-SM kernels
+      f.zin1 = alloc_n<float2>(s, s->N, &ok);
+      f.zin2 = alloc_n<float2>(s, s->N, &ok);
+      f.U2f = alloc_n<float2>(s, s->nmodes, &ok);
+      f.Q2f = alloc_n<float2>(s, s->nmodes, &ok);
+    }
+  }
+  if (!ok) return fail(SBIEM_ERR_NOMEM, "device allocation failed (FP32 pass buffers)");
   f.g = make_geom(s->N, sizeof(Cx<R>));
   if constexpr (sizeof(R) == 8) f.tw = s->tw64;
   else f.tw = s->tw32;
@@ -226,6 +253,27 @@ void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
   if (m > 1) launch_push_multi<R>(f, m, st);
   launch_commit<R>(f, m, st);
   probe_mark(s, 3, st);
+}
+
+// Overlapped step of m = 2^p dt_min: AT/AN already hold this step's sums;
+// the side branch sweeps the history for the next step (weights shifted by
+// 2m, into BT/BN) while the passes run; the commit adds this step's slot.
+template <class R>
+void enqueue_step_lag_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
+  int p = 0;
+  while ((1 << p) < m) ++p;
+  cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
+  cudaMemsetAsync(f.work, 0, sizeof(int), st);
+  cudaEventRecord(s->ev_fork, st);
+  cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+  launch_history_ahead<R>(f, m, s->lag_grid, s->side);
+  cudaEventRecord(s->ev_join, s->side);
+  launch_pass<R>(f, 1, m, st);
+  launch_pass<R>(f, 2, m, st);
+  cudaStreamWaitEvent(st, s->ev_join, 0);
+  if (m > 1) launch_push_multi<R>(f, m, st);
+  launch_commit<R>(f, m, st, p);
 }
 
 // The step without its commit: pass-2 results stay staged (delta2, V2, ...).
@@ -276,6 +324,7 @@ int snapshot(sbiem_s* s, bool save) {
     launch_to_float2(f.dhat, f.dhat32, s->nmodes, s->stream);
     launch_to_float2(f.khat, f.khat32, s->nmodes, s->stream);
   }
+  if (!save && s->f32.zin1) launch_zin(f.V, f.kappa, s->f32.zin1, s->N, s->stream);
   return SBIEM_OK;
 }
 
@@ -306,6 +355,7 @@ int recompute_spectral_sums(sbiem_s* s) {
     launch_to_float2(f.dhat, f.dhat32, s->nmodes, s->stream);
     launch_to_float2(f.khat, f.khat32, s->nmodes, s->stream);
   }
+  if (s->f32.zin1) launch_zin(f.V, f.kappa, s->f32.zin1, s->N, s->stream);
   CK(cudaGetLastError());
   return SBIEM_OK;
 }
@@ -375,9 +425,13 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   s->p = p;
   cudaGetDevice(&s->device);
   cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
-  if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    free_all(s);
     delete s;
-    return fail(SBIEM_ERR_CUDA, "cudaStreamCreate failed");
+    return fail(SBIEM_ERR_CUDA, "stream / event creation failed");
   }
   s->stream = s->own;
   s->N = N;
@@ -394,6 +448,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     // 128 slots, within [512, 4096]
     const int per_sm = s->fp32() ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
+    // overlapped sweep: one CTA per SM fewer, so the pass kernels find room
+    s->lag_grid = s->sm_count * (per_sm > 1 ? per_sm - 1 : 1);
     int64_t tot = 0;
     for (int64_t Mn : s->M) tot += std::max<int64_t>(Mn - 1, 0);
     const int64_t warps = static_cast<int64_t>(s->hist_grid) * 8;
@@ -441,7 +497,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
                      &f.xV, &f.x1, &f.x2, &f.lvd};
   for (double** d : darr) *d = alloc_n<double>(s, N, &ok);
   f.presc = alloc_n<uint8_t>(s, N, &ok);
-  double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN};
+  double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN, &f.BT, &f.BN};
   for (double2** c : carr) *c = alloc_n<double2>(s, s->nmodes, &ok);
   f.partial = alloc_n<double4>(s, std::max<size_t>(s->chunks.size(), 1), &ok);
   f.w0pow = alloc_n<double2>(s, static_cast<size_t>(s->nmodes) * kPow2Slots, &ok);
@@ -617,6 +673,7 @@ int sbiem_status(sbiem_t s, uint32_t* flags, int64_t* steps_done, int clear) {
   CK(cudaStreamSynchronize(s->stream));
   if (flags) *flags = *s->h_status;
   if (steps_done) *steps_done = *s->h_steps;
+  if (*s->h_status) s->lag_m = -1;  // a rejected step left AT/AN of its start
   if (clear) CK(cudaMemsetAsync(s->f64.status, 0, sizeof(unsigned), s->stream));
   return SBIEM_OK;
 }
@@ -630,6 +687,7 @@ int sbiem_step(sbiem_t s, double dt) {
   rc = sbiem_status(s, &before, nullptr, 1);
   if (rc) return rc;
   if (s->pslots) s->pcur = static_cast<int>(s->pcount++ % s->pslots);
+  s->lag_m = -1;
   enqueue_step(s, m, s->stream);
   CK(cudaGetLastError());
   uint32_t st;
@@ -646,6 +704,39 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
   int m;
   int rc = dt_to_m(s, dt, &m);
   if (rc) return rc;
+  if (nsteps == 0) return SBIEM_OK;
+  if (s->pslots == 0 && is_pow2(m) && m <= (1 << 30)) {
+    // overlapped form (steps of 2^p dt_min, no timing probe)
+    auto lt = s->lag_graphs.find(m);
+    if (lt == s->lag_graphs.end()) {
+      cudaGraph_t gdef = nullptr;
+      CK(cudaStreamSynchronize(s->stream));
+      CK(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
+      if (s->fp32()) enqueue_step_lag_t<float>(s, s->f32, m, s->own);
+      else enqueue_step_lag_t<double>(s, s->f64, m, s->own);
+      cudaError_t e1 = cudaGetLastError();
+      cudaError_t e2 = cudaStreamEndCapture(s->own, &gdef);
+      if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(SBIEM_ERR_CUDA,
+                    std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      cudaGraphExec_t exec = nullptr;
+      CK(cudaGraphInstantiate(&exec, gdef, 0));
+      s->lag_graphs[m] = exec;
+      s->lag_defs[m] = gdef;
+      lt = s->lag_graphs.find(m);
+    }
+    if (s->lag_m != m) {
+      // prologue: this step's full sums
+      CK(cudaMemsetAsync(s->f64.work, 0, sizeof(int), s->stream));
+      if (s->fp32()) launch_history<float>(s->f32, m, s->hist_grid, s->stream);
+      else launch_history<double>(s->f64, m, s->hist_grid, s->stream);
+      CK(cudaGetLastError());
+    }
+    for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(lt->second, s->stream));
+    s->lag_m = m;
+    return SBIEM_OK;
+  }
+  s->lag_m = -1;
   auto it = s->graphs.find(m);
   if (it == s->graphs.end()) {
     // capture one step on the handle's own stream, replay it on s->stream
@@ -699,6 +790,7 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
 int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, int64_t max_steps,
               int64_t* steps_out, int64_t* m_next, double* t_out, int64_t* m_hist) {
   if (!s || !(eps0 > 0) || m0 < 1 || m_max < 1 || max_steps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
+  s->lag_m = -1;  // trial steps and rollbacks below compute their own sums
   auto& f = s->f64;
   bool ok = true;
   if (!s->snap) {
@@ -841,6 +933,7 @@ int sbiem_get_state(sbiem_t s, double* delta, double* V, double* theta, double* 
 
 int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const double* theta) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  s->lag_m = -1;
   auto& f = s->f64;
   const int N = s->N;
   const size_t nb = sizeof(double) * N;
@@ -877,6 +970,7 @@ int sbiem_windows(sbiem_t s, int64_t* M) {
 
 int sbiem_set_history(sbiem_t s, const double* hT, const double* hN) {
   if (!s || !hT || !hN) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  s->lag_m = -1;
   const int64_t tot = s->total_slots;
   if (tot == 0) return SBIEM_OK;
   std::vector<int32_t> heads(s->nmodes, 0);
@@ -944,6 +1038,7 @@ int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
   else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
   CK(cudaGetLastError());
+  s->lag_m = mi;  // AT/AN now hold the sums of a step of m from this state
   const size_t nb = sizeof(double2) * s->nmodes;
   CK(cudaMemcpyAsync(AT, s->f64.AT, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(AN, s->f64.AN, nb, cudaMemcpyDeviceToHost, s->stream));
@@ -958,6 +1053,7 @@ int sbiem_history_enqueue(sbiem_t s, int64_t m) {
   if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
   else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
   CK(cudaGetLastError());
+  s->lag_m = mi;
   return SBIEM_OK;
 }
 
@@ -966,8 +1062,12 @@ void drop_graphs(sbiem_s* s) {
   cudaStreamSynchronize(s->stream);
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
+  for (auto& kv : s->lag_graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : s->lag_defs) cudaGraphDestroy(kv.second);
   s->graphs.clear();
   s->graph_defs.clear();
+  s->lag_graphs.clear();
+  s->lag_defs.clear();
   s->pnodes.clear();
 }
 }  // namespace
@@ -1330,6 +1430,7 @@ int sbiem_batch_set_stream(sbiem_batch_t b, void* stream) {
 
 int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps) {
   if (!b || nsteps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
+  for (auto* m : b->members) m->lag_m = -1;  // batched steps compute their own sums
   if (!b->graph) {
     CK(cudaStreamSynchronize(b->stream));
     CK(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));

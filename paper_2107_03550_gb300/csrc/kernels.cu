@@ -209,11 +209,134 @@ __global__ void k_col_b(const FftGeom g, const DevFault<R>* __restrict__ fs, int
   col_body<R, INV, PRO>(g, f.tw, nullptr, f.zt, f, pass, m_dt, m_dt * f.dt_min);
 }
 
+// ------------------------------------------------ FP32 single-CTA spectral pass
+// Radix-8/4/2 Stockham FFT held in registers between shared-memory stages:
+// N/8 threads, each owning 8 values per stage.  Stage with sub-transform
+// length Ns and radix R, for j < N/R: k = j mod Ns, v_r = A[j + r N/R]
+// times exp(-+2 pi i r k / (Ns R)), an R-point DFT, and
+// B[(j - k) R + k + r Ns] = V_r (self-sorting: natural order after the last
+// stage).  Twiddles come from the N/2-entry table exp(-2 pi i a / N).
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// v * w8^K, w8 = exp(-2 pi i / 8) (forward) or its conjugate (inverse)
+template <int K, bool INV>
+__device__ __forceinline__ float2 rot8(float2 v) {
+  constexpr float c = 0.70710678118654752f;
+  if constexpr (K == 0) return v;
+  if constexpr (K == 1) return INV ? make_float2(c * (v.x - v.y), c * (v.x + v.y)) : make_float2(c * (v.x + v.y), c * (v.y - v.x));
+  if constexpr (K == 2) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+  if constexpr (K == 3) return INV ? make_float2(-c * (v.x + v.y), c * (v.x - v.y)) : make_float2(c * (v.y - v.x), -c * (v.x + v.y));
+  return v;
+}
+
+template <int K, bool INV>
+__device__ __forceinline__ void bfly(float2& a, float2& b) {
+  const float2 s = f2add(a, b), d = f2sub(a, b);
+  a = s;
+  b = rot8<K, INV>(d);
+}
+
+// In-place DFTs of 8, 4 and 2 points (radix-2 decimation in frequency),
+// results in natural order.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  bfly<0, INV>(v[0], v[4]);
+  bfly<1, INV>(v[1], v[5]);
+  bfly<2, INV>(v[2], v[6]);
+  bfly<3, INV>(v[3], v[7]);
+  bfly<0, INV>(v[0], v[2]);
+  bfly<2, INV>(v[1], v[3]);
+  bfly<0, INV>(v[4], v[6]);
+  bfly<2, INV>(v[5], v[7]);
+  bfly<0, INV>(v[0], v[1]);
+  bfly<0, INV>(v[2], v[3]);
+  bfly<0, INV>(v[4], v[5]);
+  bfly<0, INV>(v[6], v[7]);
+  // bit reversal of 3 bits: swap 1<->4, 3<->6
+  float2 t = v[1];
+  v[1] = v[4];
+  v[4] = t;
+  t = v[3];
+  v[3] = v[6];
+  v[6] = t;
+}
+
+template <bool INV, int O>
+__device__ __forceinline__ void dft4(float2 (&v)[8]) {
+  bfly<0, INV>(v[O + 0], v[O + 2]);
+  bfly<2, INV>(v[O + 1], v[O + 3]);
+  bfly<0, INV>(v[O + 0], v[O + 1]);
+  bfly<0, INV>(v[O + 2], v[O + 3]);
+  const float2 t = v[O + 1];
+  v[O + 1] = v[O + 2];
+  v[O + 2] = t;
+}
+
+// One Stockham stage over buf (length N, nth = N/8 threads).
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, int N, int Ns, int tid, int nth) {
+  constexpr int NB = 8 / R;  // butterflies per thread
+  const int stride = N / R;
+  const int half = N >> 1;
+  float2 v[8];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int j = tid + q * nth;
+    const int k = j & (Ns - 1);
+    const int tstep = k * (N / (Ns * R));
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 x = buf[j + r * stride];
+      if (r > 0) {
+        const int a = r * tstep;
+        float2 w = a < half ? tw[a] : make_float2(-tw[a - half].x, -tw[a - half].y);
+        if (INV) w.y = -w.y;
+        x = f2mul(x, w);
+      }
+      v[q * R + r] = x;
+    }
+  }
+  if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV, 0>(v);
+    dft4<INV, 4>(v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bfly<0, INV>(v[2 * q], v[2 * q + 1]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int j = tid + q * nth;
+    const int k = j & (Ns - 1);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[q * R + r];
+  }
+  __syncthreads();
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft_r8(float2* buf, const float2* tw, int N, int lgN, int tid, int nth) {
+  int Ns = 1;
+  for (int s = 0; s < lgN / 3; ++s, Ns *= 8) stockham_stage<8, INV>(buf, tw, N, Ns, tid, nth);
+  if (lgN % 3 == 2) stockham_stage<4, INV>(buf, tw, N, Ns, tid, nth);
+  if (lgN % 3 == 1) stockham_stage<2, INV>(buf, tw, N, Ns, tid, nth);
+}
+
 // Whole spectral side of one pass of the precision form (FP32 FFTs) for
-// N <= 16384 in one CTA: predictor prologue, forward FFT of Vbar + i kappa
-// Vbar, assembly of each mode pair (m, N-m) in FP32 (Sec. 3.1, Sec. 3.3 step
-// (2)), inverse FFT, scaled output tau_el + i sigma_el.  Shared memory: N
-// complex values and N/2 twiddles.
+// N <= kFusedMaxN in one CTA of N/8 threads, with no FP64 arithmetic: the
+// input Vbar + i kappa Vbar comes prepared in FP32 (zin1 for pass 1, written
+// at commit; zin2 for pass 2, written by the pass-1 Newton), forward FFT,
+// assembly of each mode pair (m, N-m) in FP32 (Sec. 3.1, Sec. 3.3 step (2)),
+// inverse FFT, scaled output tau_el + i sigma_el.  Pass 2 leaves U, Q of the
+// step (FP32) for the commit.  Shared memory: N complex values and N/2
+// twiddles.
 __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
   using C = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -225,18 +348,15 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   if (tid == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
-  int lg = 0;
-  while ((1 << lg) < N) ++lg;
+  const int lg = 31 - __clz(N);
   for (int j = tid; j < half; j += nth) tw[j] = f.tw[j];
-  for (int n = tid; n < N; n += nth) {
-    const double vb = (pass == 1) ? f.V[n] : 0.5 * (f.V[n] + f.V1[n]);
-    f.Vbar[n] = vb;
-    buf[n] = make_float2(static_cast<float>(vb), static_cast<float>(f.kappa[n] * vb));
-  }
+  const C* zin = pass == 1 ? f.zin1 : f.zin2;
+  for (int n = tid; n < N; n += nth) buf[n] = zin[n];
   __syncthreads();
-  fft_batch<C, false>(buf, lg, 1, tw, tid, nth);
+  fft_r8<false>(buf, tw, N, lg, tid, nth);
   const float mu = static_cast<float>(f.mu);
   const float kf = static_cast<float>(kTwoPi / f.L);
+  const float S = static_cast<float>(f.S);
   const bool pow2 = (m_dt & (m_dt - 1)) == 0;
   const int p2 = pow2 ? 31 - __clz(m_dt) : 0;
   for (int m = tid; m <= half; m += nth) {
@@ -265,7 +385,6 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
       }
       // S dt + mu w0 was combined in FP64 (near cancellation); FP32 products
       const float2 D = f.dhat32[m], K = f.khat32[m], AT = f.AT32[m], AN = f.AN32[m];
-      const float S = static_cast<float>(f.S);
       tr = -k * (S * D.x + cT * Ux + mu * AT.x);
       ti = (m < half) ? -k * (S * D.y + cT * Uy + mu * AT.y) : 0.f;
       if (m < half) {
@@ -276,15 +395,15 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
       }
     }
     if (pass == 2) {
-      f.U2[m] = make_double2(Ux, Uy);
-      f.Q2[m] = make_double2(Qx, Qy);
+      f.U2f[m] = make_float2(Ux, Uy);
+      f.Q2f[m] = make_float2(Qx, Qy);
     }
     // Y_m = tau_m + i sig_m; Y_{N-m} = conj(tau_m) + i conj(sig_m)
     buf[m] = make_float2(tr - si, ti + sr);
     if (m > 0 && m < half) buf[N - m] = make_float2(tr + si, -ti + sr);
   }
   __syncthreads();
-  fft_batch<C, true>(buf, lg, 1, tw, tid, nth);
+  fft_r8<true>(buf, tw, N, lg, tid, nth);
   const float scale = 1.0f / static_cast<float>(N);
   for (int n = tid; n < N; n += nth) f.y[n] = make_float2(buf[n].x * scale, buf[n].y * scale);
 }
@@ -612,10 +731,10 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     lo = hi - d;
   }
   // a learned guess is used when it is finite, inside the bracket and calls
-  // for a substantial change (|guess - ln V_prev| >= 0.25, where the
-  // previous slip rate is a poor start); otherwise the previous slip rate
-  // (clamped to the bracket) starts Newton
-  const bool use_guess = isfinite(xguess) && xguess >= lo && xguess <= hi && fabs(xguess - x0) >= 0.25;
+  // for a substantial change (|guess - ln V_prev| >= 0.1, where the previous
+  // slip rate is a poor start); otherwise the previous slip rate (clamped to
+  // the bracket) starts Newton
+  const bool use_guess = isfinite(xguess) && xguess >= lo && xguess <= hi && fabs(xguess - x0) >= 0.1;
   double x = use_guess ? xguess : fmin(fmax(x0, lo), hi);
   const double sa = sig * a;
   for (int it = 1; it <= maxit; ++it) {
@@ -659,7 +778,8 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   double vb = 0.0, Dc = 1.0, thp = 1.0, psip = 0.0, tau = 0.0, sig = 1.0, xstart = 0.0, a = 0.01, c0 = 0.0;
   bool solve = false;
   if (have) {
-    vb = f.Vbar[i];
+    // pass slip rate: the committed one, then the mean of committed and pass-1
+    vb = (pass == 1) ? f.V[i] : 0.5 * (f.V[i] + f.V1[i]);
     Dc = f.Dc[i];
     const double psi0 = f.psi[i];
     if (f.state_law == 0) {
@@ -723,6 +843,11 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       f.V1[i] = Vn;
       f.x1[i] = x;
       f.thd1[i] = thd_new;
+      if (f.zin2) {
+        // FP32 input of the pass-2 FFT
+        const double v2 = 0.5 * (f.V[i] + Vn);
+        f.zin2[i] = make_float2(static_cast<float>(v2), static_cast<float>(f.kappa[i] * v2));
+      }
     } else {
       f.V2[i] = Vn;
       f.x2[i] = x;
@@ -761,18 +886,21 @@ __global__ void __launch_bounds__(32) k_newton_b(const DevFault<R>* __restrict__
 
 // ------------------------------------------------------------- commit
 template <class R>
-__device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, double dt) {
+__device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, double dt, int lag_p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (*f.status) return;
   if (i < f.N) {
-    f.V[i] = f.V2[i];
+    const double v = f.V2[i];
+    f.V[i] = v;
     f.xV[i] = f.x2[i];
     f.psi[i] = f.psi2[i];
     f.thd[i] = f.thd2[i];
     f.delta[i] = f.delta2[i];
+    if (f.zin1) f.zin1[i] = make_float2(static_cast<float>(v), static_cast<float>(f.kappa[i] * v));
   }
   if (i < f.nmodes) {
-    const double2 U = f.U2[i], Q = f.Q2[i];
+    const double2 U = f.U2f ? make_double2(f.U2f[i].x, f.U2f[i].y) : f.U2[i];
+    const double2 Q = f.Q2f ? make_double2(f.Q2f[i].x, f.Q2f[i].y) : f.Q2[i];
     double2 D = f.dhat[i], K = f.khat[i];
     D.x += dt * U.x;
     D.y += dt * U.y;
@@ -805,6 +933,35 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
       }
       f.head[i] = h;
     }
+    if (lag_p >= 0) {
+      // overlapped form: the next step (same m_dt) sees this step's slot at
+      // lags m_dt .. 2 m_dt - 1 and the older slots through BT/BN
+      double2 T = f.BT[i], Nn = f.BN[i];
+      if (Rn > 0) {
+        const double2 w1 = f.w0pow[static_cast<size_t>(i) * kPow2Slots + lag_p + 1];
+        const double2 w0 = f.w0pow[static_cast<size_t>(i) * kPow2Slots + lag_p];
+        const double wT = w1.x - w0.x, wN = w1.y - w0.y;
+        double2 sT, sN;
+        if constexpr (sizeof(R) == 8) {
+          sT = U;
+          sN = Q;
+        } else {
+          // the value the ring holds (FP32)
+          sT = make_double2(static_cast<float>(U.x), static_cast<float>(U.y));
+          sN = make_double2(static_cast<float>(Q.x), static_cast<float>(Q.y));
+        }
+        T.x = fma(wT, sT.x, T.x);
+        T.y = fma(wT, sT.y, T.y);
+        Nn.x = fma(wN, sN.x, Nn.x);
+        Nn.y = fma(wN, sN.y, Nn.y);
+      }
+      f.AT[i] = T;
+      f.AN[i] = Nn;
+      if (f.AT32) {
+        f.AT32[i] = make_float2(static_cast<float>(T.x), static_cast<float>(T.y));
+        f.AN32[i] = make_float2(static_cast<float>(Nn.x), static_cast<float>(Nn.y));
+      }
+    }
   }
   if (i == 0) {
     *f.steps_done += 1;
@@ -813,14 +970,14 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
 }
 
 template <class R>
-__global__ void k_commit(const __grid_constant__ DevFault<R> f, int m_dt, double dt) {
-  commit_body<R>(f, m_dt, dt);
+__global__ void k_commit(const __grid_constant__ DevFault<R> f, int m_dt, double dt, int lag_p) {
+  commit_body<R>(f, m_dt, dt, lag_p);
 }
 
 template <class R>
 __global__ void k_commit_b(const DevFault<R>* __restrict__ fs, int m_dt) {
   const DevFault<R>& f = fs[blockIdx.y];
-  commit_body<R>(f, m_dt, m_dt * f.dt_min);
+  commit_body<R>(f, m_dt, m_dt * f.dt_min, -1);
 }
 
 // Push of m_dt > 1 copies of this step's spectra (a step of m_dt dt_min,
@@ -837,7 +994,8 @@ __global__ void k_push_multi(DevFault<R> f, int m_dt) {
     const int cnt = min(m_dt, Rn);
     if (cd.i0 >= cnt) continue;
     const int hn = static_cast<int>(((f.head[n] - static_cast<int64_t>(cnt)) % Rn + Rn) % Rn);
-    const double2 U = f.U2[n], Q = f.Q2[n];
+    const double2 U = f.U2f ? make_double2(f.U2f[n].x, f.U2f[n].y) : f.U2[n];
+    const double2 Q = f.Q2f ? make_double2(f.Q2f[n].x, f.Q2f[n].y) : f.Q2[n];
     Slot<R> v;
     if constexpr (sizeof(R) == 8) {
       v.t = U;
@@ -1034,14 +1192,22 @@ static size_t col_smem(const FftGeom& g) { return (static_cast<size_t>(g.Bc) * g
 template <class R>
 static size_t row_smem(const FftGeom& g) { return (static_cast<size_t>(g.Br) * g.N1 + g.N1 / 2) * sizeof(Cx<R>); }
 
-// Opt in to the dynamic shared memory a kernel launches with (static shared
-// memory counts against the same 48 KB default, so always set it).
+// Opt in to dynamic shared memory.  The attribute belongs to the function,
+// not to a handle, and handles of different N launch the same kernels, so it
+// is raised to the device's opt-in limit (never lowered to one handle's
+// need); the launch's own size still decides occupancy.
 template <class K>
 static void allow_smem(K kernel, size_t bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, kernel);
+  const int avail = optin - static_cast<int>(fa.sharedSizeBytes);
+  if (static_cast<int>(bytes) <= avail)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
 }
 
-constexpr int kFusedMaxN = 8192;
 
 static size_t fused_smem(int N) { return static_cast<size_t>(N + N / 2) * sizeof(float2); }
 
@@ -1051,7 +1217,7 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   const double dt = m_dt * f.dt_min;
   if constexpr (sizeof(R) == 4) {
     if (f.N <= kFusedMaxN) {
-      k_spectral_fused<<<1, 1024, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
+      k_spectral_fused<<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
       k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
       return;
     }
@@ -1075,6 +1241,16 @@ void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   const int need = (f.nchunks + warps - 1) / warps;
   const int gr = grid < need ? grid : need;
   k_history_t<R, false><<<gr, kHistThreads, 0, st>>>(f, nullptr, f.chunks, f.nchunks, f.work, m_dt);
+}
+
+template <class R>
+void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+  DevFault<R> fb = f;
+  fb.AT = f.BT;
+  fb.AN = f.BN;
+  fb.AT32 = nullptr;
+  fb.AN32 = nullptr;
+  launch_history<R>(fb, 2 * m_dt, grid, st);
 }
 
 template <class R>
@@ -1103,7 +1279,7 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
                        cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (N <= kFusedMaxN) {
-      k_spectral_fused_b<<<members, 1024, fused_smem(N), st>>>(fs, pass, m_dt);
+      k_spectral_fused_b<<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
       k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);
       return;
     }
@@ -1169,15 +1345,24 @@ void launch_to_float2(const double2* a, float2* out, int n, cudaStream_t st) {
   k_to_float2<<<(n + 255) / 256, 256, 0, st>>>(a, out, n);
 }
 
+__global__ void k_zin(const double* V, const double* kappa, float2* zin, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) zin[i] = make_float2(static_cast<float>(V[i]), static_cast<float>(kappa[i] * V[i]));
+}
+
+void launch_zin(const double* V, const double* kappa, float2* zin, int n, cudaStream_t st) {
+  k_zin<<<(n + 255) / 256, 256, 0, st>>>(V, kappa, zin, n);
+}
+
 void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st) {
   k_maxdiff<<<1, 1024, 0, st>>>(a, b, n, out);
 }
 
 template <class R>
-void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st) {
+void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st, int lag_p) {
   const int n = f.N > f.nmodes ? f.N : f.nmodes;
   const int nt = 256;
-  k_commit<R><<<(n + nt - 1) / nt, nt, 0, st>>>(f, m_dt, m_dt * f.dt_min);
+  k_commit<R><<<(n + nt - 1) / nt, nt, 0, st>>>(f, m_dt, m_dt * f.dt_min, lag_p);
 }
 
 template <class R>
@@ -1257,8 +1442,10 @@ template void launch_weight_pow2<double>(const DevFault<double>&, cudaStream_t);
 template void launch_weight_pow2<float>(const DevFault<float>&, cudaStream_t);
 template void launch_ring_undo<double>(const DevFault<double>&, int, void*, int, cudaStream_t);
 template void launch_ring_undo<float>(const DevFault<float>&, int, void*, int, cudaStream_t);
-template void launch_commit<double>(const DevFault<double>&, int, cudaStream_t);
-template void launch_commit<float>(const DevFault<float>&, int, cudaStream_t);
+template void launch_commit<double>(const DevFault<double>&, int, cudaStream_t, int);
+template void launch_commit<float>(const DevFault<float>&, int, cudaStream_t, int);
+template void launch_history_ahead<double>(const DevFault<double>&, int, int, cudaStream_t);
+template void launch_history_ahead<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double, cudaStream_t);
 template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double, cudaStream_t);
 

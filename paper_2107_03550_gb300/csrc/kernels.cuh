@@ -81,6 +81,7 @@ struct DevFault {
   double2 *dhat, *khat;                    // F[delta], F[kappa delta]
   double2 *U2, *Q2;                        // staged pass-2 spectra
   double2 *AT, *AN;                        // history sums
+  double2 *BT, *BN;                        // next step's sums without its newest interval (overlapped form)
   double4* partial;                        // per-chunk partial sums
   int* counter;                            // per-mode chunk counters
   // history
@@ -89,6 +90,8 @@ struct DevFault {
   double2* w0pow;                          // [mode][p]: sum of the first 2^p weights
   float2* c0pow;                           // [mode][p]: S 2^p dt_min + mu w0 (T, N), FP32 form
   float2 *dhat32, *khat32, *AT32, *AN32;   // FP32 copies for the fused FP32 spectral kernel
+  float2 *zin1, *zin2;                     // fused FP32 form: FFT inputs (Vbar, kappa Vbar) of passes 1, 2
+  float2 *U2f, *Q2f;                       // fused FP32 form: staged pass-2 spectra
   const int64_t *ring_off, *w_off;
   const int32_t *Rn, *Mn;
   int32_t* head;
@@ -111,8 +114,15 @@ struct DevFault {
   int* work;                               // next chunk of the history convolution
 };
 
+// Largest N of the single-CTA FP32 spectral pass (N/8 threads).
+constexpr int kFusedMaxN = 8192;
+
 // Host launch wrappers (kernels.cu).
 template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
+// The same sweep with the weights shifted by 2 m_dt into BT/BN: the part of
+// the next step's sums that does not involve this step's interval, computed
+// while this step's passes run (overlapped form).
+template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
 // Ensemble launches: fs is a device array of member descriptors; the pass and
 // commit kernels take one member per blockIdx.y (all members of equal N).
 template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, int* work,
@@ -128,13 +138,18 @@ template <class R> void configure_batch_kernels(const FftGeom& g);
 // Resident CTAs per SM of the history convolution (occupancy calculator).
 template <class R> int history_blocks_per_sm();
 template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
-template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st);
+// lag_p >= 0 (m_dt = 2^lag_p): also finish the next step's history sums,
+// AT = BT + (sum of the weights of lags m_dt .. 2 m_dt - 1) x the new slot.
+template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st, int lag_p = -1);
 // Multi-slot history push for steps of m_dt > 1 (before launch_commit).
 template <class R> void launch_push_multi(const DevFault<R>& f, int m_dt, cudaStream_t st);
 // Fill f.w0pow from the weights (and f.c0pow when present).
 template <class R> void launch_weight_pow2(const DevFault<R>& f, cudaStream_t st);
 // FP32 copies of the spectral running sums (after they are recomputed).
 void launch_to_float2(const double2* a, float2* out, int n, cudaStream_t st);
+// zin1 = (V, kappa V) in FP32: the pass-1 input of the fused FP32 form
+// (after V changes outside a committed step).
+void launch_zin(const double* V, const double* kappa, float2* zin, int n, cudaStream_t st);
 // Save (dir 0) / restore (dir 1) the ring slots a push of m_dt copies overwrites.
 template <class R> void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaStream_t st);
 // *out = max_i |a_i - b_i|.

@@ -29,13 +29,19 @@ def test_mixed_step_lengths_match_oracle(precision):
         assert o.step(m) == 0
         g.step(m * g.dt_min)
         err = compare(o, g)
-        # FP32 form: the FFT rounding of F[kappa Vbar] is relative to its
-        # largest coefficient, so small normal-traction changes from a random
-        # history carry ~1e-4; the form's own contract (final slip, arrival
-        # time) is checked in test_precision_form_rupture
-        for k in ("delta", "tau_el", "sigma_el", "theta"):
-            tol = 1e-10 if precision == 0 else (1e-3 if k in ("tau_el", "sigma_el") else 1e-4)
-            assert err[k] < tol, (m, k, err)
+        if precision == 0:
+            for k in ("delta", "tau_el", "sigma_el", "theta"):
+                assert err[k] < 1e-10, (m, k, err)
+        else:
+            # FP32 form: FFT rounding is relative to the largest spectral
+            # coefficient, shared by shear and normal traction, so both are
+            # measured against the larger of the two traction scales
+            s = g.get_state()
+            scale = max(np.abs(o.last["tau_el"]).max(), np.abs(o.last["sig_el"]).max())
+            for k, ref in (("tau_el", o.last["tau_el"]), ("sigma_el", o.last["sig_el"])):
+                assert np.abs(s[k] - ref).max() < 1e-4 * scale, (m, k, err)
+            for k in ("delta", "theta"):
+                assert err[k] < 1e-4, (m, k, err)
     hT, hN = g.get_history()
     HT, HN = o.get_history()
     assert np.abs(hT - np.concatenate(HT)).max() <= (1e-12 if precision == 0 else 1e-6) * np.abs(hT).max()

@@ -26,23 +26,37 @@ def _need_gpu():
     sbiem.load_library()
 
 
+def prefill_random(g, seed):
+    from paper_2107_03550_gb300.workloads import random_history
+    R = np.maximum(g.windows() - 1, 0)
+    HT, HN, _ = random_history(R, seed, 1e-6)
+    g.set_history(HT, HN)
+
+
 def test_seamount_rupture_1000_steps_fp64():
+    # g steps one call at a time (whole-window sums); g2 replays the step
+    # graph in the overlapped form, 25 steps per call
     w = seamount_rupture()
     o = oracle_for(w)
     g = gpu_for(w)
-    worst = {}
+    g2 = gpu_for(w)
+    worst, worst2 = {}, {}
     for s in range(1000):
         assert o.step() == 0
         g.step()
-        if s % 25 == 24 or s == 999:
-            err = compare(o, g)
-            for k, v in err.items():
-                worst[k] = max(worst.get(k, 0.0), v)
+        if s % 25 == 24:
+            g2.enqueue(25)
+            for gg, wst in ((g, worst), (g2, worst2)):
+                for k, v in compare(o, gg).items():
+                    wst[k] = max(wst.get(k, 0.0), v)
     assert o.V.max() > 1.0          # the rupture is under way
-    for k in ("delta", "tau_el", "sigma_el"):
-        assert worst[k] < TOL64, (k, worst)
-    assert worst["V"] < 1e-9, worst
+    assert g2.status()[0] == 0
+    for wst in (worst, worst2):
+        for k in ("delta", "tau_el", "sigma_el"):
+            assert wst[k] < TOL64, (k, wst)
+        assert wst["V"] < 1e-9, wst
     g.close()
+    g2.close()
 
 
 @pytest.mark.parametrize("N,dx,seed", [(16, 25.0, 1), (64, 25.0, 2), (256, 10.0, 3), (2048, 10.0, 4)])
@@ -105,19 +119,52 @@ def test_history_sums_match_oracle(precision, tol, m):
 
 
 def test_graph_replay_equals_single_steps_and_is_deterministic():
+    # enqueue runs the overlapped form (the next step's history sweep beside
+    # this step's passes, the newest interval added at commit); sbiem_step
+    # sums the whole window at once: equal up to summation order
     w = seamount_rupture(N=256)
-    g1 = gpu_for(w)
-    g2 = gpu_for(w)
+    g1, g2, g3 = gpu_for(w), gpu_for(w), gpu_for(w)
+    for g in (g1, g2, g3):
+        prefill_random(g, seed=5)
     for _ in range(60):
         g1.step()
     g2.enqueue(60)
-    flags, done = g2.status()
-    assert flags == 0 and done == 60
-    s1, s2 = g1.get_state(), g2.get_state()
+    g3.enqueue(25)
+    g3.enqueue(35)
+    for g in (g2, g3):
+        flags, done = g.status()
+        assert flags == 0 and done == 60
+    s1, s2, s3 = g1.get_state(), g2.get_state(), g3.get_state()
     for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
-        assert np.array_equal(s1[k], s2[k]), k
-    g1.close()
-    g2.close()
+        assert rel(s2[k], s1[k]) < 1e-12, k
+        assert np.array_equal(s2[k], s3[k]), k
+    for g in (g1, g2, g3):
+        g.close()
+
+
+@pytest.mark.parametrize("precision,m", [(0, 1), (0, 4), (1, 1), (1, 2)])
+def test_overlapped_steps_match_oracle(precision, m):
+    # a full random history, so the lagged sums carry weight from step 1
+    w = seamount_rupture(N=256)
+    o = oracle_for(w)
+    g = gpu_for(w, precision=precision)
+    prefill(o, g, seed=9, scale=1e-6)
+    for _ in range(20):
+        assert o.step(m) == 0
+    g.enqueue(20, dt=m * g.dt_min)
+    assert g.status()[0] == 0
+    err = compare(o, g)
+    if precision == 0:
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert err[k] < 1e-10, (k, err)
+    else:
+        s = g.get_state()
+        scale = max(np.abs(o.last["tau_el"]).max(), np.abs(o.last["sig_el"]).max())
+        for k, ref in (("tau_el", o.last["tau_el"]), ("sigma_el", o.last["sig_el"])):
+            assert np.abs(s[k] - ref).max() < 1e-4 * scale, (k, err)
+        for k in ("delta", "V", "theta"):
+            assert err[k] < 1e-4, (k, err)
+    g.close()
 
 
 def test_step_host_matches_device_state():
