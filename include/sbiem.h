@@ -42,11 +42,14 @@ extern "C" {
 #define SBIEM_ERR_STATE         -6  /* theta <= 0 with the explicit state update (Sec. 3.2) */
 #define SBIEM_ERR_DTMIN         -7  /* failure at dt = dt_min in the adaptive run (Sec. 3.2) */
 #define SBIEM_ERR_UNSUPPORTED   -8  /* valid request outside what this build implements */
+#define SBIEM_ERR_WAIT          -9  /* a device-side wait ran past its iteration limit (the
+                                       step is rejected; the CUDA context stays usable) */
 
 /* bit flags of the device status word (sbiem_status) */
 #define SBIEM_FLAG_NEWTON   1u
 #define SBIEM_FLAG_OPENING  2u
 #define SBIEM_FLAG_STATE    4u
+#define SBIEM_FLAG_WAIT     8u  /* a bounded device wait (copy completion) gave up */
 
 typedef struct sbiem_s* sbiem_t;
 

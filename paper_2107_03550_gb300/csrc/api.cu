@@ -83,7 +83,7 @@ struct sbiem_s {
   std::map<int, std::vector<cudaGraphNode_t>> pnodes;  // per graph: nodes of marks 0..3
   int64_t chunk_slots = 2048;
   // adaptive run (Sec. 3.2): snapshot of the state, undo copy of ring slots
-  double* snap = nullptr;        // V, xV, psi, thd, delta (5N) + t
+  double* snap = nullptr;        // V, xV, psi, thd, delta, theta (6N) + t
   double2* snap_spec = nullptr;  // dhat, khat
   int32_t* snap_head = nullptr;
   long long* snap_steps = nullptr;
@@ -176,6 +176,7 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   f.S = s->S;
   f.mu = s->p.mu;
   f.eta = s->eta;
+  f.reta = 1.0 / s->eta;
   f.dt_min = s->dt_min;
   f.f0 = s->p.f0;
   f.V0 = s->p.V0;
@@ -201,19 +202,20 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   f = DevFault<R>{};
   fill_dev(s, f);
 #define COPYP(x) f.x = base.x
-  COPYP(V); COPYP(psi); COPYP(thd); COPYP(delta); COPYP(V1); COPYP(thd1); COPYP(Vbar);
+  COPYP(V); COPYP(psi); COPYP(th); COPYP(th2); COPYP(thd); COPYP(delta); COPYP(V1); COPYP(thd1); COPYP(Vbar);
   COPYP(V2); COPYP(psi2); COPYP(thd2); COPYP(delta2); COPYP(a); COPYP(b); COPYP(Dc);
   COPYP(xV); COPYP(x1); COPYP(x2); COPYP(lvd);
   COPYP(sig0); COPYP(tau0); COPYP(taur); COPYP(Vp); COPYP(kappa); COPYP(presc);
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(BT); COPYP(BN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
-  COPYP(chunks); COPYP(nchunks); COPYP(status); COPYP(steps_done); COPYP(t);
+  COPYP(chunks); COPYP(nchunks); COPYP(mfirst); COPYP(mcount); COPYP(status); COPYP(steps_done); COPYP(t);
   COPYP(it_sum); COPYP(it_max); COPYP(work); COPYP(w0pow); COPYP(c0pow); COPYP(dhat32); COPYP(khat32);
   COPYP(AT32); COPYP(AN32);
 #undef COPYP
   bool ok = true;
   f.ring = alloc_n<Slot<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
-  f.w = alloc_n<W2<R>>(s, static_cast<size_t>(std::max<int64_t>(s->total_w, 1)), &ok);
+  // two spare entries: the sweep's 16-byte aligned weight copies may read one past the end
+  f.w = alloc_n<W2<R>>(s, static_cast<size_t>(s->total_w + 2), &ok);
   f.zt = alloc_n<Cx<R>>(s, s->N, &ok);
   f.Z = alloc_n<Cx<R>>(s, s->N, &ok);
   f.y = alloc_n<Cx<R>>(s, s->N, &ok);
@@ -304,12 +306,12 @@ void ring_undo(sbiem_s* s, int m, int dir) {
 int snapshot(sbiem_s* s, bool save) {
   auto& f = s->f64;
   const size_t nb = sizeof(double) * s->N;
-  double* arrs[] = {f.V, f.xV, f.psi, f.thd, f.delta};
-  for (int k = 0; k < 5; ++k) {
+  double* arrs[] = {f.V, f.xV, f.psi, f.thd, f.delta, f.th};
+  for (int k = 0; k < 6; ++k) {
     double* sn = s->snap + static_cast<size_t>(k) * s->N;
     CK(cudaMemcpyAsync(save ? sn : arrs[k], save ? arrs[k] : sn, nb, cudaMemcpyDeviceToDevice, s->stream));
   }
-  double* snt = s->snap + static_cast<size_t>(5) * s->N;
+  double* snt = s->snap + static_cast<size_t>(6) * s->N;
   CK(cudaMemcpyAsync(save ? snt : f.t, save ? f.t : snt, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
   const size_t sb = sizeof(double2) * s->nmodes;
   CK(cudaMemcpyAsync(save ? s->snap_spec : f.dhat, save ? f.dhat : s->snap_spec, sb, cudaMemcpyDeviceToDevice, s->stream));
@@ -332,6 +334,7 @@ int status_to_code(unsigned st) {
   if (st & SBIEM_FLAG_NEWTON) return SBIEM_ERR_NEWTON;
   if (st & SBIEM_FLAG_OPENING) return SBIEM_ERR_OPENING;
   if (st & SBIEM_FLAG_STATE) return SBIEM_ERR_STATE;
+  if (st & SBIEM_FLAG_WAIT) return SBIEM_ERR_WAIT;
   return SBIEM_OK;
 }
 
@@ -388,6 +391,7 @@ const char* sbiem_strerror(int code) {
     case SBIEM_ERR_STATE: return "state variable not positive";
     case SBIEM_ERR_DTMIN: return "failure at the minimum time step";
     case SBIEM_ERR_UNSUPPORTED: return "unsupported request";
+    case SBIEM_ERR_WAIT: return "a device-side wait ran past its limit";
     default: return "unknown error";
   }
 }
@@ -443,18 +447,15 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   s->eta = p.mu / (2.0 * p.cs);
   windows(p, s->L, s->dt_min, s->M);
   {
-    // chunk length: about two chunks per resident warp of the history
-    // convolution (load balance vs per-chunk reduction cost), a multiple of
-    // 128 slots, within [512, 4096]
-    const int per_sm = s->fp32() ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
+    // bulk-async sweep: chunks of one stage buffer (512 lags FP32, 256 FP64),
+    // every resident CTA streaming; the overlapped sweep keeps one CTA per SM
+    // so the pass kernels find room beside it
+    if (s->fp32()) configure_kernels<float>(make_geom(N, sizeof(float2)));
+    else configure_kernels<double>(make_geom(N, sizeof(double2)));
+    const int per_sm = s->fp32() ? sweep_blocks_per_sm<float>() : sweep_blocks_per_sm<double>();
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
-    // overlapped sweep: one CTA per SM fewer, so the pass kernels find room
-    s->lag_grid = s->sm_count * (per_sm > 1 ? per_sm - 1 : 1);
-    int64_t tot = 0;
-    for (int64_t Mn : s->M) tot += std::max<int64_t>(Mn - 1, 0);
-    const int64_t warps = static_cast<int64_t>(s->hist_grid) * 8;
-    int64_t cs = (tot / (2 * warps) + 127) / 128 * 128;
-    s->chunk_slots = std::min<int64_t>(std::max<int64_t>(cs, 512), 4096);
+    s->lag_grid = s->sm_count;
+    s->chunk_slots = sweep_chunk_slots(p.precision);
   }
   s->Rn.assign(s->nmodes, 0);
   s->ring_off.assign(s->nmodes + 1, 0);
@@ -481,6 +482,12 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     for (int q = 0; q < cnt; ++q) s->chunks[c + q].first = static_cast<int32_t>(c);
     c += cnt;
   }
+  std::vector<int32_t> mfirst(s->nmodes, 0), mcount(s->nmodes, 0);
+  for (size_t c = 0; c < s->chunks.size(); ++c) {
+    const int n = s->chunks[c].mode;
+    if (mcount[n] == 0) mfirst[n] = static_cast<int32_t>(c);
+    ++mcount[n];
+  }
   s->total_slots = s->ring_off[s->nmodes];
   s->total_w = s->w_off[s->nmodes];
   if (s->total_slots > (int64_t(1) << 31) || s->Rn[1] > (int64_t(1) << 30)) {
@@ -494,7 +501,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   bool ok = true;
   double** darr[] = {&f.V, &f.psi, &f.thd, &f.delta, &f.V1, &f.thd1, &f.Vbar, &f.V2, &f.psi2, &f.thd2,
                      &f.delta2, &f.a, &f.b, &f.Dc, &f.sig0, &f.tau0, &f.taur, &f.Vp, &f.kappa,
-                     &f.xV, &f.x1, &f.x2, &f.lvd};
+                     &f.xV, &f.x1, &f.x2, &f.lvd, &f.th, &f.th2};
   for (double** d : darr) *d = alloc_n<double>(s, N, &ok);
   f.presc = alloc_n<uint8_t>(s, N, &ok);
   double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN, &f.BT, &f.BN};
@@ -515,6 +522,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   int32_t* d_Mn = alloc_n<int32_t>(s, s->nmodes, &ok);
   f.head = alloc_n<int32_t>(s, s->nmodes, &ok);
   Chunk* d_chunks = alloc_n<Chunk>(s, std::max<size_t>(s->chunks.size(), 1), &ok);
+  int32_t* d_mfirst = alloc_n<int32_t>(s, s->nmodes, &ok);
+  int32_t* d_mcount = alloc_n<int32_t>(s, s->nmodes, &ok);
   f.status = alloc_n<unsigned>(s, 1, &ok);
   f.steps_done = alloc_n<long long>(s, 1, &ok);
   f.t = alloc_n<double>(s, 1, &ok);
@@ -532,6 +541,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   f.Mn = d_Mn;
   f.chunks = d_chunks;
   f.nchunks = static_cast<int>(s->chunks.size());
+  f.mfirst = d_mfirst;
+  f.mcount = d_mcount;
   if (!ok) {
     free_all(s);
     delete s;
@@ -580,13 +591,16 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
             up(f.sig0, sigma_load, nb) == cudaSuccess && up(f.tau0, taul.data(), nb) == cudaSuccess &&
             up(f.taur, taur.data(), nb) == cudaSuccess && up(f.Vp, Vp.data(), nb) == cudaSuccess &&
             up(f.presc, pr.data(), N) == cudaSuccess && up(f.V, V.data(), nb) == cudaSuccess &&
-            up(f.psi, psi.data(), nb) == cudaSuccess && up(f.thd, thd.data(), nb) == cudaSuccess &&
+            up(f.psi, psi.data(), nb) == cudaSuccess && up(f.th, theta_init, nb) == cudaSuccess &&
+            up(f.thd, thd.data(), nb) == cudaSuccess &&
             up(f.xV, xV.data(), nb) == cudaSuccess && up(f.lvd, lvd.data(), nb) == cudaSuccess &&
             up(d_roff, s->ring_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
             up(d_woff, s->w_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
             up(d_Rn, Rn32.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
             up(d_Mn, Mn32.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
             (s->chunks.empty() || up(d_chunks, s->chunks.data(), sizeof(Chunk) * s->chunks.size()) == cudaSuccess) &&
+            up(d_mfirst, mfirst.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
+            up(d_mcount, mcount.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
             up(s->tw64, tw.data(), sizeof(double) * tw.size()) == cudaSuccess &&
             (!s->fp32() || up(s->tw32, tw32.data(), sizeof(float) * tw32.size()) == cudaSuccess);
   s->g64 = make_geom(N, sizeof(double2));
@@ -626,7 +640,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     }
   } else {
     f.ring = alloc_n<Slot64>(s, static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)), &ok);
-    f.w = alloc_n<W2<double>>(s, static_cast<size_t>(std::max<int64_t>(s->total_w, 1)), &ok);
+    f.w = alloc_n<W2<double>>(s, static_cast<size_t>(s->total_w + 2), &ok);
     f.zt = alloc_n<double2>(s, N, &ok);
     f.Z = alloc_n<double2>(s, N, &ok);
     f.y = alloc_n<double2>(s, N, &ok);
@@ -794,7 +808,7 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, i
   auto& f = s->f64;
   bool ok = true;
   if (!s->snap) {
-    s->snap = alloc_n<double>(s, static_cast<size_t>(5) * s->N + 1, &ok);
+    s->snap = alloc_n<double>(s, static_cast<size_t>(6) * s->N + 1, &ok);
     s->snap_spec = alloc_n<double2>(s, static_cast<size_t>(2) * s->nmodes, &ok);
     s->snap_head = alloc_n<int32_t>(s, s->nmodes, &ok);
     s->snap_steps = alloc_n<long long>(s, 1, &ok);
@@ -906,7 +920,7 @@ int sbiem_get_state(sbiem_t s, double* delta, double* V, double* theta, double* 
   const size_t nb = sizeof(double) * s->N;
   if (delta) CK(cudaMemcpyAsync(delta, f.delta, nb, cudaMemcpyDeviceToHost, s->stream));
   if (V) CK(cudaMemcpyAsync(V, f.V, nb, cudaMemcpyDeviceToHost, s->stream));
-  if (theta) CK(cudaMemcpyAsync(theta, f.psi, nb, cudaMemcpyDeviceToHost, s->stream));
+  if (theta) CK(cudaMemcpyAsync(theta, f.th, nb, cudaMemcpyDeviceToHost, s->stream));
   std::vector<double> y;
   std::vector<float> y32;
   if (tau_el || sigma_el) {
@@ -920,8 +934,6 @@ int sbiem_get_state(sbiem_t s, double* delta, double* V, double* theta, double* 
   }
   if (t) CK(cudaMemcpyAsync(t, f.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  if (theta)
-    for (int i = 0; i < s->N; ++i) theta[i] = std::exp(theta[i]);
   for (int i = 0; i < s->N; ++i) {
     const double tr = s->fp32() ? static_cast<double>(y32.empty() ? 0.f : y32[2 * i]) : (y.empty() ? 0.0 : y[2 * i]);
     const double si = s->fp32() ? static_cast<double>(y32.empty() ? 0.f : y32[2 * i + 1]) : (y.empty() ? 0.0 : y[2 * i + 1]);
@@ -940,12 +952,12 @@ int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const doubl
   std::vector<double> Vh(N), th(N), Dc(N), psi(N), thd(N), xV(N);
   std::vector<uint8_t> pr(N);
   CK(cudaMemcpyAsync(Vh.data(), f.V, nb, cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaMemcpyAsync(psi.data(), f.psi, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(th.data(), f.th, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(Dc.data(), f.Dc, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   if (V) Vh.assign(V, V + N);
   for (int i = 0; i < N; ++i) {
-    th[i] = theta ? theta[i] : std::exp(psi[i]);
+    if (theta) th[i] = theta[i];
     if (!(th[i] > 0)) return fail(SBIEM_ERR_INVALID, "theta must be positive");
     psi[i] = std::log(th[i]);
     thd[i] = 1.0 - th[i] * Vh[i] / Dc[i];
@@ -954,6 +966,7 @@ int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const doubl
   if (delta) CK(cudaMemcpyAsync(f.delta, delta, nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.V, Vh.data(), nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.psi, psi.data(), nb, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(f.th, th.data(), nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.thd, thd.data(), nb, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(f.xV, xV.data(), nb, cudaMemcpyHostToDevice, s->stream));
   int rc = recompute_spectral_sums(s);

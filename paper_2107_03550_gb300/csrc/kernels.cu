@@ -349,17 +349,45 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   __syncthreads();
   if (s_skip) return;
   const int lg = 31 - __clz(N);
-  for (int j = tid; j < half; j += nth) tw[j] = f.tw[j];
-  const C* zin = pass == 1 ? f.zin1 : f.zin2;
-  for (int n = tid; n < N; n += nth) buf[n] = zin[n];
+  const bool pow2 = (m_dt & (m_dt - 1)) == 0;
+  const int p2 = pow2 ? 31 - __clz(m_dt) : 0;
+  // nth = N/8: each thread owns 4 twiddles, 8 inputs and at most 5 modes
+  // (m = tid + q nth <= N/2) of the assembly.  Global loads are issued in
+  // batches (one memory latency each), the assembly inputs prefetched into
+  // L1 behind the forward FFT.
+  constexpr int kMpt = 5;
+#pragma unroll
+  for (int q = 0; q < kMpt; ++q) {
+    const int m = tid + q * nth;
+    if (m > 0 && m <= half) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.dhat32 + m));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.khat32 + m));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AT32 + m));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AN32 + m));
+      if (pow2) asm volatile("prefetch.global.L1 [%0];" ::"l"(f.c0pow + static_cast<size_t>(m) * kPow2Slots + p2));
+    }
+  }
+  {
+    const C* zin = pass == 1 ? f.zin1 : f.zin2;
+    C tv[4], zv[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tv[q] = f.tw[tid + q * nth];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) zv[q] = zin[tid + q * nth];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tw[tid + q * nth] = tv[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) buf[tid + q * nth] = zv[q];
+  }
   __syncthreads();
   fft_r8<false>(buf, tw, N, lg, tid, nth);
   const float mu = static_cast<float>(f.mu);
   const float kf = static_cast<float>(kTwoPi / f.L);
   const float S = static_cast<float>(f.S);
-  const bool pow2 = (m_dt & (m_dt - 1)) == 0;
-  const int p2 = pow2 ? 31 - __clz(m_dt) : 0;
-  for (int m = tid; m <= half; m += nth) {
+#pragma unroll 1
+  for (int q = 0; q < kMpt; ++q) {
+    const int m = tid + q * nth;
+    if (m > half) break;
     const C Zm = buf[m];
     const C Zc = buf[(N - m) & (N - 1)];
     const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
@@ -405,7 +433,11 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   __syncthreads();
   fft_r8<true>(buf, tw, N, lg, tid, nth);
   const float scale = 1.0f / static_cast<float>(N);
-  for (int n = tid; n < N; n += nth) f.y[n] = make_float2(buf[n].x * scale, buf[n].y * scale);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int n = tid + q * nth;
+    f.y[n] = make_float2(buf[n].x * scale, buf[n].y * scale);
+  }
 }
 
 __global__ void __launch_bounds__(1024) k_spectral_fused(const __grid_constant__ DevFault<float> f, int pass,
@@ -604,6 +636,235 @@ __global__ void __launch_bounds__(kHistThreads)
   }
 }
 
+// ---------------------------------------------- history sweep (bulk-async)
+// The history convolution of a single fault as a stream through shared
+// memory: each CTA takes a contiguous range of chunks (at most kSweepSlots
+// lags of one mode each); one thread issues cp.async.bulk copies of the
+// chunk's ring slots (one or two pieces, the ring wraps) and weights into a
+// kSweepStages-deep ring of stage buffers, completion tracked by an mbarrier
+// per stage; all threads reduce the stage and the CTA writes one partial sum
+// per chunk (no atomics).  A chunk's sum runs over its lags in a fixed
+// order, so results do not depend on scheduling.  Every wait is bounded: on
+// a timeout the kernel sets SBIEM_FLAG_WAIT, waits (bounded) for its copies
+// in flight and returns.
+template <class R> struct SweepCfg;
+template <> struct SweepCfg<float> { static constexpr int kSlots = 512; };   // 8 KB ring + 4 KB weights
+template <> struct SweepCfg<double> { static constexpr int kSlots = 256; };  // 8 KB ring + 4 KB weights
+constexpr int kSweepThreads = 128;
+constexpr int kSweepStages = 4;
+constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls before a wait is declared stuck
+
+template <class R>
+__host__ __device__ constexpr size_t sweep_stage_bytes() {
+  return static_cast<size_t>(SweepCfg<R>::kSlots) * sizeof(Slot<R>) +
+         static_cast<size_t>(SweepCfg<R>::kSlots + 2) * sizeof(W2<R>);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of bar; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (long long k = 0; k < kSpinLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Copy plan of one chunk (computed ahead by all threads, read by the
+// issuing thread): up to two ring pieces and one 16-byte aligned weight run.
+struct SweepPlan {
+  const void* r1;
+  const void* r2;
+  const void* wsrc;
+  unsigned b1, b2, bw;
+  int len, par;
+};
+constexpr int kPlanRing = 64;  // plans held in shared memory (a ring by chunk index)
+
+template <class R>
+__device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f, int c, int m_dt) {
+  SweepPlan pl{};
+  const Chunk cd = f.chunks[c];
+  const int n = cd.mode;
+  const int Rn = f.Rn[n];
+  const int64_t iend = min(cd.i1, static_cast<int64_t>(f.Mn[n]) - m_dt);
+  const int L = iend > cd.i0 ? static_cast<int>(iend - cd.i0) : 0;
+  pl.len = L;
+  if (L == 0) return pl;
+  int64_t p0 = f.head[n] + cd.i0;
+  if (p0 >= Rn) p0 -= Rn;
+  const int L1 = static_cast<int>(min(static_cast<int64_t>(L), Rn - p0));
+  const int L2 = L - L1;
+  // weights: 16-byte aligned start (two FP32 pairs per 16 bytes)
+  const int64_t ws = f.w_off[n] + m_dt + cd.i0;
+  constexpr int per16 = 16 / static_cast<int>(sizeof(W2<R>));  // 2 (FP32) or 1 (FP64)
+  const int64_t wa = ws / per16 * per16;
+  pl.par = static_cast<int>(ws - wa);
+  const int wc = (pl.par + L + per16 - 1) / per16 * per16;
+  const Slot<R>* ring = f.ring + f.ring_off[n];
+  pl.r1 = ring + p0;
+  pl.b1 = static_cast<unsigned>(L1 * sizeof(Slot<R>));
+  pl.r2 = ring;
+  pl.b2 = static_cast<unsigned>(L2 * sizeof(Slot<R>));
+  pl.wsrc = f.w + wa;
+  pl.bw = static_cast<unsigned>(wc * sizeof(W2<R>));
+  return pl;
+}
+
+// Thread 0: start the copies of a planned chunk into a stage.
+template <class R>
+__device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* stage_buf, uint64_t* bar) {
+  constexpr int S = SweepCfg<R>::kSlots;
+  if (pl.len == 0) {
+    mbar_arrive(bar);
+    return;
+  }
+  unsigned char* sw = stage_buf + static_cast<size_t>(S) * sizeof(Slot<R>);
+  mbar_expect_tx(bar, pl.b1 + pl.b2 + pl.bw);
+  bulk_g2s(stage_buf, pl.r1, pl.b1, bar);
+  if (pl.b2) bulk_g2s(stage_buf + pl.b1, pl.r2, pl.b2, bar);
+  bulk_g2s(sw, pl.wsrc, pl.bw, bar);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kSweepThreads)
+    k_sweep(const __grid_constant__ DevFault<R> f, int m_dt) {
+  constexpr int S = SweepCfg<R>::kSlots;
+  constexpr size_t SB = sweep_stage_bytes<R>();
+  constexpr int NW = kSweepThreads / 32;
+  extern __shared__ __align__(128) unsigned char sweep_smem[];
+  __shared__ __align__(8) uint64_t bars[kSweepStages];
+  __shared__ SweepPlan plan[kPlanRing];
+  __shared__ Acc4<R> red[2][NW];
+  __shared__ unsigned s_skip;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // one read of the status word (a concurrent pass may set it): uniform exit
+  if (tid == 0) s_skip = *f.status;
+  __syncthreads();
+  if (s_skip) return;
+  const int nch = f.nchunks;
+  const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
+  const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
+  const int nk = c1 - c0;
+  if (nk <= 0) return;
+  if (tid == 0) {
+    for (int s = 0; s < kSweepStages; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // plans of the first kPlanRing chunks (one per thread)
+  for (int j = tid; j < kPlanRing && j < nk; j += kSweepThreads) plan[j] = sweep_plan<R>(f, c0 + j, m_dt);
+  __syncthreads();
+  if (tid == 0)
+    for (int k = 0; k < kSweepStages && k < nk; ++k)
+      sweep_issue<R>(plan[k], sweep_smem + k * SB, &bars[k]);
+  bool stuck = false;
+  int k = 0;
+  for (; k < nk; ++k) {
+    const int s = k % kSweepStages;
+    // every kPlanRing/2 chunks: plans of the half-ring ahead (chunks
+    // k + kPlanRing/2 .. k + kPlanRing - 1 replace chunks already issued)
+    if (k > 0 && k % (kPlanRing / 2) == 0) {
+      const int j = k + kPlanRing / 2 + tid;
+      if (tid < kPlanRing / 2 && j < nk) plan[j % kPlanRing] = sweep_plan<R>(f, c0 + j, m_dt);
+    }
+    const unsigned parity = static_cast<unsigned>(k / kSweepStages) & 1u;
+    const bool ok = mbar_wait(&bars[s], parity);
+    Acc4<R> acc = {R(0), R(0), R(0), R(0)};
+    if (ok) {
+      const int L = plan[k % kPlanRing].len, par = plan[k % kPlanRing].par;
+      const Slot<R>* sring = reinterpret_cast<const Slot<R>*>(sweep_smem + s * SB);
+      const W2<R>* sw = reinterpret_cast<const W2<R>*>(sweep_smem + s * SB + static_cast<size_t>(S) * sizeof(Slot<R>));
+#pragma unroll 4
+      for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
+    }
+    acc.tr = warp_sum(acc.tr);
+    acc.ti = warp_sum(acc.ti);
+    acc.nr = warp_sum(acc.nr);
+    acc.ni = warp_sum(acc.ni);
+    if (lane == 0) red[k & 1][wid] = acc;
+    stuck = __syncthreads_or(!ok);
+    if (stuck) break;
+    if (tid == 0) {
+      // the stage was read by every thread (barrier above): refill it first
+      if (k + kSweepStages < nk)
+        sweep_issue<R>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
+      Acc4<R> t = red[k & 1][0];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        const Acc4<R> u = red[k & 1][w];
+        t.tr += u.tr;
+        t.ti += u.ti;
+        t.nr += u.nr;
+        t.ni += u.ni;
+      }
+      f.partial[c0 + k] = make_double4(static_cast<double>(t.tr), static_cast<double>(t.ti),
+                                       static_cast<double>(t.nr), static_cast<double>(t.ni));
+    }
+  }
+  if (stuck && tid == 0) {
+    atomicOr(f.status, SBIEM_FLAG_WAIT);
+    // copies still in flight land in this CTA's shared memory: wait for them
+    // (bounded) before the CTA exits
+    for (int q = k; q < nk && q < k + kSweepStages; ++q)
+      mbar_wait(&bars[q % kSweepStages], static_cast<unsigned>(q / kSweepStages) & 1u);
+  }
+}
+
+// Per-mode sums of the sweep's chunk partials, one warp per mode: lane q
+// adds chunks q, q + 32, ... in order, then a fixed butterfly tree over the
+// lanes (the result does not depend on scheduling).  Writes (AT, AN) or, for
+// the overlapped form, (BT, BN); the FP32 copies when `f32` is set.
+template <class R>
+__global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* outT, double2* outN, bool f32) {
+  const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (n >= f.nmodes || *f.status) return;
+  const int c0 = f.mfirst[n], cnt = f.mcount[n];
+  double4 t = make_double4(0.0, 0.0, 0.0, 0.0);
+  for (int q = lane; q < cnt; q += 32) {
+    const double4 u = f.partial[c0 + q];
+    t.x += u.x;
+    t.y += u.y;
+    t.z += u.z;
+    t.w += u.w;
+  }
+  t = make_double4(warp_sum(t.x), warp_sum(t.y), warp_sum(t.z), warp_sum(t.w));
+  if (lane == 0) {
+    outT[n] = make_double2(t.x, t.y);
+    outN[n] = make_double2(t.z, t.w);
+    if (f32 && f.AT32) {
+      f.AT32[n] = make_float2(static_cast<float>(t.x), static_cast<float>(t.y));
+      f.AN32[n] = make_float2(static_cast<float>(t.z), static_cast<float>(t.w));
+    }
+  }
+}
+
 // Ensemble version with shared weights: one warp per grouped chunk; for each
 // slot the weight is loaded once and applied to the rings of up to
 // kGroupMax members (their heads may differ).  Partial sums per (chunk,
@@ -714,44 +975,76 @@ __global__ void __launch_bounds__(kHistThreads)
 // ------------------------------------------------------------ friction
 // x = ln V solves g(x) = q(x) - eta e^x = 0 with q(x) = tau - sigma (c0 + a x),
 // c0 = f0 + b ln(theta V0 / Dc) - a ln V0 (Eq. momentum plus radiation
-// damping).  g is strictly decreasing; the quasi-static root x_qs (q = 0)
-// bounds the root from above, a lower bound comes from doubling steps.
-// Newton on g where friction dominates, on h(x) = x - ln(q/eta) where
-// radiation damping dominates (q > sigma a), bisection when a step leaves the
-// bracket.  Returns iterations (negative: not converged).
-__device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, double a, double eta,
-                                          double x0, double xguess, double tol, int maxit, double* xout) {
-  double hi = (tau / sig - c0) / a;
-  hi = fmin(hi, 700.0);
-  double d = 1.0, lo = hi - d;
-  for (int k = 0; k < 64; ++k) {
-    const double g = tau - sig * (c0 + a * lo) - eta * exp(lo);
-    if (g >= 0.0) break;
-    d *= 2.0;
-    lo = hi - d;
-  }
-  // a learned guess is used when it is finite, inside the bracket and calls
-  // for a substantial change (|guess - ln V_prev| >= 0.1, where the previous
-  // slip rate is a poor start); otherwise the previous slip rate (clamped to
-  // the bracket) starts Newton
-  const bool use_guess = isfinite(xguess) && xguess >= lo && xguess <= hi && fabs(xguess - x0) >= 0.1;
-  double x = use_guess ? xguess : fmin(fmax(x0, lo), hi);
+// damping).  g is strictly decreasing and concave, so its root is unique and
+// lies below the quasi-static root x_qs (q = 0).  Newton on g where friction
+// dominates, on h(x) = x - ln(q/eta) (same root, increasing and convex)
+// where radiation damping dominates (q > sigma a).  From either side a step
+// of either form lands at or above the root, and from above it stays in
+// [root, x): the iterates approach the root from above after the first step.
+// Guards: a step above the bracket [lo, hi] (lo: largest point seen with
+// g > 0, hi: smallest with g <= 0, initially x_qs) is replaced by
+// bisection, and a step below lo by bisection too.
+//
+// FP64 is scarce on this part, so e^x is carried along the iteration: from
+// V_prev when Newton starts at ln V_prev, then multiplied by e^dx from a
+// Taylor series when |dx| <= 1/64 (truncation below 2e-19 relative), a full
+// exp otherwise (the caller takes a full exp of the root, so no error is
+// carried from one solve to the next).  Returns iterations (negative: not
+// converged); *xout = the root.
+__device__ __forceinline__ double exp_small(double d) {
+  // e^d, |d| <= 1/64: Taylor polynomial of degree 7
+  double p = 1.0 / 5040.0;
+  p = fma(p, d, 1.0 / 720.0);
+  p = fma(p, d, 1.0 / 120.0);
+  p = fma(p, d, 1.0 / 24.0);
+  p = fma(p, d, 1.0 / 6.0);
+  p = fma(p, d, 0.5);
+  p = fma(p, d, 1.0);
+  return fma(p, d, 1.0);
+}
+
+__device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, double a, double eta, double reta,
+                                          double x0, double ex0, double xguess, double tol, int maxit,
+                                          double* xout) {
   const double sa = sig * a;
+  double hi = fmin((tau - sig * c0) / sa, 700.0);
+  double lo = -CUDART_INF;
+  // a learned guess is used when it is finite, below x_qs and calls for a
+  // substantial change (|guess - ln V_prev| >= 0.1, where the previous slip
+  // rate is a poor start); otherwise the previous slip rate (clamped to x_qs)
+  // starts Newton
+  const bool use_guess = isfinite(xguess) && xguess <= hi && fabs(xguess - x0) >= 0.1;
+  double x, ex;
+  if (use_guess) {
+    x = xguess;
+    ex = exp(x);
+  } else if (x0 <= hi) {
+    x = x0;
+    ex = ex0;
+  } else {
+    x = hi;
+    ex = exp(x);
+  }
   for (int it = 1; it <= maxit; ++it) {
-    const double e = eta * exp(x);
-    const double q = tau - sig * (c0 + a * x);
+    const double e = eta * ex;
+    const double q = tau - sig * fma(a, x, c0);
     const double g = q - e;
     if (g > 0.0) lo = x; else hi = x;
-    double xn;
-    if (q > sa) xn = x - (x - log(q / eta)) / (1.0 + sa / q);
-    else xn = x + g / (e + sa);
-    if (fabs(xn - x) <= tol) {
-      *xout = xn;
+    double dx;
+    if (q > sa) dx = -q * (x - log(q * reta)) / (q + sa);
+    else dx = g / (e + sa);
+    if (fabs(dx) <= tol) {
+      *xout = x + dx;
       return it;
     }
+    double xn = x + dx;
     // keep Newton points within tol of the bracket: roots next to the
     // quasi-static bound (vanishing radiation damping) land on it up to rounding
-    if (xn < lo - tol || xn > hi + tol) xn = 0.5 * (lo + hi);
+    if (xn > hi + tol || xn < lo - tol) {
+      xn = (lo > -CUDART_INF) ? 0.5 * (lo + hi) : hi;
+      dx = xn - x;
+    }
+    ex = fabs(dx) <= 0.015625 ? ex * exp_small(dx) : exp(xn);
     x = xn;
   }
   *xout = x;
@@ -775,21 +1068,32 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   const bool have = i < f.N;
   // per-element quantities of the solve (dummies on lanes without an element,
   // which still take part in the warp-wide network evaluation)
-  double vb = 0.0, Dc = 1.0, thp = 1.0, psip = 0.0, tau = 0.0, sig = 1.0, xstart = 0.0, a = 0.01, c0 = 0.0;
+  double vb = 0.0, Dc = 1.0, rDc = 1.0, thp = 1.0, psip = 0.0, tau = 0.0, sig = 1.0, xstart = 0.0, a = 0.01,
+         c0 = 0.0;
   bool solve = false;
   if (have) {
     // pass slip rate: the committed one, then the mean of committed and pass-1
     vb = (pass == 1) ? f.V[i] : 0.5 * (f.V[i] + f.V1[i]);
     Dc = f.Dc[i];
-    const double psi0 = f.psi[i];
+    rDc = 1.0 / Dc;
+    const double th0 = f.th[i];
     if (f.state_law == 0) {
-      // aging law integrated at constant Vbar: theta e^{-u} + dt (1 - e^{-u})/u
-      const double u = vb * dt / Dc;
-      const double phi = (u > 0.0) ? -expm1(-u) / u : 1.0;
-      thp = exp(psi0 - u) + dt * phi;
+      // aging law integrated at constant Vbar: theta e^{-u} + dt phi(u),
+      // phi(u) = (1 - e^{-u})/u, u = Vbar dt / Dc
+      const double u = vb * dt * rDc;
+      if (u < 1e-4) {
+        // series of phi to u^3 (truncation below u^4/120 < 1e-18);
+        // e^{-u} = 1 - u phi
+        const double phi = fma(fma(fma(-u, 1.0 / 24.0, 1.0 / 6.0), u, -0.5), u, 1.0);
+        thp = fma(th0, fma(-u, phi, 1.0), dt * phi);
+      } else {
+        const double em = expm1(-u);
+        const double eu = u < 1.0 ? 1.0 + em : exp(-u);
+        thp = fma(th0, eu, dt * (-em / u));
+      }
     } else {
       const double thdb = (pass == 1) ? f.thd[i] : 0.5 * (f.thd[i] + f.thd1[i]);
-      thp = exp(psi0) + thdb * dt;
+      thp = th0 + thdb * dt;
       if (!(thp > 0.0)) flags |= SBIEM_FLAG_STATE;
     }
     psip = log(thp);
@@ -821,7 +1125,9 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     } else if (!solve) {
       x = f.xV[i];
     } else {
-      const int it = solve_lnV(tau, sig, c0, a, f.eta, xstart, xguess, f.newton_tol, f.newton_maxit, &x);
+      // e^xstart: the slip rate whose log starts Newton
+      const double ex0 = (pass == 1) ? f.V[i] : f.V1[i];
+      const int it = solve_lnV(tau, sig, c0, a, f.eta, f.reta, xstart, ex0, xguess, f.newton_tol, f.newton_maxit, &x);
       if (it < 0) flags |= SBIEM_FLAG_NEWTON;
       iters = it < 0 ? -it : it;
       if (it > 0 && f.harvest) {
@@ -838,7 +1144,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       }
     }
     const double Vn = f.presc[i] ? f.Vp[i] : exp(x);
-    const double thd_new = 1.0 - thp * Vn / Dc;
+    const double thd_new = 1.0 - thp * Vn * rDc;
     if (pass == 1) {
       f.V1[i] = Vn;
       f.x1[i] = x;
@@ -852,6 +1158,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       f.V2[i] = Vn;
       f.x2[i] = x;
       f.psi2[i] = psip;
+      f.th2[i] = thp;
       f.thd2[i] = thd_new;
       f.delta2[i] = f.delta[i] + vb * dt;
     }
@@ -894,6 +1201,7 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
     f.V[i] = v;
     f.xV[i] = f.x2[i];
     f.psi[i] = f.psi2[i];
+    f.th[i] = f.th2[i];
     f.thd[i] = f.thd2[i];
     f.delta[i] = f.delta2[i];
     if (f.zin1) f.zin1[i] = make_float2(static_cast<float>(v), static_cast<float>(f.kappa[i] * v));
@@ -1235,7 +1543,7 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
 }
 
 template <class R>
-void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   if (f.nchunks == 0) return;
   const int warps = kHistThreads / 32;
   const int need = (f.nchunks + warps - 1) / warps;
@@ -1244,13 +1552,35 @@ void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
 }
 
 template <class R>
+static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+  if (f.nchunks == 0) return;
+  const int gr = grid < f.nchunks ? grid : f.nchunks;
+  k_sweep<R><<<gr, kSweepThreads, kSweepStages * sweep_stage_bytes<R>(), st>>>(f, m_dt);
+}
+
+template <class R>
+void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+  launch_sweep<R>(f, m_dt, grid, st);
+  k_sweep_finish<R><<<(f.nmodes + 7) / 8, 256, 0, st>>>(f, f.AT, f.AN, true);
+}
+
+template <class R>
 void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
-  DevFault<R> fb = f;
-  fb.AT = f.BT;
-  fb.AN = f.BN;
-  fb.AT32 = nullptr;
-  fb.AN32 = nullptr;
-  launch_history<R>(fb, 2 * m_dt, grid, st);
+  // into BT/BN; the commit adds the new slot's term
+  launch_sweep<R>(f, 2 * m_dt, grid, st);
+  k_sweep_finish<R><<<(f.nmodes + 7) / 8, 256, 0, st>>>(f, f.BT, f.BN, false);
+}
+
+template <class R>
+int sweep_blocks_per_sm() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R>, kSweepThreads,
+                                                kSweepStages * sweep_stage_bytes<R>());
+  return n;
+}
+
+int sweep_chunk_slots(int precision) {
+  return precision == 1 ? SweepCfg<float>::kSlots : SweepCfg<double>::kSlots;
 }
 
 template <class R>
@@ -1401,6 +1731,7 @@ void launch_real_part(int N, const double2* z, double* x, cudaStream_t st) {
 
 template <class R>
 void configure_kernels(const FftGeom& g) {
+  allow_smem(k_sweep<R>, kSweepStages * sweep_stage_bytes<R>());
   if constexpr (sizeof(R) == 4) {
     if (g.N <= kFusedMaxN) allow_smem(k_spectral_fused, fused_smem(g.N));
   }
@@ -1446,6 +1777,10 @@ template void launch_commit<double>(const DevFault<double>&, int, cudaStream_t, 
 template void launch_commit<float>(const DevFault<float>&, int, cudaStream_t, int);
 template void launch_history_ahead<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_history_ahead<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_history_atomic<double>(const DevFault<double>&, int, int, cudaStream_t);
+template void launch_history_atomic<float>(const DevFault<float>&, int, int, cudaStream_t);
+template int sweep_blocks_per_sm<double>();
+template int sweep_blocks_per_sm<float>();
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double, cudaStream_t);
 template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double, cudaStream_t);
 

@@ -63,13 +63,14 @@ template <class R>
 struct DevFault {
   int N;
   int nmodes;          // N/2 + 1
-  double L, S, mu, eta, dt_min, f0, V0, lnV0;
+  double L, S, mu, eta, reta, dt_min, f0, V0, lnV0;  // reta = 1/eta
   int state_law;
   int newton_epw;                          // elements per Newton warp (1..32)
   int newton_maxit;
   double newton_tol;
   // element state (FP64)
-  double *V, *psi, *thd, *delta;          // committed
+  double *V, *psi, *thd, *delta;          // committed (psi = ln theta)
+  double *th, *th2;                        // theta: committed, pass-2 (staged)
   double *V1, *thd1;                       // pass-1 results
   double *Vbar;                            // pass slip rate
   double *V2, *psi2, *thd2, *delta2;       // pass-2 results (staged)
@@ -97,6 +98,7 @@ struct DevFault {
   int32_t* head;
   const Chunk* chunks;
   int nchunks;
+  const int32_t *mfirst, *mcount;          // per mode: first chunk, chunks
   // FFT work
   Cx<R> *z, *zt, *Z, *y;                   // natural-order input, transposed, spectrum, output
   const Cx<R>* tw;                         // exp(-2 pi i j/N)
@@ -118,10 +120,19 @@ struct DevFault {
 constexpr int kFusedMaxN = 8192;
 
 // Host launch wrappers (kernels.cu).
+// History sums AT/AN of a step of m_dt (bulk-async sweep, then per-mode
+// sums of its chunk partials).
 template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
-// The same sweep with the weights shifted by 2 m_dt into BT/BN: the part of
-// the next step's sums that does not involve this step's interval, computed
-// while this step's passes run (overlapped form).
+// The one-warp-per-chunk sweep with atomic chunk hand-out and per-mode
+// last-arriver sums (writes AT/AN itself); used on caller-owned buffers.
+template <class R> void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
+// Resident CTAs per SM of the bulk-async sweep; its chunk length (lags).
+template <class R> int sweep_blocks_per_sm();
+int sweep_chunk_slots(int precision);
+// The same sweep with the weights shifted by 2 m_dt, chunk partials only:
+// the part of the next step's sums that does not involve this step's
+// interval, computed while this step's passes run (overlapped form); the
+// commit adds them up.
 template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
 // Ensemble launches: fs is a device array of member descriptors; the pass and
 // commit kernels take one member per blockIdx.y (all members of equal N).

@@ -141,7 +141,7 @@ int run(int nmodes, int m, const void* ring, const void* weights, const int64_t*
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = history_blocks_per_sm<R>();
-  launch_history<R>(f, m, sms * (per_sm > 0 ? per_sm : 1), st);
+  launch_history_atomic<R>(f, m, sms * (per_sm > 0 ? per_sm : 1), st);
   return cudaGetLastError() == cudaSuccess ? SBIEM_OK : SBIEM_ERR_CUDA;
 }
 
