@@ -31,6 +31,11 @@ template <class C> __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 
+// Shared-memory address of a generic pointer into this CTA's shared memory.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
 // --------------------------------------------------------- shared-memory FFT
 // B independent radix-2 Stockham (decimation in frequency, self-sorting)
 // transforms of length M = 2^lgM on buf[b * M + i].  twm[j] = exp(-2 pi i j/M),
@@ -329,8 +334,58 @@ __device__ __forceinline__ void fft_r8(float2* buf, const float2* tw, int N, int
   if (lgN % 3 == 1) stockham_stage<2, INV>(buf, tw, N, Ns, tid, nth);
 }
 
+// Assembly of the mode pair (m, N-m) of the precision form from the packed
+// spectrum Zm = Z[m], Zc = Z[(N-m) mod N] of Vbar + i kappa Vbar (Sec. 3.1,
+// Sec. 3.3 step (2)): returns Y[m] and Y[N-m] of tau_el + i sigma_el and, in
+// pass 2, leaves U, Q of mode m for the commit.
+__device__ __forceinline__ void assemble_pair32(const DevFault<float>& f, int m, float2 Zm, float2 Zc, int pass,
+                                                int m_dt, double dt, float2* Ym, float2* Yc) {
+  const int N = f.N, half = N >> 1;
+  const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
+  const float Qx = 0.5f * (Zm.y + Zc.y), Qy = -0.5f * (Zm.x - Zc.x);
+  float tr = 0.f, ti = 0.f, sr = 0.f, si = 0.f;
+  if (m > 0) {
+    const float mu = static_cast<float>(f.mu);
+    const float S = static_cast<float>(f.S);
+    const float k = static_cast<float>(kTwoPi / f.L) * static_cast<float>(m);
+    float cT, cN;
+    if ((m_dt & (m_dt - 1)) == 0) {
+      const float2 c = f.c0pow[static_cast<size_t>(m) * kPow2Slots + (31 - __clz(m_dt))];
+      cT = c.x;
+      cN = c.y;
+    } else {
+      double w0T = 0.0, w0N = 0.0;
+      const int lim = min(m_dt, f.Mn[m]);
+      for (int j = 0; j < lim; ++j) {
+        const W2<float> w = f.w[f.w_off[m] + j];
+        w0T += w.x;
+        w0N += w.y;
+      }
+      cT = static_cast<float>(f.S * dt + f.mu * w0T);
+      cN = static_cast<float>(f.S * dt + f.mu * w0N);
+    }
+    // S dt + mu w0 was combined in FP64 (near cancellation); FP32 products
+    const float2 D = f.dhat32[m], K = f.khat32[m], AT = f.AT32[m], AN = f.AN32[m];
+    tr = -k * (S * D.x + cT * Ux + mu * AT.x);
+    ti = (m < half) ? -k * (S * D.y + cT * Uy + mu * AT.y) : 0.f;
+    if (m < half) {
+      const float xr = S * K.x + cN * Qx + mu * AN.x;
+      const float xi = S * K.y + cN * Qy + mu * AN.y;
+      sr = xi;
+      si = -xr;
+    }
+  }
+  if (pass == 2) {
+    f.U2f[m] = make_float2(Ux, Uy);
+    f.Q2f[m] = make_float2(Qx, Qy);
+  }
+  // Y_m = tau_m + i sig_m; Y_{N-m} = conj(tau_m) + i conj(sig_m)
+  *Ym = make_float2(tr - si, ti + sr);
+  *Yc = make_float2(tr + si, -ti + sr);
+}
+
 // Whole spectral side of one pass of the precision form (FP32 FFTs) for
-// N <= kFusedMaxN in one CTA of N/8 threads, with no FP64 arithmetic: the
+// N < kClusterMinN in one CTA of N/8 threads, with no FP64 arithmetic: the
 // input Vbar + i kappa Vbar comes prepared in FP32 (zin1 for pass 1, written
 // at commit; zin2 for pass 2, written by the pass-1 Newton), forward FFT,
 // assembly of each mode pair (m, N-m) in FP32 (Sec. 3.1, Sec. 3.3 step (2)),
@@ -381,54 +436,14 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   }
   __syncthreads();
   fft_r8<false>(buf, tw, N, lg, tid, nth);
-  const float mu = static_cast<float>(f.mu);
-  const float kf = static_cast<float>(kTwoPi / f.L);
-  const float S = static_cast<float>(f.S);
 #pragma unroll 1
   for (int q = 0; q < kMpt; ++q) {
     const int m = tid + q * nth;
     if (m > half) break;
-    const C Zm = buf[m];
-    const C Zc = buf[(N - m) & (N - 1)];
-    const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
-    const float Qx = 0.5f * (Zm.y + Zc.y), Qy = -0.5f * (Zm.x - Zc.x);
-    float tr = 0.f, ti = 0.f, sr = 0.f, si = 0.f;
-    if (m > 0) {
-      const float k = kf * static_cast<float>(m);
-      float cT, cN;
-      if (pow2) {
-        const float2 c = f.c0pow[static_cast<size_t>(m) * kPow2Slots + p2];
-        cT = c.x;
-        cN = c.y;
-      } else {
-        double w0T = 0.0, w0N = 0.0;
-        const int lim = min(m_dt, f.Mn[m]);
-        for (int j = 0; j < lim; ++j) {
-          const W2<float> w = f.w[f.w_off[m] + j];
-          w0T += w.x;
-          w0N += w.y;
-        }
-        cT = static_cast<float>(f.S * dt + f.mu * w0T);
-        cN = static_cast<float>(f.S * dt + f.mu * w0N);
-      }
-      // S dt + mu w0 was combined in FP64 (near cancellation); FP32 products
-      const float2 D = f.dhat32[m], K = f.khat32[m], AT = f.AT32[m], AN = f.AN32[m];
-      tr = -k * (S * D.x + cT * Ux + mu * AT.x);
-      ti = (m < half) ? -k * (S * D.y + cT * Uy + mu * AT.y) : 0.f;
-      if (m < half) {
-        const float xr = S * K.x + cN * Qx + mu * AN.x;
-        const float xi = S * K.y + cN * Qy + mu * AN.y;
-        sr = xi;
-        si = -xr;
-      }
-    }
-    if (pass == 2) {
-      f.U2f[m] = make_float2(Ux, Uy);
-      f.Q2f[m] = make_float2(Qx, Qy);
-    }
-    // Y_m = tau_m + i sig_m; Y_{N-m} = conj(tau_m) + i conj(sig_m)
-    buf[m] = make_float2(tr - si, ti + sr);
-    if (m > 0 && m < half) buf[N - m] = make_float2(tr + si, -ti + sr);
+    C Ym, Yc;
+    assemble_pair32(f, m, buf[m], buf[(N - m) & (N - 1)], pass, m_dt, dt, &Ym, &Yc);
+    buf[m] = Ym;
+    if (m > 0 && m < half) buf[N - m] = Yc;
   }
   __syncthreads();
   fft_r8<true>(buf, tw, N, lg, tid, nth);
@@ -449,6 +464,196 @@ __global__ void __launch_bounds__(1024) k_spectral_fused_b(const DevFault<float>
                                                            int m_dt) {
   const DevFault<float>& f = fs[blockIdx.x];
   spectral_fused_body(f, pass, m_dt, m_dt * f.dt_min);
+}
+
+
+// ------------------------------------ FP32 spectral pass on a CTA cluster
+// The same pass spread over a cluster of kClusterCTAs CTAs (one SM each),
+// for kClusterMinN <= N <= kClusterMaxN: four-step FFT with N = N1 N2,
+// element n = n1 + N1 n2, mode m = k2 + N2 k1.  CTA c owns the columns
+// n1 in [c N1/C, (c+1) N1/C) and N2/C rows k2, taken from the sequence
+// 0, N2/2, 1, N2-1, 2, N2-2, ... so that a row and its mirror N2 - k2 (the
+// rows of the partners N - m) sit in the same CTA.  Forward: length-N2 FFTs
+// of the CTA's columns, twiddle w_N^{n1 k2}, scatter into the row owners'
+// shared memory (distributed shared memory), cluster barrier, length-N1
+// FFTs of the rows; assembly of each pair (m, N-m) in place; inverse: row
+// FFTs, twiddle w_N^{-n1 k2}, scatter back to the column owners, barrier,
+// column FFTs, output.  N/(8C) threads per CTA, 8 values each per stage.
+struct ClusterGeom {
+  int N1, N2, lg1, lg2, cols, rows;
+};
+
+__device__ __forceinline__ ClusterGeom cluster_geom(int N) {
+  ClusterGeom g;
+  const int lg = 31 - __clz(N);
+  g.lg1 = lg / 2;
+  g.lg2 = lg - g.lg1;
+  g.N1 = 1 << g.lg1;
+  g.N2 = 1 << g.lg2;
+  g.cols = g.N1 / kClusterCTAs;
+  g.rows = g.N2 / kClusterCTAs;
+  return g;
+}
+
+// Index of row k2 in the pair-adjacent sequence 0, N2/2, 1, N2-1, 2, ...
+__device__ __forceinline__ int row_seq(int k2, int N2) {
+  if (k2 == 0) return 0;
+  if (k2 == (N2 >> 1)) return 1;
+  return k2 < (N2 >> 1) ? 2 * k2 : 2 * (N2 - k2) + 1;
+}
+__device__ __forceinline__ int seq_row(int q, int N2) {
+  if (q == 0) return 0;
+  if (q == 1) return N2 >> 1;
+  return (q & 1) ? N2 - (q >> 1) : (q >> 1);
+}
+// w_N^a from the N/2-entry table (a < N), conjugated for the inverse
+__device__ __forceinline__ float2 tw_full(const float2* tw, int a, int half, bool inv) {
+  float2 w = a < half ? tw[a] : make_float2(-tw[a - half].x, -tw[a - half].y);
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(const void* p, unsigned rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(rank));
+  return out;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// B transforms of length L (L/8 threads each) side by side in buf.
+template <bool INV>
+__device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int L, int lgL, int tid) {
+  const int per = L >> 3;
+  fft_r8<INV>(buf + (tid / per) * L, tw, L, lgL, tid % per, per);
+}
+
+__device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
+  const unsigned c = cluster_rank();
+  const int N = f.N, half = N >> 1;
+  const ClusterGeom g = cluster_geom(N);
+  const int per = N / kClusterCTAs;  // elements per CTA (8 per thread)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* colbuf = reinterpret_cast<float2*>(smem_raw);  // [cols][N2]
+  float2* rowbuf = colbuf + per;                          // [rows][N1]
+  float2* twc = rowbuf + per;                             // w_N2^j, j < N2/2
+  float2* twr = twc + (g.N2 >> 1);                        // w_N1^j, j < N1/2
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int n1_0 = static_cast<int>(c) * g.cols;
+  const int q0 = static_cast<int>(c) * g.rows;  // first sequence index of this CTA's rows
+  // every CTA of the cluster runs before any remote store (arrive now, wait later)
+  cluster_arrive_relaxed();
+  for (int j = tid; j < (g.N2 >> 1); j += nth) twc[j] = f.tw[j * g.N1];
+  for (int j = tid; j < (g.N1 >> 1); j += nth) twr[j] = f.tw[j * g.N2];
+  // assembly inputs of this CTA's modes into L1 behind the forward FFT
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * nth;
+    const int k2 = seq_row(q0 + e / g.N1, g.N2);
+    const int m = k2 + g.N2 * (e % g.N1);
+    if (m > 0 && m <= half) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.dhat32 + m));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.khat32 + m));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AT32 + m));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AN32 + m));
+    }
+  }
+  {
+    // input columns: consecutive threads take consecutive n1 (runs of cols)
+    const float2* zin = pass == 1 ? f.zin1 : f.zin2;
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * nth;
+      v[q] = zin[(n1_0 + e % g.cols) + g.N1 * (e / g.cols)];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * nth;
+      colbuf[(e % g.cols) * g.N2 + e / g.cols] = v[q];
+    }
+  }
+  __syncthreads();
+  fft_r8_batch<false>(colbuf, twc, g.N2, g.lg2, tid);
+  cluster_wait();
+  // twiddle w_N^{n1 k2}, scatter to the row owners
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * nth;
+    const int b = e / g.N2, k2 = e % g.N2;
+    const float2 val = f2mul(colbuf[e], tw_full(f.tw, (n1_0 + b) * k2, half, false));
+    const int s = row_seq(k2, g.N2);
+    st_cluster(cluster_map(rowbuf + (s % g.rows) * g.N1 + n1_0 + b, static_cast<unsigned>(s / g.rows)), val);
+  }
+  cluster_arrive();
+  cluster_wait();
+  fft_r8_batch<false>(rowbuf, twr, g.N1, g.lg1, tid);
+  // assembly of the pairs (m, N-m) held by this CTA, in place
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * nth;
+    const int r = e / g.N1, k1 = e % g.N1;
+    const int k2 = seq_row(q0 + r, g.N2);
+    const int m = k2 + g.N2 * k1;
+    if (m > half) continue;
+    int k2p, k1p;
+    if (k2 == 0) {
+      k2p = 0;
+      k1p = (g.N1 - k1) & (g.N1 - 1);
+    } else {
+      k2p = (k2 == (g.N2 >> 1)) ? k2 : g.N2 - k2;
+      k1p = g.N1 - 1 - k1;
+    }
+    const int ep = (row_seq(k2p, g.N2) - q0) * g.N1 + k1p;
+    float2 Ym, Yc;
+    assemble_pair32(f, m, rowbuf[e], rowbuf[ep], pass, m_dt, dt, &Ym, &Yc);
+    rowbuf[e] = Ym;
+    if (ep != e) rowbuf[ep] = Yc;
+  }
+  __syncthreads();
+  fft_r8_batch<true>(rowbuf, twr, g.N1, g.lg1, tid);
+  // twiddle w_N^{-n1 k2}, scatter back to the column owners
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * nth;
+    const int r = e / g.N1, n1 = e % g.N1;
+    const int k2 = seq_row(q0 + r, g.N2);
+    const float2 val = f2mul(rowbuf[e], tw_full(f.tw, n1 * k2, half, true));
+    st_cluster(cluster_map(colbuf + (n1 % g.cols) * g.N2 + k2, static_cast<unsigned>(n1 / g.cols)), val);
+  }
+  cluster_arrive();
+  cluster_wait();
+  fft_r8_batch<true>(colbuf, twc, g.N2, g.lg2, tid);
+  const float scale = 1.0f / static_cast<float>(N);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * nth;
+    const float2 v = colbuf[(e % g.cols) * g.N2 + e / g.cols];
+    f.y[(n1_0 + e % g.cols) + g.N1 * (e / g.cols)] = make_float2(v.x * scale, v.y * scale);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_spectral_cluster(const __grid_constant__ DevFault<float> f, int pass,
+                                                           int m_dt, double dt) {
+  spectral_cluster_body(f, pass, m_dt, dt);
+}
+
+__global__ void __launch_bounds__(256) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs, int pass,
+                                                             int m_dt) {
+  const DevFault<float>& f = fs[blockIdx.x / kClusterCTAs];
+  spectral_cluster_body(f, pass, m_dt, m_dt * f.dt_min);
 }
 
 // Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
@@ -660,9 +865,6 @@ __host__ __device__ constexpr size_t sweep_stage_bytes() {
          static_cast<size_t>(SweepCfg<R>::kSlots + 2) * sizeof(W2<R>);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -703,7 +905,7 @@ struct SweepPlan {
   const void* r2;
   const void* wsrc;
   unsigned b1, b2, bw;
-  int len, par;
+  int len, par, mode;
 };
 constexpr int kPlanRing = 64;  // plans held in shared memory (a ring by chunk index)
 
@@ -716,6 +918,7 @@ __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f, int c, int
   const int64_t iend = min(cd.i1, static_cast<int64_t>(f.Mn[n]) - m_dt);
   const int L = iend > cd.i0 ? static_cast<int>(iend - cd.i0) : 0;
   pl.len = L;
+  pl.mode = n;
   if (L == 0) return pl;
   int64_t p0 = f.head[n] + cd.i0;
   if (p0 >= Rn) p0 -= Rn;
@@ -783,8 +986,12 @@ __global__ void __launch_bounds__(kSweepThreads)
   if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
       sweep_issue<R>(plan[k], sweep_smem + k * SB, &bars[k]);
+  // each thread accumulates over consecutive chunks of one mode; the CTA
+  // reduces at the end of the mode's run (a segment) and writes the sum at
+  // the segment's last chunk, zeros at the others
   bool stuck = false;
   int k = 0;
+  Acc4<R> acc = {R(0), R(0), R(0), R(0)};
   for (; k < nk; ++k) {
     const int s = k % kSweepStages;
     // every kPlanRing/2 chunks: plans of the half-ring ahead (chunks
@@ -795,7 +1002,6 @@ __global__ void __launch_bounds__(kSweepThreads)
     }
     const unsigned parity = static_cast<unsigned>(k / kSweepStages) & 1u;
     const bool ok = mbar_wait(&bars[s], parity);
-    Acc4<R> acc = {R(0), R(0), R(0), R(0)};
     if (ok) {
       const int L = plan[k % kPlanRing].len, par = plan[k % kPlanRing].par;
       const Slot<R>* sring = reinterpret_cast<const Slot<R>*>(sweep_smem + s * SB);
@@ -803,28 +1009,37 @@ __global__ void __launch_bounds__(kSweepThreads)
 #pragma unroll 4
       for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
     }
-    acc.tr = warp_sum(acc.tr);
-    acc.ti = warp_sum(acc.ti);
-    acc.nr = warp_sum(acc.nr);
-    acc.ni = warp_sum(acc.ni);
-    if (lane == 0) red[k & 1][wid] = acc;
+    const bool seg_end = k + 1 == nk || plan[(k + 1) % kPlanRing].mode != plan[k % kPlanRing].mode;
+    if (seg_end) {
+      Acc4<R> w4;
+      w4.tr = warp_sum(acc.tr);
+      w4.ti = warp_sum(acc.ti);
+      w4.nr = warp_sum(acc.nr);
+      w4.ni = warp_sum(acc.ni);
+      if (lane == 0) red[k & 1][wid] = w4;
+      acc = {R(0), R(0), R(0), R(0)};
+    }
     stuck = __syncthreads_or(!ok);
     if (stuck) break;
     if (tid == 0) {
       // the stage was read by every thread (barrier above): refill it first
       if (k + kSweepStages < nk)
         sweep_issue<R>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
-      Acc4<R> t = red[k & 1][0];
+      double4 out = make_double4(0.0, 0.0, 0.0, 0.0);
+      if (seg_end) {
+        Acc4<R> t = red[k & 1][0];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) {
-        const Acc4<R> u = red[k & 1][w];
-        t.tr += u.tr;
-        t.ti += u.ti;
-        t.nr += u.nr;
-        t.ni += u.ni;
+        for (int w = 1; w < NW; ++w) {
+          const Acc4<R> u = red[k & 1][w];
+          t.tr += u.tr;
+          t.ti += u.ti;
+          t.nr += u.nr;
+          t.ni += u.ni;
+        }
+        out = make_double4(static_cast<double>(t.tr), static_cast<double>(t.ti), static_cast<double>(t.nr),
+                           static_cast<double>(t.ni));
       }
-      f.partial[c0 + k] = make_double4(static_cast<double>(t.tr), static_cast<double>(t.ti),
-                                       static_cast<double>(t.nr), static_cast<double>(t.ni));
+      f.partial[c0 + k] = out;
     }
   }
   if (stuck && tid == 0) {
@@ -1518,6 +1733,31 @@ static void allow_smem(K kernel, size_t bytes) {
 
 
 static size_t fused_smem(int N) { return static_cast<size_t>(N + N / 2) * sizeof(float2); }
+// cluster pass: column and row buffers (N/C each) and the N2/2 + N1/2 sub-table twiddles
+static size_t cluster_smem(int N) {
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  const int N1 = 1 << (lg / 2), N2 = 1 << (lg - lg / 2);
+  return static_cast<size_t>(2 * (N / kClusterCTAs) + N1 / 2 + N2 / 2) * sizeof(float2);
+}
+
+// Cluster launch of the FP32 spectral pass (one cluster per fault).
+template <class... Args>
+static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCTAs * clusters);
+  cfg.blockDim = dim3(N / (8 * kClusterCTAs));
+  cfg.dynamicSmemBytes = cluster_smem(N);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterCTAs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 template <class R>
 void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
@@ -1525,7 +1765,8 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   const double dt = m_dt * f.dt_min;
   if constexpr (sizeof(R) == 4) {
     if (f.N <= kFusedMaxN) {
-      k_spectral_fused<<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
+      if (f.N >= kClusterMinN) launch_cluster_kernel(k_spectral_cluster, 1, f.N, st, f, pass, m_dt, dt);
+      else k_spectral_fused<<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
       k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
       return;
     }
@@ -1609,7 +1850,8 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
                        cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (N <= kFusedMaxN) {
-      k_spectral_fused_b<<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
+      if (N >= kClusterMinN) launch_cluster_kernel(k_spectral_cluster_b, members, N, st, fs, pass, m_dt);
+      else k_spectral_fused_b<<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
       k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);
       return;
     }
@@ -1632,7 +1874,8 @@ void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cu
 template <class R>
 void configure_batch_kernels(const FftGeom& g) {
   if constexpr (sizeof(R) == 4) {
-    if (g.N <= kFusedMaxN) allow_smem(k_spectral_fused_b, fused_smem(g.N));
+    if (g.N < kClusterMinN) allow_smem(k_spectral_fused_b, fused_smem(g.N));
+    else if (g.N <= kFusedMaxN) allow_smem(k_spectral_cluster_b, cluster_smem(g.N));
   }
   allow_smem(k_col_b<R, false, PRO_PASS>, col_smem<R>(g));
   allow_smem(k_col_b<R, true, PRO_ASSEMBLE>, col_smem<R>(g));
@@ -1733,7 +1976,8 @@ template <class R>
 void configure_kernels(const FftGeom& g) {
   allow_smem(k_sweep<R>, kSweepStages * sweep_stage_bytes<R>());
   if constexpr (sizeof(R) == 4) {
-    if (g.N <= kFusedMaxN) allow_smem(k_spectral_fused, fused_smem(g.N));
+    if (g.N < kClusterMinN) allow_smem(k_spectral_fused, fused_smem(g.N));
+    else if (g.N <= kFusedMaxN) allow_smem(k_spectral_cluster, cluster_smem(g.N));
   }
   const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
   allow_smem(k_col<R, false, PRO_PASS>, cs);

@@ -116,8 +116,12 @@ struct DevFault {
   int* work;                               // next chunk of the history convolution
 };
 
-// Largest N of the single-CTA FP32 spectral pass (N/8 threads).
-constexpr int kFusedMaxN = 8192;
+// One-launch FP32 spectral pass: a single CTA of N/8 threads below
+// kClusterMinN, a cluster of kClusterCTAs CTAs (N/(8 kClusterCTAs) threads
+// each) from kClusterMinN to kFusedMaxN; larger N use the four-kernel path.
+constexpr int kFusedMaxN = 16384;
+constexpr int kClusterMinN = 2048;
+constexpr int kClusterCTAs = 8;
 
 // Host launch wrappers (kernels.cu).
 // History sums AT/AN of a step of m_dt (bulk-async sweep, then per-mode

@@ -100,6 +100,34 @@ def test_full_size_rough_cycle_step():
     g.close()
 
 
+@pytest.mark.parametrize("N", [1024, 2048, 4096, 8192])
+def test_fp32_pass_single_cta_and_cluster(N):
+    # the precision form's one-launch spectral pass: one CTA below 2048,
+    # a cluster of 8 CTAs (distributed shared memory transposes) above;
+    # stepped one call at a time and in the overlapped graph form
+    w = rough_fault(N, 10.0, 3e-3, seed=N)
+    o = oracle_for(w)
+    g1 = gpu_for(w, precision=1)
+    g2 = gpu_for(w, precision=1)
+    prefill(o, g1, seed=N + 1, scale=1e-6)
+    prefill_random(g2, seed=N + 1)  # same seeded history as the oracle's
+    for _ in range(3):
+        assert o.step() == 0
+        g1.step()
+    g2.enqueue(3)
+    assert g2.status()[0] == 0
+    scale = max(np.abs(o.last["tau_el"]).max(), np.abs(o.last["sig_el"]).max())
+    for g in (g1, g2):
+        s = g.get_state()
+        for k, ref in (("tau_el", o.last["tau_el"]), ("sigma_el", o.last["sig_el"])):
+            assert np.abs(s[k] - ref).max() < 1e-4 * scale, k
+        err = compare(o, g)
+        for k in ("delta", "V", "theta"):
+            assert err[k] < 1e-4, (k, err)
+    g1.close()
+    g2.close()
+
+
 # FP64: the oracle's weights carry its own kernel rounding (W = 1 - int_0^x
 # gives a few ulps of 1, times s^2 in the kernels: up to 1e-11 at s = 200)
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-6)])
