@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include <math_constants.h>
@@ -281,18 +282,24 @@ __device__ __forceinline__ void dft4(float2 (&v)[8]) {
   v[O + 2] = t;
 }
 
-// One Stockham stage over buf (length N, nth = N/8 threads).
-template <int R, bool INV>
-__device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, int N, int Ns, int tid, int nth) {
+// One Stockham stage over buf (length L = 2^LGL, L/8 threads, tid < L/8)
+// after sub-transforms of length Ns = 2^lgNs; all index arithmetic is
+// shifts and masks of compile-time sizes.
+template <int R, bool INV, int LGL>
+__device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, int lgNs, int tid) {
+  constexpr int L = 1 << LGL;
   constexpr int NB = 8 / R;  // butterflies per thread
-  const int stride = N / R;
-  const int half = N >> 1;
+  constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+  constexpr int nth = L / 8;
+  constexpr int stride = L / R;
+  constexpr int half = L >> 1;
+  const int Ns = 1 << lgNs;
   float2 v[8];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int j = tid + q * nth;
     const int k = j & (Ns - 1);
-    const int tstep = k * (N / (Ns * R));
+    const int tstep = k << (LGL - lgNs - LGR);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       float2 x = buf[j + r * stride];
@@ -319,19 +326,20 @@ __device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, in
   for (int q = 0; q < NB; ++q) {
     const int j = tid + q * nth;
     const int k = j & (Ns - 1);
-    const int base = (j - k) * R + k;
+    const int base = ((j - k) << LGR) + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[q * R + r];
   }
   __syncthreads();
 }
 
-template <bool INV>
-__device__ __forceinline__ void fft_r8(float2* buf, const float2* tw, int N, int lgN, int tid, int nth) {
-  int Ns = 1;
-  for (int s = 0; s < lgN / 3; ++s, Ns *= 8) stockham_stage<8, INV>(buf, tw, N, Ns, tid, nth);
-  if (lgN % 3 == 2) stockham_stage<4, INV>(buf, tw, N, Ns, tid, nth);
-  if (lgN % 3 == 1) stockham_stage<2, INV>(buf, tw, N, Ns, tid, nth);
+// Forward (INV = false) or unscaled inverse FFT of length 2^LGL in buf.
+template <bool INV, int LGL>
+__device__ __forceinline__ void fft_r8(float2* buf, const float2* tw, int tid) {
+#pragma unroll
+  for (int s = 0; s < LGL / 3; ++s) stockham_stage<8, INV, LGL>(buf, tw, 3 * s, tid);
+  if constexpr (LGL % 3 == 2) stockham_stage<4, INV, LGL>(buf, tw, 3 * (LGL / 3), tid);
+  if constexpr (LGL % 3 == 1) stockham_stage<2, INV, LGL>(buf, tw, 3 * (LGL / 3), tid);
 }
 
 // Assembly of the mode pair (m, N-m) of the precision form from the packed
@@ -392,18 +400,18 @@ __device__ __forceinline__ void assemble_pair32(const DevFault<float>& f, int m,
 // inverse FFT, scaled output tau_el + i sigma_el.  Pass 2 leaves U, Q of the
 // step (FP32) for the commit.  Shared memory: N complex values and N/2
 // twiddles.
+template <int LGN>
 __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
   using C = float2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = f.N, half = N >> 1;
+  constexpr int N = 1 << LGN, half = N >> 1, nth = N / 8;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N;
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x;
   __shared__ unsigned s_skip;
   if (tid == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
-  const int lg = 31 - __clz(N);
   const bool pow2 = (m_dt & (m_dt - 1)) == 0;
   const int p2 = pow2 ? 31 - __clz(m_dt) : 0;
   // nth = N/8: each thread owns 4 twiddles, 8 inputs and at most 5 modes
@@ -435,7 +443,7 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
     for (int q = 0; q < 8; ++q) buf[tid + q * nth] = zv[q];
   }
   __syncthreads();
-  fft_r8<false>(buf, tw, N, lg, tid, nth);
+  fft_r8<false, LGN>(buf, tw, tid);
 #pragma unroll 1
   for (int q = 0; q < kMpt; ++q) {
     const int m = tid + q * nth;
@@ -446,7 +454,7 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
     if (m > 0 && m < half) buf[N - m] = Yc;
   }
   __syncthreads();
-  fft_r8<true>(buf, tw, N, lg, tid, nth);
+  fft_r8<true, LGN>(buf, tw, tid);
   const float scale = 1.0f / static_cast<float>(N);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -455,15 +463,17 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   }
 }
 
-__global__ void __launch_bounds__(1024) k_spectral_fused(const __grid_constant__ DevFault<float> f, int pass,
-                                                         int m_dt, double dt) {
-  spectral_fused_body(f, pass, m_dt, dt);
+template <int LGN>
+__global__ void __launch_bounds__((1 << LGN) / 8) k_spectral_fused(const __grid_constant__ DevFault<float> f,
+                                                                   int pass, int m_dt, double dt) {
+  spectral_fused_body<LGN>(f, pass, m_dt, dt);
 }
 
-__global__ void __launch_bounds__(1024) k_spectral_fused_b(const DevFault<float>* __restrict__ fs, int pass,
-                                                           int m_dt) {
+template <int LGN>
+__global__ void __launch_bounds__((1 << LGN) / 8) k_spectral_fused_b(const DevFault<float>* __restrict__ fs,
+                                                                     int pass, int m_dt) {
   const DevFault<float>& f = fs[blockIdx.x];
-  spectral_fused_body(f, pass, m_dt, m_dt * f.dt_min);
+  spectral_fused_body<LGN>(f, pass, m_dt, m_dt * f.dt_min);
 }
 
 
@@ -479,21 +489,14 @@ __global__ void __launch_bounds__(1024) k_spectral_fused_b(const DevFault<float>
 // FFTs of the rows; assembly of each pair (m, N-m) in place; inverse: row
 // FFTs, twiddle w_N^{-n1 k2}, scatter back to the column owners, barrier,
 // column FFTs, output.  N/(8C) threads per CTA, 8 values each per stage.
-struct ClusterGeom {
-  int N1, N2, lg1, lg2, cols, rows;
+template <int LGN>
+struct CGeom {
+  static constexpr int N = 1 << LGN;
+  static constexpr int lg1 = LGN / 2, lg2 = LGN - LGN / 2;
+  static constexpr int N1 = 1 << lg1, N2 = 1 << lg2;
+  static constexpr int cols = N1 / kClusterCTAs, rows = N2 / kClusterCTAs;
+  static constexpr int nth = N / (8 * kClusterCTAs);
 };
-
-__device__ __forceinline__ ClusterGeom cluster_geom(int N) {
-  ClusterGeom g;
-  const int lg = 31 - __clz(N);
-  g.lg1 = lg / 2;
-  g.lg2 = lg - g.lg1;
-  g.N1 = 1 << g.lg1;
-  g.N2 = 1 << g.lg2;
-  g.cols = g.N1 / kClusterCTAs;
-  g.rows = g.N2 / kClusterCTAs;
-  return g;
-}
 
 // Index of row k2 in the pair-adjacent sequence 0, N2/2, 1, N2-1, 2, ...
 __device__ __forceinline__ int row_seq(int k2, int N2) {
@@ -533,36 +536,38 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
-// B transforms of length L (L/8 threads each) side by side in buf.
-template <bool INV>
-__device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int L, int lgL, int tid) {
-  const int per = L >> 3;
-  fft_r8<INV>(buf + (tid / per) * L, tw, L, lgL, tid % per, per);
+// Transforms of length 2^LGL (2^LGL/8 threads each) side by side in buf.
+template <bool INV, int LGL>
+__device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int tid) {
+  constexpr int per = (1 << LGL) >> 3;
+  fft_r8<INV, LGL>(buf + (tid / per) * (1 << LGL), tw, tid % per);
 }
 
+template <int LGN>
 __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
+  using G = CGeom<LGN>;
   const unsigned c = cluster_rank();
-  const int N = f.N, half = N >> 1;
-  const ClusterGeom g = cluster_geom(N);
+  constexpr int N = G::N, half = N >> 1;
   const int per = N / kClusterCTAs;  // elements per CTA (8 per thread)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* colbuf = reinterpret_cast<float2*>(smem_raw);  // [cols][N2]
   float2* rowbuf = colbuf + per;                          // [rows][N1]
   float2* twc = rowbuf + per;                             // w_N2^j, j < N2/2
-  float2* twr = twc + (g.N2 >> 1);                        // w_N1^j, j < N1/2
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int n1_0 = static_cast<int>(c) * g.cols;
-  const int q0 = static_cast<int>(c) * g.rows;  // first sequence index of this CTA's rows
+  float2* twr = twc + (G::N2 >> 1);                        // w_N1^j, j < N1/2
+  const int tid = threadIdx.x;
+  constexpr int nth = G::nth;
+  const int n1_0 = static_cast<int>(c) * G::cols;
+  const int q0 = static_cast<int>(c) * G::rows;  // first sequence index of this CTA's rows
   // every CTA of the cluster runs before any remote store (arrive now, wait later)
   cluster_arrive_relaxed();
-  for (int j = tid; j < (g.N2 >> 1); j += nth) twc[j] = f.tw[j * g.N1];
-  for (int j = tid; j < (g.N1 >> 1); j += nth) twr[j] = f.tw[j * g.N2];
+  for (int j = tid; j < (G::N2 >> 1); j += nth) twc[j] = f.tw[j * G::N1];
+  for (int j = tid; j < (G::N1 >> 1); j += nth) twr[j] = f.tw[j * G::N2];
   // assembly inputs of this CTA's modes into L1 behind the forward FFT
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
-    const int k2 = seq_row(q0 + e / g.N1, g.N2);
-    const int m = k2 + g.N2 * (e % g.N1);
+    const int k2 = seq_row(q0 + e / G::N1, G::N2);
+    const int m = k2 + G::N2 * (e % G::N1);
     if (m > 0 && m <= half) {
       asm volatile("prefetch.global.L1 [%0];" ::"l"(f.dhat32 + m));
       asm volatile("prefetch.global.L1 [%0];" ::"l"(f.khat32 + m));
@@ -577,83 +582,85 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int e = tid + q * nth;
-      v[q] = zin[(n1_0 + e % g.cols) + g.N1 * (e / g.cols)];
+      v[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int e = tid + q * nth;
-      colbuf[(e % g.cols) * g.N2 + e / g.cols] = v[q];
+      colbuf[(e % G::cols) * G::N2 + e / G::cols] = v[q];
     }
   }
   __syncthreads();
-  fft_r8_batch<false>(colbuf, twc, g.N2, g.lg2, tid);
+  fft_r8_batch<false, G::lg2>(colbuf, twc, tid);
   cluster_wait();
   // twiddle w_N^{n1 k2}, scatter to the row owners
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
-    const int b = e / g.N2, k2 = e % g.N2;
+    const int b = e / G::N2, k2 = e % G::N2;
     const float2 val = f2mul(colbuf[e], tw_full(f.tw, (n1_0 + b) * k2, half, false));
-    const int s = row_seq(k2, g.N2);
-    st_cluster(cluster_map(rowbuf + (s % g.rows) * g.N1 + n1_0 + b, static_cast<unsigned>(s / g.rows)), val);
+    const int s = row_seq(k2, G::N2);
+    st_cluster(cluster_map(rowbuf + (s % G::rows) * G::N1 + n1_0 + b, static_cast<unsigned>(s / G::rows)), val);
   }
   cluster_arrive();
   cluster_wait();
-  fft_r8_batch<false>(rowbuf, twr, g.N1, g.lg1, tid);
+  fft_r8_batch<false, G::lg1>(rowbuf, twr, tid);
   // assembly of the pairs (m, N-m) held by this CTA, in place
 #pragma unroll 1
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
-    const int r = e / g.N1, k1 = e % g.N1;
-    const int k2 = seq_row(q0 + r, g.N2);
-    const int m = k2 + g.N2 * k1;
+    const int r = e / G::N1, k1 = e % G::N1;
+    const int k2 = seq_row(q0 + r, G::N2);
+    const int m = k2 + G::N2 * k1;
     if (m > half) continue;
     int k2p, k1p;
     if (k2 == 0) {
       k2p = 0;
-      k1p = (g.N1 - k1) & (g.N1 - 1);
+      k1p = (G::N1 - k1) & (G::N1 - 1);
     } else {
-      k2p = (k2 == (g.N2 >> 1)) ? k2 : g.N2 - k2;
-      k1p = g.N1 - 1 - k1;
+      k2p = (k2 == (G::N2 >> 1)) ? k2 : G::N2 - k2;
+      k1p = G::N1 - 1 - k1;
     }
-    const int ep = (row_seq(k2p, g.N2) - q0) * g.N1 + k1p;
+    const int ep = (row_seq(k2p, G::N2) - q0) * G::N1 + k1p;
     float2 Ym, Yc;
     assemble_pair32(f, m, rowbuf[e], rowbuf[ep], pass, m_dt, dt, &Ym, &Yc);
     rowbuf[e] = Ym;
     if (ep != e) rowbuf[ep] = Yc;
   }
   __syncthreads();
-  fft_r8_batch<true>(rowbuf, twr, g.N1, g.lg1, tid);
+  fft_r8_batch<true, G::lg1>(rowbuf, twr, tid);
   // twiddle w_N^{-n1 k2}, scatter back to the column owners
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
-    const int r = e / g.N1, n1 = e % g.N1;
-    const int k2 = seq_row(q0 + r, g.N2);
+    const int r = e / G::N1, n1 = e % G::N1;
+    const int k2 = seq_row(q0 + r, G::N2);
     const float2 val = f2mul(rowbuf[e], tw_full(f.tw, n1 * k2, half, true));
-    st_cluster(cluster_map(colbuf + (n1 % g.cols) * g.N2 + k2, static_cast<unsigned>(n1 / g.cols)), val);
+    st_cluster(cluster_map(colbuf + (n1 % G::cols) * G::N2 + k2, static_cast<unsigned>(n1 / G::cols)), val);
   }
   cluster_arrive();
   cluster_wait();
-  fft_r8_batch<true>(colbuf, twc, g.N2, g.lg2, tid);
+  fft_r8_batch<true, G::lg2>(colbuf, twc, tid);
   const float scale = 1.0f / static_cast<float>(N);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
-    const float2 v = colbuf[(e % g.cols) * g.N2 + e / g.cols];
-    f.y[(n1_0 + e % g.cols) + g.N1 * (e / g.cols)] = make_float2(v.x * scale, v.y * scale);
+    const float2 v = colbuf[(e % G::cols) * G::N2 + e / G::cols];
+    f.y[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)] = make_float2(v.x * scale, v.y * scale);
   }
 }
 
-__global__ void __launch_bounds__(256) k_spectral_cluster(const __grid_constant__ DevFault<float> f, int pass,
-                                                           int m_dt, double dt) {
-  spectral_cluster_body(f, pass, m_dt, dt);
+template <int LGN>
+__global__ void __launch_bounds__(CGeom<LGN>::nth) k_spectral_cluster(const __grid_constant__ DevFault<float> f,
+                                                                       int pass, int m_dt, double dt) {
+  spectral_cluster_body<LGN>(f, pass, m_dt, dt);
 }
 
-__global__ void __launch_bounds__(256) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs, int pass,
-                                                             int m_dt) {
+template <int LGN>
+__global__ void __launch_bounds__(CGeom<LGN>::nth) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs,
+                                                                         int pass, int m_dt) {
   const DevFault<float>& f = fs[blockIdx.x / kClusterCTAs];
-  spectral_cluster_body(f, pass, m_dt, m_dt * f.dt_min);
+  spectral_cluster_body<LGN>(f, pass, m_dt, m_dt * f.dt_min);
 }
 
 // Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
@@ -1410,21 +1417,48 @@ __global__ void __launch_bounds__(32) k_newton_b(const DevFault<R>* __restrict__
 template <class R>
 __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, double dt, int lag_p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (*f.status) return;
-  if (i < f.N) {
-    const double v = f.V2[i];
-    f.V[i] = v;
-    f.xV[i] = f.x2[i];
-    f.psi[i] = f.psi2[i];
-    f.th[i] = f.th2[i];
-    f.thd[i] = f.thd2[i];
-    f.delta[i] = f.delta2[i];
-    if (f.zin1) f.zin1[i] = make_float2(static_cast<float>(v), static_cast<float>(f.kappa[i] * v));
+  // every load first (one memory latency), the status decision, then stores
+  const unsigned status = *f.status;
+  const bool el = i < f.N, md = i < f.nmodes;
+  double v = 0.0, x2 = 0.0, psi2 = 0.0, th2 = 0.0, thd2 = 0.0, d2 = 0.0, kap = 0.0;
+  if (el) {
+    v = f.V2[i];
+    x2 = f.x2[i];
+    psi2 = f.psi2[i];
+    th2 = f.th2[i];
+    thd2 = f.thd2[i];
+    d2 = f.delta2[i];
+    if (f.zin1) kap = f.kappa[i];
   }
-  if (i < f.nmodes) {
-    const double2 U = f.U2f ? make_double2(f.U2f[i].x, f.U2f[i].y) : f.U2[i];
-    const double2 Q = f.Q2f ? make_double2(f.Q2f[i].x, f.Q2f[i].y) : f.Q2[i];
-    double2 D = f.dhat[i], K = f.khat[i];
+  double2 U = make_double2(0.0, 0.0), Q = U, D = U, K = U, T = U, Nn = U, w1 = U, w0 = U;
+  int Rn = 0, h = 0;
+  int64_t roff = 0;
+  if (md) {
+    U = f.U2f ? make_double2(f.U2f[i].x, f.U2f[i].y) : f.U2[i];
+    Q = f.Q2f ? make_double2(f.Q2f[i].x, f.Q2f[i].y) : f.Q2[i];
+    D = f.dhat[i];
+    K = f.khat[i];
+    Rn = f.Rn[i];
+    roff = f.ring_off[i];
+    h = f.head[i];
+    if (lag_p >= 0) {
+      T = f.BT[i];
+      Nn = f.BN[i];
+      w1 = f.w0pow[static_cast<size_t>(i) * kPow2Slots + lag_p + 1];
+      w0 = f.w0pow[static_cast<size_t>(i) * kPow2Slots + lag_p];
+    }
+  }
+  if (status) return;
+  if (el) {
+    f.V[i] = v;
+    f.xV[i] = x2;
+    f.psi[i] = psi2;
+    f.th[i] = th2;
+    f.thd[i] = thd2;
+    f.delta[i] = d2;
+    if (f.zin1) f.zin1[i] = make_float2(static_cast<float>(v), static_cast<float>(kap * v));
+  }
+  if (md) {
     D.x += dt * U.x;
     D.y += dt * U.y;
     K.x += dt * Q.x;
@@ -1435,21 +1469,22 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
       f.dhat32[i] = make_float2(static_cast<float>(D.x), static_cast<float>(D.y));
       f.khat32[i] = make_float2(static_cast<float>(K.x), static_cast<float>(K.y));
     }
-    const int Rn = f.Rn[i];
+    // the value the ring holds (FP32 in the precision form)
+    double2 sT = U, sN = Q;
     if (Rn > 0) {
-      Slot<R> s;
+      Slot<R> sl;
       if constexpr (sizeof(R) == 8) {
-        s.t = U;
-        s.n = Q;
+        sl.t = U;
+        sl.n = Q;
       } else {
-        s = make_float4(static_cast<float>(U.x), static_cast<float>(U.y), static_cast<float>(Q.x),
-                        static_cast<float>(Q.y));
+        sl = make_float4(static_cast<float>(U.x), static_cast<float>(U.y), static_cast<float>(Q.x),
+                         static_cast<float>(Q.y));
+        sT = make_double2(sl.x, sl.y);
+        sN = make_double2(sl.z, sl.w);
       }
-      Slot<R>* ring = f.ring + f.ring_off[i];
-      int h = f.head[i];
       if (m_dt == 1) {
         h = (h == 0) ? Rn - 1 : h - 1;
-        ring[h] = s;
+        f.ring[roff + h] = sl;
       } else {
         // the m_dt copies were written by k_push_multi; move the head
         h = static_cast<int>(((h - static_cast<int64_t>(m_dt)) % Rn + Rn) % Rn);
@@ -1459,20 +1494,8 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
     if (lag_p >= 0) {
       // overlapped form: the next step (same m_dt) sees this step's slot at
       // lags m_dt .. 2 m_dt - 1 and the older slots through BT/BN
-      double2 T = f.BT[i], Nn = f.BN[i];
       if (Rn > 0) {
-        const double2 w1 = f.w0pow[static_cast<size_t>(i) * kPow2Slots + lag_p + 1];
-        const double2 w0 = f.w0pow[static_cast<size_t>(i) * kPow2Slots + lag_p];
         const double wT = w1.x - w0.x, wN = w1.y - w0.y;
-        double2 sT, sN;
-        if constexpr (sizeof(R) == 8) {
-          sT = U;
-          sN = Q;
-        } else {
-          // the value the ring holds (FP32)
-          sT = make_double2(static_cast<float>(U.x), static_cast<float>(U.y));
-          sN = make_double2(static_cast<float>(Q.x), static_cast<float>(Q.y));
-        }
         T.x = fma(wT, sT.x, T.x);
         T.y = fma(wT, sT.y, T.y);
         Nn.x = fma(wN, sN.x, Nn.x);
@@ -1741,6 +1764,27 @@ static size_t cluster_smem(int N) {
   return static_cast<size_t>(2 * (N / kClusterCTAs) + N1 / 2 + N2 / 2) * sizeof(float2);
 }
 
+// fn(std::integral_constant<int, log2 N>) for the sizes of the one-launch
+// FP32 spectral pass (16 <= N <= kFusedMaxN).
+template <class F>
+static void with_lgn(int N, F&& fn) {
+  switch (31 - __builtin_clz(static_cast<unsigned>(N))) {
+    case 4: fn(std::integral_constant<int, 4>{}); break;
+    case 5: fn(std::integral_constant<int, 5>{}); break;
+    case 6: fn(std::integral_constant<int, 6>{}); break;
+    case 7: fn(std::integral_constant<int, 7>{}); break;
+    case 8: fn(std::integral_constant<int, 8>{}); break;
+    case 9: fn(std::integral_constant<int, 9>{}); break;
+    case 10: fn(std::integral_constant<int, 10>{}); break;
+    case 11: fn(std::integral_constant<int, 11>{}); break;
+    case 12: fn(std::integral_constant<int, 12>{}); break;
+    case 13: fn(std::integral_constant<int, 13>{}); break;
+    case 14: fn(std::integral_constant<int, 14>{}); break;
+    default: break;
+  }
+}
+static_assert(kFusedMaxN == 1 << 14 && kClusterMinN == 1 << 11, "with_lgn covers the one-launch pass sizes");
+
 // Cluster launch of the FP32 spectral pass (one cluster per fault).
 template <class... Args>
 static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, Args... args) {
@@ -1765,8 +1809,14 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   const double dt = m_dt * f.dt_min;
   if constexpr (sizeof(R) == 4) {
     if (f.N <= kFusedMaxN) {
-      if (f.N >= kClusterMinN) launch_cluster_kernel(k_spectral_cluster, 1, f.N, st, f, pass, m_dt, dt);
-      else k_spectral_fused<<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
+      with_lgn(f.N, [&](auto lg) {
+        constexpr int LG = decltype(lg)::value;
+        if constexpr ((1 << LG) >= kClusterMinN) {
+          launch_cluster_kernel(k_spectral_cluster<LG>, 1, f.N, st, f, pass, m_dt, dt);
+        } else {
+          k_spectral_fused<LG><<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
+        }
+      });
       k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
       return;
     }
@@ -1850,8 +1900,14 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
                        cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (N <= kFusedMaxN) {
-      if (N >= kClusterMinN) launch_cluster_kernel(k_spectral_cluster_b, members, N, st, fs, pass, m_dt);
-      else k_spectral_fused_b<<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
+      with_lgn(N, [&](auto lg) {
+        constexpr int LG = decltype(lg)::value;
+        if constexpr ((1 << LG) >= kClusterMinN) {
+          launch_cluster_kernel(k_spectral_cluster_b<LG>, members, N, st, fs, pass, m_dt);
+        } else {
+          k_spectral_fused_b<LG><<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
+        }
+      });
       k_newton_b<R><<<dim3((N + 31) / 32, members), 32, 0, st>>>(fs, pass, m_dt);
       return;
     }
@@ -1874,8 +1930,12 @@ void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cu
 template <class R>
 void configure_batch_kernels(const FftGeom& g) {
   if constexpr (sizeof(R) == 4) {
-    if (g.N < kClusterMinN) allow_smem(k_spectral_fused_b, fused_smem(g.N));
-    else if (g.N <= kFusedMaxN) allow_smem(k_spectral_cluster_b, cluster_smem(g.N));
+    if (g.N <= kFusedMaxN)
+      with_lgn(g.N, [&](auto lg) {
+        constexpr int LG = decltype(lg)::value;
+        if constexpr ((1 << LG) >= kClusterMinN) allow_smem(k_spectral_cluster_b<LG>, cluster_smem(g.N));
+        else allow_smem(k_spectral_fused_b<LG>, fused_smem(g.N));
+      });
   }
   allow_smem(k_col_b<R, false, PRO_PASS>, col_smem<R>(g));
   allow_smem(k_col_b<R, true, PRO_ASSEMBLE>, col_smem<R>(g));
@@ -1976,8 +2036,12 @@ template <class R>
 void configure_kernels(const FftGeom& g) {
   allow_smem(k_sweep<R>, kSweepStages * sweep_stage_bytes<R>());
   if constexpr (sizeof(R) == 4) {
-    if (g.N < kClusterMinN) allow_smem(k_spectral_fused, fused_smem(g.N));
-    else if (g.N <= kFusedMaxN) allow_smem(k_spectral_cluster, cluster_smem(g.N));
+    if (g.N <= kFusedMaxN)
+      with_lgn(g.N, [&](auto lg) {
+        constexpr int LG = decltype(lg)::value;
+        if constexpr ((1 << LG) >= kClusterMinN) allow_smem(k_spectral_cluster<LG>, cluster_smem(g.N));
+        else allow_smem(k_spectral_fused<LG>, fused_smem(g.N));
+      });
   }
   const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
   allow_smem(k_col<R, false, PRO_PASS>, cs);
