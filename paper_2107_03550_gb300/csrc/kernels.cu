@@ -342,12 +342,41 @@ __device__ __forceinline__ void fft_r8(float2* buf, const float2* tw, int tid) {
   if constexpr (LGL % 3 == 1) stockham_stage<2, INV, LGL>(buf, tw, 3 * (LGL / 3), tid);
 }
 
+// Per-mode inputs of the precision form's assembly: running sums F[delta],
+// F[kappa delta], history sums, and the coefficients S dt + mu w0 (T, N) of
+// the current interval (from the power-of-two table, or summed in FP64 for
+// other step lengths; the near-cancelling combination is done in FP64).
+struct ModeIn {
+  float2 D, K, AT, AN, C;
+};
+
+__device__ __forceinline__ ModeIn load_mode_in(const DevFault<float>& f, int m, int m_dt, double dt) {
+  ModeIn in;
+  in.D = f.dhat32[m];
+  in.K = f.khat32[m];
+  in.AT = f.AT32[m];
+  in.AN = f.AN32[m];
+  if ((m_dt & (m_dt - 1)) == 0) {
+    in.C = f.c0pow[static_cast<size_t>(m) * kPow2Slots + (31 - __clz(m_dt))];
+  } else {
+    double w0T = 0.0, w0N = 0.0;
+    const int lim = min(m_dt, f.Mn[m]);
+    for (int j = 0; j < lim; ++j) {
+      const W2<float> w = f.w[f.w_off[m] + j];
+      w0T += w.x;
+      w0N += w.y;
+    }
+    in.C = make_float2(static_cast<float>(f.S * dt + f.mu * w0T), static_cast<float>(f.S * dt + f.mu * w0N));
+  }
+  return in;
+}
+
 // Assembly of the mode pair (m, N-m) of the precision form from the packed
 // spectrum Zm = Z[m], Zc = Z[(N-m) mod N] of Vbar + i kappa Vbar (Sec. 3.1,
 // Sec. 3.3 step (2)): returns Y[m] and Y[N-m] of tau_el + i sigma_el and, in
-// pass 2, leaves U, Q of mode m for the commit.
+// pass 2, leaves U, Q of mode m for the commit.  FP32 products.
 __device__ __forceinline__ void assemble_pair32(const DevFault<float>& f, int m, float2 Zm, float2 Zc, int pass,
-                                                int m_dt, double dt, float2* Ym, float2* Yc) {
+                                                const ModeIn& in, float2* Ym, float2* Yc) {
   const int N = f.N, half = N >> 1;
   const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
   const float Qx = 0.5f * (Zm.y + Zc.y), Qy = -0.5f * (Zm.x - Zc.x);
@@ -356,29 +385,12 @@ __device__ __forceinline__ void assemble_pair32(const DevFault<float>& f, int m,
     const float mu = static_cast<float>(f.mu);
     const float S = static_cast<float>(f.S);
     const float k = static_cast<float>(kTwoPi / f.L) * static_cast<float>(m);
-    float cT, cN;
-    if ((m_dt & (m_dt - 1)) == 0) {
-      const float2 c = f.c0pow[static_cast<size_t>(m) * kPow2Slots + (31 - __clz(m_dt))];
-      cT = c.x;
-      cN = c.y;
-    } else {
-      double w0T = 0.0, w0N = 0.0;
-      const int lim = min(m_dt, f.Mn[m]);
-      for (int j = 0; j < lim; ++j) {
-        const W2<float> w = f.w[f.w_off[m] + j];
-        w0T += w.x;
-        w0N += w.y;
-      }
-      cT = static_cast<float>(f.S * dt + f.mu * w0T);
-      cN = static_cast<float>(f.S * dt + f.mu * w0N);
-    }
-    // S dt + mu w0 was combined in FP64 (near cancellation); FP32 products
-    const float2 D = f.dhat32[m], K = f.khat32[m], AT = f.AT32[m], AN = f.AN32[m];
-    tr = -k * (S * D.x + cT * Ux + mu * AT.x);
-    ti = (m < half) ? -k * (S * D.y + cT * Uy + mu * AT.y) : 0.f;
+    const float cT = in.C.x, cN = in.C.y;
+    tr = -k * (S * in.D.x + cT * Ux + mu * in.AT.x);
+    ti = (m < half) ? -k * (S * in.D.y + cT * Uy + mu * in.AT.y) : 0.f;
     if (m < half) {
-      const float xr = S * K.x + cN * Qx + mu * AN.x;
-      const float xi = S * K.y + cN * Qy + mu * AN.y;
+      const float xr = S * in.K.x + cN * Qx + mu * in.AN.x;
+      const float xi = S * in.K.y + cN * Qy + mu * in.AN.y;
       sr = xi;
       si = -xr;
     }
@@ -412,23 +424,15 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   if (tid == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
-  const bool pow2 = (m_dt & (m_dt - 1)) == 0;
-  const int p2 = pow2 ? 31 - __clz(m_dt) : 0;
   // nth = N/8: each thread owns 4 twiddles, 8 inputs and at most 5 modes
-  // (m = tid + q nth <= N/2) of the assembly.  Global loads are issued in
-  // batches (one memory latency each), the assembly inputs prefetched into
-  // L1 behind the forward FFT.
+  // (m = tid + q nth <= N/2) of the assembly; every global input is loaded
+  // up front (one memory latency), into registers.
   constexpr int kMpt = 5;
+  ModeIn min_[kMpt];
 #pragma unroll
   for (int q = 0; q < kMpt; ++q) {
     const int m = tid + q * nth;
-    if (m > 0 && m <= half) {
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.dhat32 + m));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.khat32 + m));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AT32 + m));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AN32 + m));
-      if (pow2) asm volatile("prefetch.global.L1 [%0];" ::"l"(f.c0pow + static_cast<size_t>(m) * kPow2Slots + p2));
-    }
+    if (m <= half) min_[q] = load_mode_in(f, m, m_dt, dt);
   }
   {
     const C* zin = pass == 1 ? f.zin1 : f.zin2;
@@ -444,14 +448,15 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   }
   __syncthreads();
   fft_r8<false, LGN>(buf, tw, tid);
-#pragma unroll 1
+#pragma unroll
   for (int q = 0; q < kMpt; ++q) {
     const int m = tid + q * nth;
-    if (m > half) break;
-    C Ym, Yc;
-    assemble_pair32(f, m, buf[m], buf[(N - m) & (N - 1)], pass, m_dt, dt, &Ym, &Yc);
-    buf[m] = Ym;
-    if (m > 0 && m < half) buf[N - m] = Yc;
+    if (m <= half) {
+      C Ym, Yc;
+      assemble_pair32(f, m, buf[m], buf[(N - m) & (N - 1)], pass, min_[q], &Ym, &Yc);
+      buf[m] = Ym;
+      if (m > 0 && m < half) buf[N - m] = Yc;
+    }
   }
   __syncthreads();
   fft_r8<true, LGN>(buf, tw, tid);
@@ -547,48 +552,46 @@ template <int LGN>
 __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
   using G = CGeom<LGN>;
   const unsigned c = cluster_rank();
-  constexpr int N = G::N, half = N >> 1;
-  const int per = N / kClusterCTAs;  // elements per CTA (8 per thread)
+  constexpr int N = G::N, half = N >> 1, nth = G::nth;
+  constexpr int per = N / kClusterCTAs;  // elements per CTA (8 per thread)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* colbuf = reinterpret_cast<float2*>(smem_raw);  // [cols][N2]
   float2* rowbuf = colbuf + per;                          // [rows][N1]
   float2* twc = rowbuf + per;                             // w_N2^j, j < N2/2
-  float2* twr = twc + (G::N2 >> 1);                        // w_N1^j, j < N1/2
+  float2* twr = twc + (G::N2 >> 1);                       // w_N1^j, j < N1/2
   const int tid = threadIdx.x;
-  constexpr int nth = G::nth;
   const int n1_0 = static_cast<int>(c) * G::cols;
   const int q0 = static_cast<int>(c) * G::rows;  // first sequence index of this CTA's rows
   // every CTA of the cluster runs before any remote store (arrive now, wait later)
   cluster_arrive_relaxed();
-  for (int j = tid; j < (G::N2 >> 1); j += nth) twc[j] = f.tw[j * G::N1];
-  for (int j = tid; j < (G::N1 >> 1); j += nth) twr[j] = f.tw[j * G::N2];
-  // assembly inputs of this CTA's modes into L1 behind the forward FFT
+  // every global input up front, in registers (one memory latency): the
+  // pass input, the four-step twiddles of both directions, the sub-table
+  // twiddles and the assembly inputs of this CTA's primary modes
+  const float2* zin = pass == 1 ? f.zin1 : f.zin2;
+  float2 z[8], wf[8], wi[8];
+  ModeIn min_[8];
+  float2 tcv = make_float2(0.f, 0.f), trv = tcv;
+  if (tid < (G::N2 >> 1)) tcv = f.tw[tid * G::N1];
+  if (tid < (G::N1 >> 1)) trv = f.tw[tid * G::N2];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
+    // input: column element (b = e mod cols, n2 = e / cols), runs of cols n1
+    z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
+    // forward twiddle of column element e = b N2 + k2
+    wf[q] = tw_full(f.tw, (n1_0 + e / G::N2) * (e % G::N2), half, false);
+    // inverse twiddle and assembly input of row element e = r N1 + k1
     const int k2 = seq_row(q0 + e / G::N1, G::N2);
+    wi[q] = tw_full(f.tw, (e % G::N1) * k2, half, true);
     const int m = k2 + G::N2 * (e % G::N1);
-    if (m > 0 && m <= half) {
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.dhat32 + m));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.khat32 + m));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AT32 + m));
-      asm volatile("prefetch.global.L1 [%0];" ::"l"(f.AN32 + m));
-    }
+    if (m <= half) min_[q] = load_mode_in(f, m, m_dt, dt);
   }
-  {
-    // input columns: consecutive threads take consecutive n1 (runs of cols)
-    const float2* zin = pass == 1 ? f.zin1 : f.zin2;
-    float2 v[8];
+  if (tid < (G::N2 >> 1)) twc[tid] = tcv;
+  if (tid < (G::N1 >> 1)) twr[tid] = trv;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = tid + q * nth;
-      v[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = tid + q * nth;
-      colbuf[(e % G::cols) * G::N2 + e / G::cols] = v[q];
-    }
+  for (int q = 0; q < 8; ++q) {
+    const int e = tid + q * nth;
+    colbuf[(e % G::cols) * G::N2 + e / G::cols] = z[q];
   }
   __syncthreads();
   fft_r8_batch<false, G::lg2>(colbuf, twc, tid);
@@ -598,34 +601,35 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
     const int b = e / G::N2, k2 = e % G::N2;
-    const float2 val = f2mul(colbuf[e], tw_full(f.tw, (n1_0 + b) * k2, half, false));
-    const int s = row_seq(k2, G::N2);
-    st_cluster(cluster_map(rowbuf + (s % G::rows) * G::N1 + n1_0 + b, static_cast<unsigned>(s / G::rows)), val);
+    const float2 val = f2mul(colbuf[e], wf[q]);
+    const int sq = row_seq(k2, G::N2);
+    st_cluster(cluster_map(rowbuf + (sq % G::rows) * G::N1 + n1_0 + b, static_cast<unsigned>(sq / G::rows)), val);
   }
   cluster_arrive();
   cluster_wait();
   fft_r8_batch<false, G::lg1>(rowbuf, twr, tid);
   // assembly of the pairs (m, N-m) held by this CTA, in place
-#pragma unroll 1
+#pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int e = tid + q * nth;
     const int r = e / G::N1, k1 = e % G::N1;
     const int k2 = seq_row(q0 + r, G::N2);
     const int m = k2 + G::N2 * k1;
-    if (m > half) continue;
-    int k2p, k1p;
-    if (k2 == 0) {
-      k2p = 0;
-      k1p = (G::N1 - k1) & (G::N1 - 1);
-    } else {
-      k2p = (k2 == (G::N2 >> 1)) ? k2 : G::N2 - k2;
-      k1p = G::N1 - 1 - k1;
+    if (m <= half) {
+      int k2p, k1p;
+      if (k2 == 0) {
+        k2p = 0;
+        k1p = (G::N1 - k1) & (G::N1 - 1);
+      } else {
+        k2p = (k2 == (G::N2 >> 1)) ? k2 : G::N2 - k2;
+        k1p = G::N1 - 1 - k1;
+      }
+      const int ep = (row_seq(k2p, G::N2) - q0) * G::N1 + k1p;
+      float2 Ym, Yc;
+      assemble_pair32(f, m, rowbuf[e], rowbuf[ep], pass, min_[q], &Ym, &Yc);
+      rowbuf[e] = Ym;
+      if (ep != e) rowbuf[ep] = Yc;
     }
-    const int ep = (row_seq(k2p, G::N2) - q0) * G::N1 + k1p;
-    float2 Ym, Yc;
-    assemble_pair32(f, m, rowbuf[e], rowbuf[ep], pass, m_dt, dt, &Ym, &Yc);
-    rowbuf[e] = Ym;
-    if (ep != e) rowbuf[ep] = Yc;
   }
   __syncthreads();
   fft_r8_batch<true, G::lg1>(rowbuf, twr, tid);
@@ -635,7 +639,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
     const int e = tid + q * nth;
     const int r = e / G::N1, n1 = e % G::N1;
     const int k2 = seq_row(q0 + r, G::N2);
-    const float2 val = f2mul(rowbuf[e], tw_full(f.tw, n1 * k2, half, true));
+    const float2 val = f2mul(rowbuf[e], wi[q]);
     st_cluster(cluster_map(colbuf + (n1 % G::cols) * G::N2 + k2, static_cast<unsigned>(n1 / G::cols)), val);
   }
   cluster_arrive();
