@@ -198,6 +198,20 @@ int sbiem_windows(sbiem_t s, int64_t* M);
 int sbiem_set_history(sbiem_t s, const double* hist_T, const double* hist_N);
 int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
 
+/* Checkpoint / restart.  sbiem_save writes to `path` (binary, little endian,
+ * this library's own format "SBIEMCK1") the parameters, the per-element
+ * inputs (kappa, a, b, Dc, loads, prescribed mask and rates), the committed
+ * state (delta, V, theta), the time, the step count and the history rings;
+ * it synchronizes the handle's stream.  sbiem_load creates a new handle from
+ * such a file; `alloc` (or NULL) supplies only the allocator fields
+ * (alloc_fn, free_fn, alloc_user).  A loaded handle continues bitwise like
+ * the saved one.  Errors: SBIEM_ERR_INVALID (bad path or file),
+ * SBIEM_ERR_NOMEM, SBIEM_ERR_CUDA. */
+int sbiem_save(sbiem_t s, const char* path);
+/* The handle's parameters (a copy; the allocator fields as given). */
+int sbiem_get_params(sbiem_t s, sbiem_params* out);
+int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc);
+
 /*
  * Timing probe.  sbiem_probe_enable(s, nslots) with nslots >= 1 makes every
  * later step record four CUDA events on the handle's stream (as event-record
@@ -269,9 +283,14 @@ int sbiem_history_sums_noalloc(int64_t nmodes, int32_t precision, int64_t m,
 
 /* sbiem_history_enqueue -- enqueue the history convolution of
  * sbiem_history_sums on the handle's stream without synchronizing or copying
- * (for timing the kernel with events on that stream).  The sums overwrite the
- * handle's internal A^T, A^N, which the next step recomputes anyway. */
+ * (for timing the kernel with events on that stream).  The sums land in the
+ * handle's A^T, A^N: exactly the sums the next step of m dt_min needs, so
+ * that step takes them instead of sweeping again.
+ * Two kernels run: the bulk-async sweep (chunk partial sums) and the
+ * per-mode finish.  `sweep_done` (a cudaEvent_t, or NULL) is recorded on the
+ * stream between the two, so the sweep alone can be timed. */
 int sbiem_history_enqueue(sbiem_t s, int64_t m);
+int sbiem_history_enqueue_marked(sbiem_t s, int64_t m, void* sweep_done);
 
 /* ------------------------------------------------------------- ensembles
  * A batch advances many faults together (independent realizations of uneven

@@ -204,7 +204,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
 #define COPYP(x) f.x = base.x
   COPYP(V); COPYP(psi); COPYP(th); COPYP(th2); COPYP(thd); COPYP(delta); COPYP(V1); COPYP(thd1); COPYP(Vbar);
   COPYP(V2); COPYP(psi2); COPYP(thd2); COPYP(delta2); COPYP(a); COPYP(b); COPYP(Dc);
-  COPYP(xV); COPYP(x1); COPYP(x2); COPYP(lvd);
+  COPYP(xV); COPYP(x1); COPYP(x2); COPYP(lvd); COPYP(rDc);
   COPYP(sig0); COPYP(tau0); COPYP(taur); COPYP(Vp); COPYP(kappa); COPYP(presc);
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(BT); COPYP(BN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
@@ -501,7 +501,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   bool ok = true;
   double** darr[] = {&f.V, &f.psi, &f.thd, &f.delta, &f.V1, &f.thd1, &f.Vbar, &f.V2, &f.psi2, &f.thd2,
                      &f.delta2, &f.a, &f.b, &f.Dc, &f.sig0, &f.tau0, &f.taur, &f.Vp, &f.kappa,
-                     &f.xV, &f.x1, &f.x2, &f.lvd, &f.th, &f.th2};
+                     &f.xV, &f.x1, &f.x2, &f.lvd, &f.th, &f.th2, &f.rDc};
   for (double** d : darr) *d = alloc_n<double>(s, N, &ok);
   f.presc = alloc_n<uint8_t>(s, N, &ok);
   double2** carr[] = {&f.dhat, &f.khat, &f.U2, &f.Q2, &f.AT, &f.AN, &f.BT, &f.BN};
@@ -567,7 +567,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     for (size_t i = 0; i < tw.size(); ++i) tw32[i] = static_cast<float>(tw[i]);
   }
   // friction arrays, load, state
-  std::vector<double> psi(N), thd(N), taul(N, 0.0), taur(N, 0.0), Vp(N, 0.0), V(N), xV(N), lvd(N);
+  std::vector<double> psi(N), thd(N), taul(N, 0.0), taur(N, 0.0), Vp(N, 0.0), V(N), xV(N), lvd(N), rDc(N);
   std::vector<uint8_t> pr(N, 0);
   for (int i = 0; i < N; ++i) {
     pr[i] = (prescribed && prescribed[i]) ? 1 : 0;
@@ -577,6 +577,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     thd[i] = 1.0 - theta_init[i] * V[i] / Dc[i];
     xV[i] = V[i] > 0.0 ? std::log(V[i]) : -745.0;
     lvd[i] = std::log(p.V0 / Dc[i]);
+    rDc[i] = 1.0 / Dc[i];
     if (tau_load_rate) taur[i] = tau_load_rate[i];
     if (tau_load) {
       taul[i] = tau_load[i];
@@ -594,6 +595,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
             up(f.psi, psi.data(), nb) == cudaSuccess && up(f.th, theta_init, nb) == cudaSuccess &&
             up(f.thd, thd.data(), nb) == cudaSuccess &&
             up(f.xV, xV.data(), nb) == cudaSuccess && up(f.lvd, lvd.data(), nb) == cudaSuccess &&
+            up(f.rDc, rDc.data(), nb) == cudaSuccess &&
             up(d_roff, s->ring_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
             up(d_woff, s->w_off.data(), sizeof(int64_t) * (s->nmodes + 1)) == cudaSuccess &&
             up(d_Rn, Rn32.data(), sizeof(int32_t) * s->nmodes) == cudaSuccess &&
@@ -1059,16 +1061,18 @@ int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   return SBIEM_OK;
 }
 
-int sbiem_history_enqueue(sbiem_t s, int64_t m) {
+int sbiem_history_enqueue_marked(sbiem_t s, int64_t m, void* sweep_done) {
   if (!s || m < 1 || m > (int64_t(1) << 30)) return fail(SBIEM_ERR_INVALID, "bad argument");
   const int mi = static_cast<int>(m);
-  CK(cudaMemsetAsync(s->f64.work, 0, sizeof(int), s->stream));
-  if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
-  else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
+  cudaEvent_t ev = static_cast<cudaEvent_t>(sweep_done);
+  if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream, ev);
+  else launch_history<double>(s->f64, mi, s->hist_grid, s->stream, ev);
   CK(cudaGetLastError());
   s->lag_m = mi;
   return SBIEM_OK;
 }
+
+int sbiem_history_enqueue(sbiem_t s, int64_t m) { return sbiem_history_enqueue_marked(s, m, nullptr); }
 
 namespace {
 void drop_graphs(sbiem_s* s) {
@@ -1520,6 +1524,188 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
   if (chunk_out) *chunk_out = best_c;
   if (blocks_out) *blocks_out = best_b;
   if (ms_out) *ms_out = best;
+  return SBIEM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- checkpoints
+namespace {
+
+constexpr char kCkMagic[8] = {'S', 'B', 'I', 'E', 'M', 'C', 'K', '1'};
+
+struct CkHeader {
+  char magic[8];
+  int64_t N, total_slots;
+  int32_t precision, state_law, kc_units, newton_maxit;
+  double dx, mu, cs, cp, beta_min, eta_w, kc_L, newton_tol, f0, V0;
+};
+
+// Element arrays of a checkpoint, in file order: inputs, then raw state.
+std::vector<double*> ck_element_arrays(sbiem_s* s) {
+  auto& f = s->f64;
+  return {f.kappa, f.a, f.b, f.Dc, f.sig0, f.tau0, f.taur, f.Vp, f.V, f.xV, f.psi, f.th, f.thd, f.delta};
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbiem_get_params(sbiem_t s, sbiem_params* out) {
+  if (!s || !out) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  *out = s->p;
+  return SBIEM_OK;
+}
+
+int sbiem_save(sbiem_t s, const char* path) {
+  if (!s || !path) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  const int N = s->N;
+  const auto& f = s->f64;
+  CkHeader hd{};
+  std::memcpy(hd.magic, kCkMagic, 8);
+  hd.N = N;
+  hd.total_slots = s->total_slots;
+  hd.precision = s->p.precision;
+  hd.state_law = s->p.state_law;
+  hd.kc_units = s->p.kc_units;
+  hd.newton_maxit = s->p.newton_maxit;
+  hd.dx = s->p.dx;
+  hd.mu = s->p.mu;
+  hd.cs = s->p.cs;
+  hd.cp = s->p.cp;
+  hd.beta_min = s->p.beta_min;
+  hd.eta_w = s->p.eta_w;
+  hd.kc_L = s->p.kc_L;
+  hd.newton_tol = s->p.newton_tol;
+  hd.f0 = s->p.f0;
+  hd.V0 = s->p.V0;
+  const auto arrs = ck_element_arrays(s);
+  std::vector<double> el(arrs.size() * static_cast<size_t>(N));
+  std::vector<uint8_t> pr(N);
+  std::vector<double2> spec(2 * static_cast<size_t>(s->nmodes));
+  std::vector<int32_t> heads(s->nmodes);
+  const size_t slot = s->fp32() ? sizeof(Slot32) : sizeof(Slot64);
+  std::vector<unsigned char> ring(slot * static_cast<size_t>(s->total_slots));
+  double t = 0.0;
+  long long steps = 0;
+  for (size_t k = 0; k < arrs.size(); ++k)
+    CK(cudaMemcpyAsync(el.data() + k * N, arrs[k], sizeof(double) * N, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(pr.data(), f.presc, N, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(spec.data(), f.dhat, sizeof(double2) * s->nmodes, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(spec.data() + s->nmodes, f.khat, sizeof(double2) * s->nmodes, cudaMemcpyDeviceToHost,
+                     s->stream));
+  CK(cudaMemcpyAsync(heads.data(), f.head, sizeof(int32_t) * s->nmodes, cudaMemcpyDeviceToHost, s->stream));
+  const void* ring_dev = s->fp32() ? static_cast<const void*>(s->f32.ring) : static_cast<const void*>(s->f64.ring);
+  if (!ring.empty()) CK(cudaMemcpyAsync(ring.data(), ring_dev, ring.size(), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&t, f.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&steps, f.steps_done, sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(SBIEM_ERR_INVALID, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(el.data(), sizeof(double), el.size(), fp) == el.size() &&
+            std::fwrite(pr.data(), 1, pr.size(), fp) == pr.size() &&
+            std::fwrite(spec.data(), sizeof(double2), spec.size(), fp) == spec.size() &&
+            std::fwrite(heads.data(), sizeof(int32_t), heads.size(), fp) == heads.size() &&
+            std::fwrite(ring.data(), 1, ring.size(), fp) == ring.size() && std::fwrite(&t, sizeof(t), 1, fp) == 1 &&
+            std::fwrite(&steps, sizeof(steps), 1, fp) == 1;
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) return fail(SBIEM_ERR_INVALID, std::string("write failed: ") + path);
+  return SBIEM_OK;
+}
+
+int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc) {
+  if (!out || !path) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(SBIEM_ERR_INVALID, std::string("cannot open ") + path);
+  CkHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, kCkMagic, 8) != 0 || hd.N < 16 ||
+      hd.N > (1 << 20) || hd.total_slots < 0) {
+    std::fclose(fp);
+    return fail(SBIEM_ERR_INVALID, std::string("not a checkpoint: ") + path);
+  }
+  const int N = static_cast<int>(hd.N);
+  const size_t nm = static_cast<size_t>(N / 2 + 1);
+  const size_t n_el = 14;
+  std::vector<double> el(n_el * static_cast<size_t>(N));
+  std::vector<uint8_t> pr(N);
+  std::vector<double2> spec(2 * nm);
+  std::vector<int32_t> heads(nm);
+  const size_t slot = hd.precision == 1 ? sizeof(Slot32) : sizeof(Slot64);
+  std::vector<unsigned char> ring(slot * static_cast<size_t>(hd.total_slots));
+  double t = 0.0;
+  long long steps = 0;
+  bool ok = std::fread(el.data(), sizeof(double), el.size(), fp) == el.size() &&
+            std::fread(pr.data(), 1, pr.size(), fp) == pr.size() &&
+            std::fread(spec.data(), sizeof(double2), spec.size(), fp) == spec.size() &&
+            std::fread(heads.data(), sizeof(int32_t), heads.size(), fp) == heads.size() &&
+            std::fread(ring.data(), 1, ring.size(), fp) == ring.size() && std::fread(&t, sizeof(t), 1, fp) == 1 &&
+            std::fread(&steps, sizeof(steps), 1, fp) == 1;
+  std::fclose(fp);
+  if (!ok) return fail(SBIEM_ERR_INVALID, std::string("truncated checkpoint: ") + path);
+  sbiem_params p;
+  sbiem_default_params(&p);
+  p.N = hd.N;
+  p.precision = hd.precision;
+  p.state_law = hd.state_law;
+  p.kc_units = hd.kc_units;
+  p.newton_maxit = hd.newton_maxit;
+  p.dx = hd.dx;
+  p.mu = hd.mu;
+  p.cs = hd.cs;
+  p.cp = hd.cp;
+  p.beta_min = hd.beta_min;
+  p.eta_w = hd.eta_w;
+  p.kc_L = hd.kc_L;
+  p.newton_tol = hd.newton_tol;
+  p.f0 = hd.f0;
+  p.V0 = hd.V0;
+  if (alloc) {
+    p.alloc_fn = alloc->alloc_fn;
+    p.free_fn = alloc->free_fn;
+    p.alloc_user = alloc->alloc_user;
+  }
+  auto arr = [&](int k) { return el.data() + static_cast<size_t>(k) * N; };
+  // inputs in file order: kappa, a, b, Dc, sigma_load, tau_load, tau_rate, V_presc;
+  // state: V, xV, psi, theta, thetadot, delta
+  bool any_pr = false;
+  for (int i = 0; i < N; ++i) any_pr = any_pr || pr[i];
+  sbiem_t s = nullptr;
+  int rc = sbiem_create(&s, &p, nullptr, arr(0), arr(1), arr(2), arr(3), arr(4), arr(5), arr(6),
+                        any_pr ? pr.data() : nullptr, any_pr ? arr(7) : nullptr, arr(8), arr(11));
+  if (rc) return rc;
+  if (static_cast<int64_t>(s->total_slots) != hd.total_slots) {
+    sbiem_destroy(s);
+    return fail(SBIEM_ERR_INVALID, "checkpoint history size does not match its parameters");
+  }
+  auto& f = s->f64;
+  double* raw[] = {f.V, f.xV, f.psi, f.th, f.thd, f.delta};
+  auto fail_cuda = [&](cudaError_t e) {
+    sbiem_destroy(s);
+    return fail(SBIEM_ERR_CUDA, std::string("load: ") + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(raw[k], arr(8 + k), sizeof(double) * N, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f.dhat, spec.data(), sizeof(double2) * nm, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(f.khat, spec.data() + nm, sizeof(double2) * nm, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f.head, heads.data(), sizeof(int32_t) * nm, cudaMemcpyHostToDevice, s->stream);
+  void* ring_dev = s->fp32() ? static_cast<void*>(s->f32.ring) : static_cast<void*>(s->f64.ring);
+  if (e == cudaSuccess && !ring.empty())
+    e = cudaMemcpyAsync(ring_dev, ring.data(), ring.size(), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f.t, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f.steps_done, &steps, sizeof(long long), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && f.dhat32) {
+    launch_to_float2(f.dhat, f.dhat32, s->nmodes, s->stream);
+    launch_to_float2(f.khat, f.khat32, s->nmodes, s->stream);
+  }
+  if (e == cudaSuccess && s->f32.zin1) launch_zin(f.V, f.kappa, s->f32.zin1, s->N, s->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return fail_cuda(e);
+  s->lag_m = -1;
+  *out = s;
   return SBIEM_OK;
 }
 

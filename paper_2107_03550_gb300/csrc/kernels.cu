@@ -228,40 +228,40 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// v * w8^K, w8 = exp(-2 pi i / 8) (forward) or its conjugate (inverse)
-template <int K, bool INV>
-__device__ __forceinline__ float2 rot8(float2 v) {
+// v * w8^K with w8 = exp(-sg 2 pi i / 8): sg = +1 forward, -1 inverse
+// (one code path for both directions keeps the kernels small)
+template <int K>
+__device__ __forceinline__ float2 rot8(float2 v, float sg) {
   constexpr float c = 0.70710678118654752f;
   if constexpr (K == 0) return v;
-  if constexpr (K == 1) return INV ? make_float2(c * (v.x - v.y), c * (v.x + v.y)) : make_float2(c * (v.x + v.y), c * (v.y - v.x));
-  if constexpr (K == 2) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
-  if constexpr (K == 3) return INV ? make_float2(-c * (v.x + v.y), c * (v.x - v.y)) : make_float2(c * (v.y - v.x), -c * (v.x + v.y));
+  if constexpr (K == 1) return make_float2(c * fmaf(sg, v.y, v.x), c * fmaf(-sg, v.x, v.y));
+  if constexpr (K == 2) return make_float2(sg * v.y, -sg * v.x);
+  if constexpr (K == 3) return make_float2(c * fmaf(sg, v.y, -v.x), -c * fmaf(sg, v.x, v.y));
   return v;
 }
 
-template <int K, bool INV>
-__device__ __forceinline__ void bfly(float2& a, float2& b) {
+template <int K>
+__device__ __forceinline__ void bfly(float2& a, float2& b, float sg) {
   const float2 s = f2add(a, b), d = f2sub(a, b);
   a = s;
-  b = rot8<K, INV>(d);
+  b = rot8<K>(d, sg);
 }
 
 // In-place DFTs of 8, 4 and 2 points (radix-2 decimation in frequency),
 // results in natural order.
-template <bool INV>
-__device__ __forceinline__ void dft8(float2 (&v)[8]) {
-  bfly<0, INV>(v[0], v[4]);
-  bfly<1, INV>(v[1], v[5]);
-  bfly<2, INV>(v[2], v[6]);
-  bfly<3, INV>(v[3], v[7]);
-  bfly<0, INV>(v[0], v[2]);
-  bfly<2, INV>(v[1], v[3]);
-  bfly<0, INV>(v[4], v[6]);
-  bfly<2, INV>(v[5], v[7]);
-  bfly<0, INV>(v[0], v[1]);
-  bfly<0, INV>(v[2], v[3]);
-  bfly<0, INV>(v[4], v[5]);
-  bfly<0, INV>(v[6], v[7]);
+__device__ __forceinline__ void dft8(float2 (&v)[8], float sg) {
+  bfly<0>(v[0], v[4], sg);
+  bfly<1>(v[1], v[5], sg);
+  bfly<2>(v[2], v[6], sg);
+  bfly<3>(v[3], v[7], sg);
+  bfly<0>(v[0], v[2], sg);
+  bfly<2>(v[1], v[3], sg);
+  bfly<0>(v[4], v[6], sg);
+  bfly<2>(v[5], v[7], sg);
+  bfly<0>(v[0], v[1], sg);
+  bfly<0>(v[2], v[3], sg);
+  bfly<0>(v[4], v[5], sg);
+  bfly<0>(v[6], v[7], sg);
   // bit reversal of 3 bits: swap 1<->4, 3<->6
   float2 t = v[1];
   v[1] = v[4];
@@ -271,22 +271,25 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
   v[6] = t;
 }
 
-template <bool INV, int O>
-__device__ __forceinline__ void dft4(float2 (&v)[8]) {
-  bfly<0, INV>(v[O + 0], v[O + 2]);
-  bfly<2, INV>(v[O + 1], v[O + 3]);
-  bfly<0, INV>(v[O + 0], v[O + 1]);
-  bfly<0, INV>(v[O + 2], v[O + 3]);
+template <int O>
+__device__ __forceinline__ void dft4(float2 (&v)[8], float sg) {
+  bfly<0>(v[O + 0], v[O + 2], sg);
+  bfly<2>(v[O + 1], v[O + 3], sg);
+  bfly<0>(v[O + 0], v[O + 1], sg);
+  bfly<0>(v[O + 2], v[O + 3], sg);
   const float2 t = v[O + 1];
   v[O + 1] = v[O + 2];
   v[O + 2] = t;
 }
 
 // One Stockham stage over buf (length L = 2^LGL, L/8 threads, tid < L/8)
-// after sub-transforms of length Ns = 2^lgNs; all index arithmetic is
-// shifts and masks of compile-time sizes.
-template <int R, bool INV, int LGL>
-__device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, int lgNs, int tid) {
+// after sub-transforms of length Ns = 2^lgNs: for j < L/R, k = j mod Ns,
+// v_r = A[j + r L/R] exp(-sg 2 pi i r k / (Ns R)), an R-point DFT, and
+// A[(j - k) R + k + r Ns] = V_r (self-sorting; natural order after the last
+// stage).  Twiddles come from the L/2-entry table exp(-2 pi i a / L); all
+// index arithmetic is shifts and masks of compile-time sizes.
+template <int R, int LGL>
+__device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, int lgNs, int tid, float sg) {
   constexpr int L = 1 << LGL;
   constexpr int NB = 8 / R;  // butterflies per thread
   constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
@@ -306,20 +309,20 @@ __device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, in
       if (r > 0) {
         const int a = r * tstep;
         float2 w = a < half ? tw[a] : make_float2(-tw[a - half].x, -tw[a - half].y);
-        if (INV) w.y = -w.y;
+        w.y *= sg;
         x = f2mul(x, w);
       }
       v[q * R + r] = x;
     }
   }
   if constexpr (R == 8) {
-    dft8<INV>(v);
+    dft8(v, sg);
   } else if constexpr (R == 4) {
-    dft4<INV, 0>(v);
-    dft4<INV, 4>(v);
+    dft4<0>(v, sg);
+    dft4<4>(v, sg);
   } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) bfly<0, INV>(v[2 * q], v[2 * q + 1]);
+    for (int q = 0; q < 4; ++q) bfly<0>(v[2 * q], v[2 * q + 1], sg);
   }
   __syncthreads();
 #pragma unroll
@@ -333,13 +336,13 @@ __device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, in
   __syncthreads();
 }
 
-// Forward (INV = false) or unscaled inverse FFT of length 2^LGL in buf.
-template <bool INV, int LGL>
-__device__ __forceinline__ void fft_r8(float2* buf, const float2* tw, int tid) {
-#pragma unroll
-  for (int s = 0; s < LGL / 3; ++s) stockham_stage<8, INV, LGL>(buf, tw, 3 * s, tid);
-  if constexpr (LGL % 3 == 2) stockham_stage<4, INV, LGL>(buf, tw, 3 * (LGL / 3), tid);
-  if constexpr (LGL % 3 == 1) stockham_stage<2, INV, LGL>(buf, tw, 3 * (LGL / 3), tid);
+// FFT of length 2^LGL in buf: sg = +1 forward, -1 unscaled inverse.
+template <int LGL>
+__device__ __noinline__ void fft_r8(float2* buf, const float2* tw, int tid, float sg) {
+#pragma unroll 1
+  for (int s = 0; s < LGL / 3; ++s) stockham_stage<8, LGL>(buf, tw, 3 * s, tid, sg);
+  if constexpr (LGL % 3 == 2) stockham_stage<4, LGL>(buf, tw, 3 * (LGL / 3), tid, sg);
+  if constexpr (LGL % 3 == 1) stockham_stage<2, LGL>(buf, tw, 3 * (LGL / 3), tid, sg);
 }
 
 // Per-mode inputs of the precision form's assembly: running sums F[delta],
@@ -447,7 +450,7 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
     for (int q = 0; q < 8; ++q) buf[tid + q * nth] = zv[q];
   }
   __syncthreads();
-  fft_r8<false, LGN>(buf, tw, tid);
+  fft_r8<LGN>(buf, tw, tid, 1.0f);
 #pragma unroll
   for (int q = 0; q < kMpt; ++q) {
     const int m = tid + q * nth;
@@ -459,7 +462,7 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
     }
   }
   __syncthreads();
-  fft_r8<true, LGN>(buf, tw, tid);
+  fft_r8<LGN>(buf, tw, tid, -1.0f);
   const float scale = 1.0f / static_cast<float>(N);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -542,10 +545,10 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
 }
 
 // Transforms of length 2^LGL (2^LGL/8 threads each) side by side in buf.
-template <bool INV, int LGL>
-__device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int tid) {
+template <int LGL>
+__device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int tid, float sg) {
   constexpr int per = (1 << LGL) >> 3;
-  fft_r8<INV, LGL>(buf + (tid / per) * (1 << LGL), tw, tid % per);
+  fft_r8<LGL>(buf + (tid / per) * (1 << LGL), tw, tid % per, sg);
 }
 
 template <int LGN>
@@ -557,98 +560,98 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* colbuf = reinterpret_cast<float2*>(smem_raw);  // [cols][N2]
   float2* rowbuf = colbuf + per;                          // [rows][N1]
-  float2* twc = rowbuf + per;                             // w_N2^j, j < N2/2
+  float2* s_wf = rowbuf + per;                            // forward four-step twiddle per column element
+  float2* s_wi = s_wf + per;                              // inverse four-step twiddle per row element
+  float2* twc = s_wi + per;                               // w_N2^j, j < N2/2
   float2* twr = twc + (G::N2 >> 1);                       // w_N1^j, j < N1/2
+  ModeIn* s_min = reinterpret_cast<ModeIn*>(twr + (G::N1 >> 1));  // assembly inputs per row element
   const int tid = threadIdx.x;
   const int n1_0 = static_cast<int>(c) * G::cols;
   const int q0 = static_cast<int>(c) * G::rows;  // first sequence index of this CTA's rows
   // every CTA of the cluster runs before any remote store (arrive now, wait later)
   cluster_arrive_relaxed();
-  // every global input up front, in registers (one memory latency): the
-  // pass input, the four-step twiddles of both directions, the sub-table
-  // twiddles and the assembly inputs of this CTA's primary modes
-  const float2* zin = pass == 1 ? f.zin1 : f.zin2;
-  float2 z[8], wf[8], wi[8];
-  ModeIn min_[8];
-  float2 tcv = make_float2(0.f, 0.f), trv = tcv;
-  if (tid < (G::N2 >> 1)) tcv = f.tw[tid * G::N1];
-  if (tid < (G::N1 >> 1)) trv = f.tw[tid * G::N2];
+  {
+    // every global input up front (one memory latency), staged in shared
+    // memory: the pass input, the four-step twiddles of both directions, the
+    // sub-table twiddles and the assembly inputs of this CTA's primary modes
+    const float2* zin = pass == 1 ? f.zin1 : f.zin2;
+    float2 z[8], wf[8], wi[8];
+    ModeIn mi[8];
+    float2 tcv = make_float2(0.f, 0.f), trv = tcv;
+    if (tid < (G::N2 >> 1)) tcv = f.tw[tid * G::N1];
+    if (tid < (G::N1 >> 1)) trv = f.tw[tid * G::N2];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = tid + q * nth;
-    // input: column element (b = e mod cols, n2 = e / cols), runs of cols n1
-    z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
-    // forward twiddle of column element e = b N2 + k2
-    wf[q] = tw_full(f.tw, (n1_0 + e / G::N2) * (e % G::N2), half, false);
-    // inverse twiddle and assembly input of row element e = r N1 + k1
-    const int k2 = seq_row(q0 + e / G::N1, G::N2);
-    wi[q] = tw_full(f.tw, (e % G::N1) * k2, half, true);
-    const int m = k2 + G::N2 * (e % G::N1);
-    if (m <= half) min_[q] = load_mode_in(f, m, m_dt, dt);
-  }
-  if (tid < (G::N2 >> 1)) twc[tid] = tcv;
-  if (tid < (G::N1 >> 1)) twr[tid] = trv;
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * nth;
+      z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
+      wf[q] = tw_full(f.tw, (n1_0 + e / G::N2) * (e % G::N2), half, false);
+      const int k2 = seq_row(q0 + e / G::N1, G::N2);
+      wi[q] = tw_full(f.tw, (e % G::N1) * k2, half, true);
+      const int m = k2 + G::N2 * (e % G::N1);
+      if (m <= half) mi[q] = load_mode_in(f, m, m_dt, dt);
+    }
+    if (tid < (G::N2 >> 1)) twc[tid] = tcv;
+    if (tid < (G::N1 >> 1)) twr[tid] = trv;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = tid + q * nth;
-    colbuf[(e % G::cols) * G::N2 + e / G::cols] = z[q];
-  }
-  __syncthreads();
-  fft_r8_batch<false, G::lg2>(colbuf, twc, tid);
-  cluster_wait();
-  // twiddle w_N^{n1 k2}, scatter to the row owners
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = tid + q * nth;
-    const int b = e / G::N2, k2 = e % G::N2;
-    const float2 val = f2mul(colbuf[e], wf[q]);
-    const int sq = row_seq(k2, G::N2);
-    st_cluster(cluster_map(rowbuf + (sq % G::rows) * G::N1 + n1_0 + b, static_cast<unsigned>(sq / G::rows)), val);
-  }
-  cluster_arrive();
-  cluster_wait();
-  fft_r8_batch<false, G::lg1>(rowbuf, twr, tid);
-  // assembly of the pairs (m, N-m) held by this CTA, in place
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = tid + q * nth;
-    const int r = e / G::N1, k1 = e % G::N1;
-    const int k2 = seq_row(q0 + r, G::N2);
-    const int m = k2 + G::N2 * k1;
-    if (m <= half) {
-      int k2p, k1p;
-      if (k2 == 0) {
-        k2p = 0;
-        k1p = (G::N1 - k1) & (G::N1 - 1);
-      } else {
-        k2p = (k2 == (G::N2 >> 1)) ? k2 : G::N2 - k2;
-        k1p = G::N1 - 1 - k1;
-      }
-      const int ep = (row_seq(k2p, G::N2) - q0) * G::N1 + k1p;
-      float2 Ym, Yc;
-      assemble_pair32(f, m, rowbuf[e], rowbuf[ep], pass, min_[q], &Ym, &Yc);
-      rowbuf[e] = Ym;
-      if (ep != e) rowbuf[ep] = Yc;
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * nth;
+      colbuf[(e % G::cols) * G::N2 + e / G::cols] = z[q];
+      s_wf[e] = wf[q];
+      s_wi[e] = wi[q];
+      s_min[e] = mi[q];
     }
   }
   __syncthreads();
-  fft_r8_batch<true, G::lg1>(rowbuf, twr, tid);
-  // twiddle w_N^{-n1 k2}, scatter back to the column owners
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = tid + q * nth;
-    const int r = e / G::N1, n1 = e % G::N1;
-    const int k2 = seq_row(q0 + r, G::N2);
-    const float2 val = f2mul(rowbuf[e], wi[q]);
-    st_cluster(cluster_map(colbuf + (n1 % G::cols) * G::N2 + k2, static_cast<unsigned>(n1 / G::cols)), val);
+  fft_r8_batch<G::lg2>(colbuf, twc, tid, 1.0f);
+  cluster_wait();
+  // twiddle w_N^{n1 k2}, scatter to the row owners
+#pragma unroll 1
+  for (int e = tid; e < per; e += nth) {
+    const int b = e / G::N2, k2 = e % G::N2;
+    const int sq = row_seq(k2, G::N2);
+    st_cluster(cluster_map(rowbuf + (sq % G::rows) * G::N1 + n1_0 + b, static_cast<unsigned>(sq / G::rows)),
+               f2mul(colbuf[e], s_wf[e]));
   }
   cluster_arrive();
   cluster_wait();
-  fft_r8_batch<true, G::lg2>(colbuf, twc, tid);
+  fft_r8_batch<G::lg1>(rowbuf, twr, tid, 1.0f);
+  // assembly of the pairs (m, N-m) held by this CTA, in place
+#pragma unroll 1
+  for (int e = tid; e < per; e += nth) {
+    const int r = e / G::N1, k1 = e % G::N1;
+    const int k2 = seq_row(q0 + r, G::N2);
+    const int m = k2 + G::N2 * k1;
+    if (m > half) continue;
+    int k2p, k1p;
+    if (k2 == 0) {
+      k2p = 0;
+      k1p = (G::N1 - k1) & (G::N1 - 1);
+    } else {
+      k2p = (k2 == (G::N2 >> 1)) ? k2 : G::N2 - k2;
+      k1p = G::N1 - 1 - k1;
+    }
+    const int ep = (row_seq(k2p, G::N2) - q0) * G::N1 + k1p;
+    float2 Ym, Yc;
+    assemble_pair32(f, m, rowbuf[e], rowbuf[ep], pass, s_min[e], &Ym, &Yc);
+    rowbuf[e] = Ym;
+    if (ep != e) rowbuf[ep] = Yc;
+  }
+  __syncthreads();
+  fft_r8_batch<G::lg1>(rowbuf, twr, tid, -1.0f);
+  // twiddle w_N^{-n1 k2}, scatter back to the column owners
+#pragma unroll 1
+  for (int e = tid; e < per; e += nth) {
+    const int r = e / G::N1, n1 = e % G::N1;
+    const int k2 = seq_row(q0 + r, G::N2);
+    st_cluster(cluster_map(colbuf + (n1 % G::cols) * G::N2 + k2, static_cast<unsigned>(n1 / G::cols)),
+               f2mul(rowbuf[e], s_wi[e]));
+  }
+  cluster_arrive();
+  cluster_wait();
+  fft_r8_batch<G::lg2>(colbuf, twc, tid, -1.0f);
   const float scale = 1.0f / static_cast<float>(N);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int e = tid + q * nth;
+#pragma unroll 1
+  for (int e = tid; e < per; e += nth) {
     const float2 v = colbuf[(e % G::cols) * G::N2 + e / G::cols];
     f.y[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)] = make_float2(v.x * scale, v.y * scale);
   }
@@ -1233,29 +1236,24 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
                                           double x0, double ex0, double xguess, double tol, int maxit,
                                           double* xout) {
   const double sa = sig * a;
+  // x_qs: only the guards below need it, so its division overlaps the
+  // first residual (a start above x_qs has g < 0 and steps down)
   double hi = fmin((tau - sig * c0) / sa, 700.0);
   double lo = -CUDART_INF;
   // a learned guess is used when it is finite, below x_qs and calls for a
   // substantial change (|guess - ln V_prev| >= 0.1, where the previous slip
-  // rate is a poor start); otherwise the previous slip rate (clamped to x_qs)
-  // starts Newton
+  // rate is a poor start); otherwise the previous slip rate starts Newton
   const bool use_guess = isfinite(xguess) && xguess <= hi && fabs(xguess - x0) >= 0.1;
-  double x, ex;
+  double x = x0, ex = ex0;
   if (use_guess) {
     x = xguess;
-    ex = exp(x);
-  } else if (x0 <= hi) {
-    x = x0;
-    ex = ex0;
-  } else {
-    x = hi;
     ex = exp(x);
   }
   for (int it = 1; it <= maxit; ++it) {
     const double e = eta * ex;
     const double q = tau - sig * fma(a, x, c0);
     const double g = q - e;
-    if (g > 0.0) lo = x; else hi = x;
+    if (g > 0.0) lo = x; else hi = fmin(hi, x);
     double dx;
     if (q > sa) dx = -q * (x - log(q * reta)) / (q + sa);
     else dx = g / (e + sa);
@@ -1301,17 +1299,34 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     // pass slip rate: the committed one, then the mean of committed and pass-1
     vb = (pass == 1) ? f.V[i] : 0.5 * (f.V[i] + f.V1[i]);
     Dc = f.Dc[i];
-    rDc = 1.0 / Dc;
+    rDc = f.rDc[i];
     const double th0 = f.th[i];
+    const double rth0 = 1.0 / th0;  // off the chain: used only in the series branch
+    bool series = false;
     if (f.state_law == 0) {
       // aging law integrated at constant Vbar: theta e^{-u} + dt phi(u),
       // phi(u) = (1 - e^{-u})/u, u = Vbar dt / Dc
       const double u = vb * dt * rDc;
       if (u < 1e-4) {
-        // series of phi to u^3 (truncation below u^4/120 < 1e-18);
-        // e^{-u} = 1 - u phi
+        // series of phi to u^3 (truncation below u^4/120 < 1e-18); with
+        // e^{-u} = 1 - u phi the update is theta (1 + z), z = phi (dt/theta - u)
         const double phi = fma(fma(fma(-u, 1.0 / 24.0, 1.0 / 6.0), u, -0.5), u, 1.0);
-        thp = fma(th0, fma(-u, phi, 1.0), dt * phi);
+        const double z = phi * fma(dt, rth0, -u);
+        thp = fma(th0, z, th0);
+        // every 1024th step takes the full log, so ln theta and theta, kept
+        // side by side, cannot drift apart by accumulated rounding
+        if (fabs(z) < 1e-3 && (*f.steps_done & 1023) != 0) {
+          // ln theta' = ln theta + log1p(z), series to z^6 (truncation below
+          // |z|^7/7 < 2e-22)
+          double l = -1.0 / 6.0;
+          l = fma(l, z, 1.0 / 5.0);
+          l = fma(l, z, -0.25);
+          l = fma(l, z, 1.0 / 3.0);
+          l = fma(l, z, -0.5);
+          l = fma(l, z, 1.0);
+          psip = fma(l, z, f.psi[i]);
+          series = true;
+        }
       } else {
         const double em = expm1(-u);
         const double eu = u < 1.0 ? 1.0 + em : exp(-u);
@@ -1322,7 +1337,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       thp = th0 + thdb * dt;
       if (!(thp > 0.0)) flags |= SBIEM_FLAG_STATE;
     }
-    psip = log(thp);
+    if (!series) psip = log(thp);
     const double t_end = *f.t + dt;
     const Cx<R> y = f.y[i];
     tau = f.tau0[i] + f.taur[i] * t_end + static_cast<double>(y.x);
@@ -1765,7 +1780,8 @@ static size_t cluster_smem(int N) {
   int lg = 0;
   while ((1 << lg) < N) ++lg;
   const int N1 = 1 << (lg / 2), N2 = 1 << (lg - lg / 2);
-  return static_cast<size_t>(2 * (N / kClusterCTAs) + N1 / 2 + N2 / 2) * sizeof(float2);
+  const size_t per = static_cast<size_t>(N / kClusterCTAs);
+  return (4 * per + N1 / 2 + N2 / 2) * sizeof(float2) + per * sizeof(ModeIn);
 }
 
 // fn(std::integral_constant<int, log2 N>) for the sizes of the one-launch
@@ -1854,8 +1870,9 @@ static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, cudaStream_t 
 }
 
 template <class R>
-void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st, cudaEvent_t sweep_done) {
   launch_sweep<R>(f, m_dt, grid, st);
+  if (sweep_done) cudaEventRecord(sweep_done, st);
   k_sweep_finish<R><<<(f.nmodes + 7) / 8, 256, 0, st>>>(f, f.AT, f.AN, true);
 }
 
@@ -2075,8 +2092,8 @@ template int history_blocks_per_sm<double>();
 template int history_blocks_per_sm<float>();
 template void configure_kernels<double>(const FftGeom&);
 template void configure_kernels<float>(const FftGeom&);
-template void launch_history<double>(const DevFault<double>&, int, int, cudaStream_t);
-template void launch_history<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_history<double>(const DevFault<double>&, int, int, cudaStream_t, cudaEvent_t);
+template void launch_history<float>(const DevFault<float>&, int, int, cudaStream_t, cudaEvent_t);
 template void launch_pass<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_pass<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_push_multi<double>(const DevFault<double>&, int, cudaStream_t);

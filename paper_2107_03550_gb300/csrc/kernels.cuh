@@ -77,6 +77,7 @@ struct DevFault {
   double *xV, *x1, *x2;                    // ln V: committed, pass 1, staged
   double *a, *b, *Dc, *sig0, *tau0, *taur, *Vp, *kappa;
   double *lvd;                             // ln(V0 / Dc) per element
+  double *rDc;                             // 1 / Dc per element
   uint8_t* presc;
   // spectral state (FP64)
   double2 *dhat, *khat;                    // F[delta], F[kappa delta]
@@ -126,7 +127,8 @@ constexpr int kClusterCTAs = 8;
 // Host launch wrappers (kernels.cu).
 // History sums AT/AN of a step of m_dt (bulk-async sweep, then per-mode
 // sums of its chunk partials).
-template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
+template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st,
+                                       cudaEvent_t sweep_done = nullptr);
 // The one-warp-per-chunk sweep with atomic chunk hand-out and per-mode
 // last-arriver sums (writes AT/AN itself); used on caller-owned buffers.
 template <class R> void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);

@@ -74,6 +74,10 @@ _SIGS = {
     "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
     "sbiem_history_enqueue": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "sbiem_history_enqueue_marked": (ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
+    "sbiem_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "sbiem_get_params": (ctypes.c_int, [_VP, ctypes.c_void_p]),
+    "sbiem_load": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_void_p]),
     "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
@@ -285,6 +289,33 @@ class Fault:
         args.update(kw)
         return cls(**args)
 
+    # ------------------------------------------------------------ checkpoint
+    def save(self, path) -> None:
+        """Write a checkpoint (parameters, inputs, state, time, history)."""
+        self._check(self.lib.sbiem_save(self.h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, use_torch=True, lib=None):
+        """New handle continuing a checkpoint written by :meth:`save`."""
+        self = cls.__new__(cls)
+        self.lib = lib or load_library()
+        p = Params()
+        self.lib.sbiem_default_params(ctypes.byref(p))
+        self._cb = _torch_allocator() if use_torch else None
+        if self._cb is not None:
+            p.alloc_fn, p.free_fn = self._cb
+        handle = _VP()
+        self._check(self.lib.sbiem_load(ctypes.byref(handle), os.fsencode(path), ctypes.cast(ctypes.byref(p),
+                                                                                              ctypes.c_void_p)))
+        self.h = handle
+        q = Params()
+        self._check(self.lib.sbiem_get_params(self.h, ctypes.cast(ctypes.byref(q), ctypes.c_void_p)))
+        self.params = q
+        self.N = int(q.N)
+        self.dt_min = q.beta_min * q.dx / q.cs
+        self._stream = None
+        return self
+
     # ---------------------------------------------------------------- errors
     def _check(self, rc):
         if rc != 0:
@@ -298,9 +329,13 @@ class Fault:
         self._stream = stream
         self._check(self.lib.sbiem_set_stream(self.h, _VP(raw or None)))
 
-    def history_enqueue(self, m: int = 1) -> None:
-        """Enqueue the history convolution alone (no synchronization), for timing."""
-        self._check(self.lib.sbiem_history_enqueue(self.h, int(m)))
+    def history_enqueue(self, m: int = 1, sweep_done=None) -> None:
+        """Enqueue the history convolution alone (no synchronization), for timing.
+
+        sweep_done: a torch.cuda.Event recorded between the sweep kernel and
+        the per-mode finish (None: not recorded)."""
+        ev = None if sweep_done is None else ctypes.c_void_p(sweep_done.cuda_event)
+        self._check(self.lib.sbiem_history_enqueue_marked(self.h, int(m), ev))
 
     def step(self, dt=None) -> None:
         self._check(self.lib.sbiem_step(self.h, float(dt or self.dt_min)))

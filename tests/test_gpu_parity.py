@@ -336,3 +336,26 @@ def test_precision_form_rupture():
     st = g.get_state()
     assert rel(st["delta"], o.delta) < 1e-4
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_continues_bitwise(tmp_path, precision):
+    from paper_2107_03550_gb300.sbiem import Fault
+    w = seamount_rupture()
+    g = gpu_for(w, precision=precision)
+    prefill_random(g, seed=21)
+    g.enqueue(300)
+    path = tmp_path / "ck.bin"
+    g.save(path)
+    h = Fault.load(path)
+    assert h.N == g.N and abs(h.dt_min - g.dt_min) == 0.0
+    g.enqueue(200)
+    h.enqueue(200)
+    assert g.status()[0] == 0 and h.status() == g.status()
+    s1, s2 = g.get_state(), h.get_state()
+    for k in ("delta", "V", "theta", "tau_el", "sigma_el", "t"):
+        assert np.array_equal(s1[k], s2[k]), k
+    H1, H2 = g.get_history(), h.get_history()
+    assert np.array_equal(H1[0], H2[0]) and np.array_equal(H1[1], H2[1])
+    g.close()
+    h.close()
