@@ -205,7 +205,7 @@ int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
  * it synchronizes the handle's stream.  sbiem_load creates a new handle from
  * such a file; `alloc` (or NULL) supplies only the allocator fields
  * (alloc_fn, free_fn, alloc_user).  A loaded handle continues bitwise like
- * the saved one.  Errors: SBIEM_ERR_INVALID (bad path or file),
+ * the saved one (after a save both recompute their next history sums).  Errors: SBIEM_ERR_INVALID (bad path or file),
  * SBIEM_ERR_NOMEM, SBIEM_ERR_CUDA. */
 int sbiem_save(sbiem_t s, const char* path);
 /* The handle's parameters (a copy; the allocator fields as given). */

@@ -25,6 +25,9 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Sweep shape of a new handle (chunk length x stages in flight).
+constexpr int kDefaultSweepShape = 3;
+
 int fail(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
@@ -74,6 +77,7 @@ struct sbiem_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int lag_m = -1;
   int lag_grid = 0;  // CTAs of the overlapped sweep (leaves room for the passes)
+  int sweep_shape = 0;  // chunk length x stages of the sweep (SBIEM_SWEEP_SHAPE overrides)
   // timing probe: 4 events per slot; graph event-record nodes are retargeted
   // to the slot of each launch
   int pslots = 0;
@@ -193,6 +197,7 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
     f.newton_epw = epw;
   }
   f.newton_maxit = s->p.newton_maxit;
+  f.sweep_shape = s->sweep_shape;
   f.newton_tol = s->p.newton_tol;
 }
 
@@ -452,10 +457,16 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     // so the pass kernels find room beside it
     if (s->fp32()) configure_kernels<float>(make_geom(N, sizeof(float2)));
     else configure_kernels<double>(make_geom(N, sizeof(double2)));
-    const int per_sm = s->fp32() ? sweep_blocks_per_sm<float>() : sweep_blocks_per_sm<double>();
+    s->sweep_shape = kDefaultSweepShape;
+    if (const char* e = std::getenv("SBIEM_SWEEP_SHAPE")) {
+      const int v = std::atoi(e);
+      if (v >= 0 && v < 4) s->sweep_shape = v;
+    }
+    const int per_sm = s->fp32() ? sweep_blocks_per_sm<float>(s->sweep_shape)
+                                 : sweep_blocks_per_sm<double>(s->sweep_shape);
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
     s->lag_grid = s->sm_count;
-    s->chunk_slots = sweep_chunk_slots(p.precision);
+    s->chunk_slots = sweep_chunk_slots(p.precision, s->sweep_shape);
   }
   s->Rn.assign(s->nmodes, 0);
   s->ring_off.assign(s->nmodes + 1, 0);
@@ -1610,6 +1621,9 @@ int sbiem_save(sbiem_t s, const char* path) {
             std::fwrite(&steps, sizeof(steps), 1, fp) == 1;
   ok = (std::fclose(fp) == 0) && ok;
   if (!ok) return fail(SBIEM_ERR_INVALID, std::string("write failed: ") + path);
+  // the next step recomputes its history sums, as a loaded handle does, so
+  // the two continue identically (the overlapped form sums in another order)
+  s->lag_m = -1;
   return SBIEM_OK;
 }
 

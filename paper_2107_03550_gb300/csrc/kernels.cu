@@ -866,17 +866,23 @@ __global__ void __launch_bounds__(kHistThreads)
 // order, so results do not depend on scheduling.  Every wait is bounded: on
 // a timeout the kernel sets SBIEM_FLAG_WAIT, waits (bounded) for its copies
 // in flight and returns.
-template <class R> struct SweepCfg;
-template <> struct SweepCfg<float> { static constexpr int kSlots = 512; };   // 8 KB ring + 4 KB weights
-template <> struct SweepCfg<double> { static constexpr int kSlots = 256; };  // 8 KB ring + 4 KB weights
+// Shapes of the sweep: lags per chunk (= stage buffer) x stages in flight per
+// CTA.  Shape 0: 512 x 4 (FP32, 12 KB stages) / 256 x 4 (FP64, 12 KB);
+// shape 1: twice the lags; shape 2: twice the stages; shape 3: 4x the lags, 2
+// stages.
+template <class R, int SH> struct SweepCfg {
+  static constexpr int kBase = sizeof(R) == 4 ? 512 : 256;
+  static constexpr int kSlots = SH == 1 ? 2 * kBase : (SH == 3 ? 4 * kBase : kBase);
+  static constexpr int kStages = SH == 2 ? 8 : (SH == 3 ? 2 : 4);
+};
+constexpr int kSweepShapes = 4;
 constexpr int kSweepThreads = 128;
-constexpr int kSweepStages = 4;
 constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls before a wait is declared stuck
 
-template <class R>
+template <class R, int SH>
 __host__ __device__ constexpr size_t sweep_stage_bytes() {
-  return static_cast<size_t>(SweepCfg<R>::kSlots) * sizeof(Slot<R>) +
-         static_cast<size_t>(SweepCfg<R>::kSlots + 2) * sizeof(W2<R>);
+  return static_cast<size_t>(SweepCfg<R, SH>::kSlots) * sizeof(Slot<R>) +
+         static_cast<size_t>(SweepCfg<R, SH>::kSlots + 2) * sizeof(W2<R>);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -910,6 +916,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Fixed-order tree sum of a warp's values, valid in lane 0.  Only the lanes
+// that keep a partial sum add (lane < o), so the FP64 pipe (scarce on GB300)
+// does 31 additions per value instead of 160.
+template <class T>
+__device__ __forceinline__ T warp_reduce_to_lane0(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T u = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane < o) v += u;
+  }
+  return v;
 }
 
 // Copy plan of one chunk (computed ahead by all threads, read by the
@@ -955,9 +975,8 @@ __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f, int c, int
 }
 
 // Thread 0: start the copies of a planned chunk into a stage.
-template <class R>
+template <class R, int S>
 __device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* stage_buf, uint64_t* bar) {
-  constexpr int S = SweepCfg<R>::kSlots;
   if (pl.len == 0) {
     mbar_arrive(bar);
     return;
@@ -969,11 +988,12 @@ __device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* 
   bulk_g2s(sw, pl.wsrc, pl.bw, bar);
 }
 
-template <class R>
+template <class R, int SH>
 __global__ void __launch_bounds__(kSweepThreads)
     k_sweep(const __grid_constant__ DevFault<R> f, int m_dt) {
-  constexpr int S = SweepCfg<R>::kSlots;
-  constexpr size_t SB = sweep_stage_bytes<R>();
+  constexpr int S = SweepCfg<R, SH>::kSlots;
+  constexpr int kSweepStages = SweepCfg<R, SH>::kStages;
+  constexpr size_t SB = sweep_stage_bytes<R, SH>();
   constexpr int NW = kSweepThreads / 32;
   extern __shared__ __align__(128) unsigned char sweep_smem[];
   __shared__ __align__(8) uint64_t bars[kSweepStages];
@@ -999,7 +1019,7 @@ __global__ void __launch_bounds__(kSweepThreads)
   __syncthreads();
   if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
-      sweep_issue<R>(plan[k], sweep_smem + k * SB, &bars[k]);
+      sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
   // each thread accumulates over consecutive chunks of one mode; the CTA
   // reduces at the end of the mode's run (a segment) and writes the sum at
   // the segment's last chunk, zeros at the others
@@ -1026,10 +1046,10 @@ __global__ void __launch_bounds__(kSweepThreads)
     const bool seg_end = k + 1 == nk || plan[(k + 1) % kPlanRing].mode != plan[k % kPlanRing].mode;
     if (seg_end) {
       Acc4<R> w4;
-      w4.tr = warp_sum(acc.tr);
-      w4.ti = warp_sum(acc.ti);
-      w4.nr = warp_sum(acc.nr);
-      w4.ni = warp_sum(acc.ni);
+      w4.tr = warp_reduce_to_lane0(acc.tr);
+      w4.ti = warp_reduce_to_lane0(acc.ti);
+      w4.nr = warp_reduce_to_lane0(acc.nr);
+      w4.ni = warp_reduce_to_lane0(acc.ni);
       if (lane == 0) red[k & 1][wid] = w4;
       acc = {R(0), R(0), R(0), R(0)};
     }
@@ -1038,7 +1058,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     if (tid == 0) {
       // the stage was read by every thread (barrier above): refill it first
       if (k + kSweepStages < nk)
-        sweep_issue<R>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
+        sweep_issue<R, S>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
       double4 out = make_double4(0.0, 0.0, 0.0, 0.0);
       if (seg_end) {
         Acc4<R> t = red[k & 1][0];
@@ -1065,32 +1085,38 @@ __global__ void __launch_bounds__(kSweepThreads)
   }
 }
 
-// Per-mode sums of the sweep's chunk partials, one warp per mode: lane q
-// adds chunks q, q + 32, ... in order, then a fixed butterfly tree over the
-// lanes (the result does not depend on scheduling).  Writes (AT, AN) or, for
-// the overlapped form, (BT, BN); the FP32 copies when `f32` is set.
+// Per-mode sums of the sweep's segment partials, one thread per mode.  The
+// sweep (grid G, CTA b taking chunks [c0(b), c0(b+1)), c0(b) = b nch / G)
+// leaves a mode's sum over one CTA at the CTA's last chunk of that mode and
+// zeros at its other chunks, so only those chunks are read: for every CTA
+// overlapping the mode's chunks [F, E), chunk min(c0(b+1), E) - 1, added in
+// chunk order.  Writes (AT, AN) or, for the overlapped form, (BT, BN); the
+// FP32 copies when `f32` is set.
 template <class R>
-__global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* outT, double2* outN, bool f32) {
-  const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+__global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* outT, double2* outN, bool f32,
+                               int G) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= f.nmodes || *f.status) return;
-  const int c0 = f.mfirst[n], cnt = f.mcount[n];
+  const int64_t nch = f.nchunks;
+  const int64_t F = f.mfirst[n], E = F + f.mcount[n];
   double4 t = make_double4(0.0, 0.0, 0.0, 0.0);
-  for (int q = lane; q < cnt; q += 32) {
-    const double4 u = f.partial[c0 + q];
-    t.x += u.x;
-    t.y += u.y;
-    t.z += u.z;
-    t.w += u.w;
-  }
-  t = make_double4(warp_sum(t.x), warp_sum(t.y), warp_sum(t.z), warp_sum(t.w));
-  if (lane == 0) {
-    outT[n] = make_double2(t.x, t.y);
-    outN[n] = make_double2(t.z, t.w);
-    if (f32 && f.AT32) {
-      f.AT32[n] = make_float2(static_cast<float>(t.x), static_cast<float>(t.y));
-      f.AN32[n] = make_float2(static_cast<float>(t.z), static_cast<float>(t.w));
+  if (E > F) {
+    auto c0 = [&](int64_t b) { return b * nch / G; };
+    // the CTA holding chunk F: the largest b with c0(b) <= F
+    for (int64_t b = ((F + 1) * G + nch - 1) / nch - 1; b < G && c0(b) < E; ++b) {
+      const int64_t end = min(c0(b + 1), E) - 1;
+      const double4 u = f.partial[end];
+      t.x += u.x;
+      t.y += u.y;
+      t.z += u.z;
+      t.w += u.w;
     }
+  }
+  outT[n] = make_double2(t.x, t.y);
+  outN[n] = make_double2(t.z, t.w);
+  if (f32 && f.AT32) {
+    f.AT32[n] = make_float2(static_cast<float>(t.x), static_cast<float>(t.y));
+    f.AN32[n] = make_float2(static_cast<float>(t.z), static_cast<float>(t.w));
   }
 }
 
@@ -1862,37 +1888,66 @@ void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_
   k_history_t<R, false><<<gr, kHistThreads, 0, st>>>(f, nullptr, f.chunks, f.nchunks, f.work, m_dt);
 }
 
+template <class R, int SH>
+static size_t sweep_smem() {
+  return SweepCfg<R, SH>::kStages * sweep_stage_bytes<R, SH>();
+}
+
+// fn(std::integral_constant<int, shape>) for a sweep shape 0..kSweepShapes-1
+template <class F>
+static void with_shape(int shape, F&& fn) {
+  switch (shape) {
+    case 1: fn(std::integral_constant<int, 1>{}); break;
+    case 2: fn(std::integral_constant<int, 2>{}); break;
+    case 3: fn(std::integral_constant<int, 3>{}); break;
+    default: fn(std::integral_constant<int, 0>{}); break;
+  }
+}
+
+// Grid of the sweep (every CTA gets at least one chunk).
+static int sweep_grid(int grid, int nchunks) { return grid < nchunks ? grid : (nchunks > 0 ? nchunks : 1); }
+
 template <class R>
 static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   if (f.nchunks == 0) return;
-  const int gr = grid < f.nchunks ? grid : f.nchunks;
-  k_sweep<R><<<gr, kSweepThreads, kSweepStages * sweep_stage_bytes<R>(), st>>>(f, m_dt);
+  const int gr = sweep_grid(grid, f.nchunks);
+  with_shape(f.sweep_shape, [&](auto sh) {
+    constexpr int SH = decltype(sh)::value;
+    k_sweep<R, SH><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(f, m_dt);
+  });
 }
 
 template <class R>
 void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st, cudaEvent_t sweep_done) {
   launch_sweep<R>(f, m_dt, grid, st);
   if (sweep_done) cudaEventRecord(sweep_done, st);
-  k_sweep_finish<R><<<(f.nmodes + 7) / 8, 256, 0, st>>>(f, f.AT, f.AN, true);
+  k_sweep_finish<R><<<(f.nmodes + 255) / 256, 256, 0, st>>>(f, f.AT, f.AN, true, sweep_grid(grid, f.nchunks));
 }
 
 template <class R>
 void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   // into BT/BN; the commit adds the new slot's term
   launch_sweep<R>(f, 2 * m_dt, grid, st);
-  k_sweep_finish<R><<<(f.nmodes + 7) / 8, 256, 0, st>>>(f, f.BT, f.BN, false);
+  k_sweep_finish<R><<<(f.nmodes + 255) / 256, 256, 0, st>>>(f, f.BT, f.BN, false, sweep_grid(grid, f.nchunks));
 }
 
 template <class R>
-int sweep_blocks_per_sm() {
+int sweep_blocks_per_sm(int shape) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R>, kSweepThreads,
-                                                kSweepStages * sweep_stage_bytes<R>());
+  with_shape(shape, [&](auto sh) {
+    constexpr int SH = decltype(sh)::value;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R, SH>, kSweepThreads, sweep_smem<R, SH>());
+  });
   return n;
 }
 
-int sweep_chunk_slots(int precision) {
-  return precision == 1 ? SweepCfg<float>::kSlots : SweepCfg<double>::kSlots;
+int sweep_chunk_slots(int precision, int shape) {
+  int n = 0;
+  with_shape(shape, [&](auto sh) {
+    constexpr int SH = decltype(sh)::value;
+    n = precision == 1 ? SweepCfg<float, SH>::kSlots : SweepCfg<double, SH>::kSlots;
+  });
+  return n;
 }
 
 template <class R>
@@ -2055,7 +2110,10 @@ void launch_real_part(int N, const double2* z, double* x, cudaStream_t st) {
 
 template <class R>
 void configure_kernels(const FftGeom& g) {
-  allow_smem(k_sweep<R>, kSweepStages * sweep_stage_bytes<R>());
+  allow_smem(k_sweep<R, 0>, sweep_smem<R, 0>());
+  allow_smem(k_sweep<R, 1>, sweep_smem<R, 1>());
+  allow_smem(k_sweep<R, 2>, sweep_smem<R, 2>());
+  allow_smem(k_sweep<R, 3>, sweep_smem<R, 3>());
   if constexpr (sizeof(R) == 4) {
     if (g.N <= kFusedMaxN)
       with_lgn(g.N, [&](auto lg) {
@@ -2108,8 +2166,8 @@ template void launch_history_ahead<double>(const DevFault<double>&, int, int, cu
 template void launch_history_ahead<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_history_atomic<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_history_atomic<float>(const DevFault<float>&, int, int, cudaStream_t);
-template int sweep_blocks_per_sm<double>();
-template int sweep_blocks_per_sm<float>();
+template int sweep_blocks_per_sm<double>(int);
+template int sweep_blocks_per_sm<float>(int);
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double, cudaStream_t);
 template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double, cudaStream_t);
 

@@ -100,6 +100,7 @@ struct DevFault {
   const Chunk* chunks;
   int nchunks;
   const int32_t *mfirst, *mcount;          // per mode: first chunk, chunks
+  int sweep_shape;                         // chunk length x stages of the history sweep (0..3)
   // FFT work
   Cx<R> *z, *zt, *Z, *y;                   // natural-order input, transposed, spectrum, output
   const Cx<R>* tw;                         // exp(-2 pi i j/N)
@@ -133,8 +134,8 @@ template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid,
 // last-arriver sums (writes AT/AN itself); used on caller-owned buffers.
 template <class R> void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
 // Resident CTAs per SM of the bulk-async sweep; its chunk length (lags).
-template <class R> int sweep_blocks_per_sm();
-int sweep_chunk_slots(int precision);
+template <class R> int sweep_blocks_per_sm(int shape);
+int sweep_chunk_slots(int precision, int shape);
 // The same sweep with the weights shifted by 2 m_dt, chunk partials only:
 // the part of the next step's sums that does not involve this step's
 // interval, computed while this step's passes run (overlapped form); the
