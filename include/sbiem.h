@@ -300,20 +300,21 @@ int sbiem_history_enqueue_marked(sbiem_t s, int64_t m, void* sweep_done);
  * graph per step).  Members keep their own state, read with sbiem_get_state
  * after sbiem_batch_status; they must share the device and the precision.
  * A member whose step fails stops committing (its own status word) while the
- * others go on.  Members with equal N, grid, material, truncation and
- * precision have equal convolution weights: the history sweep reads each
- * weight once for blocks of up to 8 such members.
+ * others go on.  The history convolution is one bulk-async sweep over the
+ * members' chunk tables laid end to end (statically partitioned over the
+ * CTAs), followed by one per-(member, mode) finish.
  *
- * sbiem_batch_create: n member handles (not owned); chunk_slots = history
- *   slots per chunk of the batched convolution (0: derived from the resident
- *   warps).  Errors: SBIEM_ERR_INVALID, SBIEM_ERR_NOMEM.
+ * sbiem_batch_create: n member handles (not owned); they must share the
+ *   device, the precision and the history sweep shape; chunk_slots must be 0
+ *   or the members' chunk length.  Errors: SBIEM_ERR_INVALID,
+ *   SBIEM_ERR_NOMEM.
  * sbiem_batch_enqueue: nsteps steps of each member's dt_min, asynchronous.
  * sbiem_batch_status: synchronize; per member (caller order) status flags
  *   and committed steps (arrays of n, may be NULL).
  * sbiem_batch_tune: autotuner -- times the batched history convolution for
- *   chunk lengths {256 ... 8192} slots and resident-CTA counts, reps timed
- *   launches each (median), and keeps the fastest; returns the choice and its
- *   time.  The state is not changed.
+ *   1 .. (occupancy limit) resident sweep CTAs per SM, reps timed launches
+ *   each (median), and keeps the fastest; returns the chunk length, the
+ *   choice and its time.  The state is not changed.
  */
 typedef struct sbiem_batch_s* sbiem_batch_t;
 int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_t chunk_slots);

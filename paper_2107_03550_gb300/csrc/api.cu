@@ -465,7 +465,10 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     const int per_sm = s->fp32() ? sweep_blocks_per_sm<float>(s->sweep_shape)
                                  : sweep_blocks_per_sm<double>(s->sweep_shape);
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
-    s->lag_grid = s->sm_count;
+    // the overlapped sweep leaves each SM room for the pass kernels: one CTA
+    // per SM beside the one-launch FP32 pass; with the four-kernel FFT
+    // (small CTAs) the full grid
+    s->lag_grid = (s->fp32() && N <= kFusedMaxN) ? s->sm_count : s->hist_grid;
     s->chunk_slots = sweep_chunk_slots(p.precision, s->sweep_shape);
   }
   s->Rn.assign(s->nmodes, 0);
@@ -1231,11 +1234,13 @@ struct sbiem_batch_s {
   };
   std::vector<Group> groups;
   void* fs = nullptr;  // DevFault<R>[members] on the device
-  GChunk* chunks = nullptr;
+  Chunk* chunks = nullptr;      // members' chunk tables, concatenated (member in Chunk::pad)
   int nchunks = 0;
-  double4* partial = nullptr;
-  int* counter = nullptr;
-  int* work = nullptr;
+  double4* partial = nullptr;   // sweep partials per chunk
+  int64_t* cbase = nullptr;     // first chunk of each member
+  int2* mm = nullptr;           // (member, mode) pairs of the per-mode sums
+  int TM = 0;
+  int shape = 0;                // sweep shape shared by the members
   std::vector<void*> allocs;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
@@ -1265,91 +1270,54 @@ void* batch_alloc(sbiem_batch_s* b, size_t bytes) {
 
 // Members with equal N, grid, material, truncation and precision have equal
 // weights and can share a sweep.
-bool same_weights(const sbiem_s* a, const sbiem_s* b) {
-  const sbiem_params &p = a->p, &q = b->p;
-  return p.N == q.N && p.dx == q.dx && p.cs == q.cs && p.cp == q.cp && p.beta_min == q.beta_min &&
-         p.eta_w == q.eta_w && p.kc_L == q.kc_L && p.kc_units == q.kc_units && p.precision == q.precision;
-}
-
-// Chunk table over all members for a given chunk length: members sharing
-// weights form blocks of up to kGroupMax swept together; partial, counter
-// and work buffers sized for it; member descriptors pointing at them.
+// Ensemble chunk table: the members' own chunk tables one after another
+// (member index in Chunk::pad), each member's first chunk, the (member,
+// mode) list of the per-mode sums; member descriptors on the device.
 template <class R>
-int batch_build(sbiem_batch_s* b, int64_t chunk_slots) {
-  std::vector<GChunk> ch;
-  std::vector<int64_t> cbase(b->members.size() + 1, 0);
-  for (size_t r = 0; r < b->members.size(); ++r) cbase[r + 1] = cbase[r] + b->members[r]->nmodes;
-  size_t r0 = 0;
-  while (r0 < b->members.size()) {
-    size_t r1 = r0 + 1;
-    while (r1 < b->members.size() && r1 - r0 < static_cast<size_t>(kGroupMax) &&
-           same_weights(b->members[r0], b->members[r1]))
-      ++r1;
-    const sbiem_s* s = b->members[r0];
-    for (int n = 0; n < s->nmodes; ++n) {
-      const int64_t cnt = (s->Rn[n] + chunk_slots - 1) / chunk_slots;
-      const int first = static_cast<int>(ch.size());
-      for (int64_t c = 0; c < cnt; ++c) {
-        GChunk k{};
-        k.mode = n;
-        k.first = first;
-        k.count = static_cast<int32_t>(cnt);
-        k.m0 = static_cast<int32_t>(r0);
-        k.mcount = static_cast<int32_t>(r1 - r0);
-        k.i0 = c * chunk_slots;
-        k.i1 = std::min<int64_t>((c + 1) * chunk_slots, s->Rn[n]);
-        ch.push_back(k);
-      }
+int batch_build(sbiem_batch_s* b) {
+  std::vector<Chunk> ch;
+  std::vector<int64_t> cbase(b->members.size(), 0);
+  std::vector<int2> mm;
+  for (size_t r = 0; r < b->members.size(); ++r) {
+    const sbiem_s* s = b->members[r];
+    cbase[r] = static_cast<int64_t>(ch.size());
+    for (Chunk c : s->chunks) {
+      c.pad = static_cast<int32_t>(r);
+      ch.push_back(c);
     }
-    r0 = r1;
+    for (int n = 0; n < s->nmodes; ++n) mm.push_back(make_int2(static_cast<int>(r), n));
   }
-  if (ch.size() > static_cast<size_t>(1) << 28) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
-  auto realloc = [&](void** p, size_t bytes) {
-    if (*p) {
-      cudaFree(*p);
-      b->allocs.erase(std::remove(b->allocs.begin(), b->allocs.end(), *p), b->allocs.end());
-    }
-    *p = batch_alloc(b, bytes);
-    return *p != nullptr;
-  };
-  bool ok = realloc(reinterpret_cast<void**>(&b->chunks), sizeof(GChunk) * std::max<size_t>(ch.size(), 1)) &&
-            realloc(reinterpret_cast<void**>(&b->partial),
-                    sizeof(double4) * kGroupMax * std::max<size_t>(ch.size(), 1));
-  if (!b->counter) ok = ok && (b->counter = static_cast<int*>(batch_alloc(b, sizeof(int) * cbase.back()))) != nullptr;
-  if (!b->work) ok = ok && (b->work = static_cast<int*>(batch_alloc(b, sizeof(int)))) != nullptr;
-  if (!b->fs) ok = ok && (b->fs = batch_alloc(b, sizeof(DevFault<R>) * b->members.size())) != nullptr;
-  if (!ok) return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed");
+  if (ch.size() > static_cast<size_t>(1) << 30) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
+  b->chunks = static_cast<Chunk*>(batch_alloc(b, sizeof(Chunk) * std::max<size_t>(ch.size(), 1)));
+  b->partial = static_cast<double4*>(batch_alloc(b, sizeof(double4) * std::max<size_t>(ch.size(), 1)));
+  b->cbase = static_cast<int64_t*>(batch_alloc(b, sizeof(int64_t) * cbase.size()));
+  b->mm = static_cast<int2*>(batch_alloc(b, sizeof(int2) * std::max<size_t>(mm.size(), 1)));
+  b->fs = batch_alloc(b, sizeof(DevFault<R>) * b->members.size());
+  if (!b->chunks || !b->partial || !b->cbase || !b->mm || !b->fs)
+    return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed");
   std::vector<DevFault<R>> fs(b->members.size());
   for (size_t r = 0; r < b->members.size(); ++r) {
     DevFault<R> f;
     if constexpr (sizeof(R) == 8) f = b->members[r]->f64;
     else f = b->members[r]->f32;
-    f.partial = b->partial;
-    f.counter = b->counter + cbase[r];
-    f.work = b->work;
     f.newton_epw = 32;  // the batched Newton launch covers 32 elements per warp
     fs[r] = f;
   }
-  CK(cudaMemsetAsync(b->counter, 0, sizeof(int) * cbase.back(), b->stream));
-  CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(GChunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
+  if (!ch.empty())
+    CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->cbase, cbase.data(), sizeof(int64_t) * cbase.size(), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->mm, mm.data(), sizeof(int2) * mm.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->fs, fs.data(), sizeof(DevFault<R>) * fs.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
   b->nchunks = static_cast<int>(ch.size());
-  b->chunk_slots = chunk_slots;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    cudaGraphDestroy(b->graph_def);
-    b->graph = nullptr;
-    b->graph_def = nullptr;
-  }
+  b->TM = static_cast<int>(mm.size());
   return SBIEM_OK;
 }
 
 template <class R>
 void batch_history(sbiem_batch_s* b, cudaStream_t st) {
-  cudaMemsetAsync(b->work, 0, sizeof(int), st);
-  launch_history_groups<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->work, b->partial, 1,
-                           b->hist_grid, st);
+  launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
+                          b->cbase, b->shape, b->hist_grid, 1, st);
 }
 
 template <class R>
@@ -1413,10 +1381,17 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
     else configure_batch_kernels<double>(gr.g);
     b->groups.push_back(gr);
   }
+  for (int r = 1; r < n; ++r)
+    if (members[r]->sweep_shape != members[0]->sweep_shape)
+      return fail(SBIEM_ERR_INVALID, "batch members must share the history sweep shape");
+  b->shape = members[0]->sweep_shape;
+  if (chunk_slots > 0 && chunk_slots != members[0]->chunk_slots)
+    return fail(SBIEM_ERR_INVALID, "chunk_slots must be 0 or the members' chunk length");
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, members[0]->device);
-  b->per_sm = fp32 ? history_blocks_per_sm<float>() : history_blocks_per_sm<double>();
+  b->per_sm = fp32 ? sweep_blocks_per_sm<float>(b->shape) : sweep_blocks_per_sm<double>(b->shape);
   if (b->per_sm < 1) b->per_sm = 1;
   b->hist_grid = b->sm_count * b->per_sm;
+  b->chunk_slots = members[0]->chunk_slots;
   if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
     delete b;
     return fail(SBIEM_ERR_CUDA, "stream creation failed");
@@ -1427,13 +1402,7 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
   b->fork_join.resize(b->groups.size());
   for (auto& e : b->fork_join) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
   for (auto* m : b->members) cudaStreamSynchronize(m->stream);
-  if (chunk_slots <= 0) {
-    int64_t tot = 0;
-    for (auto* m : b->members) tot += m->total_slots;
-    const int64_t warps = static_cast<int64_t>(b->hist_grid) * 8;
-    chunk_slots = std::min<int64_t>(std::max<int64_t>((tot / (4 * warps) + 127) / 128 * 128, 128), 4096);
-  }
-  int rc = fp32 ? batch_build<float>(b, chunk_slots) : batch_build<double>(b, chunk_slots);
+  int rc = fp32 ? batch_build<float>(b) : batch_build<double>(b);
   if (rc) {
     batch_free(b);
     delete b;
@@ -1490,49 +1459,48 @@ int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done) {
 
 int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_out, float* ms_out) {
   if (!b || reps < 1) return fail(SBIEM_ERR_INVALID, "bad argument");
-  const int64_t cand_c[] = {256, 512, 1024, 2048, 4096, 8192};
-  std::vector<int> cand_b = {b->per_sm};
-  if (b->per_sm > 1) cand_b.push_back(b->per_sm - 1);
+  // resident sweep CTAs per SM: 1 .. the occupancy limit; the chunk length
+  // is the members' (their sweep shape)
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int64_t best_c = b->chunk_slots;
   int best_b = b->hist_grid / b->sm_count;
-  for (int64_t c : cand_c) {
-    int rc = b->fp32 ? batch_build<float>(b, c) : batch_build<double>(b, c);
-    if (rc) return rc;
-    for (int bl : cand_b) {
-      b->hist_grid = b->sm_count * bl;
-      // one untimed launch, then reps timed ones; take the median
+  for (int bl = 1; bl <= b->per_sm; ++bl) {
+    b->hist_grid = b->sm_count * bl;
+    // one untimed launch, then reps timed ones; take the median
+    if (b->fp32) batch_history<float>(b, b->stream);
+    else batch_history<double>(b, b->stream);
+    std::vector<float> t;
+    for (int k = 0; k < reps; ++k) {
+      CK(cudaEventRecord(e0, b->stream));
       if (b->fp32) batch_history<float>(b, b->stream);
       else batch_history<double>(b, b->stream);
-      std::vector<float> t;
-      for (int k = 0; k < reps; ++k) {
-        CK(cudaEventRecord(e0, b->stream));
-        if (b->fp32) batch_history<float>(b, b->stream);
-        else batch_history<double>(b, b->stream);
-        CK(cudaEventRecord(e1, b->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        t.push_back(ms);
-      }
-      std::sort(t.begin(), t.end());
-      const float med = t[t.size() / 2];
-      if (med < best) {
-        best = med;
-        best_c = c;
-        best_b = bl;
-      }
+      CK(cudaEventRecord(e1, b->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    const float med = t[t.size() / 2];
+    if (med < best) {
+      best = med;
+      best_b = bl;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->hist_grid = b->sm_count * best_b;
-  int rc = b->fp32 ? batch_build<float>(b, best_c) : batch_build<double>(b, best_c);
-  if (rc) return rc;
-  if (chunk_out) *chunk_out = best_c;
+  // the step graph holds the old grid
+  CK(cudaStreamSynchronize(b->stream));
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    cudaGraphDestroy(b->graph_def);
+    b->graph = nullptr;
+    b->graph_def = nullptr;
+  }
+  if (chunk_out) *chunk_out = b->chunk_slots;
   if (blocks_out) *blocks_out = best_b;
   if (ms_out) *ms_out = best;
   return SBIEM_OK;

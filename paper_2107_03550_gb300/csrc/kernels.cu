@@ -486,8 +486,8 @@ __global__ void __launch_bounds__((1 << LGN) / 8) k_spectral_fused_b(const DevFa
 
 
 // ------------------------------------ FP32 spectral pass on a CTA cluster
-// The same pass spread over a cluster of kClusterCTAs CTAs (one SM each),
-// for kClusterMinN <= N <= kClusterMaxN: four-step FFT with N = N1 N2,
+// The same pass spread over a cluster of C = cluster_ctas(N) CTAs (one SM each),
+// for kClusterMinN <= N <= kFusedMaxN: four-step FFT with N = N1 N2,
 // element n = n1 + N1 n2, mode m = k2 + N2 k1.  CTA c owns the columns
 // n1 in [c N1/C, (c+1) N1/C) and N2/C rows k2, taken from the sequence
 // 0, N2/2, 1, N2-1, 2, N2-2, ... so that a row and its mirror N2 - k2 (the
@@ -502,8 +502,9 @@ struct CGeom {
   static constexpr int N = 1 << LGN;
   static constexpr int lg1 = LGN / 2, lg2 = LGN - LGN / 2;
   static constexpr int N1 = 1 << lg1, N2 = 1 << lg2;
-  static constexpr int cols = N1 / kClusterCTAs, rows = N2 / kClusterCTAs;
-  static constexpr int nth = N / (8 * kClusterCTAs);
+  static constexpr int C = cluster_ctas(N);
+  static constexpr int cols = N1 / C, rows = N2 / C;
+  static constexpr int nth = N / (8 * C);
 };
 
 // Index of row k2 in the pair-adjacent sequence 0, N2/2, 1, N2-1, 2, ...
@@ -556,7 +557,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   using G = CGeom<LGN>;
   const unsigned c = cluster_rank();
   constexpr int N = G::N, half = N >> 1, nth = G::nth;
-  constexpr int per = N / kClusterCTAs;  // elements per CTA (8 per thread)
+  constexpr int per = N / G::C;  // elements per CTA (8 per thread)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* colbuf = reinterpret_cast<float2*>(smem_raw);  // [cols][N2]
   float2* rowbuf = colbuf + per;                          // [rows][N1]
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(CGeom<LGN>::nth) k_spectral_cluster(const __gr
 template <int LGN>
 __global__ void __launch_bounds__(CGeom<LGN>::nth) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs,
                                                                          int pass, int m_dt) {
-  const DevFault<float>& f = fs[blockIdx.x / kClusterCTAs];
+  const DevFault<float>& f = fs[blockIdx.x / CGeom<LGN>::C];
   spectral_cluster_body<LGN>(f, pass, m_dt, m_dt * f.dt_min);
 }
 
@@ -939,14 +940,19 @@ struct SweepPlan {
   const void* r2;
   const void* wsrc;
   unsigned b1, b2, bw;
-  int len, par, mode;
+  int len, par, mode, member;
 };
 constexpr int kPlanRing = 64;  // plans held in shared memory (a ring by chunk index)
 
-template <class R>
-__device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f, int c, int m_dt) {
+// Chunk c of the sweep: the fault's own chunk table, or an ensemble table
+// whose chunks name their member (Chunk::pad) in fs.
+template <class R, bool BATCH>
+__device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const DevFault<R>* fs, const Chunk* chunks,
+                                                int c, int m_dt) {
   SweepPlan pl{};
-  const Chunk cd = f.chunks[c];
+  const Chunk cd = chunks[c];
+  const DevFault<R>& f = BATCH ? fs[cd.pad] : f0;
+  pl.member = BATCH ? cd.pad : 0;
   const int n = cd.mode;
   const int Rn = f.Rn[n];
   const int64_t iend = min(cd.i1, static_cast<int64_t>(f.Mn[n]) - m_dt);
@@ -988,9 +994,12 @@ __device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* 
   bulk_g2s(sw, pl.wsrc, pl.bw, bar);
 }
 
-template <class R, int SH>
+// BATCH: the chunks of an ensemble (member in Chunk::pad), descriptors in fs;
+// members whose step failed are swept anyway (their sums are not written).
+template <class R, int SH, bool BATCH>
 __global__ void __launch_bounds__(kSweepThreads)
-    k_sweep(const __grid_constant__ DevFault<R> f, int m_dt) {
+    k_sweep(const __grid_constant__ DevFault<R> f, const DevFault<R>* __restrict__ fs,
+            const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt) {
   constexpr int S = SweepCfg<R, SH>::kSlots;
   constexpr int kSweepStages = SweepCfg<R, SH>::kStages;
   constexpr size_t SB = sweep_stage_bytes<R, SH>();
@@ -1002,10 +1011,9 @@ __global__ void __launch_bounds__(kSweepThreads)
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // one read of the status word (a concurrent pass may set it): uniform exit
-  if (tid == 0) s_skip = *f.status;
+  if (tid == 0) s_skip = BATCH ? 0u : *f.status;
   __syncthreads();
   if (s_skip) return;
-  const int nch = f.nchunks;
   const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
   const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
   const int nk = c1 - c0;
@@ -1015,7 +1023,8 @@ __global__ void __launch_bounds__(kSweepThreads)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // plans of the first kPlanRing chunks (one per thread)
-  for (int j = tid; j < kPlanRing && j < nk; j += kSweepThreads) plan[j] = sweep_plan<R>(f, c0 + j, m_dt);
+  for (int j = tid; j < kPlanRing && j < nk; j += kSweepThreads)
+    plan[j] = sweep_plan<R, BATCH>(f, fs, chunks, c0 + j, m_dt);
   __syncthreads();
   if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
@@ -1032,7 +1041,7 @@ __global__ void __launch_bounds__(kSweepThreads)
     // k + kPlanRing/2 .. k + kPlanRing - 1 replace chunks already issued)
     if (k > 0 && k % (kPlanRing / 2) == 0) {
       const int j = k + kPlanRing / 2 + tid;
-      if (tid < kPlanRing / 2 && j < nk) plan[j % kPlanRing] = sweep_plan<R>(f, c0 + j, m_dt);
+      if (tid < kPlanRing / 2 && j < nk) plan[j % kPlanRing] = sweep_plan<R, BATCH>(f, fs, chunks, c0 + j, m_dt);
     }
     const unsigned parity = static_cast<unsigned>(k / kSweepStages) & 1u;
     const bool ok = mbar_wait(&bars[s], parity);
@@ -1043,7 +1052,8 @@ __global__ void __launch_bounds__(kSweepThreads)
 #pragma unroll 4
       for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
     }
-    const bool seg_end = k + 1 == nk || plan[(k + 1) % kPlanRing].mode != plan[k % kPlanRing].mode;
+    const SweepPlan &pc = plan[k % kPlanRing], &pn = plan[(k + 1) % kPlanRing];
+    const bool seg_end = k + 1 == nk || pn.mode != pc.mode || pn.member != pc.member;
     if (seg_end) {
       Acc4<R> w4;
       w4.tr = warp_reduce_to_lane0(acc.tr);
@@ -1073,7 +1083,7 @@ __global__ void __launch_bounds__(kSweepThreads)
         out = make_double4(static_cast<double>(t.tr), static_cast<double>(t.ti), static_cast<double>(t.nr),
                            static_cast<double>(t.ni));
       }
-      f.partial[c0 + k] = out;
+      partial[c0 + k] = out;
     }
   }
   if (stuck && tid == 0) {
@@ -1120,110 +1130,36 @@ __global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* o
   }
 }
 
-// Ensemble version with shared weights: one warp per grouped chunk; for each
-// slot the weight is loaded once and applied to the rings of up to
-// kGroupMax members (their heads may differ).  Partial sums per (chunk,
-// member); the last warp of a (member, mode) adds them in chunk order.
+// Ensemble form of k_sweep_finish: one thread per (member, mode) pair
+// mm[t]; the member's chunks sit at cbase[member] + its own chunk indices in
+// the ensemble's chunk table.  Members whose step failed are left alone.
 template <class R>
-__global__ void __launch_bounds__(kHistThreads)
-    k_history_groups(const DevFault<R>* __restrict__ fs, const GChunk* __restrict__ chunks, int nchunks,
-                     int* work, double4* __restrict__ partial, int m_dt) {
-  constexpr int U = HistCfg<R>::kUnroll / 2 > 0 ? HistCfg<R>::kUnroll / 2 : 1;
-  const int lane = threadIdx.x & 31;
-  int c = 0;
-  if (lane == 0) c = atomicAdd(work, 1);
-  c = __shfl_sync(0xffffffffu, c, 0);
-  for (; c < nchunks; c = __shfl_sync(0xffffffffu, c, 0)) {
-    const GChunk cd = chunks[c];
-    const int n = cd.mode;
-    const DevFault<R>& f0 = fs[cd.m0];
-    const int Rn = f0.Rn[n];
-    const int64_t iend = min(cd.i1, static_cast<int64_t>(f0.Mn[n]) - m_dt);
-    const W2<R>* w = f0.w + f0.w_off[n] + m_dt;
-    const Slot<R>* ring[kGroupMax];
-    int hd[kGroupMax];
-    bool live[kGroupMax];
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) {
-      live[j] = false;
-      ring[j] = nullptr;
-      hd[j] = 0;
-      if (j < cd.mcount) {
-        const DevFault<R>& fj = fs[cd.m0 + j];
-        live[j] = *fj.status == 0u;
-        ring[j] = fj.ring + fj.ring_off[n];
-        hd[j] = fj.head[n];
-      }
+__global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int TM,
+                                 const int64_t* __restrict__ cbase, int nch, int G,
+                                 const double4* __restrict__ partial) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= TM) return;
+  const int2 rn = mm[t];
+  const DevFault<R>& f = fs[rn.x];
+  if (*f.status) return;
+  const int n = rn.y;
+  const int64_t F = cbase[rn.x] + f.mfirst[n], E = F + f.mcount[n];
+  double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
+  if (E > F) {
+    auto c0 = [&](int64_t b) { return b * nch / G; };
+    for (int64_t b = ((F + 1) * G + nch - 1) / nch - 1; b < G && c0(b) < E; ++b) {
+      const double4 u = partial[min(c0(b + 1), E) - 1];
+      acc.x += u.x;
+      acc.y += u.y;
+      acc.z += u.z;
+      acc.w += u.w;
     }
-    Acc4<R> acc[kGroupMax];
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) acc[j] = {R(0), R(0), R(0), R(0)};
-    for (int64_t i = cd.i0 + lane; i < iend; i += 32 * U) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t ii = i + 32 * u;
-        if (ii < iend) {
-          const W2<R> wv = __ldg(w + ii);
-#pragma unroll
-          for (int j = 0; j < kGroupMax; ++j) {
-            if (live[j]) {
-              int64_t slot = hd[j] + ii;
-              if (slot >= Rn) slot -= Rn;
-              slot_fma(acc[j], ld_slot(ring[j] + slot), wv);
-            }
-          }
-        }
-      }
-    }
-    const int cur = c;
-    if (lane == 0) c = atomicAdd(work, 1);
-#pragma unroll
-    for (int j = 0; j < kGroupMax; ++j) {
-      if (j >= cd.mcount || !live[j]) continue;
-      const double4 v = make_double4(static_cast<double>(warp_sum(acc[j].tr)), static_cast<double>(warp_sum(acc[j].ti)),
-                                     static_cast<double>(warp_sum(acc[j].nr)), static_cast<double>(warp_sum(acc[j].ni)));
-      const DevFault<R>& fj = fs[cd.m0 + j];
-      if (cd.count == 1) {
-        if (lane == 0) {
-          fj.AT[n] = make_double2(v.x, v.y);
-          fj.AN[n] = make_double2(v.z, v.w);
-          if (fj.AT32) {
-            fj.AT32[n] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
-            fj.AN32[n] = make_float2(static_cast<float>(v.z), static_cast<float>(v.w));
-          }
-        }
-        continue;
-      }
-      int prev = 0;
-      if (lane == 0) {
-        partial[static_cast<int64_t>(cur) * kGroupMax + j] = v;
-        __threadfence();
-        prev = atomicAdd(fj.counter + n, 1);
-      }
-      prev = __shfl_sync(0xffffffffu, prev, 0);
-      if (prev == cd.count - 1) {
-        __threadfence();
-        double4 r = make_double4(0.0, 0.0, 0.0, 0.0);
-        for (int q = lane; q < cd.count; q += 32) {
-          const double2* pp = reinterpret_cast<const double2*>(partial + static_cast<int64_t>(cd.first + q) * kGroupMax + j);
-          const double2 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
-          r.x += p0.x;
-          r.y += p0.y;
-          r.z += p1.x;
-          r.w += p1.y;
-        }
-        r = make_double4(warp_sum(r.x), warp_sum(r.y), warp_sum(r.z), warp_sum(r.w));
-        if (lane == 0) {
-          fj.AT[n] = make_double2(r.x, r.y);
-          fj.AN[n] = make_double2(r.z, r.w);
-          if (fj.AT32) {
-            fj.AT32[n] = make_float2(static_cast<float>(r.x), static_cast<float>(r.y));
-            fj.AN32[n] = make_float2(static_cast<float>(r.z), static_cast<float>(r.w));
-          }
-          fj.counter[n] = 0;
-        }
-      }
-    }
+  }
+  f.AT[n] = make_double2(acc.x, acc.y);
+  f.AN[n] = make_double2(acc.z, acc.w);
+  if (f.AT32) {
+    f.AT32[n] = make_float2(static_cast<float>(acc.x), static_cast<float>(acc.y));
+    f.AN32[n] = make_float2(static_cast<float>(acc.z), static_cast<float>(acc.w));
   }
 }
 
@@ -1806,7 +1742,7 @@ static size_t cluster_smem(int N) {
   int lg = 0;
   while ((1 << lg) < N) ++lg;
   const int N1 = 1 << (lg / 2), N2 = 1 << (lg - lg / 2);
-  const size_t per = static_cast<size_t>(N / kClusterCTAs);
+  const size_t per = static_cast<size_t>(N / cluster_ctas(N));
   return (4 * per + N1 / 2 + N2 / 2) * sizeof(float2) + per * sizeof(ModeIn);
 }
 
@@ -1835,13 +1771,14 @@ static_assert(kFusedMaxN == 1 << 14 && kClusterMinN == 1 << 11, "with_lgn covers
 template <class... Args>
 static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterCTAs * clusters);
-  cfg.blockDim = dim3(N / (8 * kClusterCTAs));
+  const int C = cluster_ctas(N);
+  cfg.gridDim = dim3(C * clusters);
+  cfg.blockDim = dim3(N / (8 * C));
   cfg.dynamicSmemBytes = cluster_smem(N);
   cfg.stream = st;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kClusterCTAs;
+  at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -1913,7 +1850,8 @@ static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, cudaStream_t 
   const int gr = sweep_grid(grid, f.nchunks);
   with_shape(f.sweep_shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
-    k_sweep<R, SH><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(f, m_dt);
+    k_sweep<R, SH, false><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(f, nullptr, f.chunks, f.nchunks,
+                                                                          f.partial, m_dt);
   });
 }
 
@@ -1936,7 +1874,7 @@ int sweep_blocks_per_sm(int shape) {
   int n = 0;
   with_shape(shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R, SH>, kSweepThreads, sweep_smem<R, SH>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R, SH, false>, kSweepThreads, sweep_smem<R, SH>());
   });
   return n;
 }
@@ -1951,24 +1889,17 @@ int sweep_chunk_slots(int precision, int shape) {
 }
 
 template <class R>
-void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, int* work, int m_dt, int grid,
+void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
+                          const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
                           cudaStream_t st) {
-  if (nchunks == 0) return;
-  const int warps = kHistThreads / 32;
-  const int need = (nchunks + warps - 1) / warps;
-  const int gr = grid < need ? grid : need;
-  DevFault<R> none{};
-  k_history_t<R, true><<<gr, kHistThreads, 0, st>>>(none, fs, chunks, nchunks, work, m_dt);
-}
-
-template <class R>
-void launch_history_groups(const DevFault<R>* fs, const GChunk* chunks, int nchunks, int* work, double4* partial,
-                           int m_dt, int grid, cudaStream_t st) {
-  if (nchunks == 0) return;
-  const int warps = kHistThreads / 32;
-  const int need = (nchunks + warps - 1) / warps;
-  const int gr = grid < need ? grid : need;
-  k_history_groups<R><<<gr, kHistThreads, 0, st>>>(fs, chunks, nchunks, work, partial, m_dt);
+  const int G = sweep_grid(grid, nchunks);
+  if (nchunks > 0)
+    with_shape(shape, [&](auto sh) {
+      constexpr int SH = decltype(sh)::value;
+      DevFault<R> none{};
+      k_sweep<R, SH, true><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(none, fs, chunks, nchunks, partial, m_dt);
+    });
+  k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial);
 }
 
 template <class R>
@@ -2009,8 +1940,12 @@ void configure_batch_kernels(const FftGeom& g) {
     if (g.N <= kFusedMaxN)
       with_lgn(g.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
-        if constexpr ((1 << LG) >= kClusterMinN) allow_smem(k_spectral_cluster_b<LG>, cluster_smem(g.N));
-        else allow_smem(k_spectral_fused_b<LG>, fused_smem(g.N));
+        if constexpr ((1 << LG) >= kClusterMinN) {
+          allow_smem(k_spectral_cluster_b<LG>, cluster_smem(g.N));
+          cudaFuncSetAttribute(k_spectral_cluster_b<LG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        } else {
+          allow_smem(k_spectral_fused_b<LG>, fused_smem(g.N));
+        }
       });
   }
   allow_smem(k_col_b<R, false, PRO_PASS>, col_smem<R>(g));
@@ -2110,16 +2045,24 @@ void launch_real_part(int N, const double2* z, double* x, cudaStream_t st) {
 
 template <class R>
 void configure_kernels(const FftGeom& g) {
-  allow_smem(k_sweep<R, 0>, sweep_smem<R, 0>());
-  allow_smem(k_sweep<R, 1>, sweep_smem<R, 1>());
-  allow_smem(k_sweep<R, 2>, sweep_smem<R, 2>());
-  allow_smem(k_sweep<R, 3>, sweep_smem<R, 3>());
+  allow_smem(k_sweep<R, 0, false>, sweep_smem<R, 0>());
+  allow_smem(k_sweep<R, 1, false>, sweep_smem<R, 1>());
+  allow_smem(k_sweep<R, 2, false>, sweep_smem<R, 2>());
+  allow_smem(k_sweep<R, 3, false>, sweep_smem<R, 3>());
+  allow_smem(k_sweep<R, 0, true>, sweep_smem<R, 0>());
+  allow_smem(k_sweep<R, 1, true>, sweep_smem<R, 1>());
+  allow_smem(k_sweep<R, 2, true>, sweep_smem<R, 2>());
+  allow_smem(k_sweep<R, 3, true>, sweep_smem<R, 3>());
   if constexpr (sizeof(R) == 4) {
     if (g.N <= kFusedMaxN)
       with_lgn(g.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
-        if constexpr ((1 << LG) >= kClusterMinN) allow_smem(k_spectral_cluster<LG>, cluster_smem(g.N));
-        else allow_smem(k_spectral_fused<LG>, fused_smem(g.N));
+        if constexpr ((1 << LG) >= kClusterMinN) {
+          allow_smem(k_spectral_cluster<LG>, cluster_smem(g.N));
+          cudaFuncSetAttribute(k_spectral_cluster<LG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        } else {
+          allow_smem(k_spectral_fused<LG>, fused_smem(g.N));
+        }
       });
   }
   const size_t cs = col_smem<R>(g), rs = row_smem<R>(g);
@@ -2134,12 +2077,10 @@ void configure_kernels(const FftGeom& g) {
   allow_smem(k_row<double, true>, row_smem<double>(g64));
 }
 
-template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, int*, int, int, cudaStream_t);
-template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, int*, int, int, cudaStream_t);
-template void launch_history_groups<double>(const DevFault<double>*, const GChunk*, int, int*, double4*, int, int,
-                                            cudaStream_t);
-template void launch_history_groups<float>(const DevFault<float>*, const GChunk*, int, int*, double4*, int, int,
-                                           cudaStream_t);
+template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
+                                           const int64_t*, int, int, int, cudaStream_t);
+template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
+                                          const int64_t*, int, int, int, cudaStream_t);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
 template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t);

@@ -38,19 +38,6 @@ struct Chunk {
   int64_t i0, i1;  // slot range [i0, i1) within the mode's ring
 };
 
-// One chunk of an ensemble whose members m0 .. m0+mcount-1 share their
-// weights (equal N, grid, material and truncation): the slot range is
-// swept once per weight for all of them.
-struct GChunk {
-  int32_t mode;
-  int32_t first;   // index of the mode's first chunk (same member block)
-  int32_t count;   // chunks of this mode for this member block
-  int32_t m0;      // first member
-  int32_t mcount;  // members in the block (<= kGroupMax)
-  int32_t pad;
-  int64_t i0, i1;
-};
-constexpr int kGroupMax = 8;
 
 // Four-step FFT geometry: N = N1 * N2, column pass (length N2) then row pass
 // (length N1); B columns or rows per CTA.
@@ -124,6 +111,10 @@ struct DevFault {
 constexpr int kFusedMaxN = 16384;
 constexpr int kClusterMinN = 2048;
 constexpr int kClusterCTAs = 8;
+// CTAs per cluster for a given N: 16 (a non-portable cluster size) at
+// N = 16384, which halves the per-CTA shared memory so the pass fits beside
+// a history-sweep CTA on an SM.
+constexpr int cluster_ctas(int N) { return N >= 16384 ? 16 : kClusterCTAs; }
 
 // Host launch wrappers (kernels.cu).
 // History sums AT/AN of a step of m_dt (bulk-async sweep, then per-mode
@@ -143,12 +134,12 @@ int sweep_chunk_slots(int precision, int shape);
 template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
 // Ensemble launches: fs is a device array of member descriptors; the pass and
 // commit kernels take one member per blockIdx.y (all members of equal N).
-template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, int* work,
-                                             int m_dt, int grid, cudaStream_t st);
-// Ensemble history convolution with weights shared by member blocks;
-// partial sums indexed chunk * kGroupMax + member offset.
-template <class R> void launch_history_groups(const DevFault<R>* fs, const GChunk* chunks, int nchunks, int* work,
-                                              double4* partial, int m_dt, int grid, cudaStream_t st);
+// Ensemble history sums: one bulk-async sweep over the concatenated chunk
+// tables of all members (member in Chunk::pad), then per (member, mode) sums
+// into each member's AT/AN; cbase[r] is member r's first chunk.
+template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
+                                             double4* partial, const int2* mm, int TM, const int64_t* cbase,
+                                             int shape, int grid, int m_dt, cudaStream_t st);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);
 template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st);
