@@ -314,7 +314,13 @@ int sbiem_history_enqueue_marked(sbiem_t s, int64_t m, void* sweep_done);
  * sbiem_batch_tune: autotuner -- times the batched history convolution for
  *   1 .. (occupancy limit) resident sweep CTAs per SM, reps timed launches
  *   each (median), and keeps the fastest; returns the chunk length, the
- *   choice and its time.  The state is not changed.
+ *   choice and its time.  It also times the overlapped sweep (one CTA per
+ *   SM beside the passes) and the passes, and makes later steps sweep the
+ *   next step's history beside the passes when that is faster (a new batch
+ *   steps without overlap).  The committed state is not changed.
+ * sbiem_batch_set_overlap: overlap on (1) or off (0) by hand; *on_out (may
+ *   be NULL) gets the setting in force before the call.  Results agree
+ *   either way up to summation order.
  */
 typedef struct sbiem_batch_s* sbiem_batch_t;
 int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_t chunk_slots);
@@ -323,6 +329,7 @@ int sbiem_batch_set_stream(sbiem_batch_t b, void* cuda_stream);
 int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps);
 int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done);
 int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* blocks_per_sm, float* ms);
+int sbiem_batch_set_overlap(sbiem_batch_t b, int on, int* on_out);
 
 /* ------------------------------------------------ learned Newton initial guess
  * A 5 -> 64 -> 64 -> 1 perceptron (GELU = x Phi(x)) predicts ln V* - ln V_prev

@@ -1228,6 +1228,10 @@ struct sbiem_batch_s {
   cudaStream_t stream = nullptr, own = nullptr;
   std::vector<cudaStream_t> branch;
   std::vector<cudaEvent_t> fork_join;
+  cudaStream_t side = nullptr;                       // overlapped history sweep
+  cudaEvent_t ev_fork = nullptr, ev_side = nullptr;
+  int lag_grid = 0;
+  bool overlap = false;  // sweep the next step beside the passes (sbiem_batch_tune / set_overlap)
   struct Group {
     int N, first, count;
     FftGeom g;
@@ -1258,6 +1262,12 @@ void batch_free(sbiem_batch_s* b) {
   b->allocs.clear();
   for (auto e : b->fork_join) cudaEventDestroy(e);
   for (auto st : b->branch) cudaStreamDestroy(st);
+  if (b->side) {
+    cudaStreamSynchronize(b->side);
+    cudaStreamDestroy(b->side);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_side) cudaEventDestroy(b->ev_side);
   if (b->own) cudaStreamDestroy(b->own);
 }
 
@@ -1314,35 +1324,50 @@ int batch_build(sbiem_batch_s* b) {
   return SBIEM_OK;
 }
 
+// Whole-window sums of every member (AT, AN), or with ahead = true the next
+// step's sums without its newest interval (BT, BN; weights shifted by 2).
 template <class R>
-void batch_history(sbiem_batch_s* b, cudaStream_t st) {
+void batch_history(sbiem_batch_s* b, cudaStream_t st, bool ahead = false) {
   launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
-                          b->cbase, b->shape, b->hist_grid, 1, st);
+                          b->cbase, b->shape, ahead ? b->lag_grid : b->hist_grid, ahead ? 2 : 1, st, ahead);
 }
 
+// The groups' two passes as parallel branches of st (joined on st).
 template <class R>
-void batch_group_step(sbiem_batch_s* b, const sbiem_batch_s::Group& gr, cudaStream_t st) {
-  const DevFault<R>* fs = static_cast<const DevFault<R>*>(b->fs) + gr.first;
-  launch_pass_batch<R>(gr.g, fs, gr.count, gr.N, 1, 1, st);
-  launch_pass_batch<R>(gr.g, fs, gr.count, gr.N, 2, 1, st);
-  launch_commit_batch<R>(fs, gr.count, gr.N, 1, st);
-}
-
-template <class R>
-void batch_enqueue_step(sbiem_batch_s* b, cudaStream_t st) {
-  batch_history<R>(b, st);
-  // groups as parallel branches: fork after the history convolution, join at the end
+void batch_passes(sbiem_batch_s* b, cudaStream_t st, cudaEvent_t fork) {
   const size_t ng = b->groups.size();
-  cudaEventRecord(b->fork_join[0], st);
   for (size_t k = 0; k < ng; ++k) {
+    const auto& gr = b->groups[k];
     cudaStream_t bs = k == 0 ? st : b->branch[k - 1];
-    if (k > 0) cudaStreamWaitEvent(bs, b->fork_join[0], 0);
-    batch_group_step<R>(b, b->groups[k], bs);
+    if (k > 0) cudaStreamWaitEvent(bs, fork, 0);
+    const DevFault<R>* fs = static_cast<const DevFault<R>*>(b->fs) + gr.first;
+    launch_pass_batch<R>(gr.g, fs, gr.count, gr.N, 1, 1, bs);
+    launch_pass_batch<R>(gr.g, fs, gr.count, gr.N, 2, 1, bs);
     if (k > 0) {
       cudaEventRecord(b->fork_join[k], bs);
       cudaStreamWaitEvent(st, b->fork_join[k], 0);
     }
   }
+}
+
+// One step of every member (dt_min).  Plain: whole-window sums, passes,
+// commits.  Overlapped (every member's AT/AN already hold this step's sums):
+// a side branch sweeps the next step's sums (BT/BN) while the groups'
+// passes run; after the join the commits add each member's newest interval.
+template <class R>
+void batch_enqueue_step(sbiem_batch_s* b, cudaStream_t st) {
+  const bool ov = b->overlap;
+  if (!ov) batch_history<R>(b, st);
+  cudaEventRecord(b->ev_fork, st);
+  if (ov) {
+    cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    batch_history<R>(b, b->side, true);
+    cudaEventRecord(b->ev_side, b->side);
+  }
+  batch_passes<R>(b, st, b->ev_fork);
+  if (ov) cudaStreamWaitEvent(st, b->ev_side, 0);
+  for (const auto& gr : b->groups)
+    launch_commit_batch<R>(static_cast<const DevFault<R>*>(b->fs) + gr.first, gr.count, gr.N, 1, st, ov ? 0 : -1);
 }
 
 }  // namespace
@@ -1401,6 +1426,15 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
   for (auto& st : b->branch) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   b->fork_join.resize(b->groups.size());
   for (auto& e : b->fork_join) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&b->ev_side, cudaEventDisableTiming);
+  {
+    // the overlapped sweep leaves room for the one-launch FP32 passes
+    bool small = fp32;
+    for (auto* m : b->members) small = small && m->N <= kFusedMaxN;
+    b->lag_grid = small ? b->sm_count : b->hist_grid;
+  }
   for (auto* m : b->members) cudaStreamSynchronize(m->stream);
   int rc = fp32 ? batch_build<float>(b) : batch_build<double>(b);
   if (rc) {
@@ -1427,7 +1461,15 @@ int sbiem_batch_set_stream(sbiem_batch_t b, void* stream) {
 
 int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps) {
   if (!b || nsteps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
-  for (auto* m : b->members) m->lag_m = -1;  // batched steps compute their own sums
+  // overlapped: every member's AT/AN must hold the next step's sums (they do
+  // after an overlapped sequence, batched or not, unless a member changed)
+  bool valid = true;
+  for (auto* m : b->members) valid = valid && m->lag_m == 1;
+  if (b->overlap && !valid && nsteps > 0) {
+    if (b->fp32) batch_history<float>(b, b->stream);
+    else batch_history<double>(b, b->stream);
+    CK(cudaGetLastError());
+  }
   if (!b->graph) {
     CK(cudaStreamSynchronize(b->stream));
     CK(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal));
@@ -1440,6 +1482,8 @@ int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps) {
     CK(cudaGraphInstantiate(&b->graph, b->graph_def, 0));
   }
   for (int64_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(b->graph, b->stream));
+  if (nsteps > 0)
+    for (auto* m : b->members) m->lag_m = b->overlap ? 1 : -1;
   return SBIEM_OK;
 }
 
@@ -1453,6 +1497,21 @@ int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done) {
     if (rc) return rc;
     if (flags) flags[b->order[q]] = fl;
     if (steps_done) steps_done[b->order[q]] = sd;
+  }
+  return SBIEM_OK;
+}
+
+int sbiem_batch_set_overlap(sbiem_batch_t b, int on, int* on_out) {
+  if (!b || (on != 0 && on != 1)) return fail(SBIEM_ERR_INVALID, "bad argument");
+  if (on_out) *on_out = b->overlap ? 1 : 0;
+  if ((on == 1) == b->overlap) return SBIEM_OK;
+  CK(cudaStreamSynchronize(b->stream));
+  b->overlap = on == 1;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    cudaGraphDestroy(b->graph_def);
+    b->graph = nullptr;
+    b->graph_def = nullptr;
   }
   return SBIEM_OK;
 }
@@ -1489,9 +1548,51 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
       best_b = bl;
     }
   }
+  b->hist_grid = b->sm_count * best_b;
+  // overlap or not: the overlapped step takes about max(lag sweep, passes),
+  // the plain one sweep + passes.  The passes write only staging arrays, so
+  // timing them leaves the committed state alone; the status words they may
+  // set are put back.
+  {
+    auto timed = [&](auto&& launch, float* out) -> int {
+      launch();
+      std::vector<float> t;
+      for (int k = 0; k < reps; ++k) {
+        CK(cudaEventRecord(e0, b->stream));
+        launch();
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+      }
+      std::sort(t.begin(), t.end());
+      *out = t[t.size() / 2];
+      return SBIEM_OK;
+    };
+    std::vector<unsigned> st0(b->members.size());
+    for (size_t r = 0; r < b->members.size(); ++r)
+      CK(cudaMemcpyAsync(&st0[r], b->members[r]->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    float t_lag = 0.f, t_pass = 0.f;
+    int rc = timed([&] {
+      if (b->fp32) batch_history<float>(b, b->stream, true);
+      else batch_history<double>(b, b->stream, true);
+    }, &t_lag);
+    if (rc) return rc;
+    rc = timed([&] {
+      cudaEventRecord(b->ev_fork, b->stream);
+      if (b->fp32) batch_passes<float>(b, b->stream, b->ev_fork);
+      else batch_passes<double>(b, b->stream, b->ev_fork);
+    }, &t_pass);
+    if (rc) return rc;
+    for (size_t r = 0; r < b->members.size(); ++r)
+      CK(cudaMemcpyAsync(b->members[r]->f64.status, &st0[r], sizeof(unsigned), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->overlap = std::max(t_lag, t_pass) < best + t_pass;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->hist_grid = b->sm_count * best_b;
   // the step graph holds the old grid
   CK(cudaStreamSynchronize(b->stream));
   if (b->graph) {

@@ -1136,7 +1136,7 @@ __global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* o
 template <class R>
 __global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int TM,
                                  const int64_t* __restrict__ cbase, int nch, int G,
-                                 const double4* __restrict__ partial) {
+                                 const double4* __restrict__ partial, bool ahead) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= TM) return;
   const int2 rn = mm[t];
@@ -1154,6 +1154,12 @@ __global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2*
       acc.z += u.z;
       acc.w += u.w;
     }
+  }
+  if (ahead) {
+    // overlapped form: the next step's sums without its newest interval
+    f.BT[n] = make_double2(acc.x, acc.y);
+    f.BN[n] = make_double2(acc.z, acc.w);
+    return;
   }
   f.AT[n] = make_double2(acc.x, acc.y);
   f.AN[n] = make_double2(acc.z, acc.w);
@@ -1502,9 +1508,9 @@ __global__ void k_commit(const __grid_constant__ DevFault<R> f, int m_dt, double
 }
 
 template <class R>
-__global__ void k_commit_b(const DevFault<R>* __restrict__ fs, int m_dt) {
+__global__ void k_commit_b(const DevFault<R>* __restrict__ fs, int m_dt, int lag_p) {
   const DevFault<R>& f = fs[blockIdx.y];
-  commit_body<R>(f, m_dt, m_dt * f.dt_min, -1);
+  commit_body<R>(f, m_dt, m_dt * f.dt_min, lag_p);
 }
 
 // Push of m_dt > 1 copies of this step's spectra (a step of m_dt dt_min,
@@ -1891,7 +1897,7 @@ int sweep_chunk_slots(int precision, int shape) {
 template <class R>
 void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
                           const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool ahead) {
   const int G = sweep_grid(grid, nchunks);
   if (nchunks > 0)
     with_shape(shape, [&](auto sh) {
@@ -1899,7 +1905,7 @@ void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunk
       DevFault<R> none{};
       k_sweep<R, SH, true><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(none, fs, chunks, nchunks, partial, m_dt);
     });
-  k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial);
+  k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial, ahead);
 }
 
 template <class R>
@@ -1929,9 +1935,9 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
 }
 
 template <class R>
-void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st) {
+void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st, int lag_p) {
   const int n = N;  // N > N/2 + 1 modes
-  k_commit_b<R><<<dim3((n + 255) / 256, members), 256, 0, st>>>(fs, m_dt);
+  k_commit_b<R><<<dim3((n + 255) / 256, members), 256, 0, st>>>(fs, m_dt, lag_p);
 }
 
 template <class R>
@@ -2078,13 +2084,13 @@ void configure_kernels(const FftGeom& g) {
 }
 
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
-                                           const int64_t*, int, int, int, cudaStream_t);
+                                           const int64_t*, int, int, int, cudaStream_t, bool);
 template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
-                                          const int64_t*, int, int, int, cudaStream_t);
+                                          const int64_t*, int, int, int, cudaStream_t, bool);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
-template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t);
-template void launch_commit_batch<float>(const DevFault<float>*, int, int, int, cudaStream_t);
+template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t, int);
+template void launch_commit_batch<float>(const DevFault<float>*, int, int, int, cudaStream_t, int);
 template void configure_batch_kernels<double>(const FftGeom&);
 template void configure_batch_kernels<float>(const FftGeom&);
 template int history_blocks_per_sm<double>();

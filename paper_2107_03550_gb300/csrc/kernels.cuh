@@ -139,10 +139,11 @@ template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int
 // into each member's AT/AN; cbase[r] is member r's first chunk.
 template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
                                              double4* partial, const int2* mm, int TM, const int64_t* cbase,
-                                             int shape, int grid, int m_dt, cudaStream_t st);
+                                             int shape, int grid, int m_dt, cudaStream_t st, bool ahead);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);
-template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st);
+template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st,
+                                            int lag_p = -1);
 template <class R> void configure_batch_kernels(const FftGeom& g);
 // Resident CTAs per SM of the history convolution (occupancy calculator).
 template <class R> int history_blocks_per_sm();

@@ -90,6 +90,7 @@ _SIGS = {
     "sbiem_batch_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _I64]),
     "sbiem_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
+    "sbiem_batch_set_overlap": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "sbiem_set_mlp": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "sbiem_harvest_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_harvest_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _I64, ctypes.c_int]),
@@ -504,6 +505,12 @@ class Batch:
 
     def enqueue(self, nsteps: int) -> None:
         self._check(self.lib.sbiem_batch_enqueue(self.h, int(nsteps)))
+
+    def set_overlap(self, on: bool) -> bool:
+        """Sweep the next step's history beside the passes (True) or not; returns the old setting."""
+        old = ctypes.c_int()
+        self._check(self.lib.sbiem_batch_set_overlap(self.h, 1 if on else 0, ctypes.byref(old)))
+        return bool(old.value)
 
     def status(self):
         n = len(self.members)

@@ -24,13 +24,15 @@ def _ensemble(seed0=100):
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
-def test_batch_equals_individual_steps(precision, tol):
+@pytest.mark.parametrize("precision,tol,overlap", [(0, 1e-12, False), (1, 1e-5, False), (0, 1e-12, True),
+                                                   (1, 1e-5, True)])
+def test_batch_equals_individual_steps(precision, tol, overlap):
     from paper_2107_03550_gb300.sbiem import Batch
     ws = _ensemble()
     solo = [gpu_for(w, precision=precision) for w in ws]
     mem = [gpu_for(w, precision=precision) for w in ws]
     b = Batch(mem)
+    assert b.set_overlap(overlap) is False  # a new batch steps without overlap
     steps = 40
     b.enqueue(steps)
     fl, sd = b.status()
