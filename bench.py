@@ -58,6 +58,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="skip the other precision's measurement (profiling runs)")
     return ap.parse_args()
 
 
@@ -318,8 +319,10 @@ def run_ours(a):
     flush = _flusher(torch)
     other = "fp64" if a.precision == "fp32" else "fp32"
     # the plain FP64 path and the chosen form, same workload, same timing
-    side = _measure(torch, a, other, rank, world, flush, dev_index)
-    side["g"].close()
+    side = None
+    if not a.no_side:
+        side = _measure(torch, a, other, rank, world, flush, dev_index)
+        side["g"].close()
     main = _measure(torch, a, a.precision, rank, world, flush, dev_index)
     e2e = None if a.no_e2e else _e2e(torch, a, main["g"], main["w"], world)
     cpu = None
@@ -344,9 +347,9 @@ def run_ours(a):
                        "device_bytes": main["dev_bytes"],
                        "newton_iters_last_step": {"sum": main["it_sum"], "max": main["it_max"]},
                        "history_ms_with_finish": main["hist_ms"],
-                       f"{other}_path": {"value": side["value"], "ms_per_step": side["ms_per_step"],
-                                         "sweep_ms": side["sweep_ms"],
-                                         "sweep_GBps": side["hist_bytes"] / (side["sweep_ms"] * 1e-3) / 1e9}},
+                       f"{other}_path": None if side is None else {
+                           "value": side["value"], "ms_per_step": side["ms_per_step"], "sweep_ms": side["sweep_ms"],
+                           "sweep_GBps": side["hist_bytes"] / (side["sweep_ms"] * 1e-3) / 1e9}},
             "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
                          "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,
