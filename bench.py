@@ -169,10 +169,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _sweep_source_sha() -> str:
+    """Hash of the history sweep's source section of kernels.cu (from its banner to the finish kernel)."""
+    src = open(os.path.join(ROOT, "paper_2107_03550_gb300", "csrc", "kernels.cu")).read()
+    a = src.index("// ---------------------------------------------- history sweep (bulk-async)")
+    b = src.index("// Per-mode sums of the sweep's segment partials")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
 def _traffic(precision: str, N: int):
-    """ncu DRAM bytes per history-convolution launch, if recorded for the current kernel source."""
-    src = open(os.path.join(ROOT, "paper_2107_03550_gb300", "csrc", "kernels.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    """ncu DRAM bytes per sweep launch, if recorded for the current sweep source (else None)."""
+    sha = _sweep_source_sha()
     path = os.path.join(ROOT, "profiles", f"k_sweep_{precision}_rough_cycle_N{N}.md")
     if not os.path.exists(path):
         return None
@@ -181,7 +188,7 @@ def _traffic(precision: str, N: int):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             fields[k.strip()] = v.strip()
-    if fields.get("kernels.cu sha256[:16]") != sha:
+    if fields.get("k_sweep source sha256[:16]") != sha:
         return None
     try:
         return float(fields["dram bytes per launch"])

@@ -32,6 +32,14 @@ template <class C> __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// serialization attribute may start while its predecessor runs; it must
+// read nothing the predecessor chain writes before pdl_wait() returns.
+// pdl_trigger() lets this kernel's own dependent start launching.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Shared-memory address of a generic pointer into this CTA's shared memory.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -424,6 +432,8 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   C* tw = buf + N;
   const int tid = threadIdx.x;
   __shared__ unsigned s_skip;
+  pdl_trigger();
+  pdl_wait();
   if (tid == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
@@ -571,10 +581,14 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   const int q0 = static_cast<int>(c) * G::rows;  // first sequence index of this CTA's rows
   // every CTA of the cluster runs before any remote store (arrive now, wait later)
   cluster_arrive_relaxed();
+  pdl_trigger();
   {
     // every global input up front (one memory latency), staged in shared
     // memory: the pass input, the four-step twiddles of both directions, the
-    // sub-table twiddles and the assembly inputs of this CTA's primary modes
+    // sub-table twiddles and the assembly inputs of this CTA's primary modes.
+    // Launched early behind the pass-1 Newton (pass 2), it reads before
+    // pdl_wait() only what no kernel of this step writes: twiddles and the
+    // running and history sums of the previous commit.
     const float2* zin = pass == 1 ? f.zin1 : f.zin2;
     float2 z[8], wf[8], wi[8];
     ModeIn mi[8];
@@ -584,12 +598,17 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int e = tid + q * nth;
-      z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
       wf[q] = tw_full(f.tw, (n1_0 + e / G::N2) * (e % G::N2), half, false);
       const int k2 = seq_row(q0 + e / G::N1, G::N2);
       wi[q] = tw_full(f.tw, (e % G::N1) * k2, half, true);
       const int m = k2 + G::N2 * (e % G::N1);
       if (m <= half) mi[q] = load_mode_in(f, m, m_dt, dt);
+    }
+    pdl_wait();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * nth;
+      z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
     }
     if (tid < (G::N2 >> 1)) twc[tid] = tcv;
     if (tid < (G::N1 >> 1)) twr[tid] = trv;
@@ -1249,6 +1268,10 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   // FP64 work of small faults over more SM partitions
   const int epw = f.newton_epw;
   const int i = threadIdx.x < epw ? blockIdx.x * epw + threadIdx.x : f.N;
+  // launched early behind the spectral pass: everything it reads is written
+  // by the kernels before it
+  pdl_trigger();
+  pdl_wait();
   // one read of the status word per block: other blocks may set it while
   // this one runs, and the decision must be uniform across the warp
   __shared__ unsigned s_skip;
@@ -1775,18 +1798,39 @@ static_assert(kFusedMaxN == 1 << 14 && kClusterMinN == 1 << 11, "with_lgn covers
 
 // Cluster launch of the FP32 spectral pass (one cluster per fault).
 template <class... Args>
-static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, Args... args) {
+static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, bool early,
+                                  Args... args) {
   cudaLaunchConfig_t cfg = {};
   const int C = cluster_ctas(N);
   cfg.gridDim = dim3(C * clusters);
   cfg.blockDim = dim3(N / (8 * C));
   cfg.dynamicSmemBytes = cluster_smem(N);
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = C;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = early ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Launch that may start before its predecessor on the stream finishes
+// (programmatic dependent launch; the kernel waits in pdl_wait()).
+template <class... Args>
+static void launch_early(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                         Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, args...);
@@ -1800,13 +1844,16 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
     if (f.N <= kFusedMaxN) {
       with_lgn(f.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
+        // pass 2 starts early behind the pass-1 Newton; Newton behind the pass
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster<LG>, 1, f.N, st, f, pass, m_dt, dt);
+          launch_cluster_kernel(k_spectral_cluster<LG>, 1, f.N, st, pass == 2, f, pass, m_dt, dt);
+        } else if (pass == 2) {
+          launch_early(k_spectral_fused<LG>, dim3(1), dim3(f.N / 8), fused_smem(f.N), st, f, pass, m_dt, dt);
         } else {
           k_spectral_fused<LG><<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
         }
       });
-      k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
+      launch_early(k_newton<R>, dim3((f.N + f.newton_epw - 1) / f.newton_epw), dim3(32), 0, st, f, pass, dt);
       return;
     }
   }
@@ -1916,7 +1963,7 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
       with_lgn(N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster_b<LG>, members, N, st, fs, pass, m_dt);
+          launch_cluster_kernel(k_spectral_cluster_b<LG>, members, N, st, false, fs, pass, m_dt);
         } else {
           k_spectral_fused_b<LG><<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
         }
