@@ -181,7 +181,8 @@ int sbiem_step_host(sbiem_t s, double dt, const double* tau_load, double* V_out)
 int sbiem_get_state(sbiem_t s, double* delta, double* V, double* theta,
                     double* tau_el, double* sigma_el, double* t);
 
-/* Replace the committed state (any pointer NULL keeps that field).  The
+/* Replace the committed state (any pointer NULL keeps that field).
+ * Prescribed elements keep V = V_presc whatever V holds for them.  The
  * spectral running sums F[delta], F[kappa delta] are recomputed. */
 int sbiem_set_state(sbiem_t s, const double* delta, const double* V,
                     const double* theta);

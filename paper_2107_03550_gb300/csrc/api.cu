@@ -965,14 +965,17 @@ int sbiem_set_state(sbiem_t s, const double* delta, const double* V, const doubl
   auto& f = s->f64;
   const int N = s->N;
   const size_t nb = sizeof(double) * N;
-  std::vector<double> Vh(N), th(N), Dc(N), psi(N), thd(N), xV(N);
+  std::vector<double> Vh(N), th(N), Dc(N), psi(N), thd(N), xV(N), Vp(N);
   std::vector<uint8_t> pr(N);
   CK(cudaMemcpyAsync(Vh.data(), f.V, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(th.data(), f.th, nb, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(Dc.data(), f.Dc, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(Vp.data(), f.Vp, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(pr.data(), f.presc, N, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   if (V) Vh.assign(V, V + N);
   for (int i = 0; i < N; ++i) {
+    if (pr[i]) Vh[i] = Vp[i];  // prescribed elements keep their slip rate
     if (theta) th[i] = theta[i];
     if (!(th[i] > 0)) return fail(SBIEM_ERR_INVALID, "theta must be positive");
     psi[i] = std::log(th[i]);

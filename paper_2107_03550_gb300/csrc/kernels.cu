@@ -1262,7 +1262,9 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
   return -maxit;
 }
 
-template <class R>
+// MLP: the variant that can evaluate the learned initial guess (compiled
+// separately so the plain solve stays small in the instruction cache).
+template <class R, bool MLP>
 __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, double dt) {
   // each warp (block) takes newton_epw elements: fewer than 32 spreads the
   // FP64 work of small faults over more SM partitions
@@ -1343,7 +1345,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     }
   }
   double xguess = CUDART_NAN;
-  if (f.mlp) {
+  if (MLP && f.mlp) {
     const float feat[kMlpIn] = {static_cast<float>(xstart), static_cast<float>(psip),
                                 static_cast<float>(tau / sig), static_cast<float>(a),
                                 static_cast<float>(have ? f.b[i] : 0.015)};
@@ -1352,8 +1354,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   if (have) {
     double x;
     if (f.presc[i]) {
-      const double vp = f.Vp[i];
-      x = vp > 0.0 ? log(vp) : -745.0;
+      x = xstart;  // ln V_presc, kept in ln V since creation
     } else if (!solve) {
       x = f.xV[i];
     } else {
@@ -1412,21 +1413,26 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   }
 }
 
-template <class R>
+template <class R, bool MLP>
 __global__ void __launch_bounds__(32) k_newton(const __grid_constant__ DevFault<R> f, int pass, double dt) {
-  newton_body<R>(f, pass, dt);
+  newton_body<R, MLP>(f, pass, dt);
 }
 
 template <class R>
 __global__ void __launch_bounds__(32) k_newton_b(const DevFault<R>* __restrict__ fs, int pass, int m_dt) {
   const DevFault<R>& f = fs[blockIdx.y];
-  newton_body<R>(f, pass, m_dt * f.dt_min);
+  newton_body<R, true>(f, pass, m_dt * f.dt_min);
 }
 
 // ------------------------------------------------------------- commit
 template <class R>
 __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, double dt, int lag_p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // launched early behind the pass-2 Newton: static tables first, then the wait
+  const bool md0 = i < f.nmodes;
+  const int Rn0 = md0 ? f.Rn[i] : 0;
+  const int64_t roff0 = md0 ? f.ring_off[i] : 0;
+  pdl_wait();
   // every load first (one memory latency), the status decision, then stores
   const unsigned status = *f.status;
   const bool el = i < f.N, md = i < f.nmodes;
@@ -1448,8 +1454,8 @@ __device__ __forceinline__ void commit_body(const DevFault<R>& f, int m_dt, doub
     Q = f.Q2f ? make_double2(f.Q2f[i].x, f.Q2f[i].y) : f.Q2[i];
     D = f.dhat[i];
     K = f.khat[i];
-    Rn = f.Rn[i];
-    roff = f.ring_off[i];
+    Rn = Rn0;
+    roff = roff0;
     h = f.head[i];
     if (lag_p >= 0) {
       T = f.BT[i];
@@ -1853,7 +1859,8 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
           k_spectral_fused<LG><<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
         }
       });
-      launch_early(k_newton<R>, dim3((f.N + f.newton_epw - 1) / f.newton_epw), dim3(32), 0, st, f, pass, dt);
+      launch_early(f.mlp ? k_newton<R, true> : k_newton<R, false>, dim3((f.N + f.newton_epw - 1) / f.newton_epw),
+                   dim3(32), 0, st, f, pass, dt);
       return;
     }
   }
@@ -1866,7 +1873,8 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   kfb<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.Z, R(1), f.status);
   kia<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
   kib<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.y, R(1.0 / g.N), f.status);
-  k_newton<R><<<(f.N + f.newton_epw - 1) / f.newton_epw, 32, 0, st>>>(f, pass, dt);
+  launch_early(f.mlp ? k_newton<R, true> : k_newton<R, false>, dim3((f.N + f.newton_epw - 1) / f.newton_epw),
+               dim3(32), 0, st, f, pass, dt);
 }
 
 template <class R>
@@ -2059,7 +2067,7 @@ template <class R>
 void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st, int lag_p) {
   const int n = f.N > f.nmodes ? f.N : f.nmodes;
   const int nt = 256;
-  k_commit<R><<<(n + nt - 1) / nt, nt, 0, st>>>(f, m_dt, m_dt * f.dt_min, lag_p);
+  launch_early(k_commit<R>, dim3((n + nt - 1) / nt), dim3(nt), 0, st, f, m_dt, m_dt * f.dt_min, lag_p);
 }
 
 template <class R>
