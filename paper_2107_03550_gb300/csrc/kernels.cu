@@ -279,8 +279,8 @@ __device__ __forceinline__ void dft8(float2 (&v)[8], float sg) {
   v[6] = t;
 }
 
-template <int O>
-__device__ __forceinline__ void dft4(float2 (&v)[8], float sg) {
+template <int O, int E>
+__device__ __forceinline__ void dft4(float2 (&v)[E], float sg) {
   bfly<0>(v[O + 0], v[O + 2], sg);
   bfly<2>(v[O + 1], v[O + 3], sg);
   bfly<0>(v[O + 0], v[O + 1], sg);
@@ -290,22 +290,23 @@ __device__ __forceinline__ void dft4(float2 (&v)[8], float sg) {
   v[O + 2] = t;
 }
 
-// One Stockham stage over buf (length L = 2^LGL, L/8 threads, tid < L/8)
+// One Stockham stage over buf (length L = 2^LGL, L/EPT threads holding EPT
+// values each, tid < L/EPT)
 // after sub-transforms of length Ns = 2^lgNs: for j < L/R, k = j mod Ns,
 // v_r = A[j + r L/R] exp(-sg 2 pi i r k / (Ns R)), an R-point DFT, and
 // A[(j - k) R + k + r Ns] = V_r (self-sorting; natural order after the last
 // stage).  Twiddles come from the L/2-entry table exp(-2 pi i a / L); all
 // index arithmetic is shifts and masks of compile-time sizes.
-template <int R, int LGL>
+template <int R, int LGL, int EPT = 8>
 __device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, int lgNs, int tid, float sg) {
   constexpr int L = 1 << LGL;
-  constexpr int NB = 8 / R;  // butterflies per thread
+  constexpr int NB = EPT / R;  // butterflies per thread
   constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
-  constexpr int nth = L / 8;
+  constexpr int nth = L / EPT;
   constexpr int stride = L / R;
   constexpr int half = L >> 1;
   const int Ns = 1 << lgNs;
-  float2 v[8];
+  float2 v[EPT];
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int j = tid + q * nth;
@@ -327,10 +328,10 @@ __device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, in
     dft8(v, sg);
   } else if constexpr (R == 4) {
     dft4<0>(v, sg);
-    dft4<4>(v, sg);
+    if constexpr (EPT == 8) dft4<4>(v, sg);
   } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) bfly<0>(v[2 * q], v[2 * q + 1], sg);
+    for (int q = 0; q < EPT / 2; ++q) bfly<0>(v[2 * q], v[2 * q + 1], sg);
   }
   __syncthreads();
 #pragma unroll
@@ -345,12 +346,20 @@ __device__ __forceinline__ void stockham_stage(float2* buf, const float2* tw, in
 }
 
 // FFT of length 2^LGL in buf: sg = +1 forward, -1 unscaled inverse.
-template <int LGL>
+// EPT = 8: radix-8 stages (+4 or 2); EPT = 4: radix-4 stages (+2), twice
+// the threads for the same length.
+template <int LGL, int EPT = 8>
 __device__ __noinline__ void fft_r8(float2* buf, const float2* tw, int tid, float sg) {
+  if constexpr (EPT == 8) {
 #pragma unroll 1
-  for (int s = 0; s < LGL / 3; ++s) stockham_stage<8, LGL>(buf, tw, 3 * s, tid, sg);
-  if constexpr (LGL % 3 == 2) stockham_stage<4, LGL>(buf, tw, 3 * (LGL / 3), tid, sg);
-  if constexpr (LGL % 3 == 1) stockham_stage<2, LGL>(buf, tw, 3 * (LGL / 3), tid, sg);
+    for (int s = 0; s < LGL / 3; ++s) stockham_stage<8, LGL>(buf, tw, 3 * s, tid, sg);
+    if constexpr (LGL % 3 == 2) stockham_stage<4, LGL>(buf, tw, 3 * (LGL / 3), tid, sg);
+    if constexpr (LGL % 3 == 1) stockham_stage<2, LGL>(buf, tw, 3 * (LGL / 3), tid, sg);
+  } else {
+#pragma unroll 1
+    for (int s = 0; s < LGL / 2; ++s) stockham_stage<4, LGL, 4>(buf, tw, 2 * s, tid, sg);
+    if constexpr (LGL % 2 == 1) stockham_stage<2, LGL, 4>(buf, tw, 2 * (LGL / 2), tid, sg);
+  }
 }
 
 // Per-mode inputs of the precision form's assembly: running sums F[delta],
@@ -507,14 +516,15 @@ __global__ void __launch_bounds__((1 << LGN) / 8) k_spectral_fused_b(const DevFa
 // FFTs of the rows; assembly of each pair (m, N-m) in place; inverse: row
 // FFTs, twiddle w_N^{-n1 k2}, scatter back to the column owners, barrier,
 // column FFTs, output.  N/(8C) threads per CTA, 8 values each per stage.
-template <int LGN>
+template <int LGN, int EPT = kClusterEPT>
 struct CGeom {
   static constexpr int N = 1 << LGN;
   static constexpr int lg1 = LGN / 2, lg2 = LGN - LGN / 2;
   static constexpr int N1 = 1 << lg1, N2 = 1 << lg2;
   static constexpr int C = cluster_ctas(N);
   static constexpr int cols = N1 / C, rows = N2 / C;
-  static constexpr int nth = N / (8 * C);
+  static constexpr int ept = EPT;                 // values per thread and FFT stage
+  static constexpr int nth = N / (EPT * C);
 };
 
 // Index of row k2 in the pair-adjacent sequence 0, N2/2, 1, N2-1, 2, ...
@@ -555,19 +565,19 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
   asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
-// Transforms of length 2^LGL (2^LGL/8 threads each) side by side in buf.
-template <int LGL>
+// Transforms of length 2^LGL (2^LGL/EPT threads each) side by side in buf.
+template <int LGL, int EPT>
 __device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int tid, float sg) {
-  constexpr int per = (1 << LGL) >> 3;
-  fft_r8<LGL>(buf + (tid / per) * (1 << LGL), tw, tid % per, sg);
+  constexpr int per = (1 << LGL) / EPT;
+  fft_r8<LGL, EPT>(buf + (tid / per) * (1 << LGL), tw, tid % per, sg);
 }
 
-template <int LGN>
+template <int LGN, int EPT>
 __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
-  using G = CGeom<LGN>;
+  using G = CGeom<LGN, EPT>;
   const unsigned c = cluster_rank();
   constexpr int N = G::N, half = N >> 1, nth = G::nth;
-  constexpr int per = N / G::C;  // elements per CTA (8 per thread)
+  constexpr int per = N / G::C;  // elements per CTA (EPT per thread)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* colbuf = reinterpret_cast<float2*>(smem_raw);  // [cols][N2]
   float2* rowbuf = colbuf + per;                          // [rows][N1]
@@ -590,13 +600,13 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
     // pdl_wait() only what no kernel of this step writes: twiddles and the
     // running and history sums of the previous commit.
     const float2* zin = pass == 1 ? f.zin1 : f.zin2;
-    float2 z[8], wf[8], wi[8];
-    ModeIn mi[8];
+    float2 z[EPT], wf[EPT], wi[EPT];
+    ModeIn mi[EPT];
     float2 tcv = make_float2(0.f, 0.f), trv = tcv;
     if (tid < (G::N2 >> 1)) tcv = f.tw[tid * G::N1];
     if (tid < (G::N1 >> 1)) trv = f.tw[tid * G::N2];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * nth;
       wf[q] = tw_full(f.tw, (n1_0 + e / G::N2) * (e % G::N2), half, false);
       const int k2 = seq_row(q0 + e / G::N1, G::N2);
@@ -606,14 +616,14 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
     }
     pdl_wait();
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * nth;
       z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
     }
     if (tid < (G::N2 >> 1)) twc[tid] = tcv;
     if (tid < (G::N1 >> 1)) twr[tid] = trv;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * nth;
       colbuf[(e % G::cols) * G::N2 + e / G::cols] = z[q];
       s_wf[e] = wf[q];
@@ -622,7 +632,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
     }
   }
   __syncthreads();
-  fft_r8_batch<G::lg2>(colbuf, twc, tid, 1.0f);
+  fft_r8_batch<G::lg2, EPT>(colbuf, twc, tid, 1.0f);
   cluster_wait();
   // twiddle w_N^{n1 k2}, scatter to the row owners
 #pragma unroll 1
@@ -634,7 +644,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   }
   cluster_arrive();
   cluster_wait();
-  fft_r8_batch<G::lg1>(rowbuf, twr, tid, 1.0f);
+  fft_r8_batch<G::lg1, EPT>(rowbuf, twr, tid, 1.0f);
   // assembly of the pairs (m, N-m) held by this CTA, in place
 #pragma unroll 1
   for (int e = tid; e < per; e += nth) {
@@ -657,7 +667,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
     if (ep != e) rowbuf[ep] = Yc;
   }
   __syncthreads();
-  fft_r8_batch<G::lg1>(rowbuf, twr, tid, -1.0f);
+  fft_r8_batch<G::lg1, EPT>(rowbuf, twr, tid, -1.0f);
   // twiddle w_N^{-n1 k2}, scatter back to the column owners
 #pragma unroll 1
   for (int e = tid; e < per; e += nth) {
@@ -668,7 +678,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   }
   cluster_arrive();
   cluster_wait();
-  fft_r8_batch<G::lg2>(colbuf, twc, tid, -1.0f);
+  fft_r8_batch<G::lg2, EPT>(colbuf, twc, tid, -1.0f);
   const float scale = 1.0f / static_cast<float>(N);
 #pragma unroll 1
   for (int e = tid; e < per; e += nth) {
@@ -677,17 +687,17 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
   }
 }
 
-template <int LGN>
-__global__ void __launch_bounds__(CGeom<LGN>::nth) k_spectral_cluster(const __grid_constant__ DevFault<float> f,
-                                                                       int pass, int m_dt, double dt) {
-  spectral_cluster_body<LGN>(f, pass, m_dt, dt);
+template <int LGN, int EPT>
+__global__ void __launch_bounds__(CGeom<LGN, EPT>::nth) k_spectral_cluster(const __grid_constant__ DevFault<float> f,
+                                                                            int pass, int m_dt, double dt) {
+  spectral_cluster_body<LGN, EPT>(f, pass, m_dt, dt);
 }
 
-template <int LGN>
-__global__ void __launch_bounds__(CGeom<LGN>::nth) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs,
-                                                                         int pass, int m_dt) {
-  const DevFault<float>& f = fs[blockIdx.x / CGeom<LGN>::C];
-  spectral_cluster_body<LGN>(f, pass, m_dt, m_dt * f.dt_min);
+template <int LGN, int EPT>
+__global__ void __launch_bounds__(CGeom<LGN, EPT>::nth) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs,
+                                                                              int pass, int m_dt) {
+  const DevFault<float>& f = fs[blockIdx.x / CGeom<LGN, EPT>::C];
+  spectral_cluster_body<LGN, EPT>(f, pass, m_dt, m_dt * f.dt_min);
 }
 
 // Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
@@ -1809,7 +1819,7 @@ static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, 
   cudaLaunchConfig_t cfg = {};
   const int C = cluster_ctas(N);
   cfg.gridDim = dim3(C * clusters);
-  cfg.blockDim = dim3(N / (8 * C));
+  cfg.blockDim = dim3(N / (kClusterEPT * C));
   cfg.dynamicSmemBytes = cluster_smem(N);
   cfg.stream = st;
   cudaLaunchAttribute at[2];
@@ -1852,7 +1862,7 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
         constexpr int LG = decltype(lg)::value;
         // pass 2 starts early behind the pass-1 Newton; Newton behind the pass
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster<LG>, 1, f.N, st, pass == 2, f, pass, m_dt, dt);
+          launch_cluster_kernel(k_spectral_cluster<LG, kClusterEPT>, 1, f.N, st, pass == 2, f, pass, m_dt, dt);
         } else if (pass == 2) {
           launch_early(k_spectral_fused<LG>, dim3(1), dim3(f.N / 8), fused_smem(f.N), st, f, pass, m_dt, dt);
         } else {
@@ -1971,7 +1981,7 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
       with_lgn(N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster_b<LG>, members, N, st, false, fs, pass, m_dt);
+          launch_cluster_kernel(k_spectral_cluster_b<LG, kClusterEPT>, members, N, st, false, fs, pass, m_dt);
         } else {
           k_spectral_fused_b<LG><<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
         }
@@ -2002,8 +2012,8 @@ void configure_batch_kernels(const FftGeom& g) {
       with_lgn(g.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          allow_smem(k_spectral_cluster_b<LG>, cluster_smem(g.N));
-          cudaFuncSetAttribute(k_spectral_cluster_b<LG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+          allow_smem(k_spectral_cluster_b<LG, kClusterEPT>, cluster_smem(g.N));
+          cudaFuncSetAttribute(k_spectral_cluster_b<LG, kClusterEPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         } else {
           allow_smem(k_spectral_fused_b<LG>, fused_smem(g.N));
         }
@@ -2119,8 +2129,8 @@ void configure_kernels(const FftGeom& g) {
       with_lgn(g.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          allow_smem(k_spectral_cluster<LG>, cluster_smem(g.N));
-          cudaFuncSetAttribute(k_spectral_cluster<LG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+          allow_smem(k_spectral_cluster<LG, kClusterEPT>, cluster_smem(g.N));
+          cudaFuncSetAttribute(k_spectral_cluster<LG, kClusterEPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         } else {
           allow_smem(k_spectral_fused<LG>, fused_smem(g.N));
         }

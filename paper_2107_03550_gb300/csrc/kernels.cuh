@@ -115,6 +115,12 @@ constexpr int kClusterCTAs = 8;
 // N = 16384, which halves the per-CTA shared memory so the pass fits beside
 // a history-sweep CTA on an SM.
 constexpr int cluster_ctas(int N) { return N >= 16384 ? 16 : kClusterCTAs; }
+// Values per thread in each FFT stage of the cluster pass (4: radix-4
+// stages, 8: radix-8 stages with half the threads).
+#ifndef SBIEM_CLUSTER_EPT
+#define SBIEM_CLUSTER_EPT 4
+#endif
+constexpr int kClusterEPT = SBIEM_CLUSTER_EPT;
 
 // Host launch wrappers (kernels.cu).
 // History sums AT/AN of a step of m_dt (bulk-async sweep, then per-mode
