@@ -1214,9 +1214,10 @@ __global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2*
 // FP64 is scarce on this part, so e^x is carried along the iteration: from
 // V_prev when Newton starts at ln V_prev, then multiplied by e^dx from a
 // Taylor series when |dx| <= 1/64 (truncation below 2e-19 relative), a full
-// exp otherwise (the caller takes a full exp of the root, so no error is
-// carried from one solve to the next).  Returns iterations (negative: not
-// converged); *xout = the root.
+// exp otherwise.  Returns iterations (negative: not converged); *xout = the
+// root, *exout = e^root from the carried value (e^x (1 + dx) at the last,
+// |dx| <= tol, step).  The caller takes a full exp every 1024th step, so the
+// stored slip rate and its logarithm cannot drift apart.
 __device__ __forceinline__ double exp_small(double d) {
   // e^d, |d| <= 1/64: Taylor polynomial of degree 7
   double p = 1.0 / 5040.0;
@@ -1231,7 +1232,7 @@ __device__ __forceinline__ double exp_small(double d) {
 
 __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, double a, double eta, double reta,
                                           double x0, double ex0, double xguess, double tol, int maxit,
-                                          double* xout) {
+                                          double* xout, double* exout) {
   const double sa = sig * a;
   // x_qs: only the guards below need it, so its division overlaps the
   // first residual (a start above x_qs has g < 0 and steps down)
@@ -1256,6 +1257,7 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     else dx = g / (e + sa);
     if (fabs(dx) <= tol) {
       *xout = x + dx;
+      *exout = ex * (1.0 + dx);
       return it;
     }
     double xn = x + dx;
@@ -1269,6 +1271,7 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     x = xn;
   }
   *xout = x;
+  *exout = ex;
   return -maxit;
 }
 
@@ -1297,6 +1300,8 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   // which still take part in the warp-wide network evaluation)
   double vb = 0.0, Dc = 1.0, rDc = 1.0, thp = 1.0, psip = 0.0, tau = 0.0, sig = 1.0, xstart = 0.0, a = 0.01,
          c0 = 0.0;
+  // every 1024th step recomputes ln theta and e^x in full (see below)
+  const bool resync_off = (*f.steps_done & 1023) != 0;
   bool solve = false;
   if (have) {
     // pass slip rate: the committed one, then the mean of committed and pass-1
@@ -1318,7 +1323,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
         thp = fma(th0, z, th0);
         // every 1024th step takes the full log, so ln theta and theta, kept
         // side by side, cannot drift apart by accumulated rounding
-        if (fabs(z) < 1e-3 && (*f.steps_done & 1023) != 0) {
+        if (fabs(z) < 1e-3 && resync_off) {
           // ln theta' = ln theta + log1p(z), series to z^6 (truncation below
           // |z|^7/7 < 2e-22)
           double l = -1.0 / 6.0;
@@ -1362,7 +1367,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     xguess = xstart + static_cast<double>(mlp_residual_warp(*f.mlp, feat));
   }
   if (have) {
-    double x;
+    double x, exn = -1.0;  // exn: e^x carried by the solve (< 0: not solved)
     if (f.presc[i]) {
       x = xstart;  // ln V_presc, kept in ln V since creation
     } else if (!solve) {
@@ -1370,7 +1375,8 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     } else {
       // e^xstart: the slip rate whose log starts Newton
       const double ex0 = (pass == 1) ? f.V[i] : f.V1[i];
-      const int it = solve_lnV(tau, sig, c0, a, f.eta, f.reta, xstart, ex0, xguess, f.newton_tol, f.newton_maxit, &x);
+      const int it =
+          solve_lnV(tau, sig, c0, a, f.eta, f.reta, xstart, ex0, xguess, f.newton_tol, f.newton_maxit, &x, &exn);
       if (it < 0) flags |= SBIEM_FLAG_NEWTON;
       iters = it < 0 ? -it : it;
       if (it > 0 && f.harvest) {
@@ -1386,7 +1392,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
         }
       }
     }
-    const double Vn = f.presc[i] ? f.Vp[i] : exp(x);
+    const double Vn = f.presc[i] ? f.Vp[i] : ((exn > 0.0 && resync_off) ? exn : exp(x));
     const double thd_new = 1.0 - thp * Vn * rDc;
     if (pass == 1) {
       f.V1[i] = Vn;
