@@ -185,8 +185,8 @@ def _traffic(precision: str, N: int):
         return None
     fields = {}
     for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+        if ": " in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(": ", 1)
             fields[k.strip()] = v.strip()
     if fields.get("k_sweep source sha256[:16]") != sha:
         return None
@@ -312,6 +312,31 @@ def _e2e(torch, a, g, w, world):
             "d2h_bytes_per_step": 8 * N + 12}
 
 
+def _read_ceiling(torch, nbytes: int, flush, reps: int = 20) -> dict:
+    """The library's plain streaming read (sbiem_read_probe) of the sweep's byte count, flushed and
+    timed like the sweep: what any read of this size reaches on this GPU, beside the large-copy peak."""
+    from paper_2107_03550_gb300.sbiem import read_probe
+    nb = (nbytes + 15) // 16 * 16
+    x = torch.zeros(nb // 4, dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for r in range(reps + 3):
+        flush()
+        e0.record()
+        read_probe(x.data_ptr(), nb, sink.data_ptr(), st)
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= 3:
+            ms.append(e0.elapsed_time(e1))
+    del x
+    t = statistics.mean(ms)
+    return {"GBps": nb / (t * 1e-3) / 1e9, "ms": t, "bytes": nb,
+            "what": "sbiem_read_probe: plain 128-bit streaming read of the sweep's algorithmic bytes, "
+                    "L2 flushed the same way"}
+
+
 def run_ours(a):
     import torch
     rank, world, local = _dist()
@@ -337,6 +362,8 @@ def run_ours(a):
         cpu = _oracle_leg(a.N, a.cpu_seconds)
     peak, peak_kind = _peaks()
     achieved = main["hist_bytes"] / (main["sweep_ms"] * 1e-3) / 1e9
+    ceiling = _read_ceiling(torch, main["hist_bytes"], flush)
+    ceiling["frac_of_peak"] = ceiling["GBps"] / peak
     if rank == 0:
         w = main["w"]
         line = {
@@ -361,7 +388,9 @@ def run_ours(a):
                          "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,
                          "traffic": _traffic(a.precision, a.N), "ms_per_launch": main["sweep_ms"],
-                         "algorithmic_bytes_per_launch": main["hist_bytes"]},
+                         "algorithmic_bytes_per_launch": main["hist_bytes"],
+                         # context: a plain read of the same bytes (the size, not the kernel, caps frac)
+                         "same_size_read": ceiling},
             "clocks": main["clocks"],
             "e2e": e2e,
             # per timed step: sweep + finish (side branch), two passes of

@@ -293,6 +293,19 @@ int sbiem_history_sums_noalloc(int64_t nmodes, int32_t precision, int64_t m,
 int sbiem_history_enqueue(sbiem_t s, int64_t m);
 int sbiem_history_enqueue_marked(sbiem_t s, int64_t m, void* sweep_done);
 
+/* sbiem_read_probe -- a measurement helper, not a step of the method: read
+ * `bytes` bytes of device memory at `data` once with coalesced 128-bit loads
+ * (4 CTAs of 256 threads per SM, eight loads in flight per thread) and sum
+ * them as float4s; `sink` (device, one float) is written only if the sum
+ * equals a sentinel, which keeps the loads.  It gives the bandwidth a plain
+ * read of that many bytes reaches, the ceiling beside which the history
+ * sweep's fraction of the large-copy peak is read (fixed launch and ramp
+ * costs weigh on reads of tens of MB).  `data` must be 16-byte aligned and
+ * `bytes` a multiple of 16; enqueued on `stream` (a cudaStream_t, NULL: the
+ * legacy stream), no synchronization.  Errors: SBIEM_ERR_INVALID for a null
+ * or misaligned pointer or size, SBIEM_ERR_CUDA for a failed launch. */
+int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream);
+
 /* ------------------------------------------------------------- ensembles
  * A batch advances many faults together (independent realizations of uneven
  * N): one launch of the history convolution covers the chunks of every

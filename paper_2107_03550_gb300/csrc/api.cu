@@ -249,9 +249,6 @@ void probe_mark(sbiem_s* s, int k, cudaStream_t st) {
 template <class R>
 void enqueue_step_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
   probe_mark(s, 0, st);
-  cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
-  cudaMemsetAsync(f.work, 0, sizeof(int), st);
   probe_mark(s, 1, st);
   launch_history<R>(f, m, s->hist_grid, st);
   probe_mark(s, 2, st);
@@ -269,9 +266,6 @@ template <class R>
 void enqueue_step_lag_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
   int p = 0;
   while ((1 << p) < m) ++p;
-  cudaMemsetAsync(f.it_sum, 0, sizeof(unsigned long long), st);
-  cudaMemsetAsync(f.it_max, 0, sizeof(int), st);
-  cudaMemsetAsync(f.work, 0, sizeof(int), st);
   cudaEventRecord(s->ev_fork, st);
   cudaStreamWaitEvent(s->side, s->ev_fork, 0);
   launch_history_ahead<R>(f, m, s->lag_grid, s->side);
@@ -286,7 +280,6 @@ void enqueue_step_lag_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st
 // The step without its commit: pass-2 results stay staged (delta2, V2, ...).
 template <class R>
 void enqueue_trial_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st) {
-  cudaMemsetAsync(f.work, 0, sizeof(int), st);
   launch_history<R>(f, m, s->hist_grid, st);
   launch_pass<R>(f, 1, m, st);
   launch_pass<R>(f, 2, m, st);
@@ -757,7 +750,6 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
     }
     if (s->lag_m != m) {
       // prologue: this step's full sums
-      CK(cudaMemsetAsync(s->f64.work, 0, sizeof(int), s->stream));
       if (s->fp32()) launch_history<float>(s->f32, m, s->hist_grid, s->stream);
       else launch_history<double>(s->f64, m, s->hist_grid, s->stream);
       CK(cudaGetLastError());
@@ -1066,7 +1058,6 @@ int sbiem_get_history(sbiem_t s, double* hT, double* hN) {
 int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN) {
   if (!s || !AT || !AN || m < 1 || m > (int64_t(1) << 30)) return fail(SBIEM_ERR_INVALID, "bad argument");
   const int mi = static_cast<int>(m);
-  CK(cudaMemsetAsync(s->f64.work, 0, sizeof(int), s->stream));
   if (s->fp32()) launch_history<float>(s->f32, mi, s->hist_grid, s->stream);
   else launch_history<double>(s->f64, mi, s->hist_grid, s->stream);
   CK(cudaGetLastError());
@@ -1090,6 +1081,17 @@ int sbiem_history_enqueue_marked(sbiem_t s, int64_t m, void* sweep_done) {
 }
 
 int sbiem_history_enqueue(sbiem_t s, int64_t m) { return sbiem_history_enqueue_marked(s, m, nullptr); }
+
+int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream) {
+  if (!data || !sink || bytes <= 0 || (bytes & 15) || (reinterpret_cast<uintptr_t>(data) & 15))
+    return fail(SBIEM_ERR_INVALID, "read probe: null or misaligned pointer or size");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  launch_read_probe(data, bytes, sink, sms, static_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
+  return SBIEM_OK;
+}
 
 namespace {
 void drop_graphs(sbiem_s* s) {

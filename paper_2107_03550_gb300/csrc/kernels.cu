@@ -165,6 +165,17 @@ __device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass,
 // Column pass: for n1 in this CTA's B columns, transform x[n1 + N1 n2] over
 // n2 (length N2), multiply by exp(-+2 pi i n1 k2 / N), store to
 // out[k2 N1 + n1].
+// The Newton statistics of a step (iteration sum and maximum) start at zero:
+// the pass-1 spectral kernels reset them (one thread per fault), and both
+// Newton passes of the step run after those kernels have completed.
+template <class R>
+__device__ __forceinline__ void reset_newton_stats(const DevFault<R>& f, int pass, bool leader) {
+  if (pass == 1 && leader && f.it_sum) {
+    *f.it_sum = 0ull;
+    *f.it_max = 0;
+  }
+}
+
 template <class R, bool INV, int PRO>
 __device__ __forceinline__ void col_body(const FftGeom& g, const Cx<R>* __restrict__ tw,
                                          const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out,
@@ -175,6 +186,7 @@ __device__ __forceinline__ void col_body(const FftGeom& g, const Cx<R>* __restri
   const int M = g.N2, B = g.Bc;
   C* twm = buf + B * M;
   const int tid = threadIdx.x, nth = blockDim.x;
+  if (PRO != PRO_LOAD) reset_newton_stats(f, pass, blockIdx.x == 0 && tid == 0);
   // the status word only changes in k_newton, never while this kernel runs
   if (PRO != PRO_LOAD && *f.status) return;
   for (int j = tid; j < (M >> 1); j += nth) twm[j] = tw[j * g.N1];
@@ -443,6 +455,7 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   __shared__ unsigned s_skip;
   pdl_trigger();
   pdl_wait();
+  reset_newton_stats(f, pass, tid == 0);
   if (tid == 0) s_skip = *f.status;
   __syncthreads();
   if (s_skip) return;
@@ -615,6 +628,7 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
       if (m <= half) mi[q] = load_mode_in(f, m, m_dt, dt);
     }
     pdl_wait();
+    reset_newton_stats(f, pass, c == 0 && tid == 0);
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       const int e = tid + q * nth;
@@ -1039,15 +1053,15 @@ __global__ void __launch_bounds__(kSweepThreads)
   __shared__ Acc4<R> red[2][NW];
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // one read of the status word (a concurrent pass may set it): uniform exit
-  if (tid == 0) s_skip = BATCH ? 0u : *f.status;
-  __syncthreads();
-  if (s_skip) return;
   const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
   const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
   const int nk = c1 - c0;
   if (nk <= 0) return;
+  // one read of the status word (a concurrent pass may set it), taken beside
+  // the loads of the first plans and checked once they are in: a uniform
+  // exit without a memory round trip of its own before the first copy
   if (tid == 0) {
+    s_skip = BATCH ? 0u : *f.status;
     for (int s = 0; s < kSweepStages; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -1055,6 +1069,7 @@ __global__ void __launch_bounds__(kSweepThreads)
   for (int j = tid; j < kPlanRing && j < nk; j += kSweepThreads)
     plan[j] = sweep_plan<R, BATCH>(f, fs, chunks, c0 + j, m_dt);
   __syncthreads();
+  if (s_skip) return;
   if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
       sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
@@ -2055,6 +2070,31 @@ void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaS
   if (f.nchunks == 0) return;
   const int grid = f.nchunks < 4096 ? f.nchunks : 4096;
   k_ring_undo<R><<<grid, 256, 0, st>>>(f, m_dt, static_cast<Slot<R>*>(undo), dir);
+}
+
+// Plain streaming read of n16 float4s (grid-stride, eight loads in flight
+// per thread): see sbiem_read_probe.
+__global__ void __launch_bounds__(256) k_read_probe(const float4* __restrict__ p, int64_t n16, float* sink) {
+  constexpr int U = 8;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  float acc = 0.f;
+  for (; i + (U - 1) * stride < n16; i += U * stride) {
+    float4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = __ldcs(p + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+  }
+  for (; i < n16; i += stride) {
+    const float4 v = __ldcs(p + i);
+    acc += (v.x + v.y) + (v.z + v.w);
+  }
+  if (acc == -1234.5f) *sink = acc;
+}
+
+void launch_read_probe(const void* p, int64_t bytes, float* sink, int sm_count, cudaStream_t st) {
+  k_read_probe<<<4 * sm_count, 256, 0, st>>>(static_cast<const float4*>(p), bytes / 16, sink);
 }
 
 __global__ void k_to_float2(const double2* a, float2* out, int n) {

@@ -123,6 +123,8 @@ constexpr int cluster_ctas(int N) { return N >= 16384 ? 16 : kClusterCTAs; }
 constexpr int kClusterEPT = SBIEM_CLUSTER_EPT;
 
 // Host launch wrappers (kernels.cu).
+// Plain streaming read of `bytes` (16-byte aligned; sbiem_read_probe).
+void launch_read_probe(const void* p, int64_t bytes, float* sink, int sm_count, cudaStream_t st);
 // History sums AT/AN of a step of m_dt (bulk-async sweep, then per-mode
 // sums of its chunk partials).
 template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st,

@@ -75,6 +75,7 @@ _SIGS = {
     "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
     "sbiem_history_enqueue": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_history_enqueue_marked": (ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
+    "sbiem_read_probe": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP]),
     "sbiem_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "sbiem_get_params": (ctypes.c_int, [_VP, ctypes.c_void_p]),
     "sbiem_load": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_char_p, ctypes.c_void_p]),
@@ -186,6 +187,16 @@ def history_sums_noalloc(nmodes: int, precision: int, m: int, ring: int, weights
                                         head, AT, AN, raw or None)
     if rc != 0:
         raise SbiemError(rc, "history_sums_noalloc: invalid sizes or CUDA failure")
+
+
+def read_probe(data: int, nbytes: int, sink: int, stream=None) -> None:
+    """Enqueue one plain streaming read of nbytes at device pointer data (a measurement helper;
+    see sbiem_read_probe in the C header).  sink: device pointer to one float."""
+    lib = load_library()
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = lib.sbiem_read_probe(data, int(nbytes), sink, raw or None)
+    if rc != 0:
+        raise SbiemError(rc, "read_probe: null or misaligned pointer or size, or CUDA failure")
 
 
 MLP_PARAMS, MLP_NORM = 4609, 12

@@ -359,3 +359,16 @@ def test_checkpoint_continues_bitwise(tmp_path, precision):
     assert np.array_equal(H1[0], H2[0]) and np.array_equal(H1[1], H2[1])
     g.close()
     h.close()
+
+
+@pytest.mark.gpu
+def test_read_probe_reads_and_leaves_sink():
+    # the measurement helper: one plain read of a buffer (ragged tail of the
+    # grid stride), nothing written unless the sum hits its sentinel
+    import torch
+    from paper_2107_03550_gb300.sbiem import read_probe
+    x = torch.ones((1 << 22) + 12, dtype=torch.float32, device="cuda")
+    sink = torch.full((1,), 7.0, dtype=torch.float32, device="cuda")
+    read_probe(x.data_ptr(), x.numel() * 4, sink.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert float(sink.item()) == 7.0

@@ -69,6 +69,14 @@ def test_kernel_values_rejects_bad_input(lib):
         kernel_values(np.array([1.0]), 1.5)
 
 
+def test_read_probe_rejects_bad_arguments(lib):
+    # host-side checks only: none of these reaches a CUDA call
+    from paper_2107_03550_gb300.sbiem import SbiemError, read_probe
+    for data, nbytes, sink in ((0, 1024, 16), (16, 1000, 16), (8, 1024, 16), (16, 0, 16), (16, 1024, 0)):
+        with pytest.raises(SbiemError):
+            read_probe(data, nbytes, sink)
+
+
 def test_strerror_covers_codes(lib):
     for code in range(0, -9, -1):
         assert lib.sbiem_strerror(code)
