@@ -1306,24 +1306,39 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   // this one runs, and the decision must be uniform across the warp
   __shared__ unsigned s_skip;
   if (threadIdx.x == 0) s_skip = *f.status;
+  const bool have = i < f.N;
+  // every per-element input is loaded here, unconditionally and beside the
+  // status read: one memory latency before the arithmetic (lanes without an
+  // element read element 0; a value a branch below does not use costs only
+  // its bytes)
+  const int ic = have ? i : 0;
+  const double ld_V = f.V[ic], ld_V1 = f.V1[ic], ld_Dc = f.Dc[ic], ld_rDc = f.rDc[ic], ld_th = f.th[ic];
+  const double ld_psi = f.psi[ic], ld_thd = f.thd[ic], ld_thd1 = f.thd1[ic];
+  const Cx<R> y = f.y[ic];
+  const double ld_tau0 = f.tau0[ic], ld_taur = f.taur[ic], ld_sig0 = f.sig0[ic];
+  const double ld_xV = f.xV[ic], ld_x1 = f.x1[ic];
+  const bool ld_presc = f.presc[ic] != 0;
+  const double ld_a = f.a[ic], ld_b = f.b[ic], ld_lvd = f.lvd[ic], ld_Vp = f.Vp[ic];
+  const double ld_kappa = f.kappa[ic], ld_delta = f.delta[ic];
+  const double t_now = *f.t;
+  const long long steps = *f.steps_done;
   __syncthreads();
   if (s_skip) return;
   unsigned flags = 0u;
   int iters = 0;
-  const bool have = i < f.N;
   // per-element quantities of the solve (dummies on lanes without an element,
   // which still take part in the warp-wide network evaluation)
   double vb = 0.0, Dc = 1.0, rDc = 1.0, thp = 1.0, psip = 0.0, tau = 0.0, sig = 1.0, xstart = 0.0, a = 0.01,
          c0 = 0.0;
   // every 1024th step recomputes ln theta and e^x in full (see below)
-  const bool resync_off = (*f.steps_done & 1023) != 0;
+  const bool resync_off = (steps & 1023) != 0;
   bool solve = false;
   if (have) {
     // pass slip rate: the committed one, then the mean of committed and pass-1
-    vb = (pass == 1) ? f.V[i] : 0.5 * (f.V[i] + f.V1[i]);
-    Dc = f.Dc[i];
-    rDc = f.rDc[i];
-    const double th0 = f.th[i];
+    vb = (pass == 1) ? ld_V : 0.5 * (ld_V + ld_V1);
+    Dc = ld_Dc;
+    rDc = ld_rDc;
+    const double th0 = ld_th;
     const double rth0 = 1.0 / th0;  // off the chain: used only in the series branch
     bool series = false;
     if (f.state_law == 0) {
@@ -1347,7 +1362,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
           l = fma(l, z, 1.0 / 3.0);
           l = fma(l, z, -0.5);
           l = fma(l, z, 1.0);
-          psip = fma(l, z, f.psi[i]);
+          psip = fma(l, z, ld_psi);
           series = true;
         }
       } else {
@@ -1356,40 +1371,39 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
         thp = fma(th0, eu, dt * (-em / u));
       }
     } else {
-      const double thdb = (pass == 1) ? f.thd[i] : 0.5 * (f.thd[i] + f.thd1[i]);
+      const double thdb = (pass == 1) ? ld_thd : 0.5 * (ld_thd + ld_thd1);
       thp = th0 + thdb * dt;
       if (!(thp > 0.0)) flags |= SBIEM_FLAG_STATE;
     }
     if (!series) psip = log(thp);
-    const double t_end = *f.t + dt;
-    const Cx<R> y = f.y[i];
-    tau = f.tau0[i] + f.taur[i] * t_end + static_cast<double>(y.x);
-    sig = f.sig0[i] + static_cast<double>(y.y);
-    xstart = (pass == 1) ? f.xV[i] : f.x1[i];
-    if (!f.presc[i]) {
+    const double t_end = t_now + dt;
+    tau = ld_tau0 + ld_taur * t_end + static_cast<double>(y.x);
+    sig = ld_sig0 + static_cast<double>(y.y);
+    xstart = (pass == 1) ? ld_xV : ld_x1;
+    if (!ld_presc) {
       if (!(sig > 0.0)) flags |= SBIEM_FLAG_OPENING;
       solve = flags == 0u;
-      a = f.a[i];
+      a = ld_a;
       // f0 + a (x - ln V0) + b ln(theta V0 / Dc) = c0 + a x
-      c0 = f.f0 + f.b[i] * (psip + f.lvd[i]) - a * f.lnV0;
+      c0 = f.f0 + ld_b * (psip + ld_lvd) - a * f.lnV0;
     }
   }
   double xguess = CUDART_NAN;
   if (MLP && f.mlp) {
     const float feat[kMlpIn] = {static_cast<float>(xstart), static_cast<float>(psip),
                                 static_cast<float>(tau / sig), static_cast<float>(a),
-                                static_cast<float>(have ? f.b[i] : 0.015)};
+                                static_cast<float>(have ? ld_b : 0.015)};
     xguess = xstart + static_cast<double>(mlp_residual_warp(*f.mlp, feat));
   }
   if (have) {
     double x, exn = -1.0;  // exn: e^x carried by the solve (< 0: not solved)
-    if (f.presc[i]) {
+    if (ld_presc) {
       x = xstart;  // ln V_presc, kept in ln V since creation
     } else if (!solve) {
-      x = f.xV[i];
+      x = ld_xV;
     } else {
       // e^xstart: the slip rate whose log starts Newton
-      const double ex0 = (pass == 1) ? f.V[i] : f.V1[i];
+      const double ex0 = (pass == 1) ? ld_V : ld_V1;
       const int it =
           solve_lnV(tau, sig, c0, a, f.eta, f.reta, xstart, ex0, xguess, f.newton_tol, f.newton_maxit, &x, &exn);
       if (it < 0) flags |= SBIEM_FLAG_NEWTON;
@@ -1402,12 +1416,12 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
           row[1] = static_cast<float>(psip);
           row[2] = static_cast<float>(tau / sig);
           row[3] = static_cast<float>(a);
-          row[4] = static_cast<float>(f.b[i]);
+          row[4] = static_cast<float>(ld_b);
           row[5] = static_cast<float>(x);
         }
       }
     }
-    const double Vn = f.presc[i] ? f.Vp[i] : ((exn > 0.0 && resync_off) ? exn : exp(x));
+    const double Vn = ld_presc ? ld_Vp : ((exn > 0.0 && resync_off) ? exn : exp(x));
     const double thd_new = 1.0 - thp * Vn * rDc;
     if (pass == 1) {
       f.V1[i] = Vn;
@@ -1415,8 +1429,8 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       f.thd1[i] = thd_new;
       if (f.zin2) {
         // FP32 input of the pass-2 FFT
-        const double v2 = 0.5 * (f.V[i] + Vn);
-        f.zin2[i] = make_float2(static_cast<float>(v2), static_cast<float>(f.kappa[i] * v2));
+        const double v2 = 0.5 * (ld_V + Vn);
+        f.zin2[i] = make_float2(static_cast<float>(v2), static_cast<float>(ld_kappa * v2));
       }
     } else {
       f.V2[i] = Vn;
@@ -1424,7 +1438,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       f.psi2[i] = psip;
       f.th2[i] = thp;
       f.thd2[i] = thd_new;
-      f.delta2[i] = f.delta[i] + vb * dt;
+      f.delta2[i] = ld_delta + vb * dt;
     }
   }
   // warp-level aggregation of flags and iteration counts, one atomic per warp
