@@ -456,9 +456,8 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
   pdl_trigger();
   pdl_wait();
   reset_newton_stats(f, pass, tid == 0);
+  // the status word is read beside the inputs and checked once they are in
   if (tid == 0) s_skip = *f.status;
-  __syncthreads();
-  if (s_skip) return;
   // nth = N/8: each thread owns 4 twiddles, 8 inputs and at most 5 modes
   // (m = tid + q nth <= N/2) of the assembly; every global input is loaded
   // up front (one memory latency), into registers.
@@ -482,6 +481,7 @@ __device__ __forceinline__ void spectral_fused_body(const DevFault<float>& f, in
     for (int q = 0; q < 8; ++q) buf[tid + q * nth] = zv[q];
   }
   __syncthreads();
+  if (s_skip) return;
   fft_r8<LGN>(buf, tw, tid, 1.0f);
 #pragma unroll
   for (int q = 0; q < kMpt; ++q) {
@@ -627,12 +627,23 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
       const int m = k2 + G::N2 * (e % G::N1);
       if (m <= half) mi[q] = load_mode_in(f, m, m_dt, dt);
     }
+    // pass 1 is launched behind completed kernels: its input joins the loads
+    // above; pass 2's input is written by the pass-1 Newton it waits for
+    if (pass == 1) {
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + q * nth;
+        z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
+      }
+    }
     pdl_wait();
     reset_newton_stats(f, pass, c == 0 && tid == 0);
+    if (pass != 1) {
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * nth;
-      z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
+      for (int q = 0; q < EPT; ++q) {
+        const int e = tid + q * nth;
+        z[q] = zin[(n1_0 + e % G::cols) + G::N1 * (e / G::cols)];
+      }
     }
     if (tid < (G::N2 >> 1)) twc[tid] = tcv;
     if (tid < (G::N1 >> 1)) twr[tid] = trv;
@@ -1053,6 +1064,8 @@ __global__ void __launch_bounds__(kSweepThreads)
   __shared__ Acc4<R> red[2][NW];
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // the per-mode finish may be resident already, waiting for this grid
+  pdl_trigger();
   const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
   const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
   const int nk = c1 - c0;
@@ -1150,6 +1163,8 @@ template <class R>
 __global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* outT, double2* outN, bool f32,
                                int G) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  // launched early behind the sweep: its partials are read after the wait
+  pdl_wait();
   if (n >= f.nmodes || *f.status) return;
   const int64_t nch = f.nchunks;
   const int64_t F = f.mfirst[n], E = F + f.mcount[n];
@@ -1961,18 +1976,27 @@ static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, cudaStream_t 
   });
 }
 
+// The per-mode finish starts early behind the sweep (its blocks wait for
+// the sweep's completion on the device instead of a launch after it).
+template <class R>
+static void launch_finish(const DevFault<R>& f, double2* outT, double2* outN, bool f32, int grid, cudaStream_t st) {
+  const DevFault<R> fv = f;
+  const int G = sweep_grid(grid, f.nchunks);
+  launch_early(k_sweep_finish<R>, dim3((f.nmodes + 255) / 256), dim3(256), 0, st, fv, outT, outN, f32, G);
+}
+
 template <class R>
 void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st, cudaEvent_t sweep_done) {
   launch_sweep<R>(f, m_dt, grid, st);
   if (sweep_done) cudaEventRecord(sweep_done, st);
-  k_sweep_finish<R><<<(f.nmodes + 255) / 256, 256, 0, st>>>(f, f.AT, f.AN, true, sweep_grid(grid, f.nchunks));
+  launch_finish<R>(f, f.AT, f.AN, true, grid, st);
 }
 
 template <class R>
 void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   // into BT/BN; the commit adds the new slot's term
   launch_sweep<R>(f, 2 * m_dt, grid, st);
-  k_sweep_finish<R><<<(f.nmodes + 255) / 256, 256, 0, st>>>(f, f.BT, f.BN, false, sweep_grid(grid, f.nchunks));
+  launch_finish<R>(f, f.BT, f.BN, false, grid, st);
 }
 
 template <class R>
