@@ -78,6 +78,7 @@ struct sbiem_s {
   int lag_m = -1;
   int lag_grid = 0;  // CTAs of the overlapped sweep (leaves room for the passes)
   int sweep_shape = 0;  // chunk length x stages of the sweep (SBIEM_SWEEP_SHAPE overrides)
+  int lag_shape = 0;    // the same for the overlapped sweep
   // timing probe: 4 events per slot; graph event-record nodes are retargeted
   // to the slot of each launch
   int pslots = 0;
@@ -198,6 +199,7 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   }
   f.newton_maxit = s->p.newton_maxit;
   f.sweep_shape = s->sweep_shape;
+  f.lag_shape = s->lag_shape;
   f.newton_tol = s->p.newton_tol;
 }
 
@@ -458,10 +460,20 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     const int per_sm = s->fp32() ? sweep_blocks_per_sm<float>(s->sweep_shape)
                                  : sweep_blocks_per_sm<double>(s->sweep_shape);
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
-    // the overlapped sweep leaves each SM room for the pass kernels: one CTA
-    // per SM beside the one-launch FP32 pass; with the four-kernel FFT
+    // the overlapped sweep leaves each SM room for the pass kernels: beside
+    // the one-launch FP32 pass, shape 3's chunks in one stage (shape 4), two
+    // CTAs per SM (with shape 3's two stages only one would fit beside a
+    // pass CTA); other shapes one CTA per SM; with the four-kernel FFT
     // (small CTAs) the full grid
-    s->lag_grid = (s->fp32() && N <= kFusedMaxN) ? s->sm_count : s->hist_grid;
+    s->lag_shape = s->sweep_shape;
+    s->lag_grid = s->hist_grid;
+    if (s->fp32() && N <= kFusedMaxN) {
+      s->lag_grid = s->sm_count;
+      if (s->sweep_shape == 3) {
+        s->lag_shape = 4;
+        s->lag_grid = 2 * s->sm_count;
+      }
+    }
     s->chunk_slots = sweep_chunk_slots(p.precision, s->sweep_shape);
   }
   s->Rn.assign(s->nmodes, 0);

@@ -924,13 +924,14 @@ __global__ void __launch_bounds__(kHistThreads)
 // Shapes of the sweep: lags per chunk (= stage buffer) x stages in flight per
 // CTA.  Shape 0: 512 x 4 (FP32, 12 KB stages) / 256 x 4 (FP64, 12 KB);
 // shape 1: twice the lags; shape 2: twice the stages; shape 3: 4x the lags, 2
-// stages.
+// stages; shape 4: shape 3's chunks in one stage (49 KB), for the sweep that
+// runs beside the spectral passes: two of its CTAs and a pass CTA share an SM.
 template <class R, int SH> struct SweepCfg {
   static constexpr int kBase = sizeof(R) == 4 ? 512 : 256;
-  static constexpr int kSlots = SH == 1 ? 2 * kBase : (SH == 3 ? 4 * kBase : kBase);
-  static constexpr int kStages = SH == 2 ? 8 : (SH == 3 ? 2 : 4);
+  static constexpr int kSlots = SH == 1 ? 2 * kBase : (SH >= 3 ? 4 * kBase : kBase);
+  static constexpr int kStages = SH == 2 ? 8 : (SH == 3 ? 2 : (SH == 4 ? 1 : 4));
 };
-constexpr int kSweepShapes = 4;
+constexpr int kSweepShapes = 5;
 constexpr int kSweepThreads = 128;
 constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls before a wait is declared stuck
 
@@ -1958,6 +1959,7 @@ static void with_shape(int shape, F&& fn) {
     case 1: fn(std::integral_constant<int, 1>{}); break;
     case 2: fn(std::integral_constant<int, 2>{}); break;
     case 3: fn(std::integral_constant<int, 3>{}); break;
+    case 4: fn(std::integral_constant<int, 4>{}); break;
     default: fn(std::integral_constant<int, 0>{}); break;
   }
 }
@@ -1966,10 +1968,10 @@ static void with_shape(int shape, F&& fn) {
 static int sweep_grid(int grid, int nchunks) { return grid < nchunks ? grid : (nchunks > 0 ? nchunks : 1); }
 
 template <class R>
-static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
+static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, int shape, cudaStream_t st) {
   if (f.nchunks == 0) return;
   const int gr = sweep_grid(grid, f.nchunks);
-  with_shape(f.sweep_shape, [&](auto sh) {
+  with_shape(shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
     k_sweep<R, SH, false><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(f, nullptr, f.chunks, f.nchunks,
                                                                           f.partial, m_dt);
@@ -1987,7 +1989,7 @@ static void launch_finish(const DevFault<R>& f, double2* outT, double2* outN, bo
 
 template <class R>
 void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st, cudaEvent_t sweep_done) {
-  launch_sweep<R>(f, m_dt, grid, st);
+  launch_sweep<R>(f, m_dt, grid, f.sweep_shape, st);
   if (sweep_done) cudaEventRecord(sweep_done, st);
   launch_finish<R>(f, f.AT, f.AN, true, grid, st);
 }
@@ -1995,7 +1997,7 @@ void launch_history(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st, c
 template <class R>
 void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st) {
   // into BT/BN; the commit adds the new slot's term
-  launch_sweep<R>(f, 2 * m_dt, grid, st);
+  launch_sweep<R>(f, 2 * m_dt, grid, f.lag_shape, st);
   launch_finish<R>(f, f.BT, f.BN, false, grid, st);
 }
 
@@ -2204,10 +2206,12 @@ void configure_kernels(const FftGeom& g) {
   allow_smem(k_sweep<R, 1, false>, sweep_smem<R, 1>());
   allow_smem(k_sweep<R, 2, false>, sweep_smem<R, 2>());
   allow_smem(k_sweep<R, 3, false>, sweep_smem<R, 3>());
+  allow_smem(k_sweep<R, 4, false>, sweep_smem<R, 4>());
   allow_smem(k_sweep<R, 0, true>, sweep_smem<R, 0>());
   allow_smem(k_sweep<R, 1, true>, sweep_smem<R, 1>());
   allow_smem(k_sweep<R, 2, true>, sweep_smem<R, 2>());
   allow_smem(k_sweep<R, 3, true>, sweep_smem<R, 3>());
+  allow_smem(k_sweep<R, 4, true>, sweep_smem<R, 4>());
   if constexpr (sizeof(R) == 4) {
     if (g.N <= kFusedMaxN)
       with_lgn(g.N, [&](auto lg) {

@@ -88,6 +88,7 @@ struct DevFault {
   int nchunks;
   const int32_t *mfirst, *mcount;          // per mode: first chunk, chunks
   int sweep_shape;                         // chunk length x stages of the history sweep (0..3)
+  int lag_shape;                           // the same for the sweep beside the passes (0..4)
   // FFT work
   Cx<R> *z, *zt, *Z, *y;                   // natural-order input, transposed, spectrum, output
   const Cx<R>* tw;                         // exp(-2 pi i j/N)
