@@ -97,7 +97,15 @@ def windows(p: Params) -> np.ndarray:
     the ceiling of T_w / dt_min, taken with a relative slack of 1e-12 so that
     an exact integer ratio is not pushed up by rounding.  Mode 0 has no
     traction (|k| = 0) and gets M_0 = 0.
+
+    eta_w = 0 selects the quasi-dynamic limit (Appendix, Quasi-dynamic BIEM):
+    the past slip rate acts only through the radiation damping of
+    Eq. (momentum), so every window is empty, and with it the history sums
+    and the current-interval kernel term; the elastic response is the static
+    stiffness alone.
     """
+    if p.eta_w == 0:
+        return np.zeros(p.N // 2 + 1, dtype=np.int64)
     k = wavenumbers(p)
     Omega = p.L
     kc = p.kc_L / (p.eta_w * Omega)

@@ -5,6 +5,7 @@
 * flat fault: the normal traction change vanishes bitwise;
 * a single Fourier mode of prescribed slip rate: closed form of the
   static + truncated dynamic response, which fixes the lag/weight indexing;
+  in the quasi-dynamic limit (eta_w = 0) the static response alone;
 * truncation: a slip pulse is forgotten after the window;
 * tiny N: a brute-force space-time double sum with real-space kernels equals
   the spectral step (FFT plumbing, sgn(k), Nyquist);
@@ -23,9 +24,9 @@ from paper_2107_03550_gb300.workloads import element_x, rough_fault, seamount_ru
 from tests.golden.paper import paper_numbers
 
 
-def _params(N=64, dx=25.0, kc_L=200.0, mu=30e9, cs=3464.0, cp=None):
+def _params(N=64, dx=25.0, kc_L=200.0, mu=30e9, cs=3464.0, cp=None, eta_w=1.0):
     cp = cp or np.sqrt(3.0) * cs
-    return Params(N=N, dx=dx, mu=mu, cs=cs, cp=cp, dt_min=0.25 * dx / cs, kc_L=kc_L)
+    return Params(N=N, dx=dx, mu=mu, cs=cs, cp=cp, dt_min=0.25 * dx / cs, kc_L=kc_L, eta_w=eta_w)
 
 
 def _prescribed_oracle(p, kappa, V):
@@ -95,6 +96,30 @@ def test_single_mode_closed_form(steps):
     sN = dt * G_N(p.cs * q * (j + 0.5) * dt, p.r).sum()
     tau = -q * np.cos(q * x) * Va * (p.S * steps * dt + p.mu * sT)
     sig = np.sin(q * x) * k0 * Va * (p.S * steps * dt + p.mu * sN)
+    scale = q * Va * p.S * steps * dt
+    assert np.abs(o.last["tau_el"] - tau).max() < 1e-12 * scale
+    assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("steps", [1, 7])
+def test_quasi_dynamic_single_mode_closed_form(steps):
+    # eta_w = 0 (Appendix, Quasi-dynamic BIEM): no window, so no history and no
+    # current-interval kernel term; prescribed V = Va cos(q x) on a fault of
+    # constant curvature k0 gives after s steps the static responses alone:
+    #   tau = -q cos(qx) Va S s dt,  sig = sin(qx) k0 Va S s dt
+    p = _params(N=64, eta_w=0.0)
+    assert not windows(p).any()
+    m = 16
+    q = 2 * np.pi * m / p.L
+    x = element_x(p.N, p.dx)
+    Va, k0 = 1e-3, 3e-4
+    V = Va * np.cos(q * x)
+    o = _prescribed_oracle(p, np.full(p.N, k0), V)
+    for _ in range(steps):
+        assert o.step() == 0
+    dt = p.dt_min
+    tau = -q * np.cos(q * x) * Va * p.S * steps * dt
+    sig = np.sin(q * x) * k0 * Va * p.S * steps * dt
     scale = q * Va * p.S * steps * dt
     assert np.abs(o.last["tau_el"] - tau).max() < 1e-12 * scale
     assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * scale
