@@ -228,12 +228,12 @@ def _flusher(torch):
     return flush
 
 
-def _measure(torch, a, precision: str, rank: int, world: int, flush, clock_index: int):
+def _measure(torch, a, precision: str, rank: int, world: int, flush, clock_index: int, extra=None):
     """Time K steps (and K history-only launches) back to back on one stream."""
     from paper_2107_03550_gb300.sbiem import Fault
     N = a.N
     w = _workload(N)
-    g = Fault.from_workload(w, precision=1 if precision == "fp32" else 0)
+    g = Fault.from_workload(w, precision=1 if precision == "fp32" else 0, **(extra or {}))
     g.set_stream(torch.cuda.current_stream())
     HT, HN, _ = _history(g.windows(), 11 + rank, N)
     g.set_history(HT, HN)
@@ -355,6 +355,14 @@ def run_ours(a):
     if not a.no_side:
         side = _measure(torch, a, other, rank, world, flush, dev_index)
         side["g"].close()
+    qd = None
+    if not a.no_side:
+        # the quasi-dynamic limit (eta_w = 0) of the same workload and form
+        import copy
+        aq = copy.copy(a)
+        aq.steps = min(a.steps, 500)
+        qd = _measure(torch, aq, a.precision, rank, world, flush, dev_index, extra={"eta_w": 0.0})
+        qd["g"].close()
     main = _measure(torch, a, a.precision, rank, world, flush, dev_index)
     e2e = None if a.no_e2e else _e2e(torch, a, main["g"], main["w"], world)
     cpu = None
@@ -383,7 +391,11 @@ def run_ours(a):
                        "history_ms_with_finish": main["hist_ms"],
                        f"{other}_path": None if side is None else {
                            "value": side["value"], "ms_per_step": side["ms_per_step"], "sweep_ms": side["sweep_ms"],
-                           "sweep_GBps": side["hist_bytes"] / (side["sweep_ms"] * 1e-3) / 1e9}},
+                           "sweep_GBps": side["hist_bytes"] / (side["sweep_ms"] * 1e-3) / 1e9},
+                       "quasi_dynamic_path": None if qd is None else {
+                           "value": qd["value"], "ms_per_step": qd["ms_per_step"], "steps": min(a.steps, 500),
+                           "what": "eta_w = 0: static stiffness plus radiation damping, no history; same "
+                                   "workload and form, L2 flushed the same way"}},
             "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
                          "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,

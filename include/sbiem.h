@@ -66,7 +66,10 @@ typedef struct sbiem_params {
   double  mu;           /* shear modulus (Pa)                                  */
   double  cs, cp;       /* shear and dilatational wave speeds (m/s), cp > cs   */
   double  beta_min;     /* dt_min = beta_min dx / cs (Sec. 3.2), default 0.25  */
-  double  eta_w;        /* truncation parameter eta (Sec. 3.1), default 1      */
+  double  eta_w;        /* truncation parameter eta (Sec. 3.1), default 1;
+                           0: the quasi-dynamic limit (Appendix, Quasi-dynamic
+                           BIEM): no history, no current-interval kernel term,
+                           static stiffness plus radiation damping            */
   double  kc_L;         /* k_c * eta * Omega (Sec. 3.1), default 200           */
   int32_t kc_units;     /* 0: k_c in rad/m (default); 1: in cycles/m           */
   int32_t precision;    /* 0: FP64 throughout (default); 1: FP32 history

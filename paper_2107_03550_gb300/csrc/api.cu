@@ -160,9 +160,12 @@ bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 // Windows of the truncated convolution (Sec. 3.1): T_w = eta Omega / cs for
 // k <= k_c, (eta Omega / cs)(k_c / k) above; M_n = ceil(T_w / dt_min) with a
 // relative slack of 1e-12 against rounding of exact ratios; M_0 = 0.
+// eta = 0 is the quasi-dynamic limit (Appendix, Quasi-dynamic BIEM): every
+// window empty, so no history and no current-interval kernel term.
 void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t>& M) {
   const int64_t nm = p.N / 2 + 1;
   M.assign(nm, 0);
+  if (p.eta_w == 0.0) return;
   double kc = p.kc_L / (p.eta_w * L);
   if (p.kc_units == 1) kc *= 2.0 * M_PI;
   for (int64_t n = 1; n < nm; ++n) {
@@ -408,7 +411,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   if (!is_pow2(p.N) || p.N < 16 || p.N > (1 << 20))
     return fail(SBIEM_ERR_INVALID, "N must be a power of two in [16, 2^20]");
   if (!(p.dx > 0) || !(p.mu > 0) || !(p.cs > 0) || !(p.cp > p.cs) || !(p.beta_min > 0) ||
-      !(p.eta_w > 0) || !(p.kc_L > 0) || !(p.V0 > 0) || !(p.newton_tol > 0) || p.newton_maxit < 1)
+      !(p.eta_w >= 0) || !(p.kc_L > 0) || !(p.V0 > 0) || !(p.newton_tol > 0) || p.newton_maxit < 1)
     return fail(SBIEM_ERR_INVALID, "parameters out of range (dx, mu, cs < cp, beta_min, eta_w, kc_L, V0, Newton)");
   if (p.precision != 0 && p.precision != 1) return fail(SBIEM_ERR_INVALID, "precision must be 0 or 1");
   if (p.state_law != 0 && p.state_law != 1) return fail(SBIEM_ERR_INVALID, "state_law must be 0 or 1");

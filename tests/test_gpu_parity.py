@@ -372,3 +372,35 @@ def test_read_probe_reads_and_leaves_sink():
     read_probe(x.data_ptr(), x.numel() * 4, sink.data_ptr(), torch.cuda.current_stream())
     torch.cuda.synchronize()
     assert float(sink.item()) == 7.0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_quasi_dynamic_rupture_matches_oracle(precision):
+    # eta_w = 0: the quasi-dynamic limit (static stiffness plus radiation
+    # damping, no history) through both the single-step and the overlapped
+    # graph paths; the rupture reaches seismic slip rates within 1000 steps
+    w = seamount_rupture()
+    o = oracle_for(w, eta_w=0.0)
+    g = gpu_for(w, eta_w=0.0, precision=precision)
+    g2 = gpu_for(w, eta_w=0.0, precision=precision)
+    assert not g.windows().any()
+    worst, worst2 = {}, {}
+    for s in range(1000):
+        assert o.step() == 0
+        g.step()
+        if s % 50 == 49:
+            g2.enqueue(50)
+            for gg, wst in ((g, worst), (g2, worst2)):
+                for k, v in compare(o, gg).items():
+                    wst[k] = max(wst.get(k, 0.0), v)
+    assert o.V.max() > 1.0
+    assert g.status()[0] == 0 and g2.status()[0] == 0
+    for wst in (worst, worst2):
+        if precision == 0:
+            for k in ("delta", "tau_el", "sigma_el"):
+                assert wst[k] < TOL64, (k, wst)
+            assert wst["V"] < 1e-9, wst
+        else:
+            assert wst["delta"] < 1e-4, wst
+    g.close()
+    g2.close()
