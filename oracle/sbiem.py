@@ -61,6 +61,7 @@ class Params:
     dt_min: float                 # beta_min * dx / cs (Sec. 3.2)
     eta_w: float = 1.0            # truncation parameter eta (Sec. 3.1)
     kc_L: float = 200.0           # k_c * (eta * L) (Sec. 3.1)
+    kcN_L: float = 0.0            # k_c of the normal-traction kernel, same units; 0: kc_L
     kc_units: str = "rad"         # "rad": k_c in rad/m; "cycles": k_c in cycles/m
     state_law: str = "analytic"   # "analytic" aging at constant Vbar, or "explicit"
     newton_tol: float = 1e-13
@@ -90,13 +91,17 @@ def wavenumbers(p: Params) -> np.ndarray:
     return 2.0 * np.pi * np.arange(p.N // 2 + 1) / p.L
 
 
-def windows(p: Params) -> np.ndarray:
-    """Number of dt_min intervals M_n covering the truncation window T_w(k_n) (Sec. 3.1).
+def field_windows(p: Params):
+    """Windows (M^T_n, M^N_n) of the shear and normal kernels (Sec. 3.1).
 
-    T_w = eta L / c_s for k <= k_c and (eta L / c_s)(k_c / k) above.  M_n is
-    the ceiling of T_w / dt_min, taken with a relative slack of 1e-12 so that
-    an exact integer ratio is not pushed up by rounding.  Mode 0 has no
-    traction (|k| = 0) and gets M_0 = 0.
+    M^X_n is the number of dt_min intervals covering the truncation window
+    T_w(k_n): T_w = eta L / c_s for k <= k_c and (eta L / c_s)(k_c / k)
+    above, M^X_n the ceiling of T_w / dt_min, taken with a relative slack of
+    1e-12 so that an exact integer ratio is not pushed up by rounding.  Mode
+    0 has no traction (|k| = 0) and gets M_0 = 0.  The shear kernel is cut at
+    k_c = kc_L / (eta L); the normal kernel at kcN_L / (eta L) when kcN_L > 0,
+    the two cutting planes Sec. 3.1 proposes for the slower-converging normal
+    traction, else at the same k_c (the paper's single plane).
 
     eta_w = 0 selects the quasi-dynamic limit (Appendix, Quasi-dynamic BIEM):
     the past slip rate acts only through the radiation damping of
@@ -105,27 +110,41 @@ def windows(p: Params) -> np.ndarray:
     stiffness alone.
     """
     if p.eta_w == 0:
-        return np.zeros(p.N // 2 + 1, dtype=np.int64)
+        z = np.zeros(p.N // 2 + 1, dtype=np.int64)
+        return z, z.copy()
+    if p.kc_units not in ("rad", "cycles"):
+        raise ValueError("kc_units must be 'rad' or 'cycles'")
     k = wavenumbers(p)
     Omega = p.L
-    kc = p.kc_L / (p.eta_w * Omega)
-    if p.kc_units == "cycles":
-        kc = 2.0 * np.pi * kc
-    elif p.kc_units != "rad":
-        raise ValueError("kc_units must be 'rad' or 'cycles'")
-    Tw = np.where(k <= kc, p.eta_w * Omega / p.cs, 0.0)
-    above = k > kc
-    Tw[above] = (p.eta_w * Omega / p.cs) * (kc / k[above])
-    M = np.ceil(Tw / p.dt_min * (1.0 - 1e-12)).astype(np.int64)
-    M[0] = 0
-    return M
+
+    def one(kc_L):
+        kc = kc_L / (p.eta_w * Omega)
+        if p.kc_units == "cycles":
+            kc = 2.0 * np.pi * kc
+        Tw = np.where(k <= kc, p.eta_w * Omega / p.cs, 0.0)
+        above = k > kc
+        Tw[above] = (p.eta_w * Omega / p.cs) * (kc / k[above])
+        M = np.ceil(Tw / p.dt_min * (1.0 - 1e-12)).astype(np.int64)
+        M[0] = 0
+        return M
+
+    MT = one(p.kc_L)
+    MN = one(p.kcN_L) if p.kcN_L > 0 else MT.copy()
+    return MT, MN
+
+
+def windows(p: Params) -> np.ndarray:
+    """Lags kept per mode: M_n = max(M^T_n, M^N_n) (field_windows; one window with one plane)."""
+    MT, MN = field_windows(p)
+    return np.maximum(MT, MN)
 
 
 def weights(p: Params, M: np.ndarray | None = None):
     """Midpoint weights w_{n,j} = dt_min * C(k_n, (j + 1/2) dt_min), j = 0..M_n-1 (Sec. 3.3).
 
     Returns (wT, wN, offsets): flat arrays with mode n occupying
-    [offsets[n], offsets[n+1]).
+    [offsets[n], offsets[n+1]).  With two cutting planes a field's weights
+    are zero past its own window M^X_n (the kernel truncated there).
     """
     if M is None:
         M = windows(p)
@@ -136,7 +155,12 @@ def weights(p: Params, M: np.ndarray | None = None):
     j = np.arange(offsets[-1]) - offsets[mode]
     s = p.cs * k[mode] * (j + 0.5) * p.dt_min
     GT, GN = kernel_pair(s, p.r)
-    return p.dt_min * GT, p.dt_min * GN, offsets
+    wT, wN = p.dt_min * GT, p.dt_min * GN
+    MT, MN = field_windows(p)
+    if M.size == MT.size:
+        wT = np.where(j < MT[mode], wT, 0.0)
+        wN = np.where(j < MN[mode], wN, 0.0)
+    return wT, wN, offsets
 
 
 def state_update(theta0, Vbar, thetadot_bar, Dc, dt, law: str):

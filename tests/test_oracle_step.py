@@ -5,7 +5,10 @@
 * flat fault: the normal traction change vanishes bitwise;
 * a single Fourier mode of prescribed slip rate: closed form of the
   static + truncated dynamic response, which fixes the lag/weight indexing;
-  in the quasi-dynamic limit (eta_w = 0) the static response alone;
+  in the quasi-dynamic limit (eta_w = 0) the static response alone; with
+  two cutting planes (Sec. 3.1) each field truncated at its own window;
+* the normal cutting plane: shear unchanged bitwise, normal traction
+  converging monotonically to the long-window result;
 * truncation: a slip pulse is forgotten after the window;
 * tiny N: a brute-force space-time double sum with real-space kernels equals
   the spectral step (FFT plumbing, sgn(k), Nyquist);
@@ -123,6 +126,68 @@ def test_quasi_dynamic_single_mode_closed_form(steps):
     scale = q * Va * p.S * steps * dt
     assert np.abs(o.last["tau_el"] - tau).max() < 1e-12 * scale
     assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * scale
+
+
+def test_two_cutting_planes_single_mode_closed_form():
+    # Sec. 3.1's two cutting planes: the shear kernel cut at k_c, the normal
+    # kernel at kcN.  Prescribed V = Va cos(q x), constant curvature k0; after
+    # s steps with M^T <= s <= M^N each field's dynamic term is its own
+    # truncated sum:
+    #   tau = -q cos(qx) Va [S s dt + mu sum_{j < M^T} wT_j]
+    #   sig = sin(qx) k0 Va [S s dt + mu sum_{j < s} wN_j]
+    from oracle.sbiem import field_windows
+    p = _params(N=64, kc_L=20.0)
+    p.kcN_L = 40.0
+    m = 16
+    MT, MN = field_windows(p)
+    assert MT[m] + 5 < MN[m]
+    q = 2 * np.pi * m / p.L
+    x = element_x(p.N, p.dx)
+    Va, k0 = 1e-3, 3e-4
+    V = Va * np.cos(q * x)
+    o = _prescribed_oracle(p, np.full(p.N, k0), V)
+    steps = (MT[m] + MN[m]) // 2
+    for _ in range(steps):
+        assert o.step() == 0
+    dt = p.dt_min
+    sT = dt * G_T(p.cs * q * (np.arange(MT[m]) + 0.5) * dt, p.r).sum()
+    sN = dt * G_N(p.cs * q * (np.arange(steps) + 0.5) * dt, p.r).sum()
+    tau = -q * np.cos(q * x) * Va * (p.S * steps * dt + p.mu * sT)
+    sig = np.sin(q * x) * k0 * Va * (p.S * steps * dt + p.mu * sN)
+    scale = q * Va * p.S * steps * dt
+    assert np.abs(o.last["tau_el"] - tau).max() < 1e-12 * scale
+    assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * scale
+
+
+def test_normal_cutting_plane_convergence():
+    # Truncation study (Sec. 3.1): with the shear plane fixed, raising the
+    # normal plane leaves the shear traction bitwise unchanged and brings
+    # the normal traction monotonically to the long-window result; at equal
+    # planes the normal error exceeds the shear error (the slower-converging
+    # normal kernel the paper gives as the reason for a second plane).
+    def run(kc, kcN, steps=600):
+        p = _params(N=64, kc_L=kc)
+        p.kcN_L = kcN
+        x = element_x(p.N, p.dx)
+        rng = np.random.default_rng(3)
+        V = 1e-3 * (1 + 0.5 * sum(np.cos(2 * np.pi * m * x / p.L + rng.uniform(0, 2 * np.pi))
+                                  for m in (3, 7, 12, 21)))
+        o = _prescribed_oracle(p, 1e-4 * np.cos(2 * np.pi * 5 * x / p.L), V)
+        for _ in range(steps):
+            assert o.step() == 0
+        return o.last["tau_el"], o.last["sig_el"]
+
+    tau_ref, sig_ref = run(1e4, 1e4)
+    err = lambda a, b: np.abs(a - b).max() / np.abs(b).max()
+    taus, sig_err = [], []
+    for kcN in (10.0, 20.0, 40.0, 80.0, 160.0):
+        t, sg = run(10.0, kcN)
+        taus.append(t)
+        sig_err.append(err(sg, sig_ref))
+    assert all(np.array_equal(t, taus[0]) for t in taus)
+    assert all(b < a for a, b in zip(sig_err, sig_err[1:])), sig_err
+    assert sig_err[-1] < 0.02 * sig_err[0]
+    assert sig_err[0] > 3 * err(taus[0], tau_ref)
 
 
 def test_truncation_forgets_a_pulse():
