@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the other precision's measurement (profiling runs)")
+    ap.add_argument("--kcN-L", type=float, default=0.0,
+                    help="k_c * eta * L of the normal-traction kernel (the second cutting plane); 0: one plane")
     return ap.parse_args()
 
 
@@ -363,7 +365,8 @@ def run_ours(a):
         aq.steps = min(a.steps, 500)
         qd = _measure(torch, aq, a.precision, rank, world, flush, dev_index, extra={"eta_w": 0.0})
         qd["g"].close()
-    main = _measure(torch, a, a.precision, rank, world, flush, dev_index)
+    main = _measure(torch, a, a.precision, rank, world, flush, dev_index,
+                    extra={"kcN_L": a.kcN_L} if a.kcN_L > 0 else None)
     e2e = None if a.no_e2e else _e2e(torch, a, main["g"], main["w"], world)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -379,7 +382,8 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32/f64",
             "data": "synthetic",
-            "config": {"workload": _workload_name(w, a.N), "N": a.N, "dx_m": w.dx,
+            "config": {"workload": _workload_name(w, a.N) + (f"; normal kernel cut at k_c L = {a.kcN_L:g}"
+                                                              if a.kcN_L > 0 else ""), "N": a.N, "dx_m": w.dx,
                        "precision": a.precision + (" (FP32 history convolution and FFTs, FP64 state and Newton)"
                                                    if a.precision == "fp32" else ""),
                        "parallelism": f"replicas x{world}",

@@ -71,6 +71,12 @@ typedef struct sbiem_params {
                            BIEM): no history, no current-interval kernel term,
                            static stiffness plus radiation damping            */
   double  kc_L;         /* k_c * eta * Omega (Sec. 3.1), default 200           */
+  double  kcN_L;        /* the normal-traction kernel's own k_c * eta * Omega:
+                           the second cutting plane Sec. 3.1 proposes for the
+                           slower-converging normal kernel; each field's
+                           weights are zero past its own window, the rings
+                           keep the longer one.  0 (default): kc_L, the
+                           paper's single plane                               */
   int32_t kc_units;     /* 0: k_c in rad/m (default); 1: in cycles/m           */
   int32_t precision;    /* 0: FP64 throughout (default); 1: FP32 history
                            convolution and FFTs, FP64 state and Newton        */

@@ -54,6 +54,7 @@ struct sbiem_s {
   int N = 0, nmodes = 0;
   double L = 0, dt_min = 0, S = 0, eta = 0;
   std::vector<int64_t> M, Rn, ring_off, w_off;
+  std::vector<int64_t> MT, MN;        // the shear and normal kernels' own windows (M = max)
   int64_t total_slots = 0, total_w = 0;
   std::vector<Chunk> chunks;
   std::vector<void*> allocs;
@@ -159,14 +160,17 @@ bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Windows of the truncated convolution (Sec. 3.1): T_w = eta Omega / cs for
 // k <= k_c, (eta Omega / cs)(k_c / k) above; M_n = ceil(T_w / dt_min) with a
-// relative slack of 1e-12 against rounding of exact ratios; M_0 = 0.
-// eta = 0 is the quasi-dynamic limit (Appendix, Quasi-dynamic BIEM): every
-// window empty, so no history and no current-interval kernel term.
-void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t>& M) {
+// relative slack of 1e-12 against rounding of exact ratios; M_0 = 0.  The
+// shear kernel is cut at k_c = kc_L / (eta Omega), the normal kernel at
+// kcN_L / (eta Omega) when kcN_L > 0 (the two cutting planes of Sec. 3.1);
+// the rings keep M = max(M^T, M^N) lags.  eta = 0 is the quasi-dynamic limit
+// (Appendix, Quasi-dynamic BIEM): every window empty, so no history and no
+// current-interval kernel term.
+void windows_one(const sbiem_params& p, double kc_L, double L, double dt_min, std::vector<int64_t>& M) {
   const int64_t nm = p.N / 2 + 1;
   M.assign(nm, 0);
   if (p.eta_w == 0.0) return;
-  double kc = p.kc_L / (p.eta_w * L);
+  double kc = kc_L / (p.eta_w * L);
   if (p.kc_units == 1) kc *= 2.0 * M_PI;
   for (int64_t n = 1; n < nm; ++n) {
     const double k = 2.0 * M_PI * static_cast<double>(n) / L;
@@ -174,6 +178,15 @@ void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t
     if (k > kc) Tw *= kc / k;
     M[n] = static_cast<int64_t>(std::ceil(Tw / dt_min * (1.0 - 1e-12)));
   }
+}
+
+void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t>& M, std::vector<int64_t>& MT,
+             std::vector<int64_t>& MN) {
+  windows_one(p, p.kc_L, L, dt_min, MT);
+  if (p.kcN_L > 0.0) windows_one(p, p.kcN_L, L, dt_min, MN);
+  else MN = MT;
+  M.resize(MT.size());
+  for (size_t n = 0; n < MT.size(); ++n) M[n] = std::max(MT[n], MN[n]);
 }
 
 template <class R>
@@ -376,6 +389,7 @@ void sbiem_default_params(sbiem_params* p) {
   p->beta_min = 0.25;
   p->eta_w = 1.0;
   p->kc_L = 200.0;
+  p->kcN_L = 0.0;
   p->kc_units = 0;
   p->precision = 0;
   p->state_law = 0;
@@ -411,8 +425,9 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   if (!is_pow2(p.N) || p.N < 16 || p.N > (1 << 20))
     return fail(SBIEM_ERR_INVALID, "N must be a power of two in [16, 2^20]");
   if (!(p.dx > 0) || !(p.mu > 0) || !(p.cs > 0) || !(p.cp > p.cs) || !(p.beta_min > 0) ||
-      !(p.eta_w >= 0) || !(p.kc_L > 0) || !(p.V0 > 0) || !(p.newton_tol > 0) || p.newton_maxit < 1)
-    return fail(SBIEM_ERR_INVALID, "parameters out of range (dx, mu, cs < cp, beta_min, eta_w, kc_L, V0, Newton)");
+      !(p.eta_w >= 0) || !(p.kc_L > 0) || !(p.kcN_L >= 0) || !(p.V0 > 0) || !(p.newton_tol > 0) || p.newton_maxit < 1)
+    return fail(SBIEM_ERR_INVALID,
+                "parameters out of range (dx, mu, cs < cp, beta_min, eta_w, kc_L, kcN_L, V0, Newton)");
   if (p.precision != 0 && p.precision != 1) return fail(SBIEM_ERR_INVALID, "precision must be 0 or 1");
   if (p.state_law != 0 && p.state_law != 1) return fail(SBIEM_ERR_INVALID, "state_law must be 0 or 1");
   if (p.kc_units != 0 && p.kc_units != 1) return fail(SBIEM_ERR_INVALID, "kc_units must be 0 or 1");
@@ -448,7 +463,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   const double r = p.cs / p.cp;
   s->S = p.mu * (1.0 - r * r);
   s->eta = p.mu / (2.0 * p.cs);
-  windows(p, s->L, s->dt_min, s->M);
+  windows(p, s->L, s->dt_min, s->M, s->MT, s->MN);
   {
     // bulk-async sweep: chunks of one stage buffer (512 lags FP32, 256 FP64),
     // every resident CTA streaming; the overlapped sweep keeps one CTA per SM
@@ -655,11 +670,29 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     return fail(ok ? SBIEM_ERR_CUDA : SBIEM_ERR_NOMEM, "upload failed");
   }
   up(d_cheb, tab.coef.data(), sizeof(double) * tab.coef.size());
+  // the two kernels' own windows, when they differ (two cutting planes)
+  int32_t* d_MT = nullptr;
+  int32_t* d_MN = nullptr;
+  if (s->MT != s->MN) {
+    std::vector<int32_t> mt(s->nmodes), mn(s->nmodes);
+    for (int n = 0; n < s->nmodes; ++n) {
+      mt[n] = static_cast<int32_t>(s->MT[n]);
+      mn[n] = static_cast<int32_t>(s->MN[n]);
+    }
+    d_MT = alloc_n<int32_t>(s, s->nmodes, &ok);
+    d_MN = alloc_n<int32_t>(s, s->nmodes, &ok);
+    if (!ok || up(d_MT, mt.data(), sizeof(int32_t) * s->nmodes) != cudaSuccess ||
+        up(d_MN, mn.data(), sizeof(int32_t) * s->nmodes) != cudaSuccess) {
+      free_all(s);
+      delete s;
+      return fail(SBIEM_ERR_NOMEM, "upload failed (windows)");
+    }
+  }
   int rc;
   if (s->fp32()) {
     rc = setup_device<float>(s, s->f32, f);
     if (rc == SBIEM_OK) {
-      launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+      launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, d_MT, d_MN, s->stream);
       launch_weight_pow2<float>(s->f32, s->stream);
     }
   } else {
@@ -672,7 +705,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     f.tw = s->tw64;
     rc = ok ? SBIEM_OK : fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
     if (rc == SBIEM_OK) {
-      launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, s->stream);
+      launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, d_MT, d_MN, s->stream);
       launch_weight_pow2<double>(f, s->stream);
     }
   }
@@ -1632,13 +1665,13 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
 // ------------------------------------------------------------- checkpoints
 namespace {
 
-constexpr char kCkMagic[8] = {'S', 'B', 'I', 'E', 'M', 'C', 'K', '1'};
+constexpr char kCkMagic[8] = {'S', 'B', 'I', 'E', 'M', 'C', 'K', '2'};
 
 struct CkHeader {
   char magic[8];
   int64_t N, total_slots;
   int32_t precision, state_law, kc_units, newton_maxit;
-  double dx, mu, cs, cp, beta_min, eta_w, kc_L, newton_tol, f0, V0;
+  double dx, mu, cs, cp, beta_min, eta_w, kc_L, newton_tol, f0, V0, kcN_L;
 };
 
 // Element arrays of a checkpoint, in file order: inputs, then raw state.
@@ -1676,6 +1709,7 @@ int sbiem_save(sbiem_t s, const char* path) {
   hd.beta_min = s->p.beta_min;
   hd.eta_w = s->p.eta_w;
   hd.kc_L = s->p.kc_L;
+  hd.kcN_L = s->p.kcN_L;
   hd.newton_tol = s->p.newton_tol;
   hd.f0 = s->p.f0;
   hd.V0 = s->p.V0;
@@ -1760,6 +1794,7 @@ int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc) {
   p.beta_min = hd.beta_min;
   p.eta_w = hd.eta_w;
   p.kc_L = hd.kc_L;
+  p.kcN_L = hd.kcN_L;
   p.newton_tol = hd.newton_tol;
   p.f0 = hd.f0;
   p.V0 = hd.V0;

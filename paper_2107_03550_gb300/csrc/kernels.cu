@@ -1725,13 +1725,16 @@ __global__ void k_maxdiff(const double* a, const double* b, int n, double* out) 
 // w_{n,j} = dt_min C(k_n, (j + 1/2) dt_min): midpoint rule (Sec. 3.3),
 // kernels from the piecewise Chebyshev table (Clenshaw recurrence).
 template <class R>
+// MT, MN (may be NULL): the shear and normal kernels' own windows when they
+// are cut at two planes (Sec. 3.1); a field's weights are zero past its own.
 __global__ void k_weights(W2<R>* w, const int64_t* w_off, const int32_t* Mn, int nmodes, double L,
                           double cs, double dt, const double* __restrict__ cheb, int npieces, int deg,
-                          double h) {
+                          double h, const int32_t* MT, const int32_t* MN) {
   const int n = blockIdx.x;
   if (n == 0 || n >= nmodes) return;
   const double k = kTwoPi * n / L;
   const int M = Mn[n];
+  const int MTn = MT ? MT[n] : M, MNn = MN ? MN[n] : M;
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     const double s = cs * k * (j + 0.5) * dt;
     int p = static_cast<int>(s / h);
@@ -1748,8 +1751,8 @@ __global__ void k_weights(W2<R>* w, const int64_t* w_off, const int32_t* Mn, int
       bN1 = tN;
     }
     W2<R> out;
-    out.x = static_cast<R>(dt * (t * bT1 - bT2 + c[0]));
-    out.y = static_cast<R>(dt * (t * bN1 - bN2 + c[1]));
+    out.x = j < MTn ? static_cast<R>(dt * (t * bT1 - bT2 + c[0])) : R(0);
+    out.y = j < MNn ? static_cast<R>(dt * (t * bN1 - bN2 + c[1])) : R(0);
     w[w_off[n] + j] = out;
   }
 }
@@ -2168,8 +2171,9 @@ void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st, int lag_p) {
 
 template <class R>
 void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg, double h, double cs,
-                    cudaStream_t st) {
-  k_weights<R><<<f.nmodes, 256, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.L, cs, f.dt_min, cheb, npieces, deg, h);
+                    const int32_t* MT, const int32_t* MN, cudaStream_t st) {
+  k_weights<R><<<f.nmodes, 256, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.L, cs, f.dt_min, cheb, npieces, deg, h,
+                                         MT, MN);
 }
 
 void launch_fft64(const FftGeom& g, const double2* tw, const double2* in, double2* tmp, double2* out,
@@ -2268,7 +2272,9 @@ template void launch_history_atomic<double>(const DevFault<double>&, int, int, c
 template void launch_history_atomic<float>(const DevFault<float>&, int, int, cudaStream_t);
 template int sweep_blocks_per_sm<double>(int);
 template int sweep_blocks_per_sm<float>(int);
-template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double, cudaStream_t);
-template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double, cudaStream_t);
+template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double,
+                                     const int32_t*, const int32_t*, cudaStream_t);
+template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double,
+                                    const int32_t*, const int32_t*, cudaStream_t);
 
 }  // namespace sbiem

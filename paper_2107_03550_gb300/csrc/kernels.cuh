@@ -174,7 +174,8 @@ template <class R> void launch_ring_undo(const DevFault<R>& f, int m_dt, void* u
 // *out = max_i |a_i - b_i|.
 void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st);
 template <class R> void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg,
-                                       double h, double cs, cudaStream_t st);
+                                       double h, double cs, const int32_t* MT, const int32_t* MN,
+                                       cudaStream_t st);
 
 // FP64 utility transforms on caller buffers of length N (natural order):
 // forward: Z = sum_i z_i exp(-2 pi i n i/N); inverse: z = (1/N) sum_n Z_n exp(+...).

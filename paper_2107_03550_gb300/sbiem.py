@@ -31,7 +31,8 @@ _free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("dx", ctypes.c_double), ("mu", ctypes.c_double),
                 ("cs", ctypes.c_double), ("cp", ctypes.c_double), ("beta_min", ctypes.c_double),
-                ("eta_w", ctypes.c_double), ("kc_L", ctypes.c_double), ("kc_units", ctypes.c_int32),
+                ("eta_w", ctypes.c_double), ("kc_L", ctypes.c_double), ("kcN_L", ctypes.c_double),
+                ("kc_units", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("state_law", ctypes.c_int32),
                 ("newton_maxit", ctypes.c_int32), ("newton_tol", ctypes.c_double),
                 ("f0", ctypes.c_double), ("V0", ctypes.c_double),
@@ -256,14 +257,14 @@ class Fault:
 
     def __init__(self, N, dx, mu, cs, cp, f0, V0, a, b, Dc, sigma_load, V_init, theta_init,
                  kappa=None, h=None, tau_load=None, tau_load_rate=None, prescribed=None,
-                 V_presc=None, beta_min=0.25, eta_w=1.0, kc_L=200.0, kc_units=0, precision=0,
+                 V_presc=None, beta_min=0.25, eta_w=1.0, kc_L=200.0, kcN_L=0.0, kc_units=0, precision=0,
                  state_law=0, newton_maxit=50, newton_tol=1e-12, use_torch=True, lib=None):
         self.lib = lib or load_library()
         self.N = int(N)
         p = Params()
         self.lib.sbiem_default_params(ctypes.byref(p))
         p.N, p.dx, p.mu, p.cs, p.cp = self.N, dx, mu, cs, cp
-        p.beta_min, p.eta_w, p.kc_L, p.kc_units = beta_min, eta_w, kc_L, kc_units
+        p.beta_min, p.eta_w, p.kc_L, p.kcN_L, p.kc_units = beta_min, eta_w, kc_L, kcN_L, kc_units
         p.precision, p.state_law = precision, state_law
         p.newton_maxit, p.newton_tol, p.f0, p.V0 = newton_maxit, newton_tol, f0, V0
         self._cb = _torch_allocator() if use_torch else None

@@ -404,3 +404,36 @@ def test_quasi_dynamic_rupture_matches_oracle(precision):
             assert wst["delta"] < 1e-4, wst
     g.close()
     g2.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_cutting_planes_match_oracle(precision):
+    # Sec. 3.1's second cutting plane: the normal kernel cut at twice the
+    # shear kernel's k_c; a full random history, so both windows carry weight
+    # from step 1; single steps and the overlapped graph path
+    w = seamount_rupture(N=256)
+    o = oracle_for(w, kc_L=100.0, kcN_L=200.0)
+    g = gpu_for(w, precision=precision, kc_L=100.0, kcN_L=200.0)
+    g2 = gpu_for(w, precision=precision, kc_L=100.0, kcN_L=200.0)
+    MT = gpu_for(w, precision=precision, kc_L=100.0).windows()
+    assert (g.windows() >= MT).all() and (g.windows() > MT).any()
+    HT, HN = prefill(o, g, seed=13, scale=1e-6)
+    g2.set_history(HT, HN)
+    for _ in range(200):
+        assert o.step() == 0
+        g.step()
+    g2.enqueue(200)
+    assert g.status()[0] == 0 and g2.status()[0] == 0
+    for gg in (g, g2):
+        err = compare(o, gg)
+        if precision == 0:
+            for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+                assert err[k] < 1e-10, (k, err)
+        else:
+            s = gg.get_state()
+            scale = max(np.abs(o.last["tau_el"]).max(), np.abs(o.last["sig_el"]).max())
+            for k, ref in (("tau_el", o.last["tau_el"]), ("sigma_el", o.last["sig_el"])):
+                assert np.abs(s[k] - ref).max() < 1e-4 * scale, (k, err)
+            assert err["delta"] < 1e-4, err
+    g.close()
+    g2.close()
