@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the other precision's measurement (profiling runs)")
+    ap.add_argument("--workload", choices=["rough", "sinusoidal"], default="rough",
+                    help="rough: the rough-fault cycle (headline); sinusoidal: the paper's own cycle setup")
     ap.add_argument("--kcN-L", type=float, default=0.0,
                     help="k_c * eta * L of the normal-traction kernel (the second cutting plane); 0: one plane")
     return ap.parse_args()
@@ -71,8 +73,13 @@ def _dist():
     return rank, world, local
 
 
+_KIND = "rough"  # --workload
+
+
 def _workload(N):
-    from paper_2107_03550_gb300.workloads import rough_cycle
+    from paper_2107_03550_gb300.workloads import rough_cycle, sinusoidal_cycle
+    if _KIND == "sinusoidal":
+        return sinusoidal_cycle(N=N)
     return rough_cycle(N=N, lam_max=min(40e3, N * 10.0))
 
 
@@ -83,6 +90,11 @@ def _history(M, seed, N):
 
 
 def _workload_name(w, N):
+    if _KIND == "sinusoidal":
+        return (f"sinusoidal-fault cycle (Table 1), steady state: N={N}, dx={w.dx:g} m, fault "
+                f"{w.extra['fault_length'] / 1e3:g} km of a 4L periodic domain, null slip rate on 1.5L each "
+                f"side, h = {w.extra['amp']:g} m sin(2 pi x / {w.extra['wavelength'] / 1e3:g} km); "
+                f"dt = dt_min = 0.25 dx/cs; every history window full")
     return (f"rough-fault cycle, steady state: N={N}, dx={w.dx:g} m, Hurst-1 roughness alpha=0.005, "
             f"lambda in [20 m, {min(40e3, N * 10.0) / 1e3:g} km], central 70% rate-and-state, "
             f"outer 30% at V_pl; dt = dt_min = 0.25 dx/cs; every history window full")
@@ -421,7 +433,9 @@ def run_ours(a):
 
 
 def main():
+    global _KIND
     a = _args()
+    _KIND = a.workload
     if a.impl == "reference":
         run_reference(a)
     else:

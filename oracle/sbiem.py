@@ -287,8 +287,10 @@ class Oracle:
         if equilibrium:
             # loading in equilibrium with the initial state (Eq. momentum with
             # radiation damping and zero elastic change at t = 0)
-            fr = (self.f0 + self.a * np.log(self.V / self.V0)
-                  + self.b * np.log(self.theta * self.V0 / self.Dc))
+            # (prescribed elements may hold V = 0; their load is set to 0 below)
+            with np.errstate(divide="ignore"):
+                fr = (self.f0 + self.a * np.log(self.V / self.V0)
+                      + self.b * np.log(self.theta * self.V0 / self.Dc))
             self.tau_load = np.where(self.prescribed, 0.0,
                                      self.sigma_load * fr + p.eta_rd * self.V)
         self.k = wavenumbers(p)

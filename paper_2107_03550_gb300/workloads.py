@@ -12,6 +12,10 @@ seamount_rupture  N=256, dx=25 m, 20 m Gaussian seamount, single rupture.
 rough_cycle       N=4096, dx=10 m, Hurst-1 roughness, central 70% frictional,
                   outer 30% at plate rate.
 rough_fault       one rough-fault realization of any N (ensemble member).
+sinusoidal_cycle  the earthquake cycle of Sec. "Seismic cycles": Table 1, a
+                  sinusoidal fault of length L in a periodic domain of 4L
+                  with null slip rate on 1.5L each side, uniform loading
+                  rate 0.01 Pa/s.
 """
 from __future__ import annotations
 
@@ -20,7 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Workload", "gaussian_seamount", "seamount_rupture", "rough_profile", "rough_cycle", "rough_fault",
-           "random_history", "element_x"]
+           "sinusoidal_cycle", "random_history", "element_x"]
 
 
 @dataclass
@@ -168,6 +172,41 @@ def rough_cycle(N: int = 4096, dx: float = 10.0, alpha: float = 0.005, seed: int
         h=h, kappa=kappa, a=a, b=b, Dc=np.full(N, 1e-3), f0=0.6, V0=1e-6,
         sigma_load=np.full(N, 50e6), V_init=np.full(N, Vpl), theta_init=np.full(N, 1e-3 / Vpl),
         prescribed=~central, V_presc=np.where(central, 0.0, Vpl))
+
+
+def sinusoidal_cycle(N: int = 4096, dx: float = 10.0, amp: float = 5.0, wavelength: float = 1280.0) -> Workload:
+    """Earthquake cycle on a sinusoidal fault (Sec. "Seismic cycles", Table 1).
+
+    Table 1: f0 = 0.6, V0 = 1e-9 m/s, Dc = 1 cm, a = 0.012, b = 0.015,
+    sigma = 100 MPa, mu = 40 GPa, cs = 3464 m/s, cp = 6000 m/s, fault length
+    L = 10.24 km, ds = 10 m.  As in the paper's comparison setup (Sec.
+    "Comparison with ..."), the periodic domain is 4L and 1.5L on each side of
+    the fault is held at a null slip rate (prescribed V = 0); the fault is
+    loaded by a uniform shear-traction rate of 0.01 Pa/s.  The profile
+    h = amp sin(2 pi x / wavelength) is centred so that the fault's middle is
+    locally flat (kappa = 0 at x = 0); the text gives neither amplitude nor
+    wavelength (they are drawn in a figure), so the defaults, 5 m over
+    1.28 km (eight wavelengths on the fault, so the geometric modulation of
+    slip is distinct from the rupture-scale profile; slope at most 0.025;
+    32 wavelengths over the domain, so kappa is periodic), are this
+    generator's choice.  Initial V = V0 on the fault with steady state
+    theta = Dc / V0.
+    """
+    x = element_x(N, dx)
+    Lf = N * dx / 4.0
+    q = 2.0 * np.pi / wavelength
+    h = amp * np.sin(q * x)
+    kappa = -amp * q * q * np.sin(q * x)
+    fault = np.abs(x) < 0.5 * Lf
+    V0 = 1e-9
+    Dc = 1e-2
+    return Workload(
+        name=f"sinusoidal_cycle N={N} dx={dx:g}m fault L={Lf / 1e3:g}km amp={amp:g}m wavelength={wavelength:g}m",
+        N=N, dx=dx, mu=40e9, cs=3464.0, cp=6000.0, dt_min=0.25 * dx / 3464.0,
+        h=h, kappa=kappa, a=np.full(N, 0.012), b=np.full(N, 0.015), Dc=np.full(N, Dc), f0=0.6, V0=V0,
+        sigma_load=np.full(N, 100e6), V_init=np.full(N, V0), theta_init=np.full(N, Dc / V0),
+        prescribed=~fault, V_presc=np.zeros(N), tau_load_rate=np.where(fault, 0.01, 0.0),
+        extra={"fault": fault, "fault_length": Lf, "amp": amp, "wavelength": wavelength})
 
 
 def rough_fault(N: int, dx: float, alpha: float, seed: int, lam_min: float | None = None,

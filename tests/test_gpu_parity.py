@@ -437,3 +437,22 @@ def test_two_cutting_planes_match_oracle(precision):
             assert err["delta"] < 1e-4, err
     g.close()
     g2.close()
+
+
+def test_sinusoidal_cycle_steps_match_oracle():
+    # the paper's cycle setup (Table 1, 4L domain with null-slip zones,
+    # loading rate): a perturbed state and a full random history so that
+    # every term is exercised from step 1
+    from paper_2107_03550_gb300.workloads import sinusoidal_cycle
+    w = sinusoidal_cycle()
+    o = oracle_for(w)
+    g = gpu_for(w)
+    prefill(o, g, seed=21, scale=1e-7)
+    for _ in range(12):
+        assert o.step() == 0
+        g.step()
+    err = compare(o, g)
+    for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+        assert err[k] < 1e-10, (k, err)
+    assert np.all(g.get_state()["V"][~w.extra["fault"]] == 0.0)
+    g.close()

@@ -57,3 +57,24 @@ def test_rough_profile_curvature_is_second_derivative():
     k_num = np.fft.irfft(-(kk ** 2) * np.fft.rfft(h), n=N)
     assert np.abs(k_num - k).max() < 1e-9 * np.abs(k).max()
     assert element_x(N, dx)[0] == pytest.approx(-N * dx / 2 + dx / 2)
+
+
+def test_sinusoidal_cycle_follows_table1_and_the_domain_of_the_comparison():
+    from paper_2107_03550_gb300.workloads import sinusoidal_cycle
+    w = sinusoidal_cycle()
+    # Table 1
+    assert (w.mu, w.cs, w.cp, w.f0, w.V0) == (40e9, 3464.0, 6000.0, 0.6, 1e-9)
+    assert np.all(w.a == 0.012) and np.all(w.b == 0.015) and np.all(w.Dc == 1e-2)
+    assert np.all(w.sigma_load == 100e6) and w.dx == 10.0
+    fault = w.extra["fault"]
+    # fault length 10.24 km in a 4L periodic domain, 1.5L held at null slip rate each side
+    assert fault.sum() * w.dx == 10240.0 and w.N * w.dx == 4 * 10240.0
+    assert np.all(w.prescribed == ~fault) and np.all(w.V_presc[~fault] == 0.0)
+    x = element_x(w.N, w.dx)
+    assert np.all(np.abs(x[~fault]) > 10240.0 / 2 - w.dx)
+    assert np.all(w.tau_load_rate[fault] == 0.01)
+    # curvature is h'' (periodic second difference, O(dx^2)); flat at the middle
+    d2 = (np.roll(w.h, -1) - 2 * w.h + np.roll(w.h, 1)) / w.dx ** 2
+    assert np.abs(d2 - w.kappa).max() < 1e-3 * np.abs(w.kappa).max()
+    mid = w.N // 2  # elements -dx/2 and +dx/2 straddle x = 0, where kappa changes sign
+    assert w.kappa[mid - 1] * w.kappa[mid] < 0 and x[mid - 1] < 0 < x[mid]
