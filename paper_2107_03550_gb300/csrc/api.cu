@@ -895,7 +895,8 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, i
       rc = sbiem_status(s, &st, nullptr, 1);
       if (rc) return rc;
       if (st) {
-        rc = fail(SBIEM_ERR_DTMIN, "step failed at dt_min; state left at the start of the step");
+        rc = fail(SBIEM_ERR_DTMIN, "step failed at dt_min (status bits " + std::to_string(st) +
+                                       "); state left at the start of the step");
         break;
       }
       if (m_hist) m_hist[accepted] = 1;

@@ -4,6 +4,10 @@ scaling of Sec. "Scaling of slip distribution versus fault geometry" on its
 final slip.
 
     python -m paper_2107_03550_gb300.cycle [--events 3] [--years 400] [--precision 1]
+                                           [--workload sinusoidal|rough]
+
+(rough: the rough-fault cycle, Hurst-1 roughness with the outer 30 % of the
+fault creeping at the plate rate, N = 4096, dx = 10 m.)
 
 Prints one JSON line: simulated time, accepted steps and their step lengths,
 the events (peak slip rate above 1e-2 m/s), wall time and element-steps/s,
@@ -23,7 +27,7 @@ import time
 import numpy as np
 
 from .sbiem import Fault
-from .workloads import element_x, sinusoidal_cycle
+from .workloads import element_x, rough_cycle, sinusoidal_cycle
 
 
 def scaling_fit(delta: np.ndarray, kappa: np.ndarray, x: np.ndarray, fault_length: float, f: float,
@@ -54,7 +58,8 @@ def run_cycle(events: int = 3, years: float = 400.0, precision: int = 1, eps0: f
     w = w or sinusoidal_cycle()
     g = Fault.from_workload(w, precision=precision)
     x = element_x(w.N, w.dx)
-    fault = w.extra["fault"]
+    fault = ~w.prescribed  # the frictional part of the fault
+    fault_length = float(fault.sum() * w.dx)
     t_end = years * 365.25 * 86400.0
     m = 1
     steps = 0
@@ -70,8 +75,12 @@ def run_cycle(events: int = 3, years: float = 400.0, precision: int = 1, eps0: f
         steps += len(hist)
         m_hist += hist
         if rc != 0:
-            # SBIEM_ERR_DTMIN: a step failed at dt_min (state kept at its start)
-            stop = f"code {rc} at t = {t:.6g} s"
+            # SBIEM_ERR_DTMIN: a step failed at dt_min (state kept at its start);
+            # the library's message carries the failing step's status bits
+            msg = g.lib.sbiem_last_error().decode()
+            bits = int(msg.split("status bits ")[1].split(")")[0]) if "status bits " in msg else 0
+            why = [n for b, n in ((1, "Newton cap"), (2, "opening"), (4, "state")) if bits & b]
+            stop = f"code {rc} at t = {t:.6g} s ({', '.join(why) or msg})"
             break
         s = g.get_state()
         vmax = float(s["V"][fault].max())
@@ -92,7 +101,7 @@ def run_cycle(events: int = 3, years: float = 400.0, precision: int = 1, eps0: f
                 else ("t_end" if t >= t_end else "max_steps"))
     wall = time.perf_counter() - t0
     s = g.get_state()
-    fit = scaling_fit(s["delta"], w.kappa, x, w.extra["fault_length"], w.f0)
+    fit = scaling_fit(s["delta"], w.kappa, x, fault_length, w.f0)
     mh = np.asarray(m_hist)
     out = {
         "workload": w.name, "precision": precision, "eps0_m": eps0,
@@ -113,8 +122,10 @@ def main() -> None:
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--eps0", type=float, default=1e-7, help="step-doubling slip tolerance (m)")
     ap.add_argument("--max-steps", type=int, default=400_000)
+    ap.add_argument("--workload", choices=["sinusoidal", "rough"], default="sinusoidal")
     a = ap.parse_args()
-    print(json.dumps(run_cycle(a.events, a.years, a.precision, a.eps0, max_steps=a.max_steps)), flush=True)
+    w = sinusoidal_cycle() if a.workload == "sinusoidal" else rough_cycle()
+    print(json.dumps(run_cycle(a.events, a.years, a.precision, a.eps0, max_steps=a.max_steps, w=w)), flush=True)
 
 
 if __name__ == "__main__":
