@@ -1906,15 +1906,17 @@ static void launch_early(void (*kernel)(Args...), dim3 grid, dim3 block, size_t 
   cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// The spectral part of a pass (rows a2, a4, a5; the predictor of a1 in the
+// FP64 four-kernel form): one launch, or the four-step kernels.
 template <class R>
-void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
+void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   const FftGeom& g = f.g;
   const double dt = m_dt * f.dt_min;
   if constexpr (sizeof(R) == 4) {
     if (f.N <= kFusedMaxN) {
       with_lgn(f.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
-        // pass 2 starts early behind the pass-1 Newton; Newton behind the pass
+        // pass 2 starts early behind the pass-1 Newton
         if constexpr ((1 << LG) >= kClusterMinN) {
           launch_cluster_kernel(k_spectral_cluster<LG, kClusterEPT>, 1, f.N, st, pass == 2, f, pass, m_dt, dt);
         } else if (pass == 2) {
@@ -1923,8 +1925,6 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
           k_spectral_fused<LG><<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
         }
       });
-      launch_early(f.mlp ? k_newton<R, true> : k_newton<R, false>, dim3((f.N + f.newton_epw - 1) / f.newton_epw),
-                   dim3(32), 0, st, f, pass, dt);
       return;
     }
   }
@@ -1937,8 +1937,20 @@ void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   kfb<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.Z, R(1), f.status);
   kia<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
   kib<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.y, R(1.0 / g.N), f.status);
+}
+
+// The Newton part of a pass (rows a1, a6), started early behind the spectral part.
+template <class R>
+void launch_newton(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
+  const double dt = m_dt * f.dt_min;
   launch_early(f.mlp ? k_newton<R, true> : k_newton<R, false>, dim3((f.N + f.newton_epw - 1) / f.newton_epw),
                dim3(32), 0, st, f, pass, dt);
+}
+
+template <class R>
+void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
+  launch_spectral<R>(f, pass, m_dt, st);
+  launch_newton<R>(f, pass, m_dt, st);
 }
 
 template <class R>
@@ -2258,6 +2270,10 @@ template void launch_history<double>(const DevFault<double>&, int, int, cudaStre
 template void launch_history<float>(const DevFault<float>&, int, int, cudaStream_t, cudaEvent_t);
 template void launch_pass<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_pass<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_spectral<double>(const DevFault<double>&, int, int, cudaStream_t);
+template void launch_spectral<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_newton<double>(const DevFault<double>&, int, int, cudaStream_t);
+template void launch_newton<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_push_multi<double>(const DevFault<double>&, int, cudaStream_t);
 template void launch_push_multi<float>(const DevFault<float>&, int, cudaStream_t);
 template void launch_weight_pow2<double>(const DevFault<double>&, cudaStream_t);

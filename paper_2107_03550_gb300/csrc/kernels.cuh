@@ -157,6 +157,9 @@ template <class R> void configure_batch_kernels(const FftGeom& g);
 // Resident CTAs per SM of the history convolution (occupancy calculator).
 template <class R> int history_blocks_per_sm();
 template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
+// The two halves of launch_pass: the spectral kernels, then Newton (early).
+template <class R> void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
+template <class R> void launch_newton(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
 // lag_p >= 0 (m_dt = 2^lag_p): also finish the next step's history sums,
 // AT = BT + (sum of the weights of lags m_dt .. 2 m_dt - 1) x the new slot.
 template <class R> void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st, int lag_p = -1);
