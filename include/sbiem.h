@@ -178,8 +178,11 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max,
  * sbiem_step_host -- a step driven from host memory: copies tau_load (N
  * doubles, replaces the shear load) host->device, runs one step and copies the
  * new slip rate V (N doubles) device->host.  Either pointer may be NULL.
- * Host buffers should be pinned for asynchronous copies.  Errors as
- * sbiem_step.
+ * Host buffers should be pinned for asynchronous copies: with page-locked
+ * buffers, once a sequence of steps of one length is under way (after the
+ * first such call), the copies, the step and the read of the status word
+ * run as one CUDA graph (captured for that step length and pointer pair)
+ * with one synchronization per step.  Errors as sbiem_step.
  */
 int sbiem_step_host(sbiem_t s, double dt, const double* tau_load, double* V_out);
 

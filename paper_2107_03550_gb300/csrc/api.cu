@@ -74,6 +74,16 @@ struct sbiem_s {
   // for which AT/AN already hold the next step's sums (-1: none)
   std::map<int, cudaGraphExec_t> lag_graphs;
   std::map<int, cudaGraph_t> lag_defs;
+  // sbiem_step_host with pinned host buffers: the copies in, the overlapped
+  // step and the copies out (result, status word) as one graph, captured for
+  // one step length and one pair of host pointers
+  struct {
+    int m = 0;
+    const void* tau = nullptr;
+    void* V = nullptr;
+    cudaGraph_t def = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } host_graph;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int lag_m = -1;
@@ -129,7 +139,16 @@ T* alloc_n(sbiem_s* s, size_t n, bool* ok) {
   return ptr;
 }
 
+void drop_host_graph(sbiem_s* s) {
+  if (s->host_graph.exec) cudaGraphExecDestroy(s->host_graph.exec);
+  if (s->host_graph.def) cudaGraphDestroy(s->host_graph.def);
+  s->host_graph.exec = nullptr;
+  s->host_graph.def = nullptr;
+  s->host_graph.m = 0;
+}
+
 void free_all(sbiem_s* s) {
+  drop_host_graph(s);
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
   for (auto& kv : s->lag_graphs) cudaGraphExecDestroy(kv.second);
@@ -956,11 +975,59 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, i
   return rc;
 }
 
+namespace {
+// Page-locked (or NULL): host memory a captured copy may read or write.
+bool host_pinned(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+}  // namespace
+
 int sbiem_step_host(sbiem_t s, double dt, const double* tau_load, double* V_out) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
   int m;
   int rc = dt_to_m(s, dt, &m);
   if (rc) return rc;
+  if (s->pslots == 0 && is_pow2(m) && m <= (1 << 30) && s->lag_m == m && host_pinned(tau_load) &&
+      host_pinned(V_out)) {
+    // steady overlapped stepping with pinned buffers: one graph launch and
+    // one synchronization per step
+    auto& hg = s->host_graph;
+    if (!(hg.exec && hg.m == m && hg.tau == tau_load && hg.V == V_out)) {
+      drop_host_graph(s);
+      const size_t nb = sizeof(double) * s->N;
+      CK(cudaStreamSynchronize(s->stream));
+      CK(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
+      if (tau_load) cudaMemcpyAsync(s->f64.tau0, tau_load, nb, cudaMemcpyHostToDevice, s->own);
+      if (s->fp32()) enqueue_step_lag_t<float>(s, s->f32, m, s->own);
+      else enqueue_step_lag_t<double>(s, s->f64, m, s->own);
+      if (V_out) cudaMemcpyAsync(V_out, s->f64.V, nb, cudaMemcpyDeviceToHost, s->own);
+      cudaMemcpyAsync(s->h_status, s->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->own);
+      cudaError_t e1 = cudaGetLastError();
+      cudaError_t e2 = cudaStreamEndCapture(s->own, &hg.def);
+      if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(SBIEM_ERR_CUDA,
+                    std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      CK(cudaGraphInstantiate(&hg.exec, hg.def, 0));
+      hg.m = m;
+      hg.tau = tau_load;
+      hg.V = V_out;
+    }
+    CK(cudaGraphLaunch(hg.exec, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const unsigned st = *s->h_status;
+    if (st) {
+      s->lag_m = -1;  // a rejected step left AT/AN of its start
+      CK(cudaMemsetAsync(s->f64.status, 0, sizeof(unsigned), s->stream));
+      return fail(status_to_code(st), "step rejected; state left at the start of the step");
+    }
+    return SBIEM_OK;
+  }
   if (tau_load)
     CK(cudaMemcpyAsync(s->f64.tau0, tau_load, sizeof(double) * s->N, cudaMemcpyHostToDevice, s->stream));
   rc = sbiem_enqueue(s, dt, 1);
@@ -1149,6 +1216,7 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
 namespace {
 void drop_graphs(sbiem_s* s) {
   cudaStreamSynchronize(s->stream);
+  drop_host_graph(s);
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : s->graph_defs) cudaGraphDestroy(kv.second);
   for (auto& kv : s->lag_graphs) cudaGraphExecDestroy(kv.second);

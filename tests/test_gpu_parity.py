@@ -456,3 +456,32 @@ def test_sinusoidal_cycle_steps_match_oracle():
         assert err[k] < 1e-10, (k, err)
     assert np.all(g.get_state()["V"][~w.extra["fault"]] == 0.0)
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_host_pinned_graph_matches_enqueue(precision):
+    # page-locked buffers: after the first call of a sequence the copies and
+    # the step run as one captured graph; a new output buffer re-captures it.
+    # Same state, bitwise, as the stream-ordered path (pageable buffers).
+    import torch
+    w = seamount_rupture(N=256)
+    g = gpu_for(w, precision=precision)
+    ref = gpu_for(w, precision=precision)
+    o = oracle_for(w)
+    tau = torch.empty(w.N, dtype=torch.float64, pin_memory=True).numpy()
+    tau[:] = o.tau_load
+    outs = [torch.empty(w.N, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    for k in range(12):
+        V = outs[0] if k < 7 else outs[1]
+        g.step_host(tau_load=tau, V_out=V)
+        assert np.array_equal(V, g.get_state()["V"])
+    tau_pageable = np.array(tau)
+    V_pageable = np.empty(w.N)
+    for _ in range(12):
+        ref.step_host(tau_load=tau_pageable, V_out=V_pageable)
+    assert ref.status()[0] == 0 and g.status()[0] == 0
+    a, b = g.get_state(), ref.get_state()
+    for k in ("delta", "V", "theta"):
+        assert np.array_equal(a[k], b[k]), k
+    g.close()
+    ref.close()
