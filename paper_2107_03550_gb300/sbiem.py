@@ -253,7 +253,14 @@ def mlp_train(samples, epochs=5, batch=8192, lr=1e-3, seed=0):
 
 
 class Fault:
-    """One periodic non-planar fault on the GPU (a libsbiem handle)."""
+    """One periodic non-planar fault on the GPU (a libsbiem handle).
+
+    Arguments mirror ``sbiem_params`` and ``sbiem_create`` in the C header:
+    ``eta_w`` is the truncation parameter of Sec. 3.1 (0: the quasi-dynamic
+    limit, no history); ``kc_L`` the cutting plane k_c eta L of both kernels,
+    ``kcN_L`` (> 0) a second plane for the normal-traction kernel;
+    ``precision`` 0 (FP64) or 1 (FP32 history and FFTs, FP64 state).
+    """
 
     def __init__(self, N, dx, mu, cs, cp, f0, V0, a, b, Dc, sigma_load, V_init, theta_init,
                  kappa=None, h=None, tau_load=None, tau_load_rate=None, prescribed=None,
