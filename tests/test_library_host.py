@@ -100,3 +100,15 @@ def test_kernel_route_against_high_precision(lib):
     for s in (0.7, 11.9, 19.35, 39.95, 99.6, 198.9):
         cT, _ = kernel_values(np.array([s]), float(r))
         assert abs(cT[0] - float(GTm(s))) < 5e-14, s
+
+
+def test_truncation_parameters_are_validated_before_any_device_work(lib):
+    # eta_w >= 0 (0: quasi-dynamic limit) and kcN_L >= 0 (0: one cutting
+    # plane); negative values are rejected by the host checks, no GPU needed
+    from paper_2107_03550_gb300.sbiem import ERR, Fault, SbiemError
+    from paper_2107_03550_gb300.workloads import seamount_rupture
+    w = seamount_rupture(N=64)
+    for kw in ({"eta_w": -1.0}, {"kcN_L": -5.0}, {"kc_L": 0.0}):
+        with pytest.raises(SbiemError) as e:
+            Fault.from_workload(w, use_torch=False, **kw)
+        assert ERR.get(e.value.code) == "INVALID"

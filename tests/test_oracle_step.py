@@ -159,6 +159,14 @@ def test_two_cutting_planes_single_mode_closed_form():
     assert np.abs(o.last["sig_el"] - sig).max() < 1e-12 * scale
 
 
+def test_quasi_dynamic_limit_empties_both_planes():
+    from oracle.sbiem import field_windows
+    p = _params(N=64, eta_w=0.0)
+    p.kcN_L = 400.0
+    MT, MN = field_windows(p)
+    assert not MT.any() and not MN.any() and not windows(p).any()
+
+
 def test_normal_cutting_plane_convergence():
     # Truncation study (Sec. 3.1): with the shear plane fixed, raising the
     # normal plane leaves the shear traction bitwise unchanged and brings
