@@ -255,12 +255,14 @@ int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN);
  * sbiem_history_sums for callers that cannot allocate device memory.  The
  * paper has no counterpart; this entry point exists for library users.
  *
- * Who needs it: code that must not call cudaMalloc or any allocating routine
- * -- work recorded into the caller's own CUDA graph (device allocation is not
- * allowed during global-mode stream capture), real-time loops that cannot
- * afford the allocator's latency or locks, and frameworks that hand out all
- * device memory from their own fixed arena.  Such a caller keeps the history
- * in its own buffers and needs only the sums.
+ * Who needs it: callers that must not allocate device memory themselves or
+ * through a library.  A host application that owns every byte of the GPU
+ * (a simulation framework handing out slices of one fixed arena, or a
+ * process held to a hard device-memory budget) cannot let a library grow its
+ * footprint behind its back; a real-time loop cannot take cudaMalloc's
+ * latency, its device-wide synchronization or its locks in the middle of a
+ * step.  Such a caller keeps the history in its own buffers and needs only
+ * the sums.
  *
  * Inputs (device pointers, caller-owned, not modified):
  *   ring     nslots history slots in the library's layout: per slot the
@@ -269,7 +271,9 @@ int sbiem_history_sums(sbiem_t s, int64_t m, double* AT, double* AN);
  *   weights  per lag the pair (w^T, w^N), FP64 (16 bytes) or FP32 (8 bytes);
  *   ring_off[n], w_off[n] (int64, nmodes entries) start slot / weight of mode n;
  *   R[n] = M_n - 1 (int32, slots of mode n), M[n] = M_n (int32, weights of
- *   mode n), head[n] (int32, ring position of the newest slot of mode n).
+ *   mode n), head[n] (int32, ring position of the newest slot of mode n,
+ *   0 <= head[n] < R[n], 0 where R[n] = 0; the slot of the i-th newest value
+ *   is (head[n] + i) mod R[n]).
  * Outputs: AT, AN (device, nmodes complex FP64 each, re/im interleaved).
  * m: the history shift (a step of m dt_min), m >= 1.  stream: cudaStream_t or
  * NULL.

@@ -88,7 +88,7 @@ struct sbiem_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int lag_m = -1;
   int lag_grid = 0;  // CTAs of the overlapped sweep (leaves room for the passes)
-  int sweep_shape = 0;  // chunk length x stages of the sweep (SBIEM_SWEEP_SHAPE overrides)
+  int sweep_shape = 0;  // chunk length x stages of the sweep
   int lag_shape = 0;    // the same for the overlapped sweep
   // timing probe: 4 events per slot; graph event-record nodes are retargeted
   // to the slot of each launch
@@ -222,16 +222,7 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   f.V0 = s->p.V0;
   f.lnV0 = std::log(s->p.V0);
   f.state_law = s->p.state_law;
-  {
-    // elements per Newton warp (32 measured fastest on GB300; the variable
-    // SBIEM_NEWTON_EPW overrides it for experiments)
-    int epw = 32;
-    if (const char* e = std::getenv("SBIEM_NEWTON_EPW")) {
-      const int v = std::atoi(e);
-      if (v >= 1 && v <= 32) epw = v;
-    }
-    f.newton_epw = epw;
-  }
+  f.newton_epw = 32;  // elements per Newton warp: 32 measured fastest on GB300
   f.newton_maxit = s->p.newton_maxit;
   f.sweep_shape = s->sweep_shape;
   f.lag_shape = s->lag_shape;
@@ -494,10 +485,6 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     if (s->fp32()) configure_kernels<float>(make_geom(N, sizeof(float2)));
     else configure_kernels<double>(make_geom(N, sizeof(double2)));
     s->sweep_shape = kDefaultSweepShape;
-    if (const char* e = std::getenv("SBIEM_SWEEP_SHAPE")) {
-      const int v = std::atoi(e);
-      if (v >= 0 && v < 4) s->sweep_shape = v;
-    }
     const int per_sm = s->fp32() ? sweep_blocks_per_sm<float>(s->sweep_shape)
                                  : sweep_blocks_per_sm<double>(s->sweep_shape);
     s->hist_grid = s->sm_count * (per_sm > 0 ? per_sm : 1);
@@ -1823,16 +1810,71 @@ int sbiem_save(sbiem_t s, const char* path) {
   return SBIEM_OK;
 }
 
-int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc) {
-  if (!out || !path) return fail(SBIEM_ERR_INVALID, "NULL argument");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Every check of a checkpoint that needs no device: the header's
+// parameters, the history size they imply and each mode's ring head.  On
+// success *hd holds the header and the file is positioned after it.
+int load_checked(FILE* fp, const char* path, CkHeader* hd_out, sbiem_params* p_out, std::vector<int64_t>* R_out) {
+  CkHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, kCkMagic, 8) != 0 || !is_pow2(hd.N) ||
+      hd.N < 16 || hd.N > (1 << 20) || hd.total_slots < 0)
+    return fail(SBIEM_ERR_INVALID, std::string("not a checkpoint: ") + path);
+  sbiem_params p;
+  sbiem_default_params(&p);
+  p.N = hd.N;
+  p.precision = hd.precision;
+  p.state_law = hd.state_law;
+  p.kc_units = hd.kc_units;
+  p.newton_maxit = hd.newton_maxit;
+  p.dx = hd.dx;
+  p.mu = hd.mu;
+  p.cs = hd.cs;
+  p.cp = hd.cp;
+  p.beta_min = hd.beta_min;
+  p.eta_w = hd.eta_w;
+  p.kc_L = hd.kc_L;
+  p.kcN_L = hd.kcN_L;
+  p.newton_tol = hd.newton_tol;
+  p.f0 = hd.f0;
+  p.V0 = hd.V0;
+  if (!(p.dx > 0) || !(p.cs > 0) || !(p.cp > p.cs) || !(p.beta_min > 0) || !(p.eta_w >= 0) || !(p.kc_L > 0) ||
+      !(p.kcN_L >= 0) || (p.precision != 0 && p.precision != 1) || (p.kc_units != 0 && p.kc_units != 1) ||
+      !std::isfinite(p.dx * p.cs * p.cp * p.beta_min * p.eta_w * p.kc_L * p.kcN_L))
+    return fail(SBIEM_ERR_INVALID, std::string("checkpoint parameters out of range: ") + path);
+  // the history size the parameters imply, before any buffer is sized from the file
+  const double L = static_cast<double>(p.N) * p.dx, dt_min = p.beta_min * p.dx / p.cs;
+  const double longest = p.eta_w * L / p.cs / dt_min;
+  if (!(longest < 2.0e9)) return fail(SBIEM_ERR_INVALID, std::string("checkpoint windows too long: ") + path);
+  std::vector<int64_t> M, MT, MN;
+  windows(p, L, dt_min, M, MT, MN);
+  int64_t total = 0;
+  R_out->assign(M.size(), 0);
+  for (size_t n = 0; n < M.size(); ++n) {
+    (*R_out)[n] = std::max<int64_t>(M[n] - 1, 0);
+    total += (*R_out)[n];
+  }
+  if (total != hd.total_slots)
+    return fail(SBIEM_ERR_INVALID, "checkpoint history size does not match its parameters: " + std::string(path));
+  *hd_out = hd;
+  *p_out = p;
+  return SBIEM_OK;
+}
+
+}  // namespace
+
+static int sbiem_load_body(sbiem_t* out, const char* path, const sbiem_params* alloc) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return fail(SBIEM_ERR_INVALID, std::string("cannot open ") + path);
   CkHeader hd{};
-  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, kCkMagic, 8) != 0 || hd.N < 16 ||
-      hd.N > (1 << 20) || hd.total_slots < 0) {
+  sbiem_params p;
+  std::vector<int64_t> Rn;
+  const int rc0 = load_checked(fp, path, &hd, &p, &Rn);
+  if (rc0 != SBIEM_OK) {
     std::fclose(fp);
-    return fail(SBIEM_ERR_INVALID, std::string("not a checkpoint: ") + path);
+    return rc0;
   }
   const int N = static_cast<int>(hd.N);
   const size_t nm = static_cast<size_t>(N / 2 + 1);
@@ -1853,24 +1895,10 @@ int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc) {
             std::fread(&steps, sizeof(steps), 1, fp) == 1;
   std::fclose(fp);
   if (!ok) return fail(SBIEM_ERR_INVALID, std::string("truncated checkpoint: ") + path);
-  sbiem_params p;
-  sbiem_default_params(&p);
-  p.N = hd.N;
-  p.precision = hd.precision;
-  p.state_law = hd.state_law;
-  p.kc_units = hd.kc_units;
-  p.newton_maxit = hd.newton_maxit;
-  p.dx = hd.dx;
-  p.mu = hd.mu;
-  p.cs = hd.cs;
-  p.cp = hd.cp;
-  p.beta_min = hd.beta_min;
-  p.eta_w = hd.eta_w;
-  p.kc_L = hd.kc_L;
-  p.kcN_L = hd.kcN_L;
-  p.newton_tol = hd.newton_tol;
-  p.f0 = hd.f0;
-  p.V0 = hd.V0;
+  // ring heads index the sweep's copies: 0 <= head_n < R_n (0 where a mode has no history)
+  for (size_t n = 0; n < nm; ++n)
+    if (heads[n] < 0 || (Rn[n] > 0 ? heads[n] >= Rn[n] : heads[n] != 0))
+      return fail(SBIEM_ERR_INVALID, "checkpoint ring head out of range at mode " + std::to_string(n));
   if (alloc) {
     p.alloc_fn = alloc->alloc_fn;
     p.free_fn = alloc->free_fn;
@@ -1920,4 +1948,14 @@ int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc) {
   return SBIEM_OK;
 }
 
-}  // extern "C"
+extern "C" int sbiem_load(sbiem_t* out, const char* path, const sbiem_params* alloc) {
+  if (!out || !path) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  try {
+    return sbiem_load_body(out, path, alloc);
+  } catch (const std::exception& ex) {
+    // host buffers sized from a corrupt file (already bounded above) or any
+    // other host failure: an error code, never an exception across the C ABI
+    return fail(SBIEM_ERR_INVALID, std::string("checkpoint load failed: ") + ex.what());
+  }
+}

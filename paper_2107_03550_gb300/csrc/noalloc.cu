@@ -1,8 +1,12 @@
-// History convolution without device allocation: the same kernel as the
-// handle-based path (Sec. 3.1 window, Sec. 3.3 step (2), midpoint weights),
-// run on caller-owned device buffers, with its scratch -- chunk table,
-// per-chunk partial sums, per-mode counters -- in one fixed static device
-// array instead of memory allocated by the library.
+// History convolution without device allocation: the sums of
+// sbiem_history_sums (Sec. 3.1 window, Sec. 3.3 step (2), midpoint weights)
+// on caller-owned device buffers.  It runs the library's warp-per-chunk
+// kernel (k_history_t: chunks handed out by an atomic counter, a mode's
+// chunk sums added in chunk order by the warp that finishes last), not the
+// handle's bulk-async sweep, whose static partition and per-mode finish
+// need tables sized per fault.  Its scratch -- chunk table, per-chunk
+// partial sums, per-mode counters -- is one fixed static device array
+// instead of memory allocated by the library.
 #include <cuda_runtime.h>
 
 #include <cstdint>

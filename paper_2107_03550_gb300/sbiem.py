@@ -22,7 +22,7 @@ _LIB = None
 
 FLAG_NEWTON, FLAG_OPENING, FLAG_STATE = 1, 2, 4
 ERR = {0: "OK", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -4: "NEWTON", -5: "OPENING", -6: "STATE",
-       -7: "DTMIN", -8: "UNSUPPORTED"}
+       -7: "DTMIN", -8: "UNSUPPORTED", -9: "WAIT"}
 
 _alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)

@@ -62,18 +62,23 @@ def test_seamount_rupture_1000_steps_fp64():
 @pytest.mark.parametrize("N,dx,seed", [(16, 25.0, 1), (64, 25.0, 2), (256, 10.0, 3), (2048, 10.0, 4)])
 def test_prefilled_history_random_state(N, dx, seed):
     # random state and a full, random history: several chunks per mode with
-    # ragged tails (N = 2048: 8191 slots in mode 1, 2048 per chunk)
+    # ragged tails (N = 2048: 8191 slots in mode 1, 2048 per chunk).  The
+    # initial slip is white noise of up to 5 cm: its curvature-weighted normal
+    # traction S H[kappa delta] grows with the slip's grid-scale roughness, and
+    # at 10 cm (N >= 256) or 50 cm (every N) it exceeds the 50 MPa load
+    # (sigma_load + sigma_el <= 0, an opening, Sec. 3.2) or drives the slip
+    # rate past any Newton root, so the step is not defined there.
     w = rough_fault(N, dx, 3e-3, seed=seed)
     rng = np.random.default_rng(seed)
-    w.V_init = np.exp(rng.uniform(np.log(1e-9), np.log(1e-1), N))
+    w.V_init = np.exp(rng.uniform(np.log(1e-9), np.log(1.0), N))
     w.theta_init = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), N))
     w.tau_load = w.sigma_load * 0.6 + rng.normal(0, 1e5, N)
     o = oracle_for(w)
     g = gpu_for(w)
-    delta0 = rng.uniform(0.0, 0.02, N)
+    delta0 = rng.uniform(0.0, 0.05, N)
     o.delta = delta0.copy()
     g.set_state(delta=delta0)
-    prefill(o, g, seed, scale=1e-6)
+    prefill(o, g, seed, scale=1e-4)
     for _ in range(3):
         assert o.step() == 0
         g.step()

@@ -78,8 +78,16 @@ def test_read_probe_rejects_bad_arguments(lib):
 
 
 def test_strerror_covers_codes(lib):
-    for code in range(0, -9, -1):
-        assert lib.sbiem_strerror(code)
+    # every SBIEM_ERR_* code of the header has a message and a binding name
+    import re
+    from paper_2107_03550_gb300.sbiem import ERR
+    hdr = open(os.path.join(ROOT, "include", "sbiem.h")).read()
+    codes = {int(v) for v in re.findall(r"#define SBIEM_(?:OK|ERR_\w+)\s+(-?\d+)", hdr)}
+    assert codes == set(range(0, -10, -1))
+    unknown = lib.sbiem_strerror(-1000)
+    for code in codes:
+        assert lib.sbiem_strerror(code) and lib.sbiem_strerror(code) != unknown
+        assert code in ERR
 
 
 def test_kernel_route_against_high_precision(lib):
@@ -112,3 +120,60 @@ def test_truncation_parameters_are_validated_before_any_device_work(lib):
         with pytest.raises(SbiemError) as e:
             Fault.from_workload(w, use_torch=False, **kw)
         assert ERR.get(e.value.code) == "INVALID"
+
+
+def _write_checkpoint(path, N, heads=None, total_slots=None, head_delta=None):
+    """A checkpoint file in the library's format, written by hand (no GPU):
+    header (magic, N, total_slots, four int32, eleven doubles), 14 element
+    arrays, the prescribed mask, F[delta] and F[kappa delta], the ring heads,
+    the FP64 ring (32 bytes per slot), the time and the step count."""
+    import struct
+    from oracle.sbiem import Params, windows
+    dx, mu, cs = 25.0, 30e9, 3464.0
+    cp = np.sqrt(3.0) * cs
+    p = Params(N=N, dx=dx, mu=mu, cs=cs, cp=cp, dt_min=0.25 * dx / cs)
+    R = np.maximum(windows(p) - 1, 0)
+    slots = int(R.sum()) if total_slots is None else total_slots
+    hd = b"SBIEMCK2" + struct.pack("<qq4i11d", N, slots, 0, 0, 0, 50, dx, mu, cs, cp, 0.25, 1.0, 200.0,
+                                   1e-12, 0.6, 1e-6, 0.0)
+    el = np.ones(14 * N)
+    h = np.zeros(R.size, dtype=np.int32) if heads is None else np.asarray(heads, np.int32)
+    with open(path, "wb") as fh:
+        fh.write(hd)
+        fh.write(el.tobytes())
+        fh.write(np.zeros(N, np.uint8).tobytes())
+        fh.write(np.zeros(4 * (N // 2 + 1)).tobytes())
+        fh.write(h.tobytes())
+        fh.write(np.zeros(4 * int(R.sum())).tobytes())
+        fh.write(struct.pack("<dq", 0.0, 0))
+    return R
+
+
+def test_checkpoint_load_rejects_bad_heads_and_sizes_on_the_host(lib, tmp_path):
+    # a corrupt checkpoint must fail with SBIEM_ERR_INVALID before any device
+    # work: a ring head at or past R_n would steer the sweep's bulk copies
+    # outside the ring, and a forged history size would size host buffers
+    # from the file
+    out = ctypes.c_void_p()
+    path = str(tmp_path / "ck.bin")
+    R = _write_checkpoint(path, 64)
+    n = int(np.argmax(R))
+    heads = np.zeros(R.size, np.int32)
+    heads[n] = R[n]
+    _write_checkpoint(path, 64, heads=heads)
+    assert lib.sbiem_load(ctypes.byref(out), path.encode(), None) == -1
+    assert b"ring head" in lib.sbiem_last_error()
+    heads[n] = -1
+    _write_checkpoint(path, 64, heads=heads)
+    assert lib.sbiem_load(ctypes.byref(out), path.encode(), None) == -1
+    heads[n] = 0
+    heads[0] = 1                      # mode 0 has no history
+    _write_checkpoint(path, 64, heads=heads)
+    assert lib.sbiem_load(ctypes.byref(out), path.encode(), None) == -1
+    _write_checkpoint(path, 64, total_slots=1 << 40)
+    assert lib.sbiem_load(ctypes.byref(out), path.encode(), None) == -1
+    assert b"history size" in lib.sbiem_last_error()
+    with open(path, "r+b") as fh:      # truncated file
+        fh.truncate(200)
+    assert lib.sbiem_load(ctypes.byref(out), path.encode(), None) == -1
+    assert not out.value

@@ -52,6 +52,67 @@ def test_static_stiffness_and_table1_lengths():
     assert 2 * mup * b * Dc / (np.pi * sig * (b - a) ** 2) == pytest.approx(pn["table1_L_inf"], rel=1e-3)
 
 
+# pi to 40 digits as an exact rational: the window counts below are ceilings
+# of irrational numbers, so 40 digits decide every one of them exactly
+_PI = __import__("fractions").Fraction("3.141592653589793238462643383279502884197")
+
+
+def _exact_windows(N: int, kc_L, beta=__import__("fractions").Fraction(1, 4), cycles=False):
+    """M_n of Sec. 3.1 in exact arithmetic, written from the window's definition.
+
+    dt_min = beta dx / c_s and the full window eta L / c_s (eta = 1) give
+    T_w / dt_min = N / beta below the cutting plane.  Above it the window
+    shrinks by k_c / k_n with k_n = 2 pi n / L and k_c = kc_L / L rad/m
+    (kc_L / L cycles/m, i.e. 2 pi kc_L / L rad/m, with cycles=True), so
+    T_w / dt_min = (N / beta) kc_L / (2 pi n)  (rad)  or  (N / beta) kc_L / n
+    (cycles).  The window is continuous at k = k_c, so either side of the
+    plane gives the same count there.  M_0 = 0.
+    """
+    from fractions import Fraction
+    import math
+    full = Fraction(N) / beta
+    out = [0]
+    for n in range(1, N // 2 + 1):
+        ratio = Fraction(kc_L) / (n if cycles else 2 * _PI * n)
+        out.append(math.ceil(full * min(Fraction(1), ratio)))
+    return np.array(out, dtype=np.int64)
+
+
+def test_windows_exact_counts():
+    # The seamount rupture (N = 256, dx = 25 m, k_c L = 200 rad): 31 modes
+    # below the plane (n_c = 100/pi = 31.83) keep the full 4N = 1024 lags,
+    # mode 32 keeps ceil(102400/(32 pi)) = 1019, mode 33 988, the Nyquist
+    # mode 255; in all 77,616 lags per field.
+    p = _params(N=256, dx=25.0)
+    M = windows(p)
+    ref = _exact_windows(256, 200)
+    assert np.array_equal(M, ref)
+    assert M[31] == 1024 and M[32] == 1019 and M[33] == 988 and M[128] == 255
+    assert int(M.sum()) == 77616
+    # The rough-fault cycle (N = 4096, dx = 10 m): 2,684,079 ring slots
+    # (M_n - 1 per mode with history)
+    p = _params(N=4096, dx=10.0)
+    M = windows(p)
+    assert np.array_equal(M, _exact_windows(4096, 200))
+    assert int(np.maximum(M - 1, 0).sum()) == 2684079
+    # cycles/m with an exact integer ratio above the plane: n = 16 of N = 64
+    # at k_c L = 10 cycles has T_w / dt_min = 256 * 10 / 16 = 160 exactly,
+    # which the ceiling must not push to 161; n = 10 sits on the plane
+    p = Params(N=64, dx=25.0, mu=30e9, cs=3464.0, cp=np.sqrt(3.0) * 3464.0, dt_min=0.25 * 25.0 / 3464.0,
+               kc_L=10.0, kc_units="cycles")
+    M = windows(p)
+    assert np.array_equal(M, _exact_windows(64, 10, cycles=True))
+    assert M[16] == 160 and M[10] == 256 and M[11] == 233
+    # two planes: each field's window from its own k_c
+    p = Params(N=256, dx=25.0, mu=30e9, cs=3464.0, cp=np.sqrt(3.0) * 3464.0, dt_min=0.25 * 25.0 / 3464.0,
+               kc_L=100.0, kcN_L=300.0)
+    from oracle.sbiem import field_windows
+    MT, MN = field_windows(p)
+    assert np.array_equal(MT, _exact_windows(256, 100))
+    assert np.array_equal(MN, _exact_windows(256, 300))
+    assert np.array_equal(windows(p), np.maximum(MT, MN))
+
+
 def test_uniform_slip_rate_gives_no_elastic_shear_change():
     w = rough_fault(128, 25.0, 3e-3, seed=2, lam_min=100.0)
     p = _params(N=128, dx=25.0)
