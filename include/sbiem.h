@@ -151,6 +151,11 @@ int sbiem_step(sbiem_t s, double dt);
  */
 int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps);
 
+/* Kernels one replay of the step graph of sbiem_enqueue launches for steps
+ * of dt (a power of two times dt_min; the graph is captured if it is not
+ * yet).  The prologue sweep of a new sequence is not counted. */
+int sbiem_step_kernels(sbiem_t s, double dt, int64_t* kernels);
+
 /* Synchronize and read the device status bits (SBIEM_FLAG_*) and the number of
  * committed steps; clear != 0 resets the status word (state is unaffected). */
 int sbiem_status(sbiem_t s, uint32_t* flags, int64_t* steps_done, int clear);
@@ -209,6 +214,11 @@ int sbiem_windows(sbiem_t s, int64_t* M);
  * the normal field F[kappa Vbar].  Length of each array: 2 * sum_n (M_n - 1)
  * doubles.  The spectral convention is F[f]_n = sum_i f_i exp(-2 pi i n i/N). */
 int sbiem_set_history(sbiem_t s, const double* hist_T, const double* hist_N);
+/* The same from device memory: hist_T, hist_N are device arrays in the
+ * layout above, FP64 (values_fp32 = 0) or FP32 (values_fp32 = 1) re/im
+ * pairs, converted to the handle's precision on the device (for rings of
+ * hundreds of millions of slots).  Synchronizes the handle's stream. */
+int sbiem_set_history_device(sbiem_t s, const void* hist_T, const void* hist_N, int32_t values_fp32);
 int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
 
 /* Checkpoint / restart.  sbiem_save writes to `path` (binary, little endian,

@@ -41,7 +41,8 @@ import numpy as np
 
 from .kernels import kernel_pair
 
-__all__ = ["Params", "windows", "weights", "Oracle", "newton_lnV", "state_update",
+__all__ = ["Params", "windows", "weights", "Oracle", "newton_lnV", "state_update", "mode_history_sum",
+           "history_sums_sampled",
            "STATUS_OK", "STATUS_NEWTON", "STATUS_OPENING", "STATUS_STATE"]
 
 STATUS_OK = 0
@@ -139,28 +140,93 @@ def windows(p: Params) -> np.ndarray:
     return np.maximum(MT, MN)
 
 
-def weights(p: Params, M: np.ndarray | None = None):
+_CHUNK = 1 << 20   # kernel points evaluated per call (bounds the quadrature's temporaries)
+
+
+def _kernel_pair_chunk(args):
+    s, r = args
+    return kernel_pair(s, r)
+
+
+def _kernel_pair_all(s: np.ndarray, r: float, workers: int = 1):
+    """kernel_pair over s in chunks of _CHUNK points, optionally in worker processes.
+
+    The kernels are evaluated point by point, so chunking and the worker
+    count change only the schedule, never a value.  Workers are started with
+    the 'spawn' method (safe beside an initialized CUDA context).
+    """
+    if s.size <= _CHUNK or workers <= 1:
+        parts = [kernel_pair(s[i:i + _CHUNK], r) for i in range(0, max(s.size, 1), _CHUNK)]
+    else:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        jobs = [(s[i:i + _CHUNK], r) for i in range(0, s.size, _CHUNK)]
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_kernel_pair_chunk, jobs))
+    return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
+
+
+def weights(p: Params, M: np.ndarray | None = None, modes=None, workers: int = 1):
     """Midpoint weights w_{n,j} = dt_min * C(k_n, (j + 1/2) dt_min), j = 0..M_n-1 (Sec. 3.3).
 
     Returns (wT, wN, offsets): flat arrays with mode n occupying
     [offsets[n], offsets[n+1]).  With two cutting planes a field's weights
     are zero past its own window M^X_n (the kernel truncated there).
+    ``modes`` (optional) restricts the evaluation to those modes: the other
+    modes then get empty ranges.  ``workers`` > 1 evaluates the kernels in
+    that many processes.
     """
     if M is None:
         M = windows(p)
+    M = np.asarray(M, dtype=np.int64)
+    Mk = M
+    if modes is not None:
+        keep = np.zeros(M.size, dtype=bool)
+        keep[np.asarray(modes, dtype=np.int64)] = True
+        Mk = np.where(keep, M, 0)
     k = wavenumbers(p)
-    offsets = np.zeros(M.size + 1, dtype=np.int64)
-    offsets[1:] = np.cumsum(M)
-    mode = np.repeat(np.arange(M.size), M)
+    offsets = np.zeros(Mk.size + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(Mk)
+    mode = np.repeat(np.arange(Mk.size), Mk)
     j = np.arange(offsets[-1]) - offsets[mode]
     s = p.cs * k[mode] * (j + 0.5) * p.dt_min
-    GT, GN = kernel_pair(s, p.r)
+    GT, GN = _kernel_pair_all(s, p.r, workers)
     wT, wN = p.dt_min * GT, p.dt_min * GN
     MT, MN = field_windows(p)
-    if M.size == MT.size:
+    if Mk.size == MT.size:
         wT = np.where(j < MT[mode], wT, 0.0)
         wN = np.where(j < MN[mode], wN, 0.0)
     return wT, wN, offsets
+
+
+def mode_history_sum(wT, wN, HT, HN, m: int):
+    """One mode's history sums A^X = sum_{j=m}^{M-1} w^X_j H^X[j-m] (Sec. 3.3 step (2)).
+
+    wT, wN: the mode's M weights (lag order); HT, HN: its past spectra,
+    newest first (at least M - m of them).  The sum runs over j ascending.
+    """
+    M = len(wT)
+    if M <= m:
+        return 0j, 0j
+    j = np.arange(m, M)
+    return np.sum(wT[j] * HT[j - m]), np.sum(wN[j] * HN[j - m])
+
+
+def history_sums_sampled(p: Params, modes, HT, HN, m: int = 1, workers: int = 1):
+    """The history sums of the listed modes alone, from their own histories.
+
+    HT[i], HN[i]: the past spectra of modes[i], newest first.  The same
+    windows, weights and sums as Oracle.history_sums, with the weights
+    evaluated only for these modes (for faults too large to tabulate whole).
+    """
+    M = windows(p)
+    wT, wN, woff = weights(p, M, modes=modes, workers=workers)
+    AT = np.zeros(len(modes), dtype=np.complex128)
+    AN = np.zeros(len(modes), dtype=np.complex128)
+    for i, n in enumerate(modes):
+        w = slice(woff[n], woff[n + 1])
+        AT[i], AN[i] = mode_history_sum(wT[w], wN[w], np.asarray(HT[i]), np.asarray(HN[i]), m)
+    return AT, AN
 
 
 def state_update(theta0, Vbar, thetadot_bar, Dc, dt, law: str):
@@ -262,6 +328,7 @@ class Oracle:
     t: float = 0.0
     steps: int = 0
     thetadot: np.ndarray | None = field(default=None)
+    workers: int = 1              # processes evaluating the weight tables (values do not depend on it)
 
     def __post_init__(self):
         p = self.p
@@ -295,7 +362,7 @@ class Oracle:
                                      self.sigma_load * fr + p.eta_rd * self.V)
         self.k = wavenumbers(p)
         self.M = windows(p)
-        self.wT, self.wN, self.woff = weights(p, self.M)
+        self.wT, self.wN, self.woff = weights(p, self.M, workers=self.workers)
         # history: mode n keeps R_n = M_n - 1 past spectra; lag j (>= 1) of
         # mode n sits at ring slot (head_n + j - 1) mod R_n.
         self.R = np.maximum(self.M - 1, 0)
@@ -341,10 +408,9 @@ class Oracle:
             Mn, Rn = int(self.M[n]), int(self.R[n])
             if Mn <= m:
                 continue
-            j = np.arange(m, Mn)
-            idx = self.hoff[n] + (self.head[n] + (j - m)) % Rn
-            AT[n] = np.sum(self.wT[self.woff[n] + j] * self.hist_T[idx])
-            AN[n] = np.sum(self.wN[self.woff[n] + j] * self.hist_N[idx])
+            idx = self.hoff[n] + (self.head[n] + np.arange(Mn - m)) % Rn
+            w = slice(self.woff[n], self.woff[n] + Mn)
+            AT[n], AN[n] = mode_history_sum(self.wT[w], self.wN[w], self.hist_T[idx], self.hist_N[idx], m)
         return AT, AN
 
     def current_weights(self, m: int = 1):

@@ -759,6 +759,56 @@ int sbiem_status(sbiem_t s, uint32_t* flags, int64_t* steps_done, int clear) {
   return SBIEM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The overlapped step graph of m dt_min (captured and instantiated once).
+int lag_graph(sbiem_s* s, int m) {
+  if (s->lag_graphs.count(m)) return SBIEM_OK;
+  cudaGraph_t gdef = nullptr;
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
+  if (s->fp32()) enqueue_step_lag_t<float>(s, s->f32, m, s->own);
+  else enqueue_step_lag_t<double>(s, s->f64, m, s->own);
+  cudaError_t e1 = cudaGetLastError();
+  cudaError_t e2 = cudaStreamEndCapture(s->own, &gdef);
+  if (e1 != cudaSuccess || e2 != cudaSuccess)
+    return fail(SBIEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+  cudaGraphExec_t exec = nullptr;
+  CK(cudaGraphInstantiate(&exec, gdef, 0));
+  s->lag_graphs[m] = exec;
+  s->lag_defs[m] = gdef;
+  return SBIEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbiem_step_kernels(sbiem_t s, double dt, int64_t* kernels) {
+  if (!s || !kernels) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  int m;
+  int rc = dt_to_m(s, dt, &m);
+  if (rc) return rc;
+  if (!is_pow2(m) || m > (1 << 30)) return fail(SBIEM_ERR_INVALID, "m must be a power of two");
+  rc = lag_graph(s, m);
+  if (rc) return rc;
+  cudaGraph_t gdef = s->lag_defs[m];
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(gdef, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(gdef, nodes.data(), &nn));
+  int64_t k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    CK(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++k;
+  }
+  *kernels = k;
+  return SBIEM_OK;
+}
+
 int sbiem_step(sbiem_t s, double dt) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
   int m;
@@ -788,24 +838,9 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
   if (nsteps == 0) return SBIEM_OK;
   if (s->pslots == 0 && is_pow2(m) && m <= (1 << 30)) {
     // overlapped form (steps of 2^p dt_min, no timing probe)
+    rc = lag_graph(s, m);
+    if (rc) return rc;
     auto lt = s->lag_graphs.find(m);
-    if (lt == s->lag_graphs.end()) {
-      cudaGraph_t gdef = nullptr;
-      CK(cudaStreamSynchronize(s->stream));
-      CK(cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal));
-      if (s->fp32()) enqueue_step_lag_t<float>(s, s->f32, m, s->own);
-      else enqueue_step_lag_t<double>(s, s->f64, m, s->own);
-      cudaError_t e1 = cudaGetLastError();
-      cudaError_t e2 = cudaStreamEndCapture(s->own, &gdef);
-      if (e1 != cudaSuccess || e2 != cudaSuccess)
-        return fail(SBIEM_ERR_CUDA,
-                    std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
-      cudaGraphExec_t exec = nullptr;
-      CK(cudaGraphInstantiate(&exec, gdef, 0));
-      s->lag_graphs[m] = exec;
-      s->lag_defs[m] = gdef;
-      lt = s->lag_graphs.find(m);
-    }
     if (s->lag_m != m) {
       // prologue: this step's full sums
       if (s->fp32()) launch_history<float>(s->f32, m, s->hist_grid, s->stream);
@@ -1123,6 +1158,24 @@ int sbiem_set_history(sbiem_t s, const double* hT, const double* hN) {
     CK(cudaMemcpyAsync(s->f64.head, heads.data(), sizeof(int32_t) * s->nmodes, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
   }
+  return SBIEM_OK;
+}
+
+int sbiem_set_history_device(sbiem_t s, const void* hT, const void* hN, int32_t values_fp32) {
+  if (!s || !hT || !hN || (values_fp32 != 0 && values_fp32 != 1)) return fail(SBIEM_ERR_INVALID, "NULL argument");
+  s->lag_m = -1;
+  const int64_t tot = s->total_slots;
+  if (tot == 0) return SBIEM_OK;
+  std::vector<int32_t> heads(s->nmodes, 0);
+  if (s->fp32()) {
+    launch_set_ring<float>(s->f32.ring, hT, hN, values_fp32 == 1, tot, s->sm_count, s->stream);
+    CK(cudaMemcpyAsync(s->f32.head, heads.data(), sizeof(int32_t) * s->nmodes, cudaMemcpyHostToDevice, s->stream));
+  } else {
+    launch_set_ring<double>(s->f64.ring, hT, hN, values_fp32 == 1, tot, s->sm_count, s->stream);
+    CK(cudaMemcpyAsync(s->f64.head, heads.data(), sizeof(int32_t) * s->nmodes, cudaMemcpyHostToDevice, s->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s->stream));
   return SBIEM_OK;
 }
 

@@ -2161,6 +2161,38 @@ void launch_to_float2(const double2* a, float2* out, int n, cudaStream_t st) {
   k_to_float2<<<(n + 255) / 256, 256, 0, st>>>(a, out, n);
 }
 
+// Ring slots from two device arrays of interleaved complex values (shear,
+// normal), FP64 (in_f32 = false) or FP32, converted to the ring's precision.
+template <class R, class I>
+__global__ void k_set_ring(Slot<R>* ring, const I* __restrict__ hT, const I* __restrict__ hN, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    Slot<R> v;
+    if constexpr (sizeof(R) == 4) {
+      v = make_float4(static_cast<float>(hT[2 * i]), static_cast<float>(hT[2 * i + 1]),
+                      static_cast<float>(hN[2 * i]), static_cast<float>(hN[2 * i + 1]));
+    } else {
+      v.t = make_double2(static_cast<double>(hT[2 * i]), static_cast<double>(hT[2 * i + 1]));
+      v.n = make_double2(static_cast<double>(hN[2 * i]), static_cast<double>(hN[2 * i + 1]));
+    }
+    ring[i] = v;
+  }
+}
+
+template <class R>
+void launch_set_ring(Slot<R>* ring, const void* hT, const void* hN, bool in_f32, int64_t n, int sm_count,
+                     cudaStream_t st) {
+  if (n <= 0) return;
+  const int grid = 4 * sm_count;
+  if (in_f32)
+    k_set_ring<R, float><<<grid, 256, 0, st>>>(ring, static_cast<const float*>(hT), static_cast<const float*>(hN), n);
+  else
+    k_set_ring<R, double><<<grid, 256, 0, st>>>(ring, static_cast<const double*>(hT), static_cast<const double*>(hN),
+                                                n);
+}
+template void launch_set_ring<float>(Slot<float>*, const void*, const void*, bool, int64_t, int, cudaStream_t);
+template void launch_set_ring<double>(Slot<double>*, const void*, const void*, bool, int64_t, int, cudaStream_t);
+
 __global__ void k_zin(const double* V, const double* kappa, float2* zin, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) zin[i] = make_float2(static_cast<float>(V[i]), static_cast<float>(kappa[i] * V[i]));

@@ -174,6 +174,10 @@ void launch_to_float2(const double2* a, float2* out, int n, cudaStream_t st);
 void launch_zin(const double* V, const double* kappa, float2* zin, int n, cudaStream_t st);
 // Save (dir 0) / restore (dir 1) the ring slots a push of m_dt copies overwrites.
 template <class R> void launch_ring_undo(const DevFault<R>& f, int m_dt, void* undo, int dir, cudaStream_t st);
+// Ring slots ring[i] = (hT[i], hN[i]) from interleaved complex device arrays
+// (FP32 when in_f32, else FP64), n slots.
+template <class R> void launch_set_ring(Slot<R>* ring, const void* hT, const void* hN, bool in_f32, int64_t n,
+                                        int sm_count, cudaStream_t st);
 // *out = max_i |a_i - b_i|.
 void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st);
 template <class R> void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg,

@@ -63,6 +63,7 @@ _SIGS = {
     "sbiem_step": (ctypes.c_int, [_VP, ctypes.c_double]),
     "sbiem_enqueue": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int64]),
     "sbiem_status": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _I64, ctypes.c_int]),
+    "sbiem_step_kernels": (ctypes.c_int, [_VP, ctypes.c_double, _I64]),
     "sbiem_step_host": (ctypes.c_int, [_VP, ctypes.c_double, _D, _D]),
     "sbiem_run": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
                                  ctypes.c_int64, _I64, _I64, _D, _I64]),
@@ -71,6 +72,7 @@ _SIGS = {
     "sbiem_windows": (ctypes.c_int, [_VP, _I64]),
     "sbiem_set_history": (ctypes.c_int, [_VP, _D, _D]),
     "sbiem_get_history": (ctypes.c_int, [_VP, _D, _D]),
+    "sbiem_set_history_device": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32]),
     "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
     "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
@@ -367,6 +369,12 @@ class Fault:
     def enqueue(self, nsteps: int, dt=None) -> None:
         self._check(self.lib.sbiem_enqueue(self.h, float(dt or self.dt_min), int(nsteps)))
 
+    def step_kernels(self, dt=None) -> int:
+        """Kernel launches in one replay of the step graph of :meth:`enqueue`."""
+        k = ctypes.c_int64()
+        self._check(self.lib.sbiem_step_kernels(self.h, float(dt or self.dt_min), ctypes.byref(k)))
+        return k.value
+
     def status(self, clear: bool = False):
         fl = ctypes.c_uint32()
         st = ctypes.c_int64()
@@ -424,6 +432,21 @@ class Fault:
         a = np.ascontiguousarray(np.asarray(HT, np.complex128).reshape(tot)).view(np.float64)
         b = np.ascontiguousarray(np.asarray(HN, np.complex128).reshape(tot)).view(np.float64)
         self._check(self.lib.sbiem_set_history(self.h, a.ctypes.data_as(_D), b.ctypes.data_as(_D)))
+
+    def set_history_device(self, HT, HN) -> None:
+        """The same from device tensors: complex64/complex128 (or float pairs), flat, contiguous."""
+        import torch
+        tot = self.history_size()
+        ts = []
+        for h in (HT, HN):
+            t = torch.view_as_real(h) if h.is_complex() else h
+            if t.numel() != 2 * tot or not t.is_contiguous() or t.dtype not in (torch.float32, torch.float64):
+                raise ValueError("expected contiguous FP32/FP64 history of the handle's size on the device")
+            ts.append(t)
+        if ts[0].dtype != ts[1].dtype:
+            raise ValueError("both fields must have the same precision")
+        f32 = 1 if ts[0].dtype == torch.float32 else 0
+        self._check(self.lib.sbiem_set_history_device(self.h, ts[0].data_ptr(), ts[1].data_ptr(), f32))
 
     def get_history(self):
         tot = self.history_size()

@@ -12,6 +12,8 @@ seamount_rupture  N=256, dx=25 m, 20 m Gaussian seamount, single rupture.
 rough_cycle       N=4096, dx=10 m, Hurst-1 roughness, central 70% frictional,
                   outer 30% at plate rate.
 rough_fault       one rough-fault realization of any N (ensemble member).
+large_fault       N=262144, dx=1 m, Hurst-1 roughness (alpha=0.003) plus a
+                  200 m Gaussian seamount, friction layout of rough_cycle.
 sinusoidal_cycle  the earthquake cycle of Sec. "Seismic cycles": Table 1, a
                   sinusoidal fault of length L in a periodic domain of 4L
                   with null slip rate on 1.5L each side, uniform loading
@@ -24,7 +26,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["Workload", "gaussian_seamount", "seamount_rupture", "rough_profile", "rough_cycle", "rough_fault",
-           "sinusoidal_cycle", "random_history", "element_x"]
+           "sinusoidal_cycle", "large_fault", "random_history", "random_history_device", "element_x"]
 
 
 @dataclass
@@ -230,6 +232,52 @@ def rough_fault(N: int, dx: float, alpha: float, seed: int, lam_min: float | Non
         h=h, kappa=kappa, a=a, b=b, Dc=np.full(N, 1e-3), f0=0.6, V0=1e-6,
         sigma_load=np.full(N, 50e6), V_init=np.exp(lnV), theta_init=np.full(N, 1e-3 / 1e-9),
         prescribed=np.zeros(N, dtype=bool), V_presc=np.zeros(N))
+
+
+def random_history_device(R: np.ndarray, seed: int, scale: float, torch, dtype=None, device="cuda"):
+    """Seeded complex history drawn on the device (for rings too large to draw on the host).
+
+    Same layout as :func:`random_history` (flat, modes in order, newest
+    first); values N(0, scale^2) per part from PyTorch's generator on
+    ``device`` seeded with ``seed``.  Returns two complex tensors.
+    """
+    tot = int(np.maximum(np.asarray(R, dtype=np.int64), 0).sum())
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = []
+    for _ in range(2):
+        v = torch.randn(tot, 2, generator=g, dtype=dtype, device=device)
+        v.mul_(scale)
+        out.append(torch.view_as_complex(v))
+    return out[0], out[1]
+
+
+def large_fault(N: int = 262144, dx: float = 1.0, alpha: float = 0.003, seed: int = 4,
+                lam_min: float = 20.0, lam_max: float = 40e3, sea_amp: float = 200.0,
+                sea_sigma: float = 1000.0) -> Workload:
+    """A large rough fault with a seamount: Hurst-1 roughness (ratio alpha,
+    wavelengths in [lam_min, min(lam_max, L)]) plus a Gaussian seamount of
+    height sea_amp and standard deviation sea_sigma (2 sigma = 2 km wide, max
+    slope ~0.12) at the centre; friction and plate-rate loading of
+    :func:`rough_cycle` (central 70% rate-and-state, outer 30% at V_pl).
+    """
+    cs = 3464.0
+    x = element_x(N, dx)
+    h, kappa = rough_profile_fast(N, dx, alpha, lam_min, min(lam_max, N * dx), seed)
+    hs, ks = gaussian_seamount(x, sea_amp, sea_sigma)
+    h = h + hs
+    kappa = kappa + ks
+    a, b, central = _central_friction(x, N * dx, 0.7)
+    Vpl = 1e-9
+    return Workload(
+        name=(f"large_fault N={N} dx={dx:g}m Hurst=1 alpha={alpha:g} lambda=[{lam_min:g},{min(lam_max, N * dx):g}]m "
+              f"seed={seed} + seamount {sea_amp:g}m sigma={sea_sigma:g}m"),
+        N=N, dx=dx, mu=30e9, cs=cs, cp=np.sqrt(3.0) * cs, dt_min=0.25 * dx / cs,
+        h=h, kappa=kappa, a=a, b=b, Dc=np.full(N, 1e-3), f0=0.6, V0=1e-6,
+        sigma_load=np.full(N, 50e6), V_init=np.full(N, Vpl), theta_init=np.full(N, 1e-3 / Vpl),
+        prescribed=~central, V_presc=np.where(central, 0.0, Vpl),
+        extra={"alpha": alpha, "lam_min": lam_min, "lam_max": min(lam_max, N * dx), "seamount": (sea_amp, sea_sigma)})
 
 
 def random_history(R: np.ndarray, seed: int, scale: float = 1e-9):

@@ -13,7 +13,7 @@ def oracle_for(w: Workload, **kw) -> Oracle:
     return Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, w.tau_load, w.V_init,
                   w.theta_init, tau_load_rate=w.tau_load_rate,
                   prescribed=w.prescribed if np.any(w.prescribed) else None,
-                  V_presc=w.V_presc if np.any(w.prescribed) else None)
+                  V_presc=w.V_presc if np.any(w.prescribed) else None, workers=kw.pop("workers", 1))
 
 
 def gpu_for(w: Workload, **kw):

@@ -38,15 +38,20 @@ def test_scaling_fit_is_scale_free_and_sees_the_sign():
 
 
 def test_bench_reads_recorded_traffic_only_for_the_current_sweep_source(tmp_path, monkeypatch):
+    # a profile of a smaller fault of the same family is scaled by ring slots
     import bench
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "_sweep_source_sha", lambda: "0123456789abcdef")
-    path = os.path.join(str(tmp_path), "profiles", "k_sweep_fp32_rough_cycle_N4096.md")
+    path = os.path.join(str(tmp_path), "profiles", "k_sweep_fp32_large_N65536.md")
+    body = ("# k_sweep\n\n- k_sweep source sha256[:16]: {}\n- workload family: large\n- ring slots: 1000\n"
+            "- dram bytes per launch: 16000\n")
     with open(path, "w") as fh:
-        fh.write("# k_sweep\n\n- k_sweep source sha256[:16]: 0123456789abcdef\n- dram bytes per launch: 64743168\n")
-    assert bench._traffic("fp32", 4096) == 64743168.0
+        fh.write(body.format("0123456789abcdef"))
+    t = bench._traffic("fp32", "large", 4000)
+    assert t["bytes"] == 64000.0 and t["scaled_by_slots"] == 4.0
+    assert bench._traffic("fp32", "rough", 4000) is None
+    assert bench._traffic("fp64", "large", 4000) is None
     with open(path, "w") as fh:
-        fh.write("- k_sweep source sha256[:16]: fedcba9876543210\n- dram bytes per launch: 64743168\n")
-    assert bench._traffic("fp32", 4096) is None
-    assert bench._traffic("fp64", 4096) is None
+        fh.write(body.format("fedcba9876543210"))
+    assert bench._traffic("fp32", "large", 4000) is None

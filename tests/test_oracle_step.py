@@ -418,3 +418,38 @@ def test_seamount_rupture_nucleates_and_crosses():
         crossed = crossed or (o.V[np.argmin(np.abs(x - 1000.0))] > 1e-1)
     assert vmax > 0.1
     assert crossed
+
+
+def test_weight_evaluation_schedule_changes_no_value():
+    # restricting the weights to some modes, chunking them and evaluating them
+    # in worker processes only reschedules a pointwise evaluation: the values
+    # are bitwise those of the full table, and the sampled history sums those
+    # of Oracle.history_sums
+    import oracle.sbiem as osb
+    from oracle.sbiem import history_sums_sampled, weights
+    from paper_2107_03550_gb300.workloads import random_history
+    p = _params(N=256, dx=25.0)
+    wT, wN, off = weights(p)
+    modes = [1, 31, 32, 100, 128]
+    sT, sN, soff = weights(p, modes=modes)
+    for n in modes:
+        assert np.array_equal(sT[soff[n]:soff[n + 1]], wT[off[n]:off[n + 1]])
+        assert np.array_equal(sN[soff[n]:soff[n + 1]], wN[off[n]:off[n + 1]])
+    assert soff[-1] == sum(off[n + 1] - off[n] for n in modes)
+    old = osb._CHUNK
+    try:
+        osb._CHUNK = 4096
+        cT, cN, _ = weights(p, workers=2)
+    finally:
+        osb._CHUNK = old
+    assert np.array_equal(cT, wT) and np.array_equal(cN, wN)
+    w = seamount_rupture(N=256)
+    o = Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, None, w.V_init, w.theta_init)
+    R = np.maximum(o.M - 1, 0)
+    HT, HN, hoff = random_history(R, 3, 1e-3)
+    o.set_history([HT[hoff[n]:hoff[n + 1]] for n in range(R.size)], [HN[hoff[n]:hoff[n + 1]] for n in range(R.size)])
+    for m in (1, 3):
+        AT, AN = o.history_sums(m)
+        sAT, sAN = history_sums_sampled(p, modes, [HT[hoff[n]:hoff[n + 1]] for n in modes],
+                                        [HN[hoff[n]:hoff[n + 1]] for n in modes], m)
+        assert np.array_equal(sAT, AT[modes]) and np.array_equal(sAN, AN[modes])
