@@ -120,6 +120,8 @@ def _fill_history(torch, g, seed: int, precision: str):
     """Seeded random history drawn on the device (every window full)."""
     from paper_2107_03550_gb300.workloads import random_history_device
     R = np.maximum(g.windows() - 1, 0)
+    if R.sum() == 0:
+        return   # no history (the quasi-dynamic limit)
     dt = torch.float32 if precision == "fp32" else torch.float64
     HT, HN = random_history_device(R, seed, HIST_AMP * np.sqrt(g.N), torch, dtype=dt)
     g.set_history_device(HT, HN)
@@ -376,6 +378,7 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
     _fill_history(torch, g, 11 + rank, precision)
     if mlp is not None:
         g.set_mlp(mlp)
+    tuned = g.tune(reps=5)   # the library's autotuner: sweep shape, weight form, CTAs per SM
     hist_bytes, dev_bytes = g.footprint()
     slots = int(np.maximum(g.windows() - 1, 0).sum())
     ring_bytes = slots * (16 if precision == "fp32" else 32)
@@ -431,12 +434,14 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
                 hist_ms=statistics.mean(ms_hist), sweep_ms=statistics.mean(ms_sweep),
                 sweep_ms_median=statistics.median(ms_sweep), hist_bytes=hist_bytes, ring_bytes=ring_bytes,
                 weight_bytes=hist_bytes - ring_bytes, dev_bytes=dev_bytes, clocks=clk, it_sum=it_sum,
-                it_max=it_max, slots=slots, flushed=flushed, step_kernels=g.step_kernels(), steps=K)
+                it_max=it_max, slots=slots, flushed=flushed, step_kernels=g.step_kernels(), steps=K,
+                sweep=dict(tuned, table_err=g.get_sweep()["table_err"]))
 
 
 def _side(res: dict, what: str) -> dict:
     return {"N": res["N"], "value": res["value"], "ms_per_step": res["ms_per_step"], "sweep_ms": res["sweep_ms"],
             "ring_GBps": res["ring_bytes"] / (res["sweep_ms"] * 1e-3) / 1e9, "steps": res["steps"],
+            "sweep": res["sweep"],
             "l2": "flushed before every timed launch" if res["flushed"] else "rings larger than L2",
             "what": what}
 
@@ -627,7 +632,7 @@ def run_ours(a):
                        "weight_bytes_per_step": main["weight_bytes"], "device_bytes": main["dev_bytes"],
                        "device_bytes_limit": 180e9,
                        "newton_iters_last_step": {"sum": main["it_sum"], "max": main["it_max"]},
-                       "history_ms_with_finish": main["hist_ms"], "side": side},
+                       "history_ms_with_finish": main["hist_ms"], "sweep": main["sweep"], "side": side},
             "roofline": {"bound": "hbm", "kernel": "k_sweep", "achieved": achieved, "peak": peak,
                          "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs, burst: the sweep is timed alone)"
                          if peak_kind == "measured" else "fallback 6800 GB/s", "unit": "GB/s",

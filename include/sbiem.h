@@ -413,9 +413,37 @@ int sbiem_mlp_train(const float* samples, int64_t n, int epochs, int batch, floa
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);
 
-/* Bytes the history convolution must read per step (rings plus weights) and
- * the total device footprint of the handle. */
+/* Bytes the history convolution must read per step (rings, plus the
+ * weights unless the sweep evaluates them on chip) and the total device
+ * footprint of the handle. */
 int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_bytes);
+
+/*
+ * History sweep configuration (Sec. 3.3 step (2) runs unchanged; only its
+ * launch shape and where its weights come from change).
+ *   shape: lags per chunk x stages in flight; the chunk length is fixed at
+ *     creation (shape 3: 2048 lags FP32, 1024 FP64, two stages), so only
+ *     shapes of that chunk length are accepted (0 and 2, or 1, or 3).
+ *   generated (FP32 form only): 1 evaluates the midpoint weights
+ *     w_{n,j} = dt_min C(c_s k_n (j + 1/2) dt_min) on chip from a
+ *     piecewise-polynomial table of C^T, C^N (degree 5 on pieces of width
+ *     1/4 in s, built in FP64 from the library's kernel route, rounded to
+ *     FP32), so the sweep reads only the ring slots; 0 streams the
+ *     materialized weights with them.  A new FP32 handle evaluates them
+ *     whenever its windows' s range fits the table (about s <= 213, i.e.
+ *     k_c L <= 213 rad); table_err is the table's largest error relative to
+ *     dt_min max|C| (-1: no table).
+ *   ctas_per_sm: resident sweep CTAs per SM (0: as many as fit).
+ * sbiem_set_sweep synchronizes and rebuilds the step graphs.  sbiem_tune is
+ * the autotuner: it times `reps` launches (median, after one untimed) of the
+ * history convolution for every shape of the handle's chunk length, both
+ * weight forms and 1 .. (occupancy limit) CTAs per SM, and keeps the
+ * fastest; the committed state is unchanged.  Errors: SBIEM_ERR_INVALID,
+ * SBIEM_ERR_UNSUPPORTED (generated = 1 without a table), SBIEM_ERR_CUDA.
+ */
+int sbiem_get_sweep(sbiem_t s, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, double* table_err);
+int sbiem_set_sweep(sbiem_t s, int32_t shape, int32_t generated, int32_t ctas_per_sm);
+int sbiem_tune(sbiem_t s, int reps, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, float* ms);
 
 /*
  * sbiem_kernel_values -- host FP64 evaluation of the convolution kernels

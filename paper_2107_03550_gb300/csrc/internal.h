@@ -15,7 +15,13 @@ struct ChebTable {
   std::vector<double> coef;
 };
 
+// On-chip weight table of the FP32 history sweep: piece width (a power of
+// two, so piece indices and offsets are exact in FP32) and degree.
+constexpr double kGenH = 0.25;
+constexpr int kGenDeg = 5;
+
 void kernel_values(double s, double r, double* cT, double* cN);
+void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, int* npieces, double* max_err);
 void build_cheb(double r, double smax, ChebTable* tab);
 void build_twiddles(int64_t N, std::vector<double>& tw);
 

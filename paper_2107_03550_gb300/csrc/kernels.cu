@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "internal.h"
 #include "kernels.cuh"
 #include <math_constants.h>
 
@@ -935,10 +936,47 @@ constexpr int kSweepShapes = 5;
 constexpr int kSweepThreads = 128;
 constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls before a wait is declared stuck
 
-template <class R, int SH>
+// A stage holds a chunk's ring slots and, unless the weights are evaluated
+// on chip (GEN), its weight run.
+template <class R, int SH, bool GEN = false>
 __host__ __device__ constexpr size_t sweep_stage_bytes() {
   return static_cast<size_t>(SweepCfg<R, SH>::kSlots) * sizeof(Slot<R>) +
-         static_cast<size_t>(SweepCfg<R, SH>::kSlots + 2) * sizeof(W2<R>);
+         (GEN ? 0 : static_cast<size_t>(SweepCfg<R, SH>::kSlots + 2) * sizeof(W2<R>));
+}
+
+// On-chip weights: kGenDeg + 1 coefficient pairs (T, N) per piece of width
+// kGenH, three float4 per piece (48 bytes: an odd number of 16-byte bank
+// groups, so neighbouring pieces gathered by one warp fall in different banks).
+constexpr int kGenPairs = kGenDeg + 1;
+static_assert(kGenPairs == 6, "the evaluation below unrolls six coefficient pairs");
+constexpr float kGenHf = static_cast<float>(kGenH);
+constexpr float kGenInvH = static_cast<float>(1.0 / kGenH);
+
+// w = dt (C^T(s), C^N(s)) at s = jf ds, jf = j + 1/2, ds = dsh + dsl (two
+// floats).  p = jf dsh is rounded once; its error e = jf dsh - p comes
+// exactly from an FMA, so the offset within piece q (q kGenH exact, p - q
+// kGenH exact by Sterbenz) carries s to about 1e-8 absolute.  q is clamped to
+// the table (lags past a field's window are zeroed by the caller).
+__device__ __forceinline__ float2 gen_weight(const float4* __restrict__ tab, int qmax, float jf, float dsh,
+                                             float dsl) {
+  const float p = jf * dsh;
+  const float e = fmaf(jf, dsl, fmaf(jf, dsh, -p));
+  const float qf = floorf(p * kGenInvH);
+  int q = static_cast<int>(qf);
+  q = q < 0 ? 0 : (q > qmax ? qmax : q);
+  const float u = fmaf(-static_cast<float>(q), kGenHf, p) + e;
+  const float t = fmaf(u, 2.0f * kGenInvH, -1.0f);
+  const float4 a = tab[3 * q], b = tab[3 * q + 1], c = tab[3 * q + 2];
+  float wT = fmaf(c.z, t, c.x), wN = fmaf(c.w, t, c.y);
+  wT = fmaf(wT, t, b.z);
+  wN = fmaf(wN, t, b.w);
+  wT = fmaf(wT, t, b.x);
+  wN = fmaf(wN, t, b.y);
+  wT = fmaf(wT, t, a.z);
+  wN = fmaf(wN, t, a.w);
+  wT = fmaf(wT, t, a.x);
+  wN = fmaf(wN, t, a.y);
+  return make_float2(wT, wN);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -996,12 +1034,16 @@ struct SweepPlan {
   const void* wsrc;
   unsigned b1, b2, bw;
   int len, par, mode, member;
+  // on-chip weights: weight index of the chunk's first slot, the mode's ds
+  // as two floats and the two fields' windows
+  int j0, mt, mn;
+  float dsh, dsl;
 };
 constexpr int kPlanRing = 64;  // plans held in shared memory (a ring by chunk index)
 
 // Chunk c of the sweep: the fault's own chunk table, or an ensemble table
 // whose chunks name their member (Chunk::pad) in fs.
-template <class R, bool BATCH>
+template <class R, bool BATCH, bool GEN = false>
 __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const DevFault<R>* fs, const Chunk* chunks,
                                                 int c, int m_dt) {
   SweepPlan pl{};
@@ -1030,8 +1072,19 @@ __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const Dev
   pl.b1 = static_cast<unsigned>(L1 * sizeof(Slot<R>));
   pl.r2 = ring;
   pl.b2 = static_cast<unsigned>(L2 * sizeof(Slot<R>));
-  pl.wsrc = f.w + wa;
-  pl.bw = static_cast<unsigned>(wc * sizeof(W2<R>));
+  if constexpr (GEN) {
+    const float4 gi = f.wgen[n];
+    pl.j0 = static_cast<int>(m_dt + cd.i0);
+    pl.dsh = gi.x;
+    pl.dsl = gi.y;
+    pl.mt = __float_as_int(gi.z);
+    pl.mn = __float_as_int(gi.w);
+    pl.wsrc = nullptr;
+    pl.bw = 0;
+  } else {
+    pl.wsrc = f.w + wa;
+    pl.bw = static_cast<unsigned>(wc * sizeof(W2<R>));
+  }
   return pl;
 }
 
@@ -1046,23 +1099,29 @@ __device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* 
   mbar_expect_tx(bar, pl.b1 + pl.b2 + pl.bw);
   bulk_g2s(stage_buf, pl.r1, pl.b1, bar);
   if (pl.b2) bulk_g2s(stage_buf + pl.b1, pl.r2, pl.b2, bar);
-  bulk_g2s(sw, pl.wsrc, pl.bw, bar);
+  if (pl.bw) bulk_g2s(sw, pl.wsrc, pl.bw, bar);
 }
 
 // BATCH: the chunks of an ensemble (member in Chunk::pad), descriptors in fs;
 // members whose step failed are swept anyway (their sums are not written).
-template <class R, int SH, bool BATCH>
+// GEN (FP32): the weights are evaluated from the piecewise-polynomial table
+// wtab (wtab_pieces pieces, copied once into shared memory behind the
+// stages) instead of streamed with the ring slots.
+template <class R, int SH, bool BATCH, bool GEN>
 __global__ void __launch_bounds__(kSweepThreads)
     k_sweep(const __grid_constant__ DevFault<R> f, const DevFault<R>* __restrict__ fs,
-            const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt) {
+            const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt,
+            const float4* __restrict__ wtab, int wtab_pieces) {
+  static_assert(!GEN || sizeof(R) == 4, "on-chip weights belong to the FP32 form");
   constexpr int S = SweepCfg<R, SH>::kSlots;
   constexpr int kSweepStages = SweepCfg<R, SH>::kStages;
-  constexpr size_t SB = sweep_stage_bytes<R, SH>();
+  constexpr size_t SB = sweep_stage_bytes<R, SH, GEN>();
   constexpr int NW = kSweepThreads / 32;
   extern __shared__ __align__(128) unsigned char sweep_smem[];
   __shared__ __align__(8) uint64_t bars[kSweepStages];
+  __shared__ __align__(8) uint64_t tbar;
   __shared__ SweepPlan plan[kPlanRing];
-  __shared__ Acc4<R> red[2][NW];
+  __shared__ Acc4<double> red[2][NW];
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // the per-mode finish may be resident already, waiting for this grid
@@ -1077,49 +1136,85 @@ __global__ void __launch_bounds__(kSweepThreads)
   if (tid == 0) {
     s_skip = BATCH ? 0u : *f.status;
     for (int s = 0; s < kSweepStages; ++s) mbar_init(&bars[s], 1);
+    if (GEN) mbar_init(&tbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // plans of the first kPlanRing chunks (one per thread)
   for (int j = tid; j < kPlanRing && j < nk; j += kSweepThreads)
-    plan[j] = sweep_plan<R, BATCH>(f, fs, chunks, c0 + j, m_dt);
+    plan[j] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt);
   __syncthreads();
   if (s_skip) return;
-  if (tid == 0)
+  const float4* stab = reinterpret_cast<const float4*>(sweep_smem + kSweepStages * SB);
+  if (tid == 0) {
+    if (GEN) {
+      // the weight table, one bulk copy on its own barrier, ahead of the stages
+      const unsigned tb = static_cast<unsigned>(wtab_pieces) * 3u * 16u;
+      mbar_expect_tx(&tbar, tb);
+      bulk_g2s(sweep_smem + kSweepStages * SB, wtab, tb, &tbar);
+    }
     for (int k = 0; k < kSweepStages && k < nk; ++k)
       sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
-  // each thread accumulates over consecutive chunks of one mode; the CTA
-  // reduces at the end of the mode's run (a segment) and writes the sum at
-  // the segment's last chunk, zeros at the others
+  }
+  bool tab_ok = true;
+  if (GEN) tab_ok = mbar_wait(&tbar, 0u);
+  // each thread accumulates a chunk in R and folds it into an FP64 sum over
+  // the consecutive chunks of one mode (a run may hold hundreds of chunks,
+  // too many products for one FP32 sum); the CTA reduces at the end of the
+  // mode's run (a segment) and writes the sum at the segment's last chunk,
+  // zeros at the others
   bool stuck = false;
   int k = 0;
-  Acc4<R> acc = {R(0), R(0), R(0), R(0)};
+  Acc4<double> run = {0.0, 0.0, 0.0, 0.0};
   for (; k < nk; ++k) {
     const int s = k % kSweepStages;
     // every kPlanRing/2 chunks: plans of the half-ring ahead (chunks
     // k + kPlanRing/2 .. k + kPlanRing - 1 replace chunks already issued)
     if (k > 0 && k % (kPlanRing / 2) == 0) {
       const int j = k + kPlanRing / 2 + tid;
-      if (tid < kPlanRing / 2 && j < nk) plan[j % kPlanRing] = sweep_plan<R, BATCH>(f, fs, chunks, c0 + j, m_dt);
+      if (tid < kPlanRing / 2 && j < nk)
+        plan[j % kPlanRing] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt);
     }
     const unsigned parity = static_cast<unsigned>(k / kSweepStages) & 1u;
-    const bool ok = mbar_wait(&bars[s], parity);
+    const bool ok = mbar_wait(&bars[s], parity) && tab_ok;
+    Acc4<R> acc = {R(0), R(0), R(0), R(0)};
     if (ok) {
-      const int L = plan[k % kPlanRing].len, par = plan[k % kPlanRing].par;
+      const SweepPlan& pk = plan[k % kPlanRing];
+      const int L = pk.len;
       const Slot<R>* sring = reinterpret_cast<const Slot<R>*>(sweep_smem + s * SB);
-      const W2<R>* sw = reinterpret_cast<const W2<R>*>(sweep_smem + s * SB + static_cast<size_t>(S) * sizeof(Slot<R>));
+      if constexpr (GEN) {
+        const int j0 = pk.j0, mt = pk.mt, mn = pk.mn, qmax = wtab_pieces - 1;
+        const float dsh = pk.dsh, dsl = pk.dsl;
+        float jf = static_cast<float>(j0 + tid) + 0.5f;  // exact: lags stay below 2^23
 #pragma unroll 4
-      for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
+        for (int i = tid; i < L; i += kSweepThreads, jf += static_cast<float>(kSweepThreads)) {
+          float2 w = gen_weight(stab, qmax, jf, dsh, dsl);
+          const int j = j0 + i;
+          if (j >= mt) w.x = 0.0f;
+          if (j >= mn) w.y = 0.0f;
+          slot_fma(acc, sring[i], w);
+        }
+      } else {
+        const int par = pk.par;
+        const W2<R>* sw =
+            reinterpret_cast<const W2<R>*>(sweep_smem + s * SB + static_cast<size_t>(S) * sizeof(Slot<R>));
+#pragma unroll 4
+        for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
+      }
     }
+    run.tr += static_cast<double>(acc.tr);
+    run.ti += static_cast<double>(acc.ti);
+    run.nr += static_cast<double>(acc.nr);
+    run.ni += static_cast<double>(acc.ni);
     const SweepPlan &pc = plan[k % kPlanRing], &pn = plan[(k + 1) % kPlanRing];
     const bool seg_end = k + 1 == nk || pn.mode != pc.mode || pn.member != pc.member;
     if (seg_end) {
-      Acc4<R> w4;
-      w4.tr = warp_reduce_to_lane0(acc.tr);
-      w4.ti = warp_reduce_to_lane0(acc.ti);
-      w4.nr = warp_reduce_to_lane0(acc.nr);
-      w4.ni = warp_reduce_to_lane0(acc.ni);
+      Acc4<double> w4;
+      w4.tr = warp_reduce_to_lane0(run.tr);
+      w4.ti = warp_reduce_to_lane0(run.ti);
+      w4.nr = warp_reduce_to_lane0(run.nr);
+      w4.ni = warp_reduce_to_lane0(run.ni);
       if (lane == 0) red[k & 1][wid] = w4;
-      acc = {R(0), R(0), R(0), R(0)};
+      run = {0.0, 0.0, 0.0, 0.0};
     }
     stuck = __syncthreads_or(!ok);
     if (stuck) break;
@@ -1129,25 +1224,25 @@ __global__ void __launch_bounds__(kSweepThreads)
         sweep_issue<R, S>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
       double4 out = make_double4(0.0, 0.0, 0.0, 0.0);
       if (seg_end) {
-        Acc4<R> t = red[k & 1][0];
+        Acc4<double> t = red[k & 1][0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) {
-          const Acc4<R> u = red[k & 1][w];
+          const Acc4<double> u = red[k & 1][w];
           t.tr += u.tr;
           t.ti += u.ti;
           t.nr += u.nr;
           t.ni += u.ni;
         }
-        out = make_double4(static_cast<double>(t.tr), static_cast<double>(t.ti), static_cast<double>(t.nr),
-                           static_cast<double>(t.ni));
+        out = make_double4(t.tr, t.ti, t.nr, t.ni);
       }
       partial[c0 + k] = out;
     }
   }
   if (stuck && tid == 0) {
-    atomicOr(f.status, SBIEM_FLAG_WAIT);
+    atomicOr(BATCH ? fs[plan[k % kPlanRing].member].status : f.status, SBIEM_FLAG_WAIT);
     // copies still in flight land in this CTA's shared memory: wait for them
     // (bounded) before the CTA exits
+    if (GEN && !tab_ok) mbar_wait(&tbar, 0u);
     for (int q = k; q < nk && q < k + kSweepStages; ++q)
       mbar_wait(&bars[q % kSweepStages], static_cast<unsigned>(q / kSweepStages) & 1u);
   }
@@ -1962,9 +2057,20 @@ void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_
   k_history_t<R, false><<<gr, kHistThreads, 0, st>>>(f, nullptr, f.chunks, f.nchunks, f.work, m_dt);
 }
 
+// Dynamic shared memory of the sweep: its stages, plus the weight table
+// (gen_pieces pieces of 48 bytes) when the weights are evaluated on chip.
 template <class R, int SH>
-static size_t sweep_smem() {
+static size_t sweep_smem(int gen_pieces = 0) {
+  if (gen_pieces > 0)
+    return SweepCfg<R, SH>::kStages * sweep_stage_bytes<R, SH, true>() + static_cast<size_t>(gen_pieces) * 48;
   return SweepCfg<R, SH>::kStages * sweep_stage_bytes<R, SH>();
+}
+
+// k_sweep<R, SH, BATCH, GEN> with GEN only where R is float.
+template <class R, int SH, bool BATCH, bool GEN>
+static auto sweep_kernel() {
+  if constexpr (GEN && sizeof(R) == 4) return k_sweep<R, SH, BATCH, true>;
+  else return k_sweep<R, SH, BATCH, false>;
 }
 
 // fn(std::integral_constant<int, shape>) for a sweep shape 0..kSweepShapes-1
@@ -1986,10 +2092,15 @@ template <class R>
 static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, int shape, cudaStream_t st) {
   if (f.nchunks == 0) return;
   const int gr = sweep_grid(grid, f.nchunks);
+  const bool gen = sizeof(R) == 4 && f.gen && f.wtab;
   with_shape(shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
-    k_sweep<R, SH, false><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(f, nullptr, f.chunks, f.nchunks,
-                                                                          f.partial, m_dt);
+    if (gen)
+      sweep_kernel<R, SH, false, true>()<<<gr, kSweepThreads, sweep_smem<R, SH>(f.wtab_pieces), st>>>(
+          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, f.wtab, f.wtab_pieces);
+    else
+      k_sweep<R, SH, false, false><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(
+          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, nullptr, 0);
   });
 }
 
@@ -2017,11 +2128,16 @@ void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t
 }
 
 template <class R>
-int sweep_blocks_per_sm(int shape) {
+int sweep_blocks_per_sm(int shape, int gen_pieces) {
   int n = 0;
   with_shape(shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R, SH, false>, kSweepThreads, sweep_smem<R, SH>());
+    if (gen_pieces > 0)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<R, SH, false, true>(), kSweepThreads,
+                                                    sweep_smem<R, SH>(gen_pieces));
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R, SH, false, false>, kSweepThreads,
+                                                    sweep_smem<R, SH>());
   });
   return n;
 }
@@ -2038,13 +2154,18 @@ int sweep_chunk_slots(int precision, int shape) {
 template <class R>
 void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
                           const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
-                          cudaStream_t st, bool ahead) {
+                          cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces) {
   const int G = sweep_grid(grid, nchunks);
   if (nchunks > 0)
     with_shape(shape, [&](auto sh) {
       constexpr int SH = decltype(sh)::value;
       DevFault<R> none{};
-      k_sweep<R, SH, true><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(none, fs, chunks, nchunks, partial, m_dt);
+      if (sizeof(R) == 4 && wtab)
+        sweep_kernel<R, SH, true, true>()<<<G, kSweepThreads, sweep_smem<R, SH>(wtab_pieces), st>>>(
+            none, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces);
+      else
+        k_sweep<R, SH, true, false><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(none, fs, chunks, nchunks,
+                                                                                  partial, m_dt, nullptr, 0);
     });
   k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial, ahead);
 }
@@ -2250,16 +2371,16 @@ void launch_real_part(int N, const double2* z, double* x, cudaStream_t st) {
 
 template <class R>
 void configure_kernels(const FftGeom& g) {
-  allow_smem(k_sweep<R, 0, false>, sweep_smem<R, 0>());
-  allow_smem(k_sweep<R, 1, false>, sweep_smem<R, 1>());
-  allow_smem(k_sweep<R, 2, false>, sweep_smem<R, 2>());
-  allow_smem(k_sweep<R, 3, false>, sweep_smem<R, 3>());
-  allow_smem(k_sweep<R, 4, false>, sweep_smem<R, 4>());
-  allow_smem(k_sweep<R, 0, true>, sweep_smem<R, 0>());
-  allow_smem(k_sweep<R, 1, true>, sweep_smem<R, 1>());
-  allow_smem(k_sweep<R, 2, true>, sweep_smem<R, 2>());
-  allow_smem(k_sweep<R, 3, true>, sweep_smem<R, 3>());
-  allow_smem(k_sweep<R, 4, true>, sweep_smem<R, 4>());
+  for (int sh = 0; sh < kSweepShapes; ++sh)
+    with_shape(sh, [&](auto shc) {
+      constexpr int SH = decltype(shc)::value;
+      allow_smem(k_sweep<R, SH, false, false>, sweep_smem<R, SH>());
+      allow_smem(k_sweep<R, SH, true, false>, sweep_smem<R, SH>());
+      if constexpr (sizeof(R) == 4) {
+        allow_smem(k_sweep<R, SH, false, true>, sweep_smem<R, SH>(1));
+        allow_smem(k_sweep<R, SH, true, true>, sweep_smem<R, SH>(1));
+      }
+    });
   if constexpr (sizeof(R) == 4) {
     if (g.N <= kFusedMaxN)
       with_lgn(g.N, [&](auto lg) {
@@ -2285,9 +2406,9 @@ void configure_kernels(const FftGeom& g) {
 }
 
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
-                                           const int64_t*, int, int, int, cudaStream_t, bool);
+                                           const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int);
 template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
-                                          const int64_t*, int, int, int, cudaStream_t, bool);
+                                          const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
 template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t, int);
@@ -2318,8 +2439,8 @@ template void launch_history_ahead<double>(const DevFault<double>&, int, int, cu
 template void launch_history_ahead<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_history_atomic<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_history_atomic<float>(const DevFault<float>&, int, int, cudaStream_t);
-template int sweep_blocks_per_sm<double>(int);
-template int sweep_blocks_per_sm<float>(int);
+template int sweep_blocks_per_sm<double>(int, int);
+template int sweep_blocks_per_sm<float>(int, int);
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double,
                                      const int32_t*, const int32_t*, cudaStream_t);
 template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double,

@@ -89,6 +89,13 @@ struct DevFault {
   const int32_t *mfirst, *mcount;          // per mode: first chunk, chunks
   int sweep_shape;                         // chunk length x stages of the history sweep (0..3)
   int lag_shape;                           // the same for the sweep beside the passes (0..4)
+  // FP32 sweep with the weights evaluated on chip instead of streamed:
+  // per mode (ds_hi, ds_lo, M^T bits, M^N bits) with ds = c_s k_n dt_min as
+  // a two-float sum, and the piecewise-polynomial table of dt C(s)
+  int gen;                                 // 1: evaluate, 0: stream the materialized weights
+  const float4* wgen;
+  const float4* wtab;                      // kGenPairs / 2 float4 per piece
+  int wtab_pieces;
   // FFT work
   Cx<R> *z, *zt, *Z, *y;                   // natural-order input, transposed, spectrum, output
   const Cx<R>* tw;                         // exp(-2 pi i j/N)
@@ -133,8 +140,9 @@ template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid,
 // The one-warp-per-chunk sweep with atomic chunk hand-out and per-mode
 // last-arriver sums (writes AT/AN itself); used on caller-owned buffers.
 template <class R> void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
-// Resident CTAs per SM of the bulk-async sweep; its chunk length (lags).
-template <class R> int sweep_blocks_per_sm(int shape);
+// Resident CTAs per SM of the bulk-async sweep (with gen_pieces > 0: the
+// on-chip weight form with a table of that many pieces); its chunk length.
+template <class R> int sweep_blocks_per_sm(int shape, int gen_pieces = 0);
 int sweep_chunk_slots(int precision, int shape);
 // The same sweep with the weights shifted by 2 m_dt, chunk partials only:
 // the part of the next step's sums that does not involve this step's
@@ -146,9 +154,12 @@ template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int
 // Ensemble history sums: one bulk-async sweep over the concatenated chunk
 // tables of all members (member in Chunk::pad), then per (member, mode) sums
 // into each member's AT/AN; cbase[r] is member r's first chunk.
+// wtab (FP32 only, or NULL): the members' shared on-chip weight table of
+// wtab_pieces pieces (every member's wgen must then be set).
 template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
                                              double4* partial, const int2* mm, int TM, const int64_t* cbase,
-                                             int shape, int grid, int m_dt, cudaStream_t st, bool ahead);
+                                             int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
+                                             const float4* wtab = nullptr, int wtab_pieces = 0);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);
 template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st,

@@ -214,6 +214,81 @@ void build_cheb(double r, double smax, ChebTable* tab) {
   }
 }
 
+// FP32 table of the midpoint weights dt C(s) for the history sweep to evaluate
+// on chip (the weights depend on the mode only through s = c_s k_n (j + 1/2)
+// dt_min): pieces of width kGenH, on each a degree-kGenDeg polynomial in
+// t = 2 (s - q kGenH) / kGenH - 1 in [-1, 1), interpolating C^T and C^N at the
+// Chebyshev nodes (monomial coefficients from the nodal values by Gaussian
+// elimination in FP64, then scaled by dt and rounded to FP32).  Layout per
+// piece: coefficient pairs (T, N) for k = 0..kGenDeg, kGenDeg + 1 pairs.
+// *max_err: the largest |table - dt C| over 16 points per piece, evaluated
+// in FP64 from the rounded coefficients, over dt max|C|.
+void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, int* npieces, double* max_err) {
+  const int n = kGenDeg + 1;
+  const int P = static_cast<int>(std::ceil(smax / kGenH)) + 1;
+  *npieces = P;
+  tab.assign(static_cast<size_t>(P) * n * 2, 0.0f);
+  std::vector<double> xi(n), vT(n), vN(n), A(n * n), bT(n), bN(n);
+  for (int i = 0; i < n; ++i) xi[i] = std::cos(M_PI * (i + 0.5) / n);
+  double err = 0.0, cmax = 0.0;
+  for (int p = 0; p < P; ++p) {
+    const double a = p * kGenH;
+    for (int i = 0; i < n; ++i) kernel_values(a + 0.5 * kGenH * (xi[i] + 1.0), r, &vT[i], &vN[i]);
+    // Vandermonde system V c = v, V[i][k] = xi_i^k, by elimination with partial pivoting
+    for (int i = 0; i < n; ++i) {
+      double x = 1.0;
+      for (int k = 0; k < n; ++k) {
+        A[i * n + k] = x;
+        x *= xi[i];
+      }
+      bT[i] = vT[i];
+      bN[i] = vN[i];
+    }
+    for (int c = 0; c < n; ++c) {
+      int piv = c;
+      for (int i = c + 1; i < n; ++i)
+        if (std::fabs(A[i * n + c]) > std::fabs(A[piv * n + c])) piv = i;
+      if (piv != c) {
+        for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+        std::swap(bT[c], bT[piv]);
+        std::swap(bN[c], bN[piv]);
+      }
+      for (int i = c + 1; i < n; ++i) {
+        const double f = A[i * n + c] / A[c * n + c];
+        for (int k = c; k < n; ++k) A[i * n + k] -= f * A[c * n + k];
+        bT[i] -= f * bT[c];
+        bN[i] -= f * bN[c];
+      }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+      for (int k = c + 1; k < n; ++k) {
+        bT[c] -= A[c * n + k] * bT[k];
+        bN[c] -= A[c * n + k] * bN[k];
+      }
+      bT[c] /= A[c * n + c];
+      bN[c] /= A[c * n + c];
+    }
+    float* out = &tab[static_cast<size_t>(p) * n * 2];
+    for (int k = 0; k < n; ++k) {
+      out[2 * k] = static_cast<float>(dt * bT[k]);
+      out[2 * k + 1] = static_cast<float>(dt * bN[k]);
+    }
+    for (int q = 0; q < 16; ++q) {
+      const double t = -1.0 + (q + 0.5) / 8.0;
+      double eT = out[2 * kGenDeg], eN = out[2 * kGenDeg + 1];
+      for (int k = kGenDeg - 1; k >= 0; --k) {
+        eT = eT * t + out[2 * k];
+        eN = eN * t + out[2 * k + 1];
+      }
+      double cT, cN;
+      kernel_values(a + 0.5 * kGenH * (t + 1.0), r, &cT, &cN);
+      err = std::max(err, std::max(std::fabs(eT - dt * cT), std::fabs(eN - dt * cN)));
+      cmax = std::max(cmax, std::max(std::fabs(cT), std::fabs(cN)));
+    }
+  }
+  *max_err = cmax > 0.0 ? err / (dt * cmax) : 0.0;
+}
+
 // exp(-2 pi i j / N), j = 0..N-1, via octant symmetry so that every value is
 // a sin/cos of an angle in [0, pi/4].
 void build_twiddles(int64_t N, std::vector<double>& tw) {

@@ -85,6 +85,11 @@ _SIGS = {
     "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
+    "sbiem_get_sweep": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32), _D]),
+    "sbiem_set_sweep": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "sbiem_tune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "sbiem_history_sums_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP,
                                                   _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sbiem_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int64]),
@@ -499,6 +504,25 @@ class Fault:
         m = ctypes.c_int32()
         self._check(self.lib.sbiem_newton_stats(self.h, ctypes.byref(s), ctypes.byref(m)))
         return int(s.value), int(m.value)
+
+    def get_sweep(self) -> dict:
+        """History sweep configuration: shape, on-chip weights, CTAs per SM, weight-table error."""
+        sh, ge, ct = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        err = ctypes.c_double()
+        self._check(self.lib.sbiem_get_sweep(self.h, ctypes.byref(sh), ctypes.byref(ge), ctypes.byref(ct),
+                                             ctypes.byref(err)))
+        return {"shape": sh.value, "generated": bool(ge.value), "ctas_per_sm": ct.value, "table_err": err.value}
+
+    def set_sweep(self, shape: int = 3, generated: bool = True, ctas_per_sm: int = 0) -> None:
+        self._check(self.lib.sbiem_set_sweep(self.h, int(shape), 1 if generated else 0, int(ctas_per_sm)))
+
+    def tune(self, reps: int = 5) -> dict:
+        """Autotune the history sweep (shape, weight form, CTAs per SM); returns the choice and its time."""
+        sh, ge, ct = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ms = ctypes.c_float()
+        self._check(self.lib.sbiem_tune(self.h, int(reps), ctypes.byref(sh), ctypes.byref(ge), ctypes.byref(ct),
+                                        ctypes.byref(ms)))
+        return {"shape": sh.value, "generated": bool(ge.value), "ctas_per_sm": ct.value, "ms": ms.value}
 
     def footprint(self):
         hb = ctypes.c_int64()

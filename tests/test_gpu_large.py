@@ -71,18 +71,50 @@ def test_large_N_steps_match_oracle(N, precision):
     g2.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-6)])
-def test_history_sums_every_mode_at_65536(precision, tol):
-    # the sweep alone on the N = 65536 rings (66 M slots): every mode's sums
+@pytest.mark.parametrize("precision,generated,tol", [(0, False, 1e-10), (1, True, 2e-6), (1, False, 2e-6)])
+def test_history_sums_every_mode_at_65536(precision, generated, tol):
+    # the sweep alone on the N = 65536 rings (66 M slots): every mode's sums,
+    # FP32 with the weights evaluated on chip (the default) and streamed
     w = _workload(65536)
     o = oracle_for(w, workers=WORKERS)
     g = gpu_for(w, precision=precision)
+    sw = g.get_sweep()
+    assert sw["generated"] == (precision == 1)
+    if precision == 1:
+        assert 0 < sw["table_err"] < 2e-7
+    g.set_sweep(3, generated, 0)
     prefill(o, g, seed=17, scale=1e-3)
     for m in (1, 4):
         AT, AN = g.history_sums(m)
         rT, rN = o.history_sums(m)
         assert rel(AT, rT) < tol, (m, rel(AT, rT))
         assert rel(AN, rN) < tol, (m, rel(AN, rN))
+    g.close()
+
+
+def test_autotuner_keeps_results():
+    # the autotuner picks shape, weight form and CTAs per SM by timing; the
+    # sums (and the step) are those of any form up to FP32 rounding
+    w = _workload(16384)
+    o = oracle_for(w, workers=WORKERS)
+    g = gpu_for(w, precision=1)
+    prefill(o, g, seed=19, scale=1e-3)
+    before = g.history_sums(1)
+    choice = g.tune(reps=3)
+    assert choice["shape"] in (3, 4) or choice["shape"] in (0, 1, 2)
+    assert choice["ctas_per_sm"] >= 1 and choice["ms"] > 0
+    sw = g.get_sweep()
+    assert (sw["shape"], sw["generated"], sw["ctas_per_sm"]) == (choice["shape"], choice["generated"],
+                                                               choice["ctas_per_sm"])
+    after = g.history_sums(1)
+    rT, rN = o.history_sums(1)
+    for x, y, r in zip(before, after, (rT, rN)):
+        assert rel(y, x) < 1e-6 and rel(y, r) < 2e-6
+    g.step()
+    assert o.step() == 0
+    s = g.get_state()
+    scale = max(np.abs(o.last["tau_el"]).max(), np.abs(o.last["sig_el"]).max())
+    assert np.abs(s["tau_el"] - o.last["tau_el"]).max() < 1e-4 * scale
     g.close()
 
 
