@@ -84,6 +84,13 @@ typedef struct sbiem_params {
                            over the step (default); 1: explicit
                            theta + thetadot dt as printed in Sec. 3.3          */
   int32_t newton_maxit; /* Newton iteration cap per solve, default 50          */
+  int32_t quadrature;   /* kernel weights of the history and current-interval
+                           integrals: 0 (default) the midpoint rule of Sec.
+                           3.3, w_{n,j} = dt_min C(k_n, (j + 1/2) dt_min);
+                           1 the integral of C(k_n, tau) over each interval
+                           [j dt_min, (j + 1) dt_min] (six-point
+                           Gauss-Legendre); the two differ by O(dt^2).  With
+                           1 the FP32 sweep streams its weights           */
   double  newton_tol;   /* |delta ln V| convergence tolerance, default 1e-12   */
   double  f0, V0;       /* reference friction and slip rate (Eq. momentum)     */
   sbiem_alloc_fn alloc_fn; /* optional device allocator (NULL: cudaMalloc)     */
@@ -180,6 +187,22 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max,
               int64_t* m_hist);
 
 /*
+ * Output of sbiem_run while it runs (the slip history of a cycle, the
+ * rupture front, V_max ...): after every `every`-th accepted step, and after
+ * the last accepted step of the run, the library copies the committed slip
+ * and slip rate to page-locked host buffers it owns and calls
+ *   cb(user, step, t, m, delta, V, N)
+ * with step = accepted steps so far in this run, t = simulated time, m = that
+ * step's length in dt_min; delta and V (N doubles each) are valid during the
+ * call only.  A nonzero return stops the run after that step (sbiem_run then
+ * returns SBIEM_OK with the steps done so far).  cb = NULL removes the
+ * callback.  Errors: SBIEM_ERR_INVALID (every < 1), SBIEM_ERR_NOMEM.
+ */
+typedef int (*sbiem_output_fn)(void* user, int64_t step, double t, int64_t m, const double* delta,
+                               const double* V, int64_t N);
+int sbiem_set_output(sbiem_t s, sbiem_output_fn cb, void* user, int64_t every);
+
+/*
  * sbiem_step_host -- a step driven from host memory: copies tau_load (N
  * doubles, replaces the shear load) host->device, runs one step and copies the
  * new slip rate V (N doubles) device->host.  Either pointer may be NULL.
@@ -222,7 +245,7 @@ int sbiem_set_history_device(sbiem_t s, const void* hist_T, const void* hist_N, 
 int sbiem_get_history(sbiem_t s, double* hist_T, double* hist_N);
 
 /* Checkpoint / restart.  sbiem_save writes to `path` (binary, little endian,
- * this library's own format "SBIEMCK1") the parameters, the per-element
+ * this library's own format "SBIEMCK3") the parameters, the per-element
  * inputs (kappa, a, b, Dc, loads, prescribed mask and rates), the committed
  * state (delta, V, theta), the time, the step count and the history rings;
  * it synchronizes the handle's stream.  sbiem_load creates a new handle from
@@ -442,6 +465,19 @@ int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_
  * SBIEM_ERR_UNSUPPORTED (generated = 1 without a table), SBIEM_ERR_CUDA.
  */
 int sbiem_get_sweep(sbiem_t s, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, double* table_err);
+
+/*
+ * sbiem_set_wait_limit -- polls (mbarrier try_wait calls) the history sweep
+ * makes while it waits for a stage's bulk copy before it gives up (default
+ * SBIEM_WAIT_LIMIT_DEFAULT).  On giving up the sweep sets SBIEM_FLAG_WAIT,
+ * waits at the default limit for every copy it has in flight, and returns;
+ * the step is then rejected (SBIEM_ERR_WAIT, committed state unchanged) and
+ * the CUDA context stays usable.  polls = 0 gives up at the first wait: a
+ * way to exercise that path without any fault.  Synchronizes and rebuilds
+ * the step graphs.  Errors: SBIEM_ERR_INVALID (negative), SBIEM_ERR_CUDA.
+ */
+#define SBIEM_WAIT_LIMIT_DEFAULT 4194304
+int sbiem_set_wait_limit(sbiem_t s, int64_t polls);
 int sbiem_set_sweep(sbiem_t s, int32_t shape, int32_t generated, int32_t ctas_per_sm);
 int sbiem_tune(sbiem_t s, int reps, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, float* ms);
 

@@ -23,7 +23,9 @@ reason, in the design notes of the repository):
   -i sgn(k) under F[f]_n = sum_i f_i exp(-i k_n x_i); it is zero at k = 0 and
   at the Nyquist mode;
 * k_c = 200/(eta L) in rad/m by default; windows M_n = ceil(T_w(k_n)/dt_min);
-* quadrature weights w_{n,j} = dt_min * C(k_n, (j+1/2) dt_min), j = 0..M_n-1;
+* quadrature weights w_{n,j} = dt_min * C(k_n, (j+1/2) dt_min), j = 0..M_n-1
+  (the midpoint rule Sec. 3.3 names); the option ``quadrature="exact"``
+  takes the integral of C(k_n, tau) over [j dt_min, (j+1) dt_min] instead;
 * the state variable follows the aging law integrated exactly at constant
   Vbar over the step (Lapusta et al. 2000); the explicit form of Sec. 3.3
   (theta + thetadot dt) is an option;
@@ -64,6 +66,7 @@ class Params:
     kc_L: float = 200.0           # k_c * (eta * L) (Sec. 3.1)
     kcN_L: float = 0.0            # k_c of the normal-traction kernel, same units; 0: kc_L
     kc_units: str = "rad"         # "rad": k_c in rad/m; "cycles": k_c in cycles/m
+    quadrature: str = "midpoint"  # "midpoint" (Sec. 3.3) or "exact": the integral over each interval
     state_law: str = "analytic"   # "analytic" aging at constant Vbar, or "explicit"
     newton_tol: float = 1e-13
     newton_maxit: int = 200
@@ -166,12 +169,23 @@ def _kernel_pair_all(s: np.ndarray, r: float, workers: int = 1):
     return np.concatenate([a for a, _ in parts]), np.concatenate([b for _, b in parts])
 
 
-def weights(p: Params, M: np.ndarray | None = None, modes=None, workers: int = 1):
-    """Midpoint weights w_{n,j} = dt_min * C(k_n, (j + 1/2) dt_min), j = 0..M_n-1 (Sec. 3.3).
+# Gauss-Legendre rule of the "exact" interval weights: 8 points integrate a
+# kernel oscillating at most at c_p |k| (s/r, r = c_s/c_p) over an interval
+# of at most pi/4 in s to rounding (error term (8!)^4/(17 (16!)^3) (h w/2)^16
+# < 1e-25 relative).
+_IV_X, _IV_W = np.polynomial.legendre.leggauss(8)
 
-    Returns (wT, wN, offsets): flat arrays with mode n occupying
-    [offsets[n], offsets[n+1]).  With two cutting planes a field's weights
-    are zero past its own window M^X_n (the kernel truncated there).
+
+def weights(p: Params, M: np.ndarray | None = None, modes=None, workers: int = 1):
+    """Kernel weights of the history and current-interval sums (Sec. 3.3).
+
+    Midpoint rule (the paper's, default): w_{n,j} = dt_min C(k_n, (j + 1/2) dt_min).
+    quadrature="exact": w_{n,j} = integral of C(k_n, tau) over
+    [j dt_min, (j + 1) dt_min], by the Gauss-Legendre rule _IV_X/_IV_W on
+    the interval in s = c_s |k| tau (d tau = dt_min ds / ds_n).
+    j = 0..M_n-1.  Returns (wT, wN, offsets): flat arrays with mode n
+    occupying [offsets[n], offsets[n+1]).  With two cutting planes a field's
+    weights are zero past its own window M^X_n (the kernel truncated there).
     ``modes`` (optional) restricts the evaluation to those modes: the other
     modes then get empty ranges.  ``workers`` > 1 evaluates the kernels in
     that many processes.
@@ -189,8 +203,17 @@ def weights(p: Params, M: np.ndarray | None = None, modes=None, workers: int = 1
     offsets[1:] = np.cumsum(Mk)
     mode = np.repeat(np.arange(Mk.size), Mk)
     j = np.arange(offsets[-1]) - offsets[mode]
-    s = p.cs * k[mode] * (j + 0.5) * p.dt_min
-    GT, GN = _kernel_pair_all(s, p.r, workers)
+    if p.quadrature == "midpoint":
+        s = p.cs * k[mode] * (j + 0.5) * p.dt_min
+        GT, GN = _kernel_pair_all(s, p.r, workers)
+    elif p.quadrature == "exact":
+        ds = p.cs * k[mode] * p.dt_min                    # interval width in s
+        s = (p.cs * k[mode] * j * p.dt_min)[:, None] + ds[:, None] * 0.5 * (1.0 + _IV_X)[None, :]
+        gT, gN = _kernel_pair_all(s.ravel(), p.r, workers)
+        GT = 0.5 * (gT.reshape(s.shape) @ _IV_W)         # mean of C over the interval
+        GN = 0.5 * (gN.reshape(s.shape) @ _IV_W)
+    else:
+        raise ValueError("quadrature must be 'midpoint' or 'exact'")
     wT, wN = p.dt_min * GT, p.dt_min * GN
     MT, MN = field_windows(p)
     if Mk.size == MT.size:

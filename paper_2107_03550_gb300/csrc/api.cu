@@ -94,6 +94,15 @@ struct sbiem_s {
   int sweep_shape = 0;  // chunk length x stages of the sweep
   int lag_shape = 0;    // the same for the overlapped sweep
   int sweep_ctas = 0;   // resident sweep CTAs per SM asked for (0: as many as fit)
+  long long spin_limit = SBIEM_WAIT_LIMIT_DEFAULT;  // polls of the sweep's consumer waits
+  // output of sbiem_run: callback, its argument, every how many accepted
+  // steps, and page-locked host copies of slip and slip rate
+  sbiem_output_fn out_cb = nullptr;
+  void* out_user = nullptr;
+  int64_t out_every = 0;
+  double* h_out = nullptr;  // 2N
+  // device footprint planned at creation (for the out-of-memory message)
+  int64_t planned_bytes = 0, planned_ring = 0, planned_w = 0;
   int gen_pieces = 0;   // pieces of the on-chip weight table (0: none, weights streamed)
   double gen_err = 0.0; // its largest error relative to dt max|C|
   // timing probe: 4 events per slot; graph event-record nodes are retargeted
@@ -145,6 +154,18 @@ T* alloc_n(sbiem_s* s, size_t n, bool* ok) {
   return ptr;
 }
 
+// SBIEM_ERR_NOMEM with the footprint the handle needs: rings, weights and
+// the element and spectral arrays (planned before the first allocation),
+// and what was allocated before the failure.
+int nomem(const sbiem_s* s, const char* what) {
+  char buf[320];
+  std::snprintf(buf, sizeof(buf),
+                "device allocation failed (%s): the handle needs about %.3f GB (history rings %.3f GB, "
+                "weights %.3f GB); %.3f GB were allocated before the failure",
+                what, s->planned_bytes / 1e9, s->planned_ring / 1e9, s->planned_w / 1e9, s->device_bytes / 1e9);
+  return fail(SBIEM_ERR_NOMEM, buf);
+}
+
 void drop_host_graph(sbiem_s* s) {
   if (s->host_graph.exec) cudaGraphExecDestroy(s->host_graph.exec);
   if (s->host_graph.def) cudaGraphDestroy(s->host_graph.def);
@@ -173,6 +194,7 @@ void free_all(sbiem_s* s) {
     else cudaFree(ptr);
   }
   s->allocs.clear();
+  if (s->h_out) cudaFreeHost(s->h_out);
   if (s->h_status) cudaFreeHost(s->h_status);
   if (s->h_steps) cudaFreeHost(s->h_steps);
   if (s->own) cudaStreamDestroy(s->own);
@@ -255,6 +277,7 @@ void fill_dev(sbiem_s* s, DevFault<R>& f) {
   f.lnV0 = std::log(s->p.V0);
   f.state_law = s->p.state_law;
   f.newton_epw = 32;  // elements per Newton warp: 32 measured fastest on GB300
+  f.spin_limit = s->spin_limit;
   f.newton_maxit = s->p.newton_maxit;
   f.sweep_shape = s->sweep_shape;
   f.lag_shape = s->lag_shape;
@@ -284,7 +307,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   f.zt = alloc_n<Cx<R>>(s, s->N, &ok);
   f.Z = alloc_n<Cx<R>>(s, s->N, &ok);
   f.y = alloc_n<Cx<R>>(s, s->N, &ok);
-  if (!ok) return fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
+  if (!ok) return nomem(s, "history rings / weights");
   if constexpr (sizeof(R) == 4) {
     if (s->N <= kFusedMaxN) {
       // single-CTA spectral pass: FP32 inputs prepared by the multi-SM kernels
@@ -294,7 +317,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
       f.Q2f = alloc_n<float2>(s, s->nmodes, &ok);
     }
   }
-  if (!ok) return fail(SBIEM_ERR_NOMEM, "device allocation failed (FP32 pass buffers)");
+  if (!ok) return nomem(s, "FP32 pass buffers");
   f.g = make_geom(s->N, sizeof(Cx<R>));
   if constexpr (sizeof(R) == 8) f.tw = s->tw64;
   else f.tw = s->tw32;
@@ -477,6 +500,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   if (p.precision != 0 && p.precision != 1) return fail(SBIEM_ERR_INVALID, "precision must be 0 or 1");
   if (p.state_law != 0 && p.state_law != 1) return fail(SBIEM_ERR_INVALID, "state_law must be 0 or 1");
   if (p.kc_units != 0 && p.kc_units != 1) return fail(SBIEM_ERR_INVALID, "kc_units must be 0 or 1");
+  if (p.quadrature != 0 && p.quadrature != 1) return fail(SBIEM_ERR_INVALID, "quadrature must be 0 or 1");
   if ((!h && !kappa) || !a || !b || !Dc || !sigma_load || !V_init || !theta_init)
     return fail(SBIEM_ERR_INVALID, "required input array is NULL");
   if (prescribed && !V_presc) return fail(SBIEM_ERR_INVALID, "prescribed given without V_presc");
@@ -553,6 +577,10 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   }
   s->total_slots = s->ring_off[s->nmodes];
   s->total_w = s->w_off[s->nmodes];
+  s->planned_ring = s->total_slots * (s->fp32() ? 16 : 32);
+  s->planned_w = (s->total_w + 2) * (s->fp32() ? 8 : 16);
+  s->planned_bytes = s->planned_ring + s->planned_w + static_cast<int64_t>(s->chunks.size()) * 56 +
+                     static_cast<int64_t>(N) * 8 * 40 + static_cast<int64_t>(s->nmodes) * 16 * (20 + kPow2Slots);
   if (s->total_slots > (int64_t(1) << 31) || s->Rn[1] > (int64_t(1) << 30)) {
     free_all(s);
     delete s;
@@ -607,9 +635,10 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   f.mfirst = d_mfirst;
   f.mcount = d_mcount;
   if (!ok) {
+    const int rc_nm = nomem(s, "element and spectral arrays");
     free_all(s);
     delete s;
-    return fail(SBIEM_ERR_NOMEM, "device allocation failed");
+    return rc_nm;
   }
   cudaMallocHost(&s->h_status, sizeof(unsigned));
   cudaMallocHost(&s->h_steps, sizeof(long long));
@@ -718,7 +747,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   if (s->fp32()) {
     rc = setup_device<float>(s, s->f32, f);
     if (rc == SBIEM_OK) {
-      launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, d_MT, d_MN, s->stream);
+      launch_weights<float>(s->f32, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, d_MT, d_MN, p.quadrature,
+                            s->stream);
       launch_weight_pow2<float>(s->f32, s->stream);
     }
     // the sweep's on-chip weights: the table of dt C(s) over the s range of
@@ -728,7 +758,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     int gp = 0;
     double gerr = 0.0;
     build_gen_table(r, s->dt_min, smax, gtab, &gp, &gerr);
-    if (rc == SBIEM_OK && static_cast<int64_t>(gp) * 48 <= kGenMaxTableBytes) {
+    if (rc == SBIEM_OK && p.quadrature == 0 && static_cast<int64_t>(gp) * 48 <= kGenMaxTableBytes) {
       std::vector<float4> wg(s->nmodes);
       for (int n = 0; n < s->nmodes; ++n) {
         const double ds = p.cs * (2.0 * M_PI * n / s->L) * s->dt_min;
@@ -744,7 +774,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
       float4* d_wgen = alloc_n<float4>(s, s->nmodes, &ok);
       if (!ok || up(d_wtab, gtab.data(), sizeof(float) * gtab.size()) != cudaSuccess ||
           up(d_wgen, wg.data(), sizeof(float4) * s->nmodes) != cudaSuccess) {
-        rc = fail(SBIEM_ERR_NOMEM, "device allocation failed (weight table)");
+        rc = nomem(s, "weight table");
       } else {
         s->f32.wtab = d_wtab;
         s->f32.wgen = d_wgen;
@@ -763,9 +793,9 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     f.y = alloc_n<double2>(s, N, &ok);
     f.g = make_geom(N, sizeof(double2));
     f.tw = s->tw64;
-    rc = ok ? SBIEM_OK : fail(SBIEM_ERR_NOMEM, "device allocation failed (history rings / weights)");
+    rc = ok ? SBIEM_OK : nomem(s, "history rings / weights");
     if (rc == SBIEM_OK) {
-      launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, d_MT, d_MN, s->stream);
+      launch_weights<double>(f, d_cheb, tab.npieces, tab.deg, tab.h, p.cs, d_MT, d_MN, p.quadrature, s->stream);
       launch_weight_pow2<double>(f, s->stream);
     }
   }
@@ -952,6 +982,38 @@ int sbiem_enqueue(sbiem_t s, double dt, int64_t nsteps) {
   return SBIEM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// After accepted step `accepted` of sbiem_run: the output callback, when one
+// is set and the step is a multiple of its period (or the run's last).
+// *stop is set when the callback asks to stop.
+int run_output(sbiem_s* s, int64_t accepted, double t, int64_t m, bool last, bool* stop) {
+  if (!s->out_cb || accepted == 0) return SBIEM_OK;
+  if (!last && accepted % s->out_every != 0) return SBIEM_OK;
+  const size_t nb = sizeof(double) * s->N;
+  CK(cudaMemcpyAsync(s->h_out, s->f64.delta, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_out + s->N, s->f64.V, nb, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->out_cb(s->out_user, accepted, t, m, s->h_out, s->h_out + s->N, s->N) != 0) *stop = true;
+  return SBIEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbiem_set_output(sbiem_t s, sbiem_output_fn cb, void* user, int64_t every) {
+  if (!s || (cb && every < 1)) return fail(SBIEM_ERR_INVALID, "NULL handle or every < 1");
+  if (cb && !s->h_out && cudaMallocHost(&s->h_out, sizeof(double) * 2 * s->N) != cudaSuccess)
+    return fail(SBIEM_ERR_NOMEM, "page-locked output buffers");
+  s->out_cb = cb;
+  s->out_user = user;
+  s->out_every = cb ? every : 0;
+  return SBIEM_OK;
+}
+
 int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, int64_t max_steps,
               int64_t* steps_out, int64_t* m_next, double* t_out, int64_t* m_hist) {
   if (!s || !(eps0 > 0) || m0 < 1 || m_max < 1 || max_steps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
@@ -998,6 +1060,9 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, i
       ++accepted;
       t += s->dt_min;
       m = std::min<int64_t>(2, m_max);
+      bool stop = false;
+      rc = run_output(s, accepted, t, 1, accepted == max_steps || t >= t_end * (1.0 - 1e-15), &stop);
+      if (rc || stop) break;
       continue;
     }
     const int mi = static_cast<int>(m);
@@ -1034,10 +1099,14 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, i
     if (m_hist) m_hist[accepted] = m;
     ++accepted;
     t += static_cast<double>(m) * s->dt_min;
+    const int64_t m_acc = m;
     int64_t mn = m;
     while (static_cast<double>(mn * 2) <= factor * static_cast<double>(m) && mn < 2 * m) mn *= 2;
     while (mn > 1 && static_cast<double>(mn) > factor * static_cast<double>(m)) mn /= 2;
     m = std::max<int64_t>(1, std::min(mn, m_max));
+    bool stop = false;
+    rc = run_output(s, accepted, t, m_acc, accepted == max_steps || t >= t_end * (1.0 - 1e-15), &stop);
+    if (rc || stop) break;
   }
   CK(cudaMemcpyAsync(&t, f.t, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
@@ -1428,6 +1497,17 @@ int sbiem_footprint(sbiem_t s, int64_t* hist_bytes, int64_t* device_bytes) {
   const int64_t slot = s->fp32() ? 16 : 32, wb = gen ? 0 : (s->fp32() ? 8 : 16);
   if (hist_bytes) *hist_bytes = s->total_slots * (slot + wb);
   if (device_bytes) *device_bytes = s->device_bytes;
+  return SBIEM_OK;
+}
+
+int sbiem_set_wait_limit(sbiem_t s, int64_t polls) {
+  if (!s || polls < 0) return fail(SBIEM_ERR_INVALID, "NULL handle or negative limit");
+  CK(cudaStreamSynchronize(s->stream));
+  s->spin_limit = polls;
+  s->f64.spin_limit = polls;
+  s->f32.spin_limit = polls;
+  drop_graphs(s);
+  s->lag_m = -1;
   return SBIEM_OK;
 }
 
@@ -1947,12 +2027,12 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
 // ------------------------------------------------------------- checkpoints
 namespace {
 
-constexpr char kCkMagic[8] = {'S', 'B', 'I', 'E', 'M', 'C', 'K', '2'};
+constexpr char kCkMagic[8] = {'S', 'B', 'I', 'E', 'M', 'C', 'K', '3'};
 
 struct CkHeader {
   char magic[8];
   int64_t N, total_slots;
-  int32_t precision, state_law, kc_units, newton_maxit;
+  int32_t precision, state_law, kc_units, newton_maxit, quadrature, reserved;
   double dx, mu, cs, cp, beta_min, eta_w, kc_L, newton_tol, f0, V0, kcN_L;
 };
 
@@ -1984,6 +2064,7 @@ int sbiem_save(sbiem_t s, const char* path) {
   hd.state_law = s->p.state_law;
   hd.kc_units = s->p.kc_units;
   hd.newton_maxit = s->p.newton_maxit;
+  hd.quadrature = s->p.quadrature;
   hd.dx = s->p.dx;
   hd.mu = s->p.mu;
   hd.cs = s->p.cs;
@@ -2051,6 +2132,7 @@ int load_checked(FILE* fp, const char* path, CkHeader* hd_out, sbiem_params* p_o
   p.state_law = hd.state_law;
   p.kc_units = hd.kc_units;
   p.newton_maxit = hd.newton_maxit;
+  p.quadrature = hd.quadrature;
   p.dx = hd.dx;
   p.mu = hd.mu;
   p.cs = hd.cs;
@@ -2064,6 +2146,7 @@ int load_checked(FILE* fp, const char* path, CkHeader* hd_out, sbiem_params* p_o
   p.V0 = hd.V0;
   if (!(p.dx > 0) || !(p.cs > 0) || !(p.cp > p.cs) || !(p.beta_min > 0) || !(p.eta_w >= 0) || !(p.kc_L > 0) ||
       !(p.kcN_L >= 0) || (p.precision != 0 && p.precision != 1) || (p.kc_units != 0 && p.kc_units != 1) ||
+      (p.quadrature != 0 && p.quadrature != 1) ||
       !std::isfinite(p.dx * p.cs * p.cp * p.beta_min * p.eta_w * p.kc_L * p.kcN_L))
     return fail(SBIEM_ERR_INVALID, std::string("checkpoint parameters out of range: ") + path);
   // the history size the parameters imply, before any buffer is sized from the file

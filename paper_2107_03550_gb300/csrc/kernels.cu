@@ -934,7 +934,7 @@ template <class R, int SH> struct SweepCfg {
 };
 constexpr int kSweepShapes = 5;
 constexpr int kSweepThreads = 128;
-constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls before a wait is declared stuck
+constexpr long long kSpinLimit = SBIEM_WAIT_LIMIT_DEFAULT;  // try_wait polls before a wait is declared stuck
 
 // A stage holds a chunk's ring slots and, unless the weights are evaluated
 // on chip (GEN), its weight run.
@@ -998,9 +998,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for phase `parity` of bar; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (long long k = 0; k < kSpinLimit; ++k)
+// Bounded wait for phase `parity` of bar: at most `limit` polls; false when
+// the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = kSpinLimit) {
+  for (long long k = 0; k < limit; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1011,6 +1012,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+
+// s + c += a with the rounding error of the addition carried in c (Knuth's
+// TwoSum; FP32 only -- an FP64 sum needs no compensation here).
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float a) {
+  const float t = s + a;
+  const float bb = t - s;
+  c += (s - (t - bb)) + (a - bb);
+  s = t;
+}
+__device__ __forceinline__ void two_sum_add(double& s, double& /*c*/, double a) { s += a; }
 
 // Fixed-order tree sum of a warp's values, valid in lane 0.  Only the lanes
 // that keep a partial sum add (lane < o), so the FP64 pipe (scarce on GB300)
@@ -1121,7 +1132,7 @@ __global__ void __launch_bounds__(kSweepThreads)
   __shared__ __align__(8) uint64_t bars[kSweepStages];
   __shared__ __align__(8) uint64_t tbar;
   __shared__ SweepPlan plan[kPlanRing];
-  __shared__ Acc4<double> red[2][NW];
+  __shared__ Acc4<R> red[2][NW];
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // the per-mode finish may be resident already, waiting for this grid
@@ -1155,16 +1166,19 @@ __global__ void __launch_bounds__(kSweepThreads)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
       sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
   }
+  // the consumer waits take the handle's limit (sbiem_set_wait_limit); the
+  // drain below always waits at the full limit, so no copy is left in flight
+  const long long lim = BATCH ? kSpinLimit : f.spin_limit;
   bool tab_ok = true;
-  if (GEN) tab_ok = mbar_wait(&tbar, 0u);
-  // each thread accumulates a chunk in R and folds it into an FP64 sum over
-  // the consecutive chunks of one mode (a run may hold hundreds of chunks,
-  // too many products for one FP32 sum); the CTA reduces at the end of the
-  // mode's run (a segment) and writes the sum at the segment's last chunk,
-  // zeros at the others
+  if (GEN) tab_ok = mbar_wait(&tbar, 0u, lim);
+  // each thread accumulates a chunk in R and folds it into a compensated sum
+  // over the consecutive chunks of one mode (a run may hold hundreds of
+  // chunks: one plain FP32 sum of its thousands of products lost 5e-6); the
+  // CTA reduces at the end of the mode's run (a segment) and writes the sum
+  // at the segment's last chunk, zeros at the others
   bool stuck = false;
   int k = 0;
-  Acc4<double> run = {0.0, 0.0, 0.0, 0.0};
+  Acc4<R> run = {R(0), R(0), R(0), R(0)}, cmp = {R(0), R(0), R(0), R(0)};
   for (; k < nk; ++k) {
     const int s = k % kSweepStages;
     // every kPlanRing/2 chunks: plans of the half-ring ahead (chunks
@@ -1175,7 +1189,7 @@ __global__ void __launch_bounds__(kSweepThreads)
         plan[j % kPlanRing] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt);
     }
     const unsigned parity = static_cast<unsigned>(k / kSweepStages) & 1u;
-    const bool ok = mbar_wait(&bars[s], parity) && tab_ok;
+    const bool ok = mbar_wait(&bars[s], parity, lim) && tab_ok;
     Acc4<R> acc = {R(0), R(0), R(0), R(0)};
     if (ok) {
       const SweepPlan& pk = plan[k % kPlanRing];
@@ -1201,20 +1215,21 @@ __global__ void __launch_bounds__(kSweepThreads)
         for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
       }
     }
-    run.tr += static_cast<double>(acc.tr);
-    run.ti += static_cast<double>(acc.ti);
-    run.nr += static_cast<double>(acc.nr);
-    run.ni += static_cast<double>(acc.ni);
+    two_sum_add(run.tr, cmp.tr, acc.tr);
+    two_sum_add(run.ti, cmp.ti, acc.ti);
+    two_sum_add(run.nr, cmp.nr, acc.nr);
+    two_sum_add(run.ni, cmp.ni, acc.ni);
     const SweepPlan &pc = plan[k % kPlanRing], &pn = plan[(k + 1) % kPlanRing];
     const bool seg_end = k + 1 == nk || pn.mode != pc.mode || pn.member != pc.member;
     if (seg_end) {
-      Acc4<double> w4;
-      w4.tr = warp_reduce_to_lane0(run.tr);
-      w4.ti = warp_reduce_to_lane0(run.ti);
-      w4.nr = warp_reduce_to_lane0(run.nr);
-      w4.ni = warp_reduce_to_lane0(run.ni);
+      Acc4<R> w4;
+      w4.tr = warp_reduce_to_lane0(run.tr + cmp.tr);
+      w4.ti = warp_reduce_to_lane0(run.ti + cmp.ti);
+      w4.nr = warp_reduce_to_lane0(run.nr + cmp.nr);
+      w4.ni = warp_reduce_to_lane0(run.ni + cmp.ni);
       if (lane == 0) red[k & 1][wid] = w4;
-      run = {0.0, 0.0, 0.0, 0.0};
+      run = {R(0), R(0), R(0), R(0)};
+      cmp = {R(0), R(0), R(0), R(0)};
     }
     stuck = __syncthreads_or(!ok);
     if (stuck) break;
@@ -1224,16 +1239,17 @@ __global__ void __launch_bounds__(kSweepThreads)
         sweep_issue<R, S>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
       double4 out = make_double4(0.0, 0.0, 0.0, 0.0);
       if (seg_end) {
-        Acc4<double> t = red[k & 1][0];
+        Acc4<R> t = red[k & 1][0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) {
-          const Acc4<double> u = red[k & 1][w];
+          const Acc4<R> u = red[k & 1][w];
           t.tr += u.tr;
           t.ti += u.ti;
           t.nr += u.nr;
           t.ni += u.ni;
         }
-        out = make_double4(t.tr, t.ti, t.nr, t.ni);
+        out = make_double4(static_cast<double>(t.tr), static_cast<double>(t.ti), static_cast<double>(t.nr),
+                           static_cast<double>(t.ni));
       }
       partial[c0 + k] = out;
     }
@@ -1817,37 +1833,66 @@ __global__ void k_maxdiff(const double* a, const double* b, int n, double* out) 
 }
 
 // ------------------------------------------------------------- weights
-// w_{n,j} = dt_min C(k_n, (j + 1/2) dt_min): midpoint rule (Sec. 3.3),
-// kernels from the piecewise Chebyshev table (Clenshaw recurrence).
+// (C^T(s), C^N(s)) from the piecewise Chebyshev table (Clenshaw recurrence).
+__device__ __forceinline__ double2 cheb_kernels(const double* __restrict__ cheb, int npieces, int deg, double h,
+                                                double s) {
+  int p = static_cast<int>(s / h);
+  p = min(p, npieces - 1);
+  const double t = 2.0 * (s - p * h) / h - 1.0;
+  const double* c = cheb + static_cast<size_t>(p) * (deg + 1) * 2;
+  double bT1 = 0.0, bT2 = 0.0, bN1 = 0.0, bN2 = 0.0;
+  for (int kk = deg; kk >= 1; --kk) {
+    const double tT = 2.0 * t * bT1 - bT2 + c[2 * kk];
+    const double tN = 2.0 * t * bN1 - bN2 + c[2 * kk + 1];
+    bT2 = bT1;
+    bT1 = tT;
+    bN2 = bN1;
+    bN1 = tN;
+  }
+  return make_double2(t * bT1 - bT2 + c[0], t * bN1 - bN2 + c[1]);
+}
+
+// Six-point Gauss-Legendre rule on [-1, 1] (nodes +-x, weights w): the
+// interval weights of the exact quadrature option.  An interval spans at
+// most pi/4 in s and the kernels oscillate at most at 1/r in s, so the
+// rule's error term (6!)^4 / (13 (12!)^3) (h w / 2)^12 stays below 1e-17.
+__constant__ double kGL6x[3] = {0.2386191860831969086305017, 0.6612093864662645136613996,
+                                0.9324695142031520278123016};
+__constant__ double kGL6w[3] = {0.4679139345726910473898703, 0.3607615730481386075698335,
+                                0.1713244923791703450402961};
+
+// Weights of lag j of mode n: quadrature 0 (midpoint rule, Sec. 3.3):
+// w_{n,j} = dt_min C(k_n, (j + 1/2) dt_min); quadrature 1: the integral of
+// C(k_n, tau) over [j dt_min, (j + 1) dt_min] (six-point Gauss-Legendre on
+// the interval).  MT, MN (may be NULL): the shear and normal kernels' own
+// windows when they are cut at two planes (Sec. 3.1); a field's weights are
+// zero past its own.
 template <class R>
-// MT, MN (may be NULL): the shear and normal kernels' own windows when they
-// are cut at two planes (Sec. 3.1); a field's weights are zero past its own.
 __global__ void k_weights(W2<R>* w, const int64_t* w_off, const int32_t* Mn, int nmodes, double L,
                           double cs, double dt, const double* __restrict__ cheb, int npieces, int deg,
-                          double h, const int32_t* MT, const int32_t* MN) {
+                          double h, const int32_t* MT, const int32_t* MN, int quadrature) {
   const int n = blockIdx.x;
   if (n == 0 || n >= nmodes) return;
   const double k = kTwoPi * n / L;
+  const double ds = cs * k * dt;
   const int M = Mn[n];
   const int MTn = MT ? MT[n] : M, MNn = MN ? MN[n] : M;
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
-    const double s = cs * k * (j + 0.5) * dt;
-    int p = static_cast<int>(s / h);
-    p = min(p, npieces - 1);
-    const double t = 2.0 * (s - p * h) / h - 1.0;
-    const double* c = cheb + static_cast<size_t>(p) * (deg + 1) * 2;
-    double bT1 = 0.0, bT2 = 0.0, bN1 = 0.0, bN2 = 0.0;
-    for (int kk = deg; kk >= 1; --kk) {
-      const double tT = 2.0 * t * bT1 - bT2 + c[2 * kk];
-      const double tN = 2.0 * t * bN1 - bN2 + c[2 * kk + 1];
-      bT2 = bT1;
-      bT1 = tT;
-      bN2 = bN1;
-      bN1 = tN;
+    double2 c;
+    if (quadrature == 0) {
+      c = cheb_kernels(cheb, npieces, deg, h, ds * (j + 0.5));
+    } else {
+      c = make_double2(0.0, 0.0);
+      for (int q = 0; q < 3; ++q) {
+        const double2 a = cheb_kernels(cheb, npieces, deg, h, ds * (j + 0.5 * (1.0 - kGL6x[q])));
+        const double2 b = cheb_kernels(cheb, npieces, deg, h, ds * (j + 0.5 * (1.0 + kGL6x[q])));
+        c.x += 0.5 * kGL6w[q] * (a.x + b.x);
+        c.y += 0.5 * kGL6w[q] * (a.y + b.y);
+      }
     }
     W2<R> out;
-    out.x = j < MTn ? static_cast<R>(dt * (t * bT1 - bT2 + c[0])) : R(0);
-    out.y = j < MNn ? static_cast<R>(dt * (t * bN1 - bN2 + c[1])) : R(0);
+    out.x = j < MTn ? static_cast<R>(dt * c.x) : R(0);
+    out.y = j < MNn ? static_cast<R>(dt * c.y) : R(0);
     w[w_off[n] + j] = out;
   }
 }
@@ -2336,9 +2381,9 @@ void launch_commit(const DevFault<R>& f, int m_dt, cudaStream_t st, int lag_p) {
 
 template <class R>
 void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg, double h, double cs,
-                    const int32_t* MT, const int32_t* MN, cudaStream_t st) {
+                    const int32_t* MT, const int32_t* MN, int quadrature, cudaStream_t st) {
   k_weights<R><<<f.nmodes, 256, 0, st>>>(f.w, f.w_off, f.Mn, f.nmodes, f.L, cs, f.dt_min, cheb, npieces, deg, h,
-                                         MT, MN);
+                                         MT, MN, quadrature);
 }
 
 void launch_fft64(const FftGeom& g, const double2* tw, const double2* in, double2* tmp, double2* out,
@@ -2442,8 +2487,8 @@ template void launch_history_atomic<float>(const DevFault<float>&, int, int, cud
 template int sweep_blocks_per_sm<double>(int, int);
 template int sweep_blocks_per_sm<float>(int, int);
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double,
-                                     const int32_t*, const int32_t*, cudaStream_t);
+                                     const int32_t*, const int32_t*, int, cudaStream_t);
 template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double,
-                                    const int32_t*, const int32_t*, cudaStream_t);
+                                    const int32_t*, const int32_t*, int, cudaStream_t);
 
 }  // namespace sbiem

@@ -92,6 +92,7 @@ struct DevFault {
   // FP32 sweep with the weights evaluated on chip instead of streamed:
   // per mode (ds_hi, ds_lo, M^T bits, M^N bits) with ds = c_s k_n dt_min as
   // a two-float sum, and the piecewise-polynomial table of dt C(s)
+  long long spin_limit;                    // polls of the sweep's consumer waits before it gives up
   int gen;                                 // 1: evaluate, 0: stream the materialized weights
   const float4* wgen;
   const float4* wtab;                      // kGenPairs / 2 float4 per piece
@@ -191,9 +192,11 @@ template <class R> void launch_set_ring(Slot<R>* ring, const void* hT, const voi
                                         int sm_count, cudaStream_t st);
 // *out = max_i |a_i - b_i|.
 void launch_maxdiff(const double* a, const double* b, int n, double* out, cudaStream_t st);
+// Weights of every lag from the Chebyshev table: quadrature 0 midpoint,
+// 1 the integral over each interval.
 template <class R> void launch_weights(const DevFault<R>& f, const double* cheb, int npieces, int deg,
                                        double h, double cs, const int32_t* MT, const int32_t* MN,
-                                       cudaStream_t st);
+                                       int quadrature, cudaStream_t st);
 
 // FP64 utility transforms on caller buffers of length N (natural order):
 // forward: Z = sum_i z_i exp(-2 pi i n i/N); inverse: z = (1/N) sum_n Z_n exp(+...).

@@ -15,16 +15,18 @@ import os
 import numpy as np
 
 __all__ = ["Fault", "Batch", "SbiemError", "mlp_predict", "mlp_grad", "mlp_train", "kernel_values", "history_sums_noalloc", "load_library", "library_path", "FLAG_NEWTON", "FLAG_OPENING",
-           "FLAG_STATE", "ERR"]
+           "FLAG_STATE", "FLAG_WAIT", "ERR"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
-FLAG_NEWTON, FLAG_OPENING, FLAG_STATE = 1, 2, 4
+FLAG_NEWTON, FLAG_OPENING, FLAG_STATE, FLAG_WAIT = 1, 2, 4, 8
 ERR = {0: "OK", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -4: "NEWTON", -5: "OPENING", -6: "STATE",
        -7: "DTMIN", -8: "UNSUPPORTED", -9: "WAIT"}
 
 _alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_output_t = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64,
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_int64)
 _free_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
@@ -34,7 +36,7 @@ class Params(ctypes.Structure):
                 ("eta_w", ctypes.c_double), ("kc_L", ctypes.c_double), ("kcN_L", ctypes.c_double),
                 ("kc_units", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("state_law", ctypes.c_int32),
-                ("newton_maxit", ctypes.c_int32), ("newton_tol", ctypes.c_double),
+                ("newton_maxit", ctypes.c_int32), ("quadrature", ctypes.c_int32), ("newton_tol", ctypes.c_double),
                 ("f0", ctypes.c_double), ("V0", ctypes.c_double),
                 ("alloc_fn", _alloc_t), ("free_fn", _free_t), ("alloc_user", ctypes.c_void_p)]
 
@@ -88,6 +90,8 @@ _SIGS = {
     "sbiem_get_sweep": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32), _D]),
     "sbiem_set_sweep": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "sbiem_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "sbiem_set_output": (ctypes.c_int, [_VP, _output_t, _VP, ctypes.c_int64]),
     "sbiem_tune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "sbiem_history_sums_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP,
@@ -272,7 +276,8 @@ class Fault:
     def __init__(self, N, dx, mu, cs, cp, f0, V0, a, b, Dc, sigma_load, V_init, theta_init,
                  kappa=None, h=None, tau_load=None, tau_load_rate=None, prescribed=None,
                  V_presc=None, beta_min=0.25, eta_w=1.0, kc_L=200.0, kcN_L=0.0, kc_units=0, precision=0,
-                 state_law=0, newton_maxit=50, newton_tol=1e-12, use_torch=True, lib=None):
+                 state_law=0, newton_maxit=50, newton_tol=1e-12, quadrature=0, use_torch=True, allocator=None,
+                 lib=None):
         self.lib = lib or load_library()
         self.N = int(N)
         p = Params()
@@ -281,7 +286,13 @@ class Fault:
         p.beta_min, p.eta_w, p.kc_L, p.kcN_L, p.kc_units = beta_min, eta_w, kc_L, kcN_L, kc_units
         p.precision, p.state_law = precision, state_law
         p.newton_maxit, p.newton_tol, p.f0, p.V0 = newton_maxit, newton_tol, f0, V0
-        self._cb = _torch_allocator() if use_torch else None
+        p.quadrature = quadrature
+        if allocator is not None:
+            # caller's device memory: alloc(nbytes) -> device pointer or 0, free(ptr)
+            a_fn, f_fn = allocator
+            self._cb = (_alloc_t(lambda n, _u: a_fn(int(n)) or None), _free_t(lambda q, _u: f_fn(q)))
+        else:
+            self._cb = _torch_allocator() if use_torch else None
         if self._cb is not None:
             p.alloc_fn, p.free_fn = self._cb
         self.params = p
@@ -397,6 +408,24 @@ class Fault:
         if rc not in (0, -7):
             self._check(rc)
         return hist[:n.value].tolist(), int(mn.value), float(t.value), int(rc)
+
+    def set_output(self, fn, every: int = 1) -> None:
+        """Call fn(step, t, m, delta, V) during :meth:`run` after every `every`-th accepted step and the
+        last (delta, V: numpy copies); fn returning True stops the run.  fn=None removes it."""
+        if fn is None:
+            self._out = None
+            self._check(self.lib.sbiem_set_output(self.h, _output_t(), None, 0))
+            return
+        n = self.N
+
+        def _cb(_user, step, t, m, d, v, _n):
+            try:
+                return 1 if fn(int(step), float(t), int(m), np.ctypeslib.as_array(d, (n,)).copy(),
+                               np.ctypeslib.as_array(v, (n,)).copy()) else 0
+            except Exception:       # an exception cannot cross the C ABI: stop the run
+                return 1
+        self._out = _output_t(_cb)  # kept alive with the handle
+        self._check(self.lib.sbiem_set_output(self.h, self._out, None, int(every)))
 
     def step_host(self, dt=None, tau_load=None, V_out=None) -> None:
         ta, tp = _ptr(tau_load, np.float64, self.N)
@@ -515,6 +544,10 @@ class Fault:
 
     def set_sweep(self, shape: int = 3, generated: bool = True, ctas_per_sm: int = 0) -> None:
         self._check(self.lib.sbiem_set_sweep(self.h, int(shape), 1 if generated else 0, int(ctas_per_sm)))
+
+    def set_wait_limit(self, polls: int = 4194304) -> None:
+        """Polls of the history sweep's copy waits before it gives up (0: at once)."""
+        self._check(self.lib.sbiem_set_wait_limit(self.h, int(polls)))
 
     def tune(self, reps: int = 5) -> dict:
         """Autotune the history sweep (shape, weight form, CTAs per SM); returns the choice and its time."""

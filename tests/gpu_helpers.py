@@ -9,7 +9,8 @@ from paper_2107_03550_gb300.workloads import Workload, random_history
 def oracle_for(w: Workload, **kw) -> Oracle:
     p = Params(N=w.N, dx=w.dx, mu=w.mu, cs=w.cs, cp=w.cp, dt_min=w.dt_min,
                state_law=kw.pop("state_law", "analytic"), kc_L=kw.pop("kc_L", 200.0),
-               kc_units=kw.pop("kc_units", "rad"), eta_w=kw.pop("eta_w", 1.0), kcN_L=kw.pop("kcN_L", 0.0))
+               kc_units=kw.pop("kc_units", "rad"), eta_w=kw.pop("eta_w", 1.0), kcN_L=kw.pop("kcN_L", 0.0),
+               quadrature=kw.pop("quadrature", "midpoint"))
     return Oracle(p, w.kappa, w.a, w.b, w.Dc, w.f0, w.V0, w.sigma_load, w.tau_load, w.V_init,
                   w.theta_init, tau_load_rate=w.tau_load_rate,
                   prescribed=w.prescribed if np.any(w.prescribed) else None,

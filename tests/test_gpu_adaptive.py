@@ -98,3 +98,35 @@ def test_adaptive_run_rejects_and_recovers():
     err = compare(o, g, fields=("delta", "V", "theta"))
     assert err["delta"] < 1e-9, err
     g.close()
+
+
+def test_run_output_callback_samples_and_stops():
+    # the output callback of sbiem_run: called after every 4th accepted step
+    # and the last one, with the committed slip and slip rate of that step;
+    # a True return stops the run after that step
+    w = seamount_rupture(N=256)
+    g = gpu_for(w)
+    calls = []
+
+    def out(step, t, m, delta, V):
+        calls.append((step, t, m, delta, V))
+        return False
+
+    g.set_output(out, every=4)
+    hist, m_next, t, rc = g.run(t_end=1e9, eps0=1e-6, m0=1, max_steps=18)
+    assert rc == 0 and len(hist) == 18
+    assert [c[0] for c in calls] == [4, 8, 12, 16, 18]
+    assert [c[2] for c in calls] == [hist[k - 1] for k in (4, 8, 12, 16, 18)]
+    s = g.get_state()
+    assert np.array_equal(calls[-1][3], s["delta"]) and np.array_equal(calls[-1][4], s["V"])
+    assert calls[-1][1] == pytest.approx(s["t"], rel=1e-14)
+    g.close()
+    # stopping: the run ends after the step whose callback returned True
+    g = gpu_for(w)
+    g.set_output(lambda step, t, m, d, V: step >= 7, every=1)
+    hist, _, _, rc = g.run(t_end=1e9, eps0=1e-6, m0=1, max_steps=50)
+    assert rc == 0 and len(hist) == 7
+    g.set_output(None)
+    hist, _, _, rc = g.run(t_end=1e9, eps0=1e-6, m0=1, max_steps=3)
+    assert rc == 0 and len(hist) == 3
+    g.close()

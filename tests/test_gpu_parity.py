@@ -235,6 +235,43 @@ def test_flat_fault_and_uniform_slip_rate():
     g2.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bounded_sweep_wait_rejects_the_step_and_recovers(precision):
+    # A copy wait of the history sweep that runs past its poll limit: with a
+    # limit of zero polls the sweep gives up at its first wait (no fault is
+    # involved), flags the wait, drains the copies it has in flight and
+    # returns; the step is rejected with the state unchanged, and with the
+    # default limit back the handle steps exactly like an untouched one.
+    from paper_2107_03550_gb300.sbiem import FLAG_WAIT, SbiemError
+    w = seamount_rupture(N=256)
+    g, ref = gpu_for(w, precision=precision), gpu_for(w, precision=precision)
+    prefill_random(g, seed=31)
+    prefill_random(ref, seed=31)
+    g.set_wait_limit(0)
+    before = g.get_state()
+    with pytest.raises(SbiemError) as ei:
+        g.step()
+    assert ei.value.code == -9
+    g.enqueue(3)                      # the graph path: every step a no-op after the flag
+    flags, done = g.status(clear=True)
+    assert flags & FLAG_WAIT and done == 0
+    after = g.get_state()
+    for k in ("delta", "V", "theta"):
+        assert np.array_equal(before[k], after[k]), k
+    g.set_wait_limit()
+    for _ in range(3):
+        g.step()
+        ref.step()
+    g.enqueue(5)
+    ref.enqueue(5)
+    assert g.status()[0] == 0 and ref.status()[0] == 0
+    s1, s2 = g.get_state(), ref.get_state()
+    for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+        assert np.array_equal(s1[k], s2[k]), k
+    g.close()
+    ref.close()
+
+
 def test_failures_leave_state_unchanged():
     from paper_2107_03550_gb300.sbiem import SbiemError
     # Newton cap of one iteration cannot converge from the nucleation state
@@ -490,3 +527,60 @@ def test_step_host_pinned_graph_matches_enqueue(precision):
         assert np.array_equal(a[k], b[k]), k
     g.close()
     ref.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exact_interval_quadrature_matches_oracle(precision):
+    # quadrature = 1: every weight the integral of C over its interval (the
+    # option beside the midpoint rule of Sec. 3.3); the FP32 form then
+    # streams its weights.  Seamount rupture with a full random history.
+    w = seamount_rupture(N=256)
+    o = oracle_for(w, quadrature="exact")
+    g = gpu_for(w, precision=precision, quadrature=1)
+    g_mid = gpu_for(w, precision=precision)
+    assert g.get_sweep()["generated"] is False
+    HT, HN = prefill(o, g, seed=41, scale=1e-6)
+    g_mid.set_history(HT, HN)
+    for s in range(200):
+        assert o.step() == 0
+        g.step()
+        g_mid.step()
+    err = compare(o, g)
+    if precision == 0:
+        for k in ("delta", "tau_el", "sigma_el", "theta"):
+            assert err[k] < TOL64, (k, err)
+        assert err["V"] < 1e-9, err
+    else:
+        for k in ("delta", "V", "theta"):
+            assert err[k] < 1e-4, (k, err)
+    # the two rules differ, by O(dt^2) of the kernels' second derivative
+    d = rel(g_mid.get_state()["tau_el"], g.get_state()["tau_el"])
+    assert 0 < d < 1e-2
+    g.close()
+    g_mid.close()
+
+
+def test_out_of_memory_reports_the_footprint():
+    # a caller's allocator that refuses anything above 1 MB: creation fails
+    # with SBIEM_ERR_NOMEM and the message states what the handle needs
+    import torch
+    from paper_2107_03550_gb300.sbiem import Fault, SbiemError
+    held = {}
+
+    def alloc(n):
+        if n > (1 << 20):
+            return 0
+        t = torch.empty(n, dtype=torch.uint8, device="cuda")
+        held[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(ptr):
+        held.pop(ptr, None)
+
+    w = rough_cycle(N=4096)
+    with pytest.raises(SbiemError) as ei:
+        Fault.from_workload(w, precision=1, allocator=(alloc, free))
+    assert ei.value.code == -2
+    msg = str(ei.value)
+    assert "needs about" in msg and "history rings 0.04" in msg, msg
+    assert not held            # everything allocated before the failure was freed

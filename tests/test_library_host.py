@@ -124,7 +124,7 @@ def test_truncation_parameters_are_validated_before_any_device_work(lib):
 
 def _write_checkpoint(path, N, heads=None, total_slots=None, head_delta=None):
     """A checkpoint file in the library's format, written by hand (no GPU):
-    header (magic, N, total_slots, four int32, eleven doubles), 14 element
+    header (magic, N, total_slots, six int32, eleven doubles), 14 element
     arrays, the prescribed mask, F[delta] and F[kappa delta], the ring heads,
     the FP64 ring (32 bytes per slot), the time and the step count."""
     import struct
@@ -134,7 +134,7 @@ def _write_checkpoint(path, N, heads=None, total_slots=None, head_delta=None):
     p = Params(N=N, dx=dx, mu=mu, cs=cs, cp=cp, dt_min=0.25 * dx / cs)
     R = np.maximum(windows(p) - 1, 0)
     slots = int(R.sum()) if total_slots is None else total_slots
-    hd = b"SBIEMCK2" + struct.pack("<qq4i11d", N, slots, 0, 0, 0, 50, dx, mu, cs, cp, 0.25, 1.0, 200.0,
+    hd = b"SBIEMCK3" + struct.pack("<qq6i11d", N, slots, 0, 0, 0, 50, 0, 0, dx, mu, cs, cp, 0.25, 1.0, 200.0,
                                    1e-12, 0.6, 1e-6, 0.0)
     el = np.ones(14 * N)
     h = np.zeros(R.size, dtype=np.int32) if heads is None else np.asarray(heads, np.int32)

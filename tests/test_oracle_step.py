@@ -453,3 +453,66 @@ def test_weight_evaluation_schedule_changes_no_value():
         sAT, sAN = history_sums_sampled(p, modes, [HT[hoff[n]:hoff[n + 1]] for n in modes],
                                         [HN[hoff[n]:hoff[n + 1]] for n in modes], m)
         assert np.array_equal(sAT, AT[modes]) and np.array_equal(sAN, AN[modes])
+
+
+def _primitives(s, r):
+    """Antiderivatives P_T, P_N of the kernels in s (P(0) = 0), written here in
+    closed form from int W = x W - J0, int x^2 W = x^3 W / 3 + x^2 J2 / 3,
+    int J1 = -J0, int x J0 = x J1 (W' = -J1/x), term by term over the
+    kernels of Eq. Ct and Sec. 2.4; the P-wave terms in x = s/r."""
+    from scipy import special
+    from oracle.kernels import W
+    s = np.asarray(s, dtype=np.float64)
+    x = s / r
+    J0s, J1s, J0x, J1x = special.j0(s), special.j1(s), special.j0(x), special.j1(x)
+    J2s, J2x = special.jv(2, s), special.jv(2, x)
+    Ws, Wx = W(s), W(x)
+    r2, r3 = r * r, r ** 3
+    A = (1.0 / r2 - 2.0) ** 2 * r2 / 2.0
+    x2W = lambda z, Wz, J2z: z ** 3 * Wz / 3.0 + z * z * J2z / 3.0   # int z^2 W dz
+    xW = lambda z, Wz, J0z: z * Wz - J0z                               # int W dz
+    FT = (r3 * x2W(x, Wx, J2x) + r3 * xW(x, Wx, J0x) - x2W(s, Ws, J2s) - xW(s, Ws, J0s)
+          + r3 * J0x - 0.5 * J0s - r3 * x * J1x + s * J1s)
+    FN = ((A - r2) * r * xW(x, Wx, J0x) - r3 * x2W(x, Wx, J2x) + (1.0 - 1.0 / (2.0 * r2)) * xW(s, Ws, J0s)
+          + x2W(s, Ws, J2s) - (r2 - A) * r * J0x - (1.0 / (2.0 * r2) - 1.0) * J0s + r3 * x * J1x - s * J1s)
+    return FT - 0.5, FN
+
+
+def test_exact_interval_weights():
+    # quadrature="exact": each weight is the integral of C over its interval.
+    # (i) the closed-form primitives are antiderivatives of the kernels and
+    #     vanish at 0; (ii) the running sums of the exact weights equal the
+    #     primitive at the interval ends (a mode whose window ends at s = 31);
+    # (iii) exact minus midpoint is dt ds^2 C''(s_mid)/24 to leading order:
+    #     the O(dt^2) difference of the two rules.
+    from oracle.sbiem import weights
+    r = 1.0 / np.sqrt(3.0)
+    PT0, PN0 = _primitives(np.array([0.0]), r)
+    assert abs(PT0[0]) < 1e-15 and abs(PN0[0]) < 1e-15
+    for s0 in (0.3, 2.7, 11.0, 25.0):
+        h = 1e-4
+        pT, pN = _primitives(np.array([s0 - h, s0 + h]), r)
+        assert abs((pT[1] - pT[0]) / (2 * h) - G_T(s0, r)) < 1e-7
+        assert abs((pN[1] - pN[0]) / (2 * h) - G_N(s0, r)) < 1e-7
+    p = _params(N=64, dx=25.0)
+    pe = Params(**{**p.__dict__, "quadrature": "exact"})
+    wT, wN, off = weights(pe)
+    mT, mN, _ = weights(p)
+    n = 5                                   # 2 pi n = 31.4: window ends at s = 31.4
+    k = 2 * np.pi * n / p.L
+    ds = p.cs * k * p.dt_min
+    M = off[n + 1] - off[n]
+    PT, PN = _primitives(ds * np.arange(M + 1), r)
+    cT = np.cumsum(wT[off[n]:off[n + 1]])
+    cN = np.cumsum(wN[off[n]:off[n + 1]])
+    scale = p.dt_min / ds                   # d tau = dt_min ds / ds_n
+    assert np.abs(cT - scale * PT[1:]).max() < 1e-10 * np.abs(scale * PT).max()
+    assert np.abs(cN - scale * PN[1:]).max() < 1e-10 * np.abs(scale * PN).max()
+    j = np.arange(M)
+    sm = ds * (j + 0.5)
+    h = 1e-3
+    d2T = (G_T(sm + h, r) - 2 * G_T(sm, r) + G_T(sm - h, r)) / h ** 2
+    lead = p.dt_min * ds ** 2 * d2T / 24.0
+    diff = wT[off[n]:off[n + 1]] - mT[off[n]:off[n + 1]]
+    assert np.abs(diff - lead).max() < 1e-2 * np.abs(lead).max()
+    assert np.abs(diff).max() > 0
