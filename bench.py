@@ -74,6 +74,12 @@ def _args():
                          "the paper's own cycle setup; ensemble: 256 rough-fault realizations of uneven N")
     ap.add_argument("--kcN-L", type=float, default=0.0,
                     help="k_c * eta * L of the normal-traction kernel (the second cutting plane); 0: one plane")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="profiling runs: only W + K launches of the history convolution on the workload's handle "
+                         "(no tuning unless --weights tune), one JSON line with their times")
+    ap.add_argument("--weights", choices=["tune", "generated", "streamed"], default="tune",
+                    help="history sweep weights: autotuned (default), evaluated on chip where the modes allow, "
+                         "or streamed")
     a = ap.parse_args()
     if a.N == 0:
         a.N = DEFAULT_N[a.workload]
@@ -378,7 +384,7 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
     _fill_history(torch, g, 11 + rank, precision)
     if mlp is not None:
         g.set_mlp(mlp)
-    tuned = g.tune(reps=5)   # the library's autotuner: sweep shape, weight form, CTAs per SM
+    tuned = _sweep_setup(g, a)
     hist_bytes, dev_bytes = g.footprint()
     slots = int(np.maximum(g.windows() - 1, 0).sum())
     ring_bytes = slots * (16 if precision == "fp32" else 32)
@@ -435,7 +441,45 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
                 sweep_ms_median=statistics.median(ms_sweep), hist_bytes=hist_bytes, ring_bytes=ring_bytes,
                 weight_bytes=hist_bytes - ring_bytes, dev_bytes=dev_bytes, clocks=clk, it_sum=it_sum,
                 it_max=it_max, slots=slots, flushed=flushed, step_kernels=g.step_kernels(), steps=K,
-                sweep=dict(tuned, table_err=g.get_sweep()["table_err"]))
+                sweep=dict(tuned, table_err=g.get_sweep()["table_err"],
+                           lag_ctas_per_sm=g.get_sweep()["lag_ctas_per_sm"]))
+
+
+def _sweep_setup(g, a) -> dict:
+    """The history sweep's configuration: the library's autotuner (shape, weight form, CTAs per SM), or a
+    weight form forced for profiling (shape 3, as many CTAs as fit)."""
+    if a.weights == "tune" or g.get_sweep()["table_err"] < 0:
+        return g.tune(reps=5)
+    g.set_sweep(4, 1.0 / 64 if a.weights == "generated" else 0.0, 0)
+    sw = g.get_sweep()
+    return {"shape": sw["shape"], "gen_ds_max": sw["gen_ds_max"], "ctas_per_sm": sw["ctas_per_sm"], "ms": None}
+
+
+def _sweep_only(torch, a):
+    """W + K launches of the history convolution alone (profiling runs)."""
+    from paper_2107_03550_gb300.sbiem import Fault
+    w = _workload(a.workload, a.N)
+    g = Fault.from_workload(w, precision=1 if a.precision == "fp32" else 0)
+    g.set_stream(torch.cuda.current_stream())
+    _fill_history(torch, g, 11, a.precision)
+    cfg = _sweep_setup(g, a)
+    slots = int(np.maximum(g.windows() - 1, 0).sum())
+    for _ in range(a.warmup):
+        g.history_enqueue(1)
+    ms = []
+    for _ in range(a.steps):
+        e0, e1, em = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        em.record()
+        e0.record()
+        g.history_enqueue(1, sweep_done=em)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(em))
+    g.close()
+    ring = slots * (16 if a.precision == "fp32" else 32)
+    print(json.dumps({"sweep_only": True, "workload": _workload_name(a.workload, w), "N": a.N, "sweep": cfg,
+                      "ring_slots": slots, "ring_bytes": ring, "sweep_ms": ms,
+                      "ring_GBps_median": ring / (statistics.median(ms) * 1e-3) / 1e9}), flush=True)
 
 
 def _side(res: dict, what: str) -> dict:
@@ -571,6 +615,9 @@ def run_ours(a):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     if vis and "," not in vis and vis.strip().isdigit():
         dev_index = int(vis)
+    if a.sweep_only:
+        _sweep_only(torch, a)
+        return
     if a.workload == "ensemble":
         line = _ensemble(torch, a, rank, world, dev_index)
         if rank == 0:

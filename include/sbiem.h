@@ -435,6 +435,10 @@ int sbiem_mlp_train(const float* samples, int64_t n, int epochs, int batch, floa
 /* Device-side quantities of the last step: Newton iterations (sum, max over
  * elements and passes). */
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max);
+/* Running totals of Newton iterations and solves (every pass of every step,
+ * trial and rejected steps of sbiem_run included) since creation or the last
+ * reset (reset != 0 zeroes them after reading).  Synchronizes. */
+int sbiem_newton_totals(sbiem_t s, int64_t* iters, int64_t* solves, int reset);
 
 /* Bytes the history convolution must read per step (rings, plus the
  * weights unless the sweep evaluates them on chip) and the total device
@@ -446,25 +450,38 @@ int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_
  * launch shape and where its weights come from change).
  *   shape: lags per chunk x stages in flight; the chunk length is fixed at
  *     creation (shape 3: 2048 lags FP32, 1024 FP64, two stages), so only
- *     shapes of that chunk length are accepted (0 and 2, or 1, or 3).
- *   generated (FP32 form only): 1 evaluates the midpoint weights
- *     w_{n,j} = dt_min C(c_s k_n (j + 1/2) dt_min) on chip from a
- *     piecewise-polynomial table of C^T, C^N (degree 5 on pieces of width
- *     1/4 in s, built in FP64 from the library's kernel route, rounded to
- *     FP32), so the sweep reads only the ring slots; 0 streams the
- *     materialized weights with them.  A new FP32 handle evaluates them
- *     whenever its windows' s range fits the table (about s <= 213, i.e.
- *     k_c L <= 213 rad); table_err is the table's largest error relative to
- *     dt_min max|C| (-1: no table).
+ *     shapes of that chunk length are accepted (0 and 2, or 1, or 3 and 4;
+ *     shape 4 is shape 3's chunk in one stage).
+ *   gen_ds_max (FP32 form only): where the weights come from.  The
+ *     midpoint weights w_{n,j} = dt_min C(s) at s = (j + 1/2) ds_n,
+ *     ds_n = c_s k_n dt_min, depend on the mode only through ds_n; modes
+ *     with ds_n <= gen_ds_max evaluate them on chip from a
+ *     piecewise-polynomial table of C^T, C^N (pieces of width 1/4 in s,
+ *     each with a degree-5 polynomial valid over 1.5 piece widths, built in
+ *     FP64 from the library's kernel route, rounded to FP32, read through
+ *     L1; a thread evaluates eight consecutive lags from one piece), so for
+ *     them the sweep reads only ring slots; the other modes stream the
+ *     materialized weights with the slots.  0 streams every mode's weights;
+ *     values above 1/64 (the largest step an eight-lag block allows) are
+ *     taken as 1/64, the default of a new FP32 handle whenever its windows'
+ *     s range fits the table (k_c L <= about 340 rad); table_err is the
+ *     table's largest error relative to dt_min max|C| (-1: no table).
  *   ctas_per_sm: resident sweep CTAs per SM (0: as many as fit).
+ *   lag_ctas_per_sm (get only): the same for the next step's sweep that
+ *     sbiem_enqueue runs beside the passes.
  * sbiem_set_sweep synchronizes and rebuilds the step graphs.  sbiem_tune is
  * the autotuner: it times `reps` launches (median, after one untimed) of the
- * history convolution for every shape of the handle's chunk length, both
- * weight forms and 1 .. (occupancy limit) CTAs per SM, and keeps the
- * fastest; the committed state is unchanged.  Errors: SBIEM_ERR_INVALID,
- * SBIEM_ERR_UNSUPPORTED (generated = 1 without a table), SBIEM_ERR_CUDA.
+ * history convolution for every shape of the handle's chunk length, the
+ * thresholds 0, 1/512, 1/256, 1/128 and 1/64, and 1 .. (occupancy limit)
+ * CTAs per SM, and keeps the fastest; then it times the next step's sweep
+ * (the overlapped form of sbiem_enqueue) together with the two passes it
+ * runs beside, for 1 .. (occupancy limit) sweep CTAs per SM, and keeps the
+ * fastest.  Nothing is committed while it times; the committed state is
+ * unchanged.  Errors: SBIEM_ERR_INVALID, SBIEM_ERR_UNSUPPORTED
+ * (gen_ds_max > 0 without a table), SBIEM_ERR_CUDA.
  */
-int sbiem_get_sweep(sbiem_t s, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, double* table_err);
+int sbiem_get_sweep(sbiem_t s, int32_t* shape, double* gen_ds_max, int32_t* ctas_per_sm, int32_t* lag_ctas_per_sm,
+                    double* table_err);
 
 /*
  * sbiem_set_wait_limit -- polls (mbarrier try_wait calls) the history sweep
@@ -478,8 +495,8 @@ int sbiem_get_sweep(sbiem_t s, int32_t* shape, int32_t* generated, int32_t* ctas
  */
 #define SBIEM_WAIT_LIMIT_DEFAULT 4194304
 int sbiem_set_wait_limit(sbiem_t s, int64_t polls);
-int sbiem_set_sweep(sbiem_t s, int32_t shape, int32_t generated, int32_t ctas_per_sm);
-int sbiem_tune(sbiem_t s, int reps, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, float* ms);
+int sbiem_set_sweep(sbiem_t s, int32_t shape, double gen_ds_max, int32_t ctas_per_sm);
+int sbiem_tune(sbiem_t s, int reps, int32_t* shape, double* gen_ds_max, int32_t* ctas_per_sm, float* ms);
 
 /*
  * sbiem_kernel_values -- host FP64 evaluation of the convolution kernels

@@ -27,9 +27,13 @@ thread_local std::string g_last_error;
 
 // Sweep shape of a new handle (chunk length x stages in flight).
 constexpr int kDefaultSweepShape = 3;
-// Largest on-chip weight table (bytes): two CTAs of shape 3 (two 32 KB
-// stages each) and their tables fit in an SM's shared memory.
-constexpr int64_t kGenMaxTableBytes = 40 * 1024;
+// Largest on-chip weight table (bytes): it is read through L1 beside the
+// sweep's stages in shared memory.
+constexpr int64_t kGenMaxTableBytes = 64 * 1024;
+// Modes whose s step is at most this evaluate their weights on chip by
+// default (the largest step the sweep's blocks of eight lags allow); the
+// autotuner revisits it.
+constexpr float kGenDsMaxDefault = static_cast<float>(kGenDsBlockMax);
 
 int fail(int code, const std::string& msg) {
   g_last_error = msg;
@@ -94,6 +98,7 @@ struct sbiem_s {
   int sweep_shape = 0;  // chunk length x stages of the sweep
   int lag_shape = 0;    // the same for the overlapped sweep
   int sweep_ctas = 0;   // resident sweep CTAs per SM asked for (0: as many as fit)
+  int lag_ctas = 0;     // the same for the overlapped sweep (0: the rule of sweep_config)
   long long spin_limit = SBIEM_WAIT_LIMIT_DEFAULT;  // polls of the sweep's consumer waits
   // output of sbiem_run: callback, its argument, every how many accepted
   // steps, and page-locked host copies of slip and slip rate
@@ -104,6 +109,7 @@ struct sbiem_s {
   // device footprint planned at creation (for the out-of-memory message)
   int64_t planned_bytes = 0, planned_ring = 0, planned_w = 0;
   int gen_pieces = 0;   // pieces of the on-chip weight table (0: none, weights streamed)
+  float gen_ds_max = 0;  // modes with ds = c_s k_n dt_min <= this evaluate their weights on chip
   double gen_err = 0.0; // its largest error relative to dt max|C|
   // timing probe: 4 events per slot; graph event-record nodes are retargeted
   // to the slot of each launch
@@ -243,9 +249,10 @@ void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t
 // pass CTA); other shapes one CTA per SM; with the four-kernel FFT (small
 // CTAs) the full grid.
 void sweep_config(sbiem_s* s) {
-  const int gp = (s->fp32() && s->f32.gen) ? s->gen_pieces : 0;
-  int per_sm = s->fp32() ? sweep_blocks_per_sm<float>(s->sweep_shape, gp)
-                         : sweep_blocks_per_sm<double>(s->sweep_shape, 0);
+  const bool gen = s->fp32() && s->f32.wtab && s->gen_ds_max > 0.0f;
+  s->f32.gen_ds_max = gen ? s->gen_ds_max : 0.0f;
+  int per_sm = s->fp32() ? sweep_blocks_per_sm<float>(s->sweep_shape, gen)
+                         : sweep_blocks_per_sm<double>(s->sweep_shape, false);
   if (per_sm < 1) per_sm = 1;
   if (s->sweep_ctas > 0 && s->sweep_ctas < per_sm) per_sm = s->sweep_ctas;
   s->hist_grid = s->sm_count * per_sm;
@@ -257,6 +264,12 @@ void sweep_config(sbiem_s* s) {
       s->lag_shape = 4;
       s->lag_grid = 2 * s->sm_count;
     }
+  }
+  if (s->lag_ctas > 0) {
+    // set by the autotuner: as many CTAs per SM as timed fastest beside the passes
+    const int lim = s->fp32() ? sweep_blocks_per_sm<float>(s->lag_shape, gen)
+                              : sweep_blocks_per_sm<double>(s->lag_shape, false);
+    s->lag_grid = s->sm_count * std::max(1, std::min(s->lag_ctas, lim));
   }
   s->f64.sweep_shape = s->f32.sweep_shape = s->sweep_shape;
   s->f64.lag_shape = s->f32.lag_shape = s->lag_shape;
@@ -297,7 +310,7 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   COPYP(dhat); COPYP(khat); COPYP(U2); COPYP(Q2); COPYP(AT); COPYP(AN); COPYP(BT); COPYP(BN); COPYP(partial);
   COPYP(counter); COPYP(ring_off); COPYP(w_off); COPYP(Rn); COPYP(Mn); COPYP(head);
   COPYP(chunks); COPYP(nchunks); COPYP(mfirst); COPYP(mcount); COPYP(status); COPYP(steps_done); COPYP(t);
-  COPYP(it_sum); COPYP(it_max); COPYP(work); COPYP(w0pow); COPYP(c0pow); COPYP(dhat32); COPYP(khat32);
+  COPYP(it_sum); COPYP(it_max); COPYP(it_total); COPYP(work); COPYP(w0pow); COPYP(c0pow); COPYP(dhat32); COPYP(khat32);
   COPYP(AT32); COPYP(AN32);
 #undef COPYP
   bool ok = true;
@@ -621,6 +634,7 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   f.it_sum = alloc_n<unsigned long long>(s, 1, &ok);
   f.work = alloc_n<int>(s, 1, &ok);
   f.it_max = alloc_n<int>(s, 1, &ok);
+  f.it_total = alloc_n<unsigned long long>(s, 2, &ok);
   s->tw64 = alloc_n<double2>(s, N, &ok);
   s->u_a = alloc_n<double2>(s, N, &ok);
   s->u_b = alloc_n<double2>(s, N, &ok);
@@ -758,7 +772,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
     int gp = 0;
     double gerr = 0.0;
     build_gen_table(r, s->dt_min, smax, gtab, &gp, &gerr);
-    if (rc == SBIEM_OK && p.quadrature == 0 && static_cast<int64_t>(gp) * 48 <= kGenMaxTableBytes) {
+    if (rc == SBIEM_OK && p.quadrature == 0 &&
+        static_cast<int64_t>(gp) * (kGenDeg + 1) * 8 <= kGenMaxTableBytes) {
       std::vector<float4> wg(s->nmodes);
       for (int n = 0; n < s->nmodes; ++n) {
         const double ds = p.cs * (2.0 * M_PI * n / s->L) * s->dt_min;
@@ -779,9 +794,9 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
         s->f32.wtab = d_wtab;
         s->f32.wgen = d_wgen;
         s->f32.wtab_pieces = gp;
-        s->f32.gen = 1;
         s->gen_pieces = gp;
         s->gen_err = gerr;
+        s->gen_ds_max = kGenDsMaxDefault;
       }
     }
     sweep_config(s);
@@ -1479,6 +1494,17 @@ int sbiem_probe_read(sbiem_t s, int slot, float* ms_step, float* ms_history) {
   return SBIEM_OK;
 }
 
+int sbiem_newton_totals(sbiem_t s, int64_t* iters, int64_t* solves, int reset) {
+  if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
+  unsigned long long v[2] = {0ull, 0ull};
+  CK(cudaMemcpyAsync(v, s->f64.it_total, sizeof(v), cudaMemcpyDeviceToHost, s->stream));
+  if (reset) CK(cudaMemsetAsync(s->f64.it_total, 0, sizeof(v), s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (iters) *iters = static_cast<int64_t>(v[0]);
+  if (solves) *solves = static_cast<int64_t>(v[1]);
+  return SBIEM_OK;
+}
+
 int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
   unsigned long long sum = 0;
@@ -1493,9 +1519,15 @@ int sbiem_newton_stats(sbiem_t s, int64_t* iters_sum, int32_t* iters_max) {
 
 int sbiem_footprint(sbiem_t s, int64_t* hist_bytes, int64_t* device_bytes) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
-  const bool gen = s->fp32() && s->f32.gen;
-  const int64_t slot = s->fp32() ? 16 : 32, wb = gen ? 0 : (s->fp32() ? 8 : 16);
-  if (hist_bytes) *hist_bytes = s->total_slots * (slot + wb);
+  const int64_t slot = s->fp32() ? 16 : 32, wb = s->fp32() ? 8 : 16;
+  // weights stream only for the modes that do not evaluate them on chip
+  int64_t streamed = 0;
+  for (int n = 1; n < s->nmodes; ++n) {
+    const double ds = s->p.cs * (2.0 * M_PI * n / s->L) * s->dt_min;
+    if (!(s->fp32() && s->f32.gen_ds_max > 0.0f && static_cast<float>(ds) <= s->f32.gen_ds_max))
+      streamed += s->Rn[n];
+  }
+  if (hist_bytes) *hist_bytes = s->total_slots * slot + streamed * wb;
   if (device_bytes) *device_bytes = s->device_bytes;
   return SBIEM_OK;
 }
@@ -1511,52 +1543,62 @@ int sbiem_set_wait_limit(sbiem_t s, int64_t polls) {
   return SBIEM_OK;
 }
 
-int sbiem_get_sweep(sbiem_t s, int32_t* shape, int32_t* generated, int32_t* ctas_per_sm, double* table_err) {
+int sbiem_get_sweep(sbiem_t s, int32_t* shape, double* gen_ds_max, int32_t* ctas_per_sm, int32_t* lag_ctas_per_sm,
+                    double* table_err) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
   if (shape) *shape = s->sweep_shape;
-  if (generated) *generated = s->fp32() && s->f32.gen ? 1 : 0;
+  if (gen_ds_max) *gen_ds_max = s->fp32() ? s->f32.gen_ds_max : 0.0;
   if (ctas_per_sm) *ctas_per_sm = s->hist_grid / (s->sm_count > 0 ? s->sm_count : 1);
+  if (lag_ctas_per_sm) *lag_ctas_per_sm = s->lag_grid / (s->sm_count > 0 ? s->sm_count : 1);
   if (table_err) *table_err = s->gen_pieces > 0 ? s->gen_err : -1.0;
   return SBIEM_OK;
 }
 
-int sbiem_set_sweep(sbiem_t s, int32_t shape, int32_t generated, int32_t ctas_per_sm) {
+int sbiem_set_sweep(sbiem_t s, int32_t shape, double gen_ds_max, int32_t ctas_per_sm) {
   if (!s) return fail(SBIEM_ERR_INVALID, "NULL handle");
-  if (shape < 0 || shape > 3 || sweep_chunk_slots(s->p.precision, shape) != s->chunk_slots)
+  if (shape < 0 || shape > 4 || sweep_chunk_slots(s->p.precision, shape) != s->chunk_slots)
     return fail(SBIEM_ERR_INVALID, "shape must keep the handle's chunk length (" + std::to_string(s->chunk_slots) +
                                        " lags)");
-  if (generated != 0 && generated != 1) return fail(SBIEM_ERR_INVALID, "generated must be 0 or 1");
-  if (generated && s->gen_pieces == 0)
-    return fail(SBIEM_ERR_UNSUPPORTED, "no on-chip weight table (FP64 form, or windows past its size)");
+  if (!(gen_ds_max >= 0.0)) return fail(SBIEM_ERR_INVALID, "gen_ds_max must be >= 0");
+  if (gen_ds_max > 0.0 && s->gen_pieces == 0)
+    return fail(SBIEM_ERR_UNSUPPORTED, "no on-chip weight table (FP64 form, exact quadrature, or windows past it)");
   if (ctas_per_sm < 0) return fail(SBIEM_ERR_INVALID, "ctas_per_sm must be >= 0");
   CK(cudaStreamSynchronize(s->stream));
   s->sweep_shape = shape;
-  if (s->fp32()) s->f32.gen = generated;
+  s->gen_ds_max = static_cast<float>(std::min(gen_ds_max, kGenDsBlockMax));
   s->sweep_ctas = ctas_per_sm;
+  s->lag_ctas = 0;  // the overlapped sweep's grid follows the rule again (sbiem_tune times it)
   sweep_config(s);
   drop_graphs(s);
   s->lag_m = -1;
   return SBIEM_OK;
 }
 
-int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, int32_t* gen_out, int32_t* ctas_out, float* ms_out) {
+int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t* ctas_out, float* ms_out) {
   if (!s || reps < 1) return fail(SBIEM_ERR_INVALID, "bad argument");
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // thresholds of the on-chip weights: none, then 1/8 .. 1 of the largest
+  // s step the on-chip blocks allow
+  std::vector<float> thr = {0.0f};
+  if (s->gen_pieces > 0)
+    for (double v : {kGenDsBlockMax / 8.0, kGenDsBlockMax / 4.0, kGenDsBlockMax / 2.0, kGenDsBlockMax})
+      thr.push_back(static_cast<float>(v));
   float best = 1e30f;
-  int bshape = s->sweep_shape, bgen = s->fp32() ? s->f32.gen : 0, bctas = 0;
-  for (int shape = 0; shape <= 3; ++shape) {
+  int bshape = s->sweep_shape, bctas = 0;
+  float bthr = s->gen_ds_max;
+  for (int shape = 0; shape <= 4; ++shape) {
     if (sweep_chunk_slots(s->p.precision, shape) != s->chunk_slots) continue;
-    for (int gen = s->gen_pieces > 0 ? 1 : 0; gen >= 0; --gen) {
-      const int lim = s->fp32() ? sweep_blocks_per_sm<float>(shape, gen ? s->gen_pieces : 0)
-                                : sweep_blocks_per_sm<double>(shape, 0);
+    for (float t : thr) {
+      const int lim = s->fp32() ? sweep_blocks_per_sm<float>(shape, t > 0.0f)
+                                : sweep_blocks_per_sm<double>(shape, false);
       for (int c = 1; c <= lim; ++c) {
         s->sweep_shape = shape;
-        if (s->fp32()) s->f32.gen = gen;
+        s->gen_ds_max = t;
         s->sweep_ctas = c;
         sweep_config(s);
-        std::vector<float> t;
+        std::vector<float> tm;
         for (int k = 0; k <= reps; ++k) {
           CK(cudaEventRecord(e0, s->stream));
           if (s->fp32()) launch_history<float>(s->f32, 1, s->hist_grid, s->stream);
@@ -1565,24 +1607,80 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, int32_t* gen_out, int32_
           CK(cudaEventSynchronize(e1));
           float ms = 0.f;
           CK(cudaEventElapsedTime(&ms, e0, e1));
-          if (k > 0) t.push_back(ms);  // the first launch is untimed
+          if (k > 0) tm.push_back(ms);  // the first launch is untimed
         }
-        std::sort(t.begin(), t.end());
-        if (t[t.size() / 2] < best) {
-          best = t[t.size() / 2];
+        std::sort(tm.begin(), tm.end());
+        if (tm[tm.size() / 2] < best) {
+          best = tm[tm.size() / 2];
           bshape = shape;
-          bgen = gen;
+          bthr = t;
           bctas = c;
         }
       }
     }
   }
+  int rc = sbiem_set_sweep(s, bshape, bthr, bctas);
+  if (rc) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
+  // the overlapped step: the next step's sweep (into BT/BN) on the side
+  // stream beside this step's two passes (their results stay staged), timed
+  // together for 1 .. (occupancy limit) sweep CTAs per SM; nothing is
+  // committed, and the status word the passes may set is put back
+  {
+    unsigned st0 = 0;
+    CK(cudaMemcpyAsync(&st0, s->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->lag_ctas = 0;
+    sweep_config(s);
+    const int lim = s->fp32() ? sweep_blocks_per_sm<float>(s->lag_shape, s->f32.gen_ds_max > 0.0f)
+                              : sweep_blocks_per_sm<double>(s->lag_shape, false);
+    float lbest = 1e30f;
+    int lb = 0;
+    for (int c = 1; c <= lim; ++c) {
+      s->lag_ctas = c;
+      sweep_config(s);
+      std::vector<float> tm;
+      for (int k = 0; k <= reps; ++k) {
+        CK(cudaEventRecord(e0, s->stream));
+        CK(cudaEventRecord(s->ev_fork, s->stream));
+        CK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        if (s->fp32()) {
+          launch_history_ahead<float>(s->f32, 1, s->lag_grid, s->side);
+          launch_pass<float>(s->f32, 1, 1, s->stream);
+          launch_pass<float>(s->f32, 2, 1, s->stream);
+        } else {
+          launch_history_ahead<double>(s->f64, 1, s->lag_grid, s->side);
+          launch_pass<double>(s->f64, 1, 1, s->stream);
+          launch_pass<double>(s->f64, 2, 1, s->stream);
+        }
+        CK(cudaEventRecord(s->ev_join, s->side));
+        CK(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (k > 0) tm.push_back(ms);
+      }
+      std::sort(tm.begin(), tm.end());
+      if (tm[tm.size() / 2] < lbest) {
+        lbest = tm[tm.size() / 2];
+        lb = c;
+      }
+    }
+    CK(cudaMemcpyAsync(s->f64.status, &st0, sizeof(unsigned), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->lag_ctas = lb;
+    sweep_config(s);
+    drop_graphs(s);
+    s->lag_m = -1;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  int rc = sbiem_set_sweep(s, bshape, bgen, bctas);
-  if (rc) return rc;
   if (shape_out) *shape_out = bshape;
-  if (gen_out) *gen_out = bgen;
+  if (gen_out) *gen_out = bthr;
   if (ctas_out) *ctas_out = bctas;
   if (ms_out) *ms_out = best;
   return SBIEM_OK;
@@ -1625,6 +1723,7 @@ struct sbiem_batch_s {
   const float4* wtab = nullptr;
   int gen_pieces = 0;
   bool gen = false;
+  float gen_ds_max = 0.0f;  // in force while gen
   int per_sm_plain = 1, per_sm_gen = 1;
   std::vector<void*> allocs;
   cudaGraphExec_t graph = nullptr;
@@ -1711,7 +1810,8 @@ template <class R>
 void batch_history(sbiem_batch_s* b, cudaStream_t st, bool ahead = false) {
   launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
                           b->cbase, b->shape, ahead ? b->lag_grid : b->hist_grid, ahead ? 2 : 1, st, ahead,
-                          b->gen ? b->wtab : nullptr, b->gen ? b->gen_pieces : 0);
+                          b->gen ? b->wtab : nullptr, b->gen ? b->gen_pieces : 0,
+                          b->gen ? b->gen_ds_max : 0.0f);
 }
 
 // The groups' two passes as parallel branches of st (joined on st).
@@ -1814,10 +1914,11 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
       b->wtab = widest->f32.wtab;
       b->gen_pieces = widest->gen_pieces;
       b->gen = true;
+      b->gen_ds_max = kGenDsMaxDefault;
     }
   }
-  b->per_sm_plain = fp32 ? sweep_blocks_per_sm<float>(b->shape) : sweep_blocks_per_sm<double>(b->shape);
-  b->per_sm_gen = b->gen ? sweep_blocks_per_sm<float>(b->shape, b->gen_pieces) : 0;
+  b->per_sm_plain = fp32 ? sweep_blocks_per_sm<float>(b->shape, false) : sweep_blocks_per_sm<double>(b->shape, false);
+  b->per_sm_gen = b->gen ? sweep_blocks_per_sm<float>(b->shape, true) : 0;
   if (b->per_sm_plain < 1) b->per_sm_plain = 1;
   if (b->per_sm_gen < 1) b->per_sm_gen = 1;
   b->per_sm = b->gen ? b->per_sm_gen : b->per_sm_plain;
@@ -1932,9 +2033,14 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
   float best = 1e30f;
   int best_b = b->hist_grid / b->sm_count;
   bool best_gen = b->gen;
+  float best_thr = b->gen_ds_max;
   const bool can_gen = b->wtab != nullptr;
-  for (int g = can_gen ? 1 : 0; g >= 0; --g) {
-    b->gen = g == 1;
+  std::vector<float> thr = {0.0f};
+  if (can_gen)
+    for (double v : {kGenDsBlockMax / 4.0, kGenDsBlockMax}) thr.push_back(static_cast<float>(v));
+  for (float tv : thr) {
+    b->gen = tv > 0.0f;
+    b->gen_ds_max = tv;
     const int lim = b->gen ? b->per_sm_gen : b->per_sm_plain;
     for (int bl = 1; bl <= lim; ++bl) {
       b->hist_grid = b->sm_count * bl;
@@ -1958,10 +2064,12 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
         best = med;
         best_b = bl;
         best_gen = b->gen;
+        best_thr = tv;
       }
     }
   }
   b->gen = best_gen;
+  b->gen_ds_max = best_thr;
   b->per_sm = b->gen ? b->per_sm_gen : b->per_sm_plain;
   b->hist_grid = b->sm_count * best_b;
   // overlap or not: the overlapped step takes about max(lag sweep, passes),

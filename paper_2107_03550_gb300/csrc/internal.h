@@ -16,9 +16,14 @@ struct ChebTable {
 };
 
 // On-chip weight table of the FP32 history sweep: piece width (a power of
-// two, so piece indices and offsets are exact in FP32) and degree.
+// two, so piece indices and offsets are exact in FP32), the span of each
+// piece's polynomial in piece widths, and its degree.
 constexpr double kGenH = 0.25;
+constexpr double kGenSpan = 1.5;
 constexpr int kGenDeg = 5;
+// Largest s step of a mode whose weights the sweep evaluates on chip (a
+// thread's eight consecutive lags then stay on one piece's polynomial).
+constexpr double kGenDsBlockMax = kGenH / 16.0;
 
 void kernel_values(double s, double r, double* cT, double* cN);
 void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, int* npieces, double* max_err);

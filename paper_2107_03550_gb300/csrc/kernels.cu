@@ -934,49 +934,72 @@ template <class R, int SH> struct SweepCfg {
 };
 constexpr int kSweepShapes = 5;
 constexpr int kSweepThreads = 128;
+// Threads of a sweep CTA: the on-chip weight form evaluates a polynomial per
+// lag and needs twice the warps to hide its latency.
+__host__ __device__ constexpr int sweep_threads(bool gen) { return gen ? 2 * kSweepThreads : kSweepThreads; }
 constexpr long long kSpinLimit = SBIEM_WAIT_LIMIT_DEFAULT;  // try_wait polls before a wait is declared stuck
 
-// A stage holds a chunk's ring slots and, unless the weights are evaluated
-// on chip (GEN), its weight run.
-template <class R, int SH, bool GEN = false>
+// A stage holds a chunk's ring slots and its weight run (left unused by a
+// chunk whose weights are evaluated on chip).
+template <class R, int SH>
 __host__ __device__ constexpr size_t sweep_stage_bytes() {
   return static_cast<size_t>(SweepCfg<R, SH>::kSlots) * sizeof(Slot<R>) +
-         (GEN ? 0 : static_cast<size_t>(SweepCfg<R, SH>::kSlots + 2) * sizeof(W2<R>));
+         static_cast<size_t>(SweepCfg<R, SH>::kSlots + 2) * sizeof(W2<R>);
 }
 
 // On-chip weights: kGenDeg + 1 coefficient pairs (T, N) per piece of width
-// kGenH, three float4 per piece (48 bytes: an odd number of 16-byte bank
-// groups, so neighbouring pieces gathered by one warp fall in different banks).
+// kGenH, kGenF4 float4 per piece, read through L1 (the table is a few tens
+// of KB; a thread loads one piece per block of lags).
 constexpr int kGenPairs = kGenDeg + 1;
-static_assert(kGenPairs == 6, "the evaluation below unrolls six coefficient pairs");
+constexpr int kGenF4 = kGenPairs / 2;
+static_assert(kGenPairs % 2 == 0, "coefficient pairs come two per float4");
 constexpr float kGenHf = static_cast<float>(kGenH);
 constexpr float kGenInvH = static_cast<float>(1.0 / kGenH);
 
-// w = dt (C^T(s), C^N(s)) at s = jf ds, jf = j + 1/2, ds = dsh + dsl (two
-// floats).  p = jf dsh is rounded once; its error e = jf dsh - p comes
-// exactly from an FMA, so the offset within piece q (q kGenH exact, p - q
-// kGenH exact by Sterbenz) carries s to about 1e-8 absolute.  q is clamped to
-// the table (lags past a field's window are zeroed by the caller).
-__device__ __forceinline__ float2 gen_weight(const float4* __restrict__ tab, int qmax, float jf, float dsh,
-                                             float dsl) {
-  const float p = jf * dsh;
-  const float e = fmaf(jf, dsl, fmaf(jf, dsh, -p));
-  const float qf = floorf(p * kGenInvH);
-  int q = static_cast<int>(qf);
-  q = q < 0 ? 0 : (q > qmax ? qmax : q);
-  const float u = fmaf(-static_cast<float>(q), kGenHf, p) + e;
-  const float t = fmaf(u, 2.0f * kGenInvH, -1.0f);
-  const float4 a = tab[3 * q], b = tab[3 * q + 1], c = tab[3 * q + 2];
-  float wT = fmaf(c.z, t, c.x), wN = fmaf(c.w, t, c.y);
-  wT = fmaf(wT, t, b.z);
-  wN = fmaf(wN, t, b.w);
-  wT = fmaf(wT, t, b.x);
-  wN = fmaf(wN, t, b.y);
-  wT = fmaf(wT, t, a.z);
-  wN = fmaf(wN, t, a.w);
-  wT = fmaf(wT, t, a.x);
-  wN = fmaf(wN, t, a.y);
-  return make_float2(wT, wN);
+// Two FP32 fused multiply-adds in one packed instruction (fma.rn.f32x2):
+// each lane rounds exactly as fmaf does.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
+// The weights of a thread's block of kGenBlock consecutive lags come from
+// one piece: the block starts at lag j (s0 = (j + 1/2) ds, ds = dsh + dsl as
+// two floats) in piece q; s0 jf dsh is rounded once and its error comes
+// exactly from an FMA, so the offset within the piece (q kGenH exact,
+// p - q kGenH exact by Sterbenz) carries s to about 1e-8 absolute.  The
+// piece's polynomial holds over kGenSpan piece widths, so the block stays on
+// it while (kGenBlock - 1) ds <= (kGenSpan - 1) kGenH: modes with ds up to
+// kGenDsBlockMax.
+constexpr int kGenBlock = 8;
+constexpr float kGenTScale = static_cast<float>(2.0 / (kGenSpan * kGenH));  // dt / ds
+static_assert((kGenBlock - 1) * kGenDsBlockMax <= (kGenSpan - 1.0) * kGenH, "blocks stay on their piece");
+static_assert(sweep_threads(true) * kGenBlock == SweepCfg<float, 3>::kSlots, "a GEN stage is one block per thread");
+
+// (w^T, w^N) = the piece's polynomial at t: Horner on the coefficient pairs
+// (c[i].x, c[i].y) = pair 2i, (c[i].z, c[i].w) = pair 2i + 1, two lanes per
+// packed FMA.
+__device__ __forceinline__ float2 gen_horner(const float4 (&c)[kGenF4], float t) {
+  const float2 tt = make_float2(t, t);
+  float2 w = make_float2(c[kGenF4 - 1].z, c[kGenF4 - 1].w);
+#pragma unroll
+  for (int i = kGenF4 - 1; i >= 0; --i) {
+    if (i < kGenF4 - 1) w = ffma2(w, tt, make_float2(c[i].z, c[i].w));
+    w = ffma2(w, tt, make_float2(c[i].x, c[i].y));
+  }
+  return w;
+}
+
+// acc += (wT (s.x, s.y), wN (s.z, s.w)) in two packed FMAs.
+__device__ __forceinline__ void slot_fma2(float2& at, float2& an, const float4& s, const float2 w) {
+  at = ffma2(make_float2(w.x, w.x), make_float2(s.x, s.y), at);
+  an = ffma2(make_float2(w.y, w.y), make_float2(s.z, s.w), an);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -1045,18 +1068,20 @@ struct SweepPlan {
   const void* wsrc;
   unsigned b1, b2, bw;
   int len, par, mode, member;
-  // on-chip weights: weight index of the chunk's first slot, the mode's ds
-  // as two floats and the two fields' windows
-  int j0, mt, mn;
+  // on-chip weights (gen != 0): weight index of the chunk's first slot, the
+  // mode's ds as two floats and the two fields' windows
+  int gen, j0, mt, mn;
   float dsh, dsl;
 };
 constexpr int kPlanRing = 64;  // plans held in shared memory (a ring by chunk index)
 
 // Chunk c of the sweep: the fault's own chunk table, or an ensemble table
 // whose chunks name their member (Chunk::pad) in fs.
+// gen_ds_max (GEN only): modes whose s step ds = c_s k_n dt_min is at most
+// this evaluate their weights on chip, the others stream them.
 template <class R, bool BATCH, bool GEN = false>
 __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const DevFault<R>* fs, const Chunk* chunks,
-                                                int c, int m_dt) {
+                                                int c, int m_dt, float gen_ds_max = 0.0f) {
   SweepPlan pl{};
   const Chunk cd = chunks[c];
   const DevFault<R>& f = BATCH ? fs[cd.pad] : f0;
@@ -1083,19 +1108,23 @@ __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const Dev
   pl.b1 = static_cast<unsigned>(L1 * sizeof(Slot<R>));
   pl.r2 = ring;
   pl.b2 = static_cast<unsigned>(L2 * sizeof(Slot<R>));
+  pl.gen = 0;
   if constexpr (GEN) {
     const float4 gi = f.wgen[n];
-    pl.j0 = static_cast<int>(m_dt + cd.i0);
-    pl.dsh = gi.x;
-    pl.dsl = gi.y;
-    pl.mt = __float_as_int(gi.z);
-    pl.mn = __float_as_int(gi.w);
-    pl.wsrc = nullptr;
-    pl.bw = 0;
-  } else {
-    pl.wsrc = f.w + wa;
-    pl.bw = static_cast<unsigned>(wc * sizeof(W2<R>));
+    if (gi.x <= gen_ds_max) {
+      pl.gen = 1;
+      pl.j0 = static_cast<int>(m_dt + cd.i0);
+      pl.dsh = gi.x;
+      pl.dsl = gi.y;
+      pl.mt = __float_as_int(gi.z);
+      pl.mn = __float_as_int(gi.w);
+      pl.wsrc = nullptr;
+      pl.bw = 0;
+      return pl;
+    }
   }
+  pl.wsrc = f.w + wa;
+  pl.bw = static_cast<unsigned>(wc * sizeof(W2<R>));
   return pl;
 }
 
@@ -1115,22 +1144,22 @@ __device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* 
 
 // BATCH: the chunks of an ensemble (member in Chunk::pad), descriptors in fs;
 // members whose step failed are swept anyway (their sums are not written).
-// GEN (FP32): the weights are evaluated from the piecewise-polynomial table
-// wtab (wtab_pieces pieces, copied once into shared memory behind the
-// stages) instead of streamed with the ring slots.
+// GEN (FP32): chunks of modes with ds <= gen_ds_max evaluate their weights
+// from the piecewise-polynomial table wtab (wtab_pieces pieces, global,
+// read through L1) instead of copying them with the ring slots.
 template <class R, int SH, bool BATCH, bool GEN>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
     k_sweep(const __grid_constant__ DevFault<R> f, const DevFault<R>* __restrict__ fs,
             const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt,
-            const float4* __restrict__ wtab, int wtab_pieces) {
+            const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max) {
   static_assert(!GEN || sizeof(R) == 4, "on-chip weights belong to the FP32 form");
   constexpr int S = SweepCfg<R, SH>::kSlots;
   constexpr int kSweepStages = SweepCfg<R, SH>::kStages;
-  constexpr size_t SB = sweep_stage_bytes<R, SH, GEN>();
-  constexpr int NW = kSweepThreads / 32;
+  constexpr size_t SB = sweep_stage_bytes<R, SH>();
+  constexpr int NT = sweep_threads(GEN);
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(128) unsigned char sweep_smem[];
   __shared__ __align__(8) uint64_t bars[kSweepStages];
-  __shared__ __align__(8) uint64_t tbar;
   __shared__ SweepPlan plan[kPlanRing];
   __shared__ Acc4<R> red[2][NW];
   __shared__ unsigned s_skip;
@@ -1147,30 +1176,19 @@ __global__ void __launch_bounds__(kSweepThreads)
   if (tid == 0) {
     s_skip = BATCH ? 0u : *f.status;
     for (int s = 0; s < kSweepStages; ++s) mbar_init(&bars[s], 1);
-    if (GEN) mbar_init(&tbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // plans of the first kPlanRing chunks (one per thread)
-  for (int j = tid; j < kPlanRing && j < nk; j += kSweepThreads)
-    plan[j] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt);
+  for (int j = tid; j < kPlanRing && j < nk; j += NT)
+    plan[j] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt, gen_ds_max);
   __syncthreads();
   if (s_skip) return;
-  const float4* stab = reinterpret_cast<const float4*>(sweep_smem + kSweepStages * SB);
-  if (tid == 0) {
-    if (GEN) {
-      // the weight table, one bulk copy on its own barrier, ahead of the stages
-      const unsigned tb = static_cast<unsigned>(wtab_pieces) * 3u * 16u;
-      mbar_expect_tx(&tbar, tb);
-      bulk_g2s(sweep_smem + kSweepStages * SB, wtab, tb, &tbar);
-    }
+  if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
       sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
-  }
   // the consumer waits take the handle's limit (sbiem_set_wait_limit); the
   // drain below always waits at the full limit, so no copy is left in flight
   const long long lim = BATCH ? kSpinLimit : f.spin_limit;
-  bool tab_ok = true;
-  if (GEN) tab_ok = mbar_wait(&tbar, 0u, lim);
   // each thread accumulates a chunk in R and folds it into a compensated sum
   // over the consecutive chunks of one mode (a run may hold hundreds of
   // chunks: one plain FP32 sum of its thousands of products lost 5e-6); the
@@ -1179,6 +1197,7 @@ __global__ void __launch_bounds__(kSweepThreads)
   bool stuck = false;
   int k = 0;
   Acc4<R> run = {R(0), R(0), R(0), R(0)}, cmp = {R(0), R(0), R(0), R(0)};
+
   for (; k < nk; ++k) {
     const int s = k % kSweepStages;
     // every kPlanRing/2 chunks: plans of the half-ring ahead (chunks
@@ -1186,33 +1205,68 @@ __global__ void __launch_bounds__(kSweepThreads)
     if (k > 0 && k % (kPlanRing / 2) == 0) {
       const int j = k + kPlanRing / 2 + tid;
       if (tid < kPlanRing / 2 && j < nk)
-        plan[j % kPlanRing] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt);
+        plan[j % kPlanRing] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt, gen_ds_max);
     }
     const unsigned parity = static_cast<unsigned>(k / kSweepStages) & 1u;
-    const bool ok = mbar_wait(&bars[s], parity, lim) && tab_ok;
+    const bool ok = mbar_wait(&bars[s], parity, lim);
     Acc4<R> acc = {R(0), R(0), R(0), R(0)};
     if (ok) {
       const SweepPlan& pk = plan[k % kPlanRing];
       const int L = pk.len;
       const Slot<R>* sring = reinterpret_cast<const Slot<R>*>(sweep_smem + s * SB);
-      if constexpr (GEN) {
-        const int j0 = pk.j0, mt = pk.mt, mn = pk.mn, qmax = wtab_pieces - 1;
-        const float dsh = pk.dsh, dsl = pk.dsl;
-        float jf = static_cast<float>(j0 + tid) + 0.5f;  // exact: lags stay below 2^23
-#pragma unroll 4
-        for (int i = tid; i < L; i += kSweepThreads, jf += static_cast<float>(kSweepThreads)) {
-          float2 w = gen_weight(stab, qmax, jf, dsh, dsl);
-          const int j = j0 + i;
-          if (j >= mt) w.x = 0.0f;
-          if (j >= mn) w.y = 0.0f;
-          slot_fma(acc, sring[i], w);
-        }
-      } else {
+      auto streamed = [&] {
         const int par = pk.par;
         const W2<R>* sw =
             reinterpret_cast<const W2<R>*>(sweep_smem + s * SB + static_cast<size_t>(S) * sizeof(Slot<R>));
 #pragma unroll 4
-        for (int i = tid; i < L; i += kSweepThreads) slot_fma(acc, sring[i], sw[par + i]);
+        for (int i = tid; i < L; i += NT) slot_fma(acc, sring[i], sw[par + i]);
+      };
+      if constexpr (GEN) {
+       if (!pk.gen) {
+        streamed();
+       } else {
+        // thread tid: lags [kGenBlock tid, kGenBlock (tid + 1)) of the chunk,
+        // read in an order rotated by the lane, so the eight lanes of a
+        // quarter warp hit eight different bank groups
+        const int base = kGenBlock * tid;
+        if (base < L) {
+          const float jf = static_cast<float>(pk.j0 + base) + 0.5f;  // exact: lags stay below 2^23
+          const float p = jf * pk.dsh;
+          const float e = fmaf(jf, pk.dsl, fmaf(jf, pk.dsh, -p));
+          const float qf = fminf(floorf(p * kGenInvH), static_cast<float>(wtab_pieces - 1));
+          const int q = static_cast<int>(qf);
+          const float t0 = fmaf(fmaf(-qf, kGenHf, p) + e, kGenTScale, -1.0f);
+          const float dtv = pk.dsh * kGenTScale;
+          float4 cf[kGenF4];
+#pragma unroll
+          for (int i = 0; i < kGenF4; ++i) cf[i] = __ldg(wtab + kGenF4 * q + i);
+          const Slot<R>* blk = sring + base;
+          float2 at = make_float2(0.f, 0.f), an = make_float2(0.f, 0.f);
+          if (base + kGenBlock <= L && pk.j0 + base + kGenBlock <= min(pk.mt, pk.mn)) {
+#pragma unroll
+            for (int k = 0; k < kGenBlock; ++k) {
+              const int r = (k + lane) & (kGenBlock - 1);  // the lane-rotated lag order
+              slot_fma2(at, an, blk[r], gen_horner(cf, fmaf(static_cast<float>(r), dtv, t0)));
+            }
+          } else {
+            // the chunk's tail, or a field's window ending inside the block
+#pragma unroll
+            for (int k = 0; k < kGenBlock; ++k) {
+              const int r = (k + lane) & (kGenBlock - 1);
+              float2 w = gen_horner(cf, fmaf(static_cast<float>(r), dtv, t0));
+              if (pk.j0 + base + r >= pk.mt) w.x = 0.0f;
+              if (pk.j0 + base + r >= pk.mn) w.y = 0.0f;
+              if (base + r < L) slot_fma2(at, an, blk[r], w);
+            }
+          }
+          acc.tr = at.x;
+          acc.ti = at.y;
+          acc.nr = an.x;
+          acc.ni = an.y;
+        }
+       }
+      } else {
+        streamed();
       }
     }
     two_sum_add(run.tr, cmp.tr, acc.tr);
@@ -1258,7 +1312,6 @@ __global__ void __launch_bounds__(kSweepThreads)
     atomicOr(BATCH ? fs[plan[k % kPlanRing].member].status : f.status, SBIEM_FLAG_WAIT);
     // copies still in flight land in this CTA's shared memory: wait for them
     // (bounded) before the CTA exits
-    if (GEN && !tab_ok) mbar_wait(&tbar, 0u);
     for (int q = k; q < nk && q < k + kSweepStages; ++q)
       mbar_wait(&bars[q % kSweepStages], static_cast<unsigned>(q / kSweepStages) & 1u);
   }
@@ -1572,16 +1625,23 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   unsigned fl = flags;
   int im = iters;
   unsigned long long is = static_cast<unsigned long long>(iters);
+  unsigned ns = (have && solve && !ld_presc) ? 1u : 0u;  // Newton solves (a guess or plain start)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     fl |= __shfl_xor_sync(0xffffffffu, fl, o);
     im = max(im, __shfl_xor_sync(0xffffffffu, im, o));
     is += __shfl_xor_sync(0xffffffffu, is, o);
+    ns += __shfl_xor_sync(0xffffffffu, ns, o);
   }
   if (threadIdx.x == 0) {
     if (fl) atomicOr(f.status, fl);
     if (im) atomicMax(f.it_max, im);
     if (is) atomicAdd(f.it_sum, is);
+    if (f.it_total && ns) {
+      // running totals over every solve since the last reset (sbiem_newton_totals)
+      atomicAdd(f.it_total, is);
+      atomicAdd(f.it_total + 1, static_cast<unsigned long long>(ns));
+    }
   }
 }
 
@@ -2102,12 +2162,9 @@ void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_
   k_history_t<R, false><<<gr, kHistThreads, 0, st>>>(f, nullptr, f.chunks, f.nchunks, f.work, m_dt);
 }
 
-// Dynamic shared memory of the sweep: its stages, plus the weight table
-// (gen_pieces pieces of 48 bytes) when the weights are evaluated on chip.
+// Dynamic shared memory of the sweep: its stages.
 template <class R, int SH>
-static size_t sweep_smem(int gen_pieces = 0) {
-  if (gen_pieces > 0)
-    return SweepCfg<R, SH>::kStages * sweep_stage_bytes<R, SH, true>() + static_cast<size_t>(gen_pieces) * 48;
+static size_t sweep_smem() {
   return SweepCfg<R, SH>::kStages * sweep_stage_bytes<R, SH>();
 }
 
@@ -2137,15 +2194,15 @@ template <class R>
 static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, int shape, cudaStream_t st) {
   if (f.nchunks == 0) return;
   const int gr = sweep_grid(grid, f.nchunks);
-  const bool gen = sizeof(R) == 4 && f.gen && f.wtab;
+  const bool gen = sizeof(R) == 4 && f.gen_ds_max > 0.0f && f.wtab;
   with_shape(shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
     if (gen)
-      sweep_kernel<R, SH, false, true>()<<<gr, kSweepThreads, sweep_smem<R, SH>(f.wtab_pieces), st>>>(
-          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, f.wtab, f.wtab_pieces);
+      sweep_kernel<R, SH, false, true>()<<<gr, sweep_threads(sizeof(R) == 4), sweep_smem<R, SH>(), st>>>(
+          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, f.wtab, f.wtab_pieces, f.gen_ds_max);
     else
       k_sweep<R, SH, false, false><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(
-          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, nullptr, 0);
+          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, nullptr, 0, 0.0f);
   });
 }
 
@@ -2173,13 +2230,13 @@ void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t
 }
 
 template <class R>
-int sweep_blocks_per_sm(int shape, int gen_pieces) {
+int sweep_blocks_per_sm(int shape, bool gen) {
   int n = 0;
   with_shape(shape, [&](auto sh) {
     constexpr int SH = decltype(sh)::value;
-    if (gen_pieces > 0)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<R, SH, false, true>(), kSweepThreads,
-                                                    sweep_smem<R, SH>(gen_pieces));
+    if (gen && sizeof(R) == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<R, SH, false, true>(),
+                                                    sweep_threads(true), sweep_smem<R, SH>());
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<R, SH, false, false>, kSweepThreads,
                                                     sweep_smem<R, SH>());
@@ -2199,18 +2256,18 @@ int sweep_chunk_slots(int precision, int shape) {
 template <class R>
 void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
                           const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
-                          cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces) {
+                          cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max) {
   const int G = sweep_grid(grid, nchunks);
   if (nchunks > 0)
     with_shape(shape, [&](auto sh) {
       constexpr int SH = decltype(sh)::value;
       DevFault<R> none{};
-      if (sizeof(R) == 4 && wtab)
-        sweep_kernel<R, SH, true, true>()<<<G, kSweepThreads, sweep_smem<R, SH>(wtab_pieces), st>>>(
-            none, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces);
+      if (sizeof(R) == 4 && wtab && gen_ds_max > 0.0f)
+        sweep_kernel<R, SH, true, true>()<<<G, sweep_threads(sizeof(R) == 4), sweep_smem<R, SH>(), st>>>(
+            none, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces, gen_ds_max);
       else
-        k_sweep<R, SH, true, false><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(none, fs, chunks, nchunks,
-                                                                                  partial, m_dt, nullptr, 0);
+        k_sweep<R, SH, true, false><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(
+            none, fs, chunks, nchunks, partial, m_dt, nullptr, 0, 0.0f);
     });
   k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial, ahead);
 }
@@ -2422,8 +2479,8 @@ void configure_kernels(const FftGeom& g) {
       allow_smem(k_sweep<R, SH, false, false>, sweep_smem<R, SH>());
       allow_smem(k_sweep<R, SH, true, false>, sweep_smem<R, SH>());
       if constexpr (sizeof(R) == 4) {
-        allow_smem(k_sweep<R, SH, false, true>, sweep_smem<R, SH>(1));
-        allow_smem(k_sweep<R, SH, true, true>, sweep_smem<R, SH>(1));
+        allow_smem(k_sweep<R, SH, false, true>, sweep_smem<R, SH>());
+        allow_smem(k_sweep<R, SH, true, true>, sweep_smem<R, SH>());
       }
     });
   if constexpr (sizeof(R) == 4) {
@@ -2451,9 +2508,11 @@ void configure_kernels(const FftGeom& g) {
 }
 
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
-                                           const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int);
+                                           const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                           float);
 template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
-                                          const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int);
+                                          const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                          float);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
 template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t, int);
@@ -2484,8 +2543,8 @@ template void launch_history_ahead<double>(const DevFault<double>&, int, int, cu
 template void launch_history_ahead<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_history_atomic<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_history_atomic<float>(const DevFault<float>&, int, int, cudaStream_t);
-template int sweep_blocks_per_sm<double>(int, int);
-template int sweep_blocks_per_sm<float>(int, int);
+template int sweep_blocks_per_sm<double>(int, bool);
+template int sweep_blocks_per_sm<float>(int, bool);
 template void launch_weights<double>(const DevFault<double>&, const double*, int, int, double, double,
                                      const int32_t*, const int32_t*, int, cudaStream_t);
 template void launch_weights<float>(const DevFault<float>&, const double*, int, int, double, double,

@@ -93,7 +93,8 @@ struct DevFault {
   // per mode (ds_hi, ds_lo, M^T bits, M^N bits) with ds = c_s k_n dt_min as
   // a two-float sum, and the piecewise-polynomial table of dt C(s)
   long long spin_limit;                    // polls of the sweep's consumer waits before it gives up
-  int gen;                                 // 1: evaluate, 0: stream the materialized weights
+  float gen_ds_max;                        // modes with ds <= this evaluate their weights on chip,
+                                           // the others stream them (0: every mode streams)
   const float4* wgen;
   const float4* wtab;                      // kGenPairs / 2 float4 per piece
   int wtab_pieces;
@@ -107,6 +108,7 @@ struct DevFault {
   double* t;
   unsigned long long* it_sum;
   int* it_max;
+  unsigned long long* it_total;            // [iterations, solves] since the last reset
   const MlpDev* mlp;                       // Newton initial-guess network (NULL: off)
   float* harvest;                          // rows (ln V_prev, ln theta, tau/sigma, a, b, ln V*)
   unsigned long long* harvest_count;
@@ -141,9 +143,9 @@ template <class R> void launch_history(const DevFault<R>& f, int m_dt, int grid,
 // The one-warp-per-chunk sweep with atomic chunk hand-out and per-mode
 // last-arriver sums (writes AT/AN itself); used on caller-owned buffers.
 template <class R> void launch_history_atomic(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
-// Resident CTAs per SM of the bulk-async sweep (with gen_pieces > 0: the
-// on-chip weight form with a table of that many pieces); its chunk length.
-template <class R> int sweep_blocks_per_sm(int shape, int gen_pieces = 0);
+// Resident CTAs per SM of the bulk-async sweep (gen: the form that can
+// evaluate weights on chip); its chunk length.
+template <class R> int sweep_blocks_per_sm(int shape, bool gen = false);
 int sweep_chunk_slots(int precision, int shape);
 // The same sweep with the weights shifted by 2 m_dt, chunk partials only:
 // the part of the next step's sums that does not involve this step's
@@ -156,11 +158,13 @@ template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int
 // tables of all members (member in Chunk::pad), then per (member, mode) sums
 // into each member's AT/AN; cbase[r] is member r's first chunk.
 // wtab (FP32 only, or NULL): the members' shared on-chip weight table of
-// wtab_pieces pieces (every member's wgen must then be set).
+// wtab_pieces pieces (every member's wgen must then be set); modes with
+// ds <= gen_ds_max evaluate their weights from it.
 template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
                                              double4* partial, const int2* mm, int TM, const int64_t* cbase,
                                              int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
-                                             const float4* wtab = nullptr, int wtab_pieces = 0);
+                                             const float4* wtab = nullptr, int wtab_pieces = 0,
+                                             float gen_ds_max = 0.0f);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);
 template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st,

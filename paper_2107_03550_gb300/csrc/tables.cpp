@@ -216,13 +216,16 @@ void build_cheb(double r, double smax, ChebTable* tab) {
 
 // FP32 table of the midpoint weights dt C(s) for the history sweep to evaluate
 // on chip (the weights depend on the mode only through s = c_s k_n (j + 1/2)
-// dt_min): pieces of width kGenH, on each a degree-kGenDeg polynomial in
-// t = 2 (s - q kGenH) / kGenH - 1 in [-1, 1), interpolating C^T and C^N at the
-// Chebyshev nodes (monomial coefficients from the nodal values by Gaussian
-// elimination in FP64, then scaled by dt and rounded to FP32).  Layout per
-// piece: coefficient pairs (T, N) for k = 0..kGenDeg, kGenDeg + 1 pairs.
-// *max_err: the largest |table - dt C| over 16 points per piece, evaluated
-// in FP64 from the rounded coefficients, over dt max|C|.
+// dt_min).  Piece q starts at s = q kGenH and its polynomial of degree
+// kGenDeg holds on [q kGenH, q kGenH + kGenSpan kGenH] (a span longer than
+// the piece, so a run of consecutive lags that starts in piece q stays on its
+// polynomial), in t = (s - q kGenH) / (kGenSpan kGenH / 2) - 1 in [-1, 1];
+// it interpolates C^T and C^N at the Chebyshev nodes of that span (monomial
+// coefficients from the nodal values by Gaussian elimination in FP64, then
+// scaled by dt and rounded to FP32).  Layout per piece: coefficient pairs
+// (T, N) for k = 0..kGenDeg, kGenDeg + 1 pairs.  *max_err: the largest
+// |table - dt C| over 16 points per span, evaluated in FP64 from the rounded
+// coefficients, over dt max|C|.
 void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, int* npieces, double* max_err) {
   const int n = kGenDeg + 1;
   const int P = static_cast<int>(std::ceil(smax / kGenH)) + 1;
@@ -232,8 +235,8 @@ void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, 
   for (int i = 0; i < n; ++i) xi[i] = std::cos(M_PI * (i + 0.5) / n);
   double err = 0.0, cmax = 0.0;
   for (int p = 0; p < P; ++p) {
-    const double a = p * kGenH;
-    for (int i = 0; i < n; ++i) kernel_values(a + 0.5 * kGenH * (xi[i] + 1.0), r, &vT[i], &vN[i]);
+    const double a = p * kGenH, half = 0.5 * kGenSpan * kGenH;
+    for (int i = 0; i < n; ++i) kernel_values(a + half * (xi[i] + 1.0), r, &vT[i], &vN[i]);
     // Vandermonde system V c = v, V[i][k] = xi_i^k, by elimination with partial pivoting
     for (int i = 0; i < n; ++i) {
       double x = 1.0;
@@ -281,7 +284,7 @@ void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, 
         eN = eN * t + out[2 * k + 1];
       }
       double cT, cN;
-      kernel_values(a + 0.5 * kGenH * (t + 1.0), r, &cT, &cN);
+      kernel_values(a + half * (t + 1.0), r, &cT, &cN);
       err = std::max(err, std::max(std::fabs(eT - dt * cT), std::fabs(eN - dt * cN)));
       cmax = std::max(cmax, std::max(std::fabs(cT), std::fabs(cN)));
     }

@@ -76,6 +76,7 @@ _SIGS = {
     "sbiem_get_history": (ctypes.c_int, [_VP, _D, _D]),
     "sbiem_set_history_device": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32]),
     "sbiem_newton_stats": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_int32)]),
+    "sbiem_newton_totals": (ctypes.c_int, [_VP, _I64, _I64, ctypes.c_int]),
     "sbiem_probe_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sbiem_history_sums": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
     "sbiem_history_enqueue": (ctypes.c_int, [_VP, ctypes.c_int64]),
@@ -87,12 +88,12 @@ _SIGS = {
     "sbiem_probe_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_footprint": (ctypes.c_int, [_VP, _I64, _I64]),
-    "sbiem_get_sweep": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+    "sbiem_get_sweep": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), _D, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32), _D]),
-    "sbiem_set_sweep": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "sbiem_set_sweep": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]),
     "sbiem_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_set_output": (ctypes.c_int, [_VP, _output_t, _VP, ctypes.c_int64]),
-    "sbiem_tune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+    "sbiem_tune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _D,
                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
     "sbiem_history_sums_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP,
                                                   _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -535,27 +536,36 @@ class Fault:
         return int(s.value), int(m.value)
 
     def get_sweep(self) -> dict:
-        """History sweep configuration: shape, on-chip weights, CTAs per SM, weight-table error."""
-        sh, ge, ct = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        err = ctypes.c_double()
-        self._check(self.lib.sbiem_get_sweep(self.h, ctypes.byref(sh), ctypes.byref(ge), ctypes.byref(ct),
-                                             ctypes.byref(err)))
-        return {"shape": sh.value, "generated": bool(ge.value), "ctas_per_sm": ct.value, "table_err": err.value}
+        """History sweep configuration: shape, on-chip weight threshold, CTAs per SM, weight-table error."""
+        sh, ct, lc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        th, err = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.sbiem_get_sweep(self.h, ctypes.byref(sh), ctypes.byref(th), ctypes.byref(ct),
+                                             ctypes.byref(lc), ctypes.byref(err)))
+        return {"shape": sh.value, "gen_ds_max": th.value, "ctas_per_sm": ct.value, "lag_ctas_per_sm": lc.value,
+                "table_err": err.value}
 
-    def set_sweep(self, shape: int = 3, generated: bool = True, ctas_per_sm: int = 0) -> None:
-        self._check(self.lib.sbiem_set_sweep(self.h, int(shape), 1 if generated else 0, int(ctas_per_sm)))
+    def set_sweep(self, shape: int = 3, gen_ds_max: float = 0.0625, ctas_per_sm: int = 0) -> None:
+        """gen_ds_max: modes with s step c_s k dt_min at most this evaluate their weights on chip (0: none)."""
+        self._check(self.lib.sbiem_set_sweep(self.h, int(shape), float(gen_ds_max), int(ctas_per_sm)))
 
     def set_wait_limit(self, polls: int = 4194304) -> None:
         """Polls of the history sweep's copy waits before it gives up (0: at once)."""
         self._check(self.lib.sbiem_set_wait_limit(self.h, int(polls)))
 
     def tune(self, reps: int = 5) -> dict:
-        """Autotune the history sweep (shape, weight form, CTAs per SM); returns the choice and its time."""
-        sh, ge, ct = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        """Autotune the history sweep (shape, on-chip weight threshold, CTAs per SM); returns the choice."""
+        sh, ct = ctypes.c_int32(), ctypes.c_int32()
+        th = ctypes.c_double()
         ms = ctypes.c_float()
-        self._check(self.lib.sbiem_tune(self.h, int(reps), ctypes.byref(sh), ctypes.byref(ge), ctypes.byref(ct),
+        self._check(self.lib.sbiem_tune(self.h, int(reps), ctypes.byref(sh), ctypes.byref(th), ctypes.byref(ct),
                                         ctypes.byref(ms)))
-        return {"shape": sh.value, "generated": bool(ge.value), "ctas_per_sm": ct.value, "ms": ms.value}
+        return {"shape": sh.value, "gen_ds_max": th.value, "ctas_per_sm": ct.value, "ms": ms.value}
+
+    def newton_totals(self, reset: bool = False):
+        """(iterations, solves) of every Newton solve since creation or the last reset."""
+        it, so = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.sbiem_newton_totals(self.h, ctypes.byref(it), ctypes.byref(so), 1 if reset else 0))
+        return int(it.value), int(so.value)
 
     def footprint(self):
         hb = ctypes.c_int64()

@@ -71,18 +71,20 @@ def test_large_N_steps_match_oracle(N, precision):
     g2.close()
 
 
-@pytest.mark.parametrize("precision,generated,tol", [(0, False, 1e-10), (1, True, 2e-6), (1, False, 2e-6)])
-def test_history_sums_every_mode_at_65536(precision, generated, tol):
+@pytest.mark.parametrize("precision,gen_ds_max,tol", [(0, 0.0, 1e-10), (1, 1.0 / 64, 2e-6), (1, 1.0 / 256, 2e-6),
+                                                      (1, 0.0, 2e-6)])
+def test_history_sums_every_mode_at_65536(precision, gen_ds_max, tol):
     # the sweep alone on the N = 65536 rings (66 M slots): every mode's sums,
-    # FP32 with the weights evaluated on chip (the default) and streamed
+    # FP32 with the weights of the modes up to ds = 1/64 evaluated on chip
+    # (the default), up to 1/256, and of none
     w = _workload(65536)
     o = oracle_for(w, workers=WORKERS)
     g = gpu_for(w, precision=precision)
     sw = g.get_sweep()
-    assert sw["generated"] == (precision == 1)
+    assert sw["gen_ds_max"] == (1.0 / 64 if precision == 1 else 0.0)
     if precision == 1:
         assert 0 < sw["table_err"] < 2e-7
-    g.set_sweep(3, generated, 0)
+    g.set_sweep(3, gen_ds_max, 0)
     prefill(o, g, seed=17, scale=1e-3)
     for m in (1, 4):
         AT, AN = g.history_sums(m)
@@ -101,11 +103,11 @@ def test_autotuner_keeps_results():
     prefill(o, g, seed=19, scale=1e-3)
     before = g.history_sums(1)
     choice = g.tune(reps=3)
-    assert choice["shape"] in (3, 4) or choice["shape"] in (0, 1, 2)
+    assert choice["shape"] in (3, 4)
     assert choice["ctas_per_sm"] >= 1 and choice["ms"] > 0
     sw = g.get_sweep()
-    assert (sw["shape"], sw["generated"], sw["ctas_per_sm"]) == (choice["shape"], choice["generated"],
-                                                               choice["ctas_per_sm"])
+    assert (sw["shape"], sw["gen_ds_max"], sw["ctas_per_sm"]) == (choice["shape"], choice["gen_ds_max"],
+                                                                choice["ctas_per_sm"])
     after = g.history_sums(1)
     rT, rN = o.history_sums(1)
     for x, y, r in zip(before, after, (rT, rN)):

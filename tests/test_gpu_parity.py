@@ -538,7 +538,7 @@ def test_exact_interval_quadrature_matches_oracle(precision):
     o = oracle_for(w, quadrature="exact")
     g = gpu_for(w, precision=precision, quadrature=1)
     g_mid = gpu_for(w, precision=precision)
-    assert g.get_sweep()["generated"] is False
+    assert g.get_sweep()["gen_ds_max"] == 0.0
     HT, HN = prefill(o, g, seed=41, scale=1e-6)
     g_mid.set_history(HT, HN)
     for s in range(200):
