@@ -640,6 +640,11 @@ def run_ours(a):
         side["quasi_dynamic_path"] = _side(r, "eta_w = 0: static stiffness plus radiation damping, no history; "
                                               "same workload and form")
         r["g"].close()
+        if mlp is not None:
+            # the same form with plain Newton (the learned guess off)
+            r = _measure(torch, a, kind, N, a.precision, rank, world, flush, dev_index, min(a.steps, 1000))
+            side[f"{a.precision}_plain_newton"] = _side(r, "the chosen form without the learned Newton guess")
+            r["g"].close()
         for n2 in (4096, 65536):
             if n2 == N:
                 continue
