@@ -365,7 +365,9 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  * A member whose step fails stops committing (its own status word) while the
  * others go on.  The history convolution is one bulk-async sweep over the
  * members' chunk tables laid end to end (statically partitioned over the
- * CTAs), followed by one per-(member, mode) finish.
+ * CTAs) and the per-(member, mode) sums, in one persistent cooperative
+ * launch with a grid barrier (bounded: see sbiem_batch_set_wait_limit)
+ * between the two.
  *
  * sbiem_batch_create: n member handles (not owned); they must share the
  *   device, the precision and the history sweep shape; chunk_slots must be 0
@@ -386,6 +388,12 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  *   either way up to summation order.
  */
 typedef struct sbiem_batch_s* sbiem_batch_t;
+/* sbiem_batch_set_wait_limit: polls of the persistent history launch's grid
+ *   barrier before a CTA gives up (default SBIEM_WAIT_LIMIT_DEFAULT); a CTA
+ *   that gives up flags every member SBIEM_FLAG_WAIT, so that step is
+ *   rejected for all of them with nothing committed.  0 gives up at once: a
+ *   way to exercise the path without any fault.  Synchronizes; the step
+ *   graph is rebuilt. */
 int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_t chunk_slots);
 void sbiem_batch_destroy(sbiem_batch_t b);
 int sbiem_batch_set_stream(sbiem_batch_t b, void* cuda_stream);
@@ -393,6 +401,7 @@ int sbiem_batch_enqueue(sbiem_batch_t b, int64_t nsteps);
 int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done);
 int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* blocks_per_sm, float* ms);
 int sbiem_batch_set_overlap(sbiem_batch_t b, int on, int* on_out);
+int sbiem_batch_set_wait_limit(sbiem_batch_t b, int64_t polls);
 
 /* ------------------------------------------------ learned Newton initial guess
  * A 5 -> 64 -> 64 -> 1 perceptron (GELU = x Phi(x)) predicts ln V* - ln V_prev

@@ -1725,6 +1725,10 @@ struct sbiem_batch_s {
   bool gen = false;
   float gen_ds_max = 0.0f;  // in force while gen
   int per_sm_plain = 1, per_sm_gen = 1;
+  // the history convolution as one persistent cooperative launch: its grid
+  // barrier's counter and epoch (device), and the barrier's poll limit
+  unsigned* bar = nullptr;
+  long long bar_limit = SBIEM_WAIT_LIMIT_DEFAULT;
   std::vector<void*> allocs;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
@@ -1783,8 +1787,10 @@ int batch_build(sbiem_batch_s* b) {
   b->cbase = static_cast<int64_t*>(batch_alloc(b, sizeof(int64_t) * cbase.size()));
   b->mm = static_cast<int2*>(batch_alloc(b, sizeof(int2) * std::max<size_t>(mm.size(), 1)));
   b->fs = batch_alloc(b, sizeof(DevFault<R>) * b->members.size());
-  if (!b->chunks || !b->partial || !b->cbase || !b->mm || !b->fs)
+  b->bar = static_cast<unsigned*>(batch_alloc(b, 2 * sizeof(unsigned)));
+  if (!b->chunks || !b->partial || !b->cbase || !b->mm || !b->fs || !b->bar)
     return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed");
+  CK(cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream));
   std::vector<DevFault<R>> fs(b->members.size());
   for (size_t r = 0; r < b->members.size(); ++r) {
     DevFault<R> f;
@@ -1808,10 +1814,14 @@ int batch_build(sbiem_batch_s* b) {
 // step's sums without its newest interval (BT, BN; weights shifted by 2).
 template <class R>
 void batch_history(sbiem_batch_s* b, cudaStream_t st, bool ahead = false) {
-  launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
-                          b->cbase, b->shape, ahead ? b->lag_grid : b->hist_grid, ahead ? 2 : 1, st, ahead,
-                          b->gen ? b->wtab : nullptr, b->gen ? b->gen_pieces : 0,
-                          b->gen ? b->gen_ds_max : 0.0f);
+  // one persistent launch: every CTA resident (the grid never exceeds the
+  // occupancy the CTAs per SM were chosen within) and at least one chunk each
+  int grid = ahead ? b->lag_grid : b->hist_grid;
+  if (grid > b->nchunks) grid = b->nchunks > 0 ? b->nchunks : 1;
+  launch_history_persist<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
+                            b->cbase, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
+                            b->gen ? b->gen_pieces : 0, b->gen ? b->gen_ds_max : 0.0f, b->bar, b->bar + 1,
+                            b->bar_limit, static_cast<int>(b->members.size()));
 }
 
 // The groups' two passes as parallel branches of st (joined on st).
@@ -1917,8 +1927,8 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
       b->gen_ds_max = kGenDsMaxDefault;
     }
   }
-  b->per_sm_plain = fp32 ? sweep_blocks_per_sm<float>(b->shape, false) : sweep_blocks_per_sm<double>(b->shape, false);
-  b->per_sm_gen = b->gen ? sweep_blocks_per_sm<float>(b->shape, true) : 0;
+  b->per_sm_plain = fp32 ? persist_blocks_per_sm<float>(b->shape, false) : persist_blocks_per_sm<double>(b->shape, false);
+  b->per_sm_gen = b->gen ? persist_blocks_per_sm<float>(b->shape, true) : 0;
   if (b->per_sm_plain < 1) b->per_sm_plain = 1;
   if (b->per_sm_gen < 1) b->per_sm_gen = 1;
   b->per_sm = b->gen ? b->per_sm_gen : b->per_sm_plain;
@@ -2004,6 +2014,20 @@ int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done) {
     if (rc) return rc;
     if (flags) flags[b->order[q]] = fl;
     if (steps_done) steps_done[b->order[q]] = sd;
+  }
+  return SBIEM_OK;
+}
+
+int sbiem_batch_set_wait_limit(sbiem_batch_t b, int64_t polls) {
+  if (!b || polls < 0) return fail(SBIEM_ERR_INVALID, "NULL batch or negative limit");
+  CK(cudaStreamSynchronize(b->stream));
+  b->bar_limit = polls;
+  if (b->graph) {
+    // the step graph holds the old limit
+    cudaGraphExecDestroy(b->graph);
+    cudaGraphDestroy(b->graph_def);
+    b->graph = nullptr;
+    b->graph_def = nullptr;
   }
   return SBIEM_OK;
 }

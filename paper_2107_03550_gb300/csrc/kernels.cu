@@ -1147,11 +1147,15 @@ __device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* 
 // GEN (FP32): chunks of modes with ds <= gen_ds_max evaluate their weights
 // from the piecewise-polynomial table wtab (wtab_pieces pieces, global,
 // read through L1) instead of copying them with the ring slots.
+// The sweep of one CTA over its chunks [c0, c0 + nk) (nk >= 1).  Returns
+// false when a copy wait gave up; *k_stop is then the first chunk (counted
+// from c0) whose sum was not written, and every copy in flight has landed.
 template <class R, int SH, bool BATCH, bool GEN>
-__global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
-    k_sweep(const __grid_constant__ DevFault<R> f, const DevFault<R>* __restrict__ fs,
-            const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt,
-            const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max) {
+__device__ __forceinline__ bool sweep_chunks(const DevFault<R>& f, const DevFault<R>* __restrict__ fs,
+                                             const Chunk* __restrict__ chunks, int c0, int nk,
+                                             double4* __restrict__ partial, int m_dt,
+                                             const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max,
+                                             long long lim, bool skip_on_status, int* k_stop) {
   static_assert(!GEN || sizeof(R) == 4, "on-chip weights belong to the FP32 form");
   constexpr int S = SweepCfg<R, SH>::kSlots;
   constexpr int kSweepStages = SweepCfg<R, SH>::kStages;
@@ -1164,17 +1168,12 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
   __shared__ Acc4<R> red[2][NW];
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // the per-mode finish may be resident already, waiting for this grid
-  pdl_trigger();
-  const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
-  const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
-  const int nk = c1 - c0;
-  if (nk <= 0) return;
+  *k_stop = nk;
   // one read of the status word (a concurrent pass may set it), taken beside
   // the loads of the first plans and checked once they are in: a uniform
   // exit without a memory round trip of its own before the first copy
   if (tid == 0) {
-    s_skip = BATCH ? 0u : *f.status;
+    s_skip = skip_on_status ? *f.status : 0u;
     for (int s = 0; s < kSweepStages; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -1182,13 +1181,12 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
   for (int j = tid; j < kPlanRing && j < nk; j += NT)
     plan[j] = sweep_plan<R, BATCH, GEN>(f, fs, chunks, c0 + j, m_dt, gen_ds_max);
   __syncthreads();
-  if (s_skip) return;
+  if (s_skip) return true;
   if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
       sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
-  // the consumer waits take the handle's limit (sbiem_set_wait_limit); the
+  // the consumer waits take the caller's limit (sbiem_set_wait_limit); the
   // drain below always waits at the full limit, so no copy is left in flight
-  const long long lim = BATCH ? kSpinLimit : f.spin_limit;
   // each thread accumulates a chunk in R and folds it into a compensated sum
   // over the consecutive chunks of one mode (a run may hold hundreds of
   // chunks: one plain FP32 sum of its thousands of products lost 5e-6); the
@@ -1315,6 +1313,23 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
     for (int q = k; q < nk && q < k + kSweepStages; ++q)
       mbar_wait(&bars[q % kSweepStages], static_cast<unsigned>(q / kSweepStages) & 1u);
   }
+  *k_stop = k;
+  return !stuck;
+}
+
+template <class R, int SH, bool BATCH, bool GEN>
+__global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
+    k_sweep(const __grid_constant__ DevFault<R> f, const DevFault<R>* __restrict__ fs,
+            const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt,
+            const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max) {
+  // the per-mode finish may be resident already, waiting for this grid
+  pdl_trigger();
+  const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
+  const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
+  if (c1 <= c0) return;
+  int k_stop;
+  sweep_chunks<R, SH, BATCH, GEN>(f, fs, chunks, c0, c1 - c0, partial, m_dt, wtab, wtab_pieces, gen_ds_max,
+                                  BATCH ? kSpinLimit : f.spin_limit, !BATCH, &k_stop);
 }
 
 // Per-mode sums of the sweep's segment partials, one thread per mode.  The
@@ -1358,11 +1373,9 @@ __global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* o
 // mm[t]; the member's chunks sit at cbase[member] + its own chunk indices in
 // the ensemble's chunk table.  Members whose step failed are left alone.
 template <class R>
-__global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int TM,
-                                 const int64_t* __restrict__ cbase, int nch, int G,
-                                 const double4* __restrict__ partial, bool ahead) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= TM) return;
+__device__ __forceinline__ void finish_pair(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int t,
+                                            const int64_t* __restrict__ cbase, int nch, int G,
+                                            const double4* __restrict__ partial, bool ahead) {
   const int2 rn = mm[t];
   const DevFault<R>& f = fs[rn.x];
   if (*f.status) return;
@@ -1372,7 +1385,10 @@ __global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2*
   if (E > F) {
     auto c0 = [&](int64_t b) { return b * nch / G; };
     for (int64_t b = ((F + 1) * G + nch - 1) / nch - 1; b < G && c0(b) < E; ++b) {
-      const double4 u = partial[min(c0(b + 1), E) - 1];
+      // L2 reads: the partials come from other CTAs of the same grid in the persistent form
+      const double2* pp = reinterpret_cast<const double2*>(partial + (min(c0(b + 1), E) - 1));
+      const double2 lo = __ldcg(pp), hi = __ldcg(pp + 1);
+      const double4 u = make_double4(lo.x, lo.y, hi.x, hi.y);
       acc.x += u.x;
       acc.y += u.y;
       acc.z += u.z;
@@ -1391,6 +1407,85 @@ __global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2*
     f.AT32[n] = make_float2(static_cast<float>(acc.x), static_cast<float>(acc.y));
     f.AN32[n] = make_float2(static_cast<float>(acc.z), static_cast<float>(acc.w));
   }
+}
+
+template <class R>
+__global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int TM,
+                                 const int64_t* __restrict__ cbase, int nch, int G,
+                                 const double4* __restrict__ partial, bool ahead) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < TM) finish_pair<R>(fs, mm, t, cbase, nch, G, partial, ahead);
+}
+
+// The ensemble's history convolution in one persistent launch (cooperative:
+// every CTA is resident): each CTA sweeps its range of the members' chunk
+// tables laid end to end (its (member, mode-run) sums into the partials),
+// all CTAs meet at a grid barrier, then the grid adds every (member, mode)
+// pair's partials.  The barrier is a counter and an epoch in device memory:
+// the last CTA to arrive resets the counter and advances the epoch; the
+// others poll the epoch at most bar_limit times.  A CTA that gives up sets
+// SBIEM_FLAG_WAIT on every member and leaves (their steps are rejected,
+// nothing is committed); a CTA whose copy wait gave up flags the members of
+// the chunks it did not sum and still arrives.
+struct SweepBarrier {
+  unsigned* count;
+  unsigned* epoch;
+  long long limit;
+  int members;
+};
+
+template <class R, int SH, bool GEN>
+__global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
+    k_sweep_persist(const DevFault<R>* __restrict__ fs, const Chunk* __restrict__ chunks, int nch,
+                    double4* __restrict__ partial, int m_dt, const float4* __restrict__ wtab, int wtab_pieces,
+                    float gen_ds_max, const int2* __restrict__ mm, int TM, const int64_t* __restrict__ cbase,
+                    bool ahead, const SweepBarrier bar) {
+  __shared__ unsigned s_epoch, s_fail;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_epoch = *reinterpret_cast<volatile unsigned*>(bar.epoch);
+    s_fail = 0u;
+  }
+  __syncthreads();
+  const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
+  const int c1 = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nch / gridDim.x);
+  if (c1 > c0) {
+    DevFault<R> none{};
+    int k_stop = c1 - c0;
+    const bool ok = sweep_chunks<R, SH, true, GEN>(none, fs, chunks, c0, c1 - c0, partial, m_dt, wtab, wtab_pieces,
+                                                   gen_ds_max, kSpinLimit, false, &k_stop);
+    if (!ok && tid == 0)
+      for (int c = c0 + k_stop; c < c1; ++c) atomicOr(fs[chunks[c].pad].status, SBIEM_FLAG_WAIT);
+  }
+  // grid barrier (bounded)
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();  // this CTA's partials before its arrival
+    const unsigned ticket = atomicAdd(bar.count, 1u);
+    if (ticket == gridDim.x - 1) {
+      *reinterpret_cast<volatile unsigned*>(bar.count) = 0u;
+      __threadfence();
+      atomicAdd(bar.epoch, 1u);
+    } else {
+      bool released = false;
+      for (long long q = 0; q < bar.limit; ++q) {
+        if (*reinterpret_cast<volatile unsigned*>(bar.epoch) != s_epoch) {
+          released = true;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (!released) {
+        s_fail = 1u;
+        for (int r = 0; r < bar.members; ++r) atomicOr(fs[r].status, SBIEM_FLAG_WAIT);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_fail) return;
+  for (int t = blockIdx.x * blockDim.x + tid; t < TM; t += gridDim.x * blockDim.x)
+    finish_pair<R>(fs, mm, t, cbase, nch, gridDim.x, partial, ahead);
 }
 
 // ------------------------------------------------------------ friction
@@ -1570,10 +1665,25 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
   }
   double xguess = CUDART_NAN;
   if (MLP && f.mlp) {
-    const float feat[kMlpIn] = {static_cast<float>(xstart), static_cast<float>(psip),
-                                static_cast<float>(tau / sig), static_cast<float>(a),
-                                static_cast<float>(have ? ld_b : 0.015)};
-    xguess = xstart + static_cast<double>(mlp_residual_warp(*f.mlp, feat));
+    // The guess is used only when it lies at least 0.1 from ln V_prev, and
+    // the first Newton step from ln V_prev bounds the distance to the root
+    // (from either side a step lands at or above the root, and from above
+    // the root lies within it).  A warp whose every first step is shorter
+    // than 0.1 would land on the same roots without the guess: it skips the
+    // network (warp-uniform, as the network's tiles span the warp).
+    bool need = false;
+    if (have && solve) {
+      const double ex0 = (pass == 1) ? ld_V : ld_V1;
+      const double e = f.eta * ex0, q = tau - sig * fma(a, xstart, c0), sa = sig * a;
+      const double dx0 = q > sa ? -q * (xstart - log(q * f.reta)) / (q + sa) : (q - e) / (e + sa);
+      need = !(fabs(dx0) < 0.1);
+    }
+    if (__any_sync(0xffffffffu, need)) {
+      const float feat[kMlpIn] = {static_cast<float>(xstart), static_cast<float>(psip),
+                                  static_cast<float>(tau / sig), static_cast<float>(a),
+                                  static_cast<float>(have ? ld_b : 0.015)};
+      xguess = xstart + static_cast<double>(mlp_residual_warp(*f.mlp, feat));
+    }
   }
   if (have) {
     double x, exn = -1.0;  // exn: e^x carried by the solve (< 0: not solved)
@@ -1998,10 +2108,17 @@ FftGeom make_geom(int N, int elem_bytes) {
   g.lgN2 = lg - g.lgN1;
   g.N1 = 1 << g.lgN1;
   g.N2 = 1 << g.lgN2;
-  // B rows or columns per CTA: 32 contiguous bytes per global segment
+  // B rows or columns per CTA: 32 contiguous bytes per global segment; for
+  // large N fewer, down to one, while a pass would have fewer than 256 CTAs
+  // (the arrays are then L2 resident, and CTAs on every SM shorten the
+  // latency-bound pass)
   const int B = elem_bytes >= 32 ? 1 : 32 / elem_bytes;
   g.Bc = B < g.N1 ? B : g.N1;
   g.Br = B < g.N2 ? B : g.N2;
+  if (N >= 32768) {
+    while (g.Bc > 1 && g.N1 / g.Bc < 256) g.Bc /= 2;
+    while (g.Br > 1 && g.N2 / g.Br < 256) g.Br /= 2;
+  }
   auto threads = [](int work) {
     int t = work;
     if (t > 256) t = 256;
@@ -2254,6 +2371,55 @@ int sweep_chunk_slots(int precision, int shape) {
 }
 
 template <class R>
+void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
+                            const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
+                            cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max,
+                            unsigned* bar_count, unsigned* bar_epoch, long long bar_limit, int members) {
+  const bool gen = sizeof(R) == 4 && wtab && gen_ds_max > 0.0f;
+  const SweepBarrier bar{bar_count, bar_epoch, bar_limit, members};
+  with_shape(shape, [&](auto sh) {
+    constexpr int SH = decltype(sh)::value;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.dynamicSmemBytes = sweep_smem<R, SH>();
+    if (gen) {
+      if constexpr (sizeof(R) == 4) {
+        cfg.blockDim = dim3(sweep_threads(true));
+        cudaLaunchKernelEx(&cfg, k_sweep_persist<R, SH, true>, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces,
+                           gen_ds_max, mm, TM, cbase, ahead, bar);
+      }
+    } else {
+      cfg.blockDim = dim3(sweep_threads(false));
+      cudaLaunchKernelEx(&cfg, k_sweep_persist<R, SH, false>, fs, chunks, nchunks, partial, m_dt,
+                         static_cast<const float4*>(nullptr), 0, 0.0f, mm, TM, cbase, ahead, bar);
+    }
+  });
+}
+
+// Resident CTAs per SM of the persistent ensemble sweep (its cooperative
+// grid must fit at once).
+template <class R>
+int persist_blocks_per_sm(int shape, bool gen) {
+  int n = 0;
+  with_shape(shape, [&](auto sh) {
+    constexpr int SH = decltype(sh)::value;
+    if (gen && sizeof(R) == 4)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persist<R, SH, sizeof(R) == 4>, sweep_threads(true),
+                                                    sweep_smem<R, SH>());
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persist<R, SH, false>, sweep_threads(false),
+                                                    sweep_smem<R, SH>());
+  });
+  return n;
+}
+
+template <class R>
 void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
                           const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
                           cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max) {
@@ -2478,9 +2644,11 @@ void configure_kernels(const FftGeom& g) {
       constexpr int SH = decltype(shc)::value;
       allow_smem(k_sweep<R, SH, false, false>, sweep_smem<R, SH>());
       allow_smem(k_sweep<R, SH, true, false>, sweep_smem<R, SH>());
+      allow_smem(k_sweep_persist<R, SH, false>, sweep_smem<R, SH>());
       if constexpr (sizeof(R) == 4) {
         allow_smem(k_sweep<R, SH, false, true>, sweep_smem<R, SH>());
         allow_smem(k_sweep<R, SH, true, true>, sweep_smem<R, SH>());
+        allow_smem(k_sweep_persist<R, SH, true>, sweep_smem<R, SH>());
       }
     });
   if constexpr (sizeof(R) == 4) {
@@ -2507,6 +2675,14 @@ void configure_kernels(const FftGeom& g) {
   allow_smem(k_row<double, true>, row_smem<double>(g64));
 }
 
+template void launch_history_persist<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
+                                             const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                             float, unsigned*, unsigned*, long long, int);
+template void launch_history_persist<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
+                                            const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                            float, unsigned*, unsigned*, long long, int);
+template int persist_blocks_per_sm<double>(int, bool);
+template int persist_blocks_per_sm<float>(int, bool);
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
                                            const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
                                            float);

@@ -165,6 +165,18 @@ template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk*
                                              int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
                                              const float4* wtab = nullptr, int wtab_pieces = 0,
                                              float gen_ds_max = 0.0f);
+// The same as one persistent cooperative launch: the sweep, a grid barrier
+// (counter and epoch in device memory, polled at most bar_limit times; on
+// the limit every one of the `members` members is flagged SBIEM_FLAG_WAIT),
+// then every (member, mode) sum.  grid must not exceed the resident CTAs
+// (persist_blocks_per_sm x SMs).
+template <class R> void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
+                                               double4* partial, const int2* mm, int TM, const int64_t* cbase,
+                                               int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
+                                               const float4* wtab, int wtab_pieces, float gen_ds_max,
+                                               unsigned* bar_count, unsigned* bar_epoch, long long bar_limit,
+                                               int members);
+template <class R> int persist_blocks_per_sm(int shape, bool gen);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);
 template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st,

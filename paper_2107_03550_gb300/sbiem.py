@@ -105,6 +105,7 @@ _SIGS = {
     "sbiem_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_batch_set_overlap": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "sbiem_batch_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_set_mlp": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "sbiem_harvest_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_harvest_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _I64, ctypes.c_int]),
@@ -614,6 +615,10 @@ class Batch:
 
     def enqueue(self, nsteps: int) -> None:
         self._check(self.lib.sbiem_batch_enqueue(self.h, int(nsteps)))
+
+    def set_wait_limit(self, polls: int = 4194304) -> None:
+        """Polls of the persistent history launch's grid barrier before a CTA gives up (0: at once)."""
+        self._check(self.lib.sbiem_batch_set_wait_limit(self.h, int(polls)))
 
     def set_overlap(self, on: bool) -> bool:
         """Sweep the next step's history beside the passes (True) or not; returns the old setting."""

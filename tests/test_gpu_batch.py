@@ -75,3 +75,38 @@ def test_failed_member_stops_alone():
     assert fl[2] != 0 and sd[2] == 0
     assert np.all(np.delete(fl, 2) == 0) and np.all(np.delete(sd, 2) == 5)
     b.close()
+
+
+def test_persistent_barrier_limit_rejects_the_step_and_recovers():
+    # The ensemble's history convolution runs as one persistent cooperative
+    # launch with a grid barrier between the sweep and the per-mode sums.
+    # With a barrier limit of zero polls every CTA but the last to arrive
+    # gives up at once (no fault involved) and flags every member: the step
+    # is rejected for all of them with nothing committed.  With the default
+    # limit back the batch steps bitwise like an untouched one.
+    from paper_2107_03550_gb300.sbiem import FLAG_WAIT, Batch
+    ws = _ensemble(400)
+    mem = [gpu_for(w, precision=1) for w in ws]
+    ref = [gpu_for(w, precision=1) for w in ws]
+    b, bref = Batch(mem), Batch(ref)
+    before = [g.get_state() for g in mem]
+    b.set_wait_limit(0)
+    b.enqueue(2)
+    fl, sd = b.status()
+    assert np.all(fl & FLAG_WAIT) and np.all(sd == 0)
+    for g, s0 in zip(mem, before):
+        s1 = g.get_state()
+        for k in ("delta", "V", "theta"):
+            assert np.array_equal(s0[k], s1[k]), k
+        g.status(clear=True)
+    b.set_wait_limit()
+    b.enqueue(10)
+    bref.enqueue(10)
+    fl, sd = b.status()
+    assert np.all(fl == 0) and np.all(sd == 10)
+    for g1, g2 in zip(mem, ref):
+        s1, s2 = g1.get_state(), g2.get_state()
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert np.array_equal(s1[k], s2[k]), k
+    b.close()
+    bref.close()
