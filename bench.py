@@ -562,6 +562,7 @@ def _ensemble(torch, a, rank, world, clock_index):
     if np.any(fl):
         raise RuntimeError("ensemble warm-up failed")
     K = a.steps
+    info = b.get_sweep()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(clock_index)
     if world > 1:
@@ -580,11 +581,28 @@ def _ensemble(torch, a, rank, world, clock_index):
     if np.any(fl):
         raise RuntimeError("ensemble step failed")
     total_s = e0.elapsed_time(e1) / 1e3
+    # the same batch with the history convolution in the other form: two
+    # launches (sweep, then the per-(member, mode) sums) or one persistent
+    # launch with a grid barrier, whichever the autotuner did not keep
+    b.set_persistent(not info["persistent"])
+    K2 = max(10, K // 5)
+    b.enqueue(3)
+    torch.cuda.synchronize()
+    e0.record()
+    b.enqueue(K2)
+    e1.record()
+    torch.cuda.synchronize()
+    fl, _ = b.status()
+    if np.any(fl):
+        raise RuntimeError("ensemble step (two-launch form) failed")
+    two_s = e0.elapsed_time(e1) / 1e3 / K2
+    b.set_persistent(info["persistent"])
     if world > 1:
         t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_s = float(t.item())
     bytes_ring = slots * (16 if a.precision == "fp32" else 32)
+    peak, peak_kind = _peaks()
     line = {
         "metric": METRIC, "value": world * elems * K / total_s, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
@@ -594,7 +612,21 @@ def _ensemble(torch, a, rank, world, clock_index):
                                "full; dt = dt_min", "elements_per_step": elems, "history_slots": slots,
                    "ring_bytes_per_step": bytes_ring, "precision": a.precision,
                    "parallelism": f"replicas x{world}", "l2": "rings larger than L2 (no flush)",
-                   "tuned": {"chunk_slots": chunk, "sweep_ctas_per_sm": blocks, "sweep_ms": tune_ms}},
+                   "tuned": {"chunk_slots": chunk, "sweep_ctas_per_sm": blocks, "sweep_ms": tune_ms,
+                             "shape": info["shape"], "gen_ds_max": info["gen_ds_max"], "overlap": info["overlap"],
+                             "distinct_weight_arrays": info["distinct_weights"]},
+                   "history_form": "one persistent launch" if info["persistent"] else "two launches",
+                   "side": {"other_history_form": {
+                       "value": world * elems / two_s, "ms_per_step": 1e3 * two_s, "steps": K2,
+                       "what": ("history convolution as a sweep launch and a sum launch (no grid barrier)"
+                                if info["persistent"] else
+                                "history convolution as one persistent launch with a grid barrier")
+                               + "; the rest of the step unchanged"}}},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep_persist" if info["persistent"] else "k_sweep", "achieved": bytes_ring / (tune_ms * 1e-3) / 1e9,
+                     "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)", "unit": "GB/s",
+                     "frac": bytes_ring / (tune_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                     "algorithmic_bytes": "ring slots x 2 fields x complex", "ms_per_launch": tune_ms,
+                     "timing": "median of the autotuner's event-timed launches of the history convolution alone"},
         "ring_GBps_over_step": bytes_ring / (total_s / K) / 1e9,
         "clocks": clk, "e2e": None, "gpu_launches": None, "cpu_baseline": None,
     }

@@ -376,10 +376,19 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  * sbiem_batch_enqueue: nsteps steps of each member's dt_min, asynchronous.
  * sbiem_batch_status: synchronize; per member (caller order) status flags
  *   and committed steps (arrays of n, may be NULL).
+ * Members with bitwise equal weights (equal N, length, c_s, c_p, dt_min,
+ *   windows, quadrature and precision) read one copy of them, and the sweep
+ *   then copies ring slots under an L2 evict-first policy so that the shared
+ *   weight runs stay in L2.
  * sbiem_batch_tune: autotuner -- times the batched history convolution for
- *   1 .. (occupancy limit) resident sweep CTAs per SM, reps timed launches
- *   each (median), and keeps the fastest; returns the chunk length, the
- *   choice and its time.  It also times the overlapped sweep (one CTA per
+ *   every sweep shape that keeps the members' chunk length, each weight form
+ *   (streamed, or evaluated on chip for the modes with s step up to 1/256 or
+ *   1/64 when the members share c_s, c_p and dt_min) and 1 .. (occupancy
+ *   limit) resident sweep CTAs per SM, reps timed launches each (median), and
+ *   keeps the fastest, then the faster of the one-launch and two-launch
+ *   forms (sbiem_batch_set_persistent); returns the chunk length, the CTAs
+ *   per SM chosen and the time (sbiem_batch_get_sweep gives the rest).  It also times the
+ *   overlapped sweep (one CTA per
  *   SM beside the passes) and the passes, and makes later steps sweep the
  *   next step's history beside the passes when that is faster (a new batch
  *   steps without overlap).  The committed state is not changed.
@@ -402,6 +411,21 @@ int sbiem_batch_status(sbiem_batch_t b, uint32_t* flags, int64_t* steps_done);
 int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_slots, int* blocks_per_sm, float* ms);
 int sbiem_batch_set_overlap(sbiem_batch_t b, int on, int* on_out);
 int sbiem_batch_set_wait_limit(sbiem_batch_t b, int64_t polls);
+/* sbiem_batch_get_sweep: the batch's history-convolution configuration; any
+ *   pointer may be NULL.  shape: sweep shape (as sbiem_get_sweep);
+ *   gen_ds_max: largest s step of a mode whose weights are evaluated on chip
+ *   (0: every weight streamed); ctas_per_sm: resident CTAs per SM of the
+ *   persistent launch; overlap: 1 when the next step's sweep runs beside the
+ *   passes; distinct_weights: weight arrays read (members sharing one count
+ *   once); persistent: 1 for the one-launch form, 0 for the two-launch form.
+ * sbiem_batch_set_persistent: the history convolution as one persistent
+ *   cooperative launch (1, the default) or as a sweep launch followed by a
+ *   per-(member, mode) sum launch (0, no grid barrier).  Results are bitwise
+ *   equal either way.  *on_out (may be NULL) gets the form in force before
+ *   the call.  Synchronizes; the step graph is rebuilt. */
+int sbiem_batch_get_sweep(sbiem_batch_t b, int32_t* shape, double* gen_ds_max, int32_t* ctas_per_sm,
+                          int32_t* overlap, int32_t* distinct_weights, int32_t* persistent);
+int sbiem_batch_set_persistent(sbiem_batch_t b, int on, int* on_out);
 
 /* ------------------------------------------------ learned Newton initial guess
  * A 5 -> 64 -> 64 -> 1 perceptron (GELU = x Phi(x)) predicts ln V* - ln V_prev

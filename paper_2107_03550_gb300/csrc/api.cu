@@ -1729,6 +1729,11 @@ struct sbiem_batch_s {
   // barrier's counter and epoch (device), and the barrier's poll limit
   unsigned* bar = nullptr;
   long long bar_limit = SBIEM_WAIT_LIMIT_DEFAULT;
+  // members whose weights are equal read one copy of them (the first such
+  // member's); with any shared the sweep copies ring slots evict-first
+  int distinct_weights = 0;
+  bool shared_weights = false;
+  bool persistent = true;  // one cooperative launch; false: sweep launch + sum launch
   std::vector<void*> allocs;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
@@ -1762,8 +1767,15 @@ void* batch_alloc(sbiem_batch_s* b, size_t bytes) {
   return p;
 }
 
-// Members with equal N, grid, material, truncation and precision have equal
-// weights and can share a sweep.
+// Members with equal N, length, c_s, c_p, dt_min, windows (both fields),
+// quadrature and precision have bitwise equal weights: the weight builder
+// reads nothing else.
+bool same_weights(const sbiem_s* a, const sbiem_s* b) {
+  return a->fp32() == b->fp32() && a->p.N == b->p.N && a->L == b->L && a->dt_min == b->dt_min &&
+         a->p.cs == b->p.cs && a->p.cp == b->p.cp && a->p.quadrature == b->p.quadrature && a->MT == b->MT &&
+         a->MN == b->MN;
+}
+
 // Ensemble chunk table: the members' own chunk tables one after another
 // (member index in Chunk::pad), each member's first chunk, the (member,
 // mode) list of the per-mode sums; member descriptors on the device.
@@ -1797,8 +1809,22 @@ int batch_build(sbiem_batch_s* b) {
     if constexpr (sizeof(R) == 8) f = b->members[r]->f64;
     else f = b->members[r]->f32;
     f.newton_epw = 32;  // the batched Newton launch covers 32 elements per warp
+    // the weights of the first member with equal weights
+    for (size_t q = 0; q < r; ++q)
+      if (same_weights(b->members[q], b->members[r])) {
+        f.w = fs[q].w;
+        f.wgen = fs[q].wgen;
+        break;
+      }
     fs[r] = f;
   }
+  b->distinct_weights = 0;
+  for (size_t r = 0; r < fs.size(); ++r) {
+    bool first = true;
+    for (size_t q = 0; q < r && first; ++q) first = fs[q].w != fs[r].w;
+    b->distinct_weights += first ? 1 : 0;
+  }
+  b->shared_weights = b->distinct_weights < static_cast<int>(fs.size());
   if (!ch.empty())
     CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->cbase, cbase.data(), sizeof(int64_t) * cbase.size(), cudaMemcpyHostToDevice, b->stream));
@@ -1817,11 +1843,20 @@ void batch_history(sbiem_batch_s* b, cudaStream_t st, bool ahead = false) {
   // one persistent launch: every CTA resident (the grid never exceeds the
   // occupancy the CTAs per SM were chosen within) and at least one chunk each
   int grid = ahead ? b->lag_grid : b->hist_grid;
+  const bool gen = sizeof(R) == 4 && b->gen;
+  const int resident = b->sm_count * std::max(1, persist_blocks_per_sm<R>(b->shape, gen));
+  if (grid > resident) grid = resident;
   if (grid > b->nchunks) grid = b->nchunks > 0 ? b->nchunks : 1;
+  if (!b->persistent) {
+    launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm,
+                            b->TM, b->cbase, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
+                            b->gen ? b->gen_pieces : 0, b->gen ? b->gen_ds_max : 0.0f, b->shared_weights);
+    return;
+  }
   launch_history_persist<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
                             b->cbase, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
                             b->gen ? b->gen_pieces : 0, b->gen ? b->gen_ds_max : 0.0f, b->bar, b->bar + 1,
-                            b->bar_limit, static_cast<int>(b->members.size()));
+                            b->bar_limit, static_cast<int>(b->members.size()), b->shared_weights);
 }
 
 // The groups' two passes as parallel branches of st (joined on st).
@@ -2032,6 +2067,34 @@ int sbiem_batch_set_wait_limit(sbiem_batch_t b, int64_t polls) {
   return SBIEM_OK;
 }
 
+int sbiem_batch_get_sweep(sbiem_batch_t b, int32_t* shape, double* gen_ds_max, int32_t* ctas_per_sm,
+                          int32_t* overlap, int32_t* distinct_weights, int32_t* persistent) {
+  if (!b) return fail(SBIEM_ERR_INVALID, "NULL batch");
+  if (shape) *shape = b->shape;
+  if (gen_ds_max) *gen_ds_max = b->gen ? static_cast<double>(b->gen_ds_max) : 0.0;
+  if (ctas_per_sm) *ctas_per_sm = b->hist_grid / (b->sm_count > 0 ? b->sm_count : 1);
+  if (overlap) *overlap = b->overlap ? 1 : 0;
+  if (distinct_weights) *distinct_weights = b->distinct_weights;
+  if (persistent) *persistent = b->persistent ? 1 : 0;
+  return SBIEM_OK;
+}
+
+int sbiem_batch_set_persistent(sbiem_batch_t b, int on, int* on_out) {
+  if (!b || (on != 0 && on != 1)) return fail(SBIEM_ERR_INVALID, "bad argument");
+  if (on_out) *on_out = b->persistent ? 1 : 0;
+  if ((on == 1) == b->persistent) return SBIEM_OK;
+  CK(cudaStreamSynchronize(b->stream));
+  b->persistent = on == 1;
+  if (b->graph) {
+    // the step graph holds the other form
+    cudaGraphExecDestroy(b->graph);
+    cudaGraphDestroy(b->graph_def);
+    b->graph = nullptr;
+    b->graph_def = nullptr;
+  }
+  return SBIEM_OK;
+}
+
 int sbiem_batch_set_overlap(sbiem_batch_t b, int on, int* on_out) {
   if (!b || (on != 0 && on != 1)) return fail(SBIEM_ERR_INVALID, "bad argument");
   if (on_out) *on_out = b->overlap ? 1 : 0;
@@ -2058,14 +2121,25 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
   int best_b = b->hist_grid / b->sm_count;
   bool best_gen = b->gen;
   float best_thr = b->gen_ds_max;
+  int best_shape = b->shape;
   const bool can_gen = b->wtab != nullptr;
   std::vector<float> thr = {0.0f};
   if (can_gen)
     for (double v : {kGenDsBlockMax / 4.0, kGenDsBlockMax}) thr.push_back(static_cast<float>(v));
+  // the sweep shapes that keep the members' chunk length (their chunk
+  // tables and per-mode chunk ranges stay valid)
+  std::vector<int> shapes;
+  const int prec = b->fp32 ? 1 : 0;
+  for (int sh = 0; sh <= 4; ++sh)
+    if (sweep_chunk_slots(prec, sh) == b->chunk_slots) shapes.push_back(sh);
+  for (int sh : shapes)
   for (float tv : thr) {
+    b->shape = sh;
     b->gen = tv > 0.0f;
     b->gen_ds_max = tv;
-    const int lim = b->gen ? b->per_sm_gen : b->per_sm_plain;
+    const int lim = b->gen ? persist_blocks_per_sm<float>(sh, true)
+                           : (b->fp32 ? persist_blocks_per_sm<float>(sh, false)
+                                      : persist_blocks_per_sm<double>(sh, false));
     for (int bl = 1; bl <= lim; ++bl) {
       b->hist_grid = b->sm_count * bl;
       // one untimed launch, then reps timed ones; take the median
@@ -2089,13 +2163,43 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
         best_b = bl;
         best_gen = b->gen;
         best_thr = tv;
+        best_shape = sh;
       }
     }
   }
+  b->shape = best_shape;
   b->gen = best_gen;
   b->gen_ds_max = best_thr;
+  b->per_sm_plain = b->fp32 ? persist_blocks_per_sm<float>(b->shape, false)
+                            : persist_blocks_per_sm<double>(b->shape, false);
+  b->per_sm_gen = b->gen ? persist_blocks_per_sm<float>(b->shape, true) : b->per_sm_gen;
   b->per_sm = b->gen ? b->per_sm_gen : b->per_sm_plain;
   b->hist_grid = b->sm_count * best_b;
+  // the one-launch form or the two-launch form, whichever is faster (the
+  // two agree bitwise)
+  {
+    float tf[2] = {0.f, 0.f};
+    for (int form = 0; form < 2; ++form) {
+      b->persistent = form == 1;
+      if (b->fp32) batch_history<float>(b, b->stream);
+      else batch_history<double>(b, b->stream);
+      std::vector<float> t;
+      for (int k = 0; k < reps; ++k) {
+        CK(cudaEventRecord(e0, b->stream));
+        if (b->fp32) batch_history<float>(b, b->stream);
+        else batch_history<double>(b, b->stream);
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+      }
+      std::sort(t.begin(), t.end());
+      tf[form] = t[t.size() / 2];
+    }
+    b->persistent = tf[1] <= tf[0];
+    best = std::min(tf[0], tf[1]);
+  }
   // overlap or not: the overlapped step takes about max(lag sweep, passes),
   // the plain one sweep + passes.  The passes write only staging arrays, so
   // timing them leaves the committed state alone; the status words they may

@@ -1036,6 +1036,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
+// The same copy with an L2 eviction policy (createpolicy): the ensemble
+// sweep marks its ring slots evict-first so that the weight runs its
+// members share stay in L2.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, unsigned bytes, uint64_t* bar,
+                                              uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
 // s + c += a with the rounding error of the addition carried in c (Knuth's
 // TwoSum; FP32 only -- an FP64 sum needs no compensation here).
 __device__ __forceinline__ void two_sum_add(float& s, float& c, float a) {
@@ -1128,17 +1145,24 @@ __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const Dev
   return pl;
 }
 
-// Thread 0: start the copies of a planned chunk into a stage.
+// Thread 0: start the copies of a planned chunk into a stage (ring_pol != 0:
+// the ring pieces under that L2 policy).
 template <class R, int S>
-__device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* stage_buf, uint64_t* bar) {
+__device__ __forceinline__ void sweep_issue(const SweepPlan& pl, unsigned char* stage_buf, uint64_t* bar,
+                                            uint64_t ring_pol) {
   if (pl.len == 0) {
     mbar_arrive(bar);
     return;
   }
   unsigned char* sw = stage_buf + static_cast<size_t>(S) * sizeof(Slot<R>);
   mbar_expect_tx(bar, pl.b1 + pl.b2 + pl.bw);
-  bulk_g2s(stage_buf, pl.r1, pl.b1, bar);
-  if (pl.b2) bulk_g2s(stage_buf + pl.b1, pl.r2, pl.b2, bar);
+  if (ring_pol) {
+    bulk_g2s_hint(stage_buf, pl.r1, pl.b1, bar, ring_pol);
+    if (pl.b2) bulk_g2s_hint(stage_buf + pl.b1, pl.r2, pl.b2, bar, ring_pol);
+  } else {
+    bulk_g2s(stage_buf, pl.r1, pl.b1, bar);
+    if (pl.b2) bulk_g2s(stage_buf + pl.b1, pl.r2, pl.b2, bar);
+  }
   if (pl.bw) bulk_g2s(sw, pl.wsrc, pl.bw, bar);
 }
 
@@ -1155,7 +1179,8 @@ __device__ __forceinline__ bool sweep_chunks(const DevFault<R>& f, const DevFaul
                                              const Chunk* __restrict__ chunks, int c0, int nk,
                                              double4* __restrict__ partial, int m_dt,
                                              const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max,
-                                             long long lim, bool skip_on_status, int* k_stop) {
+                                             long long lim, bool skip_on_status, int* k_stop,
+                                             bool ring_evict_first = false) {
   static_assert(!GEN || sizeof(R) == 4, "on-chip weights belong to the FP32 form");
   constexpr int S = SweepCfg<R, SH>::kSlots;
   constexpr int kSweepStages = SweepCfg<R, SH>::kStages;
@@ -1168,6 +1193,7 @@ __device__ __forceinline__ bool sweep_chunks(const DevFault<R>& f, const DevFaul
   __shared__ Acc4<R> red[2][NW];
   __shared__ unsigned s_skip;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint64_t ring_pol = ring_evict_first && tid == 0 ? l2_policy_evict_first() : 0;
   *k_stop = nk;
   // one read of the status word (a concurrent pass may set it), taken beside
   // the loads of the first plans and checked once they are in: a uniform
@@ -1184,7 +1210,7 @@ __device__ __forceinline__ bool sweep_chunks(const DevFault<R>& f, const DevFaul
   if (s_skip) return true;
   if (tid == 0)
     for (int k = 0; k < kSweepStages && k < nk; ++k)
-      sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k]);
+      sweep_issue<R, S>(plan[k], sweep_smem + k * SB, &bars[k], ring_pol);
   // the consumer waits take the caller's limit (sbiem_set_wait_limit); the
   // drain below always waits at the full limit, so no copy is left in flight
   // each thread accumulates a chunk in R and folds it into a compensated sum
@@ -1288,7 +1314,7 @@ __device__ __forceinline__ bool sweep_chunks(const DevFault<R>& f, const DevFaul
     if (tid == 0) {
       // the stage was read by every thread (barrier above): refill it first
       if (k + kSweepStages < nk)
-        sweep_issue<R, S>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s]);
+        sweep_issue<R, S>(plan[(k + kSweepStages) % kPlanRing], sweep_smem + s * SB, &bars[s], ring_pol);
       double4 out = make_double4(0.0, 0.0, 0.0, 0.0);
       if (seg_end) {
         Acc4<R> t = red[k & 1][0];
@@ -1321,7 +1347,7 @@ template <class R, int SH, bool BATCH, bool GEN>
 __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
     k_sweep(const __grid_constant__ DevFault<R> f, const DevFault<R>* __restrict__ fs,
             const Chunk* __restrict__ chunks, int nch, double4* __restrict__ partial, int m_dt,
-            const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max) {
+            const float4* __restrict__ wtab, int wtab_pieces, float gen_ds_max, bool ring_evict_first) {
   // the per-mode finish may be resident already, waiting for this grid
   pdl_trigger();
   const int c0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nch / gridDim.x);
@@ -1329,7 +1355,7 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
   if (c1 <= c0) return;
   int k_stop;
   sweep_chunks<R, SH, BATCH, GEN>(f, fs, chunks, c0, c1 - c0, partial, m_dt, wtab, wtab_pieces, gen_ds_max,
-                                  BATCH ? kSpinLimit : f.spin_limit, !BATCH, &k_stop);
+                                  BATCH ? kSpinLimit : f.spin_limit, !BATCH, &k_stop, ring_evict_first);
 }
 
 // Per-mode sums of the sweep's segment partials, one thread per mode.  The
@@ -1439,7 +1465,7 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
     k_sweep_persist(const DevFault<R>* __restrict__ fs, const Chunk* __restrict__ chunks, int nch,
                     double4* __restrict__ partial, int m_dt, const float4* __restrict__ wtab, int wtab_pieces,
                     float gen_ds_max, const int2* __restrict__ mm, int TM, const int64_t* __restrict__ cbase,
-                    bool ahead, const SweepBarrier bar) {
+                    bool ahead, const SweepBarrier bar, bool ring_evict_first) {
   __shared__ unsigned s_epoch, s_fail;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -1453,7 +1479,7 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
     DevFault<R> none{};
     int k_stop = c1 - c0;
     const bool ok = sweep_chunks<R, SH, true, GEN>(none, fs, chunks, c0, c1 - c0, partial, m_dt, wtab, wtab_pieces,
-                                                   gen_ds_max, kSpinLimit, false, &k_stop);
+                                                   gen_ds_max, kSpinLimit, false, &k_stop, ring_evict_first);
     if (!ok && tid == 0)
       for (int c = c0 + k_stop; c < c1; ++c) atomicOr(fs[chunks[c].pad].status, SBIEM_FLAG_WAIT);
   }
@@ -2316,10 +2342,10 @@ static void launch_sweep(const DevFault<R>& f, int m_dt, int grid, int shape, cu
     constexpr int SH = decltype(sh)::value;
     if (gen)
       sweep_kernel<R, SH, false, true>()<<<gr, sweep_threads(sizeof(R) == 4), sweep_smem<R, SH>(), st>>>(
-          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, f.wtab, f.wtab_pieces, f.gen_ds_max);
+          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, f.wtab, f.wtab_pieces, f.gen_ds_max, false);
     else
       k_sweep<R, SH, false, false><<<gr, kSweepThreads, sweep_smem<R, SH>(), st>>>(
-          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, nullptr, 0, 0.0f);
+          f, nullptr, f.chunks, f.nchunks, f.partial, m_dt, nullptr, 0, 0.0f, false);
   });
 }
 
@@ -2374,7 +2400,8 @@ template <class R>
 void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
                             const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
                             cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max,
-                            unsigned* bar_count, unsigned* bar_epoch, long long bar_limit, int members) {
+                            unsigned* bar_count, unsigned* bar_epoch, long long bar_limit, int members,
+                            bool ring_evict_first) {
   const bool gen = sizeof(R) == 4 && wtab && gen_ds_max > 0.0f;
   const SweepBarrier bar{bar_count, bar_epoch, bar_limit, members};
   with_shape(shape, [&](auto sh) {
@@ -2392,12 +2419,12 @@ void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchu
       if constexpr (sizeof(R) == 4) {
         cfg.blockDim = dim3(sweep_threads(true));
         cudaLaunchKernelEx(&cfg, k_sweep_persist<R, SH, true>, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces,
-                           gen_ds_max, mm, TM, cbase, ahead, bar);
+                           gen_ds_max, mm, TM, cbase, ahead, bar, ring_evict_first);
       }
     } else {
       cfg.blockDim = dim3(sweep_threads(false));
       cudaLaunchKernelEx(&cfg, k_sweep_persist<R, SH, false>, fs, chunks, nchunks, partial, m_dt,
-                         static_cast<const float4*>(nullptr), 0, 0.0f, mm, TM, cbase, ahead, bar);
+                         static_cast<const float4*>(nullptr), 0, 0.0f, mm, TM, cbase, ahead, bar, ring_evict_first);
     }
   });
 }
@@ -2422,7 +2449,8 @@ int persist_blocks_per_sm(int shape, bool gen) {
 template <class R>
 void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
                           const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
-                          cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max) {
+                          cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max,
+                          bool ring_evict_first) {
   const int G = sweep_grid(grid, nchunks);
   if (nchunks > 0)
     with_shape(shape, [&](auto sh) {
@@ -2430,10 +2458,10 @@ void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunk
       DevFault<R> none{};
       if (sizeof(R) == 4 && wtab && gen_ds_max > 0.0f)
         sweep_kernel<R, SH, true, true>()<<<G, sweep_threads(sizeof(R) == 4), sweep_smem<R, SH>(), st>>>(
-            none, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces, gen_ds_max);
+            none, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces, gen_ds_max, ring_evict_first);
       else
         k_sweep<R, SH, true, false><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(
-            none, fs, chunks, nchunks, partial, m_dt, nullptr, 0, 0.0f);
+            none, fs, chunks, nchunks, partial, m_dt, nullptr, 0, 0.0f, ring_evict_first);
     });
   k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial, ahead);
 }
@@ -2677,18 +2705,18 @@ void configure_kernels(const FftGeom& g) {
 
 template void launch_history_persist<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
                                              const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
-                                             float, unsigned*, unsigned*, long long, int);
+                                             float, unsigned*, unsigned*, long long, int, bool);
 template void launch_history_persist<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
                                             const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
-                                            float, unsigned*, unsigned*, long long, int);
+                                            float, unsigned*, unsigned*, long long, int, bool);
 template int persist_blocks_per_sm<double>(int, bool);
 template int persist_blocks_per_sm<float>(int, bool);
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
                                            const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
-                                           float);
+                                           float, bool);
 template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
                                           const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
-                                          float);
+                                          float, bool);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);
 template void launch_commit_batch<double>(const DevFault<double>*, int, int, int, cudaStream_t, int);

@@ -164,18 +164,20 @@ template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk*
                                              double4* partial, const int2* mm, int TM, const int64_t* cbase,
                                              int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
                                              const float4* wtab = nullptr, int wtab_pieces = 0,
-                                             float gen_ds_max = 0.0f);
+                                             float gen_ds_max = 0.0f, bool ring_evict_first = false);
 // The same as one persistent cooperative launch: the sweep, a grid barrier
 // (counter and epoch in device memory, polled at most bar_limit times; on
 // the limit every one of the `members` members is flagged SBIEM_FLAG_WAIT),
 // then every (member, mode) sum.  grid must not exceed the resident CTAs
-// (persist_blocks_per_sm x SMs).
+// (persist_blocks_per_sm x SMs).  ring_evict_first: ring slots are copied
+// under an L2 evict-first policy (members share their weight runs, which
+// then stay in L2).
 template <class R> void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
                                                double4* partial, const int2* mm, int TM, const int64_t* cbase,
                                                int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
                                                const float4* wtab, int wtab_pieces, float gen_ds_max,
                                                unsigned* bar_count, unsigned* bar_epoch, long long bar_limit,
-                                               int members);
+                                               int members, bool ring_evict_first);
 template <class R> int persist_blocks_per_sm(int shape, bool gen);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);

@@ -106,6 +106,10 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_float)]),
     "sbiem_batch_set_overlap": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "sbiem_batch_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "sbiem_batch_get_sweep": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "sbiem_batch_set_persistent": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "sbiem_set_mlp": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "sbiem_harvest_enable": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_harvest_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64, _I64, ctypes.c_int]),
@@ -620,6 +624,21 @@ class Batch:
         """Polls of the persistent history launch's grid barrier before a CTA gives up (0: at once)."""
         self._check(self.lib.sbiem_batch_set_wait_limit(self.h, int(polls)))
 
+    def get_sweep(self) -> dict:
+        """History-convolution configuration: shape, weight form, CTAs per SM, overlap, shared weights, form."""
+        sh, thr, ctas, ov, dw, pe = (ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32(),
+                                     ctypes.c_int32(), ctypes.c_int32())
+        self._check(self.lib.sbiem_batch_get_sweep(self.h, ctypes.byref(sh), ctypes.byref(thr), ctypes.byref(ctas),
+                                                   ctypes.byref(ov), ctypes.byref(dw), ctypes.byref(pe)))
+        return {"shape": sh.value, "gen_ds_max": thr.value, "ctas_per_sm": ctas.value, "overlap": bool(ov.value),
+                "distinct_weights": dw.value, "persistent": bool(pe.value)}
+
+    def set_persistent(self, on: bool) -> bool:
+        """One persistent launch (True, the default) or a sweep launch plus a sum launch; returns the old form."""
+        old = ctypes.c_int()
+        self._check(self.lib.sbiem_batch_set_persistent(self.h, 1 if on else 0, ctypes.byref(old)))
+        return bool(old.value)
+
     def set_overlap(self, on: bool) -> bool:
         """Sweep the next step's history beside the passes (True) or not; returns the old setting."""
         old = ctypes.c_int()
@@ -634,7 +653,8 @@ class Batch:
         return np.array(list(fl), dtype=np.uint32), sd
 
     def tune(self, reps: int = 5):
-        """Autotune chunk length and resident CTAs of the batched history convolution."""
+        """Autotune the batched history convolution (shape, weight form, resident CTAs per SM) and the
+        overlap; returns (chunk length, CTAs per SM, ms)."""
         c = ctypes.c_int64()
         b = ctypes.c_int()
         ms = ctypes.c_float()

@@ -110,3 +110,56 @@ def test_persistent_barrier_limit_rejects_the_step_and_recovers():
             assert np.array_equal(s1[k], s2[k]), k
     b.close()
     bref.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_launch_form_equals_persistent_and_weights_shared(precision):
+    # The members of one N share their weights (equal N, dx, material, dt_min,
+    # windows): one weight array per size is read.  The two-launch form (sweep,
+    # then the per-(member, mode) sums in a second launch) partitions the chunks
+    # the same way and adds in the same order as the persistent launch, so the
+    # two step bitwise alike.
+    from paper_2107_03550_gb300.sbiem import Batch
+    ws = _ensemble(500)
+    a = [gpu_for(w, precision=precision) for w in ws]
+    c = [gpu_for(w, precision=precision) for w in ws]
+    ba, bc = Batch(a), Batch(c)
+    info = ba.get_sweep()
+    assert info["persistent"] and info["distinct_weights"] == 3
+    assert bc.set_persistent(False) is True
+    assert bc.get_sweep()["persistent"] is False
+    ba.enqueue(12)
+    bc.enqueue(12)
+    for b in (ba, bc):
+        fl, sd = b.status()
+        assert np.all(fl == 0) and np.all(sd == 12)
+    for g1, g2 in zip(a, c):
+        s1, s2 = g1.get_state(), g2.get_state()
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert np.array_equal(s1[k], s2[k]), k
+    ba.close()
+    bc.close()
+
+
+def test_batch_tuner_choice_is_reported_and_keeps_results():
+    # the tuner picks the sweep shape (among those keeping the members' chunk
+    # length), the weight form and the CTAs per SM; the step stays that of the
+    # solo handles to FP32 rounding
+    from paper_2107_03550_gb300.sbiem import Batch
+    ws = _ensemble(600)
+    solo = [gpu_for(w, precision=1) for w in ws]
+    mem = [gpu_for(w, precision=1) for w in ws]
+    b = Batch(mem)
+    chunk, blocks, ms = b.tune(reps=3)
+    info = b.get_sweep()
+    assert info["ctas_per_sm"] == blocks and info["shape"] in (3, 4) and chunk == 2048
+    assert info["gen_ds_max"] in (0.0, 1.0 / 256, 1.0 / 64)
+    b.enqueue(20)
+    assert np.all(b.status()[0] == 0)
+    for g in solo:
+        g.enqueue(20)
+    for g1, g2 in zip(solo, mem):
+        s1, s2 = g1.get_state(), g2.get_state()
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert rel(s2[k], s1[k]) <= 1e-5, k
+    b.close()
