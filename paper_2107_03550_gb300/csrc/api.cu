@@ -322,13 +322,12 @@ int setup_device(sbiem_s* s, DevFault<R>& f, const DevFault<double>& base) {
   f.y = alloc_n<Cx<R>>(s, s->N, &ok);
   if (!ok) return nomem(s, "history rings / weights");
   if constexpr (sizeof(R) == 4) {
-    if (s->N <= kFusedMaxN) {
-      // single-CTA spectral pass: FP32 inputs prepared by the multi-SM kernels
-      f.zin1 = alloc_n<float2>(s, s->N, &ok);
-      f.zin2 = alloc_n<float2>(s, s->N, &ok);
-      f.U2f = alloc_n<float2>(s, s->nmodes, &ok);
-      f.Q2f = alloc_n<float2>(s, s->nmodes, &ok);
-    }
+    // the precision form's passes: Vbar + i kappa Vbar prepared in FP32 by
+    // the commit and the pass-1 Newton, U and Q of the step kept in FP32
+    f.zin1 = alloc_n<float2>(s, s->N, &ok);
+    f.zin2 = alloc_n<float2>(s, s->N, &ok);
+    f.U2f = alloc_n<float2>(s, s->nmodes, &ok);
+    f.Q2f = alloc_n<float2>(s, s->nmodes, &ok);
   }
   if (!ok) return nomem(s, "FP32 pass buffers");
   f.g = make_geom(s->N, sizeof(Cx<R>));

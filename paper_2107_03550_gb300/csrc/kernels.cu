@@ -163,6 +163,81 @@ __device__ __forceinline__ Cx<R> assemble(const DevFault<R>& f, int n, int pass,
   return Y;
 }
 
+// Per-mode inputs of the precision form's assembly: running sums F[delta],
+// F[kappa delta], history sums, and the coefficients S dt + mu w0 (T, N) of
+// the current interval (from the power-of-two table, or summed in FP64 for
+// other step lengths; the near-cancelling combination is done in FP64).
+struct ModeIn {
+  float2 D, K, AT, AN, C;
+};
+
+__device__ __forceinline__ ModeIn load_mode_in(const DevFault<float>& f, int m, int m_dt, double dt) {
+  ModeIn in;
+  in.D = f.dhat32[m];
+  in.K = f.khat32[m];
+  in.AT = f.AT32[m];
+  in.AN = f.AN32[m];
+  if ((m_dt & (m_dt - 1)) == 0) {
+    in.C = f.c0pow[static_cast<size_t>(m) * kPow2Slots + (31 - __clz(m_dt))];
+  } else {
+    double w0T = 0.0, w0N = 0.0;
+    const int lim = min(m_dt, f.Mn[m]);
+    for (int j = 0; j < lim; ++j) {
+      const W2<float> w = f.w[f.w_off[m] + j];
+      w0T += w.x;
+      w0N += w.y;
+    }
+    in.C = make_float2(static_cast<float>(f.S * dt + f.mu * w0T), static_cast<float>(f.S * dt + f.mu * w0N));
+  }
+  return in;
+}
+
+// Assembly of the mode pair (m, N-m) of the precision form from the packed
+// spectrum Zm = Z[m], Zc = Z[(N-m) mod N] of Vbar + i kappa Vbar (Sec. 3.1,
+// Sec. 3.3 step (2)): returns Y[m] and Y[N-m] of tau_el + i sigma_el and, in
+// pass 2, leaves U, Q of mode m for the commit.  FP32 products.
+__device__ __forceinline__ void assemble_pair32(const DevFault<float>& f, int m, float2 Zm, float2 Zc, int pass,
+                                                const ModeIn& in, float2* Ym, float2* Yc) {
+  const int N = f.N, half = N >> 1;
+  const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
+  const float Qx = 0.5f * (Zm.y + Zc.y), Qy = -0.5f * (Zm.x - Zc.x);
+  float tr = 0.f, ti = 0.f, sr = 0.f, si = 0.f;
+  if (m > 0) {
+    const float mu = static_cast<float>(f.mu);
+    const float S = static_cast<float>(f.S);
+    const float k = static_cast<float>(kTwoPi / f.L) * static_cast<float>(m);
+    const float cT = in.C.x, cN = in.C.y;
+    tr = -k * (S * in.D.x + cT * Ux + mu * in.AT.x);
+    ti = (m < half) ? -k * (S * in.D.y + cT * Uy + mu * in.AT.y) : 0.f;
+    if (m < half) {
+      const float xr = S * in.K.x + cN * Qx + mu * in.AN.x;
+      const float xi = S * in.K.y + cN * Qy + mu * in.AN.y;
+      sr = xi;
+      si = -xr;
+    }
+  }
+  if (pass == 2) {
+    f.U2f[m] = make_float2(Ux, Uy);
+    f.Q2f[m] = make_float2(Qx, Qy);
+  }
+  // Y_m = tau_m + i sig_m; Y_{N-m} = conj(tau_m) + i conj(sig_m)
+  *Ym = make_float2(tr - si, ti + sr);
+  *Yc = make_float2(tr + si, -ti + sr);
+}
+
+// Precision-form assembly of one coefficient n of the full spectrum (the
+// four-step passes): the pair (m, N-m), m = min(n, N-n), in FP32 from the
+// FP32 per-mode inputs, Y[n] its half; U, Q of mode m are kept (pass 2) by
+// the thread with n <= N/2.
+__device__ __forceinline__ float2 assemble32_at(const DevFault<float>& f, int n, int pass, int m_dt, double dt) {
+  const int N = f.N, half = N >> 1;
+  const int m = n <= half ? n : N - n;
+  const ModeIn in = load_mode_in(f, m, m_dt, dt);
+  float2 Ym, Yc;
+  assemble_pair32(f, m, f.Z[m], f.Z[(N - m) & (N - 1)], n <= half ? pass : 0, in, &Ym, &Yc);
+  return n <= half ? Ym : Yc;
+}
+
 // Column pass: for n1 in this CTA's B columns, transform x[n1 + N1 n2] over
 // n2 (length N2), multiply by exp(-+2 pi i n1 k2 / N), store to
 // out[k2 N1 + n1].
@@ -200,13 +275,25 @@ __device__ __forceinline__ void col_body(const FftGeom& g, const Cx<R>* __restri
     if (PRO == PRO_LOAD) {
       v = in[n];
     } else if (PRO == PRO_PASS) {
-      // predictor slip rate of this pass (Sec. 3.3): V, then (V + V1)/2
+      // predictor slip rate of this pass (Sec. 3.3): V, then (V + V1)/2; the
+      // precision form has Vbar + i kappa Vbar ready in FP32 (written by the
+      // commit for pass 1, by the pass-1 Newton for pass 2)
+      if constexpr (sizeof(R) == 4) {
+        if (f.zin1) {
+          v = (pass == 1) ? f.zin1[n] : f.zin2[n];
+          buf[b * M + n2] = v;
+          continue;
+        }
+      }
       const double vb = (pass == 1) ? f.V[n] : 0.5 * (f.V[n] + f.V1[n]);
-      f.Vbar[n] = vb;
       v.x = static_cast<R>(vb);
       v.y = static_cast<R>(f.kappa[n] * vb);
     } else {
-      v = assemble<R>(f, n, pass, m_dt, dt);
+      if constexpr (sizeof(R) == 4) {
+        v = f.U2f ? assemble32_at(f, n, pass, m_dt, dt) : assemble<R>(f, n, pass, m_dt, dt);
+      } else {
+        v = assemble<R>(f, n, pass, m_dt, dt);
+      }
     }
     buf[b * M + n2] = v;
   }
@@ -373,68 +460,6 @@ __device__ __noinline__ void fft_r8(float2* buf, const float2* tw, int tid, floa
     for (int s = 0; s < LGL / 2; ++s) stockham_stage<4, LGL, 4>(buf, tw, 2 * s, tid, sg);
     if constexpr (LGL % 2 == 1) stockham_stage<2, LGL, 4>(buf, tw, 2 * (LGL / 2), tid, sg);
   }
-}
-
-// Per-mode inputs of the precision form's assembly: running sums F[delta],
-// F[kappa delta], history sums, and the coefficients S dt + mu w0 (T, N) of
-// the current interval (from the power-of-two table, or summed in FP64 for
-// other step lengths; the near-cancelling combination is done in FP64).
-struct ModeIn {
-  float2 D, K, AT, AN, C;
-};
-
-__device__ __forceinline__ ModeIn load_mode_in(const DevFault<float>& f, int m, int m_dt, double dt) {
-  ModeIn in;
-  in.D = f.dhat32[m];
-  in.K = f.khat32[m];
-  in.AT = f.AT32[m];
-  in.AN = f.AN32[m];
-  if ((m_dt & (m_dt - 1)) == 0) {
-    in.C = f.c0pow[static_cast<size_t>(m) * kPow2Slots + (31 - __clz(m_dt))];
-  } else {
-    double w0T = 0.0, w0N = 0.0;
-    const int lim = min(m_dt, f.Mn[m]);
-    for (int j = 0; j < lim; ++j) {
-      const W2<float> w = f.w[f.w_off[m] + j];
-      w0T += w.x;
-      w0N += w.y;
-    }
-    in.C = make_float2(static_cast<float>(f.S * dt + f.mu * w0T), static_cast<float>(f.S * dt + f.mu * w0N));
-  }
-  return in;
-}
-
-// Assembly of the mode pair (m, N-m) of the precision form from the packed
-// spectrum Zm = Z[m], Zc = Z[(N-m) mod N] of Vbar + i kappa Vbar (Sec. 3.1,
-// Sec. 3.3 step (2)): returns Y[m] and Y[N-m] of tau_el + i sigma_el and, in
-// pass 2, leaves U, Q of mode m for the commit.  FP32 products.
-__device__ __forceinline__ void assemble_pair32(const DevFault<float>& f, int m, float2 Zm, float2 Zc, int pass,
-                                                const ModeIn& in, float2* Ym, float2* Yc) {
-  const int N = f.N, half = N >> 1;
-  const float Ux = 0.5f * (Zm.x + Zc.x), Uy = 0.5f * (Zm.y - Zc.y);
-  const float Qx = 0.5f * (Zm.y + Zc.y), Qy = -0.5f * (Zm.x - Zc.x);
-  float tr = 0.f, ti = 0.f, sr = 0.f, si = 0.f;
-  if (m > 0) {
-    const float mu = static_cast<float>(f.mu);
-    const float S = static_cast<float>(f.S);
-    const float k = static_cast<float>(kTwoPi / f.L) * static_cast<float>(m);
-    const float cT = in.C.x, cN = in.C.y;
-    tr = -k * (S * in.D.x + cT * Ux + mu * in.AT.x);
-    ti = (m < half) ? -k * (S * in.D.y + cT * Uy + mu * in.AT.y) : 0.f;
-    if (m < half) {
-      const float xr = S * in.K.x + cN * Qx + mu * in.AN.x;
-      const float xi = S * in.K.y + cN * Qy + mu * in.AN.y;
-      sr = xi;
-      si = -xr;
-    }
-  }
-  if (pass == 2) {
-    f.U2f[m] = make_float2(Ux, Uy);
-    f.Q2f[m] = make_float2(Qx, Qy);
-  }
-  // Y_m = tau_m + i sig_m; Y_{N-m} = conj(tau_m) + i conj(sig_m)
-  *Ym = make_float2(tr - si, ti + sr);
-  *Yc = make_float2(tr + si, -ti + sr);
 }
 
 // Whole spectral side of one pass of the precision form (FP32 FFTs) for
@@ -1546,13 +1571,38 @@ __device__ __forceinline__ double exp_small(double d) {
   return fma(p, d, 1.0);
 }
 
+// 1/d (d > 0) without an FP64 division, for the Newton steps and guards:
+// the FP64 pipe is scarce on this part, and a division, like a conversion
+// between FP64 and FP32, runs on it.  The seed is an FP32 reciprocal
+// (rcp.approx) of d truncated to FP32 by integer operations on its bits
+// (exponent rebiased by 1023 - 127 = 896, top 23 mantissa bits), widened
+// back to FP64 the same way: relative error about 2^-22.  STEPS
+// Newton-Raphson reciprocal steps r <- r + r (1 - d r) in FP64 follow, each
+// squaring the relative error: about 6e-14 after one (a Newton step
+// dx = g / g' taken with it converges as with the exact derivative), FP64
+// rounding after two.  For d outside [1e-30, 1e30] (never met by the solve's
+// quantities), d <= 0 and NaN, the division.
+template <int STEPS>
+__device__ __forceinline__ double rcp_nr(double d) {
+  if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / d;
+  const unsigned hi = static_cast<unsigned>(__double2hiint(d)), lo = static_cast<unsigned>(__double2loint(d));
+  const unsigned fb = __funnelshift_l(lo, hi - 0x38000000u, 3);  // FP32 bits of d, truncated
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(fb)));
+  const unsigned rb = __float_as_uint(rf);
+  double r = __hiloint2double(static_cast<int>((rb >> 3) + 0x38000000u), static_cast<int>(rb << 29));
+#pragma unroll
+  for (int k = 0; k < STEPS; ++k) r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
 __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, double a, double eta, double reta,
                                           double x0, double ex0, double xguess, double tol, int maxit,
                                           double* xout, double* exout) {
   const double sa = sig * a;
   // x_qs: only the guards below need it, so its division overlaps the
   // first residual (a start above x_qs has g < 0 and steps down)
-  double hi = fmin((tau - sig * c0) / sa, 700.0);
+  double hi = fmin((tau - sig * c0) * rcp_nr<2>(sa), 700.0);
   double lo = -CUDART_INF;
   // a learned guess is used when it is finite, below x_qs and calls for a
   // substantial change (|guess - ln V_prev| >= 0.1, where the previous slip
@@ -1569,8 +1619,8 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     const double g = q - e;
     if (g > 0.0) lo = x; else hi = fmin(hi, x);
     double dx;
-    if (q > sa) dx = -q * (x - log(q * reta)) / (q + sa);
-    else dx = g / (e + sa);
+    if (q > sa) dx = -q * (x - log(q * reta)) * rcp_nr<1>(q + sa);
+    else dx = g * rcp_nr<1>(e + sa);
     if (fabs(dx) <= tol) {
       *xout = x + dx;
       *exout = ex * (1.0 + dx);
@@ -1640,7 +1690,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     Dc = ld_Dc;
     rDc = ld_rDc;
     const double th0 = ld_th;
-    const double rth0 = 1.0 / th0;  // off the chain: used only in the series branch
+    const double rth0 = rcp_nr<1>(th0);  // off the chain: used only in the series branch
     bool series = false;
     if (f.state_law == 0) {
       // aging law integrated at constant Vbar: theta e^{-u} + dt phi(u),
@@ -1701,7 +1751,8 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     if (have && solve) {
       const double ex0 = (pass == 1) ? ld_V : ld_V1;
       const double e = f.eta * ex0, q = tau - sig * fma(a, xstart, c0), sa = sig * a;
-      const double dx0 = q > sa ? -q * (xstart - log(q * f.reta)) / (q + sa) : (q - e) / (e + sa);
+      // (a threshold test: the FP32 reciprocal is enough)
+      const double dx0 = q > sa ? -q * (xstart - log(q * f.reta)) * rcp_nr<0>(q + sa) : (q - e) * rcp_nr<0>(e + sa);
       need = !(fabs(dx0) < 0.1);
     }
     if (__any_sync(0xffffffffu, need)) {
