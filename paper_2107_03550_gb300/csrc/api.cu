@@ -93,6 +93,7 @@ struct sbiem_s {
   } host_graph;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_started = nullptr;  // every CTA of the step's first pass kernel has started
   int lag_m = -1;
   int lag_grid = 0;  // CTAs of the overlapped sweep (leaves room for the passes)
   int sweep_shape = 0;  // chunk length x stages of the sweep
@@ -207,6 +208,7 @@ void free_all(sbiem_s* s) {
   if (s->side) cudaStreamDestroy(s->side);
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->ev_started) cudaEventDestroy(s->ev_started);
 }
 
 bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
@@ -244,10 +246,12 @@ void windows(const sbiem_params& p, double L, double dt_min, std::vector<int64_t
 
 // Grids and shapes of the two sweeps from sweep_shape, the weight form and
 // the CTAs per SM asked for.  Beside the one-launch FP32 pass the overlapped
-// sweep leaves each SM room for the pass kernels: shape 3's chunks in one
-// stage (shape 4) on two CTAs per SM (with two stages only one fits beside a
-// pass CTA); other shapes one CTA per SM; with the four-kernel FFT (small
-// CTAs) the full grid.
+// sweep leaves each SM room for the pass kernels: with 2048-lag chunks
+// (shapes 3 and 4) shape 4 (one stage) on two CTAs per SM (with two stages
+// only one fits beside a pass CTA; flushed N = 4096 steps: 48-50 us with
+// one CTA per SM of the on-chip weight form, 41 us with two of the streamed
+// form); other shapes
+// one CTA per SM; with the four-kernel FFT (small CTAs) the full grid.
 void sweep_config(sbiem_s* s) {
   const bool gen = s->fp32() && s->f32.wtab && s->gen_ds_max > 0.0f;
   s->f32.gen_ds_max = gen ? s->gen_ds_max : 0.0f;
@@ -260,7 +264,7 @@ void sweep_config(sbiem_s* s) {
   s->lag_grid = s->hist_grid;
   if (s->fp32() && s->N <= kFusedMaxN) {
     s->lag_grid = s->sm_count;
-    if (s->sweep_shape == 3) {
+    if (s->sweep_shape == 3 || s->sweep_shape == 4) {
       s->lag_shape = 4;
       s->lag_grid = 2 * s->sm_count;
     }
@@ -362,11 +366,15 @@ void enqueue_step_lag_t(sbiem_s* s, const DevFault<R>& f, int m, cudaStream_t st
   int p = 0;
   while ((1 << p) < m) ++p;
   cudaEventRecord(s->ev_fork, st);
-  // the pass-1 spectral kernel is captured (and so dispatched) before the
-  // side branch, whose sweep would otherwise crowd its first loads: the
-  // same dependencies, 47.2 -> 43.3 us per flushed N = 4096 step
-  launch_spectral<R>(f, 1, m, st);
+  // the side branch's sweep is dispatched once every CTA of the pass-1
+  // spectral kernel has started (a programmatic event): when the sweep was
+  // dispatched first it could hold the SMs the pass needed, and which of
+  // the graph's two branches reached the GPU first changed from one graph
+  // instance to the next (flushed N = 4096 steps of 41 or 51 us by
+  // instance; 41 us every time in this order)
+  launch_spectral<R>(f, 1, m, st, s->ev_started);
   cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+  cudaStreamWaitEvent(s->side, s->ev_started, 0);
   launch_history_ahead<R>(f, m, s->lag_grid, s->side);
   cudaEventRecord(s->ev_join, s->side);
   launch_newton<R>(f, 1, m, st);
@@ -532,7 +540,8 @@ int sbiem_create(sbiem_t* out, const sbiem_params* pin, const double* h, const d
   if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_started, cudaEventDisableTiming) != cudaSuccess) {
     free_all(s);
     delete s;
     return fail(SBIEM_ERR_CUDA, "stream / event creation failed");
@@ -1644,17 +1653,21 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
       std::vector<float> tm;
       for (int k = 0; k <= reps; ++k) {
         CK(cudaEventRecord(e0, s->stream));
-        CK(cudaEventRecord(s->ev_fork, s->stream));
-        CK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-        if (s->fp32()) {
-          launch_history_ahead<float>(s->f32, 1, s->lag_grid, s->side);
-          launch_pass<float>(s->f32, 1, 1, s->stream);
-          launch_pass<float>(s->f32, 2, 1, s->stream);
-        } else {
-          launch_history_ahead<double>(s->f64, 1, s->lag_grid, s->side);
-          launch_pass<double>(s->f64, 1, 1, s->stream);
-          launch_pass<double>(s->f64, 2, 1, s->stream);
-        }
+        // in the order of the step graph (the sweep after the pass-1
+        // spectral kernel has started)
+        auto both = [&](const auto& f) {
+          using R = typename std::decay_t<decltype(f)>::Real;
+          cudaEventRecord(s->ev_fork, s->stream);
+          launch_spectral<R>(f, 1, 1, s->stream, s->ev_started);
+          cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+          cudaStreamWaitEvent(s->side, s->ev_started, 0);
+          launch_history_ahead<R>(f, 1, s->lag_grid, s->side);
+          launch_newton<R>(f, 1, 1, s->stream);
+          launch_pass<R>(f, 2, 1, s->stream);
+        };
+        if (s->fp32()) both(s->f32);
+        else both(s->f64);
+        CK(cudaGetLastError());
         CK(cudaEventRecord(s->ev_join, s->side));
         CK(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
         CK(cudaEventRecord(e1, s->stream));

@@ -2260,26 +2260,53 @@ static void with_lgn(int N, F&& fn) {
 }
 static_assert(kFusedMaxN == 1 << 14 && kClusterMinN == 1 << 11, "with_lgn covers the one-launch pass sizes");
 
+// Launch with the attributes of the pass kernels: a cluster of `cluster`
+// CTAs (> 1), programmatic dependent launch behind the stream's previous
+// kernel (early; the kernel waits in pdl_wait()), and an event that fires
+// once every CTA has started (started, may be null: the overlapped step
+// dispatches its side-branch sweep only then, so that the sweep never takes
+// the SMs ahead of the pass's first kernel).
+template <class... Args>
+static void launch_attr(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cluster,
+                        bool early, cudaEvent_t started, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[3];
+  int na = 0;
+  if (cluster > 1) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = cluster;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (early) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (started) {
+    at[na].id = cudaLaunchAttributeProgrammaticEvent;
+    at[na].val.programmaticEvent.event = started;
+    at[na].val.programmaticEvent.flags = 0;
+    at[na].val.programmaticEvent.triggerAtBlockStart = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Cluster launch of the FP32 spectral pass (one cluster per fault).
 template <class... Args>
 static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, bool early,
-                                  Args... args) {
-  cudaLaunchConfig_t cfg = {};
+                                  cudaEvent_t started, Args... args) {
   const int C = cluster_ctas(N);
-  cfg.gridDim = dim3(C * clusters);
-  cfg.blockDim = dim3(N / (kClusterEPT * C));
-  cfg.dynamicSmemBytes = cluster_smem(N);
-  cfg.stream = st;
-  cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[1].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = early ? 2 : 1;
-  cudaLaunchKernelEx(&cfg, kernel, args...);
+  launch_attr(kernel, dim3(C * clusters), dim3(N / (kClusterEPT * C)), cluster_smem(N), st, C, early, started,
+              args...);
 }
 
 // Launch that may start before its predecessor on the stream finishes
@@ -2287,23 +2314,13 @@ static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, 
 template <class... Args>
 static void launch_early(void (*kernel)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                          Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, args...);
+  launch_attr(kernel, grid, block, smem, st, 1, true, static_cast<cudaEvent_t>(nullptr), args...);
 }
 
-// The spectral part of a pass (rows a2, a4, a5; the predictor of a1 in the
+// The spectral part of a pass (forward FFT, assembly, inverse FFT of Sec. 3.3 step (2); the predictor in the
 // FP64 four-kernel form): one launch, or the four-step kernels.
 template <class R>
-void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
+void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st, cudaEvent_t started) {
   const FftGeom& g = f.g;
   const double dt = m_dt * f.dt_min;
   if constexpr (sizeof(R) == 4) {
@@ -2312,11 +2329,11 @@ void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) 
         constexpr int LG = decltype(lg)::value;
         // pass 2 starts early behind the pass-1 Newton
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster<LG, kClusterEPT>, 1, f.N, st, pass == 2, f, pass, m_dt, dt);
-        } else if (pass == 2) {
-          launch_early(k_spectral_fused<LG>, dim3(1), dim3(f.N / 8), fused_smem(f.N), st, f, pass, m_dt, dt);
+          launch_cluster_kernel(k_spectral_cluster<LG, kClusterEPT>, 1, f.N, st, pass == 2, started, f, pass, m_dt,
+                                dt);
         } else {
-          k_spectral_fused<LG><<<1, f.N / 8, fused_smem(f.N), st>>>(f, pass, m_dt, dt);
+          launch_attr(k_spectral_fused<LG>, dim3(1), dim3(f.N / 8), fused_smem(f.N), st, 1, pass == 2, started, f,
+                      pass, m_dt, dt);
         }
       });
       return;
@@ -2327,13 +2344,14 @@ void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) 
   auto kfb = k_row<R, false>;
   auto kia = k_col<R, true, PRO_ASSEMBLE>;
   auto kib = k_row<R, true>;
-  kfa<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
+  launch_attr(kfa, dim3(g.N1 / g.Bc), dim3(g.tc), cs, st, 1, false, started, g, static_cast<const Cx<R>*>(f.tw),
+              static_cast<const Cx<R>*>(nullptr), f.zt, f, pass, m_dt, dt);
   kfb<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.Z, R(1), f.status);
   kia<<<g.N1 / g.Bc, g.tc, cs, st>>>(g, f.tw, nullptr, f.zt, f, pass, m_dt, dt);
   kib<<<g.N2 / g.Br, g.tr, rs, st>>>(g, f.tw, f.zt, f.y, R(1.0 / g.N), f.status);
 }
 
-// The Newton part of a pass (rows a1, a6), started early behind the spectral part.
+// The Newton part of a pass (state predictor and friction solve, Sec. 3.3), started early behind the spectral part.
 template <class R>
 void launch_newton(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st) {
   const double dt = m_dt * f.dt_min;
@@ -2525,7 +2543,8 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
       with_lgn(N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster_b<LG, kClusterEPT>, members, N, st, false, fs, pass, m_dt);
+          launch_cluster_kernel(k_spectral_cluster_b<LG, kClusterEPT>, members, N, st, false,
+                                static_cast<cudaEvent_t>(nullptr), fs, pass, m_dt);
         } else {
           k_spectral_fused_b<LG><<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
         }
@@ -2782,8 +2801,8 @@ template void launch_history<double>(const DevFault<double>&, int, int, cudaStre
 template void launch_history<float>(const DevFault<float>&, int, int, cudaStream_t, cudaEvent_t);
 template void launch_pass<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_pass<float>(const DevFault<float>&, int, int, cudaStream_t);
-template void launch_spectral<double>(const DevFault<double>&, int, int, cudaStream_t);
-template void launch_spectral<float>(const DevFault<float>&, int, int, cudaStream_t);
+template void launch_spectral<double>(const DevFault<double>&, int, int, cudaStream_t, cudaEvent_t);
+template void launch_spectral<float>(const DevFault<float>&, int, int, cudaStream_t, cudaEvent_t);
 template void launch_newton<double>(const DevFault<double>&, int, int, cudaStream_t);
 template void launch_newton<float>(const DevFault<float>&, int, int, cudaStream_t);
 template void launch_push_multi<double>(const DevFault<double>&, int, cudaStream_t);

@@ -48,6 +48,7 @@ struct FftGeom {
 // Pointers of one fault on the device.
 template <class R>
 struct DevFault {
+  using Real = R;
   int N;
   int nmodes;          // N/2 + 1
   double L, S, mu, eta, reta, dt_min, f0, V0, lnV0;  // reta = 1/eta
@@ -188,7 +189,10 @@ template <class R> void configure_batch_kernels(const FftGeom& g);
 template <class R> int history_blocks_per_sm();
 template <class R> void launch_pass(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
 // The two halves of launch_pass: the spectral kernels, then Newton (early).
-template <class R> void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
+// started (may be null): an event that fires once every CTA of the pass's
+// first kernel has started.
+template <class R> void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st,
+                                        cudaEvent_t started = nullptr);
 template <class R> void launch_newton(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st);
 // lag_p >= 0 (m_dt = 2^lag_p): also finish the next step's history sums,
 // AT = BT + (sum of the weights of lags m_dt .. 2 m_dt - 1) x the new slot.
