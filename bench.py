@@ -74,6 +74,8 @@ def _args():
                          "the paper's own cycle setup; ensemble: 256 rough-fault realizations of uneven N")
     ap.add_argument("--kcN-L", type=float, default=0.0,
                     help="k_c * eta * L of the normal-traction kernel (the second cutting plane); 0: one plane")
+    ap.add_argument("--members", type=int, default=256,
+                    help="ensemble members (a multiple of 4; 256 is the ensemble workload, fewer for profiling runs)")
     ap.add_argument("--sweep-only", action="store_true",
                     help="profiling runs: only W + K launches of the history convolution on the workload's handle "
                          "(no tuning unless --weights tune), one JSON line with their times")
@@ -411,6 +413,7 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    torch.cuda.nvtx.range_push("timed")  # profiling runs capture inside this range (ncu --nvtx-include timed/)
     for k in range(K):
         fl()
         ev_s[k][0].record()
@@ -420,6 +423,7 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
         ev_h[k][0].record()
         g.history_enqueue(1, sweep_done=ev_m[k])
         ev_h[k][1].record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -544,8 +548,9 @@ def _ensemble(torch, a, rank, world, clock_index):
     rng = np.random.default_rng(1000)
     Ns = [1024, 2048, 4096, 8192]
     members = []
-    for r in range(256):
-        N = Ns[r // 64]
+    nm = max(4, a.members // 4 * 4)
+    for r in range(nm):
+        N = Ns[r // (nm // 4)]
         w = rough_fault(N, 10.0, float(rng.uniform(1e-3, 1e-2)), seed=1000 + r)
         g = Fault.from_workload(w, precision=1 if a.precision == "fp32" else 0)
         _fill_history(torch, g, 5000 + r + 1000 * rank, a.precision)
@@ -570,9 +575,11 @@ def _ensemble(torch, a, rank, world, clock_index):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    torch.cuda.nvtx.range_push("timed")  # profiling runs capture inside this range (ncu --nvtx-include timed/)
     e0.record()
     b.enqueue(K)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -607,9 +614,9 @@ def _ensemble(torch, a, rank, world, clock_index):
         "metric": METRIC, "value": world * elems * K / total_s, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/f64" if a.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": "ensemble of 256 rough-fault realizations: 64 each of N = 1024, 2048, 4096, 8192, "
-                               "dx = 10 m, Hurst-1 alpha ~ U[0.001, 0.01], seeds 1000 + r; every history window "
-                               "full; dt = dt_min", "elements_per_step": elems, "history_slots": slots,
+        "config": {"workload": f"ensemble of {nm} rough-fault realizations: {nm // 4} each of N = 1024, 2048, "
+                               "4096, 8192, dx = 10 m, Hurst-1 alpha ~ U[0.001, 0.01], seeds 1000 + r; every "
+                               "history window full; dt = dt_min", "elements_per_step": elems, "history_slots": slots,
                    "ring_bytes_per_step": bytes_ring, "precision": a.precision,
                    "parallelism": f"replicas x{world}", "l2": "rings larger than L2 (no flush)",
                    "tuned": {"chunk_slots": chunk, "sweep_ctas_per_sm": blocks, "sweep_ms": tune_ms,

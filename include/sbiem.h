@@ -530,6 +530,12 @@ int sbiem_get_sweep(sbiem_t s, int32_t* shape, double* gen_ds_max, int32_t* ctas
 int sbiem_set_wait_limit(sbiem_t s, int64_t polls);
 int sbiem_set_sweep(sbiem_t s, int32_t shape, double gen_ds_max, int32_t ctas_per_sm);
 int sbiem_tune(sbiem_t s, int reps, int32_t* shape, double* gen_ds_max, int32_t* ctas_per_sm, float* ms);
+/* sbiem_set_lag_sweep -- resident CTAs per SM of the next step's sweep that
+ * sbiem_enqueue runs beside the passes (the value sbiem_tune chooses; 0:
+ * the built-in rule, which sbiem_set_sweep also restores), clamped to the
+ * occupancy limit.  Synchronizes and rebuilds the step graphs.  Errors:
+ * SBIEM_ERR_INVALID (NULL handle, negative), SBIEM_ERR_CUDA. */
+int sbiem_set_lag_sweep(sbiem_t s, int32_t lag_ctas_per_sm);
 
 /*
  * sbiem_kernel_values -- host FP64 evaluation of the convolution kernels

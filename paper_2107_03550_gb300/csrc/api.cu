@@ -1582,6 +1582,16 @@ int sbiem_set_sweep(sbiem_t s, int32_t shape, double gen_ds_max, int32_t ctas_pe
   return SBIEM_OK;
 }
 
+int sbiem_set_lag_sweep(sbiem_t s, int32_t lag_ctas_per_sm) {
+  if (!s || lag_ctas_per_sm < 0) return fail(SBIEM_ERR_INVALID, "NULL handle or negative CTA count");
+  CK(cudaStreamSynchronize(s->stream));
+  s->lag_ctas = lag_ctas_per_sm;
+  sweep_config(s);
+  drop_graphs(s);
+  s->lag_m = -1;
+  return SBIEM_OK;
+}
+
 int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t* ctas_out, float* ms_out) {
   if (!s || reps < 1) return fail(SBIEM_ERR_INVALID, "bad argument");
   cudaEvent_t e0, e1;

@@ -91,6 +91,7 @@ _SIGS = {
     "sbiem_get_sweep": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), _D, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32), _D]),
     "sbiem_set_sweep": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]),
+    "sbiem_set_lag_sweep": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "sbiem_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "sbiem_set_output": (ctypes.c_int, [_VP, _output_t, _VP, ctypes.c_int64]),
     "sbiem_tune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _D,
@@ -552,6 +553,10 @@ class Fault:
     def set_sweep(self, shape: int = 3, gen_ds_max: float = 0.0625, ctas_per_sm: int = 0) -> None:
         """gen_ds_max: modes with s step c_s k dt_min at most this evaluate their weights on chip (0: none)."""
         self._check(self.lib.sbiem_set_sweep(self.h, int(shape), float(gen_ds_max), int(ctas_per_sm)))
+
+    def set_lag_sweep(self, lag_ctas_per_sm: int = 0) -> None:
+        """Resident CTAs per SM of the next step's sweep run beside the passes (0: the built-in rule)."""
+        self._check(self.lib.sbiem_set_lag_sweep(self.h, int(lag_ctas_per_sm)))
 
     def set_wait_limit(self, polls: int = 4194304) -> None:
         """Polls of the history sweep's copy waits before it gives up (0: at once)."""
