@@ -387,11 +387,12 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  *   limit) resident sweep CTAs per SM, reps timed launches each (median), and
  *   keeps the fastest, then the faster of the one-launch and two-launch
  *   forms (sbiem_batch_set_persistent); returns the chunk length, the CTAs
- *   per SM chosen and the time (sbiem_batch_get_sweep gives the rest).  It also times the
- *   overlapped sweep (one CTA per
- *   SM beside the passes) and the passes, and makes later steps sweep the
- *   next step's history beside the passes when that is faster (a new batch
- *   steps without overlap).  The committed state is not changed.
+ *   per SM chosen and the time (sbiem_batch_get_sweep gives the rest).  It
+ *   then times the overlapped step's two branches together (the next
+ *   step's sweep beside the passes) for 1 .. (occupancy limit) sweep CTAs
+ *   per SM, and makes later steps overlap when the best of those beats the
+ *   sweep followed by the passes (a new batch steps without overlap).  The
+ *   committed state is not changed.
  * sbiem_batch_set_overlap: overlap on (1) or off (0) by hand; *on_out (may
  *   be NULL) gets the setting in force before the call.  Results agree
  *   either way up to summation order.

@@ -2247,22 +2247,45 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
     for (size_t r = 0; r < b->members.size(); ++r)
       CK(cudaMemcpyAsync(&st0[r], b->members[r]->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    float t_lag = 0.f, t_pass = 0.f;
+    float t_pass = 0.f;
     int rc = timed([&] {
-      if (b->fp32) batch_history<float>(b, b->stream, true);
-      else batch_history<double>(b, b->stream, true);
-    }, &t_lag);
-    if (rc) return rc;
-    rc = timed([&] {
       cudaEventRecord(b->ev_fork, b->stream);
       if (b->fp32) batch_passes<float>(b, b->stream, b->ev_fork);
       else batch_passes<double>(b, b->stream, b->ev_fork);
     }, &t_pass);
     if (rc) return rc;
+    // the overlapped step's two branches timed together (next step's sweep
+    // on the side stream, the passes on the batch's stream), for 1 ..
+    // (occupancy limit) sweep CTAs per SM
+    const int lim = b->gen ? persist_blocks_per_sm<float>(b->shape, true)
+                           : (b->fp32 ? persist_blocks_per_sm<float>(b->shape, false)
+                                      : persist_blocks_per_sm<double>(b->shape, false));
+    float t_ov = 1e30f;
+    int lag_best = b->lag_grid;
+    for (int lc = 1; lc <= std::max(1, lim); ++lc) {
+      b->lag_grid = b->sm_count * lc;
+      float t = 0.f;
+      rc = timed([&] {
+        cudaEventRecord(b->ev_fork, b->stream);
+        cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+        if (b->fp32) batch_history<float>(b, b->side, true);
+        else batch_history<double>(b, b->side, true);
+        cudaEventRecord(b->ev_side, b->side);
+        if (b->fp32) batch_passes<float>(b, b->stream, b->ev_fork);
+        else batch_passes<double>(b, b->stream, b->ev_fork);
+        cudaStreamWaitEvent(b->stream, b->ev_side, 0);
+      }, &t);
+      if (rc) return rc;
+      if (t < t_ov) {
+        t_ov = t;
+        lag_best = b->lag_grid;
+      }
+    }
+    b->lag_grid = lag_best;
     for (size_t r = 0; r < b->members.size(); ++r)
       CK(cudaMemcpyAsync(b->members[r]->f64.status, &st0[r], sizeof(unsigned), cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    b->overlap = std::max(t_lag, t_pass) < best + t_pass;
+    b->overlap = t_ov < best + t_pass;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
