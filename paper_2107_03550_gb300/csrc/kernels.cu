@@ -1582,9 +1582,42 @@ __device__ __forceinline__ double exp_small(double d) {
 // dx = g / g' taken with it converges as with the exact derivative), FP64
 // rounding after two.  For d outside [1e-30, 1e30] (never met by the solve's
 // quantities), d <= 0 and NaN, the division.
+// Comparisons of doubles on the integer pipe: the FP64 pipe, which also
+// executes FP64 comparisons and min/max, is what bounds the friction solve
+// on this part.  The bit pattern of a double, with the magnitude bits
+// flipped when the sign is set, orders like the value (-0 sorts just below
+// +0, which the solve never tells apart; a NaN sorts beyond the infinity of
+// its sign, so a NaN step still fails the convergence test and a NaN
+// residual still ends in the iteration cap).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool dgt(double a, double b) { return dkey(a) > dkey(b); }
+__device__ __forceinline__ double dmin(double a, double b) { return dkey(a) < dkey(b) ? a : b; }
+// |a| <= b and |a| < b for b >= 0 (false for a NaN a)
+__device__ __forceinline__ bool dabs_le(double a, double b) {
+  return (__double_as_longlong(a) & 0x7fffffffffffffffLL) <= __double_as_longlong(b);
+}
+__device__ __forceinline__ bool dabs_lt(double a, double b) {
+  return (__double_as_longlong(a) & 0x7fffffffffffffffLL) < __double_as_longlong(b);
+}
+// FP32 -> FP64 on the integer pipe: exact for normal values, zeros,
+// infinities and NaNs; FP32 subnormals (below 1.2e-38) become zero.
+__device__ __forceinline__ double widen(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = static_cast<unsigned long long>(u & 0x80000000u) << 32;
+  if (e == 0u) return __longlong_as_double(static_cast<long long>(sgn));
+  const unsigned long long ex = e == 0xffu ? 0x7ffull : static_cast<unsigned long long>(e + 896u);
+  return __longlong_as_double(
+      static_cast<long long>(sgn | (ex << 52) | (static_cast<unsigned long long>(u & 0x7fffffu) << 29)));
+}
+
 template <int STEPS>
 __device__ __forceinline__ double rcp_nr(double d) {
-  if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / d;
+  const long long db = __double_as_longlong(d);
+  if (!(db >= __double_as_longlong(1e-30) && db <= __double_as_longlong(1e30))) return 1.0 / d;
   const unsigned hi = static_cast<unsigned>(__double2hiint(d)), lo = static_cast<unsigned>(__double2loint(d));
   const unsigned fb = __funnelshift_l(lo, hi - 0x38000000u, 3);  // FP32 bits of d, truncated
   float rf;
@@ -1602,12 +1635,12 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
   const double sa = sig * a;
   // x_qs: only the guards below need it, so its division overlaps the
   // first residual (a start above x_qs has g < 0 and steps down)
-  double hi = fmin((tau - sig * c0) * rcp_nr<2>(sa), 700.0);
+  double hi = dmin((tau - sig * c0) * rcp_nr<2>(sa), 700.0);
   double lo = -CUDART_INF;
   // a learned guess is used when it is finite, below x_qs and calls for a
   // substantial change (|guess - ln V_prev| >= 0.1, where the previous slip
   // rate is a poor start); otherwise the previous slip rate starts Newton
-  const bool use_guess = isfinite(xguess) && xguess <= hi && fabs(xguess - x0) >= 0.1;
+  const bool use_guess = isfinite(xguess) && !dgt(xguess, hi) && !dabs_lt(xguess - x0, 0.1);
   double x = x0, ex = ex0;
   if (use_guess) {
     x = xguess;
@@ -1617,11 +1650,11 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     const double e = eta * ex;
     const double q = tau - sig * fma(a, x, c0);
     const double g = q - e;
-    if (g > 0.0) lo = x; else hi = fmin(hi, x);
+    if (dgt(g, 0.0)) lo = x; else hi = dmin(hi, x);
     double dx;
-    if (q > sa) dx = -q * (x - log(q * reta)) * rcp_nr<1>(q + sa);
+    if (dgt(q, sa)) dx = -q * (x - log(q * reta)) * rcp_nr<1>(q + sa);
     else dx = g * rcp_nr<1>(e + sa);
-    if (fabs(dx) <= tol) {
+    if (dabs_le(dx, tol)) {
       *xout = x + dx;
       *exout = ex * (1.0 + dx);
       return it;
@@ -1629,11 +1662,11 @@ __device__ __forceinline__ int solve_lnV(double tau, double sig, double c0, doub
     double xn = x + dx;
     // keep Newton points within tol of the bracket: roots next to the
     // quasi-static bound (vanishing radiation damping) land on it up to rounding
-    if (xn > hi + tol || xn < lo - tol) {
-      xn = (lo > -CUDART_INF) ? 0.5 * (lo + hi) : hi;
+    if (dgt(xn, hi + tol) || dgt(lo - tol, xn)) {
+      xn = (__double_as_longlong(lo) != __double_as_longlong(-CUDART_INF)) ? 0.5 * (lo + hi) : hi;
       dx = xn - x;
     }
-    ex = fabs(dx) <= 0.015625 ? ex * exp_small(dx) : exp(xn);
+    ex = dabs_le(dx, 0.015625) ? ex * exp_small(dx) : exp(xn);
     x = xn;
   }
   *xout = x;
@@ -1696,7 +1729,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       // aging law integrated at constant Vbar: theta e^{-u} + dt phi(u),
       // phi(u) = (1 - e^{-u})/u, u = Vbar dt / Dc
       const double u = vb * dt * rDc;
-      if (u < 1e-4) {
+      if (dgt(1e-4, u)) {
         // series of phi to u^3 (truncation below u^4/120 < 1e-18); with
         // e^{-u} = 1 - u phi the update is theta (1 + z), z = phi (dt/theta - u)
         const double phi = fma(fma(fma(-u, 1.0 / 24.0, 1.0 / 6.0), u, -0.5), u, 1.0);
@@ -1704,7 +1737,7 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
         thp = fma(th0, z, th0);
         // every 1024th step takes the full log, so ln theta and theta, kept
         // side by side, cannot drift apart by accumulated rounding
-        if (fabs(z) < 1e-3 && resync_off) {
+        if (dabs_lt(z, 1e-3) && resync_off) {
           // ln theta' = ln theta + log1p(z), series to z^6 (truncation below
           // |z|^7/7 < 2e-22)
           double l = -1.0 / 6.0;
@@ -1728,8 +1761,13 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
     }
     if (!series) psip = log(thp);
     const double t_end = t_now + dt;
-    tau = ld_tau0 + ld_taur * t_end + static_cast<double>(y.x);
-    sig = ld_sig0 + static_cast<double>(y.y);
+    if constexpr (sizeof(R) == 4) {
+      tau = ld_tau0 + ld_taur * t_end + widen(y.x);
+      sig = ld_sig0 + widen(y.y);
+    } else {
+      tau = ld_tau0 + ld_taur * t_end + static_cast<double>(y.x);
+      sig = ld_sig0 + static_cast<double>(y.y);
+    }
     xstart = (pass == 1) ? ld_xV : ld_x1;
     if (!ld_presc) {
       if (!(sig > 0.0)) flags |= SBIEM_FLAG_OPENING;
@@ -1752,8 +1790,9 @@ __device__ __forceinline__ void newton_body(const DevFault<R>& f, int pass, doub
       const double ex0 = (pass == 1) ? ld_V : ld_V1;
       const double e = f.eta * ex0, q = tau - sig * fma(a, xstart, c0), sa = sig * a;
       // (a threshold test: the FP32 reciprocal is enough)
-      const double dx0 = q > sa ? -q * (xstart - log(q * f.reta)) * rcp_nr<0>(q + sa) : (q - e) * rcp_nr<0>(e + sa);
-      need = !(fabs(dx0) < 0.1);
+      const double dx0 =
+          dgt(q, sa) ? -q * (xstart - log(q * f.reta)) * rcp_nr<0>(q + sa) : (q - e) * rcp_nr<0>(e + sa);
+      need = !dabs_lt(dx0, 0.1);
     }
     if (__any_sync(0xffffffffu, need)) {
       const float feat[kMlpIn] = {static_cast<float>(xstart), static_cast<float>(psip),
