@@ -313,6 +313,40 @@ def _sweep_source_sha() -> str:
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
+def _persist_source_sha() -> str:
+    """Hash of the ensemble's persistent history kernel: the sweep section and the persistent-launch section."""
+    src = open(os.path.join(ROOT, "paper_2107_03550_gb300", "csrc", "kernels.cu")).read()
+    a = src.index("// ---------------------------------------------- history sweep (bulk-async)")
+    b = src.index("// Per-mode sums of the sweep's segment partials")
+    c = src.index("// Ensemble form of k_sweep_finish")
+    d = src.index("// ------------------------------------------------------------ friction")
+    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()[:16]
+
+
+def _traffic_ensemble(precision: str, slots: int):
+    """ncu DRAM bytes of the ensemble's persistent history launch, scaled by ring slots from a smaller
+    ensemble of the same family, if recorded for the current source (else None)."""
+    sha = _persist_source_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not (fn.startswith(f"k_sweep_persist_{precision}_") and fn.endswith(".md")):
+            continue
+        fields = {}
+        for line in open(os.path.join(pdir, fn)):
+            if ": " in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(": ", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("k_sweep_persist source sha256[:16]") != sha:
+            continue
+        try:
+            dram = float(fields["dram bytes per launch"])
+            s = float(fields["ring slots"])
+        except (KeyError, ValueError):
+            continue
+        return {"bytes": dram * slots / s, "from": fn, "scaled_by_slots": slots / s}
+    return None
+
+
 def _traffic(precision: str, kind: str, slots: int):
     """ncu DRAM bytes per sweep launch, if recorded for the current sweep source (else None).
 
@@ -610,6 +644,7 @@ def _ensemble(torch, a, rank, world, clock_index):
         total_s = float(t.item())
     bytes_ring = slots * (16 if a.precision == "fp32" else 32)
     peak, peak_kind = _peaks()
+    traffic = _traffic_ensemble(a.precision, slots)
     line = {
         "metric": METRIC, "value": world * elems * K / total_s, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
@@ -631,7 +666,9 @@ def _ensemble(torch, a, rank, world, clock_index):
                                + "; the rest of the step unchanged"}}},
         "roofline": {"bound": "hbm", "kernel": "k_sweep_persist" if info["persistent"] else "k_sweep", "achieved": bytes_ring / (tune_ms * 1e-3) / 1e9,
                      "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)", "unit": "GB/s",
-                     "frac": bytes_ring / (tune_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                     "frac": bytes_ring / (tune_ms * 1e-3) / 1e9 / peak,
+                     "traffic": traffic["bytes"] if traffic and info["persistent"] else None,
+                     "traffic_source": traffic if traffic and info["persistent"] else None,
                      "algorithmic_bytes": "ring slots x 2 fields x complex", "ms_per_launch": tune_ms,
                      "timing": "median of the autotuner's event-timed launches of the history convolution alone"},
         "ring_GBps_over_step": bytes_ring / (total_s / K) / 1e9,
