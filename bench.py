@@ -356,6 +356,7 @@ def _traffic(precision: str, kind: str, slots: int):
     """
     sha = _sweep_source_sha()
     pdir = os.path.join(ROOT, "profiles")
+    found = []
     for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
         if not (fn.startswith(f"k_sweep_{precision}_") and fn.endswith(".md")):
             continue
@@ -371,8 +372,10 @@ def _traffic(precision: str, kind: str, slots: int):
             s = float(fields["ring slots"])
         except (KeyError, ValueError):
             continue
-        return {"bytes": dram * slots / s, "from": fn, "scaled_by_slots": slots / s}
-    return None
+        found.append({"bytes": dram * slots / s, "from": fn, "scaled_by_slots": slots / s})
+    # a profile of the same size first
+    found.sort(key=lambda r: abs(r["scaled_by_slots"] - 1.0))
+    return found[0] if found else None
 
 
 # -------------------------------------------------------------- reference
