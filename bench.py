@@ -670,8 +670,9 @@ def _ensemble(torch, a, rank, world, clock_index):
         "roofline": {"bound": "hbm", "kernel": "k_sweep_persist" if info["persistent"] else "k_sweep", "achieved": bytes_ring / (tune_ms * 1e-3) / 1e9,
                      "peak": peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)", "unit": "GB/s",
                      "frac": bytes_ring / (tune_ms * 1e-3) / 1e9 / peak,
-                     "traffic": traffic["bytes"] if traffic and info["persistent"] else None,
-                     "traffic_source": traffic if traffic and info["persistent"] else None,
+                     # both forms sweep with the same code and copy policy: the same DRAM bytes
+                     "traffic": traffic["bytes"] if traffic else None,
+                     "traffic_source": traffic,
                      "algorithmic_bytes": "ring slots x 2 fields x complex", "ms_per_launch": tune_ms,
                      "timing": "median of the autotuner's event-timed launches of the history convolution alone"},
         "ring_GBps_over_step": bytes_ring / (total_s / K) / 1e9,
