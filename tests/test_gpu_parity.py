@@ -584,3 +584,36 @@ def test_out_of_memory_reports_the_footprint():
     msg = str(ei.value)
     assert "needs about" in msg and "history rings 0.04" in msg, msg
     assert not held            # everything allocated before the failure was freed
+
+
+@pytest.mark.parametrize("precision,lag", [(0, 1), (0, 3), (1, 1), (1, 2), (1, 4)])
+def test_overlapped_sweep_ctas_keep_results(precision, lag):
+    # The overlapped step's side-branch sweep on 1 .. 4 CTAs per SM
+    # (sbiem_set_lag_sweep; the cluster pass of N = 4096 beside it): the
+    # CTA count only changes how the chunks are partitioned, so the steps
+    # match the oracle as with the built-in rule; the setting is reported
+    # back and sbiem_set_sweep restores the rule.
+    w = rough_fault(4096, 10.0, 3e-3, seed=41)
+    o = oracle_for(w)
+    g = gpu_for(w, precision=precision)
+    prefill(o, g, seed=43, scale=1e-6)
+    g.set_lag_sweep(lag)
+    assert g.get_sweep()["lag_ctas_per_sm"] <= lag
+    for _ in range(6):
+        assert o.step() == 0
+    g.enqueue(6)
+    assert g.status()[0] == 0
+    err = compare(o, g)
+    if precision == 0:
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert err[k] < 1e-10, (k, err)
+    else:
+        s = g.get_state()
+        scale = max(np.abs(o.last["tau_el"]).max(), np.abs(o.last["sig_el"]).max())
+        for k, ref in (("tau_el", o.last["tau_el"]), ("sigma_el", o.last["sig_el"])):
+            assert np.abs(s[k] - ref).max() < 1e-4 * scale, (k, err)
+        for k in ("delta", "V", "theta"):
+            assert err[k] < 1e-4, (k, err)
+    sw = g.get_sweep()
+    g.set_sweep(sw["shape"], sw["gen_ds_max"], 0)
+    g.close()
