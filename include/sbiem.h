@@ -376,10 +376,13 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  * sbiem_batch_enqueue: nsteps steps of each member's dt_min, asynchronous.
  * sbiem_batch_status: synchronize; per member (caller order) status flags
  *   and committed steps (arrays of n, may be NULL).
- * Members with bitwise equal weights (equal N, length, c_s, c_p, dt_min,
- *   windows, quadrature and precision) read one copy of them, and the sweep
- *   then copies ring slots under an L2 evict-first policy so that the shared
- *   weight runs stay in L2.
+ * Members share weights: with equal dx, c_s, c_p, dt_min, quadrature and
+ *   precision, mode n of N has the wavenumber of mode n 2^p of 2^p N and so
+ *   the same weights as far as both windows reach; with one cutting plane a
+ *   member whose every window is no longer than a larger member's reads a
+ *   prefix of that member's weight runs (members of equal N and windows read
+ *   one copy).  The sweep then copies ring slots under an L2 evict-first
+ *   policy so that the shared weight runs stay in L2.
  * sbiem_batch_tune: autotuner -- times the batched history convolution for
  *   every sweep shape that keeps the members' chunk length, each weight form
  *   (streamed, or evaluated on chip for the modes with s step up to 1/256 or

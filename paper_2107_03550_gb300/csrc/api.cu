@@ -1798,6 +1798,27 @@ bool same_weights(const sbiem_s* a, const sbiem_s* b) {
          a->MN == b->MN;
 }
 
+// Members whose wavenumbers coincide share weights across sizes too: with
+// equal dx, c_s, c_p, dt_min, quadrature and precision, mode n of N and mode
+// n N'/N of N' = 2^p N have the same k (k = 2 pi n / L bitwise: scaling n
+// and L by 2^p is exact), so the same weights dt C(c_s k (j + 1/2) dt) as
+// far as both windows reach.  With one cutting plane (each field's window
+// the mode's) a member whose every window is no longer than the larger
+// member's reads a prefix of that member's weight run.  Returns N'/N when
+// member r can read member c's weights, else 0.
+int64_t weight_ratio(const sbiem_s* r, const sbiem_s* c) {
+  if (r->fp32() != c->fp32() || r->p.cs != c->p.cs || r->p.cp != c->p.cp || r->dt_min != c->dt_min ||
+      r->p.quadrature != c->p.quadrature)
+    return 0;
+  if (c->p.N < r->p.N || c->p.N % r->p.N != 0) return 0;
+  const int64_t ratio = c->p.N / r->p.N;
+  if ((ratio & (ratio - 1)) != 0 || r->L * static_cast<double>(ratio) != c->L) return 0;
+  if (r->MT != r->MN || c->MT != c->MN) return 0;
+  for (int n = 1; n < r->nmodes; ++n)
+    if (r->M[n] > c->M[static_cast<size_t>(n) * ratio]) return 0;
+  return ratio;
+}
+
 // Ensemble chunk table: the members' own chunk tables one after another
 // (member index in Chunk::pad), each member's first chunk, the (member,
 // mode) list of the per-mode sums; member descriptors on the device.
@@ -1831,14 +1852,46 @@ int batch_build(sbiem_batch_s* b) {
     if constexpr (sizeof(R) == 8) f = b->members[r]->f64;
     else f = b->members[r]->f32;
     f.newton_epw = 32;  // the batched Newton launch covers 32 elements per warp
-    // the weights of the first member with equal weights
-    for (size_t q = 0; q < r; ++q)
-      if (same_weights(b->members[q], b->members[r])) {
-        f.w = fs[q].w;
-        f.wgen = fs[q].wgen;
-        break;
-      }
     fs[r] = f;
+  }
+  // weights: each member reads those of the largest member it can (itself
+  // when none); members of one size share one offset table into it
+  {
+    const size_t nm = b->members.size();
+    std::map<std::pair<size_t, int64_t>, int64_t*> maps;  // (source member, N) -> device offsets
+    for (size_t r = 0; r < nm; ++r) {
+      const sbiem_s* sr = b->members[r];
+      size_t src = r;
+      int64_t ratio = 1;
+      for (size_t q = 0; q < nm; ++q) {
+        const int64_t t = weight_ratio(sr, b->members[q]);
+        if (t > ratio || (t == ratio && t > 0 && q < src && b->members[q]->p.N == b->members[src]->p.N)) {
+          src = q;
+          ratio = t;
+        }
+      }
+      if (src == r) continue;
+      if (ratio == 1 && same_weights(sr, b->members[src])) {
+        fs[r].w = fs[src].w;
+        fs[r].w_off = fs[src].w_off;
+        fs[r].wgen = fs[src].wgen;
+        continue;
+      }
+      auto key = std::make_pair(src, static_cast<int64_t>(sr->p.N));
+      auto it = maps.find(key);
+      if (it == maps.end()) {
+        const sbiem_s* sc = b->members[src];
+        std::vector<int64_t> wo(static_cast<size_t>(sr->nmodes) + 1);
+        for (int n = 0; n <= sr->nmodes; ++n)
+          wo[n] = sc->w_off[std::min<size_t>(static_cast<size_t>(n) * ratio, static_cast<size_t>(sc->nmodes))];
+        int64_t* d = static_cast<int64_t*>(batch_alloc(b, sizeof(int64_t) * wo.size()));
+        if (!d) return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed (weight offsets)");
+        CK(cudaMemcpy(d, wo.data(), sizeof(int64_t) * wo.size(), cudaMemcpyHostToDevice));
+        it = maps.emplace(key, d).first;
+      }
+      fs[r].w = fs[src].w;
+      fs[r].w_off = it->second;
+    }
   }
   b->distinct_weights = 0;
   for (size_t r = 0; r < fs.size(); ++r) {

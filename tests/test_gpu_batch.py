@@ -114,8 +114,10 @@ def test_persistent_barrier_limit_rejects_the_step_and_recovers():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_two_launch_form_equals_persistent_and_weights_shared(precision):
-    # The members of one N share their weights (equal N, dx, material, dt_min,
-    # windows): one weight array per size is read.  The two-launch form (sweep,
+    # The members share their weights: equal dx, material and dt_min give
+    # mode n of N the wavenumber of mode 4n of 4N, and every window of the
+    # smaller members is no longer than the N = 1024 member's, so all read
+    # that member's weight array (a prefix of each mode's run).  The two-launch form (sweep,
     # then the per-(member, mode) sums in a second launch) partitions the chunks
     # the same way and adds in the same order as the persistent launch, so the
     # two step bitwise alike.
@@ -125,7 +127,7 @@ def test_two_launch_form_equals_persistent_and_weights_shared(precision):
     c = [gpu_for(w, precision=precision) for w in ws]
     ba, bc = Batch(a), Batch(c)
     info = ba.get_sweep()
-    assert info["persistent"] and info["distinct_weights"] == 3
+    assert info["persistent"] and info["distinct_weights"] == 1
     assert bc.set_persistent(False) is True
     assert bc.get_sweep()["persistent"] is False
     ba.enqueue(12)
