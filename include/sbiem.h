@@ -385,8 +385,8 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  *   policy so that the shared weight runs stay in L2.
  * sbiem_batch_tune: autotuner -- times the batched history convolution for
  *   every sweep shape that keeps the members' chunk length, each weight form
- *   (streamed, or evaluated on chip for the modes with s step up to 1/256 or
- *   1/64 when the members share c_s, c_p and dt_min) and 1 .. (occupancy
+ *   (streamed, or evaluated on chip for the modes with s step up to 1/256,
+ *   1/64 or 1/32 when the members share c_s, c_p and dt_min) and 1 .. (occupancy
  *   limit) resident sweep CTAs per SM, reps timed launches each (median), and
  *   keeps the fastest, then the faster of the one-launch and two-launch
  *   forms (sbiem_batch_set_persistent); returns the chunk length, the CTAs
@@ -499,9 +499,11 @@ int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_
  *     L1; a thread evaluates eight consecutive lags from one piece), so for
  *     them the sweep reads only ring slots; the other modes stream the
  *     materialized weights with the slots.  0 streams every mode's weights;
- *     values above 1/64 (the largest step an eight-lag block allows) are
- *     taken as 1/64, the default of a new FP32 handle whenever its windows'
- *     s range fits the table (k_c L <= about 340 rad); table_err is the
+ *     modes with ds up to 1/64 evaluate in blocks of eight lags, modes
+ *     above it (up to 1/32, the largest step a four-lag block allows;
+ *     larger values are taken as 1/32) in blocks of four.  1/64 is the
+ *     default of a new FP32 handle whenever its windows' s range fits the
+ *     table (k_c L <= about 340 rad); table_err is the
  *     table's largest error relative to dt_min max|C| (-1: no table).
  *   ctas_per_sm: resident sweep CTAs per SM (0: as many as fit).
  *   lag_ctas_per_sm (get only): the same for the next step's sweep that
@@ -509,7 +511,7 @@ int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_
  * sbiem_set_sweep synchronizes and rebuilds the step graphs.  sbiem_tune is
  * the autotuner: it times `reps` launches (median, after one untimed) of the
  * history convolution for every shape of the handle's chunk length, the
- * thresholds 0, 1/512, 1/256, 1/128 and 1/64, and 1 .. (occupancy limit)
+ * thresholds 0, 1/512, 1/256, 1/128, 1/64 and 1/32, and 1 .. (occupancy limit)
  * CTAs per SM, and keeps the fastest; then it times the next step's sweep
  * (the overlapped form of sbiem_enqueue) together with the two passes it
  * runs beside, for 1 .. (occupancy limit) sweep CTAs per SM, and keeps the

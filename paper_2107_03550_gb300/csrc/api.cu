@@ -1573,7 +1573,7 @@ int sbiem_set_sweep(sbiem_t s, int32_t shape, double gen_ds_max, int32_t ctas_pe
   if (ctas_per_sm < 0) return fail(SBIEM_ERR_INVALID, "ctas_per_sm must be >= 0");
   CK(cudaStreamSynchronize(s->stream));
   s->sweep_shape = shape;
-  s->gen_ds_max = static_cast<float>(std::min(gen_ds_max, kGenDsBlockMax));
+  s->gen_ds_max = static_cast<float>(std::min(gen_ds_max, kGenDsBlock4Max));
   s->sweep_ctas = ctas_per_sm;
   s->lag_ctas = 0;  // the overlapped sweep's grid follows the rule again (sbiem_tune times it)
   sweep_config(s);
@@ -1601,7 +1601,8 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
   // s step the on-chip blocks allow
   std::vector<float> thr = {0.0f};
   if (s->gen_pieces > 0)
-    for (double v : {kGenDsBlockMax / 8.0, kGenDsBlockMax / 4.0, kGenDsBlockMax / 2.0, kGenDsBlockMax})
+    for (double v : {kGenDsBlockMax / 8.0, kGenDsBlockMax / 4.0, kGenDsBlockMax / 2.0, kGenDsBlockMax,
+                     kGenDsBlock4Max})
       thr.push_back(static_cast<float>(v));
   float best = 1e30f;
   int bshape = s->sweep_shape, bctas = 0;
@@ -2200,7 +2201,7 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
   const bool can_gen = b->wtab != nullptr;
   std::vector<float> thr = {0.0f};
   if (can_gen)
-    for (double v : {kGenDsBlockMax / 4.0, kGenDsBlockMax}) thr.push_back(static_cast<float>(v));
+    for (double v : {kGenDsBlockMax / 4.0, kGenDsBlockMax, kGenDsBlock4Max}) thr.push_back(static_cast<float>(v));
   // the sweep shapes that keep the members' chunk length (their chunk
   // tables and per-mode chunk ranges stay valid)
   std::vector<int> shapes;

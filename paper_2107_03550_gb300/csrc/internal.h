@@ -24,6 +24,9 @@ constexpr int kGenDeg = 5;
 // Largest s step of a mode whose weights the sweep evaluates on chip (a
 // thread's eight consecutive lags then stay on one piece's polynomial).
 constexpr double kGenDsBlockMax = kGenH / 16.0;
+// The same for blocks of four consecutive lags (modes with ds above
+// kGenDsBlockMax and up to this).
+constexpr double kGenDsBlock4Max = kGenH / 8.0;
 
 void kernel_values(double s, double r, double* cT, double* cN);
 void build_gen_table(double r, double dt, double smax, std::vector<float>& tab, int* npieces, double* max_err);

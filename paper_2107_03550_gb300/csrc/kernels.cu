@@ -1002,9 +1002,13 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 // piece's polynomial holds over kGenSpan piece widths, so the block stays on
 // it while (kGenBlock - 1) ds <= (kGenSpan - 1) kGenH: modes with ds up to
 // kGenDsBlockMax.
+// Modes with ds above that and up to kGenDsBlock4Max take blocks of four
+// lags (two per thread and stage).
 constexpr int kGenBlock = 8;
+constexpr int kGenBlock4 = 4;
 constexpr float kGenTScale = static_cast<float>(2.0 / (kGenSpan * kGenH));  // dt / ds
 static_assert((kGenBlock - 1) * kGenDsBlockMax <= (kGenSpan - 1.0) * kGenH, "blocks stay on their piece");
+static_assert((kGenBlock4 - 1) * kGenDsBlock4Max <= (kGenSpan - 1.0) * kGenH, "blocks stay on their piece");
 static_assert(sweep_threads(true) * kGenBlock == SweepCfg<float, 3>::kSlots, "a GEN stage is one block per thread");
 
 // (w^T, w^N) = the piece's polynomial at t: Horner on the coefficient pairs
@@ -1117,6 +1121,44 @@ struct SweepPlan {
 };
 constexpr int kPlanRing = 64;  // plans held in shared memory (a ring by chunk index)
 
+// On-chip weights of B consecutive lags [base, base + B) of a stage (B a
+// power of two, base < L): one piece of the table serves the block, the
+// lags are read in an order rotated by the lane (so the lanes of a quarter
+// warp hit different bank groups), and (at, an) accumulate the products.
+template <int B>
+__device__ __forceinline__ void gen_block(const SweepPlan& pk, const float4* __restrict__ sring, int base, int L,
+                                          int lane, const float4* __restrict__ wtab, int wtab_pieces, float2& at,
+                                          float2& an) {
+  const float jf = static_cast<float>(pk.j0 + base) + 0.5f;  // exact: lags stay below 2^23
+  const float p = jf * pk.dsh;
+  const float e = fmaf(jf, pk.dsl, fmaf(jf, pk.dsh, -p));
+  const float qf = fminf(floorf(p * kGenInvH), static_cast<float>(wtab_pieces - 1));
+  const int q = static_cast<int>(qf);
+  const float t0 = fmaf(fmaf(-qf, kGenHf, p) + e, kGenTScale, -1.0f);
+  const float dtv = pk.dsh * kGenTScale;
+  float4 cf[kGenF4];
+#pragma unroll
+  for (int i = 0; i < kGenF4; ++i) cf[i] = __ldg(wtab + kGenF4 * q + i);
+  const float4* blk = sring + base;
+  if (base + B <= L && pk.j0 + base + B <= min(pk.mt, pk.mn)) {
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int r = (k + lane) & (B - 1);  // the lane-rotated lag order
+      slot_fma2(at, an, blk[r], gen_horner(cf, fmaf(static_cast<float>(r), dtv, t0)));
+    }
+  } else {
+    // the chunk's tail, or a field's window ending inside the block
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int r = (k + lane) & (B - 1);
+      float2 w = gen_horner(cf, fmaf(static_cast<float>(r), dtv, t0));
+      if (pk.j0 + base + r >= pk.mt) w.x = 0.0f;
+      if (pk.j0 + base + r >= pk.mn) w.y = 0.0f;
+      if (base + r < L) slot_fma2(at, an, blk[r], w);
+    }
+  }
+}
+
 // Chunk c of the sweep: the fault's own chunk table, or an ensemble table
 // whose chunks name their member (Chunk::pad) in fs.
 // gen_ds_max (GEN only): modes whose s step ds = c_s k_n dt_min is at most
@@ -1154,7 +1196,8 @@ __device__ __forceinline__ SweepPlan sweep_plan(const DevFault<R>& f0, const Dev
   if constexpr (GEN) {
     const float4 gi = f.wgen[n];
     if (gi.x <= gen_ds_max) {
-      pl.gen = 1;
+      // eight-lag blocks up to kGenDsBlockMax, four-lag blocks above
+      pl.gen = gi.x <= static_cast<float>(kGenDsBlockMax) ? 1 : 2;
       pl.j0 = static_cast<int>(m_dt + cd.i0);
       pl.dsh = gi.x;
       pl.dsl = gi.y;
@@ -1274,45 +1317,23 @@ __device__ __forceinline__ bool sweep_chunks(const DevFault<R>& f, const DevFaul
        if (!pk.gen) {
         streamed();
        } else {
-        // thread tid: lags [kGenBlock tid, kGenBlock (tid + 1)) of the chunk,
-        // read in an order rotated by the lane, so the eight lanes of a
-        // quarter warp hit eight different bank groups
-        const int base = kGenBlock * tid;
-        if (base < L) {
-          const float jf = static_cast<float>(pk.j0 + base) + 0.5f;  // exact: lags stay below 2^23
-          const float p = jf * pk.dsh;
-          const float e = fmaf(jf, pk.dsl, fmaf(jf, pk.dsh, -p));
-          const float qf = fminf(floorf(p * kGenInvH), static_cast<float>(wtab_pieces - 1));
-          const int q = static_cast<int>(qf);
-          const float t0 = fmaf(fmaf(-qf, kGenHf, p) + e, kGenTScale, -1.0f);
-          const float dtv = pk.dsh * kGenTScale;
-          float4 cf[kGenF4];
+        float2 at = make_float2(0.f, 0.f), an = make_float2(0.f, 0.f);
+        if (pk.gen == 1) {
+          // thread tid: lags [kGenBlock tid, kGenBlock (tid + 1)) of the chunk
+          const int base = kGenBlock * tid;
+          if (base < L) gen_block<kGenBlock>(pk, sring, base, L, lane, wtab, wtab_pieces, at, an);
+        } else {
+          // two blocks of four: lags [4 tid, 4 tid + 4) and the same half a stage on
 #pragma unroll
-          for (int i = 0; i < kGenF4; ++i) cf[i] = __ldg(wtab + kGenF4 * q + i);
-          const Slot<R>* blk = sring + base;
-          float2 at = make_float2(0.f, 0.f), an = make_float2(0.f, 0.f);
-          if (base + kGenBlock <= L && pk.j0 + base + kGenBlock <= min(pk.mt, pk.mn)) {
-#pragma unroll
-            for (int k = 0; k < kGenBlock; ++k) {
-              const int r = (k + lane) & (kGenBlock - 1);  // the lane-rotated lag order
-              slot_fma2(at, an, blk[r], gen_horner(cf, fmaf(static_cast<float>(r), dtv, t0)));
-            }
-          } else {
-            // the chunk's tail, or a field's window ending inside the block
-#pragma unroll
-            for (int k = 0; k < kGenBlock; ++k) {
-              const int r = (k + lane) & (kGenBlock - 1);
-              float2 w = gen_horner(cf, fmaf(static_cast<float>(r), dtv, t0));
-              if (pk.j0 + base + r >= pk.mt) w.x = 0.0f;
-              if (pk.j0 + base + r >= pk.mn) w.y = 0.0f;
-              if (base + r < L) slot_fma2(at, an, blk[r], w);
-            }
+          for (int hb = 0; hb < kGenBlock / kGenBlock4; ++hb) {
+            const int base = kGenBlock4 * tid + hb * (kGenBlock4 * NT);
+            if (base < L) gen_block<kGenBlock4>(pk, sring, base, L, lane, wtab, wtab_pieces, at, an);
           }
-          acc.tr = at.x;
-          acc.ti = at.y;
-          acc.nr = an.x;
-          acc.ni = an.y;
         }
+        acc.tr = at.x;
+        acc.ti = at.y;
+        acc.nr = an.x;
+        acc.ni = an.y;
        }
       } else {
         streamed();

@@ -155,7 +155,7 @@ def test_batch_tuner_choice_is_reported_and_keeps_results():
     chunk, blocks, ms = b.tune(reps=3)
     info = b.get_sweep()
     assert info["ctas_per_sm"] == blocks and info["shape"] in (3, 4) and chunk == 2048
-    assert info["gen_ds_max"] in (0.0, 1.0 / 256, 1.0 / 64)
+    assert info["gen_ds_max"] in (0.0, 1.0 / 256, 1.0 / 64, 1.0 / 32)
     b.enqueue(20)
     assert np.all(b.status()[0] == 0)
     for g in solo:

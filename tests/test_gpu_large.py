@@ -71,12 +71,13 @@ def test_large_N_steps_match_oracle(N, precision):
     g2.close()
 
 
-@pytest.mark.parametrize("precision,gen_ds_max,tol", [(0, 0.0, 1e-10), (1, 1.0 / 64, 2e-6), (1, 1.0 / 256, 2e-6),
-                                                      (1, 0.0, 2e-6)])
+@pytest.mark.parametrize("precision,gen_ds_max,tol", [(0, 0.0, 1e-10), (1, 1.0 / 32, 2e-6), (1, 1.0 / 64, 2e-6),
+                                                      (1, 1.0 / 256, 2e-6), (1, 0.0, 2e-6)])
 def test_history_sums_every_mode_at_65536(precision, gen_ds_max, tol):
     # the sweep alone on the N = 65536 rings (66 M slots): every mode's sums,
-    # FP32 with the weights of the modes up to ds = 1/64 evaluated on chip
-    # (the default), up to 1/256, and of none
+    # FP32 with the weights of the modes up to ds = 1/32 evaluated on chip
+    # (eight-lag blocks to 1/64, four-lag blocks above), up to 1/64 (the
+    # default), up to 1/256, and of none
     w = _workload(65536)
     o = oracle_for(w, workers=WORKERS)
     g = gpu_for(w, precision=precision)
