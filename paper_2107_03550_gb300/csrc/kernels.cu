@@ -555,12 +555,12 @@ __global__ void __launch_bounds__((1 << LGN) / 8) k_spectral_fused_b(const DevFa
 // FFTs of the rows; assembly of each pair (m, N-m) in place; inverse: row
 // FFTs, twiddle w_N^{-n1 k2}, scatter back to the column owners, barrier,
 // column FFTs, output.  N/(8C) threads per CTA, 8 values each per stage.
-template <int LGN, int EPT = kClusterEPT>
+template <int LGN, int EPT = kClusterEPT, int CC = cluster_ctas(1 << LGN)>
 struct CGeom {
   static constexpr int N = 1 << LGN;
   static constexpr int lg1 = LGN / 2, lg2 = LGN - LGN / 2;
   static constexpr int N1 = 1 << lg1, N2 = 1 << lg2;
-  static constexpr int C = cluster_ctas(N);
+  static constexpr int C = CC;
   static constexpr int cols = N1 / C, rows = N2 / C;
   static constexpr int ept = EPT;                 // values per thread and FFT stage
   static constexpr int nth = N / (EPT * C);
@@ -611,9 +611,9 @@ __device__ __forceinline__ void fft_r8_batch(float2* buf, const float2* tw, int 
   fft_r8<LGL, EPT>(buf + (tid / per) * (1 << LGL), tw, tid % per, sg);
 }
 
-template <int LGN, int EPT>
+template <int LGN, int EPT, int CC>
 __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, int pass, int m_dt, double dt) {
-  using G = CGeom<LGN, EPT>;
+  using G = CGeom<LGN, EPT, CC>;
   const unsigned c = cluster_rank();
   constexpr int N = G::N, half = N >> 1, nth = G::nth;
   constexpr int per = N / G::C;  // elements per CTA (EPT per thread)
@@ -741,14 +741,15 @@ __device__ __forceinline__ void spectral_cluster_body(const DevFault<float>& f, 
 template <int LGN, int EPT>
 __global__ void __launch_bounds__(CGeom<LGN, EPT>::nth) k_spectral_cluster(const __grid_constant__ DevFault<float> f,
                                                                             int pass, int m_dt, double dt) {
-  spectral_cluster_body<LGN, EPT>(f, pass, m_dt, dt);
+  spectral_cluster_body<LGN, EPT, cluster_ctas(1 << LGN)>(f, pass, m_dt, dt);
 }
 
 template <int LGN, int EPT>
-__global__ void __launch_bounds__(CGeom<LGN, EPT>::nth) k_spectral_cluster_b(const DevFault<float>* __restrict__ fs,
-                                                                              int pass, int m_dt) {
-  const DevFault<float>& f = fs[blockIdx.x / CGeom<LGN, EPT>::C];
-  spectral_cluster_body<LGN, EPT>(f, pass, m_dt, m_dt * f.dt_min);
+__global__ void __launch_bounds__(CGeom<LGN, EPT, batch_cluster_ctas(1 << LGN)>::nth)
+    k_spectral_cluster_b(const DevFault<float>* __restrict__ fs, int pass, int m_dt) {
+  constexpr int CC = batch_cluster_ctas(1 << LGN);
+  const DevFault<float>& f = fs[blockIdx.x / CC];
+  spectral_cluster_body<LGN, EPT, CC>(f, pass, m_dt, m_dt * f.dt_min);
 }
 
 // Row pass: for k2 in this CTA's B rows, transform t[k2 N1 + n1] over n1
@@ -2291,11 +2292,11 @@ static void allow_smem(K kernel, size_t bytes) {
 
 static size_t fused_smem(int N) { return static_cast<size_t>(N + N / 2) * sizeof(float2); }
 // cluster pass: column and row buffers (N/C each) and the N2/2 + N1/2 sub-table twiddles
-static size_t cluster_smem(int N) {
+static size_t cluster_smem(int N, int C) {
   int lg = 0;
   while ((1 << lg) < N) ++lg;
   const int N1 = 1 << (lg / 2), N2 = 1 << (lg - lg / 2);
-  const size_t per = static_cast<size_t>(N / cluster_ctas(N));
+  const size_t per = static_cast<size_t>(N / C);
   return (4 * per + N1 / 2 + N2 / 2) * sizeof(float2) + per * sizeof(ModeIn);
 }
 
@@ -2362,10 +2363,9 @@ static void launch_attr(void (*kernel)(Args...), dim3 grid, dim3 block, size_t s
 
 // Cluster launch of the FP32 spectral pass (one cluster per fault).
 template <class... Args>
-static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, cudaStream_t st, bool early,
-                                  cudaEvent_t started, Args... args) {
-  const int C = cluster_ctas(N);
-  launch_attr(kernel, dim3(C * clusters), dim3(N / (kClusterEPT * C)), cluster_smem(N), st, C, early, started,
+static void launch_cluster_kernel(void (*kernel)(Args...), int clusters, int N, int C, cudaStream_t st,
+                                  bool early, cudaEvent_t started, Args... args) {
+  launch_attr(kernel, dim3(C * clusters), dim3(N / (kClusterEPT * C)), cluster_smem(N, C), st, C, early, started,
               args...);
 }
 
@@ -2389,8 +2389,8 @@ void launch_spectral(const DevFault<R>& f, int pass, int m_dt, cudaStream_t st, 
         constexpr int LG = decltype(lg)::value;
         // pass 2 starts early behind the pass-1 Newton
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster<LG, kClusterEPT>, 1, f.N, st, pass == 2, started, f, pass, m_dt,
-                                dt);
+          launch_cluster_kernel(k_spectral_cluster<LG, kClusterEPT>, 1, f.N, cluster_ctas(f.N), st, pass == 2,
+                                started, f, pass, m_dt, dt);
         } else {
           launch_attr(k_spectral_fused<LG>, dim3(1), dim3(f.N / 8), fused_smem(f.N), st, 1, pass == 2, started, f,
                       pass, m_dt, dt);
@@ -2603,7 +2603,7 @@ void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int
       with_lgn(N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          launch_cluster_kernel(k_spectral_cluster_b<LG, kClusterEPT>, members, N, st, false,
+          launch_cluster_kernel(k_spectral_cluster_b<LG, kClusterEPT>, members, N, batch_cluster_ctas(N), st, false,
                                 static_cast<cudaEvent_t>(nullptr), fs, pass, m_dt);
         } else {
           k_spectral_fused_b<LG><<<members, N / 8, fused_smem(N), st>>>(fs, pass, m_dt);
@@ -2635,7 +2635,7 @@ void configure_batch_kernels(const FftGeom& g) {
       with_lgn(g.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          allow_smem(k_spectral_cluster_b<LG, kClusterEPT>, cluster_smem(g.N));
+          allow_smem(k_spectral_cluster_b<LG, kClusterEPT>, cluster_smem(g.N, batch_cluster_ctas(g.N)));
           cudaFuncSetAttribute(k_spectral_cluster_b<LG, kClusterEPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         } else {
           allow_smem(k_spectral_fused_b<LG>, fused_smem(g.N));
@@ -2814,7 +2814,7 @@ void configure_kernels(const FftGeom& g) {
       with_lgn(g.N, [&](auto lg) {
         constexpr int LG = decltype(lg)::value;
         if constexpr ((1 << LG) >= kClusterMinN) {
-          allow_smem(k_spectral_cluster<LG, kClusterEPT>, cluster_smem(g.N));
+          allow_smem(k_spectral_cluster<LG, kClusterEPT>, cluster_smem(g.N, cluster_ctas(g.N)));
           cudaFuncSetAttribute(k_spectral_cluster<LG, kClusterEPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         } else {
           allow_smem(k_spectral_fused<LG>, fused_smem(g.N));

@@ -118,15 +118,21 @@ struct DevFault {
 };
 
 // One-launch FP32 spectral pass: a single CTA of N/8 threads below
-// kClusterMinN, a cluster of kClusterCTAs CTAs (N/(8 kClusterCTAs) threads
-// each) from kClusterMinN to kFusedMaxN; larger N use the four-kernel path.
+// kClusterMinN, a cluster of cluster_ctas(N) CTAs from kClusterMinN to
+// kFusedMaxN; larger N use the four-kernel path.
 constexpr int kFusedMaxN = 16384;
 constexpr int kClusterMinN = 2048;
 constexpr int kClusterCTAs = 8;
-// CTAs per cluster for a given N: 16 (a non-portable cluster size) at
-// N = 16384, which halves the per-CTA shared memory so the pass fits beside
-// a history-sweep CTA on an SM.
-constexpr int cluster_ctas(int N) { return N >= 16384 ? 16 : kClusterCTAs; }
+// CTAs per cluster for a given N: 16 (a non-portable cluster size) from
+// N = 4096: half the work per CTA on the latency-bound pass (flushed steps
+// without history at N = 4096: 35.3 -> 33.0 us; N = 8192: 49.2 -> 36.9 us;
+// at N = 2048 it lost, 39.4 -> 40.9 us with history), and at N = 16384 half
+// the per-CTA shared memory, so the pass fits beside a history-sweep CTA.
+__host__ __device__ constexpr int cluster_ctas(int N) { return N >= 4096 ? 16 : kClusterCTAs; }
+// The same for the batched pass of an ensemble (one cluster per member, many
+// clusters at once, beside the overlapped sweep): 8 below N = 16384, where
+// clusters of 16 were slower (256 members: 2.42 against 2.76 ms per step).
+__host__ __device__ constexpr int batch_cluster_ctas(int N) { return N >= 16384 ? 16 : kClusterCTAs; }
 // Values per thread in each FFT stage of the cluster pass (4: radix-4
 // stages, 8: radix-8 stages with half the threads).
 #ifndef SBIEM_CLUSTER_EPT
