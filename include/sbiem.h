@@ -388,14 +388,15 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  *   (streamed, or evaluated on chip for the modes with s step up to 1/256,
  *   1/64 or 1/32 when the members share c_s, c_p and dt_min) and 1 .. (occupancy
  *   limit) resident sweep CTAs per SM, reps timed launches each (median), and
- *   keeps the fastest, then the faster of the one-launch and two-launch
- *   forms (sbiem_batch_set_persistent); returns the chunk length, the CTAs
- *   per SM chosen and the time (sbiem_batch_get_sweep gives the rest).  It
- *   then times the overlapped step's two branches together (the next
- *   step's sweep beside the passes) for 1 .. (occupancy limit) sweep CTAs
- *   per SM, and makes later steps overlap when the best of those beats the
- *   sweep followed by the passes (a new batch steps without overlap).  The
- *   committed state is not changed.
+ *   keeps the fastest.  It then chooses the history form (one persistent
+ *   launch or two launches, sbiem_batch_set_persistent) and the overlap
+ *   together: for each form, the sweep alone followed by the passes, and
+ *   the overlapped step's two branches timed together (the next step's
+ *   sweep beside the passes) for 1 .. (occupancy limit) sweep CTAs per SM;
+ *   the fastest candidate is kept (a new batch steps without overlap).
+ *   Returns the chunk length, the CTAs per SM chosen and the sweep's time
+ *   (sbiem_batch_get_sweep gives the rest).  The committed state is not
+ *   changed.
  * sbiem_batch_set_overlap: overlap on (1) or off (0) by hand; *on_out (may
  *   be NULL) gets the setting in force before the call.  Results agree
  *   either way up to summation order.

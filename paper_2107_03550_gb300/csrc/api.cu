@@ -2251,39 +2251,17 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
   b->per_sm_gen = b->gen ? persist_blocks_per_sm<float>(b->shape, true) : b->per_sm_gen;
   b->per_sm = b->gen ? b->per_sm_gen : b->per_sm_plain;
   b->hist_grid = b->sm_count * best_b;
-  // the one-launch form or the two-launch form, whichever is faster (the
-  // two agree bitwise)
+  // The history form (one persistent launch or two launches; they agree
+  // bitwise) and the overlap are chosen together: the cooperative launch
+  // waits for room beside the passes, so which form is faster depends on the
+  // overlap (256 members: 2.66 ms per step persistent without overlap, 2.42
+  // ms two-launch with it).  Candidates: each form without overlap (its
+  // sweep alone + the passes) and each form with overlap (its next-step
+  // sweep and the passes timed together, for 1 .. (occupancy limit) sweep
+  // CTAs per SM).  The passes write only staging arrays, so timing them
+  // leaves the committed state alone; the status words they may set are put
+  // back.  Nine timed launches at least per candidate: the totals are close.
   {
-    float tf[2] = {0.f, 0.f};
-    for (int form = 0; form < 2; ++form) {
-      b->persistent = form == 1;
-      if (b->fp32) batch_history<float>(b, b->stream);
-      else batch_history<double>(b, b->stream);
-      std::vector<float> t;
-      for (int k = 0; k < reps; ++k) {
-        CK(cudaEventRecord(e0, b->stream));
-        if (b->fp32) batch_history<float>(b, b->stream);
-        else batch_history<double>(b, b->stream);
-        CK(cudaEventRecord(e1, b->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        t.push_back(ms);
-      }
-      std::sort(t.begin(), t.end());
-      tf[form] = t[t.size() / 2];
-    }
-    b->persistent = tf[1] <= tf[0];
-    best = std::min(tf[0], tf[1]);
-  }
-  // overlap or not: the overlapped step takes about max(lag sweep, passes),
-  // the plain one sweep + passes.  The passes write only staging arrays, so
-  // timing them leaves the committed state alone; the status words they may
-  // set are put back.
-  {
-    // the overlap decision compares two close totals: at least nine timed
-    // launches each (with five the 256-member ensemble's choice flipped
-    // between runs, 2.42 against 2.66 ms per step)
     const int reps_ov = std::max(reps, 9);
     auto timed = [&](auto&& launch, float* out) -> int {
       launch();
@@ -2312,38 +2290,56 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
       else batch_passes<double>(b, b->stream, b->ev_fork);
     }, &t_pass);
     if (rc) return rc;
-    // the overlapped step's two branches timed together (next step's sweep
-    // on the side stream, the passes on the batch's stream), for 1 ..
-    // (occupancy limit) sweep CTAs per SM
     const int lim = b->gen ? persist_blocks_per_sm<float>(b->shape, true)
                            : (b->fp32 ? persist_blocks_per_sm<float>(b->shape, false)
                                       : persist_blocks_per_sm<double>(b->shape, false));
-    float t_ov = 1e30f;
+    float t_best = 1e30f, t_sweep_kept = best;
+    bool ov_best = false, pers_best = true;
     int lag_best = b->lag_grid;
-    for (int lc = 1; lc <= std::max(1, lim); ++lc) {
-      b->lag_grid = b->sm_count * lc;
-      float t = 0.f;
+    for (int form = 0; form < 2; ++form) {
+      b->persistent = form == 1;
+      float t_sw = 0.f;
       rc = timed([&] {
-        cudaEventRecord(b->ev_fork, b->stream);
-        cudaStreamWaitEvent(b->side, b->ev_fork, 0);
-        if (b->fp32) batch_history<float>(b, b->side, true);
-        else batch_history<double>(b, b->side, true);
-        cudaEventRecord(b->ev_side, b->side);
-        if (b->fp32) batch_passes<float>(b, b->stream, b->ev_fork);
-        else batch_passes<double>(b, b->stream, b->ev_fork);
-        cudaStreamWaitEvent(b->stream, b->ev_side, 0);
-      }, &t);
+        if (b->fp32) batch_history<float>(b, b->stream);
+        else batch_history<double>(b, b->stream);
+      }, &t_sw);
       if (rc) return rc;
-      if (t < t_ov) {
-        t_ov = t;
-        lag_best = b->lag_grid;
+      if (t_sw + t_pass < t_best) {
+        t_best = t_sw + t_pass;
+        ov_best = false;
+        pers_best = b->persistent;
+        t_sweep_kept = t_sw;
+      }
+      for (int lc = 1; lc <= std::max(1, lim); ++lc) {
+        b->lag_grid = b->sm_count * lc;
+        float t = 0.f;
+        rc = timed([&] {
+          cudaEventRecord(b->ev_fork, b->stream);
+          cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+          if (b->fp32) batch_history<float>(b, b->side, true);
+          else batch_history<double>(b, b->side, true);
+          cudaEventRecord(b->ev_side, b->side);
+          if (b->fp32) batch_passes<float>(b, b->stream, b->ev_fork);
+          else batch_passes<double>(b, b->stream, b->ev_fork);
+          cudaStreamWaitEvent(b->stream, b->ev_side, 0);
+        }, &t);
+        if (rc) return rc;
+        if (t < t_best) {
+          t_best = t;
+          ov_best = true;
+          pers_best = b->persistent;
+          lag_best = b->lag_grid;
+          t_sweep_kept = t_sw;
+        }
       }
     }
+    b->persistent = pers_best;
+    b->overlap = ov_best;
     b->lag_grid = lag_best;
+    best = t_sweep_kept;
     for (size_t r = 0; r < b->members.size(); ++r)
       CK(cudaMemcpyAsync(b->members[r]->f64.status, &st0[r], sizeof(unsigned), cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    b->overlap = t_ov < best + t_pass;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
