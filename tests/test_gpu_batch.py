@@ -165,3 +165,32 @@ def test_batch_tuner_choice_is_reported_and_keeps_results():
         for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
             assert rel(s2[k], s1[k]) <= 1e-5, k
     b.close()
+
+
+def test_weight_sharing_only_where_the_weights_agree():
+    # Sharing needs equal dx (equal wavenumbers for modes n and 2^p n) and one
+    # cutting plane (each field's window the mode's): members with another dx
+    # or a second plane keep their own weights, and every member still steps
+    # as it does alone.
+    from paper_2107_03550_gb300.sbiem import Batch
+    base = [rough_fault(N, 10.0, 3e-3, seed=700 + k) for k, N in enumerate((256, 512, 1024))]
+    other_dx = rough_fault(512, 5.0, 3e-3, seed=710)
+    ws = base + [other_dx]
+    kw = [{}, {}, {}, {}]
+    kw.append({"kcN_L": 400.0})
+    ws.append(rough_fault(512, 10.0, 3e-3, seed=711))
+    solo = [gpu_for(w, precision=1, **k) for w, k in zip(ws, kw)]
+    mem = [gpu_for(w, precision=1, **k) for w, k in zip(ws, kw)]
+    b = Batch(mem)
+    # the three of dx = 10 m share the N = 1024 member's weights; the dx = 5 m
+    # member and the two-plane member read their own
+    assert b.get_sweep()["distinct_weights"] == 3
+    b.enqueue(15)
+    assert np.all(b.status()[0] == 0)
+    for g in solo:
+        g.enqueue(15)
+    for g1, g2 in zip(solo, mem):
+        s1, s2 = g1.get_state(), g2.get_state()
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert rel(s2[k], s1[k]) <= 1e-5, k
+    b.close()
