@@ -370,9 +370,10 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  * between the two.
  *
  * sbiem_batch_create: n member handles (not owned); they must share the
- *   device, the precision and the history sweep shape; chunk_slots must be 0
- *   or the members' chunk length.  Errors: SBIEM_ERR_INVALID,
- *   SBIEM_ERR_NOMEM.
+ *   device and the precision.  chunk_slots: the lags per chunk of the
+ *   batch's own chunk table (0: the members' length; else the chunk length
+ *   of a sweep shape, 256/512/1024 FP64 or 512/1024/2048 FP32).  Errors:
+ *   SBIEM_ERR_INVALID, SBIEM_ERR_NOMEM.
  * sbiem_batch_enqueue: nsteps steps of each member's dt_min, asynchronous.
  * sbiem_batch_status: synchronize; per member (caller order) status flags
  *   and committed steps (arrays of n, may be NULL).
@@ -384,7 +385,8 @@ int sbiem_read_probe(const void* data, int64_t bytes, float* sink, void* stream)
  *   one copy).  The sweep then copies ring slots under an L2 evict-first
  *   policy so that the shared weight runs stay in L2.
  * sbiem_batch_tune: autotuner -- times the batched history convolution for
- *   every sweep shape that keeps the members' chunk length, each weight form
+ *   every sweep shape (with the batch's chunk table of that shape's chunk
+ *   length, built once per length), each weight form
  *   (streamed, or evaluated on chip for the modes with s step up to 1/256,
  *   1/64 or 1/32 when the members share c_s, c_p and dt_min) and 1 .. (occupancy
  *   limit) resident sweep CTAs per SM, reps timed launches each (median), and

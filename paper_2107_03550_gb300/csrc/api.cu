@@ -1737,7 +1737,16 @@ struct sbiem_batch_s {
   Chunk* chunks = nullptr;      // members' chunk tables, concatenated (member in Chunk::pad)
   int nchunks = 0;
   double4* partial = nullptr;   // sweep partials per chunk
-  int64_t* cbase = nullptr;     // first chunk of each member
+  int2* fc = nullptr;           // (first chunk, chunks) of each (member, mode) pair, mm order
+  // chunk tables by chunk length (the autotuner tries every shape's); the
+  // pointers above are those of the length in force (chunk_slots)
+  struct ChunkSet {
+    Chunk* chunks;
+    double4* partial;
+    int2* fc;
+    int n;
+  };
+  std::map<int64_t, ChunkSet> sets;
   int2* mm = nullptr;           // (member, mode) pairs of the per-mode sums
   int TM = 0;
   int shape = 0;                // sweep shape shared by the members
@@ -1823,29 +1832,63 @@ int64_t weight_ratio(const sbiem_s* r, const sbiem_s* c) {
 // Ensemble chunk table: the members' own chunk tables one after another
 // (member index in Chunk::pad), each member's first chunk, the (member,
 // mode) list of the per-mode sums; member descriptors on the device.
+// The ensemble's chunk table for chunks of at most `slots` lags (built once
+// per length, then reused): every member's modes in order, each mode's ring
+// cut into runs of `slots` lags (member in Chunk::pad), and per (member,
+// mode) pair its first chunk and count.  Makes that length the one in force.
+int batch_use_chunks(sbiem_batch_s* b, int64_t slots) {
+  auto it = b->sets.find(slots);
+  if (it == b->sets.end()) {
+    std::vector<Chunk> ch;
+    std::vector<int2> fc;
+    for (size_t r = 0; r < b->members.size(); ++r) {
+      const sbiem_s* s = b->members[r];
+      for (int n = 0; n < s->nmodes; ++n) {
+        const int64_t cnt = (s->Rn[n] + slots - 1) / slots;
+        fc.push_back(make_int2(static_cast<int>(ch.size()), static_cast<int>(cnt)));
+        for (int64_t c = 0; c < cnt; ++c) {
+          Chunk x{};
+          x.mode = n;
+          x.first = static_cast<int32_t>(ch.size() - c);
+          x.count = static_cast<int32_t>(cnt);
+          x.pad = static_cast<int32_t>(r);
+          x.i0 = c * slots;
+          x.i1 = std::min<int64_t>((c + 1) * slots, s->Rn[n]);
+          ch.push_back(x);
+        }
+      }
+      if (ch.size() > static_cast<size_t>(1) << 30) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
+    }
+    sbiem_batch_s::ChunkSet cs{};
+    cs.n = static_cast<int>(ch.size());
+    cs.chunks = static_cast<Chunk*>(batch_alloc(b, sizeof(Chunk) * std::max<size_t>(ch.size(), 1)));
+    cs.partial = static_cast<double4*>(batch_alloc(b, sizeof(double4) * std::max<size_t>(ch.size(), 1)));
+    cs.fc = static_cast<int2*>(batch_alloc(b, sizeof(int2) * std::max<size_t>(fc.size(), 1)));
+    if (!cs.chunks || !cs.partial || !cs.fc) return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed (chunks)");
+    if (!ch.empty()) CK(cudaMemcpy(cs.chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice));
+    if (!fc.empty()) CK(cudaMemcpy(cs.fc, fc.data(), sizeof(int2) * fc.size(), cudaMemcpyHostToDevice));
+    it = b->sets.emplace(slots, cs).first;
+  }
+  b->chunks = it->second.chunks;
+  b->partial = it->second.partial;
+  b->fc = it->second.fc;
+  b->nchunks = it->second.n;
+  b->chunk_slots = slots;
+  return SBIEM_OK;
+}
+
 template <class R>
 int batch_build(sbiem_batch_s* b) {
-  std::vector<Chunk> ch;
-  std::vector<int64_t> cbase(b->members.size(), 0);
   std::vector<int2> mm;
-  for (size_t r = 0; r < b->members.size(); ++r) {
-    const sbiem_s* s = b->members[r];
-    cbase[r] = static_cast<int64_t>(ch.size());
-    for (Chunk c : s->chunks) {
-      c.pad = static_cast<int32_t>(r);
-      ch.push_back(c);
-    }
-    for (int n = 0; n < s->nmodes; ++n) mm.push_back(make_int2(static_cast<int>(r), n));
-  }
-  if (ch.size() > static_cast<size_t>(1) << 30) return fail(SBIEM_ERR_INVALID, "batch: too many chunks");
-  b->chunks = static_cast<Chunk*>(batch_alloc(b, sizeof(Chunk) * std::max<size_t>(ch.size(), 1)));
-  b->partial = static_cast<double4*>(batch_alloc(b, sizeof(double4) * std::max<size_t>(ch.size(), 1)));
-  b->cbase = static_cast<int64_t*>(batch_alloc(b, sizeof(int64_t) * cbase.size()));
+  for (size_t r = 0; r < b->members.size(); ++r)
+    for (int n = 0; n < b->members[r]->nmodes; ++n) mm.push_back(make_int2(static_cast<int>(r), n));
   b->mm = static_cast<int2*>(batch_alloc(b, sizeof(int2) * std::max<size_t>(mm.size(), 1)));
   b->fs = batch_alloc(b, sizeof(DevFault<R>) * b->members.size());
   b->bar = static_cast<unsigned*>(batch_alloc(b, 2 * sizeof(unsigned)));
-  if (!b->chunks || !b->partial || !b->cbase || !b->mm || !b->fs || !b->bar)
-    return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed");
+  if (!b->mm || !b->fs || !b->bar) return fail(SBIEM_ERR_NOMEM, "batch: device allocation failed");
+  CK(cudaStreamSynchronize(b->stream));
+  const int rc_ch = batch_use_chunks(b, b->chunk_slots);
+  if (rc_ch) return rc_ch;
   CK(cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream));
   std::vector<DevFault<R>> fs(b->members.size());
   for (size_t r = 0; r < b->members.size(); ++r) {
@@ -1901,13 +1944,9 @@ int batch_build(sbiem_batch_s* b) {
     b->distinct_weights += first ? 1 : 0;
   }
   b->shared_weights = b->distinct_weights < static_cast<int>(fs.size());
-  if (!ch.empty())
-    CK(cudaMemcpyAsync(b->chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice, b->stream));
-  CK(cudaMemcpyAsync(b->cbase, cbase.data(), sizeof(int64_t) * cbase.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->mm, mm.data(), sizeof(int2) * mm.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaMemcpyAsync(b->fs, fs.data(), sizeof(DevFault<R>) * fs.size(), cudaMemcpyHostToDevice, b->stream));
   CK(cudaStreamSynchronize(b->stream));
-  b->nchunks = static_cast<int>(ch.size());
   b->TM = static_cast<int>(mm.size());
   return SBIEM_OK;
 }
@@ -1925,12 +1964,12 @@ void batch_history(sbiem_batch_s* b, cudaStream_t st, bool ahead = false) {
   if (grid > b->nchunks) grid = b->nchunks > 0 ? b->nchunks : 1;
   if (!b->persistent) {
     launch_history_batch<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm,
-                            b->TM, b->cbase, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
+                            b->TM, b->fc, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
                             b->gen ? b->gen_pieces : 0, b->gen ? b->gen_ds_max : 0.0f, b->shared_weights);
     return;
   }
   launch_history_persist<R>(static_cast<const DevFault<R>*>(b->fs), b->chunks, b->nchunks, b->partial, b->mm, b->TM,
-                            b->cbase, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
+                            b->fc, b->shape, grid, ahead ? 2 : 1, st, ahead, b->gen ? b->wtab : nullptr,
                             b->gen ? b->gen_pieces : 0, b->gen ? b->gen_ds_max : 0.0f, b->bar, b->bar + 1,
                             b->bar_limit, static_cast<int>(b->members.size()), b->shared_weights);
 }
@@ -2016,8 +2055,15 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
     }
   b->shape = members[0]->sweep_shape;
   if (chunk_slots > 0 && chunk_slots != members[0]->chunk_slots) {
-    delete b;
-    return fail(SBIEM_ERR_INVALID, "chunk_slots must be 0 or the members' chunk length");
+    // another chunk length: the first sweep shape with chunks of that length
+    int sh_ok = -1;
+    for (int sh = 0; sh <= 4 && sh_ok < 0; ++sh)
+      if (sweep_chunk_slots(fp32 ? 1 : 0, sh) == chunk_slots) sh_ok = sh;
+    if (sh_ok < 0) {
+      delete b;
+      return fail(SBIEM_ERR_INVALID, "chunk_slots must be 0 or the chunk length of a sweep shape");
+    }
+    b->shape = sh_ok;
   }
   cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, members[0]->device);
   if (fp32) {
@@ -2044,7 +2090,7 @@ int sbiem_batch_create(sbiem_batch_t* out, int n, const sbiem_t* members, int64_
   if (b->per_sm_gen < 1) b->per_sm_gen = 1;
   b->per_sm = b->gen ? b->per_sm_gen : b->per_sm_plain;
   b->hist_grid = b->sm_count * b->per_sm;
-  b->chunk_slots = members[0]->chunk_slots;
+  b->chunk_slots = chunk_slots > 0 ? chunk_slots : members[0]->chunk_slots;
   if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
     delete b;
     return fail(SBIEM_ERR_CUDA, "stream creation failed");
@@ -2204,12 +2250,15 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
     for (double v : {kGenDsBlockMax / 4.0, kGenDsBlockMax, kGenDsBlock4Max}) thr.push_back(static_cast<float>(v));
   // the sweep shapes that keep the members' chunk length (their chunk
   // tables and per-mode chunk ranges stay valid)
-  std::vector<int> shapes;
+  // every sweep shape, each with the ensemble's chunk table of its chunk
+  // length (the mode-block size: 512, 1024 or 2048 lags in FP32)
   const int prec = b->fp32 ? 1 : 0;
   for (int sh = 0; sh <= 4; ++sh)
-    if (sweep_chunk_slots(prec, sh) == b->chunk_slots) shapes.push_back(sh);
-  for (int sh : shapes)
   for (float tv : thr) {
+    {
+      const int rc_ch = batch_use_chunks(b, sweep_chunk_slots(prec, sh));
+      if (rc_ch) return rc_ch;
+    }
     b->shape = sh;
     b->gen = tv > 0.0f;
     b->gen_ds_max = tv;
@@ -2244,6 +2293,10 @@ int sbiem_batch_tune(sbiem_batch_t b, int reps, int64_t* chunk_out, int* blocks_
     }
   }
   b->shape = best_shape;
+  {
+    const int rc_ch = batch_use_chunks(b, sweep_chunk_slots(prec, best_shape));
+    if (rc_ch) return rc_ch;
+  }
   b->gen = best_gen;
   b->gen_ds_max = best_thr;
   b->per_sm_plain = b->fp32 ? persist_blocks_per_sm<float>(b->shape, false)

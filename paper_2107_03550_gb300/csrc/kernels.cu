@@ -1443,17 +1443,18 @@ __global__ void k_sweep_finish(const __grid_constant__ DevFault<R> f, double2* o
 }
 
 // Ensemble form of k_sweep_finish: one thread per (member, mode) pair
-// mm[t]; the member's chunks sit at cbase[member] + its own chunk indices in
-// the ensemble's chunk table.  Members whose step failed are left alone.
+// mm[t], whose chunks are [fc[t].x, fc[t].x + fc[t].y) of the ensemble's
+// chunk table.  Members whose step failed are left alone.
 template <class R>
 __device__ __forceinline__ void finish_pair(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int t,
-                                            const int64_t* __restrict__ cbase, int nch, int G,
+                                            const int2* __restrict__ fc, int nch, int G,
                                             const double4* __restrict__ partial, bool ahead) {
   const int2 rn = mm[t];
   const DevFault<R>& f = fs[rn.x];
   if (*f.status) return;
   const int n = rn.y;
-  const int64_t F = cbase[rn.x] + f.mfirst[n], E = F + f.mcount[n];
+  const int2 q = fc[t];
+  const int64_t F = q.x, E = F + q.y;
   double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
   if (E > F) {
     auto c0 = [&](int64_t b) { return b * nch / G; };
@@ -1484,10 +1485,10 @@ __device__ __forceinline__ void finish_pair(const DevFault<R>* __restrict__ fs, 
 
 template <class R>
 __global__ void k_sweep_finish_b(const DevFault<R>* __restrict__ fs, const int2* __restrict__ mm, int TM,
-                                 const int64_t* __restrict__ cbase, int nch, int G,
+                                 const int2* __restrict__ fc, int nch, int G,
                                  const double4* __restrict__ partial, bool ahead) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < TM) finish_pair<R>(fs, mm, t, cbase, nch, G, partial, ahead);
+  if (t < TM) finish_pair<R>(fs, mm, t, fc, nch, G, partial, ahead);
 }
 
 // The ensemble's history convolution in one persistent launch (cooperative:
@@ -1511,7 +1512,7 @@ template <class R, int SH, bool GEN>
 __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
     k_sweep_persist(const DevFault<R>* __restrict__ fs, const Chunk* __restrict__ chunks, int nch,
                     double4* __restrict__ partial, int m_dt, const float4* __restrict__ wtab, int wtab_pieces,
-                    float gen_ds_max, const int2* __restrict__ mm, int TM, const int64_t* __restrict__ cbase,
+                    float gen_ds_max, const int2* __restrict__ mm, int TM, const int2* __restrict__ fc,
                     bool ahead, const SweepBarrier bar, bool ring_evict_first) {
   __shared__ unsigned s_epoch, s_fail;
   const int tid = threadIdx.x;
@@ -1558,7 +1559,7 @@ __global__ void __launch_bounds__(sweep_threads(GEN), GEN ? 4 : 1)
   __syncthreads();
   if (s_fail) return;
   for (int t = blockIdx.x * blockDim.x + tid; t < TM; t += gridDim.x * blockDim.x)
-    finish_pair<R>(fs, mm, t, cbase, nch, gridDim.x, partial, ahead);
+    finish_pair<R>(fs, mm, t, fc, nch, gridDim.x, partial, ahead);
 }
 
 // ------------------------------------------------------------ friction
@@ -2527,7 +2528,7 @@ int sweep_chunk_slots(int precision, int shape) {
 
 template <class R>
 void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
-                            const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
+                            const int2* mm, int TM, const int2* fc, int shape, int grid, int m_dt,
                             cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max,
                             unsigned* bar_count, unsigned* bar_epoch, long long bar_limit, int members,
                             bool ring_evict_first) {
@@ -2548,12 +2549,12 @@ void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchu
       if constexpr (sizeof(R) == 4) {
         cfg.blockDim = dim3(sweep_threads(true));
         cudaLaunchKernelEx(&cfg, k_sweep_persist<R, SH, true>, fs, chunks, nchunks, partial, m_dt, wtab, wtab_pieces,
-                           gen_ds_max, mm, TM, cbase, ahead, bar, ring_evict_first);
+                           gen_ds_max, mm, TM, fc, ahead, bar, ring_evict_first);
       }
     } else {
       cfg.blockDim = dim3(sweep_threads(false));
       cudaLaunchKernelEx(&cfg, k_sweep_persist<R, SH, false>, fs, chunks, nchunks, partial, m_dt,
-                         static_cast<const float4*>(nullptr), 0, 0.0f, mm, TM, cbase, ahead, bar, ring_evict_first);
+                         static_cast<const float4*>(nullptr), 0, 0.0f, mm, TM, fc, ahead, bar, ring_evict_first);
     }
   });
 }
@@ -2577,7 +2578,7 @@ int persist_blocks_per_sm(int shape, bool gen) {
 
 template <class R>
 void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks, double4* partial,
-                          const int2* mm, int TM, const int64_t* cbase, int shape, int grid, int m_dt,
+                          const int2* mm, int TM, const int2* fc, int shape, int grid, int m_dt,
                           cudaStream_t st, bool ahead, const float4* wtab, int wtab_pieces, float gen_ds_max,
                           bool ring_evict_first) {
   const int G = sweep_grid(grid, nchunks);
@@ -2592,7 +2593,7 @@ void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunk
         k_sweep<R, SH, true, false><<<G, kSweepThreads, sweep_smem<R, SH>(), st>>>(
             none, fs, chunks, nchunks, partial, m_dt, nullptr, 0, 0.0f, ring_evict_first);
     });
-  k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, cbase, nchunks, G, partial, ahead);
+  k_sweep_finish_b<R><<<(TM + 255) / 256, 256, 0, st>>>(fs, mm, TM, fc, nchunks, G, partial, ahead);
 }
 
 template <class R>
@@ -2834,18 +2835,18 @@ void configure_kernels(const FftGeom& g) {
 }
 
 template void launch_history_persist<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
-                                             const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                             const int2*, int, int, int, cudaStream_t, bool, const float4*, int,
                                              float, unsigned*, unsigned*, long long, int, bool);
 template void launch_history_persist<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
-                                            const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                            const int2*, int, int, int, cudaStream_t, bool, const float4*, int,
                                             float, unsigned*, unsigned*, long long, int, bool);
 template int persist_blocks_per_sm<double>(int, bool);
 template int persist_blocks_per_sm<float>(int, bool);
 template void launch_history_batch<double>(const DevFault<double>*, const Chunk*, int, double4*, const int2*, int,
-                                           const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                           const int2*, int, int, int, cudaStream_t, bool, const float4*, int,
                                            float, bool);
 template void launch_history_batch<float>(const DevFault<float>*, const Chunk*, int, double4*, const int2*, int,
-                                          const int64_t*, int, int, int, cudaStream_t, bool, const float4*, int,
+                                          const int2*, int, int, int, cudaStream_t, bool, const float4*, int,
                                           float, bool);
 template void launch_pass_batch<double>(const FftGeom&, const DevFault<double>*, int, int, int, int, cudaStream_t);
 template void launch_pass_batch<float>(const FftGeom&, const DevFault<float>*, int, int, int, int, cudaStream_t);

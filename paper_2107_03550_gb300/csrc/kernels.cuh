@@ -161,14 +161,15 @@ int sweep_chunk_slots(int precision, int shape);
 template <class R> void launch_history_ahead(const DevFault<R>& f, int m_dt, int grid, cudaStream_t st);
 // Ensemble launches: fs is a device array of member descriptors; the pass and
 // commit kernels take one member per blockIdx.y (all members of equal N).
-// Ensemble history sums: one bulk-async sweep over the concatenated chunk
-// tables of all members (member in Chunk::pad), then per (member, mode) sums
-// into each member's AT/AN; cbase[r] is member r's first chunk.
+// Ensemble history sums: one bulk-async sweep over the ensemble's chunk
+// table (every member's modes in order, member in Chunk::pad), then per
+// (member, mode) pair mm[t] the sum of its chunks [fc[t].x, fc[t].x +
+// fc[t].y) into the member's AT/AN.
 // wtab (FP32 only, or NULL): the members' shared on-chip weight table of
 // wtab_pieces pieces (every member's wgen must then be set); modes with
 // ds <= gen_ds_max evaluate their weights from it.
 template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
-                                             double4* partial, const int2* mm, int TM, const int64_t* cbase,
+                                             double4* partial, const int2* mm, int TM, const int2* fc,
                                              int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
                                              const float4* wtab = nullptr, int wtab_pieces = 0,
                                              float gen_ds_max = 0.0f, bool ring_evict_first = false);
@@ -180,7 +181,7 @@ template <class R> void launch_history_batch(const DevFault<R>* fs, const Chunk*
 // under an L2 evict-first policy (members share their weight runs, which
 // then stay in L2).
 template <class R> void launch_history_persist(const DevFault<R>* fs, const Chunk* chunks, int nchunks,
-                                               double4* partial, const int2* mm, int TM, const int64_t* cbase,
+                                               double4* partial, const int2* mm, int TM, const int2* fc,
                                                int shape, int grid, int m_dt, cudaStream_t st, bool ahead,
                                                const float4* wtab, int wtab_pieces, float gen_ds_max,
                                                unsigned* bar_count, unsigned* bar_epoch, long long bar_limit,

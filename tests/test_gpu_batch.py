@@ -144,9 +144,9 @@ def test_two_launch_form_equals_persistent_and_weights_shared(precision):
 
 
 def test_batch_tuner_choice_is_reported_and_keeps_results():
-    # the tuner picks the sweep shape (among those keeping the members' chunk
-    # length), the weight form and the CTAs per SM; the step stays that of the
-    # solo handles to FP32 rounding
+    # the tuner picks the sweep shape with its chunk length (the ensemble
+    # builds a chunk table per length), the weight form and the CTAs per SM;
+    # the step stays that of the solo handles to FP32 rounding
     from paper_2107_03550_gb300.sbiem import Batch
     ws = _ensemble(600)
     solo = [gpu_for(w, precision=1) for w in ws]
@@ -154,7 +154,10 @@ def test_batch_tuner_choice_is_reported_and_keeps_results():
     b = Batch(mem)
     chunk, blocks, ms = b.tune(reps=3)
     info = b.get_sweep()
-    assert info["ctas_per_sm"] == blocks and info["shape"] in (3, 4) and chunk == 2048
+    # the chunk length goes with the shape (FP32: 512 lags for shapes 0 and
+    # 2, 1024 for shape 1, 2048 for shapes 3 and 4)
+    assert info["ctas_per_sm"] == blocks
+    assert chunk == {0: 512, 1: 1024, 2: 512, 3: 2048, 4: 2048}[info["shape"]]
     assert info["gen_ds_max"] in (0.0, 1.0 / 256, 1.0 / 64, 1.0 / 32)
     b.enqueue(20)
     assert np.all(b.status()[0] == 0)
@@ -189,6 +192,26 @@ def test_weight_sharing_only_where_the_weights_agree():
     assert np.all(b.status()[0] == 0)
     for g in solo:
         g.enqueue(15)
+    for g1, g2 in zip(solo, mem):
+        s1, s2 = g1.get_state(), g2.get_state()
+        for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+            assert rel(s2[k], s1[k]) <= 1e-5, k
+    b.close()
+
+
+@pytest.mark.parametrize("chunk_slots", [512, 1024])
+def test_batch_with_another_chunk_length_equals_solo(chunk_slots):
+    # a batch cut into shorter chunks than its members' (its own chunk table)
+    # steps like the solo handles
+    from paper_2107_03550_gb300.sbiem import Batch
+    ws = _ensemble(800)
+    solo = [gpu_for(w, precision=1) for w in ws]
+    mem = [gpu_for(w, precision=1) for w in ws]
+    b = Batch(mem, chunk_slots=chunk_slots)
+    b.enqueue(12)
+    assert np.all(b.status()[0] == 0)
+    for g in solo:
+        g.enqueue(12)
     for g1, g2 in zip(solo, mem):
         s1, s2 = g1.get_state(), g2.get_state()
         for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
