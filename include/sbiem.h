@@ -515,10 +515,13 @@ int sbiem_footprint(sbiem_t s, int64_t* history_bytes_per_step, int64_t* device_
  * the autotuner: it times `reps` launches (median, after one untimed) of the
  * history convolution for every shape of the handle's chunk length, the
  * thresholds 0, 1/512, 1/256, 1/128, 1/64 and 1/32, and 1 .. (occupancy limit)
- * CTAs per SM, and keeps the fastest; then it times the next step's sweep
- * (the overlapped form of sbiem_enqueue) together with the two passes it
- * runs beside, for 1 .. (occupancy limit) sweep CTAs per SM, and keeps the
- * fastest.  Nothing is committed while it times; the committed state is
+ * CTAs per SM, and keeps the fastest; then, in the FP32 form with N <=
+ * 16384 (one-launch passes), it times the next step's sweep (the overlapped
+ * form of sbiem_enqueue) together with the two passes it runs beside, for
+ * 1 .. (occupancy limit) sweep CTAs per SM, and keeps the fastest; in the
+ * FP32 form with N > 16384 it times the best setting of each shape over
+ * real overlapped steps, each undone after its timing (state and the
+ * overwritten ring slots restored), and keeps the fastest step.  Nothing is committed while it times; the committed state is
  * unchanged.  Errors: SBIEM_ERR_INVALID, SBIEM_ERR_UNSUPPORTED
  * (gen_ds_max > 0 without a table), SBIEM_ERR_CUDA.
  */

@@ -125,6 +125,7 @@ struct sbiem_s {
   double2* snap_spec = nullptr;  // dhat, khat
   int32_t* snap_head = nullptr;
   long long* snap_steps = nullptr;
+  void* tune_slots = nullptr;   // one ring slot per mode (the autotuner's timed steps)
   void* undo = nullptr;          // ring-sized
   double* dfull = nullptr;
   double* d_err = nullptr;
@@ -405,6 +406,18 @@ void enqueue_trial(sbiem_s* s, int m, cudaStream_t st) {
 void ring_undo(sbiem_s* s, int m, int dir) {
   if (s->fp32()) launch_ring_undo<float>(s->f32, m, s->undo, dir, s->stream);
   else launch_ring_undo<double>(s->f64, m, s->undo, dir, s->stream);
+}
+
+// Device buffers of the state snapshot (allocated on first use).
+bool ensure_snapshot(sbiem_s* s) {
+  bool ok = true;
+  if (!s->snap) {
+    s->snap = alloc_n<double>(s, static_cast<size_t>(6) * s->N + 1, &ok);
+    s->snap_spec = alloc_n<double2>(s, static_cast<size_t>(2) * s->nmodes, &ok);
+    s->snap_head = alloc_n<int32_t>(s, s->nmodes, &ok);
+    s->snap_steps = alloc_n<long long>(s, 1, &ok);
+  }
+  return ok && s->snap && s->snap_spec && s->snap_head && s->snap_steps;
 }
 
 // Save (save = true) or restore the committed state that a step changes.
@@ -1042,19 +1055,15 @@ int sbiem_run(sbiem_t s, double t_end, double eps0, int64_t m0, int64_t m_max, i
   if (!s || !(eps0 > 0) || m0 < 1 || m_max < 1 || max_steps < 0) return fail(SBIEM_ERR_INVALID, "bad argument");
   s->lag_m = -1;  // trial steps and rollbacks below compute their own sums
   auto& f = s->f64;
-  bool ok = true;
-  if (!s->snap) {
-    s->snap = alloc_n<double>(s, static_cast<size_t>(6) * s->N + 1, &ok);
-    s->snap_spec = alloc_n<double2>(s, static_cast<size_t>(2) * s->nmodes, &ok);
-    s->snap_head = alloc_n<int32_t>(s, s->nmodes, &ok);
-    s->snap_steps = alloc_n<long long>(s, 1, &ok);
+  bool ok = ensure_snapshot(s);
+  if (!s->undo) {
     s->dfull = alloc_n<double>(s, s->N, &ok);
     s->d_err = alloc_n<double>(s, 1, &ok);
     const size_t slot = s->fp32() ? sizeof(Slot32) : sizeof(Slot64);
     s->undo = dev_alloc(s, slot * static_cast<size_t>(std::max<int64_t>(s->total_slots, 1)));
     if (!s->undo) ok = false;
-    if (!ok) return fail(SBIEM_ERR_NOMEM, "adaptive run: snapshot allocation failed");
   }
+  if (!ok) return fail(SBIEM_ERR_NOMEM, "adaptive run: snapshot allocation failed");
   // m: a power of two in [1, 2^30]
   auto pow2_floor = [](int64_t v) {
     int64_t p = 1;
@@ -1607,6 +1616,12 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
   float best = 1e30f;
   int bshape = s->sweep_shape, bctas = 0;
   float bthr = s->gen_ds_max;
+  struct ShapeBest {
+    float ms, thr;
+    int ctas;
+  };
+  ShapeBest shape_best[5];
+  for (auto& x : shape_best) x = {1e30f, 0.0f, 0};
   for (int shape = 0; shape <= 4; ++shape) {
     if (sweep_chunk_slots(s->p.precision, shape) != s->chunk_slots) continue;
     for (float t : thr) {
@@ -1629,14 +1644,85 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
           if (k > 0) tm.push_back(ms);  // the first launch is untimed
         }
         std::sort(tm.begin(), tm.end());
-        if (tm[tm.size() / 2] < best) {
-          best = tm[tm.size() / 2];
+        const float med = tm[tm.size() / 2];
+        if (med < best) {
+          best = med;
           bshape = shape;
           bthr = t;
           bctas = c;
         }
+        if (med < shape_best[shape].ms) shape_best[shape] = {med, t, c};
       }
     }
+  }
+  // With the four-kernel passes (FP32, N > kFusedMaxN) the sweep that is
+  // fastest alone need not give the fastest step: at N = 65536 and 262144
+  // two two-stage CTAs per SM (shape 3) leave the passes room beside the
+  // next step's sweep (steps 0.271 and 1.113 ms, against 0.292 and 1.150 ms
+  // for four one-stage CTAs, the faster sweep alone).  So the best setting
+  // of each shape is timed over real overlapped steps, each undone after
+  // its timing (state snapshot and the overwritten ring slot restored), and
+  // the fastest step is kept.
+  if (s->fp32() && s->N > kFusedMaxN && s->nmodes > 0) {
+    bool ok = ensure_snapshot(s);
+    if (ok && !s->tune_slots) {
+      s->tune_slots = dev_alloc(s, sizeof(Slot32) * static_cast<size_t>(s->nmodes));
+      ok = s->tune_slots != nullptr;
+    }
+    if (!ok) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return nomem(s, "autotuner snapshot");
+    }
+    unsigned st0 = 0;
+    unsigned long long tot0[2] = {0ull, 0ull};
+    CK(cudaMemcpyAsync(&st0, s->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(tot0, s->f64.it_total, sizeof(tot0), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    float step_best = 1e30f;
+    int sb_shape = bshape, sb_ctas = bctas;
+    float sb_thr = bthr;
+    for (int shape = 0; shape <= 4; ++shape) {
+      if (shape_best[shape].ms >= 1e29f) continue;
+      int rc0 = sbiem_set_sweep(s, shape, shape_best[shape].thr, shape_best[shape].ctas);
+      if (rc0 == SBIEM_OK) rc0 = lag_graph(s, 1);
+      if (rc0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc0;
+      }
+      std::vector<float> tm;
+      for (int k = 0; k <= reps; ++k) {
+        int rcs = snapshot(s, true);
+        if (rcs) return rcs;
+        launch_slot_swap<float>(s->f32, s->tune_slots, 0, s->stream);
+        launch_history<float>(s->f32, 1, s->hist_grid, s->stream);  // this step's sums (the prologue)
+        CK(cudaEventRecord(e0, s->stream));
+        CK(cudaGraphLaunch(s->lag_graphs[1], s->stream));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        rcs = snapshot(s, false);
+        if (rcs) return rcs;
+        launch_slot_swap<float>(s->f32, s->tune_slots, 1, s->stream);
+        CK(cudaMemcpyAsync(s->f64.status, &st0, sizeof(unsigned), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (k > 0) tm.push_back(ms);
+      }
+      std::sort(tm.begin(), tm.end());
+      if (tm[tm.size() / 2] < step_best) {
+        step_best = tm[tm.size() / 2];
+        sb_shape = shape;
+        sb_thr = shape_best[shape].thr;
+        sb_ctas = shape_best[shape].ctas;
+      }
+    }
+    CK(cudaMemcpy(s->f64.it_total, tot0, sizeof(tot0), cudaMemcpyHostToDevice));
+    bshape = sb_shape;
+    bthr = sb_thr;
+    bctas = sb_ctas;
+    best = shape_best[bshape].ms;
   }
   int rc = sbiem_set_sweep(s, bshape, bthr, bctas);
   if (rc) {
@@ -1647,8 +1733,13 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
   // the overlapped step: the next step's sweep (into BT/BN) on the side
   // stream beside this step's two passes (their results stay staged), timed
   // together for 1 .. (occupancy limit) sweep CTAs per SM; nothing is
-  // committed, and the status word the passes may set is put back
-  {
+  // committed, and the status word the passes may set is put back.  Only
+  // where the passes are one-launch kernels that fit beside the sweep (FP32,
+  // N <= kFusedMaxN): with the four-kernel passes the full grid is best (per
+  // step, 3 against 4 CTAs per SM: 1.34 against 1.15 ms at N = 262144, 0.31
+  // against 0.27-0.29 ms at N = 65536), and this proxy, which leaves out the
+  // commit and the graph, picked 3 at N = 65536.
+  if (s->fp32() && s->N <= kFusedMaxN) {
     unsigned st0 = 0;
     CK(cudaMemcpyAsync(&st0, s->f64.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -1658,11 +1749,15 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
                               : sweep_blocks_per_sm<double>(s->lag_shape, false);
     float lbest = 1e30f;
     int lb = 0;
+    // nine timed launches at least: the candidates' totals are close (with
+    // five, the N = 65536 rough cycle's step came out at 0.27 or 0.31 ms
+    // from run to run)
+    const int reps_lag = std::max(reps, 9);
     for (int c = 1; c <= lim; ++c) {
       s->lag_ctas = c;
       sweep_config(s);
       std::vector<float> tm;
-      for (int k = 0; k <= reps; ++k) {
+      for (int k = 0; k <= reps_lag; ++k) {
         CK(cudaEventRecord(e0, s->stream));
         // in the order of the step graph (the sweep after the pass-1
         // spectral kernel has started)

@@ -2126,6 +2126,28 @@ __global__ void k_ring_undo(DevFault<R> f, int m_dt, Slot<R>* undo, int dir) {
   }
 }
 
+// The ring slot a step of one dt_min overwrites in each mode (the slot
+// before the head): saved into buf[n] (dir 0) or put back (dir 1), so that
+// a step taken only to time it can be undone with the state snapshot.
+template <class R>
+__global__ void k_slot_swap(DevFault<R> f, Slot<R>* buf, int dir) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= f.nmodes) return;
+  const int Rn = f.Rn[n];
+  if (Rn <= 0) return;
+  const int h = f.head[n];
+  Slot<R>* slot = f.ring + f.ring_off[n] + (h == 0 ? Rn - 1 : h - 1);
+  if (dir == 0) buf[n] = *slot;
+  else *slot = buf[n];
+}
+
+template <class R>
+void launch_slot_swap(const DevFault<R>& f, void* buf, int dir, cudaStream_t st) {
+  k_slot_swap<R><<<(f.nmodes + 255) / 256, 256, 0, st>>>(f, static_cast<Slot<R>*>(buf), dir);
+}
+template void launch_slot_swap<double>(const DevFault<double>&, void*, int, cudaStream_t);
+template void launch_slot_swap<float>(const DevFault<float>&, void*, int, cudaStream_t);
+
 // max_i |a_i - b_i| into *out (one block).
 __global__ void k_maxdiff(const double* a, const double* b, int n, double* out) {
   __shared__ double sh[32];

@@ -187,6 +187,9 @@ template <class R> void launch_history_persist(const DevFault<R>* fs, const Chun
                                                unsigned* bar_count, unsigned* bar_epoch, long long bar_limit,
                                                int members, bool ring_evict_first);
 template <class R> int persist_blocks_per_sm(int shape, bool gen);
+// Save (dir 0) or restore (dir 1) the ring slot of each mode that a step of
+// one dt_min overwrites (buf: nmodes slots).
+template <class R> void launch_slot_swap(const DevFault<R>& f, void* buf, int dir, cudaStream_t st);
 template <class R> void launch_pass_batch(const FftGeom& g, const DevFault<R>* fs, int members, int N, int pass,
                                           int m_dt, cudaStream_t st);
 template <class R> void launch_commit_batch(const DevFault<R>* fs, int members, int N, int m_dt, cudaStream_t st,

@@ -229,3 +229,37 @@ def test_closed_form_steady_modes_at_262144(precision):
         assert np.abs(s["delta"] - V * dt).max() <= 1e-12 * np.abs(V * dt).max()
         g.close()
         torch.cuda.empty_cache()
+
+
+def test_autotuner_undoes_its_timed_steps_at_32768():
+    # With the four-kernel passes (N > 16384) the autotuner also times real
+    # overlapped steps and undoes each (state snapshot, overwritten ring slot
+    # put back): the committed state and the history after tuning are those
+    # before, bitwise, and the tuned handle then steps bitwise like a fresh
+    # handle given the same history and the tuner's setting.
+    w = _workload(32768)
+    g = gpu_for(w, precision=1)
+    R = np.maximum(g.windows() - 1, 0)
+    from paper_2107_03550_gb300.workloads import random_history
+    HT, HN, _ = random_history(R, 29, 1e-5)
+    g.set_history(HT, HN)
+    s0 = g.get_state()
+    h0 = g.get_history()
+    choice = g.tune(reps=2)
+    s1 = g.get_state()
+    h1 = g.get_history()
+    for k in ("delta", "V", "theta", "t"):
+        assert np.array_equal(s0[k], s1[k]), k
+    for a, b in zip(h0, h1):
+        assert np.array_equal(a, b)
+    g2 = gpu_for(w, precision=1)
+    g2.set_history(HT, HN)
+    g2.set_sweep(choice["shape"], choice["gen_ds_max"], choice["ctas_per_sm"])
+    g.enqueue(3)
+    g2.enqueue(3)
+    assert g.status()[0] == 0 and g2.status()[0] == 0
+    a, b = g.get_state(), g2.get_state()
+    for k in ("delta", "V", "theta", "tau_el", "sigma_el"):
+        assert np.array_equal(a[k], b[k]), k
+    g.close()
+    g2.close()
