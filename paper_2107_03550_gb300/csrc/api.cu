@@ -1694,7 +1694,11 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
       std::vector<float> tm;
       for (int k = 0; k <= reps; ++k) {
         int rcs = snapshot(s, true);
-        if (rcs) return rcs;
+        if (rcs) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rcs;
+        }
         launch_slot_swap<float>(s->f32, s->tune_slots, 0, s->stream);
         launch_history<float>(s->f32, 1, s->hist_grid, s->stream);  // this step's sums (the prologue)
         CK(cudaEventRecord(e0, s->stream));
@@ -1702,7 +1706,11 @@ int sbiem_tune(sbiem_t s, int reps, int32_t* shape_out, double* gen_out, int32_t
         CK(cudaEventRecord(e1, s->stream));
         CK(cudaEventSynchronize(e1));
         rcs = snapshot(s, false);
-        if (rcs) return rcs;
+        if (rcs) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rcs;
+        }
         launch_slot_swap<float>(s->f32, s->tune_slots, 1, s->stream);
         CK(cudaMemcpyAsync(s->f64.status, &st0, sizeof(unsigned), cudaMemcpyHostToDevice, s->stream));
         CK(cudaStreamSynchronize(s->stream));
