@@ -413,6 +413,20 @@ def _flusher(torch):
     return flush
 
 
+def _max_over_ranks(torch, seconds: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (replicas: every rank runs its own fault; the job's time is the maximum)."""
+    if world <= 1:
+        return seconds
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(world: int, elements_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job element-steps/s: every rank's elements times the steps, over the slowest rank's time."""
+    return world * elements_per_rank * steps / seconds
+
+
 def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, clock_index: int, steps: int,
              extra=None, mlp=None):
     """Time `steps` steps (and as many history-only launches) back to back on one stream."""
@@ -472,12 +486,8 @@ def _measure(torch, a, kind, N, precision: str, rank: int, world: int, flush, cl
     ms_hist = [x.elapsed_time(y) for x, y in ev_h]
     ms_sweep = [x[0].elapsed_time(m) for x, m in zip(ev_h, ev_m)]
     it_sum, it_max = g.newton_stats()
-    total_s = sum(ms_step) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    return dict(g=g, w=w, N=N, value=world * N * K / total_s, ms_per_step=1e3 * total_s / K,
+    total_s = _max_over_ranks(torch, sum(ms_step) / 1e3, world)
+    return dict(g=g, w=w, N=N, value=_job_rate(world, N, K, total_s), ms_per_step=1e3 * total_s / K,
                 hist_ms=statistics.mean(ms_hist), sweep_ms=statistics.mean(ms_sweep),
                 sweep_ms_median=statistics.median(ms_sweep), hist_bytes=hist_bytes, ring_bytes=ring_bytes,
                 weight_bytes=hist_bytes - ring_bytes, dev_bytes=dev_bytes, clocks=clk, it_sum=it_sum,
@@ -546,8 +556,8 @@ def _e2e(torch, a, g, w, world):
     t0 = time.perf_counter()
     for _ in range(a.e2e_steps):
         g.step_host(tau_load=tau_np, V_out=v_np)
-    el = time.perf_counter() - t0
-    return {"value": N * a.e2e_steps / el * world, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+    el = _max_over_ranks(torch, time.perf_counter() - t0, world)
+    return {"value": _job_rate(world, N, a.e2e_steps, el), "unit": UNIT, "h2d_bytes_per_step": 8 * N,
             "d2h_bytes_per_step": 8 * N + 12}
 
 
@@ -641,15 +651,12 @@ def _ensemble(torch, a, rank, world, clock_index):
         raise RuntimeError("ensemble step (two-launch form) failed")
     two_s = e0.elapsed_time(e1) / 1e3 / K2
     b.set_persistent(info["persistent"])
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = _max_over_ranks(torch, total_s, world)
     bytes_ring = slots * (16 if a.precision == "fp32" else 32)
     peak, peak_kind = _peaks()
     traffic = _traffic_ensemble(a.precision, slots)
     line = {
-        "metric": METRIC, "value": world * elems * K / total_s, "unit": UNIT, "n_gpus": world, "steps": K,
+        "metric": METRIC, "value": _job_rate(world, elems, K, total_s), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": a.warmup, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/f64" if a.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": f"ensemble of {nm} rough-fault realizations: {nm // 4} each of N = 1024, 2048, "
